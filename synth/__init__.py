@@ -1,0 +1,308 @@
+"""Seeded synthetic inputs shared by the GPU library's tests/bench and the oracle.
+
+This module only *draws* inputs: template geometry (collision spheres, support
+polygons, static-world boxes, relation graphs), IK target poses and MLP
+training inputs. It holds none of the method's arithmetic (no sampling of
+poses, no distances, no kinematics). Every array is plain numpy so the same
+object feeds the FP64 oracle and the CUDA library.
+
+The paper's benchmark scenes are built from its own mesh assets (an apple, a
+banana in a drawer, a cabinet; Sec. V-A), which are not available; the shapes
+below stand in for them with the sizes of the tabletop/shelf workloads:
+
+  * tabletop:  1 template, 1.2 x 0.8 m table at z = 0.75, 8 objects x 16 spheres,
+               all free, B = 1024 candidates (seed 0).
+  * shelf:     1 template, 32 objects x 64 spheres, 25% on-top / 25% next-to /
+               50% free, 20 random OBBs, B = 65,536 (seed 1).
+  * ragged:    4096 templates, 4..64 objects, 8..128 spheres per object, convex
+               4..10-gon supports of area 0.5..2 m^2, 64 candidates each (seed 2).
+
+Object assets: sphere centres uniform in a local box of per-axis half extent
+U(0.05, 0.15) m, radii U(0.01, 0.05) m; the object frame is then moved to the
+centre of the spheres' tight axis-aligned bounding box, whose half extents
+(Hx, Hy, Hz) and xy bounding radius rho are part of the asset description.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+REL_FREE, REL_ON_TOP, REL_NEXT_TO = 0, 1, 2
+REL_REACH = 0x10
+
+# 7-DoF arm used by the reachability workload: standard DH parameters.
+ARM_D = (0.333, 0.0, 0.316, 0.0, 0.384, 0.0, 0.107)
+ARM_A = (0.0, 0.0, 0.0, 0.0825, -0.0825, 0.0, 0.088)
+ARM_ALPHA = (0.0, -math.pi / 2, math.pi / 2, math.pi / 2, -math.pi / 2, math.pi / 2, math.pi / 2)
+ARM_QLIM = 2.8
+
+
+@dataclasses.dataclass
+class SceneBatch:
+    """CSR-packed scene templates plus candidate ranges (host numpy arrays).
+
+    Layouts (all little-endian, C-contiguous):
+      tmpl_obj_off  int32 [T+1]  objects of template t are [off[t], off[t+1])
+      obj_sph_off   int32 [O+1]  spheres of object o
+      sph_local     f32 [S,4]    (x, y, z, r) in the object frame
+      obj_half      f32 [O,4]    (Hx, Hy, Hz, rho_xy)
+      obj_rel       int32 [O]    kind | REL_REACH flag | (reference local index << 8)
+      obj_rel_param f32 [O,4]    (dmin, dmax, ratio_on_support, 0)
+      tmpl_poly_off int32 [T+1]; poly_verts f32 [V,2] (CCW)
+      tmpl_support_z f32 [T]
+      tmpl_obb_off  int32 [T+1]; obb f32 [n_obb,12] centre(x,y,z,0) quat(x,y,z,w) half(x,y,z,0)
+      cand_tmpl_off int32 [T+1]  candidates of template t
+      tmpl_base     f32 [T,4]    robot base (x, y, z, yaw)
+    """
+
+    tmpl_obj_off: np.ndarray
+    obj_sph_off: np.ndarray
+    sph_local: np.ndarray
+    obj_half: np.ndarray
+    obj_rel: np.ndarray
+    obj_rel_param: np.ndarray
+    tmpl_poly_off: np.ndarray
+    poly_verts: np.ndarray
+    tmpl_support_z: np.ndarray
+    tmpl_obb_off: np.ndarray
+    obb: np.ndarray
+    cand_tmpl_off: np.ndarray
+    tmpl_base: np.ndarray
+    name: str = ""
+
+    @property
+    def n_templates(self) -> int:
+        return len(self.tmpl_obj_off) - 1
+
+    @property
+    def n_objects(self) -> int:
+        return len(self.obj_half)
+
+    @property
+    def n_spheres(self) -> int:
+        return len(self.sph_local)
+
+    @property
+    def n_cand(self) -> int:
+        return int(self.cand_tmpl_off[-1])
+
+    def n_obj_of(self, t: int) -> int:
+        return int(self.tmpl_obj_off[t + 1] - self.tmpl_obj_off[t])
+
+    def cand_template(self) -> np.ndarray:
+        """Template index of every candidate (int32 [B])."""
+        counts = np.diff(self.cand_tmpl_off)
+        return np.repeat(np.arange(self.n_templates, dtype=np.int32), counts)
+
+    def tmpl_pose_off(self) -> np.ndarray:
+        """Start of each template's block in the CSR pose array (int64 [T+1]):
+        template t holds n_cand(t) x n_obj(t) poses, candidate-major."""
+        sizes = np.diff(self.cand_tmpl_off).astype(np.int64) * np.diff(self.tmpl_obj_off).astype(np.int64)
+        return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+    def n_poses(self) -> int:
+        return int(self.tmpl_pose_off()[-1])
+
+    def sphere_count_of_template(self) -> np.ndarray:
+        return (self.obj_sph_off[self.tmpl_obj_off[1:]] - self.obj_sph_off[self.tmpl_obj_off[:-1]]).astype(np.int64)
+
+    def subset(self, templates) -> "SceneBatch":
+        """A batch made of the listed templates (their candidates keep their count)."""
+        templates = list(templates)
+        parts = []
+        for t in templates:
+            o0, o1 = int(self.tmpl_obj_off[t]), int(self.tmpl_obj_off[t + 1])
+            s0, s1 = int(self.obj_sph_off[o0]), int(self.obj_sph_off[o1])
+            v0, v1 = int(self.tmpl_poly_off[t]), int(self.tmpl_poly_off[t + 1])
+            b0, b1 = int(self.tmpl_obb_off[t]), int(self.tmpl_obb_off[t + 1])
+            parts.append(dict(
+                sph=self.sph_local[s0:s1], nsph=np.diff(self.obj_sph_off[o0:o1 + 1]),
+                half=self.obj_half[o0:o1], rel=self.obj_rel[o0:o1], relp=self.obj_rel_param[o0:o1],
+                poly=self.poly_verts[v0:v1], z=self.tmpl_support_z[t], obb=self.obb[b0:b1],
+                ncand=int(self.cand_tmpl_off[t + 1] - self.cand_tmpl_off[t]), base=self.tmpl_base[t]))
+        return _pack(parts, name=f"{self.name}[subset {len(templates)}]")
+
+
+def _pack(parts, name="") -> SceneBatch:
+    def off(counts):
+        return np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+
+    nobj = [len(p["half"]) for p in parts]
+    nsph = np.concatenate([p["nsph"] for p in parts]).astype(np.int64)
+    return SceneBatch(
+        tmpl_obj_off=off(nobj),
+        obj_sph_off=off(nsph),
+        sph_local=np.ascontiguousarray(np.concatenate([p["sph"] for p in parts]).astype(np.float32)),
+        obj_half=np.ascontiguousarray(np.concatenate([p["half"] for p in parts]).astype(np.float32)),
+        obj_rel=np.ascontiguousarray(np.concatenate([p["rel"] for p in parts]).astype(np.int32)),
+        obj_rel_param=np.ascontiguousarray(np.concatenate([p["relp"] for p in parts]).astype(np.float32)),
+        tmpl_poly_off=off([len(p["poly"]) for p in parts]),
+        poly_verts=np.ascontiguousarray(np.concatenate([p["poly"] for p in parts]).astype(np.float32)),
+        tmpl_support_z=np.array([p["z"] for p in parts], dtype=np.float32),
+        tmpl_obb_off=off([len(p["obb"]) for p in parts]),
+        obb=np.ascontiguousarray(np.concatenate([p["obb"] for p in parts]).astype(np.float32).reshape(-1, 12)),
+        cand_tmpl_off=off([p["ncand"] for p in parts]),
+        tmpl_base=np.ascontiguousarray(np.array([p["base"] for p in parts], dtype=np.float32).reshape(-1, 4)),
+        name=name,
+    )
+
+
+def draw_object(rng: np.random.Generator, n_spheres: int):
+    """One object asset: (spheres [n,4] in the AABB-centred frame, half extents (Hx,Hy,Hz), rho)."""
+    h = rng.uniform(0.05, 0.15, size=3)
+    c = rng.uniform(-h, h, size=(n_spheres, 3))
+    r = rng.uniform(0.01, 0.05, size=n_spheres)
+    lo = (c - r[:, None]).min(axis=0)
+    hi = (c + r[:, None]).max(axis=0)
+    centre = 0.5 * (lo + hi)
+    half = 0.5 * (hi - lo)
+    c = c - centre
+    # asset description: xy bounding radius of the sphere set in its own frame
+    rho = float(np.max(np.hypot(c[:, 0], c[:, 1]) + r))
+    sph = np.concatenate([c, r[:, None]], axis=1).astype(np.float32)
+    return sph, half.astype(np.float32), np.float32(rho)
+
+
+def draw_relations(rng: np.random.Generator, n: int, n_reach: int = 0):
+    """Relation kinds and reference objects: object 0 free; round(n/4) on-top and
+    round(n/4) next-to objects chosen by a random permutation of 1..n-1; each
+    refers to a uniformly random earlier object. The first n_reach objects carry
+    the reachability flag."""
+    kinds = np.zeros(n, dtype=np.int32)
+    refs = np.zeros(n, dtype=np.int32)
+    q = int(math.floor(0.25 * n + 0.5))
+    perm = rng.permutation(np.arange(1, n))
+    kinds[perm[:q]] = REL_ON_TOP
+    kinds[perm[q:2 * q]] = REL_NEXT_TO
+    for k in range(1, n):
+        if kinds[k] != REL_FREE:
+            refs[k] = rng.integers(0, k)
+    rel = kinds | (refs << 8)
+    rel[: min(n_reach, n)] |= REL_REACH
+    return rel.astype(np.int32)
+
+
+def rect_polygon(lx: float, ly: float) -> np.ndarray:
+    return np.array([[-lx / 2, -ly / 2], [lx / 2, -ly / 2], [lx / 2, ly / 2], [-lx / 2, ly / 2]], dtype=np.float32)
+
+
+def convex_polygon(rng: np.random.Generator, n_verts: int, area: float) -> np.ndarray:
+    """Convex CCW n-gon: sorted uniform angles on the unit circle, scaled to `area`."""
+    ang = np.sort(rng.uniform(0.0, 2 * math.pi, size=n_verts))
+    v = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    x, y = v[:, 0], v[:, 1]
+    a0 = 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
+    return (v * math.sqrt(area / a0)).astype(np.float32)
+
+
+def random_obbs(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Shelf-like static world: centres uniform in [-1.2,1.2]x[-1,1]x[0,2] m,
+    uniformly random rotations (Shoemake's subgroup algorithm), sides U(0.02, 1.0) m."""
+    out = np.zeros((n, 12), dtype=np.float64)
+    out[:, 0] = rng.uniform(-1.2, 1.2, n)
+    out[:, 1] = rng.uniform(-1.0, 1.0, n)
+    out[:, 2] = rng.uniform(0.0, 2.0, n)
+    u1, u2, u3 = rng.uniform(size=(3, n))
+    out[:, 4] = np.sqrt(1 - u1) * np.sin(2 * math.pi * u2)
+    out[:, 5] = np.sqrt(1 - u1) * np.cos(2 * math.pi * u2)
+    out[:, 6] = np.sqrt(u1) * np.sin(2 * math.pi * u3)
+    out[:, 7] = np.sqrt(u1) * np.cos(2 * math.pi * u3)
+    out[:, 8:11] = 0.5 * rng.uniform(0.02, 1.0, size=(n, 3))
+    return out.astype(np.float32)
+
+
+def make_template(rng, n_obj, sph_counts, poly, support_z=0.75, n_obb=0, relations=True, n_reach=0,
+                  ratio_on_support=0.0, base=None):
+    sph, nsph, half = [], [], []
+    for k in range(n_obj):
+        s, h, rho = draw_object(rng, int(sph_counts[k]))
+        sph.append(s)
+        nsph.append(len(s))
+        half.append([h[0], h[1], h[2], rho])
+    if relations:
+        rel = draw_relations(rng, n_obj, n_reach)
+    else:
+        rel = np.zeros(n_obj, dtype=np.int32)
+        rel[: min(n_reach, n_obj)] |= REL_REACH
+    relp = np.tile(np.array([0.05, 0.2, ratio_on_support, 0.0], dtype=np.float32), (n_obj, 1))
+    obb = random_obbs(rng, n_obb) if n_obb else np.zeros((0, 12), np.float32)
+    if base is None:  # robot at the middle of the support's -x side, facing +x
+        base = [float(poly[:, 0].min()), 0.0, support_z, 0.0]
+    return dict(sph=np.concatenate(sph), nsph=np.array(nsph), half=np.array(half, np.float32), rel=rel, relp=relp,
+                poly=poly, z=support_z, obb=obb, base=np.array(base, np.float32))
+
+
+def tabletop(seed: int = 0, n_cand: int = 1024, n_obj: int = 8, n_sph: int = 16) -> SceneBatch:
+    """Small tabletop workload: 1.2 x 0.8 m table, 8 free objects x 16 spheres."""
+    rng = np.random.default_rng(seed)
+    p = make_template(rng, n_obj, [n_sph] * n_obj, rect_polygon(1.2, 0.8), relations=False, n_reach=4,
+                      base=[-0.6, 0.0, 0.75, 0.0])
+    p["ncand"] = n_cand
+    return _pack([p], name=f"tabletop {n_obj}x{n_sph} B={n_cand}")
+
+
+def shelf(seed: int = 1, n_cand: int = 65536, n_obj: int = 32, n_sph: int = 64, n_obb: int = 20) -> SceneBatch:
+    """Shelf workload: 32 objects x 64 spheres with relations, 20 random OBBs."""
+    rng = np.random.default_rng(seed)
+    p = make_template(rng, n_obj, [n_sph] * n_obj, rect_polygon(1.2, 0.8), n_obb=n_obb, n_reach=4,
+                      base=[-0.6, 0.0, 0.75, 0.0])
+    p["ncand"] = n_cand
+    return _pack([p], name=f"shelf {n_obj}x{n_sph} obb={n_obb} B={n_cand}")
+
+
+def ragged(seed: int = 2, n_templates: int = 4096, cand_per_template: int = 64, obj_range=(4, 64),
+           sph_range=(8, 128), n_reach: int = 4) -> SceneBatch:
+    """Ragged workload: many templates with uneven object and sphere counts."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_templates):
+        n = int(rng.integers(obj_range[0], obj_range[1] + 1))
+        counts = rng.integers(sph_range[0], sph_range[1] + 1, size=n)
+        poly = convex_polygon(rng, int(rng.integers(4, 11)), float(rng.uniform(0.5, 2.0)))
+        p = make_template(rng, n, counts, poly, n_reach=n_reach)
+        p["ncand"] = cand_per_template
+        parts.append(p)
+    return _pack(parts, name=f"ragged T={n_templates}x{cand_per_template}")
+
+
+def random_poses(batch: SceneBatch, seed: int, spread: float = 0.6) -> np.ndarray:
+    """Arbitrary object poses (float32 [P,4]: x, y, z, yaw) for exercising the
+    collision check on its own: xy uniform in [-spread, spread]^2 around the
+    support, z = support + U(0, 0.3), yaw U(0, 2pi)."""
+    rng = np.random.default_rng(seed)
+    n = batch.n_poses()
+    p = np.empty((n, 4), dtype=np.float64)
+    p[:, 0] = rng.uniform(-spread, spread, n)
+    p[:, 1] = rng.uniform(-spread, spread, n)
+    zs = np.repeat(batch.tmpl_support_z.astype(np.float64), np.diff(batch.tmpl_pose_off()))
+    p[:, 2] = zs + rng.uniform(0.0, 0.3, n)
+    p[:, 3] = rng.uniform(0.0, 2 * math.pi, n)
+    return p.astype(np.float32)
+
+
+def topdown_targets(seed: int, n: int, box=((0.0, 1.2), (-0.4, 0.4), (0.02, 0.5))) -> np.ndarray:
+    """Top-down grasp targets in the robot base frame (float32 [n,12]: R row-major, p).
+
+    Positions are uniform in `box` (metres, base frame; the default covers a
+    1.2 x 0.8 m table whose near edge holds the robot, heights from a resting
+    object's top up to a stacked one). The tool z axis points down, the tool x
+    axis is at a uniform yaw psi: columns x = (cos, sin, 0), y = (sin, -cos, 0),
+    z = (0, 0, -1)."""
+    rng = np.random.default_rng(seed)
+    t = np.zeros((n, 12), dtype=np.float64)
+    psi = rng.uniform(0.0, 2 * math.pi, n)
+    c, s = np.cos(psi), np.sin(psi)
+    t[:, 0], t[:, 1], t[:, 2] = c, s, 0.0
+    t[:, 3], t[:, 4], t[:, 5] = s, -c, 0.0
+    t[:, 6], t[:, 7], t[:, 8] = 0.0, 0.0, -1.0
+    for i, (lo, hi) in enumerate(box):
+        t[:, 9 + i] = rng.uniform(lo, hi, n)
+    return t.astype(np.float32)
+
+
+def arm_arrays():
+    """(d, a, alpha, qmin, qmax) float32 arrays of the 7-DoF arm."""
+    f = lambda v: np.array(v, dtype=np.float32)
+    return f(ARM_D), f(ARM_A), f(ARM_ALPHA), f([-ARM_QLIM] * 7), f([ARM_QLIM] * 7)

@@ -1,0 +1,564 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the value: a closed form, a library routine written
+by someone else (numpy's Philox4x64, scipy's rotations, torch's bfloat16
+conversion, numpy.linalg), an invariance, or brute force on hand-made cases.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy import stats
+
+import oracle
+import synth
+from oracle import mlp
+
+# --------------------------------------------------------------------------- Philox
+
+
+@pytest.mark.parametrize("key,ctr", [((0, 0), (0, 0, 0, 0)), ((123, 456), (7, 8, 9, 10)),
+                                     ((2**64 - 1, 2**63), (2**64 - 2, 5, 6, 7)), ((1, 2), (2**64 - 1, 0, 0, 0))])
+def test_philox4x64_matches_numpy(key, ctr):
+    """numpy.random.Philox is Philox4x64-10 and encrypts counter+1 for its first
+    block. The oracle's 4x64 instance shares the round, permutation and key
+    schedule code with the 4x32 instance the sampler uses."""
+    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(ctr, dtype=np.uint64))
+    raw = [int(x) for x in g.random_raw(8)]
+    c = list(ctr)
+    outs = []
+    for _ in range(2):
+        c[0] = (c[0] + 1) % 2**64
+        if c[0] == 0:
+            c[1] = (c[1] + 1) % 2**64
+        outs += [int(x) for x in oracle.philox4x64(c, key)]
+    assert raw == outs
+
+
+def test_philox4x32_statistics():
+    """Uniformity (chi^2 on the top byte of every word), full avalanche on a
+    one-bit counter change and on a one-bit key change."""
+    n = 20000
+    words = np.array([oracle.philox4x32([i, 0, 0, 0], [17, 0]) for i in range(n)], dtype=np.uint32)
+    top = (words >> 24).ravel()
+    chi2, p = stats.chisquare(np.bincount(top, minlength=256))
+    assert p > 1e-4, p
+    rng = np.random.default_rng(5)
+    flips = []
+    for _ in range(400):
+        ctr = rng.integers(0, 2**32, 4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2**32, 2, dtype=np.uint64).astype(np.uint32)
+        a = oracle.philox4x32(ctr, key)
+        c2 = ctr.copy(); c2[rng.integers(4)] ^= np.uint32(1 << int(rng.integers(32)))
+        k2 = key.copy(); k2[rng.integers(2)] ^= np.uint32(1 << int(rng.integers(32)))
+        for b in (oracle.philox4x32(c2, key), oracle.philox4x32(ctr, k2)):
+            flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)) / 128.0)
+    assert abs(np.mean(flips) - 0.5) < 0.01
+    assert min(flips) > 0.25
+
+
+def test_uniform_is_top_24_bits():
+    """u = (x >> 8) 2^-24: a multiple of 2^-24 in [0, 1), same bits as the word."""
+    seed = 0x123456789ABCDEF
+    w = oracle.philox4x32([3, 1, 2, 5], [seed & 0xFFFFFFFF, seed >> 32])
+    u = oracle.uniform4(seed, 3, 1, 2, 5)
+    assert np.all(u * 2**24 == (w >> 8).astype(np.float64))
+    assert np.all((u >= 0) & (u < 1))
+
+
+# --------------------------------------------------------------------------- point in polygon
+
+SQUARE = [(0, 0), (1, 0), (1, 1), (0, 1)]
+L_SHAPE = [(0, 0), (2, 0), (2, 1), (1, 1), (1, 2), (0, 2)]
+
+
+@pytest.mark.parametrize("poly", [SQUARE, SQUARE[::-1]])
+@pytest.mark.parametrize("p,inside,dist", [((0.5, 0.5), True, 0.5), ((1.5, 0.5), False, 0.5), ((1.0, 0.5), True, 0.0),
+                                           ((0.0, 0.0), True, 0.0), ((-1, -1), False, math.sqrt(2)),
+                                           ((-0.5, 0.0), False, 0.5), ((0.9, 0.2), True, 0.1)])
+def test_pip_square(poly, p, inside, dist):
+    got_in, got_d = oracle.point_in_polygon(poly, p)
+    assert got_in == inside
+    assert got_d == pytest.approx(dist, abs=1e-12)
+
+
+@pytest.mark.parametrize("poly", [L_SHAPE, L_SHAPE[::-1]])
+@pytest.mark.parametrize("p,inside,dist", [((1.5, 1.5), False, 0.5), ((0.5, 1.5), True, 0.5), ((1.5, 0.5), True, 0.5),
+                                           ((1.2, 1.1), False, 0.1), ((0.5, 1.0), True, 0.5), ((3.0, 1.0), False, 1.0),
+                                           ((1.0, 1.5), True, 0.0)])
+def test_pip_concave(poly, p, inside, dist):
+    got_in, got_d = oracle.point_in_polygon(poly, p)
+    assert got_in == inside
+    assert got_d == pytest.approx(dist, abs=1e-12)
+
+
+def test_pip_random_convex_against_halfplanes():
+    """For a convex CCW polygon, inside <=> left of (or on) every edge line;
+    an independent test from the crossing-number walk."""
+    rng = np.random.default_rng(0)
+    poly = synth.convex_polygon(rng, 7, 1.3).astype(np.float64)
+    for _ in range(2000):
+        p = rng.uniform(-1, 1, 2)
+        e = np.roll(poly, -1, axis=0) - poly
+        cross = e[:, 0] * (p[1] - poly[:, 1]) - e[:, 1] * (p[0] - poly[:, 0])
+        got, d = oracle.point_in_polygon(poly, p)
+        assert got == bool(np.all(cross >= 0))
+        if got:  # distance to the boundary of a convex polygon = min distance to edge lines
+            assert d == pytest.approx(np.min(cross / np.hypot(e[:, 0], e[:, 1])), abs=1e-12)
+
+
+# --------------------------------------------------------------------------- distances
+
+
+def test_sphere_sphere_closed_form():
+    """Two spheres of radius r at centre distance D: d = D - 2r; collide iff D < 2r."""
+    r = 0.03
+    for D in np.linspace(0.0, 0.2, 41):
+        a = [0.1, -0.2, 0.7, r]
+        b = [0.1 + D * 0.6, -0.2 + D * 0.8, 0.7, r]
+        d = oracle.sphere_sphere(a, b)
+        assert d == pytest.approx(D - 2 * r, abs=1e-15)
+        assert oracle.sphere_sphere(b, a) == d
+        if abs(D - 2 * r) > 1e-12:  # exact contact is a band case
+            assert (d < 0) == (D < 2 * r)
+
+
+BOX_C, BOX_H = (1.0, 2.0, 3.0), (0.5, 1.0, 2.0)
+
+
+def _box(centre=BOX_C, quat=(0, 0, 0, 1), half=BOX_H):
+    return np.array([*centre, 0, *quat, *half, 0], dtype=np.float32)
+
+
+@pytest.mark.parametrize("p,expect", [
+    ((1.8, 2.0, 3.0), 0.3),                                        # face
+    ((1.8, 3.4, 3.0), 0.5),                                        # edge (0.3, 0.4)
+    ((1.5 + 0.1, 3.0 + 0.2, 5.0 + 0.2), math.sqrt(0.09)),          # corner (0.1, 0.2, 0.2)
+    ((1.2, 2.0, 3.0), -0.3),                                       # interior: nearest face 0.3 away
+    ((1.0, 2.0, 3.0), -0.5),                                       # centre
+    ((1.0, 2.9, 3.0), -0.1),                                       # interior near the y face
+])
+def test_sphere_obb_closed_forms(p, expect):
+    r = 0.05
+    assert oracle.sphere_obb([*p, r], _box()) == pytest.approx(expect - r, abs=1e-6)
+
+
+def test_sphere_obb_rotation_invariance_and_quat_scale():
+    """Rotating box and sphere together about the box centre leaves d unchanged;
+    the quaternion is normalised (a scaled quaternion gives the same box)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        R = Rotation.random(random_state=rng)
+        q = R.as_quat()  # (x, y, z, w)
+        local = rng.uniform(-3, 3, 3)
+        r = rng.uniform(0.0, 0.1)
+        d_axis = oracle.sphere_obb([*(np.array(BOX_C) + local), r], _box())
+        world = np.array(BOX_C) + R.apply(local)
+        box = _box(quat=tuple(q))
+        d_rot = oracle.sphere_obb([*world, r], box)
+        assert d_rot == pytest.approx(d_axis, abs=2e-6)  # float32 quaternion storage
+        box2 = _box(quat=tuple(2.5 * q))
+        assert oracle.sphere_obb([*world, r], box2) == pytest.approx(d_rot, abs=2e-6)
+
+
+def test_sphere_world_yaw():
+    """Yaw pi/2 maps the local (x, y) to (-y, x); z is shifted, r kept."""
+    w = oracle.sphere_world([0.1, 0.2, 0.3, 0.04], [1.0, 2.0, 3.0, math.pi / 2])
+    assert np.allclose(w, [1.0 - 0.2, 2.0 + 0.1, 3.3, 0.04], atol=1e-7)
+
+
+# --------------------------------------------------------------------------- collision on hand-made scenes
+
+
+def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_cand=1, rel=None):
+    """objects: list of sphere lists [(x,y,z,r), ...] in object frames."""
+    parts = dict(
+        sph=np.array([s for o in objects for s in o], np.float32), nsph=np.array([len(o) for o in objects]),
+        half=np.array([[0.1, 0.1, 0.1, 0.15]] * len(objects), np.float32),
+        rel=np.zeros(len(objects), np.int32) if rel is None else np.array(rel, np.int32),
+        relp=np.tile(np.array([0.05, 0.2, 0.0, 0.0], np.float32), (len(objects), 1)),
+        poly=np.array(poly, np.float32), z=0.0, obb=np.array(obbs, np.float32).reshape(-1, 12), ncand=n_cand,
+        base=np.zeros(4, np.float32))
+    return synth._pack([parts])
+
+
+def test_collide_brute_force_tiny():
+    """(Radii are stored as float32, hence 1e-7.) Three one/two-sphere objects at hand-placed poses; every pair distance
+    computed by hand: objects 0-1: centres 0.5 apart, radii 0.1+0.1 -> 0.3;
+    0-2: centres 0.25 apart -> 0.05 (second sphere of object 2 at 0.25+0.1
+    in x); 1-2: far."""
+    b = tiny_batch([[(0, 0, 0, 0.1)], [(0, 0, 0, 0.1)], [(0, 0, 0, 0.1), (0.1, 0, 0, 0.1)]])
+    poses = np.array([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.45, 0, 0]], np.float64)
+    col, md, band = oracle.collide(b, poses)
+    # 0-2: sphere (0,0.45) vs (0,0): 0.45-0.2 = 0.25; sphere (0.1,0.45) vs (0,0): sqrt(0.01+0.2025)-0.2
+    d02 = min(0.25, math.sqrt(0.01 + 0.2025) - 0.2)
+    d12 = min(math.hypot(0.5, 0.45) - 0.2, math.hypot(0.4, 0.45) - 0.2)
+    assert md[0] == pytest.approx(min(0.3, d02, d12), abs=1e-7)
+    assert col[0] == 0
+    # first_new = 2: only pairs with object 2
+    _, md2, _ = oracle.collide(b, poses, first_new=2)
+    assert md2[0] == pytest.approx(min(d02, d12), abs=1e-7)
+    # first_new = 3: nothing new -> +FLT_MAX
+    _, md3, _ = oracle.collide(b, poses, first_new=3)
+    assert md3[0] == pytest.approx(np.finfo(np.float32).max)
+    # yaw pi of object 2 moves its second sphere to x = -0.1
+    poses[2, 3] = math.pi
+    _, md4, _ = oracle.collide(b, poses, first_new=2)
+    assert md4[0] == pytest.approx(min(0.25, math.hypot(0.5, 0.45) - 0.2, math.hypot(0.6, 0.45) - 0.2), abs=1e-7)
+
+
+def test_collide_touching_is_free_and_overlap_collides():
+    b = tiny_batch([[(0, 0, 0, 0.125)], [(0, 0, 0, 0.125)]])
+    col, md, band = oracle.collide(b, np.array([[0, 0, 0, 0], [0.25, 0, 0, 0]], np.float64))
+    assert md[0] == 0.0 and col[0] == 0 and band[0] == 1
+    col, md, band = oracle.collide(b, np.array([[0, 0, 0, 0], [0.2, 0, 0, 0]], np.float64))
+    assert md[0] == pytest.approx(-0.05) and col[0] == 1 and band[0] == 0
+
+
+def test_collide_world_only_and_intra_object_ignored():
+    """Spheres of one object overlapping each other never count; a sphere
+    inside a world box does."""
+    b = tiny_batch([[(0, 0, 0, 0.1), (0.05, 0, 0, 0.1)]], obbs=[[3, 0, 0, 0, 0, 0, 0, 1, 0.5, 0.5, 0.5, 0]])
+    col, md, _ = oracle.collide(b, np.array([[0, 0, 0, 0]], np.float64))
+    assert md[0] == pytest.approx(2.5 - 0.05 - 0.1, abs=1e-7) and col[0] == 0
+    col, md, _ = oracle.collide(b, np.array([[2.9, 0, 0, 0]], np.float64))
+    assert md[0] == pytest.approx(-(0.5 - 0.05) - 0.1, abs=1e-6) and col[0] == 1
+
+
+def _shelf_small(n_cand=6, n_obj=6, n_sph=5, n_obb=4, seed=11):
+    return synth.shelf(seed=seed, n_cand=n_cand, n_obj=n_obj, n_sph=n_sph, n_obb=n_obb)
+
+
+def test_collide_rigid_motion_invariance():
+    """A global yaw psi and translation applied to every object pose and world
+    box leaves every signed distance unchanged (up to float32 input storage)."""
+    b = _shelf_small()
+    poses = synth.random_poses(b, seed=3, spread=0.5).astype(np.float64)
+    col, md, _ = oracle.collide(b, poses)
+    psi, t = 0.7, np.array([0.3, -0.2, 0.1])
+    c, s = math.cos(psi), math.sin(psi)
+    p2 = poses.copy()
+    p2[:, 0] = c * poses[:, 0] - s * poses[:, 1] + t[0]
+    p2[:, 1] = s * poses[:, 0] + c * poses[:, 1] + t[1]
+    p2[:, 2] = poses[:, 2] + t[2]
+    p2[:, 3] = poses[:, 3] + psi
+    obb = b.obb.astype(np.float64).copy()
+    obb[:, 0] = c * b.obb[:, 0] - s * b.obb[:, 1] + t[0]
+    obb[:, 1] = s * b.obb[:, 0] + c * b.obb[:, 1] + t[1]
+    obb[:, 2] = b.obb[:, 2] + t[2]
+    q = (Rotation.from_euler("z", psi) * Rotation.from_quat(b.obb[:, 4:8].astype(np.float64))).as_quat()
+    obb[:, 4:8] = q
+    import dataclasses
+    b2 = dataclasses.replace(b, obb=obb.astype(np.float32))
+    col2, md2, _ = oracle.collide(b2, p2)
+    assert np.allclose(md, md2, atol=2e-6)
+    assert np.array_equal(col[np.abs(md) > 1e-5], col2[np.abs(md) > 1e-5])
+
+
+def test_collide_object_relabelling_invariance():
+    """Whole-scene minimum distance does not depend on the object order."""
+    b = _shelf_small(n_obb=0)
+    poses = synth.random_poses(b, seed=4, spread=0.4).astype(np.float64)
+    _, md, _ = oracle.collide(b, poses)
+    n_obj = b.n_obj_of(0)
+    perm = np.random.default_rng(0).permutation(n_obj)
+    spheres = [b.sph_local[b.obj_sph_off[o]:b.obj_sph_off[o + 1]] for o in range(n_obj)]
+    b2 = tiny_batch([spheres[k].tolist() for k in perm], n_cand=b.n_cand)
+    p2 = poses.reshape(b.n_cand, n_obj, 4)[:, perm].reshape(-1, 4)
+    _, md2, _ = oracle.collide(b2, p2)
+    assert np.allclose(md, md2, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- sampler
+
+
+def test_free_samples_uniform_on_table():
+    """Free objects on the 1.2 x 0.8 table: x, y, yaw uniform (KS); z = table + Hz."""
+    b = synth.tabletop(seed=0, n_cand=4000)
+    P, ok, band = oracle.sample_poses(b, seed=9)
+    assert ok.all()
+    P = P.reshape(4000, 8, 4)
+    for k in range(8):
+        assert stats.kstest(P[:, k, 0], stats.uniform(-0.6, 1.2).cdf).pvalue > 1e-4
+        assert stats.kstest(P[:, k, 1], stats.uniform(-0.4, 0.8).cdf).pvalue > 1e-4
+        assert stats.kstest(P[:, k, 3], stats.uniform(0, 2 * math.pi).cdf).pvalue > 1e-4
+        assert np.allclose(P[:, k, 2], 0.75 + b.obj_half[k, 2], atol=1e-7)
+    # the same counters give the same poses; another retry index gives others
+    P2, _, _ = oracle.sample_poses(b, seed=9)
+    assert np.array_equal(P.reshape(-1, 4), P2)
+    P3, _, _ = oracle.sample_poses(b, seed=9, retry=1)
+    assert not np.any(P3[:, 0] == P.reshape(-1, 4)[:, 0])
+
+
+def test_convex_support_samples_inside_and_uniform():
+    """Accepted xy lie in the polygon (half-plane test), and the fraction on
+    each side of a line through the polygon matches the area fraction."""
+    rng = np.random.default_rng(4)
+    poly = synth.convex_polygon(rng, 6, 1.0)
+    b = tiny_batch([[(0, 0, 0, 0.02)]], poly=poly, n_cand=6000)
+    P, ok, band = oracle.sample_poses(b, seed=2)
+    assert ok.mean() > 0.999
+    xy = P[ok.astype(bool), :2]
+    e = np.roll(poly, -1, axis=0) - poly
+    cross = e[None, :, 0] * (xy[:, None, 1] - poly[None, :, 1]) - e[None, :, 1] * (xy[:, None, 0] - poly[None, :, 0])
+    assert np.all(cross >= -1e-12)
+    # area left of x = 0 by shoelace on the clipped polygon, via dense grid estimate
+    gx, gy = np.meshgrid(np.linspace(-1.5, 1.5, 1201), np.linspace(-1.5, 1.5, 1201))
+    g = np.stack([gx.ravel(), gy.ravel()], 1)
+    gc = e[None, :, 0] * (g[:, None, 1] - poly[None, :, 1]) - e[None, :, 1] * (g[:, None, 0] - poly[None, :, 0])
+    inside = np.all(gc >= 0, axis=1)
+    frac = np.mean(g[inside, 0] < 0)
+    n = len(xy)
+    assert abs(np.mean(xy[:, 0] < 0) - frac) < 4 * math.sqrt(frac * (1 - frac) / n) + 0.005
+
+
+def test_erosion_ratio_on_support():
+    """ratio_on_support = 1 keeps the pivot at least min(Hx, Hy) inside the table edge."""
+    b = synth.tabletop(seed=0, n_cand=500)
+    b.obj_rel_param[:, 2] = 1.0
+    P, ok, _ = oracle.sample_poses(b, seed=3)
+    P = P.reshape(500, 8, 4)
+    for k in range(8):
+        e = min(b.obj_half[k, 0], b.obj_half[k, 1])
+        sel = ok.astype(bool)
+        assert np.all(np.abs(P[sel, k, 0]) <= 0.6 - e + 1e-9)
+        assert np.all(np.abs(P[sel, k, 1]) <= 0.4 - e + 1e-9)
+
+
+def test_on_top_and_next_to_relations():
+    """On-top: bottom of the child = top of the parent (exact), pivot inside the
+    parent's top face in the parent frame, uniform there. Next-to: centre
+    distance in [rho_a + rho_t + 0.05, rho_a + rho_t + 0.2], on the support."""
+    b = synth.shelf(seed=1, n_cand=3000, n_obj=12, n_sph=4, n_obb=0)
+    P, ok, band = oracle.sample_poses(b, seed=5)
+    P = P.reshape(b.n_cand, 12, 4)
+    kinds, refs = b.obj_rel & 0xF, b.obj_rel >> 8
+    assert (kinds == synth.REL_ON_TOP).sum() == 3 and (kinds == synth.REL_NEXT_TO).sum() == 3
+    H = b.obj_half.astype(np.float64)
+    for k in range(12):
+        p = refs[k]
+        if kinds[k] == synth.REL_ON_TOP:
+            assert np.allclose(P[:, k, 2] - H[k, 2], P[:, p, 2] + H[p, 2], atol=1e-12)
+            d = P[:, k, :2] - P[:, p, :2]
+            c, s = np.cos(P[:, p, 3]), np.sin(P[:, p, 3])
+            xl, yl = c * d[:, 0] + s * d[:, 1], -s * d[:, 0] + c * d[:, 1]
+            assert np.all(np.abs(xl) <= H[p, 0] + 1e-12) and np.all(np.abs(yl) <= H[p, 1] + 1e-12)
+            assert stats.kstest(xl / H[p, 0], stats.uniform(-1, 2).cdf).pvalue > 1e-4
+        elif kinds[k] == synth.REL_NEXT_TO:
+            dist = np.hypot(P[:, k, 0] - P[:, p, 0], P[:, k, 1] - P[:, p, 1])
+            lo, hi = H[p, 3] + H[k, 3] + 0.05, H[p, 3] + H[k, 3] + 0.2
+            sel = ok.astype(bool)
+            assert np.all(dist[sel] >= lo - 1e-12) and np.all(dist[sel] <= hi + 1e-12)
+            assert np.all(np.abs(P[sel, k, 0]) <= 0.6) and np.all(np.abs(P[sel, k, 1]) <= 0.4)
+            assert np.allclose(P[:, k, 2], 0.75 + H[k, 2])
+
+
+# --------------------------------------------------------------------------- generation
+
+
+def test_generate_valid_scenes_are_collision_free():
+    """Every scene the loop marks valid passes the whole-scene check (all pairs)."""
+    b = synth.tabletop(seed=0, n_cand=256)
+    P, valid, band, tries = oracle.generate(b, seed=1)
+    assert valid.mean() > 0.5
+    sel = np.nonzero(valid)[0]
+    col, md, cb = oracle.collide(b, P, active=sel.astype(np.int32))
+    assert np.all(md >= -1e-12)
+    assert np.all(tries[valid.astype(bool)] >= 8) and np.all(tries <= 8 * 11)
+
+
+def test_generate_without_retries_equals_whole_scene_check():
+    """With no retries every object keeps its retry-0 sample, so a scene is valid
+    exactly when the retry-0 samples are all accepted and the whole scene is
+    collision-free: the incremental per-object checks cover every pair once."""
+    b = synth.tabletop(seed=0, n_cand=512)
+    P, valid, band, _ = oracle.generate(b, seed=2, max_retries=0)
+    Ps, ok, sband = oracle.sample_poses(b, seed=2)
+    col, md, cband = oracle.collide(b, Ps)
+    whole = ok.astype(bool) & (md >= 0)
+    keep = ~(band.astype(bool) | sband.astype(bool) | cband.astype(bool))
+    assert np.array_equal(valid.astype(bool)[keep], whole[keep])
+    assert whole.sum() > 0
+
+
+# --------------------------------------------------------------------------- kinematics
+
+ARM = oracle.make_arm(*synth.arm_arrays())
+
+
+def _dh_scipy(q):
+    T = np.eye(4)
+    for i in range(7):
+        Rz = np.eye(4); Rz[:3, :3] = Rotation.from_euler("z", q[i]).as_matrix()
+        Tz = np.eye(4); Tz[2, 3] = synth.ARM_D[i]
+        Tx = np.eye(4); Tx[0, 3] = synth.ARM_A[i]
+        Rx = np.eye(4); Rx[:3, :3] = Rotation.from_euler("x", float(np.float32(synth.ARM_ALPHA[i]))).as_matrix()
+        T = T @ Rz @ Tz @ Tx @ Rx
+    return T
+
+
+def test_fk_matches_scipy_dh_chain():
+    rng = np.random.default_rng(2)
+    for q in [np.zeros(7)] + [rng.uniform(-2.8, 2.8, 7) for _ in range(20)]:
+        F = oracle.fk_frames(ARM, q)
+        assert np.allclose(F[7], _dh_scipy(q), atol=1e-7)  # float32 DH parameters
+    # hand product at q = 0: Tz(d1); Rx(-pi/2); Tz(d3) along world +y; Rx(pi/2) -> R = I;
+    # Tx(a4); Rx(pi/2); Tz(d5) along world -y; Tx(a5); Rx(-pi/2) -> I; Rx(pi/2);
+    # Tz(d7) along -y; Tx(a7); Rx(pi/2): p = (a4 + a5 + a7, d3 - d5 - d7, d1), R = Rx(pi)
+    F0 = oracle.fk_frames(ARM, np.zeros(7))[7]
+    assert np.allclose(F0[:3, 3], [0.088, 0.316 - 0.384 - 0.107, 0.333], atol=1e-7)
+    assert np.allclose(F0[:3, :3], np.diag([1.0, -1.0, -1.0]), atol=1e-6)
+
+
+def test_jacobian_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for _ in range(10):
+        q = rng.uniform(-2.5, 2.5, 7)
+        J = oracle.jacobian(ARM, q)
+        for i in range(7):
+            dq = np.zeros(7); dq[i] = h
+            Fp, Fm = oracle.fk_frames(ARM, q + dq)[7], oracle.fk_frames(ARM, q - dq)[7]
+            v = (Fp[:3, 3] - Fm[:3, 3]) / (2 * h)
+            w = Rotation.from_matrix(Fp[:3, :3] @ Fm[:3, :3].T).as_rotvec() / (2 * h)
+            assert np.allclose(J[:3, i], v, atol=1e-7)
+            assert np.allclose(J[3:, i], w, atol=1e-7)
+
+
+def test_orientation_error_and_angle_closed_forms():
+    """R* = Rot(a, delta) R  =>  1/2 sum r_k x r*_k = sin(delta) a and the
+    rotation angle of R^T R* is delta; the position part is p* - p."""
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        q = rng.uniform(-2.5, 2.5, 7)
+        T = oracle.fk_frames(ARM, q)[7]
+        a = rng.normal(size=3); a /= np.linalg.norm(a)
+        delta = rng.uniform(0.0, 3.0)
+        Rs = Rotation.from_rotvec(delta * a).as_matrix() @ T[:3, :3]
+        dp = rng.normal(size=3) * 0.1
+        tgt = np.concatenate([Rs.ravel(), T[:3, 3] + dp])
+        e = oracle.ik_error(ARM, q, tgt)
+        assert np.allclose(e[:3], dp, atol=1e-12)
+        assert np.allclose(e[3:], math.sin(delta) * a, atol=1e-12)
+        pe, re = oracle.pose_error(ARM, q, tgt)
+        assert pe == pytest.approx(np.linalg.norm(dp), abs=1e-12)
+        assert re == pytest.approx(delta, abs=1e-9)
+
+
+def test_dls_step_push_through_identity():
+    """J^T (J J^T + l^2 I)^-1 e == (J^T J + l^2 I)^-1 J^T e (numpy.linalg.solve)."""
+    rng = np.random.default_rng(5)
+    lam = 0.05
+    for _ in range(20):
+        q = rng.uniform(-1.5, 1.5, 7)
+        T = oracle.fk_frames(ARM, q)[7]
+        tgt = np.concatenate([(Rotation.from_rotvec(rng.normal(size=3) * 0.05).as_matrix() @ T[:3, :3]).ravel(),
+                              T[:3, 3] + rng.normal(size=3) * 0.02])
+        J = oracle.jacobian(ARM, q)
+        e = oracle.ik_error(ARM, q, tgt)
+        dq = np.linalg.solve(J.T @ J + lam**2 * np.eye(7), J.T @ e)
+        assert np.all(np.abs(q + dq) < 2.8)
+        assert np.allclose(oracle.dls_step(ARM, lam, q, tgt) - q, dq, atol=1e-10)
+
+
+def test_ik_reaches_fk_targets_and_never_beyond_reach():
+    rng = np.random.default_rng(6)
+    P = oracle.ik_params(seeds=8, iters=100)
+    qs = rng.uniform(-2.5, 2.5, (40, 7))
+    tg = np.array([np.concatenate([oracle.fk_frames(ARM, q)[7][:3, :3].ravel(), oracle.fk_frames(ARM, q)[7][:3, 3]])
+                   for q in qs], np.float32)
+    reach, qo, err, _ = oracle.ik_reach(ARM, P, tg)
+    assert reach.mean() >= 0.8
+    for i in np.nonzero(reach)[0]:
+        pe, re = oracle.pose_error(ARM, qo[i], tg[i].astype(np.float64))
+        assert pe <= 5e-3 and re <= 0.05
+        assert np.all(np.abs(qo[i]) <= 2.8)
+    # the tool can never be farther from the base origin than sum(|d_i| + |a_i|)
+    bound = sum(abs(x) for x in synth.ARM_D) + sum(abs(x) for x in synth.ARM_A)
+    far = synth.topdown_targets(7, 30, box=((1.45, 2.0), (-0.5, 0.5), (-0.3, 0.3)))
+    assert np.all(np.linalg.norm(far[:, 9:], axis=1) > bound)
+    reach, _, _, _ = oracle.ik_reach(ARM, P, far)
+    assert reach.sum() == 0
+
+
+def test_grasp_target_frame():
+    """Top-down grasp: tool z = -world z, tool x along the object yaw (in the base
+    frame), position = top of the object; a base yaw rotates both."""
+    base = np.array([-0.6, 0.1, 0.75, 0.3], np.float32)
+    pose = np.array([0.2, -0.1, 0.9, 1.1])
+    t = oracle.grasp_target(pose, 0.05, base)
+    R = t[:9].reshape(3, 3)
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-12) and np.linalg.det(R) == pytest.approx(1.0)
+    assert np.allclose(R[:, 2], [0, 0, -1])
+    ang = 1.1 - float(base[3])
+    assert np.allclose(R[:, 0], [math.cos(ang), math.sin(ang), 0], atol=1e-7)
+    Rb = Rotation.from_euler("z", float(base[3])).as_matrix()
+    assert np.allclose(Rb @ t[9:], pose[:3] + [0, 0, 0.05] - base[:3], atol=1e-7)
+
+
+# --------------------------------------------------------------------------- MLP
+
+
+def test_bf16_round_matches_torch():
+    import torch
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=10000) * 10.0 ** rng.integers(-8, 8, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.0078125, 65504.0, 3.0e38, 1e-40]])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(x), ref)
+
+
+def test_bce_closed_forms():
+    assert mlp.bce_with_logits(0.0, 0.0) == pytest.approx(math.log(2), abs=1e-15)
+    assert mlp.bce_with_logits(0.0, 1.0) == pytest.approx(math.log(2), abs=1e-15)
+    assert mlp.bce_with_logits(40.0, 1.0) == pytest.approx(math.exp(-40), rel=1e-9)
+    assert mlp.bce_with_logits(40.0, 0.0) == pytest.approx(40.0, rel=1e-12)
+    z = np.linspace(-5, 5, 11)
+    ref = -(np.log(1 / (1 + np.exp(-z))))
+    assert np.allclose(mlp.bce_with_logits(z, 1.0), ref, atol=1e-12)
+
+
+def test_silu_grad_finite_difference():
+    a = np.linspace(-6, 6, 101)
+    h = 1e-6
+    assert np.allclose(mlp.silu_grad(a), (mlp.silu(a + h) - mlp.silu(a - h)) / (2 * h), atol=1e-8)
+
+
+def test_mlp_backward_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    P = mlp.init_params(rng, mu=rng.normal(size=9) * 0.1, sigma=rng.uniform(0.5, 2, 9))
+    tg = synth.topdown_targets(3, 6)
+    y = rng.integers(0, 2, 6).astype(np.float64)
+    L, dW, db = mlp.backward(P, tg, y, bf16=False)
+    h = 1e-6
+    for l in range(4):
+        for _ in range(6):
+            i, j = rng.integers(P.W[l].shape[0]), rng.integers(P.W[l].shape[1])
+            P.W[l][i, j] += h; Lp = mlp.loss(P, tg, y, bf16=False)
+            P.W[l][i, j] -= 2 * h; Lm = mlp.loss(P, tg, y, bf16=False)
+            P.W[l][i, j] += h
+            assert dW[l][i, j] == pytest.approx((Lp - Lm) / (2 * h), abs=1e-8)
+        i = rng.integers(P.b[l].shape[0])
+        P.b[l][i] += h; Lp = mlp.loss(P, tg, y, bf16=False)
+        P.b[l][i] -= 2 * h; Lm = mlp.loss(P, tg, y, bf16=False)
+        P.b[l][i] += h
+        assert db[l][i] == pytest.approx((Lp - Lm) / (2 * h), abs=1e-8)
+
+
+def test_mlp_bf16_close_to_exact():
+    """The bf16 rounding points move the loss by O(2^-8) relative, no more."""
+    rng = np.random.default_rng(2)
+    P = mlp.init_params(rng)
+    tg = synth.topdown_targets(4, 64)
+    y = rng.integers(0, 2, 64).astype(np.float64)
+    assert mlp.loss(P, tg, y, bf16=True) == pytest.approx(mlp.loss(P, tg, y, bf16=False), rel=2e-2)
+
+
+def test_adam_first_step_closed_form():
+    """From zero moments the bias-corrected first step is -lr g / (|g| + eps)."""
+    g = np.array([1e-3, -2.0, 0.5, 0.0])
+    w0 = np.array([1.0, 2.0, 3.0, 4.0])
+    w1, m, v = mlp.adam_step(w0, g, np.zeros(4), np.zeros(4), 1)
+    assert np.allclose(w1 - w0, -1e-3 * g / (np.abs(g) + 1e-8), atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
