@@ -1,0 +1,212 @@
+/*
+ * sceniris.h - C ABI of libsceniris_b300.so, the B300 (sm_103a) hot path of
+ * Sceniris (arXiv 2512.16896): batched pose sampling and collision rejection
+ * over many scene variations at once, plus the reachability check.
+ *
+ * Conventions (apply to every call unless stated otherwise):
+ *  - Units are metres and radians; frames are right-handed with z up.
+ *  - Every array argument is a DEVICE pointer owned by the caller. Inputs are
+ *    read-only during the call; outputs are written in full. The library
+ *    never frees or keeps a caller pointer after the call is enqueued.
+ *  - Calls are asynchronous on the context's CUDA stream unless they return
+ *    host data. sc_ctx_synchronize() waits and reports device-side errors.
+ *  - No call aborts and no exception crosses the ABI: failures return a
+ *    non-zero sc_status and a message readable with sc_last_error().
+ *  - Arguments are validated on the host before anything is launched; a call
+ *    that returns SC_ERR_INVALID has enqueued no work.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key = the
+ *    64-bit seed (low word, high word) and a counter that names the draw,
+ *    so every result is a pure function of (seed, indices) and is
+ *    reproducible in any order, on any device and across calls.
+ */
+#ifndef SCENIRIS_H
+#define SCENIRIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SC_OK = 0,
+  SC_ERR_INVALID = 1,     /* bad argument; nothing was launched */
+  SC_ERR_OOM = 2,         /* a context allocation failed */
+  SC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  SC_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  SC_ERR_UNSUPPORTED = 5, /* valid request this build does not handle (message says what) */
+  SC_ERR_DEVICE = 6       /* a kernel latched an error in the device status word */
+} sc_status;
+
+/* ---------------------------------------------------------------- context */
+
+/* Opaque context: one device, one stream, owns the library's scratch memory
+ * (work counters, per-launch statistics, device status word). Not thread-safe:
+ * use one context per host thread. */
+typedef struct sc_ctx sc_ctx;
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). *out receives the context.
+ * Errors: SC_ERR_INVALID (out NULL, bad device), SC_ERR_CUDA, SC_ERR_OOM. */
+sc_status sc_ctx_create(int device, void* cuda_stream, sc_ctx** out);
+/* Destroy a context (NULL is ignored). Waits for the context's stream first. */
+void sc_ctx_destroy(sc_ctx* ctx);
+/* Change the stream later calls enqueue on. */
+sc_status sc_ctx_set_stream(sc_ctx* ctx, void* cuda_stream);
+/* Wait for the stream, then read and clear the device status word.
+ * Returns SC_ERR_DEVICE if a kernel latched an error since the last check. */
+sc_status sc_ctx_synchronize(sc_ctx* ctx);
+/* Message of the last failing call on this host thread ("" if none). The
+ * pointer stays valid until the next library call on the same thread. */
+const char* sc_last_error(void);
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int32_t sc_version(void);
+/* Number of SMs of the context's device (read at creation). */
+int32_t sc_ctx_num_sms(const sc_ctx* ctx);
+
+/* ---------------------------------------------------------- scene batch */
+
+/* Relation kinds stored in obj_rel (low 4 bits), see sc_sample_poses. */
+enum { SC_REL_FREE = 0, SC_REL_ON_TOP = 1, SC_REL_NEXT_TO = 2, SC_REL_KIND_MASK = 0xF, SC_REL_REACH = 0x10 };
+
+/* A batch of scene templates and the candidates (scene variations) drawn
+ * from them, CSR-packed (Sec. IV-B: one transform per instance per edge; here
+ * one pose per (candidate, object)). All pointers are DEVICE pointers.
+ *
+ *  tmpl_obj_off  int32 [T+1]  objects of template t: [tmpl_obj_off[t], tmpl_obj_off[t+1]);
+ *                             template-local object k is global object tmpl_obj_off[t]+k.
+ *                             Placement order = local index order.
+ *  obj_sph_off   int32 [O+1]  collision spheres of object o (spheres of one template
+ *                             are contiguous, in object order).
+ *  sph_local     float [S][4] sphere (x, y, z, r) in its object's frame.
+ *  obj_half      float [O][4] (Hx, Hy, Hz, rho): half extents of the object's box in its
+ *                             frame (its bottom face rests on the support) and the
+ *                             radius of its xy bounding circle.
+ *  obj_rel       int32 [O]    kind | SC_REL_REACH flag | (reference local index << 8);
+ *                             the reference (parent / anchor) is an EARLIER object.
+ *  obj_rel_param float [O][4] (dmin, dmax, ratio_on_support, unused).
+ *  tmpl_poly_off int32 [T+1], poly_verts float [V][2]: support polygon of template t
+ *                             (closed, any orientation, >= 3 vertices) on the plane
+ *                             z = tmpl_support_z[t].
+ *  tmpl_obb_off  int32 [T+1], obb float [n_obb][12]: static world boxes of template t,
+ *                             each (cx, cy, cz, -, qx, qy, qz, qw, hx, hy, hz, -); the
+ *                             quaternion need not be normalised.
+ *  cand_tmpl_off int32 [T+1]  candidates of template t: [cand_tmpl_off[t], cand_tmpl_off[t+1]);
+ *                             the global candidate index is the Philox counter word 0.
+ *  tmpl_pose_off int64 [T+1]  start of template t's block in the pose array; candidate
+ *                             c of template t (l = c - cand_tmpl_off[t]) owns the
+ *                             n_t poses at tmpl_pose_off[t] + l * n_t + k.
+ *  tmpl_base     float [T][4] robot base (x, y, z, yaw) per template; may be NULL
+ *                             when no reachability check is requested.
+ * Host-known sizes: n_* are the lengths above, max_obj / max_sph the largest object
+ * and sphere count of any template (they size on-chip buffers: max_sph <= 8192,
+ * max_obj <= 256, at most 64 vertices per polygon and 64 boxes per template). */
+typedef struct {
+  int32_t n_templates, n_objects, n_spheres, n_verts, n_obb, n_cand;
+  int32_t max_obj, max_sph;
+  const int32_t* tmpl_obj_off;
+  const int32_t* obj_sph_off;
+  const float* sph_local;
+  const float* obj_half;
+  const int32_t* obj_rel;
+  const float* obj_rel_param;
+  const int32_t* tmpl_poly_off;
+  const float* poly_verts;
+  const float* tmpl_support_z;
+  const int32_t* tmpl_obb_off;
+  const float* obb;
+  const int32_t* cand_tmpl_off;
+  const int64_t* tmpl_pose_off;
+  const float* tmpl_base;
+} sc_scene_batch;
+
+/* ------------------------------------------------------------- sampling */
+
+typedef struct {
+  uint64_t seed;        /* Philox key */
+  int32_t max_attempts; /* proposals per object per try (point-in-polygon rejection), 1..1024 */
+  int32_t retry;        /* try index r >= 0 (Philox counter word 2) */
+  int32_t first_obj;    /* first template-local object to sample */
+  int32_t n_obj;        /* how many objects from first_obj (clipped to each template) */
+} sc_sample_params;
+
+/* Sample object poses for the listed candidates (Sec. III position sampling,
+ * Sec. IV-C batch sampling with the canonical polygon moved per instance,
+ * Sec. IV-F relations and ratio_on_support). For every listed candidate c and
+ * object k in [first_obj, first_obj + n_obj) (in order; earlier objects of c
+ * must already hold poses), attempt a = 0..max_attempts-1 draws
+ * u = Philox(seed; c, k, retry, a), u_i = (word_i >> 8) 2^-24, and proposes:
+ *   FREE    xy uniform in the support polygon's bounding box;
+ *   NEXT_TO around the anchor: angle 2 pi u0, distance rho_anchor + rho + dmin +
+ *           (dmax - dmin) u1 (the annulus between min_r and max_r of Sec. IV-F, v = Null);
+ *   ON_TOP  xy uniform in the parent's top face (its frame) moved by the parent's pose,
+ *           z = parent z + parent Hz + Hz; accepted at attempt 0 (may overhang).
+ * FREE / NEXT_TO proposals are accepted when inside the support polygon and at
+ * least e = ratio_on_support * min(Hx, Hy) from its boundary; z = support + Hz.
+ * yaw = 2 pi u2. The first accepted attempt wins; if none is accepted the pose
+ * of the last attempt is written and the object counts as failed.
+ * poses   float [P][4] (x, y, z, yaw), CSR layout of the batch; read (earlier
+ *         objects) and written (sampled objects).
+ * active  int32 [n_active] candidate indices to sample, or NULL for all n_cand
+ *         (then n_active is ignored). Duplicates are not allowed.
+ * sample_ok [n] u8: 1 if every sampled object of the candidate was accepted.
+ * band      [n] u8: 1 if an accept/reject decision that fixed the outcome lay
+ *           within 1e-5 m of the polygon boundary or of the erosion distance.
+ * Errors: SC_ERR_INVALID for NULL outputs, max_attempts outside 1..1024,
+ * retry < 0, n_obj < 0 or sizes beyond the limits of sc_scene_batch. */
+sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sample_params* params,
+                          const int32_t* active, int32_t n_active, float* poses, uint8_t* sample_ok,
+                          uint8_t* band);
+
+/* ------------------------------------------------------------ collision */
+
+/* Launch shape of the persistent collision kernel; a zeroed struct (or NULL)
+ * selects the built-in default. threads: 128..1024, multiple of 32.
+ * a_per_lane: spheres each lane holds from the A side (1, 2 or 4).
+ * seg_len: B-sphere segment per work unit (multiple of 8, 8..4096).
+ * ctas_per_sm: resident CTAs per SM the grid is sized for (1..8). */
+typedef struct {
+  int32_t threads, a_per_lane, seg_len, ctas_per_sm;
+} sc_collide_config;
+
+/* Collision check of the listed candidates (Sec. IV-D; the paper uses cuRobo
+ * meshes, this build per-object sphere sets and oriented boxes). Each sphere
+ * is moved by its object's pose (rotation about z by yaw, then translation),
+ * and the minimum signed distance
+ *   min( |c_i - c_j| - r_i - r_j  over spheres i of object a, j of object b,
+ *                                  a < b, b >= first_new_obj,
+ *        sdf_box(c_i) - r_i       over spheres of objects >= first_new_obj and
+ *                                  the template's world boxes )
+ * is reduced per candidate; the empty set gives FLT_MAX. Touching (d = 0) is
+ * free: collide = min_dist < 0. band = |min_dist| <= 1e-5 m.
+ * first_new_obj = 0 checks the whole scene; k re-checks object k (and later)
+ * against everything placed before it (Sec. IV-D re-checks only what changed).
+ * The kernel is persistent: CTAs take candidates from `active` in list order
+ * through an atomic counter, so list the heaviest candidates first (see
+ * sc_order_by_work) for ragged batches.
+ * Outputs [n]: collide u8, min_dist float, band u8 (n = n_active, or n_cand
+ * when active is NULL). Errors: SC_ERR_INVALID (NULL outputs, first_new_obj < 0,
+ * bad config, limits of sc_scene_batch). */
+sc_status sc_collide(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
+                     int32_t n_active, int32_t first_new_obj, uint8_t* collide, float* min_dist, uint8_t* band);
+sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
+                        int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
+                        float* min_dist, uint8_t* band);
+
+/* Number of sphere pairs (and sphere-box pairs) the last sc_collide /
+ * sc_collide_ex call on this context evaluated in its inner loop, read back
+ * after the call completes (synchronises the stream). Pairs that the kernel
+ * proved unable to lower the minimum are not counted. */
+sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs);
+
+/* Host helper: order candidates heaviest first (LPT) by their exhaustive
+ * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],
+ * cand_tmpl_off [T+1]; out_order [n_cand] receives candidate indices. */
+sc_status sc_order_by_work(int32_t n_templates, const int32_t* tmpl_obj_off, const int32_t* obj_sph_off,
+                           const int32_t* cand_tmpl_off, int32_t* out_order);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCENIRIS_H */

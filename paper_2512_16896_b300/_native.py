@@ -1,0 +1,223 @@
+"""ctypes view of include/sceniris.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsceniris_b300.so")
+
+SC_OK, SC_ERR_INVALID, SC_ERR_OOM, SC_ERR_CUDA, SC_ERR_TIMEOUT, SC_ERR_UNSUPPORTED, SC_ERR_DEVICE = range(7)
+_NAMES = ["SC_OK", "SC_ERR_INVALID", "SC_ERR_OOM", "SC_ERR_CUDA", "SC_ERR_TIMEOUT", "SC_ERR_UNSUPPORTED",
+          "SC_ERR_DEVICE"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SceniError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES[status] if 0 <= status < len(_NAMES) else status}: {msg}")
+        self.status = status
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+
+
+class ScSceneBatch(ctypes.Structure):
+    _fields_ = [(n, I32) for n in ("n_templates", "n_objects", "n_spheres", "n_verts", "n_obb", "n_cand", "max_obj",
+                                   "max_sph")] + [
+        (n, P) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel", "obj_rel_param",
+                         "tmpl_poly_off", "poly_verts", "tmpl_support_z", "tmpl_obb_off", "obb", "cand_tmpl_off",
+                         "tmpl_pose_off", "tmpl_base")]
+
+
+class ScSampleParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("retry", I32), ("first_obj", I32), ("n_obj", I32)]
+
+
+class CollideConfig(ctypes.Structure):
+    _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32)]
+
+    def as_tuple(self):
+        return (self.threads, self.a_per_lane, self.seg_len, self.ctas_per_sm)
+
+
+# name -> (restype, argtypes); mirrors include/sceniris.h
+SIGNATURES = {
+    "sc_version": (I32, []),
+    "sc_last_error": (ctypes.c_char_p, []),
+    "sc_ctx_create": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(P)]),
+    "sc_ctx_destroy": (None, [P]),
+    "sc_ctx_set_stream": (ctypes.c_int, [P, P]),
+    "sc_ctx_synchronize": (ctypes.c_int, [P]),
+    "sc_ctx_num_sms": (I32, [P]),
+    "sc_sample_poses": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScSampleParams), P, I32, P, P,
+                                       P]),
+    "sc_collide": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
+    "sc_collide_ex": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, ctypes.POINTER(CollideConfig), P,
+                                     P, P]),
+    "sc_collide_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
+}
+
+
+def lib():
+    """The loaded library (raises if it is not built; there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is not built; run python -m paper_2512_16896_b300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SC_OK:
+        raise SceniError(status, lib().sc_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """An sc_ctx on one device, enqueuing on torch's current stream for that device."""
+
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None):
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = P()
+        _check(lib().sc_ctx_create(self.device, P(self.stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        _check(lib().sc_ctx_set_stream(self.handle, P(stream.cuda_stream)))
+
+    def synchronize(self):
+        _check(lib().sc_ctx_synchronize(self.handle))
+
+    @property
+    def num_sms(self) -> int:
+        return lib().sc_ctx_num_sms(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceBatch:
+    """Device copies of a scene batch's CSR arrays (any object with the fields
+    of sc_scene_batch as numpy arrays) and the sc_scene_batch that points at them."""
+
+    FIELDS = {"tmpl_obj_off": torch.int32, "obj_sph_off": torch.int32, "sph_local": torch.float32,
+              "obj_half": torch.float32, "obj_rel": torch.int32, "obj_rel_param": torch.float32,
+              "tmpl_poly_off": torch.int32, "poly_verts": torch.float32, "tmpl_support_z": torch.float32,
+              "tmpl_obb_off": torch.int32, "obb": torch.float32, "cand_tmpl_off": torch.int32,
+              "tmpl_base": torch.float32}
+
+    def __init__(self, batch, device: int | str | torch.device = "cuda", pinned_host: bool = False):
+        self.t = {}
+        for name, dt in self.FIELDS.items():
+            a = np.ascontiguousarray(getattr(batch, name))
+            x = torch.from_numpy(a).to(dt)
+            if x.numel() == 0:
+                x = torch.zeros(16, dtype=dt)  # keep a valid aligned pointer for empty arrays
+            self.t[name] = x.to(device) if not pinned_host else x.pin_memory()
+        tpo = np.concatenate([[0], np.cumsum(np.diff(batch.cand_tmpl_off).astype(np.int64) *
+                                             np.diff(batch.tmpl_obj_off).astype(np.int64))]).astype(np.int64)
+        self.t["tmpl_pose_off"] = torch.from_numpy(tpo).to(device)
+        self.tmpl_obj_off = np.asarray(batch.tmpl_obj_off, np.int32)
+        self.obj_sph_off = np.asarray(batch.obj_sph_off, np.int32)
+        self.cand_tmpl_off = np.asarray(batch.cand_tmpl_off, np.int32)
+        n_t = len(self.tmpl_obj_off) - 1
+        nobj = np.diff(self.tmpl_obj_off)
+        nsph = self.obj_sph_off[self.tmpl_obj_off[1:]] - self.obj_sph_off[self.tmpl_obj_off[:-1]]
+        self.n_poses = int(tpo[-1])
+        self.n_cand = int(self.cand_tmpl_off[-1])
+        self.c = ScSceneBatch(
+            n_t, len(batch.obj_half), len(batch.sph_local), len(batch.poly_verts), len(batch.obb), self.n_cand,
+            int(nobj.max()), int(nsph.max()),
+            *[_ptr(self.t[n]) for n, _ in ScSceneBatch._fields_[8:]])
+        if len(batch.obb) == 0:
+            self.c.obb = None
+
+    def new_poses(self, device="cuda") -> torch.Tensor:
+        return torch.zeros((self.n_poses, 4), dtype=torch.float32, device=device)
+
+
+def _n_items(db: DeviceBatch, active):
+    return db.n_cand if active is None else int(active.numel())
+
+
+def sample_poses(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, retry: int = 0, first_obj: int = 0,
+                 n_obj: int = 1 << 30, active: torch.Tensor | None = None, poses: torch.Tensor | None = None):
+    """sc_sample_poses. Returns (poses [P,4] f32, sample_ok [n] u8, band [n] u8) on the device."""
+    dev = torch.device("cuda", ctx.device)
+    poses = db.new_poses(dev) if poses is None else poses
+    n = _n_items(db, active)
+    ok = torch.empty(n, dtype=torch.uint8, device=dev)
+    band = torch.empty(n, dtype=torch.uint8, device=dev)
+    p = ScSampleParams(seed, max_attempts, retry, first_obj, n_obj)
+    _check(lib().sc_sample_poses(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _ptr(active), n, _ptr(poses),
+                                 _ptr(ok), _ptr(band)))
+    return poses, ok, band
+
+
+def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Tensor | None = None, first_new: int = 0,
+            config: CollideConfig | tuple | None = None, out=None):
+    """sc_collide_ex. Returns (collide [n] u8, min_dist [n] f32, band [n] u8) on the device."""
+    dev = torch.device("cuda", ctx.device)
+    n = _n_items(db, active)
+    if out is None:
+        col = torch.empty(n, dtype=torch.uint8, device=dev)
+        md = torch.empty(n, dtype=torch.float32, device=dev)
+        band = torch.empty(n, dtype=torch.uint8, device=dev)
+    else:
+        col, md, band = out
+    cfg = None
+    if config is not None:
+        cfg = config if isinstance(config, CollideConfig) else CollideConfig(*config)
+    _check(lib().sc_collide_ex(ctx.handle, ctypes.byref(db.c), _ptr(poses), _ptr(active), n, first_new,
+                               None if cfg is None else ctypes.byref(cfg), _ptr(col), _ptr(md), _ptr(band)))
+    return col, md, band
+
+
+def collide_last_work(ctx: Context):
+    """(sphere pairs, sphere-box pairs) evaluated by the last collide call (synchronises)."""
+    a, b = I64(), I64()
+    _check(lib().sc_collide_last_work(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def order_by_work(batch) -> np.ndarray:
+    """Candidate indices heaviest first (host helper sc_order_by_work)."""
+    t = np.ascontiguousarray(batch.tmpl_obj_off, np.int32)
+    o = np.ascontiguousarray(batch.obj_sph_off, np.int32)
+    c = np.ascontiguousarray(batch.cand_tmpl_off, np.int32)
+    out = np.empty(int(c[-1]), np.int32)
+    _check(lib().sc_order_by_work(len(t) - 1, _ptr(t), _ptr(o), _ptr(c), _ptr(out)))
+    return out

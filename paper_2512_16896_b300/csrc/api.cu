@@ -1,0 +1,249 @@
+// C ABI of libsceniris_b300: context management, host-side argument
+// validation and the entry points declared in include/sceniris.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+struct sc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  // scratch (one allocation): [0] status word, [1] collide work counter, then stats
+  void* scratch = nullptr;
+  int* d_status = nullptr;
+  unsigned int* d_counter = nullptr;
+  unsigned long long* d_stats = nullptr;  // [2]
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sc_status fail(sc_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+sc_status fail(sc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+sc_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SC_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+sc_status check_batch(const sc_scene_batch* b) {
+  if (!b) return fail(SC_ERR_INVALID, "batch is NULL");
+  if (b->n_templates < 1 || b->n_objects < 1 || b->n_spheres < 1 || b->n_verts < 3 || b->n_obb < 0 || b->n_cand < 0)
+    return fail(SC_ERR_INVALID, "batch sizes out of range (templates %d, objects %d, spheres %d, verts %d, obb %d, cand %d)",
+                b->n_templates, b->n_objects, b->n_spheres, b->n_verts, b->n_obb, b->n_cand);
+  if (b->max_obj < 1 || b->max_obj > sc::kMaxObj)
+    return fail(SC_ERR_INVALID, "max_obj = %d outside 1..%d", b->max_obj, sc::kMaxObj);
+  if (b->max_sph < 1 || b->max_sph > sc::kMaxSph)
+    return fail(SC_ERR_INVALID, "max_sph = %d outside 1..%d", b->max_sph, sc::kMaxSph);
+  const void* req[] = {b->tmpl_obj_off, b->obj_sph_off, b->sph_local, b->obj_half, b->obj_rel, b->obj_rel_param,
+                       b->tmpl_poly_off, b->poly_verts, b->tmpl_support_z, b->tmpl_obb_off, b->cand_tmpl_off,
+                       b->tmpl_pose_off};
+  for (const void* p : req)
+    if (!p) return fail(SC_ERR_INVALID, "a required batch array is NULL");
+  if (b->n_obb > 0 && !b->obb) return fail(SC_ERR_INVALID, "obb is NULL but n_obb = %d", b->n_obb);
+  if (!aligned(b->sph_local, 16) || !aligned(b->obj_half, 16) || !aligned(b->obj_rel_param, 16) ||
+      !aligned(b->poly_verts, 8) || (b->obb && !aligned(b->obb, 16)) || (b->tmpl_base && !aligned(b->tmpl_base, 16)))
+    return fail(SC_ERR_INVALID, "float4 / float2 batch arrays must be 16 / 8 byte aligned");
+  return SC_OK;
+}
+
+sc_status check_ctx(sc_ctx* ctx) {
+  if (!ctx) return fail(SC_ERR_INVALID, "ctx is NULL");
+  return SC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sc_version(void) { return 100; }
+
+const char* sc_last_error(void) { return g_err.c_str(); }
+
+sc_status sc_ctx_create(int device, void* cuda_stream, sc_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(SC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(SC_ERR_INVALID, "device %d outside 0..%d", device, n - 1);
+  DeviceGuard g(device);
+  sc_ctx* c = new (std::nothrow) sc_ctx;
+  if (!c) return fail(SC_ERR_OOM, "host allocation of the context failed");
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  e = cudaMalloc(&c->scratch, 256);
+  if (e != cudaSuccess) { delete c; return fail(SC_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e)); }
+  char* base = static_cast<char*>(c->scratch);
+  c->d_status = reinterpret_cast<int*>(base);
+  c->d_counter = reinterpret_cast<unsigned int*>(base + 16);
+  c->d_stats = reinterpret_cast<unsigned long long*>(base + 32);
+  e = cudaMemset(c->scratch, 0, 256);
+  if (e != cudaSuccess) { cudaFree(c->scratch); delete c; return cuda_fail(e, "cudaMemset"); }
+  *out = c;
+  return SC_OK;
+}
+
+void sc_ctx_destroy(sc_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->scratch);
+  delete ctx;
+}
+
+sc_status sc_ctx_set_stream(sc_ctx* ctx, void* cuda_stream) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return SC_OK;
+}
+
+int32_t sc_ctx_num_sms(const sc_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
+
+sc_status sc_ctx_synchronize(sc_ctx* ctx) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (st != 0) {
+    cudaMemset(ctx->d_status, 0, sizeof(int));
+    return fail(SC_ERR_DEVICE, "a kernel latched device error code %d (1 bad template, 2 too many spheres, "
+                "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation)", st);
+  }
+  return SC_OK;
+}
+
+sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sample_params* params,
+                          const int32_t* active, int32_t n_active, float* poses, uint8_t* sample_ok, uint8_t* band) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (sc_status s = check_batch(batch)) return s;
+  if (!params) return fail(SC_ERR_INVALID, "params is NULL");
+  if (!poses || !sample_ok || !band) return fail(SC_ERR_INVALID, "an output pointer is NULL");
+  if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
+  if (params->max_attempts < 1 || params->max_attempts > 1024)
+    return fail(SC_ERR_INVALID, "max_attempts = %d outside 1..1024", params->max_attempts);
+  if (params->retry < 0 || params->first_obj < 0 || params->n_obj < 0)
+    return fail(SC_ERR_INVALID, "retry, first_obj and n_obj must be >= 0");
+  if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
+  const int n = active ? n_active : batch->n_cand;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::launch_sample(*batch, *params, active, n, poses, sample_ok, band, ctx->d_status, ctx->num_sms,
+                                    ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sample_kernel launch");
+  return SC_OK;
+}
+
+static const sc_collide_config kDefaultCollide = {256, 4, 256, 4};
+
+sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
+                        int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
+                        float* min_dist, uint8_t* band) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (sc_status s = check_batch(batch)) return s;
+  if (!poses || !collide || !min_dist || !band) return fail(SC_ERR_INVALID, "an input or output pointer is NULL");
+  if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
+  if (first_new_obj < 0) return fail(SC_ERR_INVALID, "first_new_obj = %d < 0", first_new_obj);
+  if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
+  sc_collide_config cfg = kDefaultCollide;
+  if (config && (config->threads | config->a_per_lane | config->seg_len | config->ctas_per_sm)) cfg = *config;
+  sc::CollideLaunch a;
+  a.poses = poses;
+  a.active = active;
+  a.n_items = active ? n_active : batch->n_cand;
+  a.first_new = first_new_obj;
+  a.collide = collide;
+  a.min_dist = min_dist;
+  a.band = band;
+  a.counter = ctx->d_counter;
+  a.stats = ctx->d_stats;
+  a.status = ctx->d_status;
+  DeviceGuard g(ctx->device);
+  const char* why = nullptr;
+  cudaError_t e = sc::launch_collide(*batch, a, cfg, ctx->num_sms, ctx->stream, &why);
+  if (why) return fail(SC_ERR_INVALID, "collide config: %s", why);
+  if (e != cudaSuccess) return cuda_fail(e, "collide_kernel launch");
+  return SC_OK;
+}
+
+sc_status sc_collide(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
+                     int32_t n_active, int32_t first_new_obj, uint8_t* collide, float* min_dist, uint8_t* band) {
+  return sc_collide_ex(ctx, batch, poses, active, n_active, first_new_obj, nullptr, collide, min_dist, band);
+}
+
+sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  DeviceGuard g(ctx->device);
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stats read");
+  if (sphere_pairs) *sphere_pairs = (int64_t)h[0];
+  if (sphere_box_pairs) *sphere_box_pairs = (int64_t)h[1];
+  return SC_OK;
+}
+
+sc_status sc_order_by_work(int32_t n_templates, const int32_t* tmpl_obj_off, const int32_t* obj_sph_off,
+                           const int32_t* cand_tmpl_off, int32_t* out_order) {
+  g_err.clear();
+  if (n_templates < 1 || !tmpl_obj_off || !obj_sph_off || !cand_tmpl_off || !out_order)
+    return fail(SC_ERR_INVALID, "bad arguments to sc_order_by_work");
+  std::vector<double> work(n_templates);
+  for (int t = 0; t < n_templates; ++t) {
+    double s = 0, s2 = 0;
+    for (int o = tmpl_obj_off[t]; o < tmpl_obj_off[t + 1]; ++o) {
+      double n = obj_sph_off[o + 1] - obj_sph_off[o];
+      s += n;
+      s2 += n * n;
+    }
+    work[t] = 0.5 * (s * s - s2);  // pairs of spheres in different objects
+  }
+  std::vector<int> tm(n_templates);
+  std::iota(tm.begin(), tm.end(), 0);
+  std::stable_sort(tm.begin(), tm.end(), [&](int x, int y) { return work[x] > work[y]; });
+  int k = 0;
+  for (int t : tm)
+    for (int c = cand_tmpl_off[t]; c < cand_tmpl_off[t + 1]; ++c) out_order[k++] = c;
+  return SC_OK;
+}
+
+}  // extern "C"

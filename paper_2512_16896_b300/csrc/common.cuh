@@ -1,0 +1,85 @@
+// Device-side helpers shared by the kernels of libsceniris_b300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sceniris.h"
+
+namespace sc {
+
+constexpr float kBand = 1e-5f;                       // decision band (metres)
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kFarSentinel = 1e18f;                // "no distance seen yet"
+constexpr int kMaxObj = 256;                         // object ids fit in a byte
+constexpr int kMaxSph = 8192;                        // spheres of one template
+constexpr int kMaxPolyVerts = 64;
+constexpr int kMaxObbPerTemplate = 64;
+
+// Device status codes latched into the context's status word (first error wins).
+enum DeviceError : int {
+  kDevOk = 0,
+  kDevBadTemplate = 1,   // candidate index outside every template range
+  kDevTooManySpheres = 2,
+  kDevTooManyObjects = 3,
+  kDevTooManyBoxes = 4,
+  kDevBadPolygon = 5,
+  kDevBadRelation = 6,  // relation refers to itself or a later object
+};
+
+__device__ __forceinline__ void latch_error(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Philox4x32-10 as published by Salmon, Moraes, Dror and Shaw (SC'11): ten
+// rounds of two 32x32->64 multiplications whose high halves are mixed with the
+// other counter words and the round key, the key advanced by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t hi_a = __umulhi(m0, x.x), lo_a = m0 * x.x;
+    uint32_t hi_b = __umulhi(m1, x.z), lo_b = m1 * x.z;
+    x = make_uint4(hi_b ^ x.y ^ k0, lo_b, hi_a ^ x.w ^ k1, lo_a);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return x;
+}
+
+// Uniform float in [0, 1) from the top 24 bits of a word (exact in FP32).
+__device__ __forceinline__ float unit_float(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
+
+__device__ __forceinline__ float4 draw_uniform4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  uint4 w = philox4x32_10(make_uint4(c0, c1, c2, c3), (uint32_t)seed, (uint32_t)(seed >> 32));
+  return make_float4(unit_float(w.x), unit_float(w.y), unit_float(w.z), unit_float(w.w));
+}
+
+// Template owning candidate c: last t with cand_tmpl_off[t] <= c (binary search).
+__device__ __forceinline__ int template_of(const sc_scene_batch& b, int c) {
+  int lo = 0, hi = b.n_templates;  // invariant: off[lo] <= c < off[hi]
+  if (c < 0 || c >= b.cand_tmpl_off[b.n_templates]) return -1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(&b.cand_tmpl_off[mid]) <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Order-preserving map of a float onto a signed int (for atomicMin on floats).
+__device__ __forceinline__ int float_key(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : (i ^ 0x7FFFFFFF);
+}
+__device__ __forceinline__ float key_float(int k) {
+  return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF));
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+}  // namespace sc

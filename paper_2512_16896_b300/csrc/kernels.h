@@ -1,0 +1,35 @@
+// Host-side launch wrappers of the CUDA kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sceniris.h"
+
+namespace sc {
+
+cudaError_t launch_sample(const sc_scene_batch& b, const sc_sample_params& p, const int32_t* active, int n_items,
+                          float* poses, uint8_t* ok, uint8_t* band, int* status, int num_sms, cudaStream_t s);
+
+struct CollideLaunch {
+  const float* poses;
+  const int32_t* active;
+  int n_items;
+  int first_new;
+  uint8_t* collide;
+  float* min_dist;
+  uint8_t* band;
+  unsigned int* counter;          // scratch: work counter, zeroed by the launcher
+  unsigned long long* stats;      // scratch: [0] sphere pairs, [1] sphere-box pairs
+  int* status;
+};
+
+// Validates the config against the batch (returns cudaErrorInvalidValue with
+// *why set when it cannot run) and enqueues the persistent kernel.
+cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, const sc_collide_config& cfg, int num_sms,
+                           cudaStream_t s, const char** why);
+
+// Dynamic shared memory one collide CTA needs for this batch and config.
+size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg);
+
+}  // namespace sc

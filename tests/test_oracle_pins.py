@@ -14,6 +14,7 @@ from scipy import stats
 import oracle
 import synth
 from oracle import mlp
+from scenes import tiny_batch
 
 # --------------------------------------------------------------------------- Philox
 
@@ -169,18 +170,6 @@ def test_sphere_world_yaw():
 
 
 # --------------------------------------------------------------------------- collision on hand-made scenes
-
-
-def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_cand=1, rel=None):
-    """objects: list of sphere lists [(x,y,z,r), ...] in object frames."""
-    parts = dict(
-        sph=np.array([s for o in objects for s in o], np.float32), nsph=np.array([len(o) for o in objects]),
-        half=np.array([[0.1, 0.1, 0.1, 0.15]] * len(objects), np.float32),
-        rel=np.zeros(len(objects), np.int32) if rel is None else np.array(rel, np.int32),
-        relp=np.tile(np.array([0.05, 0.2, 0.0, 0.0], np.float32), (len(objects), 1)),
-        poly=np.array(poly, np.float32), z=0.0, obb=np.array(obbs, np.float32).reshape(-1, 12), ncand=n_cand,
-        base=np.zeros(4, np.float32))
-    return synth._pack([parts])
 
 
 def test_collide_brute_force_tiny():
