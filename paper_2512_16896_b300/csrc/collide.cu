@@ -314,9 +314,10 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
         for (int k = 0; k < nobb; ++k) {
           const float* d = obbd + 16 * k;
           const float vx = w.x - d[9], vy = w.y - d[10], vz = w.z - d[11];
-          const float px = d[0] * vx + d[3] * vy + d[6] * vz;
-          const float py = d[1] * vx + d[4] * vy + d[7] * vz;
-          const float pz = d[2] * vx + d[5] * vy + d[8] * vz;
+          // box frame: p = R^T v, i.e. p_k = (column k of R) . v
+          const float px = d[0] * vx + d[1] * vy + d[2] * vz;
+          const float py = d[3] * vx + d[4] * vy + d[5] * vz;
+          const float pz = d[6] * vx + d[7] * vy + d[8] * vz;
           const float qx = fabsf(px) - d[12], qy = fabsf(py) - d[13], qz = fabsf(pz) - d[14];
           const float qm = fmaxf(qx, fmaxf(qy, qz));
           if (qm - w.w < m) {  // lower bound of the box distance
