@@ -173,6 +173,23 @@ def _n_items(db: DeviceBatch, active):
     return db.n_cand if active is None else int(active.numel())
 
 
+_EMPTY = {}
+
+
+def _active_ptr(active):
+    """Device pointer of an active list; an empty list gets a valid placeholder
+    pointer (NULL would mean "all candidates")."""
+    if active is None:
+        return None
+    if active.numel() == 0:
+        dev = active.device
+        if dev not in _EMPTY:
+            _EMPTY[dev] = torch.zeros(4, dtype=torch.int32, device=dev)
+        return _ptr(_EMPTY[dev])
+    assert active.dtype == torch.int32 and active.is_contiguous()
+    return _ptr(active)
+
+
 def sample_poses(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, retry: int = 0, first_obj: int = 0,
                  n_obj: int = 1 << 30, active: torch.Tensor | None = None, poses: torch.Tensor | None = None):
     """sc_sample_poses. Returns (poses [P,4] f32, sample_ok [n] u8, band [n] u8) on the device."""
@@ -182,7 +199,7 @@ def sample_poses(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 1
     ok = torch.empty(n, dtype=torch.uint8, device=dev)
     band = torch.empty(n, dtype=torch.uint8, device=dev)
     p = ScSampleParams(seed, max_attempts, retry, first_obj, n_obj)
-    _check(lib().sc_sample_poses(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _ptr(active), n, _ptr(poses),
+    _check(lib().sc_sample_poses(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(active), n, _ptr(poses),
                                  _ptr(ok), _ptr(band)))
     return poses, ok, band
 
@@ -201,7 +218,7 @@ def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Te
     cfg = None
     if config is not None:
         cfg = config if isinstance(config, CollideConfig) else CollideConfig(*config)
-    _check(lib().sc_collide_ex(ctx.handle, ctypes.byref(db.c), _ptr(poses), _ptr(active), n, first_new,
+    _check(lib().sc_collide_ex(ctx.handle, ctypes.byref(db.c), _ptr(poses), _active_ptr(active), n, first_new,
                                None if cfg is None else ctypes.byref(cfg), _ptr(col), _ptr(md), _ptr(band)))
     return col, md, band
 

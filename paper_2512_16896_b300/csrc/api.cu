@@ -156,6 +156,8 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
   if (sc_status s = check_ctx(ctx)) return s;
   if (sc_status s = check_batch(batch)) return s;
   if (!params) return fail(SC_ERR_INVALID, "params is NULL");
+  if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
+  if ((active ? n_active : batch->n_cand) == 0) return SC_OK;  // nothing to sample
   if (!poses || !sample_ok || !band) return fail(SC_ERR_INVALID, "an output pointer is NULL");
   if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
   if (params->max_attempts < 1 || params->max_attempts > 1024)
@@ -179,6 +181,8 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;
   if (sc_status s = check_batch(batch)) return s;
+  if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
+  if ((active ? n_active : batch->n_cand) == 0) return SC_OK;  // nothing to check
   if (!poses || !collide || !min_dist || !band) return fail(SC_ERR_INVALID, "an input or output pointer is NULL");
   if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
   if (first_new_obj < 0) return fail(SC_ERR_INVALID, "first_new_obj = %d < 0", first_new_obj);
