@@ -206,6 +206,39 @@ sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphe
 sc_status sc_order_by_work(int32_t n_templates, const int32_t* tmpl_obj_off, const int32_t* obj_sph_off,
                            const int32_t* cand_tmpl_off, int32_t* out_order);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* Largest candidate list one sc_collide_noalloc call accepts. */
+#define SC_NOALLOC_MAX_ITEMS (1 << 30)
+
+/* The collision check of sc_collide for callers that cannot allocate device
+ * memory. The paper has no counterpart: this exists for users of the library.
+ * Creating an sc_ctx calls cudaMalloc for the kernel's scratch (its work
+ * counter and pair statistics); some callers cannot do that, for example code
+ * whose device memory is owned by a framework's own pool, per-frame loops in
+ * which a cudaMalloc would synchronise the device and stall, or code that
+ * keeps no library context. This entry point takes no context and allocates
+ * nothing: the scratch is a 256-byte array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *  - Runs on the CURRENT device, enqueued on `cuda_stream` (a cudaStream_t;
+ *    NULL = legacy default stream).
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) and the SM count; make that first call before any
+ *    stream capture on that device.
+ *  - Every call shares the one array per device; the launch zeroes the work
+ *    counter before the kernel runs. Calls that overlap on the GPU (on two
+ *    streams, or from two host threads at once) race on it and must not be
+ *    issued; calls in order on one stream are fine.
+ *  - Arguments, layouts, outputs and results are those of sc_collide (the same
+ *    kernel, default launch shape). Candidates the kernel's own checks reject
+ *    come back with min_dist = NaN and band = 1 (no status word is kept).
+ *  - Errors: SC_ERR_INVALID for the cases of sc_collide and for more than
+ *    SC_NOALLOC_MAX_ITEMS candidates; SC_ERR_CUDA if the set-up or the launch
+ *    fails. Messages through sc_last_error(). */
+sc_status sc_collide_noalloc(void* cuda_stream, const sc_scene_batch* batch, const float* poses,
+                             const int32_t* active, int32_t n_active, int32_t first_new_obj, uint8_t* collide,
+                             float* min_dist, uint8_t* band);
+
 #ifdef __cplusplus
 }
 #endif

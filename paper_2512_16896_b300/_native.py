@@ -64,6 +64,7 @@ SIGNATURES = {
                                      P, P]),
     "sc_collide_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
+    "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
 }
 
 

@@ -83,6 +83,11 @@ sc_status check_ctx(sc_ctx* ctx) {
 
 }  // namespace
 
+namespace sc {
+void set_error_message(const std::string& msg) { g_err = msg; }
+sc_status validate_batch(const sc_scene_batch* b) { return check_batch(b); }
+}  // namespace sc
+
 extern "C" {
 
 int32_t sc_version(void) { return 100; }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "sceniris.h"
 
 namespace sc {
@@ -28,6 +30,11 @@ struct CollideLaunch {
 // *why set when it cannot run) and enqueues the persistent kernel.
 cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, const sc_collide_config& cfg, int num_sms,
                            cudaStream_t s, const char** why);
+
+// Error message / batch validation of the C ABI (defined in api.cu) for entry
+// points that live in other files.
+void set_error_message(const std::string& msg);
+sc_status validate_batch(const sc_scene_batch* b);
 
 // Dynamic shared memory one collide CTA needs for this batch and config.
 size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg);
