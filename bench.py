@@ -1,22 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the Sceniris hot path on one B300 (or N replicas).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ragged|shelf|tabletop]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ragged|shelf|tabletop] [--path generate|whole]
 
-One step = one pass of the hot path over one batch of synthetic scenes that
-are already resident in HBM: Philox pose sampling of every object of every
-candidate, then the collision reduction of every candidate (persistent kernel,
-heaviest candidates first). A scene counts as verified collision-free when all
-its objects were accepted by the support test and its exact minimum signed
-distance is >= 0.
+One step = one pass of the hot path over one batch of synthetic scene
+candidates already resident in HBM. Default path (`generate`, the paper's
+placement loop of Sec. IV-A with 10 retries per object, Sec. V-A): for every
+object in order, sample its pose (Philox, point-in-polygon, relations), check
+it against the placed objects and the world, retry the failing candidates, mark
+candidates that run out of tries invalid. A scene counts as verified
+collision-free when every object was placed by exact decisions. `--path whole`
+times the plain whole-scene pass instead (sample every object, then the exact
+minimum distance of every candidate).
 
 Prints ONE JSON line (rank 0). `value` is verified collision-free scenes per
 second over all ranks; `e2e` is the same metric through the public C-ABI calls
 with the batch copied from pinned host memory every step and the poses and
-masks copied back. `roofline` is the collision kernel's FP32-pipe throughput
-(algorithmic operations it evaluated / its CUDA-event time) against the
-B300's FP32 issue peak. `cpu_baseline` is the FP64 oracle on the host cores
-over a bounded random sample of the same workload.
+valid flags copied back. `roofline` is the dominant kernel's FP32-pipe
+throughput (algorithmic operations it evaluated / its CUDA-event time) against
+the B300's FP32 issue peak. `cpu_baseline` is the FP64 oracle on the host
+cores over a bounded random sample of the same workload.
 
 --impl reference runs that oracle (as it is) as the reference arm.
 """
@@ -45,8 +49,14 @@ OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
 L2_BYTES = 126 * 1024 * 1024
 
+PATHS = {
+    "generate": "per-object placement loop: sample, decide collisions against placed objects and world, "
+                "retry <= 10 times, invalid after that",
+    "whole": "plain whole-scene: sample all objects, one exact-minimum collision pass",
+}
+
 WORKLOADS = {
-    "ragged": dict(make=lambda seed: synth.ragged(seed=seed), seed=2,
+    "ragged": dict(make=lambda seed, T=4096: synth.ragged(seed=seed, n_templates=T), seed=2,
                    desc="ragged 4096 templates x 64 candidates, 4-64 objects, 8-128 spheres/object, convex 4-10-gon supports"),
     "shelf": dict(make=lambda seed: synth.shelf(seed=seed), seed=1,
                   desc="shelf 65536 candidates x 32 objects x 64 spheres, 25% on-top / 25% next-to, 20 world OBBs"),
@@ -140,25 +150,32 @@ def measured_traffic(kernel_file: str, workload: str):
 # --------------------------------------------------------------------------- oracle legs
 
 
-def oracle_rate(batch, seed, budget_s: float, rng_seed: int = 0):
+def oracle_rate(batch, seed, budget_s: float, path: str = "generate", rng_seed: int = 0, max_retries: int = 10):
     """Verified collision-free scenes/s of the FP64 oracle on a bounded random
     sample of candidates (sized from a probe so the sample takes ~budget_s)."""
     import oracle
     sc = oracle.Scene(batch)
     rng = np.random.default_rng(rng_seed)
     threads = oracle.default_threads()
-    probe = rng.choice(batch.n_cand, min(batch.n_cand, 2 * threads), replace=False).astype(np.int32)
+
+    def run(pick):
+        if path == "generate":
+            _, valid, _, _ = oracle.generate(sc, seed, max_retries=max_retries, active=pick, threads=threads)
+            return int(valid.sum())
+        P, ok, _ = oracle.sample_poses(sc, seed, active=pick, threads=threads)
+        col, md, _ = oracle.collide(sc, P, active=pick, threads=threads)
+        return int(np.sum(ok.astype(bool) & (md >= 0)))
+
+    probe = rng.choice(batch.n_cand, min(batch.n_cand, 4 * threads), replace=False).astype(np.int32)
+    run(probe[: 2 * threads])  # load and warm the library
     t0 = time.perf_counter()
-    P, ok, _ = oracle.sample_poses(sc, seed, active=probe, threads=threads)
-    oracle.collide(sc, P, active=probe, threads=threads)
+    run(probe)
     dt = max(time.perf_counter() - t0, 1e-3)
     n = int(min(batch.n_cand, max(len(probe), len(probe) * budget_s / dt)))
     pick = rng.choice(batch.n_cand, n, replace=False).astype(np.int32)
     t0 = time.perf_counter()
-    P, ok, _ = oracle.sample_poses(sc, seed, active=pick, threads=threads)
-    col, md, _ = oracle.collide(sc, P, active=pick, threads=threads)
+    valid = run(pick)
     dt = time.perf_counter() - t0
-    valid = int(np.sum(ok.astype(bool) & (md >= 0)))
     return {"valid": valid, "n": n, "seconds": dt, "threads": threads,
             "scenes_per_s": n / dt, "valid_per_s": valid / dt}
 
@@ -170,7 +187,8 @@ def run_reference(args, wl):
     batch = wl["make"](wl["seed"])
     times, valids, ns = [], [], []
     for i in range(args.warmup + args.steps):
-        r = oracle_rate(batch, seed=wl["seed"], budget_s=args.ref_step_s, rng_seed=100 + i)
+        r = oracle_rate(batch, seed=wl["seed"], budget_s=args.ref_step_s, path=args.path, rng_seed=100 + i,
+                        max_retries=args.retries)
         if i >= args.warmup:
             times.append(r["seconds"]); valids.append(r["valid"]); ns.append(r["n"])
     value = sum(valids) / sum(times)
@@ -179,7 +197,8 @@ def run_reference(args, wl):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample_per_step": f"{ns[0]} random candidates of the workload"},
+        "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
+                   "sample_per_step": f"{ns[0]} random candidates of the workload"},
         "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{ns[0]} random candidates per step of the {args.workload} workload"},
         "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -209,53 +228,78 @@ def run_ours(args, wl):
     order = torch.from_numpy(sc.order_by_work(batch)).to(dev)
     poses = db.new_poses(dev)
     n = batch.n_cand
-    ok = torch.empty(n, dtype=torch.uint8, device=dev)
-    sband = torch.empty(n, dtype=torch.uint8, device=dev)
-    col = torch.empty(n, dtype=torch.uint8, device=dev)
+    u8 = lambda: torch.zeros(n, dtype=torch.uint8, device=dev)
+    valid, band, tries = u8(), u8(), torch.zeros(n, dtype=torch.int32, device=dev)
+    ok, sband, col, cband = u8(), u8(), u8(), u8()
     md = torch.empty(n, dtype=torch.float32, device=dev)
-    cband = torch.empty(n, dtype=torch.uint8, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    gen = args.path == "generate"
+
+    # launch shape: explicit, autotuned on a sample of this batch, or the default
+    cfg = None
+    tune_info = "library default"
+    if args.collide_config:
+        cfg = tuple(int(x) for x in args.collide_config.split(","))
+        tune_info = "given"
+    elif not args.no_tune and not gen:
+        from paper_2512_16896_b300 import autotune
+        sc.sample_poses(ctx, db, seed=seed, poses=poses)
+        cfg, entry = autotune.tune_collide(ctx, db, batch, poses, order, verbose=args.tune_verbose)
+        tune_info = f"autotuned ({entry['sample']} sampled candidates, {entry['ms']:.2f} ms)"
+
+    def enqueue(step_seed, ev=None):
+        """One step on the device; ev = (start, end) events around the dominant kernel(s)."""
+        if gen:
+            if ev:
+                ev[0].record(stream)
+            sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
+                        out=(valid, band, tries))
+            if ev:
+                ev[1].record(stream)
+        else:
+            sc.sample_poses(ctx, db, seed=step_seed, poses=poses, out=(ok, sband))
+            if ev:
+                ev[0].record(stream)
+            sc.collide(ctx, db, poses, active=order, out=(col, md, cband), config=cfg)
+            if ev:
+                ev[1].record(stream)
+
     ok_by_list = torch.empty(n, dtype=torch.uint8, device=dev)
 
-    def step(step_seed):
-        sc.sample_poses(ctx, db, seed=step_seed, poses=poses)
-        sc.collide(ctx, db, poses, active=order, out=(col, md, cband))
-
-    def valid_count():
-        # outputs of collide are in list order; sample_ok is by candidate
-        torch.index_select(ok, 0, order.long(), out=ok_by_list)
+    def count_valid():
+        if gen:
+            return int(valid.sum().item())
+        torch.index_select(ok, 0, order.long(), out=ok_by_list)  # collide outputs are in list order
         return int(((ok_by_list == 1) & (col == 0)).sum().item())
 
     for i in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
-        step(seed * 7919 + i)
+        enqueue(seed * 7919 + i)
     torch.cuda.synchronize()
+    ctx.synchronize()
     if world > 1:
         dist.barrier()
 
-    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    cevents = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_kern = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     valids, pairs, boxes = [], [], []
     with ClockSampler(local) as clocks:
         torch.cuda.synchronize()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()  # evict L2 between timed steps (not timed)
-            events[i][0].record(stream)
-            s_seed = seed * 7919 + 1000 + i
-            _, ok, sband = sc.sample_poses(ctx, db, seed=s_seed, poses=poses)
-            cevents[i][0].record(stream)
-            sc.collide(ctx, db, poses, active=order, out=(col, md, cband))
-            cevents[i][1].record(stream)
-            events[i][1].record(stream)
+            ev_step[i][0].record(stream)
+            enqueue(seed * 7919 + 1000 + i, ev_kern[i])
+            ev_step[i][1].record(stream)
             p, bx = sc.collide_last_work(ctx)  # synchronises after the step's end event
-            pairs.append(p); boxes.append(bx)
-            valids.append(valid_count())
+            pairs.append(p)
+            boxes.append(bx)
+            valids.append(count_valid())
         torch.cuda.synchronize()
     ctx.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in events]
-    coll_ms = [a.elapsed_time(b) for a, b in cevents]
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    kern_ms = [a.elapsed_time(b) for a, b in ev_kern]
     total_s = sum(step_ms) / 1000.0
     total_valid = sum(valids)
 
@@ -263,8 +307,8 @@ def run_ours(args, wl):
     hb = sc.DeviceBatch(batch, pinned_host=True)
     h2d = sum(t.numel() * t.element_size() for k, t in hb.t.items() if k != "tmpl_pose_off")
     h_poses = torch.empty_like(poses, device="cpu").pin_memory()
-    h_out = [torch.empty(n, dtype=torch.uint8).pin_memory() for _ in range(2)] + [torch.empty(n).pin_memory()]
-    d2h = h_poses.numel() * 4 + n * (1 + 1 + 4)
+    h_valid = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d2h = h_poses.numel() * 4 + n
     e2e_ms, e2e_valid = [], []
     for i in range(0 if args.no_e2e else args.warmup + args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,19 +319,19 @@ def run_ours(args, wl):
             for k, t in hb.t.items():
                 if k != "tmpl_pose_off":
                     db.t[k].copy_(t, non_blocking=True)
-        _, ok, sband = sc.sample_poses(ctx, db, seed=seed * 7919 + 5000 + i, poses=poses)
-        sc.collide(ctx, db, poses, active=order, out=(col, md, cband))
+        enqueue(seed * 7919 + 5000 + i)
         with torch.cuda.stream(stream):
             h_poses.copy_(poses, non_blocking=True)
-            h_out[0].copy_(ok, non_blocking=True)
-            h_out[1].copy_(col, non_blocking=True)
-            h_out[2].copy_(md, non_blocking=True)
+            if gen:
+                h_valid.copy_(valid, non_blocking=True)
+            else:
+                torch.index_select(ok, 0, order.long(), out=ok_by_list)
+                h_valid.copy_((ok_by_list == 1) & (col == 0), non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-            okl = h_out[0].numpy()[order.cpu().numpy()]
-            e2e_valid.append(int(np.sum((okl == 1) & (h_out[1].numpy() == 0))))
+            e2e_valid.append(int(h_valid.numpy().sum()))
 
     # ---- aggregate over ranks (max time, summed work)
     stats = torch.tensor([total_s, total_valid, max(sum(e2e_ms), 1e-9) / 1000.0, sum(e2e_valid)], dtype=torch.float64,
@@ -306,9 +350,13 @@ def run_ours(args, wl):
     sm_count = ctx.num_sms
     peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6  # FP32 lanes x max SM clock
     ops = np.array(pairs, np.float64) * OPS_PER_SPHERE_PAIR + np.array(boxes, np.float64) * OPS_PER_SPHERE_BOX
-    achieved = float(np.sum(ops) / (np.sum(coll_ms) / 1000.0))
+    achieved = float(np.sum(ops) / (np.sum(kern_ms) / 1000.0))
     clk = clocks.summary()
-    cpu = oracle_rate(batch, seed=seed, budget_s=args.cpu_budget_s) if world == 1 and args.cpu_budget_s > 0 else None
+    cpu = None
+    if world == 1 and args.cpu_budget_s > 0:
+        cpu = oracle_rate(batch, seed=seed, budget_s=args.cpu_budget_s, path=args.path, max_retries=args.retries)
+    kname = "gen_step_kernel (+ its sampling)" if gen else "collide_kernel"
+    launches_per_step = (1 + db.c.max_obj * (args.retries + 1)) if gen else 2
     line = {
         "metric": "verified collision-free scenes/sec",
         "value": total_valid / total_s,
@@ -322,22 +370,24 @@ def run_ours(args, wl):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "path": "plain whole-scene: sample all objects, one collision pass",
+        "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
+                   "collide_launch": {"shape": list(cfg) if cfg else None, "source": tune_info},
                    "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
                    "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "collide_kernel", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": achieved / peak_ops,
-                     "traffic": measured_traffic("collide.cu", args.workload),
-                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz ({peak_src} max clock)",
-                     "ms_per_launch": float(np.mean(coll_ms)),
-                     "pairs_per_launch": float(np.mean(pairs)), "box_pairs_per_launch": float(np.mean(boxes))},
+                     "traffic": measured_traffic("generate.cu" if gen else "collide.cu", args.workload),
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "
+                                    f"({peak_src} max clock)",
+                     "ms_per_step_in_kernel": float(np.mean(kern_ms)),
+                     "pairs_per_step": float(np.mean(pairs)), "box_pairs_per_step": float(np.mean(boxes))},
         "cpu_baseline": None if cpu is None else {
             "value": cpu["valid_per_s"], "unit": "scenes/s", "cores": cpu["threads"], "kind": "oracle",
             "sample": f"{cpu['n']} random candidates of the same workload ({cpu['seconds']:.1f} s)"},
         "e2e": None if args.no_e2e else {"value": e2e_valid_sum / e2e_s, "unit": "scenes/s",
                                           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -353,11 +403,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ragged")
+    ap.add_argument("--path", choices=sorted(PATHS), default="generate")
+    ap.add_argument("--retries", type=int, default=10)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--templates", type=int, default=4096, help="ragged workload: number of templates (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="use the library's default collide launch shape")
+    ap.add_argument("--collide-config", type=str, default="", help="threads,a_per_lane,seg_len,ctas_per_sm")
+    ap.add_argument("--tune-verbose", action="store_true")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.workload == "ragged" and args.templates != 4096:
+        T = args.templates
+        wl["make"] = lambda seed: synth.ragged(seed=seed, n_templates=T)
+        wl["desc"] = wl["desc"].replace("4096 templates", f"{T} templates")
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

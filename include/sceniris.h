@@ -161,13 +161,19 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
 
 /* ------------------------------------------------------------ collision */
 
-/* Launch shape of the persistent collision kernel; a zeroed struct (or NULL)
- * selects the built-in default. threads: 128..1024, multiple of 32.
- * a_per_lane: spheres each lane holds from the A side (1, 2 or 4).
+/* Launch shape and mode of the persistent collision kernel. A field left 0
+ * (or a NULL config) takes the built-in default. threads: 128..1024, multiple
+ * of 32. a_per_lane: spheres each lane holds from the A side (1, 2 or 4).
  * seg_len: B-sphere segment per work unit (multiple of 8, 8..4096).
- * ctas_per_sm: resident CTAs per SM the grid is sized for (1..8). */
+ * ctas_per_sm: resident CTAs per SM the grid is sized for (1..8).
+ * decide_only: 0 = exact minimum distance for every candidate; 1 = decide
+ * only: a candidate stops at its first pair closer than -1e-5 m (a certain
+ * collision); collide and band are the same as in mode 0, and min_dist is the
+ * exact minimum only where it is <= 1e-5 m (elsewhere some distance > 1e-5 m
+ * or FLT_MAX). */
 typedef struct {
   int32_t threads, a_per_lane, seg_len, ctas_per_sm;
+  int32_t decide_only;
 } sc_collide_config;
 
 /* Collision check of the listed candidates (Sec. IV-D; the paper uses cuRobo
@@ -194,11 +200,49 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
                         int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
                         float* min_dist, uint8_t* band);
 
-/* Number of sphere pairs (and sphere-box pairs) the last sc_collide /
- * sc_collide_ex call on this context evaluated in its inner loop, read back
- * after the call completes (synchronises the stream). Pairs that the kernel
- * proved unable to lower the minimum are not counted. */
+/* Number of sphere pairs (and sphere-box pairs) the last sc_collide,
+ * sc_collide_ex or sc_generate call on this context evaluated in its inner
+ * loop, read back after the call completes (synchronises the stream). Pairs
+ * that the kernel proved unable to change the result are not counted. */
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs);
+
+/* ----------------------------------------------------------- generation */
+
+typedef struct {
+  uint64_t seed;        /* Philox key of the pose draws */
+  int32_t max_attempts; /* proposals per object per try, 1..1024 (as sc_sample_params) */
+  int32_t max_retries;  /* retries per object after its first try, 0..1000 (the paper uses 10) */
+} sc_gen_params;
+
+/* Generate scenes: the paper's placement loop (Sec. IV-A, Fig. 2) over the
+ * listed candidates. Objects are placed in template order. For object k each
+ * candidate still alive tries r = 0..max_retries: sample object k's pose with
+ * try index r (exactly sc_sample_poses for that object), then check object k
+ * against objects 0..k-1 and the world boxes (the decision of sc_collide with
+ * first_new_obj = k; only the scenes that retry are re-checked, Sec. IV-D).
+ * The first try whose proposal is accepted and collision-free fixes the
+ * pose; a candidate that exhausts its tries is invalid (Sec. V-A) and its
+ * later objects are not placed.
+ * order   int32 [n_order] candidates to generate (NULL: all n_cand; then
+ *         n_order is ignored); the heaviest first balances the first steps.
+ * config  launch shape of the per-step kernel (NULL: default; decide_only is
+ *         implied).
+ * Outputs, indexed by candidate (only listed candidates are written):
+ * poses   float [P][4] CSR pose layout; objects never placed are NaN.
+ * valid   u8 [n_cand]: 1 when every object was placed.
+ * band    u8 [n_cand]: 1 when any decision on the candidate's path (a support
+ *         test of an attempt that fixed an outcome, or a minimum distance)
+ *         lay within 1e-5 m of its threshold.
+ * tries   int32 [n_cand]: tries spent over all objects.
+ * The first call (or one with more candidates than before) allocates the
+ * context's generation scratch (4 int32 lists of the candidates plus
+ * counters); later calls reuse it. Enqueues 1 + max_obj * (max_retries + 1)
+ * kernels; launches whose list is empty exit at once.
+ * Errors: SC_ERR_INVALID (NULL outputs, max_attempts / max_retries out of
+ * range, bad config, batch limits), SC_ERR_OOM, SC_ERR_CUDA. */
+sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
+                      int32_t n_order, const sc_collide_config* config, float* poses, uint8_t* valid, uint8_t* band,
+                      int32_t* tries);
 
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],

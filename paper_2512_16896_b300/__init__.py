@@ -16,5 +16,6 @@ from ._native import (  # noqa: F401
     sample_poses,
     collide,
     collide_last_work,
+    generate,
     order_by_work,
 )

@@ -41,11 +41,15 @@ class ScSampleParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("retry", I32), ("first_obj", I32), ("n_obj", I32)]
 
 
+class ScGenParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("max_retries", I32)]
+
+
 class CollideConfig(ctypes.Structure):
-    _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32)]
+    _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32), ("decide_only", I32)]
 
     def as_tuple(self):
-        return (self.threads, self.a_per_lane, self.seg_len, self.ctas_per_sm)
+        return (self.threads, self.a_per_lane, self.seg_len, self.ctas_per_sm, self.decide_only)
 
 
 # name -> (restype, argtypes); mirrors include/sceniris.h
@@ -64,6 +68,8 @@ SIGNATURES = {
                                      P, P]),
     "sc_collide_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
+    "sc_generate": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScGenParams), P, I32,
+                                   ctypes.POINTER(CollideConfig), P, P, P, P]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
 }
 
@@ -192,13 +198,17 @@ def _active_ptr(active):
 
 
 def sample_poses(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, retry: int = 0, first_obj: int = 0,
-                 n_obj: int = 1 << 30, active: torch.Tensor | None = None, poses: torch.Tensor | None = None):
+                 n_obj: int = 1 << 30, active: torch.Tensor | None = None, poses: torch.Tensor | None = None,
+                 out=None):
     """sc_sample_poses. Returns (poses [P,4] f32, sample_ok [n] u8, band [n] u8) on the device."""
     dev = torch.device("cuda", ctx.device)
     poses = db.new_poses(dev) if poses is None else poses
     n = _n_items(db, active)
-    ok = torch.empty(n, dtype=torch.uint8, device=dev)
-    band = torch.empty(n, dtype=torch.uint8, device=dev)
+    if out is None:
+        ok = torch.empty(n, dtype=torch.uint8, device=dev)
+        band = torch.empty(n, dtype=torch.uint8, device=dev)
+    else:
+        ok, band = out
     p = ScSampleParams(seed, max_attempts, retry, first_obj, n_obj)
     _check(lib().sc_sample_poses(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(active), n, _ptr(poses),
                                  _ptr(ok), _ptr(band)))
@@ -222,6 +232,28 @@ def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Te
     _check(lib().sc_collide_ex(ctx.handle, ctypes.byref(db.c), _ptr(poses), _active_ptr(active), n, first_new,
                                None if cfg is None else ctypes.byref(cfg), _ptr(col), _ptr(md), _ptr(band)))
     return col, md, band
+
+
+def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, max_retries: int = 10,
+             order: torch.Tensor | None = None, config=None, poses: torch.Tensor | None = None, out=None):
+    """sc_generate. Returns (poses [P,4] f32, valid [n_cand] u8, band [n_cand] u8, tries [n_cand] i32)."""
+    dev = torch.device("cuda", ctx.device)
+    poses = db.new_poses(dev) if poses is None else poses
+    if out is None:
+        valid = torch.zeros(db.n_cand, dtype=torch.uint8, device=dev)
+        band = torch.zeros(db.n_cand, dtype=torch.uint8, device=dev)
+        tries = torch.zeros(db.n_cand, dtype=torch.int32, device=dev)
+    else:
+        valid, band, tries = out
+    cfg = None
+    if config is not None:
+        cfg = config if isinstance(config, CollideConfig) else CollideConfig(*config)
+    p = ScGenParams(seed, max_attempts, max_retries)
+    n = 0 if order is None else int(order.numel())
+    _check(lib().sc_generate(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(order), n,
+                             None if cfg is None else ctypes.byref(cfg), _ptr(poses), _ptr(valid), _ptr(band),
+                             _ptr(tries)))
+    return poses, valid, band, tries
 
 
 def collide_last_work(ctx: Context):

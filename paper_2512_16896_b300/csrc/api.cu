@@ -20,6 +20,9 @@ struct sc_ctx {
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;
   unsigned long long* d_stats = nullptr;  // [2]
+  // grow-on-demand scratch of sc_generate (candidate lists and counters)
+  void* gen_scratch = nullptr;
+  size_t gen_scratch_bytes = 0;
 };
 
 namespace {
@@ -126,6 +129,7 @@ void sc_ctx_destroy(sc_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->scratch);
+  if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
   delete ctx;
 }
 
@@ -178,7 +182,7 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
   return SC_OK;
 }
 
-static const sc_collide_config kDefaultCollide = {256, 4, 256, 4};
+static const sc_collide_config kDefaultCollide = {256, 4, 256, 4, 0};
 
 sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
                         int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
@@ -193,7 +197,13 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
   if (first_new_obj < 0) return fail(SC_ERR_INVALID, "first_new_obj = %d < 0", first_new_obj);
   if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
   sc_collide_config cfg = kDefaultCollide;
-  if (config && (config->threads | config->a_per_lane | config->seg_len | config->ctas_per_sm)) cfg = *config;
+  if (config) {  // zero fields keep the default
+    if (config->threads) cfg.threads = config->threads;
+    if (config->a_per_lane) cfg.a_per_lane = config->a_per_lane;
+    if (config->seg_len) cfg.seg_len = config->seg_len;
+    if (config->ctas_per_sm) cfg.ctas_per_sm = config->ctas_per_sm;
+    cfg.decide_only = config->decide_only;
+  }
   sc::CollideLaunch a;
   a.poses = poses;
   a.active = active;
@@ -216,6 +226,61 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
 sc_status sc_collide(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
                      int32_t n_active, int32_t first_new_obj, uint8_t* collide, float* min_dist, uint8_t* band) {
   return sc_collide_ex(ctx, batch, poses, active, n_active, first_new_obj, nullptr, collide, min_dist, band);
+}
+
+sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
+                      int32_t n_order, const sc_collide_config* config, float* poses, uint8_t* valid, uint8_t* band,
+                      int32_t* tries) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (sc_status s = check_batch(batch)) return s;
+  if (!params) return fail(SC_ERR_INVALID, "params is NULL");
+  if (params->max_attempts < 1 || params->max_attempts > 1024)
+    return fail(SC_ERR_INVALID, "max_attempts = %d outside 1..1024", params->max_attempts);
+  if (params->max_retries < 0 || params->max_retries > 1000)
+    return fail(SC_ERR_INVALID, "max_retries = %d outside 0..1000", params->max_retries);
+  if (order && n_order < 0) return fail(SC_ERR_INVALID, "n_order < 0");
+  const int n = order ? n_order : batch->n_cand;
+  if (n == 0) return SC_OK;
+  if (!poses || !valid || !band || !tries) return fail(SC_ERR_INVALID, "an output pointer is NULL");
+  if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
+  sc_collide_config cfg = kDefaultCollide;
+  if (config) {
+    if (config->threads) cfg.threads = config->threads;
+    if (config->a_per_lane) cfg.a_per_lane = config->a_per_lane;
+    if (config->seg_len) cfg.seg_len = config->seg_len;
+    if (config->ctas_per_sm) cfg.ctas_per_sm = config->ctas_per_sm;
+  }
+  DeviceGuard g(ctx->device);
+  const size_t need = sc::generate_scratch_bytes(n, batch->max_obj, params->max_retries);
+  if (need > ctx->gen_scratch_bytes) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
+    ctx->gen_scratch = nullptr;
+    ctx->gen_scratch_bytes = 0;
+    e = cudaMalloc(&ctx->gen_scratch, need);
+    if (e != cudaSuccess) return fail(SC_ERR_OOM, "generation scratch (%zu bytes): %s", need, cudaGetErrorString(e));
+    ctx->gen_scratch_bytes = need;
+  }
+  sc::GenerateLaunch a;
+  a.order = order;
+  a.n_items = n;
+  a.seed = params->seed;
+  a.max_attempts = params->max_attempts;
+  a.max_retries = params->max_retries;
+  a.poses = poses;
+  a.valid = valid;
+  a.band = band;
+  a.tries = tries;
+  a.scratch = ctx->gen_scratch;
+  a.stats = ctx->d_stats;
+  a.status = ctx->d_status;
+  const char* why = nullptr;
+  cudaError_t e = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->stream, &why);
+  if (why) return fail(SC_ERR_INVALID, "generate config: %s", why);
+  if (e != cudaSuccess) return cuda_fail(e, "generate launch");
+  return SC_OK;
 }
 
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs) {

@@ -36,6 +36,28 @@ cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, cons
 void set_error_message(const std::string& msg);
 sc_status validate_batch(const sc_scene_batch* b);
 
+struct GenerateLaunch {
+  const int32_t* order;  // candidates to generate (NULL: 0..n_items-1)
+  int n_items;
+  uint64_t seed;
+  int max_attempts, max_retries;
+  float* poses;
+  uint8_t* valid;
+  uint8_t* band;
+  int32_t* tries;
+  void* scratch;  // generate_scratch_bytes(n_items, max_obj, max_retries)
+  unsigned long long* stats;
+  int* status;
+};
+
+size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
+// Enqueues the whole generation (init + one launch per object and try).
+cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
+                             int num_sms, cudaStream_t s, const char** why);
+
+// NULL if the launch shape is valid, else why not.
+const char* check_collide_config(const sc_collide_config& cfg);
+
 // Dynamic shared memory one collide CTA needs for this batch and config.
 size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg);
 
