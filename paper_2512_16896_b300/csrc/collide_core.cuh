@@ -253,9 +253,12 @@ __device__ __forceinline__ float slow_group(const ABlock<APL>& A, const float4* 
   return warp_min(mloc);
 }
 
+// best_key (MIN): CTA-wide minimum to lower; hit (DECIDE, may be NULL): flag
+// raised on a certain collision. Either way `alive` turns false when the
+// caller should stop this unit.
 template <int APL, bool MASKED, bool DECIDE>
 __device__ __forceinline__ void sweep(ABlock<APL>& A, const float4* W, const float* beta, int jb, int je, int S,
-                                      float& m, float rmax, float eps, CtaShared& sh, bool& alive) {
+                                      float& m, float rmax, float eps, int* best_key, int* hit, bool& alive) {
   for (int j = jb; j < je; j += kGroup) {
     float4 B[kGroup];
     float bt[kGroup];
@@ -290,12 +293,12 @@ __device__ __forceinline__ void sweep(ABlock<APL>& A, const float4* W, const flo
         m = mn;
         if (DECIDE) {
           if (m < -kBand) {  // certain collision: stop this candidate
-            if ((threadIdx.x & 31) == 0) *(volatile int*)&sh.hit = 1;
+            if (hit && (threadIdx.x & 31) == 0) *(volatile int*)hit = 1;
             alive = false;
             return;
           }
         } else {
-          if ((threadIdx.x & 31) == 0) atomicMin(&sh.best_key, float_key(m));
+          if ((threadIdx.x & 31) == 0) atomicMin(best_key, float_key(m));
           alive = refresh<APL, false>(A, m, rmax, eps);
           if (!alive) return;
         }
@@ -379,9 +382,9 @@ __device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f
     for (int s = 0; s < APL; ++s)
       if (A.act[s]) my_pairs += (unsigned long long)max(0, j1 - max(j0, A.bst[s]));
     const int jm = min(j1, mend);
-    if (j0 < jm) sweep<APL, true, DECIDE>(A, sm.W, sm.beta, j0, jm, S, m, rmax, eps, sh, alive);
+    if (j0 < jm) sweep<APL, true, DECIDE>(A, sm.W, sm.beta, j0, jm, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
     if (alive && max(j0, mend) < j1)
-      sweep<APL, false, DECIDE>(A, sm.W, sm.beta, max(j0, mend), j1, S, m, rmax, eps, sh, alive);
+      sweep<APL, false, DECIDE>(A, sm.W, sm.beta, max(j0, mend), j1, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
     if (DECIDE && !alive) break;
   }
   return m;

@@ -13,6 +13,7 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kFarSentinel = 1e18f;                // "no distance seen yet"
 constexpr int kMaxObj = 256;                         // object ids fit in a byte
 constexpr int kMaxSph = 8192;                        // spheres of one template
+constexpr int kMaxSphPerObj = 256;                   // spheres of one object (generation)
 constexpr int kMaxPolyVerts = 64;
 constexpr int kMaxObbPerTemplate = 64;
 

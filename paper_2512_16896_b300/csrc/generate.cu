@@ -3,15 +3,15 @@
 // scenes that retry; Sec. V-A: 10 retries per object, failing scenes invalid).
 //
 // One launch per (object k, try r) processes a device-resident list of the
-// candidates that still need object k. A persistent CTA takes a candidate,
-// its warp 0 samples object k (sample_core.cuh), the CTA moves objects 0..k
-// to shared memory and decides whether object k collides with objects
-// 0..k-1 or the world (collide_core.cuh, decide mode: exits at the first
-// certain collision). Thread 0 then appends the candidate to the list for
-// object k+1 (or marks it valid after its last object), to the retry list for
-// try r+1, or leaves it invalid after the last try. The launch sequence is a
-// fixed function of (max objects, retries), so it is captured once into a
-// CUDA graph and replayed.
+// candidates that still need object k. Each warp of the persistent grid takes
+// one candidate at a time (most tries are small: one object against the few
+// placed before it, so a warp, not a CTA, is the unit of work): it samples
+// object k (sample_core.cuh), stages object k's spheres in its own slice of
+// shared memory and streams the spheres of objects 0..k-1 through registers
+// (the A side of the prune test in collide_core.cuh, decide mode: it stops at
+// the first certain collision). Lane 0 then appends the candidate to the list
+// for object k+1 (or marks it valid after its last object), to the retry list
+// for try r+1, or leaves it invalid after the last try.
 #include <vector>
 
 #include "collide_core.cuh"
@@ -43,26 +43,51 @@ struct GenStepArgs {
   int* status;
 };
 
-template <int APL, int MAXT>
-__global__ void __launch_bounds__(MAXT) gen_step_kernel(GenStepArgs g) {
+// Shared memory of one warp: objects 0..k (sphere offsets, poses, sin/cos of
+// yaw) and the new object's spheres in the world frame (relative to object
+// 0's position) with |c|^2 - r^2.
+struct WarpLayout {
+  int off, pose, sc, B, beta, bytes;
+};
+
+__host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
+  WarpLayout W;
+  W.off = 0;
+  W.pose = align16(4 * (max_obj + 1));
+  W.sc = align16(W.pose + 16 * max_obj);
+  W.B = align16(W.sc + 8 * max_obj);
+  W.beta = align16(W.B + 16 * (kMaxSphPerObj + kPad));
+  W.bytes = align16(W.beta + 4 * (kMaxSphPerObj + kPad));
+  return W;
+}
+
+// One warp per candidate: sample object k, then decide whether any sphere of
+// object k is closer than the band to a sphere of objects 0..k-1 (A side,
+// moved into registers 32*APL at a time) or to a world box.
+template <int APL>
+__global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ CtaShared sh;
   const sc_scene_batch& b = g.b;
-  const Layout L = make_layout(b.max_sph, b.max_obj, APL);
-  const Smem sm = smem_view(smem, L);
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const WarpLayout WL = make_warp_layout(b.max_obj);
+  const int lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * WL.bytes;
+  int* off = reinterpret_cast<int*>(base + WL.off);
+  float4* opose = reinterpret_cast<float4*>(base + WL.pose);
+  float2* osc = reinterpret_cast<float2*>(base + WL.sc);
+  float4* Bs = reinterpret_cast<float4*>(base + WL.B);
+  float* Bb = reinterpret_cast<float*>(base + WL.beta);
   const int n_items = *(volatile const int*)g.n_in;
   const int k = g.k;
   unsigned long long my_pairs = 0, my_box = 0;
 
   for (;;) {
-    if (tid == 0) sh.item = (int)atomicAdd(g.counter, 1u);
-    __syncthreads();
-    const int item = sh.item;
+    int item = 0;
+    if (lane == 0) item = (int)atomicAdd(g.counter, 1u);
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
     if (item >= n_items) break;
     const int c = __ldg(&g.list_in[item]);
     const int t = template_of(b, c);
-    int o0 = 0, nt = 0, s0 = 0, S = 0, nobb = 0, bx0 = 0;
+    int o0 = 0, nt = 0, s0 = 0, Sprev = 0, Sk = 0, nobb = 0, bx0 = 0;
     int64_t pbase = 0;
     if (t >= 0) {
       o0 = __ldg(&b.tmpl_obj_off[t]);
@@ -71,70 +96,136 @@ __global__ void __launch_bounds__(MAXT) gen_step_kernel(GenStepArgs g) {
       bx0 = __ldg(&b.tmpl_obb_off[t]);
       nobb = __ldg(&b.tmpl_obb_off[t + 1]) - bx0;
       pbase = __ldg(&b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&b.cand_tmpl_off[t])) * nt;
-      if (k < nt) S = __ldg(&b.obj_sph_off[o0 + k + 1]) - s0;  // spheres of objects 0..k
+      if (k < nt) {
+        Sprev = __ldg(&b.obj_sph_off[o0 + k]) - s0;
+        Sk = __ldg(&b.obj_sph_off[o0 + k + 1]) - s0 - Sprev;
+      }
     }
     const int err = t < 0 ? kDevBadTemplate
                     : (k >= nt || nt > b.max_obj || nt > kMaxObj) ? kDevTooManyObjects
-                    : (S > b.max_sph || S + kPad > L.cap) ? kDevTooManySpheres
+                    : (Sk > kMaxSphPerObj || Sprev + Sk > b.max_sph) ? kDevTooManySpheres
                     : (nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
     if (err != kDevOk) {
-      if (tid == 0) {
+      if (lane == 0) {
         latch_error(g.status, err);
         if (t >= 0) g.band[c] = 1;
       }
-      __syncthreads();
       continue;
     }
-    // ---- sample object k (warp 0)
-    if (warp == 0) {
-      const Support sup = warp_support(b, t, lane);
-      SampleResult r;
-      r.placed = false;
-      r.band = true;
-      r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (sup.ok) {
-        r = warp_sample_object(b, sup, g.seed, g.max_attempts, g.retry, c, k, o0, g.poses, pbase, g.status, lane);
-      } else if (lane == 0) {
-        latch_error(g.status, kDevBadPolygon);
+    // ---- sample object k
+    const Support sup = warp_support(b, t, lane);
+    SampleResult r;
+    r.placed = false;
+    r.band = true;
+    r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sup.ok) {
+      r = warp_sample_object(b, sup, g.seed, g.max_attempts, g.retry, c, k, o0, g.poses, pbase, g.status, lane);
+    } else if (lane == 0) {
+      latch_error(g.status, kDevBadPolygon);
+    }
+    if (lane == 0) g.poses[pbase + k] = r.pose;
+    bool pass = false, bnd = r.band;
+    if (r.placed) {
+      // ---- objects 0..k
+      for (int j = lane; j <= k; j += 32) {
+        const float4 p = (j == k) ? r.pose : g.poses[pbase + j];
+        float sn, cs;
+        sincosf(p.w, &sn, &cs);
+        opose[j] = p;
+        osc[j] = make_float2(sn, cs);
+        off[j] = __ldg(&b.obj_sph_off[o0 + j]) - s0;
       }
-      if (lane == 0) {
-        g.poses[pbase + k] = r.pose;
-        sh.new_ok = r.placed;
-        sh.new_band = r.band;
+      __syncwarp();
+      const float4 ref = opose[0];
+      // ---- object k's spheres (B side)
+      {
+        const float4 p = opose[k];
+        const float2 sc2 = osc[k];
+        float r2 = 0.f;
+        for (int q = lane; q < Sk + kPad; q += 32) {
+          if (q < Sk) {
+            const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
+            const float x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
+            const float y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
+            const float z = (p.z - ref.z) + l.z;
+            const float c2 = x * x + y * y + z * z;
+            Bs[q] = make_float4(x, y, z, l.w);
+            Bb[q] = c2 - l.w * l.w;
+            r2 = fmaxf(r2, c2);
+          } else {
+            Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
+            Bb[q] = 3e12f;
+          }
+        }
+        __syncwarp();
+        float m = kFarSentinel;
+        // ---- object k vs world boxes
+        for (int bi = 0; bi < nobb; ++bi) {
+          const float* o = b.obb + 12 * (bx0 + bi);
+          float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
+          const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+          qx *= inv; qy *= inv; qz *= inv; qw *= inv;
+          // columns of R (R maps box frame to world)
+          const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
+          const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
+          const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
+          const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
+          const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
+          for (int q = lane; q < Sk; q += 32) {
+            const float4 w = Bs[q];
+            const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
+            const float px = c00 * vx + c01 * vy + c02 * vz;
+            const float py = c10 * vx + c11 * vy + c12 * vz;
+            const float pz = c20 * vx + c21 * vy + c22 * vz;
+            const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
+            const float em = fmaxf(ex, fmaxf(ey, ez));
+            if (em - w.w < kBand) {
+              const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
+              m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
+            }
+          }
+        }
+        my_box += (unsigned long long)nobb * (unsigned long long)(lane < Sk ? (Sk - lane + 31) / 32 : 0);
+        m = warp_min(m);
+        bool alive = !(m < -kBand);
+        r2 = -warp_min(-r2);
+        // ---- object k vs objects 0..k-1 (A side in registers)
+        for (int i0 = 0; alive && i0 < Sprev; i0 += 32 * APL) {
+          ABlock<APL> A;
+          float a2max = 0.f;
+          int nval = 0;
+#pragma unroll
+          for (int s = 0; s < APL; ++s) {
+            const int q = i0 + s * 32 + lane;
+            const bool valid = q < Sprev;
+            float x = 0.f, y = 0.f, z = 0.f, rr = 0.f;
+            if (valid) {
+              const int j = upper_index(off, k + 1, q);
+              const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
+              const float4 p = opose[j];
+              const float2 sc2 = osc[j];
+              x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
+              y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
+              z = (p.z - ref.z) + l.z;
+              rr = l.w;
+              ++nval;
+            }
+            A.ax[s] = -2.f * x; A.ay[s] = -2.f * y; A.az[s] = -2.f * z;
+            A.a2[s] = x * x + y * y + z * z;
+            A.r[s] = rr;
+            A.bst[s] = valid ? 0 : INT_MAX;
+            a2max = fmaxf(a2max, A.a2[s]);
+          }
+          const float eps = 1e-5f * (fmaxf(r2, -warp_min(-a2max)) + 0.01f);
+          refresh<APL, true>(A, 0.f, 0.f, eps);
+          my_pairs += (unsigned long long)nval * (unsigned long long)Sk;
+          sweep<APL, false, true>(A, Bs, Bb, 0, Sk, Sk, m, 0.f, eps, nullptr, nullptr, alive);
+        }
+        pass = alive && !(m < 0.f);
+        bnd = bnd || fabsf(m) <= kBand;
       }
     }
-    if (tid == 0) {
-      sh.r2max_key = 0;
-      sh.rmax_key = 0;
-      sh.hit = 0;
-    }
-    __syncthreads();
-    const bool ok = sh.new_ok;
-    float m = kFarSentinel;
-    if (ok) {
-      // ---- decide: object k against objects 0..k-1 and the world
-      stage_objects(b, g.poses, pbase, o0, s0, k + 1, sm, tid, nthr);
-      __syncthreads();
-      stage_spheres(b, s0, k + 1, S, sm, sh, tid, nthr, lane);
-      stage_boxes(b, bx0, nobb, sm, tid, nthr);
-      __syncthreads();
-      if (tid == 0) build_units(k, k + 1, S, 32 * APL, g.seg_len, sm, sh);
-      __syncthreads();
-      const float rmax = __int_as_float(sh.rmax_key);
-      const float eps = 1e-5f * (__int_as_float(sh.r2max_key) + 0.01f);
-      if (nobb > 0) m = box_phase<true>(sm, nobb, sm.off[k], S, m, tid, nthr, my_box);
-      m = warp_min(m);
-      if (lane == 0 && m < -kBand) *(volatile int*)&sh.hit = 1;
-      m = pair_units<APL, true>(sm, sh, k, k + 1, S, g.seg_len, m, rmax, eps, lane, my_pairs);
-    }
-    m = warp_min(m);
-    if (lane == 0) sh.warp_min[warp] = m;
-    __syncthreads();
-    if (tid == 0) {
-      float mm = kFarSentinel;
-      for (int w = 0; w < nwarps; ++w) mm = fminf(mm, sh.warp_min[w]);
-      const bool pass = ok && !(mm < 0.f);
-      const bool bnd = sh.new_band || (ok && fabsf(mm) <= kBand);
+    if (lane == 0) {
       if (bnd) g.band[c] = 1;
       g.tries[c] += 1;
       if (pass) {
@@ -144,7 +235,7 @@ __global__ void __launch_bounds__(MAXT) gen_step_kernel(GenStepArgs g) {
         g.list_retry[atomicAdd(g.n_retry, 1)] = c;
       }
     }
-    __syncthreads();
+    __syncwarp();  // the warp's shared memory is reused by its next candidate
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -184,22 +275,22 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   if (blockIdx.x == 0 && threadIdx.x < 2 && stats) stats[threadIdx.x] = 0;
 }
 
-template <int APL, int MAXT>
-cudaError_t prepare_step_kernel(size_t smem, const sc_collide_config& cfg, int num_sms, int* grid) {
-  auto kern = gen_step_kernel<APL, MAXT>;
+template <int APL>
+cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int num_sms, int* grid) {
+  auto kern = gen_warp_kernel<APL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  *grid = num_sms * (cfg.ctas_per_sm < per_sm ? cfg.ctas_per_sm : per_sm);
+  *grid = num_sms * (ctas_per_sm < per_sm ? ctas_per_sm : per_sm);
   return cudaSuccess;
 }
 
-template <int APL, int MAXT>
+template <int APL>
 void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaStream_t s) {
-  gen_step_kernel<APL, MAXT><<<grid, threads, smem, s>>>(g);
+  gen_warp_kernel<APL><<<grid, threads, smem, s>>>(g);
 }
 
 }  // namespace
@@ -214,8 +305,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
                              int num_sms, cudaStream_t s, const char** why) {
   *why = check_collide_config(cfg);
   if (*why) return cudaErrorInvalidValue;
-  const size_t smem = make_layout(b.max_sph, b.max_obj, cfg.a_per_lane).total;
-  if (smem > 227 * 1024) { *why = "batch needs more shared memory than one CTA has (max_sph too large)"; return cudaErrorInvalidValue; }
+  if (cfg.threads > 512) { *why = "generation uses at most 512 threads per CTA"; return cudaErrorInvalidValue; }
+  const size_t smem = (size_t)(cfg.threads / 32) * make_warp_layout(b.max_obj).bytes;
+  if (smem > 227 * 1024) { *why = "threads x per-warp shared memory exceeds one CTA's (lower threads)"; return cudaErrorInvalidValue; }
   const int n = a.n_items;
   const int K = b.max_obj, R = a.max_retries;
   // scratch carve-up: 4 lists of n ints, counts[K+1] (list sizes per object),
@@ -233,9 +325,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int grid = 0;
   cudaError_t e;
   switch (cfg.a_per_lane) {
-    case 1: e = prepare_step_kernel<1, 1024>(smem, cfg, num_sms, &grid); break;
-    case 2: e = prepare_step_kernel<2, 1024>(smem, cfg, num_sms, &grid); break;
-    default: e = prepare_step_kernel<4, 512>(smem, cfg, num_sms, &grid); break;
+    case 1: e = prepare_step_kernel<1>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
+    case 2: e = prepare_step_kernel<2>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
+    default: e = prepare_step_kernel<4>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
   }
   if (e != cudaSuccess) return e;
   {
@@ -271,9 +363,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       g.n_retry = cnt_retry + k * (R + 1) + r;
       g.counter = counters + k * (R + 1) + r;
       switch (cfg.a_per_lane) {
-        case 1: launch_step<1, 1024>(g, grid, cfg.threads, smem, s); break;
-        case 2: launch_step<2, 1024>(g, grid, cfg.threads, smem, s); break;
-        default: launch_step<4, 512>(g, grid, cfg.threads, smem, s); break;
+        case 1: launch_step<1>(g, grid, cfg.threads, smem, s); break;
+        case 2: launch_step<2>(g, grid, cfg.threads, smem, s); break;
+        default: launch_step<4>(g, grid, cfg.threads, smem, s); break;
       }
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
