@@ -198,6 +198,7 @@ def run_reference(args, wl):
         "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
+                   "launch": ("eager" if args.no_graph else "CUDA graph replay") if gen else "eager",
                    "sample_per_step": f"{ns[0]} random candidates of the workload"},
         "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{ns[0]} random candidates per step of the {args.workload} workload"},
@@ -253,7 +254,7 @@ def run_ours(args, wl):
             if ev:
                 ev[0].record(stream)
             sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
-                        out=(valid, band, tries))
+                        out=(valid, band, tries), use_graph=not args.no_graph)
             if ev:
                 ev[1].record(stream)
         else:
@@ -371,6 +372,7 @@ def run_ours(args, wl):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
+                   "launch": ("eager" if args.no_graph else "CUDA graph replay") if gen else "eager",
                    "collide_launch": {"shape": list(cfg) if cfg else None, "source": tune_info},
                    "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
                    "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
@@ -412,6 +414,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the library's default collide launch shape")
     ap.add_argument("--collide-config", type=str, default="", help="threads,a_per_lane,seg_len,ctas_per_sm")
     ap.add_argument("--tune-verbose", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the generation steps eagerly")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.workload == "ragged" and args.templates != 4096:

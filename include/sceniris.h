@@ -212,6 +212,8 @@ typedef struct {
   uint64_t seed;        /* Philox key of the pose draws */
   int32_t max_attempts; /* proposals per object per try, 1..1024 (as sc_sample_params) */
   int32_t max_retries;  /* retries per object after its first try, 0..1000 (the paper uses 10) */
+  int32_t use_graph;    /* 1: capture the launch sequence into a CUDA graph once (per batch, order,
+                           output pointers, retries and launch shape) and replay it; 0: launch eagerly */
 } sc_gen_params;
 
 /* Generate scenes: the paper's placement loop (Sec. IV-A, Fig. 2) over the
@@ -237,7 +239,10 @@ typedef struct {
  * The first call (or one with more candidates than before) allocates the
  * context's generation scratch (4 int32 lists of the candidates plus
  * counters); later calls reuse it. Enqueues 1 + max_obj * (max_retries + 1)
- * kernels; launches whose list is empty exit at once.
+ * kernels (as one graph launch when use_graph = 1; the seed is read from
+ * device memory, so a replay with a new seed is not re-captured); launches
+ * whose list is empty exit at once. A call with use_graph = 1 must not itself
+ * be issued inside another stream capture.
  * Errors: SC_ERR_INVALID (NULL outputs, max_attempts / max_retries out of
  * range, bad config, batch limits), SC_ERR_OOM, SC_ERR_CUDA. */
 sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,

@@ -42,7 +42,7 @@ class ScSampleParams(ctypes.Structure):
 
 
 class ScGenParams(ctypes.Structure):
-    _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("max_retries", I32)]
+    _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("max_retries", I32), ("use_graph", I32)]
 
 
 class CollideConfig(ctypes.Structure):
@@ -235,7 +235,8 @@ def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Te
 
 
 def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, max_retries: int = 10,
-             order: torch.Tensor | None = None, config=None, poses: torch.Tensor | None = None, out=None):
+             order: torch.Tensor | None = None, config=None, poses: torch.Tensor | None = None, out=None,
+             use_graph: bool = True):
     """sc_generate. Returns (poses [P,4] f32, valid [n_cand] u8, band [n_cand] u8, tries [n_cand] i32)."""
     dev = torch.device("cuda", ctx.device)
     poses = db.new_poses(dev) if poses is None else poses
@@ -248,7 +249,7 @@ def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, m
     cfg = None
     if config is not None:
         cfg = config if isinstance(config, CollideConfig) else CollideConfig(*config)
-    p = ScGenParams(seed, max_attempts, max_retries)
+    p = ScGenParams(seed, max_attempts, max_retries, int(use_graph))
     n = 0 if order is None else int(order.numel())
     _check(lib().sc_generate(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(order), n,
                              None if cfg is None else ctypes.byref(cfg), _ptr(poses), _ptr(valid), _ptr(band),

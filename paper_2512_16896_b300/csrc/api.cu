@@ -23,6 +23,13 @@ struct sc_ctx {
   // grow-on-demand scratch of sc_generate (candidate lists and counters)
   void* gen_scratch = nullptr;
   size_t gen_scratch_bytes = 0;
+  // sc_generate's launch sequence captured as a CUDA graph, and what it was captured for
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t gen_graph = nullptr;
+  cudaGraphExec_t gen_exec = nullptr;
+  unsigned char gen_key[512] = {};
+  size_t gen_key_len = 0;
+  unsigned long long seed_host = 0;
 };
 
 namespace {
@@ -129,6 +136,9 @@ void sc_ctx_destroy(sc_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->scratch);
+  if (ctx->gen_exec) cudaGraphExecDestroy(ctx->gen_exec);
+  if (ctx->gen_graph) cudaGraphDestroy(ctx->gen_graph);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
   delete ctx;
 }
@@ -266,7 +276,10 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   sc::GenerateLaunch a;
   a.order = order;
   a.n_items = n;
-  a.seed = params->seed;
+  // the seed lives in device scratch (last 8 bytes), written before each run
+  unsigned long long* seed_dev =
+      reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->gen_scratch) + need - 8);
+  a.seed_dev = seed_dev;
   a.max_attempts = params->max_attempts;
   a.max_retries = params->max_retries;
   a.poses = poses;
@@ -276,10 +289,66 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.scratch = ctx->gen_scratch;
   a.stats = ctx->d_stats;
   a.status = ctx->d_status;
+  ctx->seed_host = params->seed;
+  cudaError_t e = cudaMemcpyAsync(seed_dev, &ctx->seed_host, 8, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "seed upload");
   const char* why = nullptr;
-  cudaError_t e = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->stream, &why);
-  if (why) return fail(SC_ERR_INVALID, "generate config: %s", why);
-  if (e != cudaSuccess) return cuda_fail(e, "generate launch");
+  if (!params->use_graph) {
+    e = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->stream, &why);
+    if (why) return fail(SC_ERR_INVALID, "generate config: %s", why);
+    if (e != cudaSuccess) return cuda_fail(e, "generate launch");
+    return SC_OK;
+  }
+  // graph replay: capture once per (batch, list, outputs, tries, launch shape)
+  struct Key {
+    sc_scene_batch batch;
+    const int32_t* order;
+    int32_t n, max_attempts, max_retries;
+    sc_collide_config cfg;
+    float* poses;
+    uint8_t* valid;
+    uint8_t* band;
+    int32_t* tries;
+    void* scratch;
+  } key;
+  static_assert(sizeof(Key) <= sizeof(ctx->gen_key), "graph key too large");
+  std::memset(&key, 0, sizeof(key));
+  key.batch = *batch;
+  key.order = order;
+  key.n = n;
+  key.max_attempts = params->max_attempts;
+  key.max_retries = params->max_retries;
+  key.cfg = cfg;
+  key.poses = poses;
+  key.valid = valid;
+  key.band = band;
+  key.tries = tries;
+  key.scratch = ctx->gen_scratch;
+  const bool hit = ctx->gen_exec && ctx->gen_key_len == sizeof(key) && !std::memcmp(ctx->gen_key, &key, sizeof(key));
+  if (!hit) {
+    if (ctx->gen_exec) { cudaGraphExecDestroy(ctx->gen_exec); ctx->gen_exec = nullptr; }
+    if (ctx->gen_graph) { cudaGraphDestroy(ctx->gen_graph); ctx->gen_graph = nullptr; }
+    ctx->gen_key_len = 0;
+    if (!ctx->capture_stream) {
+      e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t e_enq = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->capture_stream, &why);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (why) { if (graph) cudaGraphDestroy(graph); return fail(SC_ERR_INVALID, "generate config: %s", why); }
+    if (e_enq != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e_enq, "generate capture"); }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->gen_exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphInstantiate"); }
+    ctx->gen_graph = graph;
+    std::memcpy(ctx->gen_key, &key, sizeof(key));
+    ctx->gen_key_len = sizeof(key);
+  }
+  e = cudaGraphLaunch(ctx->gen_exec, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return SC_OK;
 }
 

@@ -26,7 +26,7 @@ using namespace core;
 
 struct GenStepArgs {
   sc_scene_batch b;
-  uint64_t seed;
+  const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, retry, max_retries, k, seg_len;
   const int32_t* list_in;
   const int* n_in;
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
   float* Bb = reinterpret_cast<float*>(base + WL.beta);
   const int n_items = *(volatile const int*)g.n_in;
   const int k = g.k;
+  const uint64_t seed = *g.seed;
   unsigned long long my_pairs = 0, my_box = 0;
 
   for (;;) {
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
     r.band = true;
     r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sup.ok) {
-      r = warp_sample_object(b, sup, g.seed, g.max_attempts, g.retry, c, k, o0, g.poses, pbase, g.status, lane);
+      r = warp_sample_object(b, sup, seed, g.max_attempts, g.retry, c, k, o0, g.poses, pbase, g.status, lane);
     } else if (lane == 0) {
       latch_error(g.status, kDevBadPolygon);
     }
@@ -298,7 +299,7 @@ void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaS
 size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries) {
   const size_t lists = 4 * (size_t)n_cand * sizeof(int32_t);
   const size_t counts = (size_t)(max_obj + 1) + (size_t)max_obj * (max_retries + 1);
-  return lists + 2 * counts * sizeof(int) + 256;
+  return lists + 2 * counts * sizeof(int) + 256;  // + 256: the seed scalar and alignment
 }
 
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
@@ -321,6 +322,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int* cnt_retry = counts + (K + 1);
   unsigned int* counters = reinterpret_cast<unsigned int*>(counts + n_counts);
   const int n_counters = K * (R + 1);
+  const unsigned long long* seed_dev = a.seed_dev;
 
   int grid = 0;
   cudaError_t e;
@@ -341,7 +343,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   }
   GenStepArgs g;
   g.b = b;
-  g.seed = a.seed;
+  g.seed = seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
   g.seg_len = cfg.seg_len;

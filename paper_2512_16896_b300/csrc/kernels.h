@@ -39,7 +39,7 @@ sc_status validate_batch(const sc_scene_batch* b);
 struct GenerateLaunch {
   const int32_t* order;  // candidates to generate (NULL: 0..n_items-1)
   int n_items;
-  uint64_t seed;
+  const unsigned long long* seed_dev;  // device scalar holding the Philox seed
   int max_attempts, max_retries;
   float* poses;
   uint8_t* valid;

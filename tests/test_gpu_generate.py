@@ -102,3 +102,23 @@ def test_generate_full_ragged_sampled(sc, ctx):
     op, ov, ob, ot = oracle.generate(b, seed=2, active=pick)
     compare(b, gp, gv, gb, gt, op, ov, ob, ot, pick, max_band=0.05)
     assert gv.sum().item() > 0
+
+
+def test_graph_replay_equals_eager_and_takes_new_seeds(sc, ctx):
+    """use_graph=1 captures once and replays; a new seed (read from device
+    memory by the kernels) changes the result exactly as an eager run does."""
+    b = synth.ragged(seed=9, n_templates=20, cand_per_template=8, obj_range=(2, 16))
+    db = sc.DeviceBatch(b)
+    order = torch.from_numpy(sc.order_by_work(b)).cuda()
+    poses = db.new_poses()
+    out = [torch.zeros(b.n_cand, dtype=torch.uint8, device="cuda"), torch.zeros(b.n_cand, dtype=torch.uint8, device="cuda"),
+           torch.zeros(b.n_cand, dtype=torch.int32, device="cuda")]
+    for seed in (11, 12, 11):
+        sc.generate(ctx, db, seed=seed, order=order, poses=poses, out=out, use_graph=True)
+        g = [x.clone() for x in (poses, *out)]
+        e = sc.generate(ctx, db, seed=seed, order=order, use_graph=False)
+        ctx.synchronize()
+        for x, y in zip(g, e):
+            assert torch.equal(torch.nan_to_num(x, 7.0), torch.nan_to_num(y, 7.0))
+    op, ov, ob, ot = oracle.generate(b, seed=11)
+    compare(b, g[0], g[1], g[2], g[3], op, ov, ob, ot, np.arange(b.n_cand, dtype=np.int32))
