@@ -82,7 +82,9 @@ enum { SC_REL_FREE = 0, SC_REL_ON_TOP = 1, SC_REL_NEXT_TO = 2, SC_REL_KIND_MASK 
  *  sph_local     float [S][4] sphere (x, y, z, r) in its object's frame.
  *  obj_half      float [O][4] (Hx, Hy, Hz, rho): half extents of the object's box in its
  *                             frame (its bottom face rests on the support) and the
- *                             radius of its xy bounding circle.
+ *                             radius of its xy bounding circle. The box must contain
+ *                             every sphere of the object: sc_generate skips pairs of
+ *                             objects whose bounding balls (radius |H|) are apart.
  *  obj_rel       int32 [O]    kind | SC_REL_REACH flag | (reference local index << 8);
  *                             the reference (parent / anchor) is an EARLIER object.
  *  obj_rel_param float [O][4] (dmin, dmax, ratio_on_support, unused).

@@ -11,6 +11,7 @@ namespace sc {
 constexpr float kBand = 1e-5f;                       // decision band (metres)
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kFarSentinel = 1e18f;                // "no distance seen yet"
+constexpr float kBroadMargin = 1e-3f;                // object-level culling slack (metres), >> kBand + FP32 error
 constexpr int kMaxObj = 256;                         // object ids fit in a byte
 constexpr int kMaxSph = 8192;                        // spheres of one template
 constexpr int kMaxSphPerObj = 256;                   // spheres of one object (generation)

@@ -47,7 +47,7 @@ struct GenStepArgs {
 // yaw) and the new object's spheres in the world frame (relative to object
 // 0's position) with |c|^2 - r^2.
 struct WarpLayout {
-  int off, pose, sc, B, beta, bytes;
+  int off, pose, sc, kobj, kpref, B, beta, bytes;
 };
 
 __host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
@@ -55,7 +55,9 @@ __host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
   W.off = 0;
   W.pose = align16(4 * (max_obj + 1));
   W.sc = align16(W.pose + 16 * max_obj);
-  W.B = align16(W.sc + 8 * max_obj);
+  W.kobj = align16(W.sc + 8 * max_obj);
+  W.kpref = align16(W.kobj + 4 * max_obj);
+  W.B = align16(W.kpref + 4 * (max_obj + 1));
   W.beta = align16(W.B + 16 * (kMaxSphPerObj + kPad));
   W.bytes = align16(W.beta + 4 * (kMaxSphPerObj + kPad));
   return W;
@@ -64,8 +66,12 @@ __host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
 // One warp per candidate: sample object k, then decide whether any sphere of
 // object k is closer than the band to a sphere of objects 0..k-1 (A side,
 // moved into registers 32*APL at a time) or to a world box.
+// Broad phase (exact): every sphere of an object lies in the ball of radius
+// |H| (its box's half-diagonal) around the object's frame origin, so two
+// objects whose origins are farther apart than |H_j| + |H_k| + margin have no
+// sphere pair within the band; only the other objects' spheres are streamed.
 template <int APL>
-__global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
+__global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
   const WarpLayout WL = make_warp_layout(b.max_obj);
@@ -74,6 +80,8 @@ __global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
   int* off = reinterpret_cast<int*>(base + WL.off);
   float4* opose = reinterpret_cast<float4*>(base + WL.pose);
   float2* osc = reinterpret_cast<float2*>(base + WL.sc);
+  int* kobj = reinterpret_cast<int*>(base + WL.kobj);
+  int* kpref = reinterpret_cast<int*>(base + WL.kpref);
   float4* Bs = reinterpret_cast<float4*>(base + WL.B);
   float* Bb = reinterpret_cast<float*>(base + WL.beta);
   const int n_items = *(volatile const int*)g.n_in;
@@ -138,6 +146,47 @@ __global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
       }
       __syncwarp();
       const float4 ref = opose[0];
+      // ---- broad phase: earlier objects whose bounding balls come near object k's
+      int nkeep = 0;
+      {
+        const float4 pk = opose[k];
+        const float4 Hk = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + k);
+        const float rk = sqrtf(Hk.x * Hk.x + Hk.y * Hk.y + Hk.z * Hk.z);
+        for (int j0 = 0; j0 < k; j0 += 32) {
+          const int j = j0 + lane;
+          bool keep = false;
+          int cnt = 0;
+          if (j < k) {
+            const float4 pj = opose[j];
+            const float4 Hj = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
+            const float rj = sqrtf(Hj.x * Hj.x + Hj.y * Hj.y + Hj.z * Hj.z);
+            const float dx = pj.x - pk.x, dy = pj.y - pk.y, dz = pj.z - pk.z;
+            const float lim = rj + rk + kBroadMargin;
+            keep = dx * dx + dy * dy + dz * dz <= lim * lim;
+            cnt = off[j + 1] - off[j];
+          }
+          const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+          // prefix of kept sphere counts within this chunk of 32 objects
+          int pre = keep ? cnt : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+            if (lane >= o) pre += v;
+          }
+          const int base_sph = nkeep == 0 ? 0 : kpref[nkeep];
+          if (keep) {
+            const int slot = nkeep + __popc(mask & ((1u << lane) - 1u));
+            kobj[slot] = j;
+            kpref[slot + 1] = base_sph + pre;
+          }
+          if (nkeep == 0 && lane == 0) kpref[0] = 0;
+          nkeep += __popc(mask);
+          __syncwarp();
+        }
+        if (lane == 0 && nkeep == 0) kpref[0] = 0;
+        __syncwarp();
+      }
+      const int Skeep = kpref[nkeep];
       // ---- object k's spheres (B side)
       {
         const float4 p = opose[k];
@@ -190,18 +239,20 @@ __global__ void __launch_bounds__(512) gen_warp_kernel(GenStepArgs g) {
         m = warp_min(m);
         bool alive = !(m < -kBand);
         r2 = -warp_min(-r2);
-        // ---- object k vs objects 0..k-1 (A side in registers)
-        for (int i0 = 0; alive && i0 < Sprev; i0 += 32 * APL) {
+        // ---- object k vs the kept earlier objects (A side in registers)
+        for (int i0 = 0; alive && i0 < Skeep; i0 += 32 * APL) {
           ABlock<APL> A;
           float a2max = 0.f;
           int nval = 0;
 #pragma unroll
           for (int s = 0; s < APL; ++s) {
-            const int q = i0 + s * 32 + lane;
-            const bool valid = q < Sprev;
+            const int qq = i0 + s * 32 + lane;
+            const bool valid = qq < Skeep;
             float x = 0.f, y = 0.f, z = 0.f, rr = 0.f;
             if (valid) {
-              const int j = upper_index(off, k + 1, q);
+              const int jj = upper_index(kpref, nkeep + 1, qq);
+              const int j = kobj[jj];
+              const int q = off[j] + (qq - kpref[jj]);
               const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
               const float4 p = opose[j];
               const float2 sc2 = osc[j];
