@@ -251,6 +251,50 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
                       int32_t n_order, const sc_collide_config* config, float* poses, uint8_t* valid, uint8_t* band,
                       int32_t* tries);
 
+/* --------------------------------------------------------- reachability */
+
+/* 7-DoF serial arm in standard Denavit-Hartenberg form:
+ * T_i = Rz(q_i) Tz(d_i) Tx(a_i) Rx(alpha_i), tool frame = frame 7, joint
+ * limits [qmin_i, qmax_i]. Targets are expressed in the arm's base frame. */
+typedef struct {
+  float dh_d[7], dh_a[7], dh_alpha[7], qmin[7], qmax[7];
+} sc_arm;
+
+typedef struct {
+  float lambda;   /* damping (0.05) */
+  float tol_pos;  /* success: position error <= tol_pos (metres) */
+  float tol_rot;  /* and rotation angle <= tol_rot (radians, in (0, pi/2)) */
+  int32_t iters;  /* DLS steps per seed (100) */
+  int32_t seeds;  /* seeds per target, 1..32 */
+  uint64_t seed;  /* Philox key of the seeds */
+} sc_ik_params;
+
+/* Can the arm reach each target? (Sec. IV-E: the sampled pose is rejected when
+ * the robot cannot reach it; the paper looks the answer up in an RM4D map,
+ * this build solves damped-least-squares IK.) Seeds q_j = qmin_j + (qmax_j -
+ * qmin_j) u_j with u from Philox(seed; target id, seed index, j / 4, 0), word
+ * j % 4. All seeds of a target iterate in lock step: check every seed (position
+ * error <= tol_pos and angle(R^T R*) <= tol_rot), and stop at the first check
+ * where one succeeds, returning the lowest such seed; otherwise take one step
+ * dq = J^T (J J^T + lambda^2 I)^-1 e with e = [p* - p; 1/2 sum_k r_k x r*_k] and
+ * clamp q to the limits. After `iters` steps and a final check the target is
+ * unreachable and the seed with the smallest position error is returned.
+ * targets    float [n][12] (R row-major, p), base frame.
+ * target_ids uint32 [n] Philox counter word of each target, or NULL (= index).
+ * reachable  u8 [n]; q_out float [n][7]; err float [n][2] = (position error,
+ *            rotation angle) of the returned configuration.
+ * Errors: SC_ERR_INVALID (NULL pointers, seeds outside 1..32, iters < 0,
+ * non-positive tolerances or tol_rot >= pi/2). */
+sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params, const float* targets,
+                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err);
+
+/* One damped-least-squares step (the update of sc_ik_reach, including the
+ * clamp) for n independent (target, configuration) pairs: q_out[i] = step of
+ * q_in[i] towards targets[i]. tool (optional, float [n][12]) receives the
+ * forward kinematics of q_in[i] (R row-major, p). */
+sc_status sc_ik_dls_step(sc_ctx* ctx, const sc_arm* arm, float lambda, const float* targets, const float* q_in,
+                         int32_t n, float* q_out, float* tool);
+
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],
  * cand_tmpl_off [T+1]; out_order [n_cand] receives candidate indices. */

@@ -17,5 +17,9 @@ from ._native import (  # noqa: F401
     collide,
     collide_last_work,
     generate,
+    ik_reach,
+    ik_dls_step,
+    make_arm,
+    ik_params,
     order_by_work,
 )

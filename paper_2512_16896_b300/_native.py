@@ -45,6 +45,24 @@ class ScGenParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("max_retries", I32), ("use_graph", I32)]
 
 
+class ScArm(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float * 7) for n in ("dh_d", "dh_a", "dh_alpha", "qmin", "qmax")]
+
+
+class ScIkParams(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_float), ("tol_pos", ctypes.c_float), ("tol_rot", ctypes.c_float), ("iters", I32),
+                ("seeds", I32), ("seed", ctypes.c_uint64)]
+
+
+def make_arm(d, a, alpha, qmin, qmax) -> ScArm:
+    f = lambda v: (ctypes.c_float * 7)(*[float(x) for x in v])
+    return ScArm(f(d), f(a), f(alpha), f(qmin), f(qmax))
+
+
+def ik_params(lam=0.05, tol_pos=5e-3, tol_rot=0.05, iters=100, seeds=32, seed=3) -> ScIkParams:
+    return ScIkParams(lam, tol_pos, tol_rot, iters, seeds, seed)
+
+
 class CollideConfig(ctypes.Structure):
     _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32), ("decide_only", I32)]
 
@@ -70,6 +88,8 @@ SIGNATURES = {
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
     "sc_generate": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScGenParams), P, I32,
                                    ctypes.POINTER(CollideConfig), P, P, P, P]),
+    "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P]),
+    "sc_ik_dls_step": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.c_float, P, P, I32, P, P]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
 }
 
@@ -255,6 +275,28 @@ def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, m
                              None if cfg is None else ctypes.byref(cfg), _ptr(poses), _ptr(valid), _ptr(band),
                              _ptr(tries)))
     return poses, valid, band, tries
+
+
+def ik_reach(ctx: Context, arm: ScArm, params: ScIkParams, targets: torch.Tensor, target_ids=None):
+    """sc_ik_reach. targets [n,12] f32 (device). Returns (reach u8 [n], q f32 [n,7], err f32 [n,2])."""
+    dev = torch.device("cuda", ctx.device)
+    n = targets.shape[0]
+    reach = torch.empty(n, dtype=torch.uint8, device=dev)
+    q = torch.empty((n, 7), dtype=torch.float32, device=dev)
+    err = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    _check(lib().sc_ik_reach(ctx.handle, ctypes.byref(arm), ctypes.byref(params), _ptr(targets), _ptr(target_ids), n,
+                             _ptr(reach), _ptr(q), _ptr(err)))
+    return reach, q, err
+
+
+def ik_dls_step(ctx: Context, arm: ScArm, lam: float, targets: torch.Tensor, q_in: torch.Tensor):
+    """sc_ik_dls_step. Returns (q_out [n,7], tool [n,12] = FK of q_in)."""
+    n = targets.shape[0]
+    q_out = torch.empty_like(q_in)
+    tool = torch.empty((n, 12), dtype=torch.float32, device=q_in.device)
+    _check(lib().sc_ik_dls_step(ctx.handle, ctypes.byref(arm), lam, _ptr(targets), _ptr(q_in), n, _ptr(q_out),
+                                _ptr(tool)))
+    return q_out, tool
 
 
 def collide_last_work(ctx: Context):

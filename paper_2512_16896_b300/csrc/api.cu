@@ -352,6 +352,39 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   return SC_OK;
 }
 
+sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params, const float* targets,
+                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!arm || !params) return fail(SC_ERR_INVALID, "arm or params is NULL");
+  if (n < 0) return fail(SC_ERR_INVALID, "n < 0");
+  if (n == 0) return SC_OK;
+  if (!targets || !reachable || !q_out || !err) return fail(SC_ERR_INVALID, "an input or output pointer is NULL");
+  if (params->seeds < 1 || params->seeds > 32) return fail(SC_ERR_INVALID, "seeds = %d outside 1..32", params->seeds);
+  if (params->iters < 0) return fail(SC_ERR_INVALID, "iters < 0");
+  if (!(params->tol_pos > 0.f) || !(params->tol_rot > 0.f) || !(params->tol_rot < 1.5707963f) || !(params->lambda >= 0.f))
+    return fail(SC_ERR_INVALID, "tolerances must be positive, tol_rot < pi/2, lambda >= 0");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::launch_ik(*arm, *params, targets, target_ids, n, reachable, q_out, err, nullptr, ctx->num_sms,
+                                ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ik_kernel launch");
+  return SC_OK;
+}
+
+sc_status sc_ik_dls_step(sc_ctx* ctx, const sc_arm* arm, float lambda, const float* targets, const float* q_in,
+                         int32_t n, float* q_out, float* tool) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!arm) return fail(SC_ERR_INVALID, "arm is NULL");
+  if (n < 0) return fail(SC_ERR_INVALID, "n < 0");
+  if (n == 0) return SC_OK;
+  if (!targets || !q_in || !q_out) return fail(SC_ERR_INVALID, "an input or output pointer is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::launch_ik_step(*arm, lambda, targets, q_in, n, q_out, tool, ctx->num_sms, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ik_step_kernel launch");
+  return SC_OK;
+}
+
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs) {
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;

@@ -55,6 +55,12 @@ size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
                              int num_sms, cudaStream_t s, const char** why);
 
+cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
+                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, int num_sms,
+                      cudaStream_t s);
+cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets, const float* q_in, int n,
+                           float* q_out, float* tool, int num_sms, cudaStream_t s);
+
 // NULL if the launch shape is valid, else why not.
 const char* check_collide_config(const sc_collide_config& cfg);
 
