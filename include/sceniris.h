@@ -295,6 +295,65 @@ sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params
 sc_status sc_ik_dls_step(sc_ctx* ctx, const sc_arm* arm, float lambda, const float* targets, const float* q_in,
                          int32_t n, float* q_out, float* tool);
 
+/* ------------------------------------------------------------ surrogate */
+
+/* Learned reachability gate (not in the paper, which queries RM4D for
+ * Sec. IV-E): an MLP 9 -> 256 -> 256 -> 256 -> 1 with SiLU activations on the
+ * features x = (p, R[:,0], R[:,1]) of a target (position and the first two
+ * columns of its rotation, base frame), standardised by a stored mean / std.
+ * BF16 weights and activations on the tensor cores, FP32 accumulation, biases
+ * and Adam state; the bf16 rounding points are: standardised input, every
+ * SiLU output, the weight copies, and every dL/da in the backward pass.
+ * Parameters are packed FP32: W1 [256][9], b1 [256], W2 [256][256], b2, W3
+ * [256][256], b3, W4 [256], b4 [1] (sc_mlp_param_count() = 134401). */
+typedef struct sc_mlp sc_mlp;
+
+int32_t sc_mlp_param_count(void);
+/* New network: weights and biases U(-1/sqrt(fan_in), +1/sqrt(fan_in)) from
+ * Philox(seed), mean 0 / std 1 standardisation, threshold 0, Adam step 0. */
+sc_status sc_mlp_create(sc_ctx* ctx, uint64_t seed, sc_mlp** out);
+void sc_mlp_destroy(sc_mlp* mlp);
+/* Copy parameters / standardisation / threshold to or from HOST memory (any
+ * pointer may be NULL to skip it). Synchronises the context's stream. */
+sc_status sc_mlp_get(sc_ctx* ctx, const sc_mlp* mlp, float* params, float* mu, float* sigma, float* tau);
+sc_status sc_mlp_set(sc_ctx* ctx, sc_mlp* mlp, const float* params, const float* mu, const float* sigma, float tau);
+/* logits[i] of targets[i] (float [n][12], device). */
+sc_status sc_surrogate_infer(sc_ctx* ctx, const sc_mlp* mlp, const float* targets, int32_t n, float* logits);
+/* Gradients of the mean binary cross-entropy on logits,
+ * BCE(z, y) = max(z, 0) - z y + log(1 + exp(-|z|)), over all n targets
+ * (labels u8 [n], 1 = reachable): grads (device, packed like the parameters,
+ * may be NULL) and the loss (host, may be NULL). n <= 2^20. */
+sc_status sc_surrogate_grads(sc_ctx* ctx, sc_mlp* mlp, const float* targets, const uint8_t* labels, int32_t n,
+                             float* grads, float* loss);
+
+typedef struct {
+  int32_t epochs, batch;  /* passes over the data; minibatch size (16..65536) */
+  float lr, beta1, beta2, eps;  /* Adam (1e-3, 0.9, 0.999, 1e-8) */
+  uint64_t seed;          /* epoch shuffles */
+} sc_train_params;
+
+/* One Adam step with the given gradients (device, packed; NULL = the last
+ * gradients sc_surrogate_grads or training computed):
+ * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+sc_status sc_mlp_adam_step(sc_ctx* ctx, sc_mlp* mlp, const float* grads, const sc_train_params* params);
+/* Train on n labelled targets (device): a fresh network (Adam step 0) first
+ * takes its standardisation from the training set; every epoch visits the
+ * targets in a shuffled order (an affine permutation mod n) in whole
+ * minibatches, each one gradient + Adam step. loss_per_epoch (host, may be
+ * NULL) receives the mean BCE of each epoch's last minibatch. */
+sc_status sc_surrogate_train(sc_ctx* ctx, sc_mlp* mlp, const float* targets, const uint8_t* labels, int32_t n,
+                             const sc_train_params* params, float* loss_per_epoch);
+/* Set the gate threshold to the largest tau whose recall on these labelled
+ * targets is >= min_recall (ties included: keep z >= tau); report the recall
+ * and the fraction of targets that pass. */
+sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* mlp, const float* targets, const uint8_t* labels, int32_t n,
+                                      float min_recall, float* tau, float* recall, float* pass_rate);
+/* Checkpoint: parameters, Adam moments and step, standardisation and
+ * threshold in one little-endian file ("SCMLP001" header). */
+sc_status sc_mlp_save(sc_ctx* ctx, const sc_mlp* mlp, const char* path);
+sc_status sc_mlp_load(sc_ctx* ctx, const char* path, sc_mlp** out);
+
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],
  * cand_tmpl_off [T+1]; out_order [n_cand] receives candidate indices. */

@@ -21,5 +21,7 @@ from ._native import (  # noqa: F401
     ik_dls_step,
     make_arm,
     ik_params,
+    Surrogate,
+    train_params,
     order_by_work,
 )

@@ -63,6 +63,15 @@ def ik_params(lam=0.05, tol_pos=5e-3, tol_rot=0.05, iters=100, seeds=32, seed=3)
     return ScIkParams(lam, tol_pos, tol_rot, iters, seeds, seed)
 
 
+class ScTrainParams(ctypes.Structure):
+    _fields_ = [("epochs", I32), ("batch", I32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def train_params(epochs=4, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=4) -> ScTrainParams:
+    return ScTrainParams(epochs, batch, lr, beta1, beta2, eps, seed)
+
+
 class CollideConfig(ctypes.Structure):
     _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32), ("decide_only", I32)]
 
@@ -90,6 +99,18 @@ SIGNATURES = {
                                    ctypes.POINTER(CollideConfig), P, P, P, P]),
     "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P]),
     "sc_ik_dls_step": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.c_float, P, P, I32, P, P]),
+    "sc_mlp_param_count": (I32, []),
+    "sc_mlp_create": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(P)]),
+    "sc_mlp_destroy": (None, [P]),
+    "sc_mlp_get": (ctypes.c_int, [P, P, P, P, P, P]),
+    "sc_mlp_set": (ctypes.c_int, [P, P, P, P, P, ctypes.c_float]),
+    "sc_surrogate_infer": (ctypes.c_int, [P, P, P, I32, P]),
+    "sc_surrogate_grads": (ctypes.c_int, [P, P, P, P, I32, P, P]),
+    "sc_mlp_adam_step": (ctypes.c_int, [P, P, P, ctypes.POINTER(ScTrainParams)]),
+    "sc_surrogate_train": (ctypes.c_int, [P, P, P, P, I32, ctypes.POINTER(ScTrainParams), P]),
+    "sc_surrogate_tune_threshold": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, P]),
+    "sc_mlp_save": (ctypes.c_int, [P, P, ctypes.c_char_p]),
+    "sc_mlp_load": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.POINTER(P)]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
 }
 
@@ -297,6 +318,81 @@ def ik_dls_step(ctx: Context, arm: ScArm, lam: float, targets: torch.Tensor, q_i
     _check(lib().sc_ik_dls_step(ctx.handle, ctypes.byref(arm), lam, _ptr(targets), _ptr(q_in), n, _ptr(q_out),
                                 _ptr(tool)))
     return q_out, tool
+
+
+class Surrogate:
+    """An sc_mlp handle (reachability gate)."""
+
+    def __init__(self, ctx: Context, seed: int = 0, handle=None):
+        self.ctx = ctx
+        if handle is None:
+            handle = P()
+            _check(lib().sc_mlp_create(ctx.handle, seed, ctypes.byref(handle)))
+        self.handle = handle
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Surrogate":
+        h = P()
+        _check(lib().sc_mlp_load(ctx.handle, path.encode(), ctypes.byref(h)))
+        return cls(ctx, handle=h)
+
+    def save(self, path: str):
+        _check(lib().sc_mlp_save(self.ctx.handle, self.handle, path.encode()))
+
+    @staticmethod
+    def param_count() -> int:
+        return lib().sc_mlp_param_count()
+
+    def get(self):
+        """(params [134401] f32, mu [9], sigma [9], tau) as numpy."""
+        n = self.param_count()
+        p, mu, sd, tau = np.zeros(n, np.float32), np.zeros(9, np.float32), np.zeros(9, np.float32), ctypes.c_float()
+        _check(lib().sc_mlp_get(self.ctx.handle, self.handle, _ptr(p), _ptr(mu), _ptr(sd), ctypes.byref(tau)))
+        return p, mu, sd, tau.value
+
+    def set(self, params=None, mu=None, sigma=None, tau=0.0):
+        c = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+        p, m, s_ = c(params), c(mu), c(sigma)
+        _check(lib().sc_mlp_set(self.ctx.handle, self.handle, _ptr(p), _ptr(m), _ptr(s_), float(tau)))
+
+    def infer(self, targets: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(targets.shape[0], dtype=torch.float32, device=targets.device)
+        _check(lib().sc_surrogate_infer(self.ctx.handle, self.handle, _ptr(targets), targets.shape[0], _ptr(out)))
+        return out
+
+    def grads(self, targets: torch.Tensor, labels: torch.Tensor):
+        g = torch.empty(self.param_count(), dtype=torch.float32, device=targets.device)
+        loss = ctypes.c_float()
+        _check(lib().sc_surrogate_grads(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels), targets.shape[0],
+                                        _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, grads: torch.Tensor | None, params: ScTrainParams):
+        _check(lib().sc_mlp_adam_step(self.ctx.handle, self.handle, _ptr(grads), ctypes.byref(params)))
+
+    def train(self, targets: torch.Tensor, labels: torch.Tensor, params: ScTrainParams):
+        loss = np.zeros(max(1, params.epochs), np.float32)
+        _check(lib().sc_surrogate_train(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels), targets.shape[0],
+                                        ctypes.byref(params), _ptr(loss)))
+        return loss[: params.epochs]
+
+    def tune_threshold(self, targets: torch.Tensor, labels: torch.Tensor, min_recall: float = 0.99):
+        tau, rec, pr = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        _check(lib().sc_surrogate_tune_threshold(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels),
+                                                 targets.shape[0], float(min_recall), ctypes.byref(tau),
+                                                 ctypes.byref(rec), ctypes.byref(pr)))
+        return tau.value, rec.value, pr.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def collide_last_work(ctx: Context):

@@ -1,6 +1,7 @@
 // C ABI of libsceniris_b300: context management, host-side argument
 // validation and the entry points declared in include/sceniris.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -382,6 +383,291 @@ sc_status sc_ik_dls_step(sc_ctx* ctx, const sc_arm* arm, float lambda, const flo
   DeviceGuard g(ctx->device);
   cudaError_t e = sc::launch_ik_step(*arm, lambda, targets, q_in, n, q_out, tool, ctx->num_sms, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "ik_step_kernel launch");
+  return SC_OK;
+}
+
+// ------------------------------------------------------------- surrogate
+
+struct sc_mlp {
+  int device = 0;
+  sc::MlpState* st = nullptr;
+  float tau = 0.f;
+  int32_t* index = nullptr;  // epoch permutation scratch
+  int index_cap = 0;
+  float* loss_dev = nullptr;
+};
+
+int32_t sc_mlp_param_count(void) { return sc::mlp_param_count(); }
+
+sc_status sc_mlp_create(sc_ctx* ctx, uint64_t seed, sc_mlp** out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(SC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  sc_mlp* m = new (std::nothrow) sc_mlp;
+  if (!m) return fail(SC_ERR_OOM, "host allocation failed");
+  m->device = ctx->device;
+  cudaError_t e = sc::mlp_alloc(&m->st);
+  if (e == cudaSuccess) e = cudaMalloc(&m->loss_dev, 256);
+  if (e != cudaSuccess) { sc_mlp_destroy(m); return fail(SC_ERR_OOM, "surrogate allocation: %s", cudaGetErrorString(e)); }
+  e = sc::mlp_init(m->st, seed, ctx->stream);
+  if (e != cudaSuccess) { sc_mlp_destroy(m); return cuda_fail(e, "surrogate init"); }
+  *out = m;
+  return SC_OK;
+}
+
+void sc_mlp_destroy(sc_mlp* m) {
+  if (!m) return;
+  DeviceGuard g(m->device);
+  cudaDeviceSynchronize();
+  sc::mlp_free(m->st);
+  if (m->index) cudaFree(m->index);
+  if (m->loss_dev) cudaFree(m->loss_dev);
+  delete m;
+}
+
+sc_status sc_mlp_get(sc_ctx* ctx, const sc_mlp* m, float* params, float* mu, float* sigma, float* tau) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  const int n = sc::mlp_param_count();
+  if (!e && params) e = cudaMemcpy(params, sc::mlp_params_ptr(m->st), n * 4, cudaMemcpyDeviceToHost);
+  float inv[9];
+  if (!e && mu) e = cudaMemcpy(mu, sc::mlp_mu_ptr(m->st), 36, cudaMemcpyDeviceToHost);
+  if (!e && sigma) {
+    e = cudaMemcpy(inv, sc::mlp_inv_sigma_ptr(m->st), 36, cudaMemcpyDeviceToHost);
+    for (int i = 0; i < 9; ++i) sigma[i] = 1.f / inv[i];
+  }
+  if (e) return cuda_fail(e, "surrogate read-back");
+  if (tau) *tau = m->tau;
+  return SC_OK;
+}
+
+sc_status sc_mlp_set(sc_ctx* ctx, sc_mlp* m, const float* params, const float* mu, const float* sigma, float tau) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  const int n = sc::mlp_param_count();
+  if (!e && params) e = cudaMemcpy(sc::mlp_params_ptr(m->st), params, n * 4, cudaMemcpyHostToDevice);
+  if (!e && mu) e = cudaMemcpy(sc::mlp_mu_ptr(m->st), mu, 36, cudaMemcpyHostToDevice);
+  if (!e && sigma) {
+    float inv[9];
+    for (int i = 0; i < 9; ++i) {
+      if (!(sigma[i] > 0.f)) return fail(SC_ERR_INVALID, "sigma[%d] must be > 0", i);
+      inv[i] = 1.f / sigma[i];
+    }
+    e = cudaMemcpy(sc::mlp_inv_sigma_ptr(m->st), inv, 36, cudaMemcpyHostToDevice);
+  }
+  if (!e) e = sc::mlp_refresh_copies(m->st, ctx->stream);
+  if (e) return cuda_fail(e, "surrogate upload");
+  m->tau = tau;
+  return SC_OK;
+}
+
+sc_status sc_surrogate_infer(sc_ctx* ctx, const sc_mlp* m, const float* targets, int32_t n, float* logits) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (n < 0) return fail(SC_ERR_INVALID, "n < 0");
+  if (n == 0) return SC_OK;
+  if (!targets || !logits) return fail(SC_ERR_INVALID, "targets or logits is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::mlp_infer(m->st, targets, nullptr, n, logits, ctx->num_sms, ctx->stream);
+  if (e) return cuda_fail(e, "surrogate inference");
+  return SC_OK;
+}
+
+sc_status sc_surrogate_grads(sc_ctx* ctx, sc_mlp* m, const float* targets, const uint8_t* labels, int32_t n,
+                             float* grads, float* loss) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (n < 1 || n > (1 << 20)) return fail(SC_ERR_INVALID, "n = %d outside 1..2^20", n);
+  if (!targets || !labels) return fail(SC_ERR_INVALID, "targets or labels is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::mlp_reserve(m->st, n);
+  if (e) return fail(SC_ERR_OOM, "surrogate training buffers: %s", cudaGetErrorString(e));
+  e = sc::mlp_gradients(m->st, targets, labels, nullptr, n, m->loss_dev, ctx->num_sms, ctx->stream);
+  if (!e && grads)
+    e = cudaMemcpyAsync(grads, sc::mlp_grads_ptr(m->st), sc::mlp_param_count() * 4, cudaMemcpyDeviceToDevice,
+                        ctx->stream);
+  if (!e && loss) {
+    e = cudaMemcpyAsync(loss, m->loss_dev, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e) return cuda_fail(e, "surrogate gradients");
+  return SC_OK;
+}
+
+static sc_status check_train(const sc_train_params* p) {
+  if (!p) return fail(SC_ERR_INVALID, "train params is NULL");
+  if (p->epochs < 0 || p->batch < 16 || p->batch > 65536)
+    return fail(SC_ERR_INVALID, "epochs >= 0 and batch in 16..65536 required");
+  if (!(p->lr > 0.f) || !(p->beta1 >= 0.f && p->beta1 < 1.f) || !(p->beta2 >= 0.f && p->beta2 < 1.f) || !(p->eps > 0.f))
+    return fail(SC_ERR_INVALID, "lr > 0, betas in [0, 1), eps > 0 required");
+  return SC_OK;
+}
+
+sc_status sc_mlp_adam_step(sc_ctx* ctx, sc_mlp* m, const float* grads, const sc_train_params* p) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (sc_status s = check_train(p)) return s;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaSuccess;
+  if (grads)
+    e = cudaMemcpyAsync(sc::mlp_grads_ptr(m->st), grads, sc::mlp_param_count() * 4, cudaMemcpyDeviceToDevice,
+                        ctx->stream);
+  if (!e) e = sc::mlp_adam(m->st, p->lr, p->beta1, p->beta2, p->eps, ctx->stream);
+  if (e) return cuda_fail(e, "adam step");
+  return SC_OK;
+}
+
+sc_status sc_surrogate_train(sc_ctx* ctx, sc_mlp* m, const float* targets, const uint8_t* labels, int32_t n,
+                             const sc_train_params* p, float* loss_per_epoch) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (sc_status s = check_train(p)) return s;
+  if (n < p->batch) return fail(SC_ERR_INVALID, "n = %d smaller than one batch (%d)", n, p->batch);
+  if (!targets || !labels) return fail(SC_ERR_INVALID, "targets or labels is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::mlp_reserve(m->st, p->batch);
+  if (!e && m->index_cap < n) {
+    if (m->index) cudaFree(m->index);
+    m->index = nullptr;
+    m->index_cap = 0;
+    e = cudaMalloc(&m->index, (size_t)n * 4);
+    if (!e) m->index_cap = n;
+  }
+  if (e) return fail(SC_ERR_OOM, "training buffers: %s", cudaGetErrorString(e));
+  if (sc::mlp_step(m->st) == 0) {  // a fresh network takes its input standardisation from the training set
+    e = sc::mlp_set_norm_from(m->st, targets, n, ctx->stream);
+    if (e) return cuda_fail(e, "feature standardisation");
+  }
+  const int nb = n / p->batch;  // whole batches per epoch (the remainder changes with the shuffle)
+  for (int ep = 0; ep < p->epochs; ++ep) {
+    e = sc::mlp_epoch_index(n, p->seed, (int)(sc::mlp_step(m->st) / nb), m->index, ctx->stream);
+    if (e) return cuda_fail(e, "epoch shuffle");
+    float loss_acc = 0.f;
+    for (int bi = 0; bi < nb; ++bi) {
+      e = sc::mlp_gradients(m->st, targets, labels, m->index + (size_t)bi * p->batch, p->batch, m->loss_dev,
+                            ctx->num_sms, ctx->stream);
+      if (!e) e = sc::mlp_adam(m->st, p->lr, p->beta1, p->beta2, p->eps, ctx->stream);
+      if (e) return cuda_fail(e, "training step");
+      if (loss_per_epoch && bi == nb - 1) {  // the epoch's last batch reports its mean BCE
+        float l = 0.f;
+        e = cudaMemcpyAsync(&l, m->loss_dev, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (!e) e = cudaStreamSynchronize(ctx->stream);
+        if (e) return cuda_fail(e, "loss read-back");
+        loss_acc = l;
+      }
+    }
+    if (loss_per_epoch) loss_per_epoch[ep] = loss_acc;
+  }
+  return SC_OK;
+}
+
+sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* m, const float* targets, const uint8_t* labels, int32_t n,
+                                      float min_recall, float* tau_out, float* recall_out, float* pass_rate_out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (n < 1 || !targets || !labels) return fail(SC_ERR_INVALID, "need n >= 1 targets and labels");
+  if (!(min_recall > 0.f && min_recall <= 1.f)) return fail(SC_ERR_INVALID, "min_recall must be in (0, 1]");
+  DeviceGuard g(ctx->device);
+  float* logits = nullptr;
+  cudaError_t e = cudaMalloc(&logits, (size_t)n * 4);
+  if (e) return fail(SC_ERR_OOM, "logit buffer: %s", cudaGetErrorString(e));
+  e = sc::mlp_infer(m->st, targets, nullptr, n, logits, ctx->num_sms, ctx->stream);
+  std::vector<float> z(n);
+  std::vector<uint8_t> y(n);
+  if (!e) e = cudaMemcpyAsync(z.data(), logits, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaMemcpyAsync(y.data(), labels, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(logits);
+  if (e) return cuda_fail(e, "threshold tuning");
+  // largest tau with recall >= min_recall: keep the top ceil(min_recall * P) positive logits
+  std::vector<float> pos;
+  for (int i = 0; i < n; ++i)
+    if (y[i]) pos.push_back(z[i]);
+  if (pos.empty()) return fail(SC_ERR_INVALID, "no positive labels");
+  std::sort(pos.begin(), pos.end(), std::greater<float>());
+  const size_t need = (size_t)std::ceil((double)min_recall * pos.size());
+  const float tau = pos[std::min(pos.size(), std::max<size_t>(need, 1)) - 1];
+  size_t tp = 0, pass = 0;
+  for (int i = 0; i < n; ++i)
+    if (z[i] >= tau) { ++pass; tp += y[i] ? 1 : 0; }
+  m->tau = tau;
+  if (tau_out) *tau_out = tau;
+  if (recall_out) *recall_out = (float)tp / pos.size();
+  if (pass_rate_out) *pass_rate_out = (float)pass / n;
+  return SC_OK;
+}
+
+// File: "SCMLP001", int64 step, int32 n_params, float params[n], m[n], v[n], mu[9], sigma[9], tau.
+sc_status sc_mlp_save(sc_ctx* ctx, const sc_mlp* m, const char* path) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m || !path) return fail(SC_ERR_INVALID, "mlp or path is NULL");
+  DeviceGuard g(ctx->device);
+  const int n = sc::mlp_param_count();
+  std::vector<float> buf(3 * (size_t)n + 18);
+  float inv[9];
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (!e) e = cudaMemcpy(buf.data(), sc::mlp_params_ptr(m->st), n * 4, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(buf.data() + n, sc::mlp_m_ptr(m->st), n * 4, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(buf.data() + 2 * n, sc::mlp_v_ptr(m->st), n * 4, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(buf.data() + 3 * n, sc::mlp_mu_ptr(m->st), 36, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(inv, sc::mlp_inv_sigma_ptr(m->st), 36, cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(e, "surrogate read-back");
+  for (int i = 0; i < 9; ++i) buf[3 * (size_t)n + 9 + i] = 1.f / inv[i];
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(SC_ERR_INVALID, "cannot open %s for writing", path);
+  const int64_t step = sc::mlp_step(m->st);
+  const int32_t np = n;
+  bool ok = fwrite("SCMLP001", 1, 8, f) == 8 && fwrite(&step, 8, 1, f) == 1 && fwrite(&np, 4, 1, f) == 1 &&
+            fwrite(buf.data(), 4, buf.size(), f) == buf.size() && fwrite(&m->tau, 4, 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(SC_ERR_INVALID, "write to %s failed", path);
+  return SC_OK;
+}
+
+sc_status sc_mlp_load(sc_ctx* ctx, const char* path, sc_mlp** out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!path || !out) return fail(SC_ERR_INVALID, "path or out is NULL");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(SC_ERR_INVALID, "cannot open %s", path);
+  char magic[8];
+  int64_t step = 0;
+  int32_t np = 0;
+  const int n = sc::mlp_param_count();
+  std::vector<float> buf(3 * (size_t)n + 18);
+  float tau = 0.f;
+  bool ok = fread(magic, 1, 8, f) == 8 && !std::memcmp(magic, "SCMLP001", 8) && fread(&step, 8, 1, f) == 1 &&
+            fread(&np, 4, 1, f) == 1 && np == n && fread(buf.data(), 4, buf.size(), f) == buf.size() &&
+            fread(&tau, 4, 1, f) == 1;
+  fclose(f);
+  if (!ok) return fail(SC_ERR_INVALID, "%s is not a surrogate file of this version", path);
+  sc_mlp* m = nullptr;
+  if (sc_status s = sc_mlp_create(ctx, 0, &m)) return s;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (!e) e = cudaMemcpy(sc::mlp_m_ptr(m->st), buf.data() + n, n * 4, cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(sc::mlp_v_ptr(m->st), buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice);
+  if (e) { sc_mlp_destroy(m); return cuda_fail(e, "surrogate upload"); }
+  if (sc_status s = sc_mlp_set(ctx, m, buf.data(), buf.data() + 3 * n, buf.data() + 3 * n + 9, tau)) {
+    sc_mlp_destroy(m);
+    return s;
+  }
+  sc::mlp_set_step(m->st, step);
+  *out = m;
   return SC_OK;
 }
 

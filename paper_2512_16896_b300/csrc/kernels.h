@@ -61,6 +61,30 @@ cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* tar
 cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets, const float* q_in, int n,
                            float* q_out, float* tool, int num_sms, cudaStream_t s);
 
+// ---- surrogate MLP (mlp.cu)
+struct MlpState;
+int mlp_param_count();
+cudaError_t mlp_alloc(MlpState** out);
+void mlp_free(MlpState* S);
+cudaError_t mlp_init(MlpState* S, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_refresh_copies(MlpState* S, cudaStream_t s);
+cudaError_t mlp_set_norm_from(MlpState* S, const float* targets, int n, cudaStream_t s);
+cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* index, int n, float* logits,
+                      int num_sms, cudaStream_t s);
+cudaError_t mlp_reserve(MlpState* S, int Bcap);
+cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
+                          float* loss_dev, int num_sms, cudaStream_t s);
+cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t mlp_epoch_index(int n, uint64_t seed, int epoch, int32_t* index, cudaStream_t s);
+float* mlp_params_ptr(MlpState* S);
+float* mlp_grads_ptr(MlpState* S);
+float* mlp_mu_ptr(MlpState* S);
+float* mlp_inv_sigma_ptr(MlpState* S);
+float* mlp_m_ptr(MlpState* S);
+float* mlp_v_ptr(MlpState* S);
+int64_t mlp_step(const MlpState* S);
+void mlp_set_step(MlpState* S, int64_t t);
+
 // NULL if the launch shape is valid, else why not.
 const char* check_collide_config(const sc_collide_config& cfg);
 
