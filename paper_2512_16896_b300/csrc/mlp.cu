@@ -541,9 +541,20 @@ cudaError_t mlp_set_norm_from(MlpState* S, const float* targets, int n, cudaStre
   return cudaGetLastError();
 }
 
+// Kernels that take more than 48 KB of dynamic shared memory opt in once.
+static cudaError_t smem_opt_in() {
+  cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       4 * kWarpSmem);
+  if (!e) e = cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWarpSmem);
+  if (!e)
+    e = cudaFuncSetAttribute(mlp_backward_act_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWarpSmemBwd);
+  return e;
+}
+
 cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* index, int n, float* logits,
                       int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (cudaError_t e = smem_opt_in()) return e;
   const int warps = 4, rows_per_block = warps * 16;
   int blocks = (n + rows_per_block - 1) / rows_per_block;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
@@ -603,6 +614,7 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
                           float* loss_dev, int num_sms, cudaStream_t s) {
   const int Bpad = (B + 15) & ~15;
   if (Bpad > S->Bcap) return cudaErrorInvalidValue;
+  if (cudaError_t e = smem_opt_in()) return e;
   TrainViews v = carve(S, S->Bcap);
   v.tc.B = S->Bcap;
   cudaError_t e;
