@@ -208,49 +208,6 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
  * that the kernel proved unable to change the result are not counted. */
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs);
 
-/* ----------------------------------------------------------- generation */
-
-typedef struct {
-  uint64_t seed;        /* Philox key of the pose draws */
-  int32_t max_attempts; /* proposals per object per try, 1..1024 (as sc_sample_params) */
-  int32_t max_retries;  /* retries per object after its first try, 0..1000 (the paper uses 10) */
-  int32_t use_graph;    /* 1: capture the launch sequence into a CUDA graph once (per batch, order,
-                           output pointers, retries and launch shape) and replay it; 0: launch eagerly */
-} sc_gen_params;
-
-/* Generate scenes: the paper's placement loop (Sec. IV-A, Fig. 2) over the
- * listed candidates. Objects are placed in template order. For object k each
- * candidate still alive tries r = 0..max_retries: sample object k's pose with
- * try index r (exactly sc_sample_poses for that object), then check object k
- * against objects 0..k-1 and the world boxes (the decision of sc_collide with
- * first_new_obj = k; only the scenes that retry are re-checked, Sec. IV-D).
- * The first try whose proposal is accepted and collision-free fixes the
- * pose; a candidate that exhausts its tries is invalid (Sec. V-A) and its
- * later objects are not placed.
- * order   int32 [n_order] candidates to generate (NULL: all n_cand; then
- *         n_order is ignored); the heaviest first balances the first steps.
- * config  launch shape of the per-step kernel (NULL: default; decide_only is
- *         implied).
- * Outputs, indexed by candidate (only listed candidates are written):
- * poses   float [P][4] CSR pose layout; objects never placed are NaN.
- * valid   u8 [n_cand]: 1 when every object was placed.
- * band    u8 [n_cand]: 1 when any decision on the candidate's path (a support
- *         test of an attempt that fixed an outcome, or a minimum distance)
- *         lay within 1e-5 m of its threshold.
- * tries   int32 [n_cand]: tries spent over all objects.
- * The first call (or one with more candidates than before) allocates the
- * context's generation scratch (4 int32 lists of the candidates plus
- * counters); later calls reuse it. Enqueues 1 + max_obj * (max_retries + 1)
- * kernels (as one graph launch when use_graph = 1; the seed is read from
- * device memory, so a replay with a new seed is not re-captured); launches
- * whose list is empty exit at once. A call with use_graph = 1 must not itself
- * be issued inside another stream capture.
- * Errors: SC_ERR_INVALID (NULL outputs, max_attempts / max_retries out of
- * range, bad config, batch limits), SC_ERR_OOM, SC_ERR_CUDA. */
-sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
-                      int32_t n_order, const sc_collide_config* config, float* poses, uint8_t* valid, uint8_t* band,
-                      int32_t* tries);
-
 /* --------------------------------------------------------- reachability */
 
 /* 7-DoF serial arm in standard Denavit-Hartenberg form:
@@ -353,6 +310,69 @@ sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* mlp, const float* tar
  * threshold in one little-endian file ("SCMLP001" header). */
 sc_status sc_mlp_save(sc_ctx* ctx, const sc_mlp* mlp, const char* path);
 sc_status sc_mlp_load(sc_ctx* ctx, const char* path, sc_mlp** out);
+
+/* ----------------------------------------------------------- generation */
+
+typedef struct {
+  uint64_t seed;        /* Philox key of the pose draws */
+  int32_t max_attempts; /* proposals per object per try, 1..1024 (as sc_sample_params) */
+  int32_t max_retries;  /* retries per object after its first try, 0..1000 (the paper uses 10) */
+  int32_t use_graph;    /* 1: capture the launch sequence into a CUDA graph once (per batch, order,
+                           output pointers, retries and launch shape) and replay it; 0: launch eagerly */
+} sc_gen_params;
+
+/* Optional reachability stage of sc_generate (Sec. IV-E: a sampled pose the
+ * robot cannot reach is rejected). Objects with the SC_REL_REACH flag are,
+ * after a collision-free try, checked for a top-down grasp: position = top
+ * centre of the object's box, tool z = -world z, tool x along the object's
+ * yaw, expressed in the template's robot base frame (tmpl_base). With a gate,
+ * the surrogate's logit must reach the gate's threshold (sc_mlp_set /
+ * sc_surrogate_tune_threshold) first; a rejected try retries like a
+ * collision. Exact IK (sc_ik_reach semantics, seeds keyed by (candidate,
+ * seed, block, object << 16 | try)) then decides; an unreachable grasp
+ * retries too. Every emitted scene is thus verified by exact collision and
+ * exact IK decisions; the gate only skips IK on tries it predicts to fail. */
+typedef struct {
+  const sc_arm* arm;       /* NULL: no reachability stage */
+  const sc_ik_params* ik;  /* exact IK settings */
+  const sc_mlp* gate;      /* NULL: exact IK on every collision-free try */
+} sc_gen_reach;
+
+/* Generate scenes: the paper's placement loop (Sec. IV-A, Fig. 2) over the
+ * listed candidates. Objects are placed in template order. For object k each
+ * candidate still alive tries r = 0..max_retries: sample object k's pose with
+ * try index r (exactly sc_sample_poses for that object), then check object k
+ * against objects 0..k-1 and the world boxes (the decision of sc_collide with
+ * first_new_obj = k; only the scenes that retry are re-checked, Sec. IV-D).
+ * The first try whose proposal is accepted and collision-free fixes the
+ * pose; a candidate that exhausts its tries is invalid (Sec. V-A) and its
+ * later objects are not placed.
+ * order   int32 [n_order] candidates to generate (NULL: all n_cand; then
+ *         n_order is ignored); the heaviest first balances the first steps.
+ * config  launch shape of the per-step kernel (NULL: default; decide_only is
+ *         implied).
+ * Outputs, indexed by candidate (only listed candidates are written):
+ * poses   float [P][4] CSR pose layout; objects never placed are NaN.
+ * valid   u8 [n_cand]: 1 when every object was placed.
+ * band    u8 [n_cand]: 1 when any decision on the candidate's path (a support
+ *         test of an attempt that fixed an outcome, or a minimum distance)
+ *         lay within 1e-5 m of its threshold.
+ * tries   int32 [n_cand]: tries spent over all objects.
+ * reach   optional reachability stage (NULL: none).
+ * q_reach float [P][7] (may be NULL): for every reach-checked object that was
+ *         placed, the IK solution that verified it (pose-slot layout).
+ * The first call (or one with more candidates than before) allocates the
+ * context's generation scratch (4 int32 lists of the candidates plus
+ * counters); later calls reuse it. Enqueues 1 + max_obj * (max_retries + 1)
+ * kernels (as one graph launch when use_graph = 1; the seed is read from
+ * device memory, so a replay with a new seed is not re-captured); launches
+ * whose list is empty exit at once. A call with use_graph = 1 must not itself
+ * be issued inside another stream capture.
+ * Errors: SC_ERR_INVALID (NULL outputs, max_attempts / max_retries out of
+ * range, bad config, batch limits), SC_ERR_OOM, SC_ERR_CUDA. */
+sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
+                      int32_t n_order, const sc_collide_config* config, const sc_gen_reach* reach, float* poses,
+                      uint8_t* valid, uint8_t* band, int32_t* tries, float* q_reach);
 
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],

@@ -448,7 +448,8 @@ extern "C" {
 //   Success (checked before every step and after the last one):
 //     |p* - p| <= tol_pos and angle(R^T R*) <= tol_rot.
 //   Seeds: q0_j = qmin_j + (qmax_j - qmin_j) u_j, u from Philox4x32-10 with
-//   key = IK seed, counter = (target, seed index, j / 4, 0), word j % 4.
+//   key = IK seed, counter = (target, seed index, j / 4, hi), word j % 4;
+//   hi = 0 for a plain target list, object << 16 | try inside generation.
 //   All seeds of a target iterate in lock step; the target is reachable at the
 //   first check where any seed succeeds and returns the lowest such seed index;
 //   otherwise it returns the seed with the smallest position error at the end.
@@ -596,10 +597,11 @@ void or_dls_step(const or_arm* arm, double lambda, const double* Rt, const doubl
   }
 }
 
-void or_ik_seed(const or_arm* arm, uint64_t seed, uint32_t target, uint32_t s, double* q) {
+static void ik_seed_words(const or_arm* arm, uint64_t seed, uint32_t target, uint32_t target_hi, uint32_t s,
+                          double* q) {
   for (int b = 0; b < 2; ++b) {
     double u[4];
-    draw4(seed, target, s, (uint32_t)b, 0u, u);
+    draw4(seed, target, s, (uint32_t)b, target_hi, u);
     for (int w = 0; w < 4; ++w) {
       int j = 4 * b + w;
       if (j < 7) q[j] = (double)arm->qmin[j] + ((double)arm->qmax[j] - (double)arm->qmin[j]) * u[w];
@@ -607,17 +609,21 @@ void or_ik_seed(const or_arm* arm, uint64_t seed, uint32_t target, uint32_t s, d
   }
 }
 
+void or_ik_seed(const or_arm* arm, uint64_t seed, uint32_t target, uint32_t s, double* q) {
+  ik_seed_words(arm, seed, target, 0u, s, q);
+}
+
 // IK for one target (12 floats: R row-major, p). Returns reachable; q_out[7],
 // err[2] = (position error, rotation angle) of the returned configuration,
 // *iter_out = the check index at which it ended.
-static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target, uint32_t tid,
+static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target, uint32_t tid, uint32_t tid_hi,
                   double* q_out, double* err, int* iter_out) {
   double Rt[9], pt[3];
   for (int i = 0; i < 9; ++i) Rt[i] = target[i];
   for (int i = 0; i < 3; ++i) pt[i] = target[9 + i];
   int S = P->seeds;
   std::vector<double> q(7 * S);
-  for (int s = 0; s < S; ++s) or_ik_seed(arm, P->seed, tid, (uint32_t)s, &q[7 * s]);
+  for (int s = 0; s < S; ++s) ik_seed_words(arm, P->seed, tid, tid_hi, (uint32_t)s, &q[7 * s]);
   std::vector<double> pe(S), re(S);
   for (int it = 0; it <= P->iters; ++it) {
     int hit = -1;
@@ -650,7 +656,8 @@ int or_ik_reach(const or_arm* arm, const or_ik_params* P, const float* targets, 
                 uint8_t* reach, double* q_out, double* err, int32_t* iters, int nthreads) {
   parallel_for(n, nthreads, [&](int i) {
     int it;
-    reach[i] = (uint8_t)ik_one(arm, P, targets + 12 * i, target_ids ? target_ids[i] : (uint32_t)i, q_out + 7 * i, err + 2 * i, &it);
+    reach[i] = (uint8_t)ik_one(arm, P, targets + 12 * i, target_ids ? target_ids[i] : (uint32_t)i, 0u, q_out + 7 * i,
+                               err + 2 * i, &it);
     if (iters) iters[i] = it;
   });
   return 0;
@@ -719,9 +726,8 @@ int or_generate(const or_scene* s, const or_gen_params* G, const or_arm* arm, co
           for (int q = 0; q < 12; ++q) tf[q] = (float)tgt[q];
           double qo[7], e2[2];
           int it;
-          // IK counter: one target id per (candidate, object, try)
-          uint32_t tid = (uint32_t)(((uint32_t)c * 64u + (uint32_t)k) * 16u + (uint32_t)r);
-          if (!ik_one(arm, ikp, tf, tid, qo, e2, &it)) continue;
+          // IK seeds of this try: counter (candidate, seed, block, object << 16 | try)
+          if (!ik_one(arm, ikp, tf, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, qo, e2, &it)) continue;
         }
         placed = true;
       }

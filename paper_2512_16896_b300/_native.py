@@ -41,6 +41,10 @@ class ScSampleParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("retry", I32), ("first_obj", I32), ("n_obj", I32)]
 
 
+class ScGenReach(ctypes.Structure):
+    _fields_ = [("arm", P), ("ik", P), ("gate", P)]
+
+
 class ScGenParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("max_retries", I32), ("use_graph", I32)]
 
@@ -96,7 +100,7 @@ SIGNATURES = {
     "sc_collide_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
     "sc_generate": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScGenParams), P, I32,
-                                   ctypes.POINTER(CollideConfig), P, P, P, P]),
+                                   ctypes.POINTER(CollideConfig), ctypes.POINTER(ScGenReach), P, P, P, P, P]),
     "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P]),
     "sc_ik_dls_step": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.c_float, P, P, I32, P, P]),
     "sc_mlp_param_count": (I32, []),
@@ -277,8 +281,10 @@ def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Te
 
 def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, max_retries: int = 10,
              order: torch.Tensor | None = None, config=None, poses: torch.Tensor | None = None, out=None,
-             use_graph: bool = True):
-    """sc_generate. Returns (poses [P,4] f32, valid [n_cand] u8, band [n_cand] u8, tries [n_cand] i32)."""
+             use_graph: bool = True, arm=None, ik=None, gate=None, q_reach: torch.Tensor | None = None):
+    """sc_generate. Returns (poses [P,4] f32, valid [n_cand] u8, band [n_cand] u8, tries [n_cand] i32).
+    With `arm` (and `ik`), designated objects must also be reachable; `gate` (a
+    Surrogate) filters tries before IK; q_reach [P,7] receives the IK solutions."""
     dev = torch.device("cuda", ctx.device)
     poses = db.new_poses(dev) if poses is None else poses
     if out is None:
@@ -292,9 +298,14 @@ def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, m
         cfg = config if isinstance(config, CollideConfig) else CollideConfig(*config)
     p = ScGenParams(seed, max_attempts, max_retries, int(use_graph))
     n = 0 if order is None else int(order.numel())
+    reach = None
+    if arm is not None:
+        ik = ik if ik is not None else ik_params()
+        reach = ScGenReach(ctypes.cast(ctypes.pointer(arm), P), ctypes.cast(ctypes.pointer(ik), P),
+                           None if gate is None else gate.handle)
     _check(lib().sc_generate(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(order), n,
-                             None if cfg is None else ctypes.byref(cfg), _ptr(poses), _ptr(valid), _ptr(band),
-                             _ptr(tries)))
+                             None if cfg is None else ctypes.byref(cfg), None if reach is None else ctypes.byref(reach),
+                             _ptr(poses), _ptr(valid), _ptr(band), _ptr(tries), _ptr(q_reach)))
     return poses, valid, band, tries
 
 

@@ -31,6 +31,18 @@ struct sc_ctx {
   unsigned char gen_key[512] = {};
   size_t gen_key_len = 0;
   unsigned long long seed_host = 0;
+  // cached reach extent of the last batch seen with a reachability stage
+  const void* reach_key[3] = {nullptr, nullptr, nullptr};
+  int reach_extent = -1;
+};
+
+struct sc_mlp {
+  int device = 0;
+  sc::MlpState* st = nullptr;
+  float tau = 0.f;
+  int32_t* index = nullptr;  // epoch permutation scratch
+  int index_cap = 0;
+  float* loss_dev = nullptr;
 };
 
 namespace {
@@ -240,8 +252,8 @@ sc_status sc_collide(sc_ctx* ctx, const sc_scene_batch* batch, const float* pose
 }
 
 sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
-                      int32_t n_order, const sc_collide_config* config, float* poses, uint8_t* valid, uint8_t* band,
-                      int32_t* tries) {
+                      int32_t n_order, const sc_collide_config* config, const sc_gen_reach* reach, float* poses,
+                      uint8_t* valid, uint8_t* band, int32_t* tries, float* q_reach) {
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;
   if (sc_status s = check_batch(batch)) return s;
@@ -255,6 +267,17 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   if (n == 0) return SC_OK;
   if (!poses || !valid || !band || !tries) return fail(SC_ERR_INVALID, "an output pointer is NULL");
   if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
+  const bool want_reach = reach && reach->arm;
+  if (want_reach) {
+    if (!reach->ik) return fail(SC_ERR_INVALID, "reach->ik is NULL");
+    if (!batch->tmpl_base) return fail(SC_ERR_INVALID, "a reachability stage needs batch->tmpl_base");
+    const sc_ik_params& P = *reach->ik;
+    if (P.seeds < 1 || P.seeds > 32 || P.iters < 0 || !(P.tol_pos > 0.f) || !(P.tol_rot > 0.f) ||
+        !(P.tol_rot < 1.5707963f) || !(P.lambda >= 0.f))
+      return fail(SC_ERR_INVALID, "bad IK parameters (seeds 1..32, iters >= 0, tolerances > 0, tol_rot < pi/2)");
+    if (params->max_retries > 65535) return fail(SC_ERR_INVALID, "max_retries > 65535 with a reachability stage");
+    if (batch->max_obj > 65535) return fail(SC_ERR_INVALID, "max_obj > 65535 with a reachability stage");
+  }
   sc_collide_config cfg = kDefaultCollide;
   if (config) {
     if (config->threads) cfg.threads = config->threads;
@@ -290,6 +313,24 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.scratch = ctx->gen_scratch;
   a.stats = ctx->d_stats;
   a.status = ctx->d_status;
+  a.arm = want_reach ? reach->arm : nullptr;
+  a.ik = want_reach ? reach->ik : nullptr;
+  a.gate = (want_reach && reach->gate) ? reach->gate->st : nullptr;
+  a.tau = (want_reach && reach->gate) ? reach->gate->tau : 0.f;
+  a.q_reach = want_reach ? q_reach : nullptr;
+  a.reach_objects = 0;
+  if (want_reach) {
+    const void* key[3] = {batch->tmpl_obj_off, batch->obj_rel,
+                          reinterpret_cast<const void*>((intptr_t)batch->n_templates)};
+    if (ctx->reach_extent < 0 || std::memcmp(key, ctx->reach_key, sizeof(key))) {
+      int ext = 0;
+      cudaError_t e = sc::reach_extent(*batch, ctx->d_status + 2, &ext, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "reach extent scan");
+      std::memcpy(ctx->reach_key, key, sizeof(key));
+      ctx->reach_extent = ext;
+    }
+    a.reach_objects = ctx->reach_extent;
+  }
   ctx->seed_host = params->seed;
   cudaError_t e = cudaMemcpyAsync(seed_dev, &ctx->seed_host, 8, cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "seed upload");
@@ -311,6 +352,12 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     uint8_t* band;
     int32_t* tries;
     void* scratch;
+    sc_arm arm;
+    sc_ik_params ik;
+    const void* gate;
+    float tau;
+    float* q_reach;
+    int reach_objects;
   } key;
   static_assert(sizeof(Key) <= sizeof(ctx->gen_key), "graph key too large");
   std::memset(&key, 0, sizeof(key));
@@ -325,6 +372,14 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   key.band = band;
   key.tries = tries;
   key.scratch = ctx->gen_scratch;
+  if (want_reach) {
+    key.arm = *reach->arm;
+    key.ik = *reach->ik;
+  }
+  key.gate = a.gate;
+  key.tau = a.tau;
+  key.q_reach = a.q_reach;
+  key.reach_objects = a.reach_objects;
   const bool hit = ctx->gen_exec && ctx->gen_key_len == sizeof(key) && !std::memcmp(ctx->gen_key, &key, sizeof(key));
   if (!hit) {
     if (ctx->gen_exec) { cudaGraphExecDestroy(ctx->gen_exec); ctx->gen_exec = nullptr; }
@@ -388,14 +443,6 @@ sc_status sc_ik_dls_step(sc_ctx* ctx, const sc_arm* arm, float lambda, const flo
 
 // ------------------------------------------------------------- surrogate
 
-struct sc_mlp {
-  int device = 0;
-  sc::MlpState* st = nullptr;
-  float tau = 0.f;
-  int32_t* index = nullptr;  // epoch permutation scratch
-  int index_cap = 0;
-  float* loss_dev = nullptr;
-};
 
 int32_t sc_mlp_param_count(void) { return sc::mlp_param_count(); }
 

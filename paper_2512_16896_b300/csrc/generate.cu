@@ -12,9 +12,11 @@
 // the first certain collision). Lane 0 then appends the candidate to the list
 // for object k+1 (or marks it valid after its last object), to the retry list
 // for try r+1, or leaves it invalid after the last try.
+#include <cstring>
 #include <vector>
 
 #include "collide_core.cuh"
+#include "ik_core.cuh"
 #include "kernels.h"
 #include "sample_core.cuh"
 
@@ -34,6 +36,8 @@ struct GenStepArgs {
   int* n_retry;
   int32_t* list_next;
   int* n_next;
+  int32_t* list_reach;  // collision-free tries of reach-flagged objects (NULL: no reach stage)
+  int* n_reach;
   float4* poses;
   uint8_t* valid;
   uint8_t* band;
@@ -281,7 +285,8 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
       if (bnd) g.band[c] = 1;
       g.tries[c] += 1;
       if (pass) {
-        if (k + 1 == nt) g.valid[c] = 1;
+        if (g.list_reach && (__ldg(&b.obj_rel[o0 + k]) & SC_REL_REACH)) g.list_reach[atomicAdd(g.n_reach, 1)] = c;
+        else if (k + 1 == nt) g.valid[c] = 1;
         else g.list_next[atomicAdd(g.n_next, 1)] = c;
       } else if (g.retry < g.max_retries) {
         g.list_retry[atomicAdd(g.n_retry, 1)] = c;
@@ -297,6 +302,125 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   if (lane == 0 && g.stats) {
     atomicAdd(&g.stats[0], my_pairs);
     atomicAdd(&g.stats[1], my_box);
+  }
+}
+
+// ---- reachability stage (Sec. IV-E): the collision-free tries of
+// reach-flagged objects, in the reach list, get a top-down grasp target in
+// the robot base frame; an optional learned gate sends the ones it predicts
+// unreachable back to retry; exact IK decides the rest.
+struct ReachArgs {
+  sc_scene_batch b;
+  int k, retry, max_retries, gated;
+  float tol_pos, tol_rot, tau;
+  const int32_t* list_reach;
+  const int* n_reach;
+  float* targets;        // [cap][12]
+  const float* logits;   // [cap]
+  int32_t* list_ik;      // positions in the reach list the gate passed
+  int* n_ik;
+  int32_t* list_retry;
+  int* n_retry;
+  int32_t* list_next;
+  int* n_next;
+  const float4* poses;
+  uint8_t* valid;
+  uint8_t* band;
+  float* q_reach;        // [P][7] or NULL
+  unsigned long long* stats;
+  ikc::IkArgs ik;
+};
+
+// Top-down grasp of object k: position = top centre of its box, tool z =
+// -world z, tool x along the object's yaw; expressed in the template's robot
+// base frame (x, y, z, yaw). R row-major, then p.
+__global__ void reach_targets_kernel(ReachArgs A) {
+  const int n = *(volatile const int*)A.n_reach;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = A.list_reach[i];
+    const int t = template_of(A.b, c);
+    const int o0 = __ldg(&A.b.tmpl_obj_off[t]), nt = __ldg(&A.b.tmpl_obj_off[t + 1]) - o0;
+    const int64_t pbase = __ldg(&A.b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&A.b.cand_tmpl_off[t])) * nt;
+    const float4 p = A.poses[pbase + A.k];
+    const float hz = __ldg(&A.b.obj_half[4 * (o0 + A.k) + 2]);
+    const float4 base = __ldg(reinterpret_cast<const float4*>(A.b.tmpl_base) + t);
+    float sb, cb, sp, cp;
+    sincosf(base.w, &sb, &cb);
+    sincosf(p.w - base.w, &sp, &cp);
+    const float wx = p.x - base.x, wy = p.y - base.y, wz = p.z + hz - base.z;
+    float* o = A.targets + 12 * (size_t)i;
+    o[0] = cp; o[1] = sp; o[2] = 0.f;
+    o[3] = sp; o[4] = -cp; o[5] = 0.f;
+    o[6] = 0.f; o[7] = 0.f; o[8] = -1.f;
+    o[9] = cb * wx + sb * wy;
+    o[10] = -sb * wx + cb * wy;
+    o[11] = wz;
+  }
+}
+
+// Gate: logit >= tau goes on to IK, the rest retries (or ends invalid).
+__global__ void gate_split_kernel(ReachArgs A) {
+  const int n = *(volatile const int*)A.n_reach;
+  unsigned long long rejected = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (A.logits[i] >= A.tau) {
+      A.list_ik[atomicAdd(A.n_ik, 1)] = i;
+    } else {
+      ++rejected;
+      if (A.retry < A.max_retries) A.list_retry[atomicAdd(A.n_retry, 1)] = A.list_reach[i];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rejected += __shfl_xor_sync(0xFFFFFFFFu, rejected, o);
+  if ((threadIdx.x & 31) == 0 && rejected) atomicAdd(&A.stats[3], rejected);
+}
+
+// Exact IK, one warp per entry; seeds keyed by (candidate, object, try).
+__global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const int n = A.gated ? *(volatile const int*)A.n_ik : *(volatile const int*)A.n_reach;
+  unsigned long long solves = 0, seed_iters = 0;
+  for (int j = blockIdx.x * warps + (threadIdx.x >> 5); j < n; j += gridDim.x * warps) {
+    const int i = A.gated ? A.list_ik[j] : j;
+    const int c = A.list_reach[i];
+    const ikc::Target T = ikc::load_target(A.targets + 12 * (size_t)i);
+    float q[7], pe2, sr, cr;
+    const ikc::Solve r = ikc::warp_solve(A.ik, T, (uint32_t)c, ((uint32_t)A.k << 16) | (uint32_t)A.retry, lane, q, pe2,
+                                         sr, cr);
+    ++solves;
+    seed_iters += (unsigned long long)(r.it + 1) * (unsigned long long)A.ik.seeds;
+    if (lane == r.winner) {
+      const int t = template_of(A.b, c);
+      const int o0 = __ldg(&A.b.tmpl_obj_off[t]), nt = __ldg(&A.b.tmpl_obj_off[t + 1]) - o0;
+      const int64_t pbase = __ldg(&A.b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&A.b.cand_tmpl_off[t])) * nt;
+      const float pe = sqrtf(pe2), ang = atan2f(sr, cr);
+      if (fabsf(pe - A.tol_pos) <= kBand || fabsf(ang - A.tol_rot) <= kBand) A.band[c] = 1;
+      if (r.found) {
+        if (A.q_reach) {
+#pragma unroll
+          for (int jq = 0; jq < 7; ++jq) A.q_reach[7 * (pbase + A.k) + jq] = q[jq];
+        }
+        if (A.k + 1 == nt) A.valid[c] = 1;
+        else A.list_next[atomicAdd(A.n_next, 1)] = c;
+      } else if (A.retry < A.max_retries) {
+        A.list_retry[atomicAdd(A.n_retry, 1)] = c;
+      }
+    }
+  }
+  if (lane == 0 && solves) {
+    atomicAdd(&A.stats[2], solves);
+    atomicAdd(&A.stats[4], seed_iters);
+  }
+}
+
+// 1 + the largest template-local index of an object carrying the reach flag.
+__global__ void reach_extent_kernel(sc_scene_batch b, int* out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_templates; t += gridDim.x * blockDim.x) {
+    const int o0 = b.tmpl_obj_off[t], o1 = b.tmpl_obj_off[t + 1];
+    int ext = 0;
+    for (int o = o0; o < o1; ++o)
+      if (b.obj_rel[o] & SC_REL_REACH) ext = o - o0 + 1;
+    if (ext) atomicMax(out, ext);
   }
 }
 
@@ -324,7 +448,7 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += stride) counts[i] = (i == 0) ? n : 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counters; i += stride) counters[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x < 2 && stats) stats[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 5 && stats) stats[threadIdx.x] = 0;
 }
 
 template <int APL>
@@ -347,10 +471,24 @@ void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaS
 
 }  // namespace
 
+cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_host, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(scratch_int, 0, sizeof(int), s);
+  if (e) return e;
+  reach_extent_kernel<<<64, 256, 0, s>>>(b, scratch_int);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaMemcpyAsync(out_host, scratch_int, sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
+  return cudaStreamSynchronize(s);
+}
+
+// Scratch: 6 int32 lists of n (next x2, retry x2, reach, gate-passed), the
+// grasp targets (12 floats) and logits of the reach list, counts
+// [K+1] + 3 x [K][R+1], work counters [K][R+1], then the seed scalar.
 size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries) {
-  const size_t lists = 4 * (size_t)n_cand * sizeof(int32_t);
-  const size_t counts = (size_t)(max_obj + 1) + (size_t)max_obj * (max_retries + 1);
-  return lists + 2 * counts * sizeof(int) + 256;  // + 256: the seed scalar and alignment
+  const size_t n = (size_t)n_cand;
+  const size_t lists = 6 * n * sizeof(int32_t) + 13 * n * sizeof(float);
+  const size_t counts = (size_t)(max_obj + 1) + 3 * (size_t)max_obj * (max_retries + 1);
+  const size_t counters = (size_t)max_obj * (max_retries + 1);
+  return lists + (counts + counters) * sizeof(int) + 256;  // + 256: the seed scalar and alignment
 }
 
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
@@ -364,13 +502,19 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   const int K = b.max_obj, R = a.max_retries;
   // scratch carve-up: 4 lists of n ints, counts[K+1] (list sizes per object),
   // retry counts[K][R+1], work counters[K][R+1]
-  char* base = static_cast<char*>(a.scratch);
-  int32_t* L[2] = {reinterpret_cast<int32_t*>(base), reinterpret_cast<int32_t*>(base) + n};
-  int32_t* Rl[2] = {reinterpret_cast<int32_t*>(base) + 2 * (size_t)n, reinterpret_cast<int32_t*>(base) + 3 * (size_t)n};
-  int* counts = reinterpret_cast<int*>(base + 4 * (size_t)n * sizeof(int32_t));
-  const int n_counts = (K + 1) + K * (R + 1);
+  int32_t* ib = static_cast<int32_t*>(a.scratch);
+  int32_t* L[2] = {ib, ib + n};
+  int32_t* Rl[2] = {ib + 2 * (size_t)n, ib + 3 * (size_t)n};
+  int32_t* list_reach = ib + 4 * (size_t)n;
+  int32_t* list_ik = ib + 5 * (size_t)n;
+  float* targets = reinterpret_cast<float*>(ib + 6 * (size_t)n);
+  float* logits = targets + 12 * (size_t)n;
+  int* counts = reinterpret_cast<int*>(logits + n);
+  const int n_counts = (K + 1) + 3 * K * (R + 1);
   int* cnt_list = counts;
   int* cnt_retry = counts + (K + 1);
+  int* cnt_reach = cnt_retry + K * (R + 1);
+  int* cnt_ik = cnt_reach + K * (R + 1);
   unsigned int* counters = reinterpret_cast<unsigned int*>(counts + n_counts);
   const int n_counters = K * (R + 1);
   const unsigned long long* seed_dev = a.seed_dev;
@@ -404,10 +548,35 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.tries = a.tries;
   g.stats = a.stats;
   g.status = a.status;
+  ReachArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  const bool reach = a.arm != nullptr;
+  if (reach) {
+    ra.b = b;
+    ra.max_retries = R;
+    ra.gated = a.gate != nullptr;
+    ra.tol_pos = a.ik->tol_pos;
+    ra.tol_rot = a.ik->tol_rot;
+    ra.tau = a.tau;
+    ra.list_reach = list_reach;
+    ra.targets = targets;
+    ra.logits = logits;
+    ra.list_ik = list_ik;
+    ra.poses = reinterpret_cast<const float4*>(a.poses);
+    ra.valid = a.valid;
+    ra.band = a.band;
+    ra.q_reach = a.q_reach;
+    ra.stats = a.stats;
+    ikc::fill_params(ra.ik, *a.arm, *a.ik);
+  }
+  int small_blocks = (n + 255) / 256;
+  small_blocks = small_blocks < num_sms * 4 ? small_blocks : num_sms * 4;
+  if (small_blocks < 1) small_blocks = 1;
   for (int k = 0; k < K; ++k) {
     g.k = k;
     g.list_next = L[(k + 1) & 1];
     g.n_next = cnt_list + k + 1;
+    const bool reach_k = reach && k < a.reach_objects;
     for (int r = 0; r <= R; ++r) {
       g.retry = r;
       g.list_in = r == 0 ? L[k & 1] : Rl[(r - 1) & 1];
@@ -415,11 +584,29 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       g.list_retry = Rl[r & 1];
       g.n_retry = cnt_retry + k * (R + 1) + r;
       g.counter = counters + k * (R + 1) + r;
+      g.list_reach = reach_k ? list_reach : nullptr;
+      g.n_reach = reach_k ? cnt_reach + k * (R + 1) + r : nullptr;
       switch (cfg.a_per_lane) {
         case 1: launch_step<1>(g, grid, cfg.threads, smem, s); break;
         case 2: launch_step<2>(g, grid, cfg.threads, smem, s); break;
         default: launch_step<4>(g, grid, cfg.threads, smem, s); break;
       }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (!reach_k) continue;
+      ra.k = k;
+      ra.retry = r;
+      ra.n_reach = g.n_reach;
+      ra.n_ik = cnt_ik + k * (R + 1) + r;
+      ra.list_retry = g.list_retry;
+      ra.n_retry = g.n_retry;
+      ra.list_next = g.list_next;
+      ra.n_next = g.n_next;
+      reach_targets_kernel<<<small_blocks, 256, 0, s>>>(ra);
+      if (ra.gated) {
+        if ((e = mlp_infer_counted(a.gate, targets, ra.n_reach, n, logits, num_sms, s)) != cudaSuccess) return e;
+        gate_split_kernel<<<small_blocks, 256, 0, s>>>(ra);
+      }
+      reach_ik_kernel<<<num_sms * 8, 128, 0, s>>>(ra);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }

@@ -1,0 +1,251 @@
+// Device core of the batched damped-least-squares IK (Sec. IV-E reachability,
+// solved exactly instead of the paper's RM4D lookup): forward kinematics of
+// a standard-DH 7-DoF arm, the success test, one DLS step, and the warp-level
+// lock-step solve over the seeds of one target. Shared by the IK kernels and
+// the reachability stage of the generation loop.
+#pragma once
+
+#include "common.cuh"
+
+namespace sc {
+namespace ikc {
+
+struct ArmK {
+  float d[7], a[7], ca[7], sa[7], qmin[7], qmax[7];
+};
+
+struct IkArgs {
+  ArmK arm;
+  float lambda2, tol_pos2, cos_tol, sin_tol;
+  int iters, seeds;
+  uint64_t seed;
+  const float* targets;
+  const uint32_t* target_ids;
+  int n;
+  uint8_t* reach;
+  float* q_out;
+  float* err;
+  int32_t* iters_out;
+};
+
+// Forward kinematics; z[i], p[i] = z axis and origin of frame i (i = 0..6,
+// the frame joint i+1 rotates about); R, t = tool frame.
+__device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3], float p[7][3], float R[9],
+                                   float t[3]) {
+  R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
+  R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
+  R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
+  t[0] = t[1] = t[2] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    z[i][0] = R[2]; z[i][1] = R[5]; z[i][2] = R[8];
+    p[i][0] = t[0]; p[i][1] = t[1]; p[i][2] = t[2];
+    float st, ct;
+    sincosf(q[i], &st, &ct);
+    const float ca = A.ca[i], sa = A.sa[i];
+    // rotation part of Rz(q) Rx(alpha): columns c0 = (ct, st, 0), c1 = (-st ca, ct ca, sa), c2 = (st sa, -ct sa, ca)
+    const float c1x = -st * ca, c1y = ct * ca, c2x = st * sa, c2y = -ct * sa;
+    // translation Rz(q) (a, 0, d) = (a ct, a st, d) in the current frame
+    const float lx = A.a[i] * ct, ly = A.a[i] * st, lz = A.d[i];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
+      t[r] += r0 * lx + r1 * ly + r2 * lz;
+      R[3 * r] = r0 * ct + r1 * st;
+      R[3 * r + 1] = r0 * c1x + r1 * c1y + r2 * sa;
+      R[3 * r + 2] = r0 * c2x + r1 * c2y + r2 * ca;
+    }
+  }
+}
+
+struct Target {
+  float R[9], p[3];
+};
+
+// Success test and errors of one configuration.
+__device__ __forceinline__ bool check(const IkArgs& K, const Target& T, const float R[9], const float t[3],
+                                      float* pos_err2, float* s_out, float* c_out) {
+  const float dx = T.p[0] - t[0], dy = T.p[1] - t[1], dz = T.p[2] - t[2];
+  const float pe2 = dx * dx + dy * dy + dz * dz;
+  // M = R^T R*; angle = atan2(|vee(M - M^T)| / 2, (tr M - 1) / 2)
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = R[r] * T.R[c] + R[3 + r] * T.R[3 + c] + R[6 + r] * T.R[6 + c];
+  const float vx = 0.5f * (M[7] - M[5]), vy = 0.5f * (M[2] - M[6]), vz = 0.5f * (M[3] - M[1]);
+  const float s = sqrtf(vx * vx + vy * vy + vz * vz);
+  const float c = 0.5f * (M[0] + M[4] + M[8] - 1.f);
+  *pos_err2 = pe2;
+  *s_out = s;
+  *c_out = c;
+  // angle <= tol  <=>  s cos(tol) <= c sin(tol)   (angle in [0, pi], tol in (0, pi/2))
+  return pe2 <= K.tol_pos2 && s * K.cos_tol <= c * K.sin_tol;
+}
+
+// One damped-least-squares step of q (in place) towards T, given the forward
+// kinematics (z, p, R, t) of q.
+__device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Target& T, float q[7],
+                                         const float z[7][3], const float p[7][3], const float R[9], const float t[3]) {
+  float e[6];
+  e[0] = T.p[0] - t[0];
+  e[1] = T.p[1] - t[1];
+  e[2] = T.p[2] - t[2];
+  e[3] = e[4] = e[5] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // 1/2 sum_k r_k x r*_k (columns)
+    const float rx = R[k], ry = R[3 + k], rz = R[6 + k];
+    const float sx = T.R[k], sy = T.R[3 + k], sz = T.R[6 + k];
+    e[3] += 0.5f * (ry * sz - rz * sy);
+    e[4] += 0.5f * (rz * sx - rx * sz);
+    e[5] += 0.5f * (rx * sy - ry * sx);
+  }
+  float J[6][7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float ux = t[0] - p[i][0], uy = t[1] - p[i][1], uz = t[2] - p[i][2];
+    J[0][i] = z[i][1] * uz - z[i][2] * uy;
+    J[1][i] = z[i][2] * ux - z[i][0] * uz;
+    J[2][i] = z[i][0] * uy - z[i][1] * ux;
+    J[3][i] = z[i][0];
+    J[4][i] = z[i][1];
+    J[5][i] = z[i][2];
+  }
+  // A = J J^T + lambda^2 I, Cholesky A = L L^T (lower, in place)
+  float L[6][6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      float acc = (r == c) ? lambda2 : 0.f;
+#pragma unroll
+      for (int i = 0; i < 7; ++i) acc = fmaf(J[r][i], J[c][i], acc);
+      L[r][c] = acc;
+    }
+  float inv_diag[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float d = L[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    const float ljj = sqrtf(d);
+    inv_diag[j] = 1.f / ljj;
+    L[j][j] = ljj;
+#pragma unroll
+    for (int r = j + 1; r < 6; ++r) {
+      float v = L[r][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[r][k] * L[j][k];
+      L[r][j] = v * inv_diag[j];
+    }
+  }
+  float y[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {  // L w = e
+    float v = e[r];
+#pragma unroll
+    for (int k = 0; k < r; ++k) v -= L[r][k] * y[k];
+    y[r] = v * inv_diag[r];
+  }
+#pragma unroll
+  for (int r = 5; r >= 0; --r) {  // L^T y = w
+    float v = y[r];
+#pragma unroll
+    for (int k = r + 1; k < 6; ++k) v -= L[k][r] * y[k];
+    y[r] = v * inv_diag[r];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    float dq = 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) dq = fmaf(J[r][i], y[r], dq);
+    q[i] = fminf(fmaxf(q[i] + dq, A.qmin[i]), A.qmax[i]);
+  }
+}
+
+__device__ __forceinline__ Target load_target(const float* tg) {
+  Target T;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) T.R[i] = __ldg(tg + i);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) T.p[i] = __ldg(tg + 9 + i);
+  return T;
+}
+
+
+struct Solve {
+  bool found;
+  int winner;  // lane holding the returned configuration
+  int it;      // check index at which the solve ended
+};
+
+// Lock-step solve of one target by the whole warp (seed = lane). Returns the
+// winning lane; that lane's q, pe2, s, c hold the returned configuration and
+// its errors. Philox counter of seed lane: (id_lo, lane, block, id_hi).
+__device__ __forceinline__ Solve warp_solve(const IkArgs& K, const Target& T, uint32_t id_lo, uint32_t id_hi, int lane,
+                                            float q[7], float& pe2, float& s, float& c) {
+  const bool active = lane < K.seeds;
+  {
+    const float4 u0 = draw_uniform4(K.seed, id_lo, (uint32_t)lane, 0u, id_hi);
+    const float4 u1 = draw_uniform4(K.seed, id_lo, (uint32_t)lane, 1u, id_hi);
+    const float u[7] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z};
+#pragma unroll
+    for (int j = 0; j < 7; ++j) q[j] = K.arm.qmin[j] + (K.arm.qmax[j] - K.arm.qmin[j]) * u[j];
+  }
+  Solve r{false, -1, 0};
+  pe2 = 0.f;
+  s = 0.f;
+  c = 1.f;
+  for (;; ++r.it) {
+    float z[7][3], p[7][3], R[9], t[3];
+    fk(K.arm, q, z, p, R, t);
+    const bool ok = active && check(K, T, R, t, &pe2, &s, &c);
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+    if (m) {
+      r.winner = __ffs(m) - 1;
+      r.found = true;
+      return r;
+    }
+    if (r.it == K.iters) break;
+    if (active) dls_step(K.arm, K.lambda2, T, q, z, p, R, t);
+  }
+  // smallest position error, lowest index on ties
+  float best = active ? pe2 : 3e38f;
+  int who = lane;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+    const int ow = __shfl_xor_sync(0xFFFFFFFFu, who, o);
+    if (ob < best || (ob == best && ow < who)) { best = ob; who = ow; }
+  }
+  r.winner = who;
+  return r;
+}
+
+// Host: arm constants (cos / sin of the twist angles) and solver parameters.
+inline ArmK make_arm(const sc_arm& a) {
+  ArmK k;
+  for (int i = 0; i < 7; ++i) {
+    k.d[i] = a.dh_d[i];
+    k.a[i] = a.dh_a[i];
+    k.ca[i] = (float)cos((double)a.dh_alpha[i]);
+    k.sa[i] = (float)sin((double)a.dh_alpha[i]);
+    k.qmin[i] = a.qmin[i];
+    k.qmax[i] = a.qmax[i];
+  }
+  return k;
+}
+
+inline void fill_params(IkArgs& K, const sc_arm& arm, const sc_ik_params& P) {
+  K.arm = make_arm(arm);
+  K.lambda2 = P.lambda * P.lambda;
+  K.tol_pos2 = P.tol_pos * P.tol_pos;
+  K.cos_tol = (float)cos((double)P.tol_rot);
+  K.sin_tol = (float)sin((double)P.tol_rot);
+  K.iters = P.iters;
+  K.seeds = P.seeds;
+  K.seed = P.seed;
+}
+
+}  // namespace ikc
+}  // namespace sc

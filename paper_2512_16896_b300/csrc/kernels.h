@@ -36,6 +36,8 @@ cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, cons
 void set_error_message(const std::string& msg);
 sc_status validate_batch(const sc_scene_batch* b);
 
+struct MlpState;
+
 struct GenerateLaunch {
   const int32_t* order;  // candidates to generate (NULL: 0..n_items-1)
   int n_items;
@@ -46,11 +48,21 @@ struct GenerateLaunch {
   uint8_t* band;
   int32_t* tries;
   void* scratch;  // generate_scratch_bytes(n_items, max_obj, max_retries)
-  unsigned long long* stats;
+  unsigned long long* stats;  // [0] sphere pairs [1] sphere-box pairs [2] IK solves [3] gate rejections
+                              // [4] IK seed-iterations
   int* status;
+  // reachability (arm == NULL: none)
+  const sc_arm* arm;
+  const sc_ik_params* ik;
+  const MlpState* gate;  // NULL: exact IK on every candidate
+  float tau;
+  int reach_objects;     // object indices < reach_objects may carry the reach flag
+  float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
 };
 
 size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
+// 1 + largest object index with the reach flag (synchronises the stream).
+cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_host, cudaStream_t s);
 // Enqueues the whole generation (init + one launch per object and try).
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
                              int num_sms, cudaStream_t s, const char** why);
@@ -71,6 +83,8 @@ cudaError_t mlp_refresh_copies(MlpState* S, cudaStream_t s);
 cudaError_t mlp_set_norm_from(MlpState* S, const float* targets, int n, cudaStream_t s);
 cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* index, int n, float* logits,
                       int num_sms, cudaStream_t s);
+cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int* n_dev, int n_cap, float* logits,
+                              int num_sms, cudaStream_t s);
 cudaError_t mlp_reserve(MlpState* S, int Bcap);
 cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
                           float* loss_dev, int num_sms, cudaStream_t s);

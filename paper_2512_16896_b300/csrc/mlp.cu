@@ -198,11 +198,15 @@ __device__ void warp_forward(const MlpDev& M, const float* targets, const int32_
 constexpr int kWarpSmem = 2 * 16 * AST * 2;
 constexpr int kWarpSmemBwd = kWarpSmem + 64;
 
+// n_rows_dev (optional): the row count is read from device memory (lists
+// produced on the device), n_rows is then only an upper bound.
 template <bool TRAIN>
 __global__ void __launch_bounds__(128) mlp_forward_kernel(MlpDev M, const float* targets, const int32_t* index,
-                                                          int n_rows, float* logits, TrainCache tc) {
+                                                          int n_rows, const int* n_rows_dev, float* logits,
+                                                          TrainCache tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  if (n_rows_dev) n_rows = min(n_rows, *(volatile const int*)n_rows_dev);
   __nv_bfloat16* act0 = reinterpret_cast<__nv_bfloat16*>(smem + w * kWarpSmem);
   __nv_bfloat16* act1 = act0 + 16 * AST;
   for (int row0 = (blockIdx.x * warps + w) * 16; row0 < n_rows; row0 += gridDim.x * warps * 16)
@@ -559,7 +563,21 @@ cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* in
   int blocks = (n + rows_per_block - 1) / rows_per_block;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
   TrainCache tc{};
-  mlp_forward_kernel<false><<<blocks, warps * 32, warps * kWarpSmem, s>>>(dev_view(*S), targets, index, n, logits, tc);
+  mlp_forward_kernel<false><<<blocks, warps * 32, warps * kWarpSmem, s>>>(dev_view(*S), targets, index, n, nullptr,
+                                                                           logits, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int* n_dev, int n_cap, float* logits,
+                              int num_sms, cudaStream_t s) {
+  if (n_cap <= 0) return cudaSuccess;
+  if (cudaError_t e = smem_opt_in()) return e;
+  const int warps = 4, rows_per_block = warps * 16;
+  int blocks = (n_cap + rows_per_block - 1) / rows_per_block;
+  if (blocks > num_sms * 8) blocks = num_sms * 8;
+  TrainCache tc{};
+  mlp_forward_kernel<false><<<blocks, warps * 32, warps * kWarpSmem, s>>>(dev_view(*S), targets, nullptr, n_cap, n_dev,
+                                                                           logits, tc);
   return cudaGetLastError();
 }
 
@@ -626,7 +644,8 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
   int blocks = (B + rows_per_block - 1) / rows_per_block;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
   const MlpDev M = dev_view(*S);
-  mlp_forward_kernel<true><<<blocks, warps * 32, warps * kWarpSmem, s>>>(M, targets, index, B, v.logits, v.tc);
+  mlp_forward_kernel<true><<<blocks, warps * 32, warps * kWarpSmem, s>>>(M, targets, index, B, nullptr, v.logits,
+                                                                          v.tc);
   mlp_backward_act_kernel<<<blocks, warps * 32, warps * kWarpSmemBwd, s>>>(M, v.logits, labels, index, B, 1.f / B,
                                                                             v.tc, v.bo);
   const int ld = S->Bcap;
