@@ -300,9 +300,9 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   sc::GenerateLaunch a;
   a.order = order;
   a.n_items = n;
-  // the seed lives in device scratch (last 8 bytes), written before each run
-  unsigned long long* seed_dev =
-      reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->gen_scratch) + need - 8);
+  // the seed lives in device scratch (an aligned slot after the lists), written before each run
+  unsigned long long* seed_dev = reinterpret_cast<unsigned long long*>(
+      static_cast<char*>(ctx->gen_scratch) + sc::generate_seed_offset(n, batch->max_obj, params->max_retries));
   a.seed_dev = seed_dev;
   a.max_attempts = params->max_attempts;
   a.max_retries = params->max_retries;

@@ -483,12 +483,17 @@ cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_hos
 // Scratch: 6 int32 lists of n (next x2, retry x2, reach, gate-passed), the
 // grasp targets (12 floats) and logits of the reach list, counts
 // [K+1] + 3 x [K][R+1], work counters [K][R+1], then the seed scalar.
-size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries) {
+size_t generate_seed_offset(int n_cand, int max_obj, int max_retries) {
   const size_t n = (size_t)n_cand;
   const size_t lists = 6 * n * sizeof(int32_t) + 13 * n * sizeof(float);
   const size_t counts = (size_t)(max_obj + 1) + 3 * (size_t)max_obj * (max_retries + 1);
   const size_t counters = (size_t)max_obj * (max_retries + 1);
-  return lists + (counts + counters) * sizeof(int) + 256;  // + 256: the seed scalar and alignment
+  const size_t body = lists + (counts + counters) * sizeof(int);
+  return (body + 255) & ~size_t(255);  // the 8-byte seed sits on a 256-byte boundary
+}
+
+size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries) {
+  return generate_seed_offset(n_cand, max_obj, max_retries) + 256;
 }
 
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,

@@ -61,6 +61,8 @@ struct GenerateLaunch {
 };
 
 size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
+// Byte offset of the 8-byte seed scalar inside that scratch (256-aligned).
+size_t generate_seed_offset(int n_cand, int max_obj, int max_retries);
 // 1 + largest object index with the reach flag (synchronises the stream).
 cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_host, cudaStream_t s);
 // Enqueues the whole generation (init + one launch per object and try).
