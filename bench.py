@@ -2,17 +2,23 @@
 """Benchmark of the Sceniris hot path on one B300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload ragged|shelf|tabletop] [--path generate|whole]
+                    [--workload ragged|shelf|tabletop]
 
 One step = one pass of the hot path over one batch of synthetic scene
 candidates already resident in HBM. Default path (`generate`, the paper's
 placement loop of Sec. IV-A with 10 retries per object, Sec. V-A): for every
 object in order, sample its pose (Philox, point-in-polygon, relations), check
 it against the placed objects and the world, retry the failing candidates, mark
-candidates that run out of tries invalid. A scene counts as verified
-collision-free when every object was placed by exact decisions. `--path whole`
-times the plain whole-scene pass instead (sample every object, then the exact
-minimum distance of every candidate).
+candidates that run out of tries invalid; the first four objects of every
+template must also be reachable by a 7-DoF arm (top-down grasp), decided by
+exact damped-least-squares IK, with a learned gate (trained before timing on
+the project's own IK labels, recall >= 0.99) skipping IK on tries it predicts
+unreachable. A scene counts as verified when every object was placed by exact
+collision and IK decisions. `value` is the gated, graph-replayed path;
+`plain` is the same loop launched eagerly with exact IK on every try.
+`kernels` times each stage's kernel alone on its own workload (exact-minimum
+collision of the shelf batch, IK of 262,144 targets, gate inference and one
+training epoch).
 
 Prints ONE JSON line (rank 0). `value` is verified collision-free scenes per
 second over all ranks; `e2e` is the same metric through the public C-ABI calls
@@ -47,12 +53,13 @@ import synth  # noqa: E402
 # Algorithmic FP32-pipe operations per evaluated pair ("Rooflines"):
 OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 1 FADD + 4 FFMA
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
+OPS_PER_IK_SEED_ITER = 720  # one check + DLS step: FK 280, check 40, error 21, J 63, J J^T 147, Cholesky 50,
+                            # solves 60, J^T y 42, clamp 14 (FP32-pipe operations, sincos counted once)
 L2_BYTES = 126 * 1024 * 1024
 
 PATHS = {
     "generate": "per-object placement loop: sample, decide collisions against placed objects and world, "
-                "retry <= 10 times, invalid after that",
-    "whole": "plain whole-scene: sample all objects, one exact-minimum collision pass",
+                "(designated objects) learned gate then exact IK, retry <= 10 times, invalid after that",
 }
 
 WORKLOADS = {
@@ -150,7 +157,8 @@ def measured_traffic(kernel_file: str, workload: str):
 # --------------------------------------------------------------------------- oracle legs
 
 
-def oracle_rate(batch, seed, budget_s: float, path: str = "generate", rng_seed: int = 0, max_retries: int = 10):
+def oracle_rate(batch, seed, budget_s: float, path: str = "generate", rng_seed: int = 0, max_retries: int = 10,
+                reach: bool = False):
     """Verified collision-free scenes/s of the FP64 oracle on a bounded random
     sample of candidates (sized from a probe so the sample takes ~budget_s)."""
     import oracle
@@ -160,7 +168,10 @@ def oracle_rate(batch, seed, budget_s: float, path: str = "generate", rng_seed: 
 
     def run(pick):
         if path == "generate":
-            _, valid, _, _ = oracle.generate(sc, seed, max_retries=max_retries, active=pick, threads=threads)
+            arm = oracle.make_arm(*synth.arm_arrays()) if reach else None
+            ikp = oracle.ik_params(seed=seed + 3) if reach else None
+            _, valid, _, _ = oracle.generate(sc, seed, max_retries=max_retries, active=pick, threads=threads, arm=arm,
+                                             ikp=ikp)
             return int(valid.sum())
         P, ok, _ = oracle.sample_poses(sc, seed, active=pick, threads=threads)
         col, md, _ = oracle.collide(sc, P, active=pick, threads=threads)
@@ -188,7 +199,7 @@ def run_reference(args, wl):
     times, valids, ns = [], [], []
     for i in range(args.warmup + args.steps):
         r = oracle_rate(batch, seed=wl["seed"], budget_s=args.ref_step_s, path=args.path, rng_seed=100 + i,
-                        max_retries=args.retries)
+                        max_retries=args.retries, reach=args.path == "generate" and not args.no_reach)
         if i >= args.warmup:
             times.append(r["seconds"]); valids.append(r["valid"]); ns.append(r["n"])
     value = sum(valids) / sum(times)
@@ -231,78 +242,73 @@ def run_ours(args, wl):
     n = batch.n_cand
     u8 = lambda: torch.zeros(n, dtype=torch.uint8, device=dev)
     valid, band, tries = u8(), u8(), torch.zeros(n, dtype=torch.int32, device=dev)
-    ok, sband, col, cband = u8(), u8(), u8(), u8()
-    md = torch.empty(n, dtype=torch.float32, device=dev)
+    q_reach = torch.zeros((db.n_poses, 7), dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    gen = args.path == "generate"
+    reach = args.path == "generate" and not args.no_reach
+    arm = sc.make_arm(*synth.arm_arrays())
+    ikp = sc.ik_params(seed=seed + 3)
+    cfg = tuple(int(x) for x in args.collide_config.split(",")) if args.collide_config else None
 
-    # launch shape: explicit, autotuned on a sample of this batch, or the default
-    cfg = None
-    tune_info = "library default"
-    if args.collide_config:
-        cfg = tuple(int(x) for x in args.collide_config.split(","))
-        tune_info = "given"
-    elif not args.no_tune and not gen:
-        from paper_2512_16896_b300 import autotune
-        sc.sample_poses(ctx, db, seed=seed, poses=poses)
-        cfg, entry = autotune.tune_collide(ctx, db, batch, poses, order, verbose=args.tune_verbose)
-        tune_info = f"autotuned ({entry['sample']} sampled candidates, {entry['ms']:.2f} ms)"
+    # ---- surrogate gate (untimed set-up: IK labels, training, threshold)
+    gate = None
+    gate_info = None
+    if reach and not args.no_gate:
+        t0 = time.perf_counter()
+        box = ((-0.2, 2.2), (-1.3, 1.3), (0.0, 0.8))  # base-frame region of the workload's grasp targets
+        tr = torch.from_numpy(synth.topdown_targets(seed=seed + 4, n=args.train_labels, box=box)).to(dev)
+        ho = torch.from_numpy(synth.topdown_targets(seed=seed + 5, n=262144, box=box)).to(dev)
+        ytr, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=seed + 4), tr)
+        yho, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=seed + 5), ho)
+        ctx.synchronize()
+        t1 = time.perf_counter()
+        gate = sc.Surrogate(ctx, seed=seed + 6)
+        loss = gate.train(tr, ytr, sc.train_params(epochs=args.train_epochs, batch=4096, seed=seed + 4))
+        ctx.synchronize()
+        t2 = time.perf_counter()
+        tau, recall, pass_rate = gate.tune_threshold(ho, yho, 0.99)
+        gate_info = {"train_labels": int(tr.shape[0]), "epochs": args.train_epochs, "final_loss": float(loss[-1]),
+                     "tau": tau, "heldout_recall": recall, "heldout_pass_rate": pass_rate,
+                     "heldout_reachable": float(yho.float().mean().item()),
+                     "label_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
+                     "train_samples_per_s": int(args.train_epochs * tr.shape[0] / max(t2 - t1, 1e-9))}
+        del tr, ho, ytr, yho
 
-    def enqueue(step_seed, ev=None):
-        """One step on the device; ev = (start, end) events around the dominant kernel(s)."""
-        if gen:
-            if ev:
-                ev[0].record(stream)
-            sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
-                        out=(valid, band, tries), use_graph=not args.no_graph)
-            if ev:
-                ev[1].record(stream)
-        else:
-            sc.sample_poses(ctx, db, seed=step_seed, poses=poses, out=(ok, sband))
-            if ev:
-                ev[0].record(stream)
-            sc.collide(ctx, db, poses, active=order, out=(col, md, cband), config=cfg)
-            if ev:
-                ev[1].record(stream)
+    def enqueue(step_seed, use_gate=True, use_graph=True):
+        sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
+                    out=(valid, band, tries), use_graph=use_graph and not args.no_graph,
+                    arm=arm if reach else None, ik=ikp, gate=gate if use_gate else None,
+                    q_reach=q_reach if reach else None)
 
-    ok_by_list = torch.empty(n, dtype=torch.uint8, device=dev)
-
-    def count_valid():
-        if gen:
-            return int(valid.sum().item())
-        torch.index_select(ok, 0, order.long(), out=ok_by_list)  # collide outputs are in list order
-        return int(((ok_by_list == 1) & (col == 0)).sum().item())
-
-    for i in range(args.warmup):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        enqueue(seed * 7919 + i)
-    torch.cuda.synchronize()
-    ctx.synchronize()
-    if world > 1:
-        dist.barrier()
-
-    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ev_kern = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    valids, pairs, boxes = [], [], []
-    with ClockSampler(local) as clocks:
-        torch.cuda.synchronize()
-        for i in range(args.steps):
+    def timed(label, use_gate, use_graph, steps, warmup):
+        ctx.set_timing(True)
+        for i in range(warmup):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            enqueue(seed * 7919 + i, use_gate, use_graph)
+        ctx.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        vals, stats = [], []
+        for i in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()  # evict L2 between timed steps (not timed)
-            ev_step[i][0].record(stream)
-            enqueue(seed * 7919 + 1000 + i, ev_kern[i])
-            ev_step[i][1].record(stream)
-            p, bx = sc.collide_last_work(ctx)  # synchronises after the step's end event
-            pairs.append(p)
-            boxes.append(bx)
-            valids.append(count_valid())
+            ev[i][0].record(stream)
+            enqueue(seed * 7919 + 1000 + i, use_gate, use_graph)
+            ev[i][1].record(stream)
+            stats.append(ctx.generate_stats())  # synchronises after the step
+            vals.append(int(valid.sum().item()))
         torch.cuda.synchronize()
-    ctx.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev_step]
-    kern_ms = [a.elapsed_time(b) for a, b in ev_kern]
-    total_s = sum(step_ms) / 1000.0
-    total_valid = sum(valids)
+        ctx.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return {"label": label, "ms": ms, "valid": vals, "stats": stats}
+
+    with ClockSampler(local) as clocks:
+        main = timed("batched+surrogate" if gate is not None else "batched", gate is not None, True, args.steps,
+                     args.warmup)
+    plain = None
+    if reach and not args.no_plain:
+        plain = timed("plain", False, False, args.plain_steps, min(args.warmup, 3))
 
     # ---- end to end through the C ABI with host buffers
     hb = sc.DeviceBatch(batch, pinned_host=True)
@@ -311,6 +317,7 @@ def run_ours(args, wl):
     h_valid = torch.empty(n, dtype=torch.uint8).pin_memory()
     d2h = h_poses.numel() * 4 + n
     e2e_ms, e2e_valid = [], []
+    ctx.set_timing(False)
     for i in range(0 if args.no_e2e else args.warmup + args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -320,14 +327,10 @@ def run_ours(args, wl):
             for k, t in hb.t.items():
                 if k != "tmpl_pose_off":
                     db.t[k].copy_(t, non_blocking=True)
-        enqueue(seed * 7919 + 5000 + i)
+        enqueue(seed * 7919 + 5000 + i, gate is not None, True)
         with torch.cuda.stream(stream):
             h_poses.copy_(poses, non_blocking=True)
-            if gen:
-                h_valid.copy_(valid, non_blocking=True)
-            else:
-                torch.index_select(ok, 0, order.long(), out=ok_by_list)
-                h_valid.copy_((ok_by_list == 1) & (col == 0), non_blocking=True)
+            h_valid.copy_(valid, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
@@ -335,13 +338,15 @@ def run_ours(args, wl):
             e2e_valid.append(int(h_valid.numpy().sum()))
 
     # ---- aggregate over ranks (max time, summed work)
-    stats = torch.tensor([total_s, total_valid, max(sum(e2e_ms), 1e-9) / 1000.0, sum(e2e_valid)], dtype=torch.float64,
-                         device=dev)
+    total_s = sum(main["ms"]) / 1000.0
+    total_valid = sum(main["valid"])
+    stats_t = torch.tensor([total_s, total_valid, max(sum(e2e_ms), 1e-9) / 1000.0, sum(e2e_valid)],
+                           dtype=torch.float64, device=dev)
     if world > 1:
-        mx = stats[[0, 2]].clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = stats[[1, 3]].clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        stats = torch.stack([mx[0], sm[0], mx[1], sm[1]])
-    total_s, total_valid, e2e_s, e2e_valid_sum = [float(x) for x in stats.cpu()]
+        mx = stats_t[[0, 2]].clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = stats_t[[1, 3]].clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        stats_t = torch.stack([mx[0], sm[0], mx[1], sm[1]])
+    total_s, total_valid, e2e_s, e2e_valid_sum = [float(x) for x in stats_t.cpu()]
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -350,14 +355,38 @@ def run_ours(args, wl):
     peaks, peak_src = read_peaks()
     sm_count = ctx.num_sms
     peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6  # FP32 lanes x max SM clock
-    ops = np.array(pairs, np.float64) * OPS_PER_SPHERE_PAIR + np.array(boxes, np.float64) * OPS_PER_SPHERE_BOX
-    achieved = float(np.sum(ops) / (np.sum(kern_ms) / 1000.0))
+
+    def stage_roofline(run):
+        st = run["stats"]
+        ms_gen = sum(s["ms_stage"][0] for s in st)
+        ms_ik = sum(s["ms_stage"][2] for s in st)
+        ops_gen = sum(s["sphere_pairs"] for s in st) * OPS_PER_SPHERE_PAIR + \
+            sum(s["sphere_box_pairs"] for s in st) * OPS_PER_SPHERE_BOX
+        ops_ik = sum(s["ik_seed_iterations"] for s in st) * OPS_PER_IK_SEED_ITER
+        gen = {"kernel": "gen_warp_kernel (sample + collision decision)", "ms_per_step": ms_gen / len(st),
+               "launches_per_step": st[0]["launches_stage"][0],
+               "achieved": ops_gen / max(ms_gen, 1e-9) / 1e9, "frac": ops_gen / max(ms_gen, 1e-9) * 1e3 / peak_ops}
+        ik = {"kernel": "reach_ik_kernel (DLS IK)", "ms_per_step": ms_ik / len(st),
+              "launches_per_step": st[0]["launches_stage"][2],
+              "achieved": ops_ik / max(ms_ik, 1e-9) / 1e9, "frac": ops_ik / max(ms_ik, 1e-9) * 1e3 / peak_ops}
+        return gen, ik
+
+    gen_rf, ik_rf = stage_roofline(main)
+    dom = gen_rf if gen_rf["ms_per_step"] >= ik_rf["ms_per_step"] else ik_rf
+    dom_file = "generate.cu" if dom is gen_rf else "ik_core.cuh"
     clk = clocks.summary()
     cpu = None
     if world == 1 and args.cpu_budget_s > 0:
-        cpu = oracle_rate(batch, seed=seed, budget_s=args.cpu_budget_s, path=args.path, max_retries=args.retries)
-    kname = "gen_step_kernel (+ its sampling)" if gen else "collide_kernel"
-    launches_per_step = (1 + db.c.max_obj * (args.retries + 1)) if gen else 2
+        cpu = oracle_rate(batch, seed=seed, budget_s=args.cpu_budget_s, path=args.path, max_retries=args.retries,
+                          reach=reach)
+    st0 = main["stats"][-1]
+    plain_line = None
+    if plain:
+        p_s = sum(plain["ms"]) / 1000.0
+        p_ik = plain["stats"][-1]
+        plain_line = {"value": sum(plain["valid"]) / p_s, "unit": "scenes/s", "ms_per_step": 1000 * p_s / len(plain["ms"]),
+                      "steps": len(plain["ms"]), "valid_per_step": sum(plain["valid"]) / len(plain["valid"]),
+                      "ik_solves_per_step": p_ik["ik_solves"], "launch": "eager", "gate": None}
     line = {
         "metric": "verified collision-free scenes/sec",
         "value": total_valid / total_s,
@@ -372,30 +401,119 @@ def run_ours(args, wl):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
-                   "launch": ("eager" if args.no_graph else "CUDA graph replay") if gen else "eager",
-                   "collide_launch": {"shape": list(cfg) if cfg else None, "source": tune_info},
+                   "reachability": ("top-down grasp of the first 4 objects of every template, 7-DoF arm at the "
+                                    "support's -x edge, exact DLS IK (32 seeds x 100 iterations)") if reach else None,
+                   "gate": gate_info, "launch": "eager" if args.no_graph else "CUDA graph replay",
                    "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
                    "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s", "frac": achieved / peak_ops,
-                     "traffic": measured_traffic("generate.cu" if gen else "collide.cu", args.workload),
+        "plain": plain_line,
+        "stages": {"gen_ms_per_step": gen_rf["ms_per_step"], "ik_ms_per_step": ik_rf["ms_per_step"],
+                   "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
+                   "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
+                   "sphere_pairs_per_step": st0["sphere_pairs"], "ik_seed_iterations_per_step": st0["ik_seed_iterations"],
+                   "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"]},
+        "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"] / 1e3, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s", "frac": dom["frac"], "traffic": measured_traffic(dom_file, args.workload),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "
                                     f"({peak_src} max clock)",
-                     "ms_per_step_in_kernel": float(np.mean(kern_ms)),
-                     "pairs_per_step": float(np.mean(pairs)), "box_pairs_per_step": float(np.mean(boxes))},
+                     "ms_per_step_in_kernel": dom["ms_per_step"], "launches_per_step": dom["launches_per_step"]},
         "cpu_baseline": None if cpu is None else {
             "value": cpu["valid_per_s"], "unit": "scenes/s", "cores": cpu["threads"], "kind": "oracle",
             "sample": f"{cpu['n']} random candidates of the same workload ({cpu['seconds']:.1f} s)"},
         "e2e": None if args.no_e2e else {"value": e2e_valid_sum / e2e_s, "unit": "scenes/s",
                                           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step(db, args, reach, gate) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def kernel_suite(sc, ctx, dev, peak_ops):
+    """Each row's kernel alone, timed with CUDA events on the context's stream."""
+    import torch
+    stream = ctx.stream
+    out = {}
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    # exact-minimum collision, shelf batch (65,536 x 32 objects x 64 spheres, 20 boxes)
+    shelf = synth.shelf(seed=1)
+    db = sc.DeviceBatch(shelf, device=dev)
+    order = torch.from_numpy(sc.order_by_work(shelf)).to(dev)
+    poses, _, _ = sc.sample_poses(ctx, db, seed=1)
+    col = torch.empty(shelf.n_cand, dtype=torch.uint8, device=dev)
+    md = torch.empty(shelf.n_cand, dtype=torch.float32, device=dev)
+    cb = torch.empty(shelf.n_cand, dtype=torch.uint8, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    for mode in (0, 1):
+        ms, work = [], []
+        for i in range(5):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a, b = ev()
+            a.record(stream)
+            sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=(0, 0, 0, 0, mode))
+            b.record(stream)
+            work.append(sc.collide_last_work(ctx))
+            if i >= 2:
+                ms.append(a.elapsed_time(b))
+        ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX for p, q in work[2:]])
+        key = "collide_exact_min_shelf" if mode == 0 else "collide_decide_shelf"
+        out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": shelf.n_cand / (np.mean(ms) / 1e3),
+                    "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
+                    "box_pairs": float(np.mean([w[1] for w in work[2:]])),
+                    "exhaustive_pairs": float(shelf.n_cand * 496 * 64 * 64),
+                    "roofline_frac": float(ops / (np.mean(ms) / 1e3) / peak_ops)}
+    del db, poses, col, md, cb
+    # IK: 262,144 top-down grasp targets over the tabletop region, 32 seeds x 100 iterations
+    arm = sc.make_arm(*synth.arm_arrays())
+    tg = torch.from_numpy(synth.topdown_targets(seed=3, n=262144)).to(dev)
+    ms = []
+    for i in range(4):
+        a, b = ev()
+        a.record(stream)
+        r, q, err = sc.ik_reach(ctx, arm, sc.ik_params(seed=3), tg)
+        b.record(stream)
+        b.synchronize()
+        if i >= 1:
+            ms.append(a.elapsed_time(b))
+    out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / (np.mean(ms) / 1e3),
+                                "reachable": float(r.float().mean().item())}
+    # gate inference and one training epoch
+    net = sc.Surrogate(ctx, seed=1)
+    ms = []
+    for i in range(4):
+        a, b = ev()
+        a.record(stream)
+        net.infer(tg)
+        b.record(stream)
+        b.synchronize()
+        if i >= 1:
+            ms.append(a.elapsed_time(b))
+    flops = 2.0 * 262144 * (9 * 256 + 2 * 256 * 256 + 256)
+    out["gate_infer_262144"] = {"ms": float(np.mean(ms)), "samples_per_s": 262144 / (np.mean(ms) / 1e3),
+                                "tflops": flops / (np.mean(ms) / 1e3) / 1e12}
+    y = (torch.rand(262144, device=dev) < 0.5).to(torch.uint8)
+    a, b = ev()
+    a.record(stream)
+    net.train(tg, y, sc.train_params(epochs=1, batch=4096))
+    b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b)
+    out["gate_train_epoch_262144"] = {"ms": t, "samples_per_s": 262144 / (t / 1e3),
+                                      "tflops": 3 * flops / (t / 1e3) / 1e12}
+    net.close()
+    return out
+
+
+def launches_per_step(db, args, reach, gate):
+    """Kernels one sc_generate call enqueues (init + per object and try; reach stage for the first objects)."""
+    K, R = db.c.max_obj, args.retries
+    per_try_reach = 4 if gate is not None else 2  # grasp targets, [gate forward, gate split], IK
+    n_reach = min(4, K) if reach else 0
+    return 1 + K * (R + 1) + n_reach * (R + 1) * per_try_reach
 
 
 def main():
@@ -415,6 +533,13 @@ def main():
     ap.add_argument("--collide-config", type=str, default="", help="threads,a_per_lane,seg_len,ctas_per_sm")
     ap.add_argument("--tune-verbose", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the generation steps eagerly")
+    ap.add_argument("--no-reach", action="store_true", help="generation without the reachability stage")
+    ap.add_argument("--no-gate", action="store_true", help="no learned gate (exact IK on every try)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain (eager, ungated) comparison run")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel measurements")
+    ap.add_argument("--train-labels", type=int, default=4194304)
+    ap.add_argument("--train-epochs", type=int, default=2)
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.workload == "ragged" and args.templates != 4096:

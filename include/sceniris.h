@@ -374,6 +374,22 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
                       int32_t n_order, const sc_collide_config* config, const sc_gen_reach* reach, float* poses,
                       uint8_t* valid, uint8_t* band, int32_t* tries, float* q_reach);
 
+/* Work and time of the last sc_generate call (synchronises the stream). */
+typedef struct {
+  int64_t sphere_pairs;        /* sphere pairs the collision stage evaluated */
+  int64_t sphere_box_pairs;
+  int64_t ik_solves;           /* targets the exact IK solved */
+  int64_t gate_rejections;     /* tries the learned gate sent back without IK */
+  int64_t ik_seed_iterations;  /* sum over solves of seeds x (checks made) */
+  float ms_stage[3];           /* with timing on: device time of the generation-step launches,
+                                  the grasp-target + gate launches, and the IK launches */
+  int32_t launches_stage[3];
+} sc_gen_stats;
+sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
+/* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured
+ * with one setting is re-captured for the other). */
+sc_status sc_ctx_set_timing(sc_ctx* ctx, int32_t on);
+
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],
  * cand_tmpl_off [T+1]; out_order [n_cand] receives candidate indices. */

@@ -41,6 +41,17 @@ class ScSampleParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_attempts", I32), ("retry", I32), ("first_obj", I32), ("n_obj", I32)]
 
 
+class ScGenStats(ctypes.Structure):
+    _fields_ = [("sphere_pairs", I64), ("sphere_box_pairs", I64), ("ik_solves", I64), ("gate_rejections", I64),
+                ("ik_seed_iterations", I64), ("ms_stage", ctypes.c_float * 3), ("launches_stage", I32 * 3)]
+
+    def as_dict(self):
+        return {"sphere_pairs": self.sphere_pairs, "sphere_box_pairs": self.sphere_box_pairs,
+                "ik_solves": self.ik_solves, "gate_rejections": self.gate_rejections,
+                "ik_seed_iterations": self.ik_seed_iterations, "ms_stage": list(self.ms_stage),
+                "launches_stage": list(self.launches_stage)}
+
+
 class ScGenReach(ctypes.Structure):
     _fields_ = [("arm", P), ("ik", P), ("gate", P)]
 
@@ -115,6 +126,8 @@ SIGNATURES = {
     "sc_surrogate_tune_threshold": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, P]),
     "sc_mlp_save": (ctypes.c_int, [P, P, ctypes.c_char_p]),
     "sc_mlp_load": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.POINTER(P)]),
+    "sc_generate_stats": (ctypes.c_int, [P, ctypes.POINTER(ScGenStats)]),
+    "sc_ctx_set_timing": (ctypes.c_int, [P, I32]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
 }
 
@@ -164,6 +177,14 @@ class Context:
 
     def synchronize(self):
         _check(lib().sc_ctx_synchronize(self.handle))
+
+    def set_timing(self, on: bool):
+        _check(lib().sc_ctx_set_timing(self.handle, int(on)))
+
+    def generate_stats(self) -> dict:
+        st = ScGenStats()
+        _check(lib().sc_generate_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
 
     @property
     def num_sms(self) -> int:

@@ -31,6 +31,11 @@ struct sc_ctx {
   unsigned char gen_key[512] = {};
   size_t gen_key_len = 0;
   unsigned long long seed_host = 0;
+  // stage timing (sc_ctx_set_timing)
+  int timing = 0;
+  std::vector<cudaEvent_t> tev;
+  std::vector<int> tcls;
+  sc::StageTimer timer;
   // cached reach extent of the last batch seen with a reachability stage
   const void* reach_key[3] = {nullptr, nullptr, nullptr};
   int reach_extent = -1;
@@ -152,6 +157,7 @@ void sc_ctx_destroy(sc_ctx* ctx) {
   if (ctx->gen_exec) cudaGraphExecDestroy(ctx->gen_exec);
   if (ctx->gen_graph) cudaGraphDestroy(ctx->gen_graph);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
   delete ctx;
 }
@@ -319,6 +325,11 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.tau = (want_reach && reach->gate) ? reach->gate->tau : 0.f;
   a.q_reach = want_reach ? q_reach : nullptr;
   a.reach_objects = 0;
+  a.timer = nullptr;
+  if (ctx->timing) {
+    ctx->timer.used = 0;
+    a.timer = &ctx->timer;
+  }
   if (want_reach) {
     const void* key[3] = {batch->tmpl_obj_off, batch->obj_rel,
                           reinterpret_cast<const void*>((intptr_t)batch->n_templates)};
@@ -358,6 +369,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     float tau;
     float* q_reach;
     int reach_objects;
+    int timing;
   } key;
   static_assert(sizeof(Key) <= sizeof(ctx->gen_key), "graph key too large");
   std::memset(&key, 0, sizeof(key));
@@ -380,6 +392,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   key.tau = a.tau;
   key.q_reach = a.q_reach;
   key.reach_objects = a.reach_objects;
+  key.timing = ctx->timing;
   const bool hit = ctx->gen_exec && ctx->gen_key_len == sizeof(key) && !std::memcmp(ctx->gen_key, &key, sizeof(key));
   if (!hit) {
     if (ctx->gen_exec) { cudaGraphExecDestroy(ctx->gen_exec); ctx->gen_exec = nullptr; }
@@ -715,6 +728,62 @@ sc_status sc_mlp_load(sc_ctx* ctx, const char* path, sc_mlp** out) {
   }
   sc::mlp_set_step(m->st, step);
   *out = m;
+  return SC_OK;
+}
+
+sc_status sc_ctx_set_timing(sc_ctx* ctx, int32_t on) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  DeviceGuard g(ctx->device);
+  if (on && ctx->tev.empty()) {
+    const int cap = 8192;
+    ctx->tev.resize(2 * cap);
+    ctx->tcls.resize(cap);
+    for (auto& e : ctx->tev) {
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) {
+        for (auto& x : ctx->tev)
+          if (x) cudaEventDestroy(x);
+        ctx->tev.clear();
+        ctx->tcls.clear();
+        return cuda_fail(err, "cudaEventCreate");
+      }
+    }
+    ctx->timer.ev = ctx->tev.data();
+    ctx->timer.cls = ctx->tcls.data();
+    ctx->timer.cap = cap;
+  }
+  ctx->timing = on ? 1 : 0;
+  return SC_OK;
+}
+
+sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(SC_ERR_INVALID, "out is NULL");
+  DeviceGuard g(ctx->device);
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaStreamSynchronize(ctx->stream);
+  if (e) return cuda_fail(e, "stats read");
+  std::memset(out, 0, sizeof(*out));
+  out->sphere_pairs = (int64_t)h[0];
+  out->sphere_box_pairs = (int64_t)h[1];
+  out->ik_solves = (int64_t)h[2];
+  out->gate_rejections = (int64_t)h[3];
+  out->ik_seed_iterations = (int64_t)h[4];
+  if (ctx->timing) {
+    for (int i = 0; i < ctx->timer.used; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]);
+      if (e) return cuda_fail(e, "cudaEventElapsedTime");
+      const int c = ctx->tcls[i];
+      if (c >= 0 && c < 3) {
+        out->ms_stage[c] += ms;
+        out->launches_stage[c] += 1;
+      }
+    }
+  }
   return SC_OK;
 }
 

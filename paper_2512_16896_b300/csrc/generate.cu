@@ -591,11 +591,13 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       g.counter = counters + k * (R + 1) + r;
       g.list_reach = reach_k ? list_reach : nullptr;
       g.n_reach = reach_k ? cnt_reach + k * (R + 1) + r : nullptr;
+      if (a.timer) a.timer->begin(0, s);
       switch (cfg.a_per_lane) {
         case 1: launch_step<1>(g, grid, cfg.threads, smem, s); break;
         case 2: launch_step<2>(g, grid, cfg.threads, smem, s); break;
         default: launch_step<4>(g, grid, cfg.threads, smem, s); break;
       }
+      if (a.timer) a.timer->end(s);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if (!reach_k) continue;
       ra.k = k;
@@ -606,12 +608,18 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       ra.n_retry = g.n_retry;
       ra.list_next = g.list_next;
       ra.n_next = g.n_next;
+      if (a.timer) a.timer->begin(1, s);
       reach_targets_kernel<<<small_blocks, 256, 0, s>>>(ra);
       if (ra.gated) {
         if ((e = mlp_infer_counted(a.gate, targets, ra.n_reach, n, logits, num_sms, s)) != cudaSuccess) return e;
         gate_split_kernel<<<small_blocks, 256, 0, s>>>(ra);
       }
+      if (a.timer) {
+        a.timer->end(s);
+        a.timer->begin(2, s);
+      }
       reach_ik_kernel<<<num_sms * 8, 128, 0, s>>>(ra);
+      if (a.timer) a.timer->end(s);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }

@@ -38,6 +38,25 @@ sc_status validate_batch(const sc_scene_batch* b);
 
 struct MlpState;
 
+// Optional stage timing: event pairs recorded around launches, by class
+// (0 = generation step, 1 = grasp targets + gate, 2 = exact IK).
+struct StageTimer {
+  cudaEvent_t* ev = nullptr;  // pool of 2 * cap events
+  int* cls = nullptr;         // class of each pair
+  int cap = 0;
+  int used = 0;
+  void begin(int c, cudaStream_t s) {
+    if (!ev || used >= cap) return;
+    cls[used] = c;
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s) {
+    if (!ev || used >= cap) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+  }
+};
+
 struct GenerateLaunch {
   const int32_t* order;  // candidates to generate (NULL: 0..n_items-1)
   int n_items;
@@ -58,6 +77,7 @@ struct GenerateLaunch {
   float tau;
   int reach_objects;     // object indices < reach_objects may carry the reach flag
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
+  StageTimer* timer;     // NULL: no timing
 };
 
 size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
