@@ -363,12 +363,13 @@ def run_ours(args, wl):
         ops_gen = sum(s["sphere_pairs"] for s in st) * OPS_PER_SPHERE_PAIR + \
             sum(s["sphere_box_pairs"] for s in st) * OPS_PER_SPHERE_BOX
         ops_ik = sum(s["ik_seed_iterations"] for s in st) * OPS_PER_IK_SEED_ITER
+        rate_gen = ops_gen / max(ms_gen / 1e3, 1e-12)  # FP32-pipe operations per second
+        rate_ik = ops_ik / max(ms_ik / 1e3, 1e-12)
         gen = {"kernel": "gen_warp_kernel (sample + collision decision)", "ms_per_step": ms_gen / len(st),
-               "launches_per_step": st[0]["launches_stage"][0],
-               "achieved": ops_gen / max(ms_gen, 1e-9) / 1e9, "frac": ops_gen / max(ms_gen, 1e-9) * 1e3 / peak_ops}
+               "launches_per_step": st[0]["launches_stage"][0], "achieved": rate_gen / 1e12,
+               "frac": rate_gen / peak_ops}
         ik = {"kernel": "reach_ik_kernel (DLS IK)", "ms_per_step": ms_ik / len(st),
-              "launches_per_step": st[0]["launches_stage"][2],
-              "achieved": ops_ik / max(ms_ik, 1e-9) / 1e9, "frac": ops_ik / max(ms_ik, 1e-9) * 1e3 / peak_ops}
+              "launches_per_step": st[0]["launches_stage"][2], "achieved": rate_ik / 1e12, "frac": rate_ik / peak_ops}
         return gen, ik
 
     gen_rf, ik_rf = stage_roofline(main)
@@ -413,7 +414,7 @@ def run_ours(args, wl):
                    "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
                    "sphere_pairs_per_step": st0["sphere_pairs"], "ik_seed_iterations_per_step": st0["ik_seed_iterations"],
                    "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"]},
-        "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"] / 1e3, "peak": peak_ops / 1e12,
+        "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": dom["frac"], "traffic": measured_traffic(dom_file, args.workload),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "
                                     f"({peak_src} max clock)",
@@ -426,6 +427,8 @@ def run_ours(args, wl):
         "gpu_launches": launches_per_step(db, args, reach, gate) * args.steps,
         "clocks": clk,
     }
+    if not args.no_kernels and world == 1:
+        line["kernels"] = kernel_suite(sc, ctx, dev, peak_ops)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -36,6 +36,7 @@ struct sc_ctx {
   std::vector<cudaEvent_t> tev;
   std::vector<int> tcls;
   sc::StageTimer timer;
+  int gen_timer_used = 0;  // event pairs the captured graph records
   // cached reach extent of the last batch seen with a reachability stage
   const void* reach_key[3] = {nullptr, nullptr, nullptr};
   int reach_extent = -1;
@@ -415,7 +416,9 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     ctx->gen_graph = graph;
     std::memcpy(ctx->gen_key, &key, sizeof(key));
     ctx->gen_key_len = sizeof(key);
+    ctx->gen_timer_used = ctx->timer.used;
   }
+  if (ctx->timing) ctx->timer.used = ctx->gen_timer_used;  // the replay records the captured events again
   e = cudaGraphLaunch(ctx->gen_exec, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return SC_OK;
