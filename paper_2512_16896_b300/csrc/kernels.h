@@ -48,11 +48,13 @@ struct StageTimer {
   void begin(int c, cudaStream_t s) {
     if (!ev || used >= cap) return;
     cls[used] = c;
-    cudaEventRecord(ev[2 * used], s);
+    // External: inside a stream capture this becomes an event-record node of
+    // the graph (a plain record would only be an internal dependency).
+    cudaEventRecordWithFlags(ev[2 * used], s, cudaEventRecordExternal);
   }
   void end(cudaStream_t s) {
     if (!ev || used >= cap) return;
-    cudaEventRecord(ev[2 * used + 1], s);
+    cudaEventRecordWithFlags(ev[2 * used + 1], s, cudaEventRecordExternal);
     ++used;
   }
 };
