@@ -348,6 +348,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   if (e != cudaSuccess) return cuda_fail(e, "seed upload");
   const char* why = nullptr;
   if (!params->use_graph) {
+    ctx->timer.flags = cudaEventRecordDefault;
     e = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->stream, &why);
     if (why) return fail(SC_ERR_INVALID, "generate config: %s", why);
     if (e != cudaSuccess) return cuda_fail(e, "generate launch");
@@ -405,6 +406,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     }
     e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    ctx->timer.flags = cudaEventRecordExternal;
     cudaError_t e_enq = sc::enqueue_generate(*batch, a, cfg, ctx->num_sms, ctx->capture_stream, &why);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(ctx->capture_stream, &graph);

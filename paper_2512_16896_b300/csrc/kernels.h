@@ -45,16 +45,17 @@ struct StageTimer {
   int* cls = nullptr;         // class of each pair
   int cap = 0;
   int used = 0;
+  // Inside a stream capture the records must be external event nodes (a plain
+  // record would only be an internal dependency); outside, plain records.
+  unsigned int flags = cudaEventRecordDefault;
   void begin(int c, cudaStream_t s) {
     if (!ev || used >= cap) return;
     cls[used] = c;
-    // External: inside a stream capture this becomes an event-record node of
-    // the graph (a plain record would only be an internal dependency).
-    cudaEventRecordWithFlags(ev[2 * used], s, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(ev[2 * used], s, flags);
   }
   void end(cudaStream_t s) {
     if (!ev || used >= cap) return;
-    cudaEventRecordWithFlags(ev[2 * used + 1], s, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(ev[2 * used + 1], s, flags);
     ++used;
   }
 };
