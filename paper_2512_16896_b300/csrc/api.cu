@@ -183,6 +183,7 @@ sc_status sc_ctx_synchronize(sc_ctx* ctx) {
   if (e != cudaSuccess) return cuda_fail(e, "status read");
   if (st != 0) {
     cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (st == sc::kDevTimeout) return fail(SC_ERR_TIMEOUT, "a bounded tensor-core wait gave up (device code 7)");
     return fail(SC_ERR_DEVICE, "a kernel latched device error code %d (1 bad template, 2 too many spheres, "
                 "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation)", st);
   }
@@ -542,7 +543,7 @@ sc_status sc_surrogate_infer(sc_ctx* ctx, const sc_mlp* m, const float* targets,
   if (n == 0) return SC_OK;
   if (!targets || !logits) return fail(SC_ERR_INVALID, "targets or logits is NULL");
   DeviceGuard g(ctx->device);
-  cudaError_t e = sc::mlp_infer(m->st, targets, nullptr, n, logits, ctx->num_sms, ctx->stream);
+  cudaError_t e = sc::mlp_infer(m->st, targets, n, logits, ctx->d_status, ctx->num_sms, ctx->stream);
   if (e) return cuda_fail(e, "surrogate inference");
   return SC_OK;
 }
@@ -649,7 +650,7 @@ sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* m, const float* targe
   float* logits = nullptr;
   cudaError_t e = cudaMalloc(&logits, (size_t)n * 4);
   if (e) return fail(SC_ERR_OOM, "logit buffer: %s", cudaGetErrorString(e));
-  e = sc::mlp_infer(m->st, targets, nullptr, n, logits, ctx->num_sms, ctx->stream);
+  e = sc::mlp_infer(m->st, targets, n, logits, ctx->d_status, ctx->num_sms, ctx->stream);
   std::vector<float> z(n);
   std::vector<uint8_t> y(n);
   if (!e) e = cudaMemcpyAsync(z.data(), logits, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream);

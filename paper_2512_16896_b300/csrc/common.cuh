@@ -27,7 +27,16 @@ enum DeviceError : int {
   kDevTooManyBoxes = 4,
   kDevBadPolygon = 5,
   kDevBadRelation = 6,  // relation refers to itself or a later object
+  kDevTimeout = 7,      // a bounded wait on a tensor-core MMA or bulk copy gave up
 };
+
+// Byte offset of element (r, k) of a [rows][K] bf16 matrix in the canonical
+// no-swizzle K-major layout of the tensor cores: core matrices of 8 rows x 16
+// bytes, adjacent core matrices along K 128 bytes apart, 8-row groups
+// K / 8 * 128 bytes apart.
+__host__ __device__ __forceinline__ uint32_t canon_offset(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
 
 __device__ __forceinline__ void latch_error(int* status, int code) {
   if (status) atomicCAS(status, 0, code);

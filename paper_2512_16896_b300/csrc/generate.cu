@@ -611,7 +611,8 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       if (a.timer) a.timer->begin(1, s);
       reach_targets_kernel<<<small_blocks, 256, 0, s>>>(ra);
       if (ra.gated) {
-        if ((e = mlp_infer_counted(a.gate, targets, ra.n_reach, n, logits, num_sms, s)) != cudaSuccess) return e;
+        e = mlp_infer_counted(a.gate, targets, ra.n_reach, n, logits, a.status, num_sms, s);
+        if (e != cudaSuccess) return e;
         gate_split_kernel<<<small_blocks, 256, 0, s>>>(ra);
       }
       if (a.timer) {

@@ -101,15 +101,31 @@ cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets
 // ---- surrogate MLP (mlp.cu)
 struct MlpState;
 int mlp_param_count();
+
+// Weights of the surrogate as the tensor-core forward pass reads them.
+struct MlpTcWeights {
+  const float* params;     // FP32 masters (biases)
+  const void* W1c;         // bf16 [256][16] canonical layout (see canon_offset)
+  const void* W2c;         // bf16 [256][256] canonical layout
+  const void* W3c;
+  const void* W4;          // bf16 [256]
+  const float* mu;         // [9]
+  const float* inv_sigma;  // [9]
+  int off_b1, off_b2, off_b3, off_b4;
+};
+// Logits of n rows of targets (or min(n, *n_dev) when n_dev is set) on
+// tcgen05; a wait that gives up latches kDevTimeout into *status.
+cudaError_t mlp_forward_tc(const MlpTcWeights& w, const float* targets, int n, const int* n_dev, float* logits,
+                           int* status, int num_sms, cudaStream_t s);
 cudaError_t mlp_alloc(MlpState** out);
 void mlp_free(MlpState* S);
 cudaError_t mlp_init(MlpState* S, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_refresh_copies(MlpState* S, cudaStream_t s);
 cudaError_t mlp_set_norm_from(MlpState* S, const float* targets, int n, cudaStream_t s);
-cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* index, int n, float* logits,
+cudaError_t mlp_infer(const MlpState* S, const float* targets, int n, float* logits, int* status,
                       int num_sms, cudaStream_t s);
 cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int* n_dev, int n_cap, float* logits,
-                              int num_sms, cudaStream_t s);
+                              int* status, int num_sms, cudaStream_t s);
 cudaError_t mlp_reserve(MlpState* S, int Bcap);
 cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
                           float* loss_dev, int num_sms, cudaStream_t s);

@@ -393,8 +393,11 @@ __global__ void mlp_adam_kernel(float* params, const float* grads, float* m, flo
   }
 }
 
+// bf16 copies of the weights: row-major [out][in] (training forward), the
+// transposes (backward) and the canonical tensor-core layout (inference).
 __global__ void mlp_copies_kernel(const float* params, __nv_bfloat16* W1, __nv_bfloat16* W2, __nv_bfloat16* W3,
-                                  __nv_bfloat16* W4, __nv_bfloat16* W2t, __nv_bfloat16* W3t) {
+                                  __nv_bfloat16* W4, __nv_bfloat16* W2t, __nv_bfloat16* W3t, __nv_bfloat16* W1c,
+                                  __nv_bfloat16* W2c, __nv_bfloat16* W3c) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * H; i += gridDim.x * blockDim.x) {
     const int n = i / H, k = i % H;
     const __nv_bfloat16 w2 = __float2bfloat16_rn(params[OFF_W2 + i]);
@@ -403,9 +406,13 @@ __global__ void mlp_copies_kernel(const float* params, __nv_bfloat16* W1, __nv_b
     W3[i] = w3;
     W2t[k * H + n] = w2;
     W3t[k * H + n] = w3;
+    W2c[canon_offset(n, k, H) / 2] = w2;
+    W3c[canon_offset(n, k, H) / 2] = w3;
     if (i < H * KIN) {
       const int n1 = i / KIN, k1 = i % KIN;
-      W1[i] = __float2bfloat16_rn(k1 < 9 ? params[OFF_W1 + n1 * 9 + k1] : 0.f);
+      const __nv_bfloat16 w1 = __float2bfloat16_rn(k1 < 9 ? params[OFF_W1 + n1 * 9 + k1] : 0.f);
+      W1[i] = w1;
+      W1c[canon_offset(n1, k1, KIN) / 2] = w1;
     }
     if (i < H) W4[i] = __float2bfloat16_rn(params[OFF_W4 + i]);
   }
@@ -476,6 +483,7 @@ struct MlpState {
   float* v = nullptr;
   float* grads = nullptr;
   __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W4 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  __nv_bfloat16 *W1c = nullptr, *W2c = nullptr, *W3c = nullptr;  // canonical tensor-core layout (inference)
   float* mu = nullptr;
   float* inv_sigma = nullptr;
   double* moments = nullptr;
@@ -502,7 +510,9 @@ cudaError_t mlp_alloc(MlpState** out) {
   if ((e = cudaMalloc(&S->params, nf * 4)) || (e = cudaMalloc(&S->m, nf * 4)) || (e = cudaMalloc(&S->v, nf * 4)) ||
       (e = cudaMalloc(&S->grads, nf * 4)) || (e = cudaMalloc(&S->W1, H * KIN * 2)) ||
       (e = cudaMalloc(&S->W2, H * H * 2)) || (e = cudaMalloc(&S->W3, H * H * 2)) || (e = cudaMalloc(&S->W4, H * 2)) ||
-      (e = cudaMalloc(&S->W2t, H * H * 2)) || (e = cudaMalloc(&S->W3t, H * H * 2)) || (e = cudaMalloc(&S->mu, 64)) ||
+      (e = cudaMalloc(&S->W2t, H * H * 2)) || (e = cudaMalloc(&S->W3t, H * H * 2)) ||
+      (e = cudaMalloc(&S->W1c, H * KIN * 2)) || (e = cudaMalloc(&S->W2c, H * H * 2)) ||
+      (e = cudaMalloc(&S->W3c, H * H * 2)) || (e = cudaMalloc(&S->mu, 64)) ||
       (e = cudaMalloc(&S->inv_sigma, 64)) || (e = cudaMalloc(&S->moments, 18 * 8))) {
     mlp_free(S);
     return e;
@@ -513,15 +523,16 @@ cudaError_t mlp_alloc(MlpState** out) {
 
 void mlp_free(MlpState* S) {
   if (!S) return;
-  void* ptrs[] = {S->params, S->m, S->v, S->grads, S->W1, S->W2, S->W3, S->W4, S->W2t, S->W3t, S->mu, S->inv_sigma,
-                  S->moments, S->train_buf};
+  void* ptrs[] = {S->params, S->m,   S->v,   S->grads, S->W1, S->W2,        S->W3,      S->W4,
+                  S->W2t,    S->W3t, S->W1c, S->W2c, S->W3c,  S->mu, S->inv_sigma, S->moments, S->train_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete S;
 }
 
 cudaError_t mlp_refresh_copies(MlpState* S, cudaStream_t s) {
-  mlp_copies_kernel<<<128, 256, 0, s>>>(S->params, S->W1, S->W2, S->W3, S->W4, S->W2t, S->W3t);
+  mlp_copies_kernel<<<128, 256, 0, s>>>(S->params, S->W1, S->W2, S->W3, S->W4, S->W2t, S->W3t, S->W1c, S->W2c,
+                                         S->W3c);
   return cudaGetLastError();
 }
 
@@ -547,38 +558,39 @@ cudaError_t mlp_set_norm_from(MlpState* S, const float* targets, int n, cudaStre
 
 // Kernels that take more than 48 KB of dynamic shared memory opt in once.
 static cudaError_t smem_opt_in() {
-  cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       4 * kWarpSmem);
-  if (!e) e = cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWarpSmem);
+  cudaError_t e =
+      cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWarpSmem);
   if (!e)
     e = cudaFuncSetAttribute(mlp_backward_act_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWarpSmemBwd);
   return e;
 }
 
-cudaError_t mlp_infer(const MlpState* S, const float* targets, const int32_t* index, int n, float* logits,
-                      int num_sms, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  if (cudaError_t e = smem_opt_in()) return e;
-  const int warps = 4, rows_per_block = warps * 16;
-  int blocks = (n + rows_per_block - 1) / rows_per_block;
-  if (blocks > num_sms * 8) blocks = num_sms * 8;
-  TrainCache tc{};
-  mlp_forward_kernel<false><<<blocks, warps * 32, warps * kWarpSmem, s>>>(dev_view(*S), targets, index, n, nullptr,
-                                                                           logits, tc);
-  return cudaGetLastError();
+static MlpTcWeights tc_view(const MlpState& S) {
+  MlpTcWeights w;
+  w.params = S.params;
+  w.W1c = S.W1c;
+  w.W2c = S.W2c;
+  w.W3c = S.W3c;
+  w.W4 = S.W4;
+  w.mu = S.mu;
+  w.inv_sigma = S.inv_sigma;
+  w.off_b1 = OFF_B1;
+  w.off_b2 = OFF_B2;
+  w.off_b3 = OFF_B3;
+  w.off_b4 = OFF_B4;
+  return w;
+}
+
+// Inference runs on tcgen05 (mlp_tc.cu); the mma.sync forward above serves
+// training, where the pre-activations and transposed caches are written too.
+cudaError_t mlp_infer(const MlpState* S, const float* targets, int n, float* logits, int* status, int num_sms,
+                      cudaStream_t s) {
+  return mlp_forward_tc(tc_view(*S), targets, n, nullptr, logits, status, num_sms, s);
 }
 
 cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int* n_dev, int n_cap, float* logits,
-                              int num_sms, cudaStream_t s) {
-  if (n_cap <= 0) return cudaSuccess;
-  if (cudaError_t e = smem_opt_in()) return e;
-  const int warps = 4, rows_per_block = warps * 16;
-  int blocks = (n_cap + rows_per_block - 1) / rows_per_block;
-  if (blocks > num_sms * 8) blocks = num_sms * 8;
-  TrainCache tc{};
-  mlp_forward_kernel<false><<<blocks, warps * 32, warps * kWarpSmem, s>>>(dev_view(*S), targets, nullptr, n_cap, n_dev,
-                                                                           logits, tc);
-  return cudaGetLastError();
+                              int* status, int num_sms, cudaStream_t s) {
+  return mlp_forward_tc(tc_view(*S), targets, n_cap, n_dev, logits, status, num_sms, s);
 }
 
 // Batch buffers: caches + backward outputs for Bcap rows.

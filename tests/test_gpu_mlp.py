@@ -58,12 +58,16 @@ def random_net(seed):
     return P
 
 
-def test_forward_matches_oracle(sc, ctx):
+# 1 row; a ragged tail past 128-row tiles; more tiles than CTAs (each CTA
+# takes several tiles and reloads the layer weights between them)
+@pytest.mark.parametrize("n", [1, 4099, 2 * 148 * 128 + 77])
+def test_forward_matches_oracle(sc, ctx, n):
     P = random_net(1)
     net = sc.Surrogate(ctx, seed=0)
     net.set(pack(P), P.mu, P.sigma, 0.0)
-    tg = synth.topdown_targets(seed=11, n=4099)  # a ragged tail past a 64-row tile
+    tg = synth.topdown_targets(seed=11, n=n)
     z = net.infer(torch.from_numpy(tg).cuda()).cpu().numpy().astype(np.float64)
+    ctx.synchronize()  # raises if a bounded device wait gave up
     zr, _ = omlp.forward(P, tg, bf16=True)
     scale = max(1.0, np.abs(zr).max())
     assert np.abs(z - zr).max() <= 2e-2 * scale, np.abs(z - zr).max()
