@@ -349,8 +349,8 @@ typedef struct {
  * later objects are not placed.
  * order   int32 [n_order] candidates to generate (NULL: all n_cand; then
  *         n_order is ignored); the heaviest first balances the first steps.
- * config  launch shape of the per-step kernel (NULL: default; decide_only is
- *         implied).
+ * config  launch shape of the per-step kernel (NULL: default {256, 1, 256, 4};
+ *         zero fields keep their default; decide_only is implied).
  * Outputs, indexed by candidate (only listed candidates are written):
  * poses   float [P][4] CSR pose layout; objects never placed are NaN.
  * valid   u8 [n_cand]: 1 when every object was placed.

@@ -37,9 +37,10 @@ struct sc_ctx {
   std::vector<int> tcls;
   sc::StageTimer timer;
   int gen_timer_used = 0;  // event pairs the captured graph records
-  // cached reach extent of the last batch seen with a reachability stage
-  const void* reach_key[3] = {nullptr, nullptr, nullptr};
+  // cached scan of the last batch generated from: reach extent, most spheres of one object
+  const void* scan_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int reach_extent = -1;
+  int max_sph_obj = -1;
 };
 
 struct sc_mlp {
@@ -214,6 +215,10 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
 }
 
 static const sc_collide_config kDefaultCollide = {256, 4, 256, 4, 0};
+// The generation step culls spheres before its pair sweep, so its register
+// blocks are small; one A sphere per lane also keeps its instruction
+// footprint smallest (the step is bound by instruction fetch, not the FMA pipe).
+static const sc_collide_config kDefaultGenerate = {256, 1, 256, 4, 1};
 
 sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
                         int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
@@ -286,7 +291,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     if (params->max_retries > 65535) return fail(SC_ERR_INVALID, "max_retries > 65535 with a reachability stage");
     if (batch->max_obj > 65535) return fail(SC_ERR_INVALID, "max_obj > 65535 with a reachability stage");
   }
-  sc_collide_config cfg = kDefaultCollide;
+  sc_collide_config cfg = kDefaultGenerate;
   if (config) {
     if (config->threads) cfg.threads = config->threads;
     if (config->a_per_lane) cfg.a_per_lane = config->a_per_lane;
@@ -294,7 +299,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     if (config->ctas_per_sm) cfg.ctas_per_sm = config->ctas_per_sm;
   }
   DeviceGuard g(ctx->device);
-  const size_t need = sc::generate_scratch_bytes(n, batch->max_obj, params->max_retries);
+  const size_t need = sc::generate_scratch_bytes(*batch, n, params->max_retries);
   if (need > ctx->gen_scratch_bytes) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -310,7 +315,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.n_items = n;
   // the seed lives in device scratch (an aligned slot after the lists), written before each run
   unsigned long long* seed_dev = reinterpret_cast<unsigned long long*>(
-      static_cast<char*>(ctx->gen_scratch) + sc::generate_seed_offset(n, batch->max_obj, params->max_retries));
+      static_cast<char*>(ctx->gen_scratch) + sc::generate_seed_offset(*batch, n, params->max_retries));
   a.seed_dev = seed_dev;
   a.max_attempts = params->max_attempts;
   a.max_retries = params->max_retries;
@@ -327,22 +332,26 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.tau = (want_reach && reach->gate) ? reach->gate->tau : 0.f;
   a.q_reach = want_reach ? q_reach : nullptr;
   a.reach_objects = 0;
+  a.max_sph_obj = 0;
   a.timer = nullptr;
   if (ctx->timing) {
     ctx->timer.used = 0;
     a.timer = &ctx->timer;
   }
-  if (want_reach) {
-    const void* key[3] = {batch->tmpl_obj_off, batch->obj_rel,
-                          reinterpret_cast<const void*>((intptr_t)batch->n_templates)};
-    if (ctx->reach_extent < 0 || std::memcmp(key, ctx->reach_key, sizeof(key))) {
-      int ext = 0;
-      cudaError_t e = sc::reach_extent(*batch, ctx->d_status + 2, &ext, ctx->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "reach extent scan");
-      std::memcpy(ctx->reach_key, key, sizeof(key));
-      ctx->reach_extent = ext;
+  {
+    const void* key[5] = {batch->tmpl_obj_off, batch->obj_rel, batch->obj_sph_off,
+                          reinterpret_cast<const void*>((intptr_t)batch->n_templates),
+                          reinterpret_cast<const void*>((intptr_t)batch->n_objects)};
+    if (ctx->reach_extent < 0 || std::memcmp(key, ctx->scan_key, sizeof(key))) {
+      int out[2] = {0, 0};
+      cudaError_t e = sc::batch_scan(*batch, ctx->d_status + 2, out, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "batch scan");
+      std::memcpy(ctx->scan_key, key, sizeof(key));
+      ctx->reach_extent = out[0];
+      ctx->max_sph_obj = out[1];
     }
-    a.reach_objects = ctx->reach_extent;
+    a.reach_objects = want_reach ? ctx->reach_extent : 0;
+    a.max_sph_obj = ctx->max_sph_obj;
   }
   ctx->seed_host = params->seed;
   cudaError_t e = cudaMemcpyAsync(seed_dev, &ctx->seed_host, 8, cudaMemcpyHostToDevice, ctx->stream);
@@ -372,6 +381,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     float tau;
     float* q_reach;
     int reach_objects;
+    int max_sph_obj;
     int timing;
   } key;
   static_assert(sizeof(Key) <= sizeof(ctx->gen_key), "graph key too large");
@@ -395,6 +405,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   key.tau = a.tau;
   key.q_reach = a.q_reach;
   key.reach_objects = a.reach_objects;
+  key.max_sph_obj = a.max_sph_obj;
   key.timing = ctx->timing;
   const bool hit = ctx->gen_exec && ctx->gen_key_len == sizeof(key) && !std::memcmp(ctx->gen_key, &key, sizeof(key));
   if (!hit) {

@@ -259,6 +259,7 @@ __device__ __forceinline__ float slow_group(const ABlock<APL>& A, const float4* 
 template <int APL, bool MASKED, bool DECIDE>
 __device__ __forceinline__ void sweep(ABlock<APL>& A, const float4* W, const float* beta, int jb, int je, int S,
                                       float& m, float rmax, float eps, int* best_key, int* hit, bool& alive) {
+#pragma unroll 1
   for (int j = jb; j < je; j += kGroup) {
     float4 B[kGroup];
     float bt[kGroup];

@@ -26,10 +26,25 @@ namespace {
 
 using namespace core;
 
+// Per-template constants gathered once per generation call (one 64-byte
+// record, read with four vector loads instead of a chain of CSR lookups).
+struct TmplInfo {
+  int o0, nt, s0, bx0;           // first object, objects, first sphere, first world box
+  int nobb, v0, nv, cand0;       // world boxes, first polygon vertex, vertices, first candidate
+  long long pose0;               // first pose row
+  float z, pad;                  // support height
+  float xmin, xmax, ymin, ymax;  // support polygon bounding box
+};
+static_assert(sizeof(TmplInfo) == 64, "TmplInfo is four 16-byte loads");
+
 struct GenStepArgs {
   sc_scene_batch b;
+  const int32_t* cand_t;    // [n_cand] template of each candidate (-1: none)
+  const TmplInfo* tinfo;    // [n_templates]
+  const float* edge_inv;    // [n_verts] 1 / squared length of the edge ending at each vertex
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, retry, max_retries, k, seg_len;
+  int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
   const int32_t* list_in;
   const int* n_in;
   int32_t* list_retry;
@@ -51,20 +66,76 @@ struct GenStepArgs {
 // yaw) and the new object's spheres in the world frame (relative to object
 // 0's position) with |c|^2 - r^2.
 struct WarpLayout {
-  int off, pose, sc, kobj, kpref, B, beta, bytes;
+  int off, pose, sc, kobj, kball, B, beta, astage, bytes;
 };
 
-__host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
+// max_sk: most spheres of one object in the batch (B side); apl: A spheres
+// per lane of the register block (A staging holds one block plus 64).
+__host__ __device__ inline WarpLayout make_warp_layout(int max_obj, int max_sk, int apl) {
   WarpLayout W;
   W.off = 0;
   W.pose = align16(4 * (max_obj + 1));
   W.sc = align16(W.pose + 16 * max_obj);
   W.kobj = align16(W.sc + 8 * max_obj);
-  W.kpref = align16(W.kobj + 4 * max_obj);
-  W.B = align16(W.kpref + 4 * (max_obj + 1));
-  W.beta = align16(W.B + 16 * (kMaxSphPerObj + kPad));
-  W.bytes = align16(W.beta + 4 * (kMaxSphPerObj + kPad));
+  W.kball = align16(W.kobj + 4 * max_obj);
+  W.B = align16(W.kball + 16 * max_obj);
+  W.beta = align16(W.B + 16 * (max_sk + kPad));
+  W.astage = align16(W.beta + 4 * (max_sk + kPad));
+  W.bytes = align16(W.astage + 16 * (32 * apl + 64));
   return W;
+}
+
+// Asynchronous global -> shared copies (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Decides the staged A spheres [0, fill) (slot s * 32 + lane of the register
+// block) against the B spheres [0, Sc) in shared memory (decide mode, fixed
+// tolerance eps).
+template <int APL>
+__device__ __forceinline__ void sweep_block(const float4* astage, int fill, const float4* Bs, const float* Bb, int Sc,
+                                            float eps, int lane, float& m, bool& alive) {
+  ABlock<APL> A;
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    const bool valid = s * 32 + lane < fill;
+    const float4 w = valid ? astage[s * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    A.ax[s] = -2.f * w.x; A.ay[s] = -2.f * w.y; A.az[s] = -2.f * w.z;
+    A.a2[s] = w.x * w.x + w.y * w.y + w.z * w.z;
+    A.r[s] = w.w;
+    A.bst[s] = valid ? 0 : INT_MAX;
+  }
+  refresh<APL, true>(A, 0.f, 0.f, eps);
+  sweep<APL, false, true>(A, Bs, Bb, 0, Sc, Sc, m, 0.f, eps, nullptr, nullptr, alive);
+}
+
+// Routing of a finished try (warp-uniform).
+enum Route : int { kRouteNone = 0, kRouteReach = 1, kRouteNext = 2, kRouteRetry = 3 };
+
+// Appends the warp's pending routed candidates (lane i holds entry i < npend)
+// to their lists: one atomic per list and flush instead of one per try.
+__device__ __forceinline__ void flush_routes(const GenStepArgs& g, int pend_c, int pend_r, int npend, int lane) {
+#pragma unroll
+  for (int d = kRouteReach; d <= kRouteRetry; ++d) {
+    const bool mine = lane < npend && pend_r == d;
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, mine);
+    if (!mask) continue;
+    int* cnt = d == kRouteReach ? g.n_reach : d == kRouteNext ? g.n_next : g.n_retry;
+    int32_t* list = d == kRouteReach ? g.list_reach : d == kRouteNext ? g.list_next : g.list_retry;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (mine) list[base + __popc(mask & ((1u << lane) - 1u))] = pend_c;
+  }
 }
 
 // One warp per candidate: sample object k, then decide whether any sphere of
@@ -74,225 +145,350 @@ __host__ __device__ inline WarpLayout make_warp_layout(int max_obj) {
 // |H| (its box's half-diagonal) around the object's frame origin, so two
 // objects whose origins are farther apart than |H_j| + |H_k| + margin have no
 // sphere pair within the band; only the other objects' spheres are streamed.
+// Work distribution: warp w takes item w first, then items claimed from the
+// launch's counter (the claim for the next item is issued before the current
+// one is processed, so its latency overlaps the work); routed candidates are
+// buffered per warp and appended 32 at a time.
 template <int APL>
 __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
-  const WarpLayout WL = make_warp_layout(b.max_obj);
+  const WarpLayout WL = make_warp_layout(b.max_obj, g.max_sk, APL);
   const int lane = threadIdx.x & 31;
+  const int warps_per_block = blockDim.x >> 5;
   unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * WL.bytes;
   int* off = reinterpret_cast<int*>(base + WL.off);
   float4* opose = reinterpret_cast<float4*>(base + WL.pose);
   float2* osc = reinterpret_cast<float2*>(base + WL.sc);
   int* kobj = reinterpret_cast<int*>(base + WL.kobj);
-  int* kpref = reinterpret_cast<int*>(base + WL.kpref);
+  float4* kball = reinterpret_cast<float4*>(base + WL.kball);
   float4* Bs = reinterpret_cast<float4*>(base + WL.B);
   float* Bb = reinterpret_cast<float*>(base + WL.beta);
+  float4* astage = reinterpret_cast<float4*>(base + WL.astage);
   const int n_items = *(volatile const int*)g.n_in;
   const int k = g.k;
+  const int warps_total = gridDim.x * warps_per_block;
+  int item = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+  if (item >= n_items) return;  // no atomic traffic from warps without work
   const uint64_t seed = *g.seed;
   unsigned long long my_pairs = 0, my_box = 0;
+  int pend_c = 0, pend_r = kRouteNone, npend = 0;
 
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = (int)atomicAdd(g.counter, 1u);
-    item = __shfl_sync(0xFFFFFFFFu, item, 0);
-    if (item >= n_items) break;
+  while (item < n_items) {
+    int next = 0;
+    if (lane == 0) next = warps_total + (int)atomicAdd(g.counter, 1u);
     const int c = __ldg(&g.list_in[item]);
-    const int t = template_of(b, c);
-    int o0 = 0, nt = 0, s0 = 0, Sprev = 0, Sk = 0, nobb = 0, bx0 = 0;
-    int64_t pbase = 0;
+    const int t = (c >= 0 && c < b.n_cand) ? __ldg(&g.cand_t[c]) : -1;
+    TmplInfo T = {};
     if (t >= 0) {
-      o0 = __ldg(&b.tmpl_obj_off[t]);
-      nt = __ldg(&b.tmpl_obj_off[t + 1]) - o0;
-      s0 = __ldg(&b.obj_sph_off[o0]);
-      bx0 = __ldg(&b.tmpl_obb_off[t]);
-      nobb = __ldg(&b.tmpl_obb_off[t + 1]) - bx0;
-      pbase = __ldg(&b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&b.cand_tmpl_off[t])) * nt;
-      if (k < nt) {
-        Sprev = __ldg(&b.obj_sph_off[o0 + k]) - s0;
-        Sk = __ldg(&b.obj_sph_off[o0 + k + 1]) - s0 - Sprev;
-      }
+      const int4* src = reinterpret_cast<const int4*>(g.tinfo + t);
+      const int4 q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2), q3 = __ldg(src + 3);
+      T.o0 = q0.x; T.nt = q0.y; T.s0 = q0.z; T.bx0 = q0.w;
+      T.nobb = q1.x; T.v0 = q1.y; T.nv = q1.z; T.cand0 = q1.w;
+      T.pose0 = (long long)(((unsigned long long)(unsigned)q2.y << 32) | (unsigned)q2.x);
+      T.z = __int_as_float(q2.z);
+      T.xmin = __int_as_float(q3.x); T.xmax = __int_as_float(q3.y);
+      T.ymin = __int_as_float(q3.z); T.ymax = __int_as_float(q3.w);
+    }
+    const int o0 = T.o0, nt = T.nt;
+    int Sprev = 0, Sk = 0, rel = 0;
+    if (t >= 0 && k < nt) {
+      Sprev = __ldg(&b.obj_sph_off[o0 + k]) - T.s0;
+      Sk = __ldg(&b.obj_sph_off[o0 + k + 1]) - T.s0 - Sprev;
+      rel = __ldg(&b.obj_rel[o0 + k]);
     }
     const int err = t < 0 ? kDevBadTemplate
                     : (k >= nt || nt > b.max_obj || nt > kMaxObj) ? kDevTooManyObjects
-                    : (Sk > kMaxSphPerObj || Sprev + Sk > b.max_sph) ? kDevTooManySpheres
-                    : (nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
+                    : (Sk > g.max_sk || Sprev + Sk > b.max_sph) ? kDevTooManySpheres
+                    : (T.nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
+    int route = kRouteNone;
     if (err != kDevOk) {
       if (lane == 0) {
         latch_error(g.status, err);
         if (t >= 0) g.band[c] = 1;
       }
-      continue;
-    }
-    // ---- sample object k
-    const Support sup = warp_support(b, t, lane);
-    SampleResult r;
-    r.placed = false;
-    r.band = true;
-    r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (sup.ok) {
-      r = warp_sample_object(b, sup, seed, g.max_attempts, g.retry, c, k, o0, g.poses, pbase, g.status, lane);
-    } else if (lane == 0) {
-      latch_error(g.status, kDevBadPolygon);
-    }
-    if (lane == 0) g.poses[pbase + k] = r.pose;
-    bool pass = false, bnd = r.band;
-    if (r.placed) {
-      // ---- objects 0..k
-      for (int j = lane; j <= k; j += 32) {
-        const float4 p = (j == k) ? r.pose : g.poses[pbase + j];
-        float sn, cs;
-        sincosf(p.w, &sn, &cs);
-        opose[j] = p;
-        osc[j] = make_float2(sn, cs);
-        off[j] = __ldg(&b.obj_sph_off[o0 + j]) - s0;
+    } else {
+      const int s0 = T.s0, nobb = T.nobb, bx0 = T.bx0;
+      const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * nt;
+      // ---- sample object k
+      Support sup;
+      sup.P.v = reinterpret_cast<const float2*>(b.poly_verts) + T.v0;
+      sup.P.n = T.nv;
+      sup.P.inv = g.edge_inv + T.v0;
+      sup.ok = T.nv >= 3 && T.nv <= kMaxPolyVerts;
+      sup.z = T.z;
+      sup.xmin = T.xmin; sup.xmax = T.xmax; sup.ymin = T.ymin; sup.ymax = T.ymax;
+      const ObjectSpec spec = load_object_spec(b, o0, k, rel, g.poses, pbase, g.status, lane);
+      // Earlier objects' poses, half extents (into the kept-ball slots, which
+      // the broad phase overwrites after reading) and sphere offsets are
+      // copied to shared memory asynchronously while object k is sampled.
+#pragma unroll 1
+      for (int j = lane; j < k; j += 32) {
+        cp_async16(opose + j, g.poses + pbase + j);
+        cp_async16(kball + j, reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
       }
+#pragma unroll 1
+      for (int j = lane; j <= k; j += 32) cp_async4(off + j, b.obj_sph_off + o0 + j);
+      cp_async_commit();
+      SampleResult r;
+      r.placed = false;
+      r.band = true;
+      r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (sup.ok) {
+        r = warp_sample_spec(sup, spec, seed, g.max_attempts, g.retry, c, k, lane);
+      } else if (lane == 0) {
+        latch_error(g.status, kDevBadPolygon);
+      }
+      if (lane == 0) g.poses[pbase + k] = r.pose;
+      cp_async_wait_all();
       __syncwarp();
-      const float4 ref = opose[0];
-      // ---- broad phase: earlier objects whose bounding balls come near object k's
-      int nkeep = 0;
-      {
+      bool pass = false, bnd = r.band;
+      if (r.placed) {
+        // ---- objects 0..k: yaw sin/cos (off[] holds absolute sphere offsets)
+#pragma unroll 1
+        for (int j = lane; j <= k; j += 32) {
+          const float4 p = (j == k) ? r.pose : opose[j];
+          float sn, cs;
+          sincosf(p.w, &sn, &cs);
+          if (j == k) opose[k] = p;
+          osc[j] = make_float2(sn, cs);
+        }
+        __syncwarp();
+        const float4 ref = opose[0];
+        // ---- broad phase: earlier objects whose bounding balls come near
+        // object k's; the kept ones' balls (relative to ref) go to kball
+        int nkeep = 0;
+        float a_bound = 0.f;  // bound on |a| over the kept objects' spheres
         const float4 pk = opose[k];
-        const float4 Hk = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + k);
+        const float4 Hk = spec.H;
         const float rk = sqrtf(Hk.x * Hk.x + Hk.y * Hk.y + Hk.z * Hk.z);
+#pragma unroll 1
         for (int j0 = 0; j0 < k; j0 += 32) {
           const int j = j0 + lane;
           bool keep = false;
-          int cnt = 0;
+          float4 ball = make_float4(0.f, 0.f, 0.f, 0.f);
           if (j < k) {
             const float4 pj = opose[j];
-            const float4 Hj = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
+            const float4 Hj = kball[j];
             const float rj = sqrtf(Hj.x * Hj.x + Hj.y * Hj.y + Hj.z * Hj.z);
             const float dx = pj.x - pk.x, dy = pj.y - pk.y, dz = pj.z - pk.z;
             const float lim = rj + rk + kBroadMargin;
             keep = dx * dx + dy * dy + dz * dz <= lim * lim;
-            cnt = off[j + 1] - off[j];
+            ball = make_float4(pj.x - ref.x, pj.y - ref.y, pj.z - ref.z, rj);
+            if (keep) a_bound = fmaxf(a_bound, sqrtf(ball.x * ball.x + ball.y * ball.y + ball.z * ball.z) + rj);
           }
           const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
-          // prefix of kept sphere counts within this chunk of 32 objects
-          int pre = keep ? cnt : 0;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
-            if (lane >= o) pre += v;
-          }
-          const int base_sph = nkeep == 0 ? 0 : kpref[nkeep];
+          __syncwarp();  // every half extent of this chunk is read before slots are overwritten
           if (keep) {
             const int slot = nkeep + __popc(mask & ((1u << lane) - 1u));
             kobj[slot] = j;
-            kpref[slot + 1] = base_sph + pre;
+            kball[slot] = ball;
           }
-          if (nkeep == 0 && lane == 0) kpref[0] = 0;
           nkeep += __popc(mask);
           __syncwarp();
         }
-        if (lane == 0 && nkeep == 0) kpref[0] = 0;
-        __syncwarp();
-      }
-      const int Skeep = kpref[nkeep];
-      // ---- object k's spheres (B side)
-      {
-        const float4 p = opose[k];
-        const float2 sc2 = osc[k];
-        float r2 = 0.f;
-        for (int q = lane; q < Sk + kPad; q += 32) {
-          if (q < Sk) {
-            const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
-            const float x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
-            const float y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
-            const float z = (p.z - ref.z) + l.z;
-            const float c2 = x * x + y * y + z * z;
-            Bs[q] = make_float4(x, y, z, l.w);
-            Bb[q] = c2 - l.w * l.w;
-            r2 = fmaxf(r2, c2);
-          } else {
+        a_bound = -warp_min(-a_bound);
+        // ---- object k's spheres (B side)
+        {
+          const float4 p = opose[k];
+          const float2 sc2 = osc[k];
+          float r2 = 0.f;
+#pragma unroll 1
+          for (int q = lane; q < Sk + kPad; q += 32) {
+            if (q < Sk) {
+              const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
+              const float x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
+              const float y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
+              const float z = (p.z - ref.z) + l.z;
+              const float c2 = x * x + y * y + z * z;
+              Bs[q] = make_float4(x, y, z, l.w);
+              Bb[q] = c2 - l.w * l.w;
+              r2 = fmaxf(r2, c2);
+            } else {
+              Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
+              Bb[q] = 3e12f;
+            }
+          }
+          __syncwarp();
+          float m = kFarSentinel;
+          // ---- object k vs world boxes
+#pragma unroll 1
+          for (int bi = 0; bi < nobb; ++bi) {
+            const float* o = b.obb + 12 * (bx0 + bi);
+            float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
+            const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+            qx *= inv; qy *= inv; qz *= inv; qw *= inv;
+            // columns of R (R maps box frame to world)
+            const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
+            const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
+            const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
+            const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
+            const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
+#pragma unroll 1
+            for (int q = lane; q < Sk; q += 32) {
+              const float4 w = Bs[q];
+              const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
+              const float px = c00 * vx + c01 * vy + c02 * vz;
+              const float py = c10 * vx + c11 * vy + c12 * vz;
+              const float pz = c20 * vx + c21 * vy + c22 * vz;
+              const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
+              const float em = fmaxf(ex, fmaxf(ey, ez));
+              if (em - w.w < kBand) {
+                const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
+                m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
+              }
+            }
+          }
+          my_box += (unsigned long long)nobb * (unsigned long long)(lane < Sk ? (Sk - lane + 31) / 32 : 0);
+          m = warp_min(m);
+          bool alive = !(m < -kBand);
+          r2 = -warp_min(-r2);
+          // ---- sphere-level cull (exact): every sphere lies in its object's
+          // bounding ball, so a B sphere farther than band + margin from every
+          // kept object's ball, or an A sphere that far from object k's ball,
+          // has no pair within the band. B is compacted in place, A into the
+          // register block; decisions are unchanged.
+          unsigned keepbits = 0;  // bit u: sphere lane + 32 u is near a kept object
+#pragma unroll 1
+          for (int jj = 0; alive && jj < nkeep; ++jj) {
+            const float4 kb = kball[jj];
+#pragma unroll 1
+            for (int q = lane, u = 0; q < Sk; q += 32, ++u) {
+              const float4 w = Bs[q];
+              const float dx = w.x - kb.x, dy = w.y - kb.y, dz = w.z - kb.z;
+              const float lim = kb.w + w.w + kBand + kBroadMargin;
+              if (dx * dx + dy * dy + dz * dz <= lim * lim) keepbits |= 1u << u;
+            }
+          }
+          int Sc = 0;  // B spheres kept
+#pragma unroll 1
+          for (int q0 = 0, u = 0; q0 < Sk; q0 += 32, ++u) {
+            const int q = q0 + lane;
+            const bool keep = (keepbits >> u) & 1u;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            float bb = 0.f;
+            if (keep) {
+              w = Bs[q];
+              bb = Bb[q];
+            }
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+            __syncwarp();  // this chunk is read before it is overwritten
+            if (keep) {
+              const int pos = Sc + __popc(mask & ((1u << lane) - 1u));
+              Bs[pos] = w;
+              Bb[pos] = bb;
+            }
+            Sc += __popc(mask);
+          }
+#pragma unroll 1
+          for (int q = Sc + lane; q < Sc + kPad; q += 32) {
             Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
             Bb[q] = 3e12f;
           }
-        }
-        __syncwarp();
-        float m = kFarSentinel;
-        // ---- object k vs world boxes
-        for (int bi = 0; bi < nobb; ++bi) {
-          const float* o = b.obb + 12 * (bx0 + bi);
-          float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
-          const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
-          qx *= inv; qy *= inv; qz *= inv; qw *= inv;
-          // columns of R (R maps box frame to world)
-          const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
-          const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
-          const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
-          const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
-          const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
-          for (int q = lane; q < Sk; q += 32) {
-            const float4 w = Bs[q];
-            const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
-            const float px = c00 * vx + c01 * vy + c02 * vz;
-            const float py = c10 * vx + c11 * vy + c12 * vz;
-            const float pz = c20 * vx + c21 * vy + c22 * vz;
-            const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
-            const float em = fmaxf(ex, fmaxf(ey, ez));
-            if (em - w.w < kBand) {
-              const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
-              m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
-            }
-          }
-        }
-        my_box += (unsigned long long)nobb * (unsigned long long)(lane < Sk ? (Sk - lane + 31) / 32 : 0);
-        m = warp_min(m);
-        bool alive = !(m < -kBand);
-        r2 = -warp_min(-r2);
-        // ---- object k vs the kept earlier objects (A side in registers)
-        for (int i0 = 0; alive && i0 < Skeep; i0 += 32 * APL) {
-          ABlock<APL> A;
-          float a2max = 0.f;
-          int nval = 0;
-#pragma unroll
-          for (int s = 0; s < APL; ++s) {
-            const int qq = i0 + s * 32 + lane;
-            const bool valid = qq < Skeep;
-            float x = 0.f, y = 0.f, z = 0.f, rr = 0.f;
-            if (valid) {
-              const int jj = upper_index(kpref, nkeep + 1, qq);
+          __syncwarp();
+          // one tolerance for the whole try, from bounds on |a| and |b|
+          const float eps = 1e-5f * (fmaxf(r2, a_bound * a_bound) + 0.01f);
+          const float ckx = pk.x - ref.x, cky = pk.y - ref.y, ckz = pk.z - ref.z;
+          // ---- object k vs the kept earlier objects: A spheres are read 64 at
+          // a time per kept object, culled against object k's ball, staged in
+          // shared memory and decided 32 * APL at a time from registers (one
+          // sweep site: a full block, or the remainder once nothing is left)
+          constexpr int kCap = 32 * APL;
+          int fill = 0, jj = 0, qb = 0, q1 = 0;
+          bool have_obj = false;
+          float px = 0.f, py = 0.f, pz = 0.f;
+          float2 osj = make_float2(0.f, 1.f);  // sin, cos of the current kept object's yaw
+#pragma unroll 1
+          for (;;) {
+#pragma unroll 1
+            while (!have_obj && jj < nkeep) {
               const int j = kobj[jj];
-              const int q = off[j] + (qq - kpref[jj]);
-              const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
+              qb = off[j] - s0;
+              q1 = off[j + 1] - s0;
               const float4 p = opose[j];
-              const float2 sc2 = osc[j];
-              x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
-              y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
-              z = (p.z - ref.z) + l.z;
-              rr = l.w;
-              ++nval;
+              osj = osc[j];
+              px = p.x - ref.x; py = p.y - ref.y; pz = p.z - ref.z;
+              have_obj = qb < q1;
+              if (!have_obj) ++jj;
             }
-            A.ax[s] = -2.f * x; A.ay[s] = -2.f * y; A.az[s] = -2.f * z;
-            A.a2[s] = x * x + y * y + z * z;
-            A.r[s] = rr;
-            A.bst[s] = valid ? 0 : INT_MAX;
-            a2max = fmaxf(a2max, A.a2[s]);
+            const bool more = Sc > 0 && have_obj;
+            if (alive && more && fill < kCap) {
+              float4 cand[2];
+              bool ck[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int q = qb + u * 32 + lane;
+                cand[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ck[u] = false;
+                if (q < q1) {
+                  const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
+                  cand[u].x = px + (osj.y * l.x - osj.x * l.y);
+                  cand[u].y = py + (osj.x * l.x + osj.y * l.y);
+                  cand[u].z = pz + l.z;
+                  cand[u].w = l.w;
+                  const float dx = cand[u].x - ckx, dy = cand[u].y - cky, dz = cand[u].z - ckz;
+                  const float lim = rk + l.w + kBand + kBroadMargin;
+                  ck[u] = dx * dx + dy * dy + dz * dz <= lim * lim;
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, ck[u]);
+                if (ck[u]) astage[fill + __popc(mask & ((1u << lane) - 1u))] = cand[u];
+                fill += __popc(mask);
+              }
+              qb += 64;
+              if (qb >= q1) {
+                have_obj = false;
+                ++jj;
+              }
+            }
+            const int n_sw = fill >= kCap ? kCap : (more ? 0 : fill);
+            if (alive && n_sw > 0) {
+              __syncwarp();
+              my_pairs += (unsigned long long)n_sw * (unsigned long long)Sc;
+              sweep_block<APL>(astage, n_sw, Bs, Bb, Sc, eps, lane, m, alive);
+              // move the staged overflow (at most 63 spheres) to the front
+              const int over = fill - n_sw;
+              __syncwarp();
+              const float4 v0 = lane < over ? astage[n_sw + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float4 v1 = lane + 32 < over ? astage[n_sw + 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+              __syncwarp();
+              if (lane < over) astage[lane] = v0;
+              if (lane + 32 < over) astage[lane + 32] = v1;
+              fill = over;
+            }
+            if (!alive || (!more && fill == 0)) break;
           }
-          const float eps = 1e-5f * (fmaxf(r2, -warp_min(-a2max)) + 0.01f);
-          refresh<APL, true>(A, 0.f, 0.f, eps);
-          my_pairs += (unsigned long long)nval * (unsigned long long)Sk;
-          sweep<APL, false, true>(A, Bs, Bb, 0, Sk, Sk, m, 0.f, eps, nullptr, nullptr, alive);
+          pass = alive && !(m < 0.f);
+          bnd = bnd || fabsf(m) <= kBand;
         }
-        pass = alive && !(m < 0.f);
-        bnd = bnd || fabsf(m) <= kBand;
+      }
+      if (pass) {
+        if (g.list_reach && (rel & SC_REL_REACH)) route = kRouteReach;
+        else if (k + 1 < nt) route = kRouteNext;
+      } else if (g.retry < g.max_retries) {
+        route = kRouteRetry;
+      }
+      if (lane == 0) {
+        if (bnd) g.band[c] = 1;
+        atomicAdd(&g.tries[c], 1);
+        if (pass && route == kRouteNone) g.valid[c] = 1;  // object k was the last one
       }
     }
-    if (lane == 0) {
-      if (bnd) g.band[c] = 1;
-      g.tries[c] += 1;
-      if (pass) {
-        if (g.list_reach && (__ldg(&b.obj_rel[o0 + k]) & SC_REL_REACH)) g.list_reach[atomicAdd(g.n_reach, 1)] = c;
-        else if (k + 1 == nt) g.valid[c] = 1;
-        else g.list_next[atomicAdd(g.n_next, 1)] = c;
-      } else if (g.retry < g.max_retries) {
-        g.list_retry[atomicAdd(g.n_retry, 1)] = c;
+    if (route != kRouteNone) {
+      if (lane == npend) {
+        pend_c = c;
+        pend_r = route;
       }
+      ++npend;
     }
     __syncwarp();  // the warp's shared memory is reused by its next candidate
+    item = __shfl_sync(0xFFFFFFFFu, next, 0);
+    if (npend == 32 || (npend > 0 && item >= n_items)) {
+      flush_routes(g, pend_c, pend_r, npend, lane);
+      npend = 0;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -413,14 +609,53 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
   }
 }
 
-// 1 + the largest template-local index of an object carrying the reach flag.
-__global__ void reach_extent_kernel(sc_scene_batch b, int* out) {
+// out[0]: 1 + the largest template-local index of an object carrying the
+// reach flag; out[1]: the most spheres of one object.
+__global__ void batch_scan_kernel(sc_scene_batch b, int* out) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_templates; t += gridDim.x * blockDim.x) {
     const int o0 = b.tmpl_obj_off[t], o1 = b.tmpl_obj_off[t + 1];
     int ext = 0;
     for (int o = o0; o < o1; ++o)
       if (b.obj_rel[o] & SC_REL_REACH) ext = o - o0 + 1;
     if (ext) atomicMax(out, ext);
+  }
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < b.n_objects; o += gridDim.x * blockDim.x)
+    atomicMax(out + 1, b.obj_sph_off[o + 1] - b.obj_sph_off[o]);
+}
+
+// Per-call tables: the template of every candidate, one TmplInfo record per
+// template (with the support polygon's bounding box) and the inverse squared
+// length of every polygon edge (edge i runs from vertex i-1 to vertex i,
+// cyclically within its polygon; 0 for a zero-length edge).
+__global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* tinfo, float* edge_inv) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b.n_cand; c += stride) cand_t[c] = template_of(b, c);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_templates; t += stride) {
+    TmplInfo T;
+    T.o0 = b.tmpl_obj_off[t];
+    T.nt = b.tmpl_obj_off[t + 1] - T.o0;
+    T.s0 = b.obj_sph_off[T.o0];
+    T.bx0 = b.tmpl_obb_off[t];
+    T.nobb = b.tmpl_obb_off[t + 1] - T.bx0;
+    T.v0 = b.tmpl_poly_off[t];
+    T.nv = b.tmpl_poly_off[t + 1] - T.v0;
+    T.cand0 = b.cand_tmpl_off[t];
+    T.pose0 = b.tmpl_pose_off[t];
+    T.z = b.tmpl_support_z[t];
+    T.pad = 0.f;
+    float xmin = 3e38f, xmax = -3e38f, ymin = 3e38f, ymax = -3e38f;
+    if (T.nv >= 3 && T.nv <= kMaxPolyVerts) {
+      const float2* v = reinterpret_cast<const float2*>(b.poly_verts) + T.v0;
+      for (int i = 0; i < T.nv; ++i) {
+        const float2 a = v[i == 0 ? T.nv - 1 : i - 1], p = v[i];
+        xmin = fminf(xmin, p.x); xmax = fmaxf(xmax, p.x);
+        ymin = fminf(ymin, p.y); ymax = fmaxf(ymax, p.y);
+        const float ex = p.x - a.x, ey = p.y - a.y, len2 = ex * ex + ey * ey;
+        edge_inv[T.v0 + i] = len2 > 0.f ? 1.f / len2 : 0.f;
+      }
+    }
+    T.xmin = xmin; T.xmax = xmax; T.ymin = ymin; T.ymax = ymax;
+    tinfo[t] = T;
   }
 }
 
@@ -471,29 +706,46 @@ void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaS
 
 }  // namespace
 
-cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_host, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(scratch_int, 0, sizeof(int), s);
+cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(scratch_int2, 0, 2 * sizeof(int), s);
   if (e) return e;
-  reach_extent_kernel<<<64, 256, 0, s>>>(b, scratch_int);
+  batch_scan_kernel<<<64, 256, 0, s>>>(b, scratch_int2);
   if ((e = cudaGetLastError())) return e;
-  if ((e = cudaMemcpyAsync(out_host, scratch_int, sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaMemcpyAsync(out_host2, scratch_int2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
   return cudaStreamSynchronize(s);
 }
 
 // Scratch: 6 int32 lists of n (next x2, retry x2, reach, gate-passed), the
 // grasp targets (12 floats) and logits of the reach list, counts
-// [K+1] + 3 x [K][R+1], work counters [K][R+1], then the seed scalar.
-size_t generate_seed_offset(int n_cand, int max_obj, int max_retries) {
-  const size_t n = (size_t)n_cand;
-  const size_t lists = 6 * n * sizeof(int32_t) + 13 * n * sizeof(float);
-  const size_t counts = (size_t)(max_obj + 1) + 3 * (size_t)max_obj * (max_retries + 1);
-  const size_t counters = (size_t)max_obj * (max_retries + 1);
-  const size_t body = lists + (counts + counters) * sizeof(int);
-  return (body + 255) & ~size_t(255);  // the 8-byte seed sits on a 256-byte boundary
+// [K+1] + 3 x [K][R+1], work counters [K][R+1], the per-call tables
+// (candidate templates, TmplInfo records, inverse edge lengths), then the
+// seed scalar.
+struct GenScratch {
+  size_t lists, counts, counters, cand_t, tinfo, edge_inv, seed, total;
+};
+
+static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int max_retries) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t n = (size_t)n_items;
+  const size_t K = (size_t)b.max_obj, R1 = (size_t)max_retries + 1;
+  GenScratch L;
+  L.lists = 0;
+  L.counts = up(L.lists + 6 * n * sizeof(int32_t) + 13 * n * sizeof(float));
+  L.counters = L.counts + ((K + 1) + 3 * K * R1) * sizeof(int);
+  L.cand_t = up(L.counters + K * R1 * sizeof(unsigned int));
+  L.tinfo = up(L.cand_t + (size_t)b.n_cand * sizeof(int32_t));
+  L.edge_inv = up(L.tinfo + (size_t)b.n_templates * sizeof(TmplInfo));
+  L.seed = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));  // the 8-byte seed on a 256-byte boundary
+  L.total = L.seed + 256;
+  return L;
 }
 
-size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries) {
-  return generate_seed_offset(n_cand, max_obj, max_retries) + 256;
+size_t generate_seed_offset(const sc_scene_batch& b, int n_items, int max_retries) {
+  return gen_scratch_layout(b, n_items, max_retries).seed;
+}
+
+size_t generate_scratch_bytes(const sc_scene_batch& b, int n_items, int max_retries) {
+  return gen_scratch_layout(b, n_items, max_retries).total;
 }
 
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
@@ -501,27 +753,31 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   *why = check_collide_config(cfg);
   if (*why) return cudaErrorInvalidValue;
   if (cfg.threads > 512) { *why = "generation uses at most 512 threads per CTA"; return cudaErrorInvalidValue; }
-  const size_t smem = (size_t)(cfg.threads / 32) * make_warp_layout(b.max_obj).bytes;
+  const int max_sk = a.max_sph_obj > 0 ? a.max_sph_obj : kMaxSphPerObj;
+  const size_t smem = (size_t)(cfg.threads / 32) * make_warp_layout(b.max_obj, max_sk, cfg.a_per_lane).bytes;
   if (smem > 227 * 1024) { *why = "threads x per-warp shared memory exceeds one CTA's (lower threads)"; return cudaErrorInvalidValue; }
   const int n = a.n_items;
   const int K = b.max_obj, R = a.max_retries;
-  // scratch carve-up: 4 lists of n ints, counts[K+1] (list sizes per object),
-  // retry counts[K][R+1], work counters[K][R+1]
-  int32_t* ib = static_cast<int32_t*>(a.scratch);
+  const GenScratch SL = gen_scratch_layout(b, n, R);
+  char* sb = static_cast<char*>(a.scratch);
+  int32_t* ib = reinterpret_cast<int32_t*>(sb + SL.lists);
   int32_t* L[2] = {ib, ib + n};
   int32_t* Rl[2] = {ib + 2 * (size_t)n, ib + 3 * (size_t)n};
   int32_t* list_reach = ib + 4 * (size_t)n;
   int32_t* list_ik = ib + 5 * (size_t)n;
   float* targets = reinterpret_cast<float*>(ib + 6 * (size_t)n);
   float* logits = targets + 12 * (size_t)n;
-  int* counts = reinterpret_cast<int*>(logits + n);
+  int* counts = reinterpret_cast<int*>(sb + SL.counts);
   const int n_counts = (K + 1) + 3 * K * (R + 1);
   int* cnt_list = counts;
   int* cnt_retry = counts + (K + 1);
   int* cnt_reach = cnt_retry + K * (R + 1);
   int* cnt_ik = cnt_reach + K * (R + 1);
-  unsigned int* counters = reinterpret_cast<unsigned int*>(counts + n_counts);
+  unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
   const int n_counters = K * (R + 1);
+  int32_t* cand_t = reinterpret_cast<int32_t*>(sb + SL.cand_t);
+  TmplInfo* tinfo = reinterpret_cast<TmplInfo*>(sb + SL.tinfo);
+  float* edge_inv = reinterpret_cast<float*>(sb + SL.edge_inv);
   const unsigned long long* seed_dev = a.seed_dev;
 
   int grid = 0;
@@ -539,13 +795,20 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, L[0], counts, n_counts, counters, n_counters,
                                            reinterpret_cast<float4*>(a.poses), a.valid, a.band, a.tries, a.stats,
                                            a.status);
+    int tb = ((b.n_cand > b.n_templates ? b.n_cand : b.n_templates) + 255) / 256;
+    tb = tb < num_sms * 4 ? tb : num_sms * 4;
+    gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   GenStepArgs g;
   g.b = b;
+  g.cand_t = cand_t;
+  g.tinfo = tinfo;
+  g.edge_inv = edge_inv;
   g.seed = seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
+  g.max_sk = max_sk;
   g.seg_len = cfg.seg_len;
   g.poses = reinterpret_cast<float4*>(a.poses);
   g.valid = a.valid;

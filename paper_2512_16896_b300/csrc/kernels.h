@@ -69,7 +69,7 @@ struct GenerateLaunch {
   uint8_t* valid;
   uint8_t* band;
   int32_t* tries;
-  void* scratch;  // generate_scratch_bytes(n_items, max_obj, max_retries)
+  void* scratch;  // generate_scratch_bytes(batch, n_items, max_retries)
   unsigned long long* stats;  // [0] sphere pairs [1] sphere-box pairs [2] IK solves [3] gate rejections
                               // [4] IK seed-iterations
   int* status;
@@ -79,15 +79,17 @@ struct GenerateLaunch {
   const MlpState* gate;  // NULL: exact IK on every candidate
   float tau;
   int reach_objects;     // object indices < reach_objects may carry the reach flag
+  int max_sph_obj;       // most spheres of one object in the batch (batch_scan)
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
   StageTimer* timer;     // NULL: no timing
 };
 
-size_t generate_scratch_bytes(int n_cand, int max_obj, int max_retries);
+size_t generate_scratch_bytes(const sc_scene_batch& b, int n_items, int max_retries);
 // Byte offset of the 8-byte seed scalar inside that scratch (256-aligned).
-size_t generate_seed_offset(int n_cand, int max_obj, int max_retries);
-// 1 + largest object index with the reach flag (synchronises the stream).
-cudaError_t reach_extent(const sc_scene_batch& b, int* scratch_int, int* out_host, cudaStream_t s);
+size_t generate_seed_offset(const sc_scene_batch& b, int n_items, int max_retries);
+// out_host2[0]: 1 + largest object index with the reach flag; out_host2[1]:
+// most spheres of one object (uses 2 device ints; synchronises the stream).
+cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host2, cudaStream_t s);
 // Enqueues the whole generation (init + one launch per object and try).
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
                              int num_sms, cudaStream_t s, const char** why);

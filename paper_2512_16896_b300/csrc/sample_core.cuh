@@ -11,28 +11,38 @@ namespace sc {
 struct PolyView {
   const float2* v;
   int n;
+  const float* inv;  // optional: 1 / |v_i - v_{i-1}|^2 per vertex (0 for a zero-length edge)
 };
 
 // Crossing-number point-in-polygon (boundary counts as inside) and the
-// Euclidean distance to the boundary (minimum over the edge segments).
+// Euclidean distance to the boundary (minimum over the edge segments). The
+// crossing test compares (px - ax) * ey with (py - ay) * ex instead of
+// dividing by ey, which is the same test for every point off the boundary.
 __device__ __forceinline__ bool pip_with_distance(const PolyView& P, float px, float py, float* dist) {
   bool odd = false;
   float d2 = 3.0e38f;
   float2 a = __ldg(&P.v[P.n - 1]);
+#pragma unroll 1
   for (int i = 0; i < P.n; ++i) {
-    float2 b = __ldg(&P.v[i]);
+    const float2 b = __ldg(&P.v[i]);
     // distance to segment a-b
-    float ex = b.x - a.x, ey = b.y - a.y;
-    float wx = px - a.x, wy = py - a.y;
-    float len2 = ex * ex + ey * ey;
-    float t = len2 > 0.f ? (wx * ex + wy * ey) / len2 : 0.f;
+    const float ex = b.x - a.x, ey = b.y - a.y;
+    const float wx = px - a.x, wy = py - a.y;
+    const float dot = wx * ex + wy * ey;
+    float t;
+    if (P.inv) {
+      t = dot * __ldg(&P.inv[i]);
+    } else {
+      const float len2 = ex * ex + ey * ey;
+      t = len2 > 0.f ? dot / len2 : 0.f;
+    }
     t = fminf(fmaxf(t, 0.f), 1.f);
-    float qx = wx - t * ex, qy = wy - t * ey;
+    const float qx = wx - t * ex, qy = wy - t * ey;
     d2 = fminf(d2, qx * qx + qy * qy);
-    // does edge a-b cross the ray from p towards +x?
+    // does edge a-b cross the ray from p towards +x? (ey != 0 here)
     if ((a.y > py) != (b.y > py)) {
-      float xc = a.x + (py - a.y) * (b.x - a.x) / (b.y - a.y);
-      if (px < xc) odd = !odd;
+      const float lhs = wx * ey, rhs = wy * ex;
+      if (ey > 0.f ? lhs < rhs : lhs > rhs) odd = !odd;
     }
     a = b;
   }
@@ -52,6 +62,7 @@ __device__ __forceinline__ Support warp_support(const sc_scene_batch& b, int t, 
   const int v0 = __ldg(&b.tmpl_poly_off[t]);
   s.P.v = reinterpret_cast<const float2*>(b.poly_verts) + v0;
   s.P.n = __ldg(&b.tmpl_poly_off[t + 1]) - v0;
+  s.P.inv = nullptr;
   s.ok = s.P.n >= 3 && s.P.n <= kMaxPolyVerts;
   s.z = __ldg(&b.tmpl_support_z[t]);
   float xmin = 3e38f, xmax = -3e38f, ymin = 3e38f, ymax = -3e38f;
@@ -79,57 +90,82 @@ struct SampleResult {
   bool band;
 };
 
-// Sample template-local object k of candidate c for try `retry`; the whole
-// warp calls this (uniform arguments). Earlier objects' poses are read from
-// poses[pbase + ref] (written before this call; the caller orders the
-// accesses). Attempts run one per lane; the lowest accepted attempt wins,
-// which equals trying them in order. Lane 0's result is the valid one; every
-// lane gets the same values.
-__device__ __forceinline__ SampleResult warp_sample_object(const sc_scene_batch& b, const Support& sup,
-                                                          uint64_t seed, int max_attempts, int retry, int c, int k,
-                                                          int o0, const float4* poses, int64_t pbase, int* status,
-                                                          int lane) {
+// What sampling object k needs besides the support: its relation, half
+// extents (w: rho), relation parameters and, for a relation, the reference
+// object's pose and half extents. Loaded by load_object_spec so a caller can
+// issue these loads early.
+struct ObjectSpec {
+  int kind, ref;
+  float4 H, RP;
+  float4 ref_pose, ref_half;
+};
+
+// Relation of template-local object k (a relation must refer to an earlier
+// object: otherwise kDevBadRelation is latched and the object is sampled as
+// free). The reference pose is read from poses[pbase + ref], written before
+// this call (the caller orders the accesses).
+__device__ __forceinline__ ObjectSpec load_object_spec(const sc_scene_batch& b, int o0, int k, int rel,
+                                                       const float4* poses, int64_t pbase, int* status, int lane) {
+  ObjectSpec S;
+  const int o = o0 + k;
+  S.kind = rel & SC_REL_KIND_MASK;
+  S.ref = rel >> 8;
+  if (S.kind != SC_REL_FREE && (S.ref < 0 || S.ref >= k || S.kind > SC_REL_NEXT_TO)) {
+    if (lane == 0) latch_error(status, kDevBadRelation);
+    S.kind = SC_REL_FREE;
+  }
+  S.H = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o);
+  S.RP = __ldg(reinterpret_cast<const float4*>(b.obj_rel_param) + o);
+  S.ref_pose = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.ref_half = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (S.kind != SC_REL_FREE) {
+    S.ref_pose = poses[pbase + S.ref];
+    S.ref_half = __ldg(reinterpret_cast<const float4*>(b.obj_half) + (o0 + S.ref));
+  }
+  return S;
+}
+
+// Sample object k (spec S) of candidate c for try `retry`; the whole warp
+// calls this (uniform arguments). Attempts run one per lane; the lowest
+// accepted attempt wins, which equals trying them in order. Every lane gets
+// the same result.
+__device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, const ObjectSpec& S, uint64_t seed,
+                                                        int max_attempts, int retry, int c, int k, int lane) {
   SampleResult R;
   R.band = false;
   R.placed = false;
   R.pose = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int o = o0 + k;
-  const int rel = __ldg(&b.obj_rel[o]);
-  int kind = rel & SC_REL_KIND_MASK;
-  const int ref = rel >> 8;
-  if (kind != SC_REL_FREE && (ref < 0 || ref >= k || kind > SC_REL_NEXT_TO)) {
-    // a relation must refer to an earlier object: report, sample it as free
-    if (lane == 0) latch_error(status, kDevBadRelation);
-    kind = SC_REL_FREE;
-  }
-  const float4 H = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o);
-  const float4 RP = __ldg(reinterpret_cast<const float4*>(b.obj_rel_param) + o);
-  if (kind == SC_REL_ON_TOP) {
-    const float4 u = draw_uniform4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, 0u);
-    const float4 pp = poses[pbase + ref];
-    const float4 pH = __ldg(reinterpret_cast<const float4*>(b.obj_half) + (o0 + ref));
-    const float xl = pH.x * (2.f * u.x - 1.f), yl = pH.y * (2.f * u.y - 1.f);
-    float sy, cy;
-    sincosf(pp.w, &sy, &cy);
-    R.pose = make_float4(pp.x + cy * xl - sy * yl, pp.y + sy * xl + cy * yl, pp.z + pH.z + H.z, kTwoPi * u.z);
-    R.placed = true;
-    return R;
-  }
+  const float4 H = S.H, RP = S.RP;
+  const bool on_top = S.kind == SC_REL_ON_TOP;
   const float e = RP.z * fminf(H.x, H.y);  // ratio_on_support erosion
   float4 anchor = make_float4(0.f, 0.f, 0.f, 0.f);
   float rho_sum = 0.f;
-  if (kind == SC_REL_NEXT_TO) {
-    anchor = poses[pbase + ref];
-    rho_sum = __ldg(&b.obj_half[4 * (o0 + ref) + 3]) + H.w;
+  if (S.kind == SC_REL_NEXT_TO) {
+    anchor = S.ref_pose;
+    rho_sum = S.ref_half.w + H.w;
   }
+#pragma unroll 1
   for (int a0 = 0; a0 < max_attempts && !R.placed; a0 += 32) {
     const int a = a0 + lane;
     const bool valid = a < max_attempts;
+    const float4 u = draw_uniform4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, (uint32_t)a);
+    if (on_top) {
+      // attempt 0 (lane 0's draw) places the object on the reference's top face
+      const float4 pp = S.ref_pose;
+      const float4 pH = S.ref_half;
+      const float ux = __shfl_sync(0xFFFFFFFFu, u.x, 0), uy = __shfl_sync(0xFFFFFFFFu, u.y, 0),
+                  uz = __shfl_sync(0xFFFFFFFFu, u.z, 0);
+      const float xl = pH.x * (2.f * ux - 1.f), yl = pH.y * (2.f * uy - 1.f);
+      float sy, cy;
+      sincosf(pp.w, &sy, &cy);
+      R.pose = make_float4(pp.x + cy * xl - sy * yl, pp.y + sy * xl + cy * yl, pp.z + pH.z + H.z, kTwoPi * uz);
+      R.placed = true;
+      return R;
+    }
     float x = 0.f, y = 0.f, yaw = 0.f;
     bool acc = false, bnd = false;
     if (valid) {
-      const float4 u = draw_uniform4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, (uint32_t)a);
-      if (kind == SC_REL_NEXT_TO) {
+      if (S.kind == SC_REL_NEXT_TO) {
         float sp, cp;
         sincosf(kTwoPi * u.x, &sp, &cp);
         const float r = rho_sum + RP.x + (RP.y - RP.x) * u.y;
@@ -163,6 +199,16 @@ __device__ __forceinline__ SampleResult warp_sample_object(const sc_scene_batch&
   }
   R.pose.z = sup.z + H.z;
   return R;
+}
+
+// Sample template-local object k of candidate c for try `retry` (loads the
+// object's spec, then samples it).
+__device__ __forceinline__ SampleResult warp_sample_object(const sc_scene_batch& b, const Support& sup,
+                                                          uint64_t seed, int max_attempts, int retry, int c, int k,
+                                                          int o0, const float4* poses, int64_t pbase, int* status,
+                                                          int lane) {
+  const ObjectSpec S = load_object_spec(b, o0, k, __ldg(&b.obj_rel[o0 + k]), poses, pbase, status, lane);
+  return warp_sample_spec(sup, S, seed, max_attempts, retry, c, k, lane);
 }
 
 }  // namespace sc
