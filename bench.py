@@ -24,8 +24,11 @@ Prints ONE JSON line (rank 0). `value` is verified collision-free scenes per
 second over all ranks; `e2e` is the same metric through the public C-ABI calls
 with the batch copied from pinned host memory every step and the poses and
 valid flags copied back. `roofline` is the dominant kernel's FP32-pipe
-throughput (algorithmic operations it evaluated / its CUDA-event time) against
-the B300's FP32 issue peak. `cpu_baseline` is the FP64 oracle on the host
+throughput (algorithmic operations it evaluated: pair tests after the exact
+sphere-level cull, sphere-box tests and the cull's own ball tests, over its
+CUDA-event time) against the B300's FP32 issue peak; the stage block also
+gives the throughput an exhaustive pair check would need for the same
+decisions in the same time (exhaustive_equivalent_frac). `cpu_baseline` is the FP64 oracle on the host
 cores over a bounded random sample of the same workload.
 
 --impl reference runs that oracle (as it is) as the reference arm.
@@ -53,6 +56,8 @@ import synth  # noqa: E402
 # Algorithmic FP32-pipe operations per evaluated pair ("Rooflines"):
 OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 1 FADD + 4 FFMA
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
+OPS_PER_CULL_TEST = 10     # sphere vs bounding ball: 3 FADD, FMUL + 2 FFMA, 2 FADD (limit), FMUL, FSETP
+OPS_PER_EXHAUSTIVE_PAIR = 9  # one pair of an uncalled exhaustive check (3 FADD, FMUL + 2 FFMA, FADD, FMUL, FSETP)
 OPS_PER_IK_SEED_ITER = 720  # one check + DLS step: FK 280, check 40, error 21, J 63, J J^T 147, Cholesky 50,
                             # solves 60, J^T y 42, clamp 14 (FP32-pipe operations, sincos counted once)
 L2_BYTES = 126 * 1024 * 1024
@@ -361,13 +366,16 @@ def run_ours(args, wl):
         ms_gen = sum(s["ms_stage"][0] for s in st)
         ms_ik = sum(s["ms_stage"][2] for s in st)
         ops_gen = sum(s["sphere_pairs"] for s in st) * OPS_PER_SPHERE_PAIR + \
-            sum(s["sphere_box_pairs"] for s in st) * OPS_PER_SPHERE_BOX
+            sum(s["sphere_box_pairs"] for s in st) * OPS_PER_SPHERE_BOX + \
+            sum(s["cull_tests"] for s in st) * OPS_PER_CULL_TEST
+        ops_exh = sum(s["exhaustive_pairs"] for s in st) * OPS_PER_EXHAUSTIVE_PAIR
         ops_ik = sum(s["ik_seed_iterations"] for s in st) * OPS_PER_IK_SEED_ITER
         rate_gen = ops_gen / max(ms_gen / 1e3, 1e-12)  # FP32-pipe operations per second
         rate_ik = ops_ik / max(ms_ik / 1e3, 1e-12)
         gen = {"kernel": "gen_warp_kernel (sample + collision decision)", "ms_per_step": ms_gen / len(st),
                "launches_per_step": st[0]["launches_stage"][0], "achieved": rate_gen / 1e12,
-               "frac": rate_gen / peak_ops}
+               "frac": rate_gen / peak_ops,
+               "exhaustive_equivalent_frac": ops_exh / max(ms_gen / 1e3, 1e-12) / peak_ops}
         ik = {"kernel": "reach_ik_kernel (DLS IK)", "ms_per_step": ms_ik / len(st),
               "launches_per_step": st[0]["launches_stage"][2], "achieved": rate_ik / 1e12, "frac": rate_ik / peak_ops}
         return gen, ik
@@ -412,8 +420,11 @@ def run_ours(args, wl):
         "stages": {"gen_ms_per_step": gen_rf["ms_per_step"], "ik_ms_per_step": ik_rf["ms_per_step"],
                    "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
                    "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
-                   "sphere_pairs_per_step": st0["sphere_pairs"], "ik_seed_iterations_per_step": st0["ik_seed_iterations"],
-                   "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"]},
+                   "sphere_pairs_per_step": st0["sphere_pairs"], "cull_tests_per_step": st0["cull_tests"],
+                   "exhaustive_pairs_per_step": st0["exhaustive_pairs"],
+                   "ik_seed_iterations_per_step": st0["ik_seed_iterations"],
+                   "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"],
+                   "gen_exhaustive_equivalent_frac": gen_rf["exhaustive_equivalent_frac"]},
         "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": dom["frac"], "traffic": measured_traffic(dom_file, args.workload),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "

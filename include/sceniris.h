@@ -376,7 +376,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
 
 /* Work and time of the last sc_generate call (synchronises the stream). */
 typedef struct {
-  int64_t sphere_pairs;        /* sphere pairs the collision stage evaluated */
+  int64_t sphere_pairs;        /* sphere pairs the collision stage evaluated (after the cull) */
   int64_t sphere_box_pairs;
   int64_t ik_solves;           /* targets the exact IK solved */
   int64_t gate_rejections;     /* tries the learned gate sent back without IK */
@@ -384,6 +384,9 @@ typedef struct {
   float ms_stage[3];           /* with timing on: device time of the generation-step launches,
                                   the grasp-target + gate launches, and the IK launches */
   int32_t launches_stage[3];
+  int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull */
+  int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
+                                  spheres x all spheres of the objects placed before it) */
 } sc_gen_stats;
 sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured

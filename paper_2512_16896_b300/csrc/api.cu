@@ -20,7 +20,7 @@ struct sc_ctx {
   void* scratch = nullptr;
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;
-  unsigned long long* d_stats = nullptr;  // [2]
+  unsigned long long* d_stats = nullptr;  // [7] (generation); [2] (collision)
   // grow-on-demand scratch of sc_generate (candidate lists and counters)
   void* gen_scratch = nullptr;
   size_t gen_scratch_bytes = 0;
@@ -779,7 +779,7 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   if (sc_status s = check_ctx(ctx)) return s;
   if (!out) return fail(SC_ERR_INVALID, "out is NULL");
   DeviceGuard g(ctx->device);
-  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  unsigned long long h[7] = {0, 0, 0, 0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
   if (!e) e = cudaStreamSynchronize(ctx->stream);
   if (e) return cuda_fail(e, "stats read");
@@ -789,6 +789,8 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   out->ik_solves = (int64_t)h[2];
   out->gate_rejections = (int64_t)h[3];
   out->ik_seed_iterations = (int64_t)h[4];
+  out->cull_tests = (int64_t)h[5];
+  out->exhaustive_pairs = (int64_t)h[6];
   if (ctx->timing) {
     for (int i = 0; i < ctx->timer.used; ++i) {
       float ms = 0.f;

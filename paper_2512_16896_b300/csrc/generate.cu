@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   int item = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   if (item >= n_items) return;  // no atomic traffic from warps without work
   const uint64_t seed = *g.seed;
-  unsigned long long my_pairs = 0, my_box = 0;
+  unsigned long long my_pairs = 0, my_box = 0, my_cull = 0, my_exh = 0;  // counted by lane 0
   int pend_c = 0, pend_r = kRouteNone, npend = 0;
 
   while (item < n_items) {
@@ -339,7 +339,10 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
               }
             }
           }
-          my_box += (unsigned long long)nobb * (unsigned long long)(lane < Sk ? (Sk - lane + 31) / 32 : 0);
+          if (lane == 0) {
+            my_box += (unsigned long long)nobb * (unsigned long long)Sk;
+            my_exh += (unsigned long long)Sprev * (unsigned long long)Sk;
+          }
           m = warp_min(m);
           bool alive = !(m < -kBand);
           r2 = -warp_min(-r2);
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
               if (dx * dx + dy * dy + dz * dz <= lim * lim) keepbits |= 1u << u;
             }
           }
+          if (lane == 0) my_cull += (unsigned long long)Sk * (unsigned long long)nkeep;
           int Sc = 0;  // B spheres kept
 #pragma unroll 1
           for (int q0 = 0, u = 0; q0 < Sk; q0 += 32, ++u) {
@@ -437,6 +441,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
                 if (ck[u]) astage[fill + __popc(mask & ((1u << lane) - 1u))] = cand[u];
                 fill += __popc(mask);
               }
+              if (lane == 0) my_cull += (unsigned long long)min(64, q1 - qb);
               qb += 64;
               if (qb >= q1) {
                 have_obj = false;
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
             const int n_sw = fill >= kCap ? kCap : (more ? 0 : fill);
             if (alive && n_sw > 0) {
               __syncwarp();
-              my_pairs += (unsigned long long)n_sw * (unsigned long long)Sc;
+              if (lane == 0) my_pairs += (unsigned long long)n_sw * (unsigned long long)Sc;
               sweep_block<APL>(astage, n_sw, Bs, Bb, Sc, eps, lane, m, alive);
               // move the staged overflow (at most 63 spheres) to the front
               const int over = fill - n_sw;
@@ -490,14 +495,11 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
       npend = 0;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    my_pairs += __shfl_xor_sync(0xFFFFFFFFu, my_pairs, o);
-    my_box += __shfl_xor_sync(0xFFFFFFFFu, my_box, o);
-  }
   if (lane == 0 && g.stats) {
     atomicAdd(&g.stats[0], my_pairs);
     atomicAdd(&g.stats[1], my_box);
+    atomicAdd(&g.stats[5], my_cull);
+    atomicAdd(&g.stats[6], my_exh);
   }
 }
 
@@ -683,7 +685,7 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += stride) counts[i] = (i == 0) ? n : 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counters; i += stride) counters[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x < 5 && stats) stats[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 7 && stats) stats[threadIdx.x] = 0;
 }
 
 template <int APL>

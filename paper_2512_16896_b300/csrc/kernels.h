@@ -71,7 +71,7 @@ struct GenerateLaunch {
   int32_t* tries;
   void* scratch;  // generate_scratch_bytes(batch, n_items, max_retries)
   unsigned long long* stats;  // [0] sphere pairs [1] sphere-box pairs [2] IK solves [3] gate rejections
-                              // [4] IK seed-iterations
+                              // [4] IK seed-iterations [5] cull tests [6] exhaustive pairs
   int* status;
   // reachability (arm == NULL: none)
   const sc_arm* arm;
