@@ -81,6 +81,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate_ranks(time_s, valid, e2e_s, e2e_valid, world, device):
+    """Whole-job totals over the replicas: the slowest rank's timed seconds
+    (timed region and end-to-end) and the summed valid scenes."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([time_s, valid, e2e_s, e2e_valid], dtype=torch.float64, device=device)
+    if world > 1:
+        mx = t[[0, 2]].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t[[1, 3]].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t = torch.stack([mx[0], sm[0], mx[1], sm[1]])
+    return [float(x) for x in t.cpu()]
+
+
+def replica_seed(base_seed, rank):
+    """Each rank generates an independent replica of the workload (weak scaling)."""
+    return base_seed + 1000 * rank
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -196,15 +216,21 @@ def oracle_rate(batch, seed, budget_s: float, path: str = "generate", rng_seed: 
             "scenes_per_s": n / dt, "valid_per_s": valid / dt}
 
 
+reach_desc = ("top-down grasp of the first 4 objects of every template, 7-DoF arm at the support's -x edge, "
+              "exact DLS IK (32 seeds x 100 iterations)")
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     batch = wl["make"](wl["seed"])
-    times, valids, ns = [], [], []
+    reach = args.path == "generate" and not args.no_reach
+    times, valids, ns, threads = [], [], [], 0
     for i in range(args.warmup + args.steps):
         r = oracle_rate(batch, seed=wl["seed"], budget_s=args.ref_step_s, path=args.path, rng_seed=100 + i,
-                        max_retries=args.retries, reach=args.path == "generate" and not args.no_reach)
+                        max_retries=args.retries, reach=reach)
+        threads = r["threads"]
         if i >= args.warmup:
             times.append(r["seconds"]); valids.append(r["valid"]); ns.append(r["n"])
     value = sum(valids) / sum(times)
@@ -214,9 +240,10 @@ def run_reference(args, wl):
         "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
-                   "launch": ("eager" if args.no_graph else "CUDA graph replay") if gen else "eager",
+                   "reachability": reach_desc if reach else None,
+                   "launch": f"FP64 oracle on {threads} host threads",
                    "sample_per_step": f"{ns[0]} random candidates of the workload"},
-        "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": os.cpu_count(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": threads, "kind": "oracle",
                          "sample": f"{ns[0]} random candidates per step of the {args.workload} workload"},
         "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -237,7 +264,7 @@ def run_ours(args, wl):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    seed = wl["seed"] + 1000 * rank  # independent replica per rank (weak scaling)
+    seed = replica_seed(wl["seed"], rank)
     batch = wl["make"](seed)
     ctx = sc.Context(local)
     stream = ctx.stream
@@ -343,15 +370,8 @@ def run_ours(args, wl):
             e2e_valid.append(int(h_valid.numpy().sum()))
 
     # ---- aggregate over ranks (max time, summed work)
-    total_s = sum(main["ms"]) / 1000.0
-    total_valid = sum(main["valid"])
-    stats_t = torch.tensor([total_s, total_valid, max(sum(e2e_ms), 1e-9) / 1000.0, sum(e2e_valid)],
-                           dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = stats_t[[0, 2]].clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = stats_t[[1, 3]].clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        stats_t = torch.stack([mx[0], sm[0], mx[1], sm[1]])
-    total_s, total_valid, e2e_s, e2e_valid_sum = [float(x) for x in stats_t.cpu()]
+    total_s, total_valid, e2e_s, e2e_valid_sum = aggregate_ranks(
+        sum(main["ms"]) / 1000.0, sum(main["valid"]), max(sum(e2e_ms), 1e-9) / 1000.0, sum(e2e_valid), world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -410,8 +430,7 @@ def run_ours(args, wl):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
-                   "reachability": ("top-down grasp of the first 4 objects of every template, 7-DoF arm at the "
-                                    "support's -x edge, exact DLS IK (32 seeds x 100 iterations)") if reach else None,
+                   "reachability": reach_desc if reach else None,
                    "gate": gate_info, "launch": "eager" if args.no_graph else "CUDA graph replay",
                    "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
                    "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
