@@ -62,27 +62,70 @@ struct GenStepArgs {
   int* status;
 };
 
-// Shared memory of one warp: objects 0..k (sphere offsets, poses, sin/cos of
-// yaw) and the new object's spheres in the world frame (relative to object
-// 0's position) with |c|^2 - r^2.
+// Shared memory of one warp: the candidate's objects (absolute sphere
+// offsets, poses, sin/cos of yaw, bounding-ball radii), the kept objects of
+// the current try, the new object's spheres in the world frame (relative to
+// object 0's position) with |c|^2 - r^2, and the A staging area.
 struct WarpLayout {
-  int off, pose, sc, kobj, kball, B, beta, astage, bytes;
+  int tmpl, off, pose, sc, rad, kobj, kball, B, beta, astage, bytes;
 };
 
 // max_sk: most spheres of one object in the batch (B side); apl: A spheres
 // per lane of the register block (A staging holds one block plus 64).
 __host__ __device__ inline WarpLayout make_warp_layout(int max_obj, int max_sk, int apl) {
   WarpLayout W;
-  W.off = 0;
-  W.pose = align16(4 * (max_obj + 1));
+  W.tmpl = 0;
+  W.off = 64;
+  W.pose = align16(W.off + 4 * (max_obj + 1));
   W.sc = align16(W.pose + 16 * max_obj);
-  W.kobj = align16(W.sc + 8 * max_obj);
+  W.rad = align16(W.sc + 8 * max_obj);
+  W.kobj = align16(W.rad + 4 * max_obj);
   W.kball = align16(W.kobj + 4 * max_obj);
   W.B = align16(W.kball + 16 * max_obj);
   W.beta = align16(W.B + 16 * (max_sk + kPad));
   W.astage = align16(W.beta + 4 * (max_sk + kPad));
   W.bytes = align16(W.astage + 16 * (32 * apl + 64));
   return W;
+}
+
+struct WarpState {
+  TmplInfo* tmpl; // the current candidate's template record
+  int* off;       // [max_obj + 1] absolute sphere offsets of the candidate's objects
+  float4* opose;  // [max_obj] poses of objects 0..k
+  float2* osc;    // [max_obj] sin, cos of their yaw
+  float* orad;    // [max_obj] bounding-ball radii |H|
+  int* kobj;      // kept objects of the current try
+  float4* kball;  // their balls (centre relative to object 0, radius)
+  float4* Bs;     // object k's spheres
+  float* Bb;      // |b|^2 - r^2
+  float4* astage; // A survivors
+};
+
+__device__ __forceinline__ WarpState warp_state(unsigned char* smem, const WarpLayout& WL) {
+  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * WL.bytes;
+  WarpState W;
+  W.tmpl = reinterpret_cast<TmplInfo*>(base + WL.tmpl);
+  W.off = reinterpret_cast<int*>(base + WL.off);
+  W.opose = reinterpret_cast<float4*>(base + WL.pose);
+  W.osc = reinterpret_cast<float2*>(base + WL.sc);
+  W.orad = reinterpret_cast<float*>(base + WL.rad);
+  W.kobj = reinterpret_cast<int*>(base + WL.kobj);
+  W.kball = reinterpret_cast<float4*>(base + WL.kball);
+  W.Bs = reinterpret_cast<float4*>(base + WL.B);
+  W.Bb = reinterpret_cast<float*>(base + WL.beta);
+  W.astage = reinterpret_cast<float4*>(base + WL.astage);
+  return W;
+}
+
+// Copies template t's record into the warp's slot (t < 0: a zeroed record).
+__device__ __forceinline__ const TmplInfo& load_tmpl(const TmplInfo* tinfo, int t, TmplInfo* slot, int lane) {
+  if (lane < 4) {
+    int4 v = make_int4(0, 0, 0, 0);
+    if (t >= 0) v = __ldg(reinterpret_cast<const int4*>(tinfo + t) + lane);
+    reinterpret_cast<int4*>(slot)[lane] = v;
+  }
+  __syncwarp();
+  return *slot;
 }
 
 // Asynchronous global -> shared copies (completed by cp_async_wait_all).
@@ -117,6 +160,298 @@ __device__ __forceinline__ void sweep_block(const float4* astage, int fill, cons
   sweep<APL, false, true>(A, Bs, Bb, 0, Sc, Sc, m, 0.f, eps, nullptr, nullptr, alive);
 }
 
+// Work counted by lane 0 of a warp.
+struct TryCounters {
+  unsigned long long pairs = 0, box = 0, cull = 0, exh = 0;
+};
+
+struct TryOut {
+  bool pass;  // placed and collision-free
+  bool band;  // a decision of the try lay within the band
+};
+
+// One try (Sec. IV-A, Fig. 2) of template-local object k of candidate c:
+// sample its pose (the pose is written to poses[pbase + k] whatever the
+// outcome), then decide it against the kept earlier objects and the world
+// boxes. On entry the warp state holds objects 0..k-1 (opose, osc, orad,
+// off[0..k]); with PREFETCHED, their poses, half extents (in kball) and
+// offsets are cp.async copies still in flight, completed here after the
+// sampling, and osc / orad are derived from them. On return, when the pose
+// was accepted, opose[k], osc[k] and orad[k] hold object k.
+// Broad phase (exact): every sphere of an object lies in the ball of radius
+// |H| (its box's half-diagonal) around the object's frame origin, so two
+// objects whose origins are farther apart than |H_j| + |H_k| + margin have no
+// sphere pair within the band. Sphere-level cull (exact, same argument): a B
+// sphere farther than band + margin from every kept object's ball, or an A
+// sphere that far from object k's ball, has no pair within the band.
+template <int APL, bool PREFETCHED>
+__device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& T, const WarpState& W, int c, int k,
+                                          int retry, int rel, int Sprev, int Sk, int64_t pbase, uint64_t seed,
+                                          const float4* ref_poses, int lane, TryCounters& cnt) {
+  const sc_scene_batch& b = g.b;
+  const int o0 = T.o0, s0 = T.s0, nobb = T.nobb, bx0 = T.bx0;
+  // ---- sample object k
+  Support sup;
+  sup.P.v = reinterpret_cast<const float2*>(b.poly_verts) + T.v0;
+  sup.P.n = T.nv;
+  sup.P.inv = g.edge_inv + T.v0;
+  sup.ok = T.nv >= 3 && T.nv <= kMaxPolyVerts;
+  sup.z = T.z;
+  sup.xmin = T.xmin; sup.xmax = T.xmax; sup.ymin = T.ymin; sup.ymax = T.ymax;
+  const ObjectSpec spec = load_object_spec(b, o0, k, rel, ref_poses, 0, g.status, lane);
+  SampleResult r;
+  r.placed = false;
+  r.band = true;
+  r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (sup.ok) {
+    r = warp_sample_spec(sup, spec, seed, g.max_attempts, retry, c, k, lane);
+  } else if (lane == 0) {
+    latch_error(g.status, kDevBadPolygon);
+  }
+  if (lane == 0) g.poses[pbase + k] = r.pose;
+  if (PREFETCHED) {
+    cp_async_wait_all();
+    __syncwarp();
+#pragma unroll 1
+    for (int j = lane; j < k; j += 32) {
+      const float4 p = W.opose[j], H = W.kball[j];
+      float sn, cs;
+      sincosf(p.w, &sn, &cs);
+      W.osc[j] = make_float2(sn, cs);
+      W.orad[j] = sqrtf(H.x * H.x + H.y * H.y + H.z * H.z);
+    }
+  }
+  TryOut out;
+  out.pass = false;
+  out.band = r.band;
+  if (!r.placed) return out;
+  const float4 pk = r.pose;
+  const float rk = sqrtf(spec.H.x * spec.H.x + spec.H.y * spec.H.y + spec.H.z * spec.H.z);
+  float skn, kcs;
+  sincosf(pk.w, &skn, &kcs);
+  if (lane == 0) {
+    W.opose[k] = pk;
+    W.osc[k] = make_float2(skn, kcs);
+    W.orad[k] = rk;
+  }
+  __syncwarp();
+  const float4 ref = k == 0 ? pk : W.opose[0];
+  // ---- broad phase: earlier objects whose bounding balls come near object
+  // k's; the kept ones' balls (relative to ref) go to kball
+  int nkeep = 0;
+  float a_bound = 0.f;  // bound on |a| over the kept objects' spheres
+#pragma unroll 1
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int j = j0 + lane;
+    bool keep = false;
+    float4 ball = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < k) {
+      const float4 pj = W.opose[j];
+      const float rj = W.orad[j];
+      const float dx = pj.x - pk.x, dy = pj.y - pk.y, dz = pj.z - pk.z;
+      const float lim = rj + rk + kBroadMargin;
+      keep = dx * dx + dy * dy + dz * dz <= lim * lim;
+      ball = make_float4(pj.x - ref.x, pj.y - ref.y, pj.z - ref.z, rj);
+      if (keep) a_bound = fmaxf(a_bound, sqrtf(ball.x * ball.x + ball.y * ball.y + ball.z * ball.z) + rj);
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+    __syncwarp();  // every ball input of this chunk is read before kball slots are overwritten
+    if (keep) {
+      const int slot = nkeep + __popc(mask & ((1u << lane) - 1u));
+      W.kobj[slot] = j;
+      W.kball[slot] = ball;
+    }
+    nkeep += __popc(mask);
+    __syncwarp();
+  }
+  a_bound = -warp_min(-a_bound);
+  // ---- object k's spheres (B side)
+  float r2 = 0.f;
+#pragma unroll 1
+  for (int q = lane; q < Sk + kPad; q += 32) {
+    if (q < Sk) {
+      const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
+      const float x = (pk.x - ref.x) + (kcs * l.x - skn * l.y);
+      const float y = (pk.y - ref.y) + (skn * l.x + kcs * l.y);
+      const float z = (pk.z - ref.z) + l.z;
+      const float c2 = x * x + y * y + z * z;
+      W.Bs[q] = make_float4(x, y, z, l.w);
+      W.Bb[q] = c2 - l.w * l.w;
+      r2 = fmaxf(r2, c2);
+    } else {
+      W.Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
+      W.Bb[q] = 3e12f;
+    }
+  }
+  __syncwarp();
+  float m = kFarSentinel;
+  // ---- object k vs world boxes
+#pragma unroll 1
+  for (int bi = 0; bi < nobb; ++bi) {
+    const float* o = b.obb + 12 * (bx0 + bi);
+    float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
+    const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx *= inv; qy *= inv; qz *= inv; qw *= inv;
+    // columns of R (R maps box frame to world)
+    const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
+    const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
+    const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
+    const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
+#pragma unroll 1
+    for (int q = lane; q < Sk; q += 32) {
+      const float4 w = W.Bs[q];
+      const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
+      const float px = c00 * vx + c01 * vy + c02 * vz;
+      const float py = c10 * vx + c11 * vy + c12 * vz;
+      const float pz = c20 * vx + c21 * vy + c22 * vz;
+      const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
+      const float em = fmaxf(ex, fmaxf(ey, ez));
+      if (em - w.w < kBand) {
+        const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
+        m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
+      }
+    }
+  }
+  if (lane == 0) {
+    cnt.box += (unsigned long long)nobb * (unsigned long long)Sk;
+    cnt.exh += (unsigned long long)Sprev * (unsigned long long)Sk;
+  }
+  m = warp_min(m);
+  bool alive = !(m < -kBand);
+  r2 = -warp_min(-r2);
+  // ---- B cull against the kept objects' balls, compacted in place
+  unsigned keepbits = 0;  // bit u: sphere lane + 32 u is near a kept object
+#pragma unroll 1
+  for (int jj = 0; alive && jj < nkeep; ++jj) {
+    const float4 kb = W.kball[jj];
+#pragma unroll 1
+    for (int q = lane, u = 0; q < Sk; q += 32, ++u) {
+      const float4 w = W.Bs[q];
+      const float dx = w.x - kb.x, dy = w.y - kb.y, dz = w.z - kb.z;
+      const float lim = kb.w + w.w + kBand + kBroadMargin;
+      if (dx * dx + dy * dy + dz * dz <= lim * lim) keepbits |= 1u << u;
+    }
+  }
+  if (lane == 0) cnt.cull += (unsigned long long)Sk * (unsigned long long)nkeep;
+  int Sc = 0;  // B spheres kept
+#pragma unroll 1
+  for (int q0 = 0, u = 0; q0 < Sk; q0 += 32, ++u) {
+    const int q = q0 + lane;
+    const bool keep = (keepbits >> u) & 1u;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    float bb = 0.f;
+    if (keep) {
+      w = W.Bs[q];
+      bb = W.Bb[q];
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+    __syncwarp();  // this chunk is read before it is overwritten
+    if (keep) {
+      const int pos = Sc + __popc(mask & ((1u << lane) - 1u));
+      W.Bs[pos] = w;
+      W.Bb[pos] = bb;
+    }
+    Sc += __popc(mask);
+  }
+#pragma unroll 1
+  for (int q = Sc + lane; q < Sc + kPad; q += 32) {
+    W.Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
+    W.Bb[q] = 3e12f;
+  }
+  __syncwarp();
+  // one tolerance for the whole try, from bounds on |a| and |b|
+  const float eps = 1e-5f * (fmaxf(r2, a_bound * a_bound) + 0.01f);
+  const float ckx = pk.x - ref.x, cky = pk.y - ref.y, ckz = pk.z - ref.z;
+  // ---- object k vs the kept earlier objects: A spheres are read 64 at a
+  // time per kept object, culled against object k's ball, staged in shared
+  // memory and decided 32 * APL at a time from registers (one sweep site: a
+  // full block, or the remainder once nothing is left)
+  constexpr int kCap = 32 * APL;
+  int fill = 0, jj = 0, qb = 0, q1 = 0;
+  bool have_obj = false;
+  float px = 0.f, py = 0.f, pz = 0.f;
+  float2 osj = make_float2(0.f, 1.f);  // sin, cos of the current kept object's yaw
+#pragma unroll 1
+  for (;;) {
+#pragma unroll 1
+    while (!have_obj && jj < nkeep) {
+      const int j = W.kobj[jj];
+      qb = W.off[j] - s0;
+      q1 = W.off[j + 1] - s0;
+      const float4 p = W.opose[j];
+      osj = W.osc[j];
+      px = p.x - ref.x; py = p.y - ref.y; pz = p.z - ref.z;
+      have_obj = qb < q1;
+      if (!have_obj) ++jj;
+    }
+    const bool more = Sc > 0 && have_obj;
+    if (alive && more && fill < kCap) {
+      float4 cand[2];
+      bool ck[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = qb + u * 32 + lane;
+        cand[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ck[u] = false;
+        if (q < q1) {
+          const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
+          cand[u].x = px + (osj.y * l.x - osj.x * l.y);
+          cand[u].y = py + (osj.x * l.x + osj.y * l.y);
+          cand[u].z = pz + l.z;
+          cand[u].w = l.w;
+          const float dx = cand[u].x - ckx, dy = cand[u].y - cky, dz = cand[u].z - ckz;
+          const float lim = rk + l.w + kBand + kBroadMargin;
+          ck[u] = dx * dx + dy * dy + dz * dz <= lim * lim;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, ck[u]);
+        if (ck[u]) W.astage[fill + __popc(mask & ((1u << lane) - 1u))] = cand[u];
+        fill += __popc(mask);
+      }
+      if (lane == 0) cnt.cull += (unsigned long long)min(64, q1 - qb);
+      qb += 64;
+      if (qb >= q1) {
+        have_obj = false;
+        ++jj;
+      }
+    }
+    const int n_sw = fill >= kCap ? kCap : (more ? 0 : fill);
+    if (alive && n_sw > 0) {
+      __syncwarp();
+      if (lane == 0) cnt.pairs += (unsigned long long)n_sw * (unsigned long long)Sc;
+      sweep_block<APL>(W.astage, n_sw, W.Bs, W.Bb, Sc, eps, lane, m, alive);
+      // move the staged overflow (at most 63 spheres) to the front
+      const int over = fill - n_sw;
+      __syncwarp();
+      const float4 v0 = lane < over ? W.astage[n_sw + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v1 = lane + 32 < over ? W.astage[n_sw + 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+      if (lane < over) W.astage[lane] = v0;
+      if (lane + 32 < over) W.astage[lane + 32] = v1;
+      fill = over;
+    }
+    if (!alive || (!more && fill == 0)) break;
+  }
+  __syncwarp();
+  out.pass = alive && !(m < 0.f);
+  out.band = out.band || fabsf(m) <= kBand;
+  return out;
+}
+
+// Position of the candidate in the template and the checks every launch
+// makes before working on object k (error code, 0 when fine).
+__device__ __forceinline__ int check_object(const GenStepArgs& g, const TmplInfo& T, int t, int k, int Sprev,
+                                            int Sk) {
+  const sc_scene_batch& b = g.b;
+  return t < 0 ? kDevBadTemplate
+         : (k >= T.nt || T.nt > b.max_obj || T.nt > kMaxObj) ? kDevTooManyObjects
+         : (Sk > g.max_sk || Sprev + Sk > b.max_sph) ? kDevTooManySpheres
+         : (T.nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
+}
+
 // Routing of a finished try (warp-uniform).
 enum Route : int { kRouteNone = 0, kRouteReach = 1, kRouteNext = 2, kRouteRetry = 3 };
 
@@ -138,40 +473,36 @@ __device__ __forceinline__ void flush_routes(const GenStepArgs& g, int pend_c, i
   }
 }
 
-// One warp per candidate: sample object k, then decide whether any sphere of
-// object k is closer than the band to a sphere of objects 0..k-1 (A side,
-// moved into registers 32*APL at a time) or to a world box.
-// Broad phase (exact): every sphere of an object lies in the ball of radius
-// |H| (its box's half-diagonal) around the object's frame origin, so two
-// objects whose origins are farther apart than |H_j| + |H_k| + margin have no
-// sphere pair within the band; only the other objects' spheres are streamed.
-// Work distribution: warp w takes item w first, then items claimed from the
-// launch's counter (the claim for the next item is issued before the current
-// one is processed, so its latency overlaps the work); routed candidates are
-// buffered per warp and appended 32 at a time.
+__device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCounters& cnt, int lane) {
+  if (lane == 0 && g.stats) {
+    atomicAdd(&g.stats[0], cnt.pairs);
+    atomicAdd(&g.stats[1], cnt.box);
+    atomicAdd(&g.stats[5], cnt.cull);
+    atomicAdd(&g.stats[6], cnt.exh);
+  }
+}
+
+// One launch per (object k, try r) for the objects that carry reachability
+// (the gate and IK stages run between these launches): each warp takes one
+// listed candidate at a time and makes one try. Work distribution: warp w
+// takes item w first, then items claimed from the launch's counter (the
+// claim for the next item is issued before the current one is processed);
+// routed candidates are buffered per warp and appended 32 at a time.
 template <int APL>
 __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
   const WarpLayout WL = make_warp_layout(b.max_obj, g.max_sk, APL);
+  const WarpState W = warp_state(smem, WL);
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
-  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * WL.bytes;
-  int* off = reinterpret_cast<int*>(base + WL.off);
-  float4* opose = reinterpret_cast<float4*>(base + WL.pose);
-  float2* osc = reinterpret_cast<float2*>(base + WL.sc);
-  int* kobj = reinterpret_cast<int*>(base + WL.kobj);
-  float4* kball = reinterpret_cast<float4*>(base + WL.kball);
-  float4* Bs = reinterpret_cast<float4*>(base + WL.B);
-  float* Bb = reinterpret_cast<float*>(base + WL.beta);
-  float4* astage = reinterpret_cast<float4*>(base + WL.astage);
   const int n_items = *(volatile const int*)g.n_in;
   const int k = g.k;
   const int warps_total = gridDim.x * warps_per_block;
   int item = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   if (item >= n_items) return;  // no atomic traffic from warps without work
   const uint64_t seed = *g.seed;
-  unsigned long long my_pairs = 0, my_box = 0, my_cull = 0, my_exh = 0;  // counted by lane 0
+  TryCounters cnt;
   int pend_c = 0, pend_r = kRouteNone, npend = 0;
 
   while (item < n_items) {
@@ -179,17 +510,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
     if (lane == 0) next = warps_total + (int)atomicAdd(g.counter, 1u);
     const int c = __ldg(&g.list_in[item]);
     const int t = (c >= 0 && c < b.n_cand) ? __ldg(&g.cand_t[c]) : -1;
-    TmplInfo T = {};
-    if (t >= 0) {
-      const int4* src = reinterpret_cast<const int4*>(g.tinfo + t);
-      const int4 q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2), q3 = __ldg(src + 3);
-      T.o0 = q0.x; T.nt = q0.y; T.s0 = q0.z; T.bx0 = q0.w;
-      T.nobb = q1.x; T.v0 = q1.y; T.nv = q1.z; T.cand0 = q1.w;
-      T.pose0 = (long long)(((unsigned long long)(unsigned)q2.y << 32) | (unsigned)q2.x);
-      T.z = __int_as_float(q2.z);
-      T.xmin = __int_as_float(q3.x); T.xmax = __int_as_float(q3.y);
-      T.ymin = __int_as_float(q3.z); T.ymax = __int_as_float(q3.w);
-    }
+    const TmplInfo& T = load_tmpl(g.tinfo, t, W.tmpl, lane);
     const int o0 = T.o0, nt = T.nt;
     int Sprev = 0, Sk = 0, rel = 0;
     if (t >= 0 && k < nt) {
@@ -197,10 +518,7 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
       Sk = __ldg(&b.obj_sph_off[o0 + k + 1]) - T.s0 - Sprev;
       rel = __ldg(&b.obj_rel[o0 + k]);
     }
-    const int err = t < 0 ? kDevBadTemplate
-                    : (k >= nt || nt > b.max_obj || nt > kMaxObj) ? kDevTooManyObjects
-                    : (Sk > g.max_sk || Sprev + Sk > b.max_sph) ? kDevTooManySpheres
-                    : (T.nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
+    const int err = check_object(g, T, t, k, Sprev, Sk);
     int route = kRouteNone;
     if (err != kDevOk) {
       if (lane == 0) {
@@ -208,277 +526,29 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
         if (t >= 0) g.band[c] = 1;
       }
     } else {
-      const int s0 = T.s0, nobb = T.nobb, bx0 = T.bx0;
       const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * nt;
-      // ---- sample object k
-      Support sup;
-      sup.P.v = reinterpret_cast<const float2*>(b.poly_verts) + T.v0;
-      sup.P.n = T.nv;
-      sup.P.inv = g.edge_inv + T.v0;
-      sup.ok = T.nv >= 3 && T.nv <= kMaxPolyVerts;
-      sup.z = T.z;
-      sup.xmin = T.xmin; sup.xmax = T.xmax; sup.ymin = T.ymin; sup.ymax = T.ymax;
-      const ObjectSpec spec = load_object_spec(b, o0, k, rel, g.poses, pbase, g.status, lane);
-      // Earlier objects' poses, half extents (into the kept-ball slots, which
-      // the broad phase overwrites after reading) and sphere offsets are
-      // copied to shared memory asynchronously while object k is sampled.
+      // earlier objects' poses, half extents (into the kept-ball slots) and
+      // sphere offsets, copied while object k is sampled
 #pragma unroll 1
       for (int j = lane; j < k; j += 32) {
-        cp_async16(opose + j, g.poses + pbase + j);
-        cp_async16(kball + j, reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
+        cp_async16(W.opose + j, g.poses + pbase + j);
+        cp_async16(W.kball + j, reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
       }
 #pragma unroll 1
-      for (int j = lane; j <= k; j += 32) cp_async4(off + j, b.obj_sph_off + o0 + j);
+      for (int j = lane; j <= k + 1; j += 32) cp_async4(W.off + j, b.obj_sph_off + o0 + j);
       cp_async_commit();
-      SampleResult r;
-      r.placed = false;
-      r.band = true;
-      r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (sup.ok) {
-        r = warp_sample_spec(sup, spec, seed, g.max_attempts, g.retry, c, k, lane);
-      } else if (lane == 0) {
-        latch_error(g.status, kDevBadPolygon);
-      }
-      if (lane == 0) g.poses[pbase + k] = r.pose;
-      cp_async_wait_all();
-      __syncwarp();
-      bool pass = false, bnd = r.band;
-      if (r.placed) {
-        // ---- objects 0..k: yaw sin/cos (off[] holds absolute sphere offsets)
-#pragma unroll 1
-        for (int j = lane; j <= k; j += 32) {
-          const float4 p = (j == k) ? r.pose : opose[j];
-          float sn, cs;
-          sincosf(p.w, &sn, &cs);
-          if (j == k) opose[k] = p;
-          osc[j] = make_float2(sn, cs);
-        }
-        __syncwarp();
-        const float4 ref = opose[0];
-        // ---- broad phase: earlier objects whose bounding balls come near
-        // object k's; the kept ones' balls (relative to ref) go to kball
-        int nkeep = 0;
-        float a_bound = 0.f;  // bound on |a| over the kept objects' spheres
-        const float4 pk = opose[k];
-        const float4 Hk = spec.H;
-        const float rk = sqrtf(Hk.x * Hk.x + Hk.y * Hk.y + Hk.z * Hk.z);
-#pragma unroll 1
-        for (int j0 = 0; j0 < k; j0 += 32) {
-          const int j = j0 + lane;
-          bool keep = false;
-          float4 ball = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j < k) {
-            const float4 pj = opose[j];
-            const float4 Hj = kball[j];
-            const float rj = sqrtf(Hj.x * Hj.x + Hj.y * Hj.y + Hj.z * Hj.z);
-            const float dx = pj.x - pk.x, dy = pj.y - pk.y, dz = pj.z - pk.z;
-            const float lim = rj + rk + kBroadMargin;
-            keep = dx * dx + dy * dy + dz * dz <= lim * lim;
-            ball = make_float4(pj.x - ref.x, pj.y - ref.y, pj.z - ref.z, rj);
-            if (keep) a_bound = fmaxf(a_bound, sqrtf(ball.x * ball.x + ball.y * ball.y + ball.z * ball.z) + rj);
-          }
-          const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
-          __syncwarp();  // every half extent of this chunk is read before slots are overwritten
-          if (keep) {
-            const int slot = nkeep + __popc(mask & ((1u << lane) - 1u));
-            kobj[slot] = j;
-            kball[slot] = ball;
-          }
-          nkeep += __popc(mask);
-          __syncwarp();
-        }
-        a_bound = -warp_min(-a_bound);
-        // ---- object k's spheres (B side)
-        {
-          const float4 p = opose[k];
-          const float2 sc2 = osc[k];
-          float r2 = 0.f;
-#pragma unroll 1
-          for (int q = lane; q < Sk + kPad; q += 32) {
-            if (q < Sk) {
-              const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
-              const float x = (p.x - ref.x) + (sc2.y * l.x - sc2.x * l.y);
-              const float y = (p.y - ref.y) + (sc2.x * l.x + sc2.y * l.y);
-              const float z = (p.z - ref.z) + l.z;
-              const float c2 = x * x + y * y + z * z;
-              Bs[q] = make_float4(x, y, z, l.w);
-              Bb[q] = c2 - l.w * l.w;
-              r2 = fmaxf(r2, c2);
-            } else {
-              Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
-              Bb[q] = 3e12f;
-            }
-          }
-          __syncwarp();
-          float m = kFarSentinel;
-          // ---- object k vs world boxes
-#pragma unroll 1
-          for (int bi = 0; bi < nobb; ++bi) {
-            const float* o = b.obb + 12 * (bx0 + bi);
-            float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
-            const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
-            qx *= inv; qy *= inv; qz *= inv; qw *= inv;
-            // columns of R (R maps box frame to world)
-            const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
-            const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
-            const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
-            const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
-            const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
-#pragma unroll 1
-            for (int q = lane; q < Sk; q += 32) {
-              const float4 w = Bs[q];
-              const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
-              const float px = c00 * vx + c01 * vy + c02 * vz;
-              const float py = c10 * vx + c11 * vy + c12 * vz;
-              const float pz = c20 * vx + c21 * vy + c22 * vz;
-              const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
-              const float em = fmaxf(ex, fmaxf(ey, ez));
-              if (em - w.w < kBand) {
-                const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
-                m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
-              }
-            }
-          }
-          if (lane == 0) {
-            my_box += (unsigned long long)nobb * (unsigned long long)Sk;
-            my_exh += (unsigned long long)Sprev * (unsigned long long)Sk;
-          }
-          m = warp_min(m);
-          bool alive = !(m < -kBand);
-          r2 = -warp_min(-r2);
-          // ---- sphere-level cull (exact): every sphere lies in its object's
-          // bounding ball, so a B sphere farther than band + margin from every
-          // kept object's ball, or an A sphere that far from object k's ball,
-          // has no pair within the band. B is compacted in place, A into the
-          // register block; decisions are unchanged.
-          unsigned keepbits = 0;  // bit u: sphere lane + 32 u is near a kept object
-#pragma unroll 1
-          for (int jj = 0; alive && jj < nkeep; ++jj) {
-            const float4 kb = kball[jj];
-#pragma unroll 1
-            for (int q = lane, u = 0; q < Sk; q += 32, ++u) {
-              const float4 w = Bs[q];
-              const float dx = w.x - kb.x, dy = w.y - kb.y, dz = w.z - kb.z;
-              const float lim = kb.w + w.w + kBand + kBroadMargin;
-              if (dx * dx + dy * dy + dz * dz <= lim * lim) keepbits |= 1u << u;
-            }
-          }
-          if (lane == 0) my_cull += (unsigned long long)Sk * (unsigned long long)nkeep;
-          int Sc = 0;  // B spheres kept
-#pragma unroll 1
-          for (int q0 = 0, u = 0; q0 < Sk; q0 += 32, ++u) {
-            const int q = q0 + lane;
-            const bool keep = (keepbits >> u) & 1u;
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-            float bb = 0.f;
-            if (keep) {
-              w = Bs[q];
-              bb = Bb[q];
-            }
-            const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
-            __syncwarp();  // this chunk is read before it is overwritten
-            if (keep) {
-              const int pos = Sc + __popc(mask & ((1u << lane) - 1u));
-              Bs[pos] = w;
-              Bb[pos] = bb;
-            }
-            Sc += __popc(mask);
-          }
-#pragma unroll 1
-          for (int q = Sc + lane; q < Sc + kPad; q += 32) {
-            Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
-            Bb[q] = 3e12f;
-          }
-          __syncwarp();
-          // one tolerance for the whole try, from bounds on |a| and |b|
-          const float eps = 1e-5f * (fmaxf(r2, a_bound * a_bound) + 0.01f);
-          const float ckx = pk.x - ref.x, cky = pk.y - ref.y, ckz = pk.z - ref.z;
-          // ---- object k vs the kept earlier objects: A spheres are read 64 at
-          // a time per kept object, culled against object k's ball, staged in
-          // shared memory and decided 32 * APL at a time from registers (one
-          // sweep site: a full block, or the remainder once nothing is left)
-          constexpr int kCap = 32 * APL;
-          int fill = 0, jj = 0, qb = 0, q1 = 0;
-          bool have_obj = false;
-          float px = 0.f, py = 0.f, pz = 0.f;
-          float2 osj = make_float2(0.f, 1.f);  // sin, cos of the current kept object's yaw
-#pragma unroll 1
-          for (;;) {
-#pragma unroll 1
-            while (!have_obj && jj < nkeep) {
-              const int j = kobj[jj];
-              qb = off[j] - s0;
-              q1 = off[j + 1] - s0;
-              const float4 p = opose[j];
-              osj = osc[j];
-              px = p.x - ref.x; py = p.y - ref.y; pz = p.z - ref.z;
-              have_obj = qb < q1;
-              if (!have_obj) ++jj;
-            }
-            const bool more = Sc > 0 && have_obj;
-            if (alive && more && fill < kCap) {
-              float4 cand[2];
-              bool ck[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int q = qb + u * 32 + lane;
-                cand[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                ck[u] = false;
-                if (q < q1) {
-                  const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + q);
-                  cand[u].x = px + (osj.y * l.x - osj.x * l.y);
-                  cand[u].y = py + (osj.x * l.x + osj.y * l.y);
-                  cand[u].z = pz + l.z;
-                  cand[u].w = l.w;
-                  const float dx = cand[u].x - ckx, dy = cand[u].y - cky, dz = cand[u].z - ckz;
-                  const float lim = rk + l.w + kBand + kBroadMargin;
-                  ck[u] = dx * dx + dy * dy + dz * dz <= lim * lim;
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const unsigned mask = __ballot_sync(0xFFFFFFFFu, ck[u]);
-                if (ck[u]) astage[fill + __popc(mask & ((1u << lane) - 1u))] = cand[u];
-                fill += __popc(mask);
-              }
-              if (lane == 0) my_cull += (unsigned long long)min(64, q1 - qb);
-              qb += 64;
-              if (qb >= q1) {
-                have_obj = false;
-                ++jj;
-              }
-            }
-            const int n_sw = fill >= kCap ? kCap : (more ? 0 : fill);
-            if (alive && n_sw > 0) {
-              __syncwarp();
-              if (lane == 0) my_pairs += (unsigned long long)n_sw * (unsigned long long)Sc;
-              sweep_block<APL>(astage, n_sw, Bs, Bb, Sc, eps, lane, m, alive);
-              // move the staged overflow (at most 63 spheres) to the front
-              const int over = fill - n_sw;
-              __syncwarp();
-              const float4 v0 = lane < over ? astage[n_sw + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-              const float4 v1 = lane + 32 < over ? astage[n_sw + 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-              __syncwarp();
-              if (lane < over) astage[lane] = v0;
-              if (lane + 32 < over) astage[lane + 32] = v1;
-              fill = over;
-            }
-            if (!alive || (!more && fill == 0)) break;
-          }
-          pass = alive && !(m < 0.f);
-          bnd = bnd || fabsf(m) <= kBand;
-        }
-      }
-      if (pass) {
+      const TryOut res =
+          gen_try<APL, true>(g, T, W, c, k, g.retry, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
+      if (res.pass) {
         if (g.list_reach && (rel & SC_REL_REACH)) route = kRouteReach;
         else if (k + 1 < nt) route = kRouteNext;
       } else if (g.retry < g.max_retries) {
         route = kRouteRetry;
       }
       if (lane == 0) {
-        if (bnd) g.band[c] = 1;
+        if (res.band) g.band[c] = 1;
         atomicAdd(&g.tries[c], 1);
-        if (pass && route == kRouteNone) g.valid[c] = 1;  // object k was the last one
+        if (res.pass && route == kRouteNone) g.valid[c] = 1;  // object k was the last one
       }
     }
     if (route != kRouteNone) {
@@ -495,12 +565,100 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
       npend = 0;
     }
   }
-  if (lane == 0 && g.stats) {
-    atomicAdd(&g.stats[0], my_pairs);
-    atomicAdd(&g.stats[1], my_box);
-    atomicAdd(&g.stats[5], my_cull);
-    atomicAdd(&g.stats[6], my_exh);
+  add_counters(g, cnt, lane);
+}
+
+// The objects after the reachability stage (all objects when there is none):
+// one warp runs a candidate's whole remaining placement loop (every object,
+// every try) with the candidate's placed objects kept in its shared memory.
+// Candidates are taken in the caller's order (heaviest first, candidates of
+// a template together, so concurrent warps share the template's spheres in
+// the caches), skipping those not alive at object k_begin.
+struct ChainArgs {
+  const int32_t* order;  // candidate order (NULL: 0..n-1)
+  int n;
+  int k_begin;
+  const uint8_t* alive;  // [n_cand] alive at object k_begin
+  unsigned int* counter;
+};
+
+template <int APL>
+__global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainArgs ca) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const sc_scene_batch& b = g.b;
+  const WarpLayout WL = make_warp_layout(b.max_obj, g.max_sk, APL);
+  const WarpState W = warp_state(smem, WL);
+  const int lane = threadIdx.x & 31;
+  const int warps_per_block = blockDim.x >> 5;
+  const int warps_total = gridDim.x * warps_per_block;
+  int item = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+  if (item >= ca.n) return;
+  const uint64_t seed = *g.seed;
+  TryCounters cnt;
+  while (item < ca.n) {
+    int next = 0;
+    if (lane == 0) next = warps_total + (int)atomicAdd(ca.counter, 1u);
+    const int c = ca.order ? __ldg(&ca.order[item]) : item;
+    const bool live = c >= 0 && c < b.n_cand && __ldg(&ca.alive[c]);
+    const int t = live ? __ldg(&g.cand_t[c]) : -1;
+    if (t >= 0) {
+      const TmplInfo& T = load_tmpl(g.tinfo, t, W.tmpl, lane);
+      const int o0 = T.o0, nt = T.nt;
+      const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * nt;
+      // objects placed before k_begin (by the per-try launches) and the
+      // sphere offsets of all objects
+      const int k0 = min(ca.k_begin, nt);
+#pragma unroll 1
+      for (int j = lane; j < k0; j += 32) {
+        const float4 p = g.poses[pbase + j];
+        const float4 H = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
+        float sn, cs;
+        sincosf(p.w, &sn, &cs);
+        W.opose[j] = p;
+        W.osc[j] = make_float2(sn, cs);
+        W.orad[j] = sqrtf(H.x * H.x + H.y * H.y + H.z * H.z);
+      }
+      const int n_off = min(nt, b.max_obj) + 1;
+#pragma unroll 1
+      for (int j = lane; j < n_off; j += 32) W.off[j] = __ldg(&b.obj_sph_off[o0 + j]);
+      __syncwarp();
+      int ntries = 0;
+      bool band = false, dead = false;
+#pragma unroll 1
+      for (int k = k0; k < nt && !dead; ++k) {
+        const int Sprev = W.off[k] - T.s0;
+        const int Sk = W.off[k + 1] - W.off[k];
+        const int err = check_object(g, T, t, k, Sprev, Sk);
+        if (err != kDevOk) {
+          if (lane == 0) latch_error(g.status, err);
+          band = true;
+          dead = true;
+          break;
+        }
+        const int rel = __ldg(&b.obj_rel[o0 + k]);
+        bool placed = false;
+#pragma unroll 1
+        for (int r = 0; r <= g.max_retries && !placed; ++r) {
+          const TryOut res =
+              gen_try<APL, false>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
+          ++ntries;
+          band = band || res.band;
+          placed = res.pass;
+        }
+        dead = !placed;
+      }
+      if (lane == 0) {
+        g.tries[c] += ntries;
+        if (band) g.band[c] = 1;
+        if (!dead) g.valid[c] = 1;
+      }
+    } else if (live && lane == 0) {
+      latch_error(g.status, kDevBadTemplate);
+    }
+    __syncwarp();
+    item = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
+  add_counters(g, cnt, lane);
 }
 
 // ---- reachability stage (Sec. IV-E): the collision-free tries of
@@ -663,9 +821,12 @@ __global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* t
 
 // First list = the caller's order (or 0..n-1); outputs of the listed
 // candidates cleared, their poses set to NaN until placed.
+// alive: 1 for every listed candidate when the chained kernel starts at
+// object 0, else 0 (set from the list of object k_begin later).
 __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, int32_t* list0, int* counts,
                                 int n_counts, unsigned int* counters, int n_counters, float4* poses, uint8_t* valid,
-                                uint8_t* band, int32_t* tries, unsigned long long* stats, int* status) {
+                                uint8_t* band, int32_t* tries, unsigned long long* stats, int* status,
+                                uint8_t* alive, uint8_t alive_value) {
   const int stride = gridDim.x * blockDim.x;
   const float nan = __int_as_float(0x7FC00000);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -679,6 +840,7 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
     valid[c] = 0;
     band[c] = 0;
     tries[c] = 0;
+    alive[c] = alive_value;
     const int o0 = b.tmpl_obj_off[t], nt = b.tmpl_obj_off[t + 1] - o0;
     const int64_t pbase = b.tmpl_pose_off[t] + (int64_t)(c - b.cand_tmpl_off[t]) * nt;
     for (int k = 0; k < nt; ++k) poses[pbase + k] = make_float4(nan, nan, nan, nan);
@@ -688,10 +850,18 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   if (blockIdx.x == 0 && threadIdx.x < 7 && stats) stats[threadIdx.x] = 0;
 }
 
+// Candidates listed for object k_begin are alive for the chained kernel.
+__global__ void mark_alive_kernel(const int32_t* list, const int* n_dev, uint8_t* alive) {
+  const int n = *(volatile const int*)n_dev;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alive[list[i]] = 1;
+}
+
 template <int APL>
 cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int num_sms, int* grid) {
   auto kern = gen_warp_kernel<APL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gen_chain_kernel<APL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -704,6 +874,11 @@ cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int n
 template <int APL>
 void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaStream_t s) {
   gen_warp_kernel<APL><<<grid, threads, smem, s>>>(g);
+}
+
+template <int APL>
+void launch_chain(const GenStepArgs& g, const ChainArgs& ca, int grid, int threads, size_t smem, cudaStream_t s) {
+  gen_chain_kernel<APL><<<grid, threads, smem, s>>>(g, ca);
 }
 
 }  // namespace
@@ -723,7 +898,7 @@ cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host
 // (candidate templates, TmplInfo records, inverse edge lengths), then the
 // seed scalar.
 struct GenScratch {
-  size_t lists, counts, counters, cand_t, tinfo, edge_inv, seed, total;
+  size_t lists, counts, counters, cand_t, tinfo, edge_inv, alive, seed, total;
 };
 
 static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int max_retries) {
@@ -733,11 +908,12 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   GenScratch L;
   L.lists = 0;
   L.counts = up(L.lists + 6 * n * sizeof(int32_t) + 13 * n * sizeof(float));
-  L.counters = L.counts + ((K + 1) + 3 * K * R1) * sizeof(int);
-  L.cand_t = up(L.counters + K * R1 * sizeof(unsigned int));
+  L.counters = L.counts + ((K + 1) + 3 * K * R1) * sizeof(int);  // [K][R+1] + 1 (chained kernel)
+  L.cand_t = up(L.counters + (K * R1 + 1) * sizeof(unsigned int));
   L.tinfo = up(L.cand_t + (size_t)b.n_cand * sizeof(int32_t));
   L.edge_inv = up(L.tinfo + (size_t)b.n_templates * sizeof(TmplInfo));
-  L.seed = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));  // the 8-byte seed on a 256-byte boundary
+  L.alive = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));
+  L.seed = up(L.alive + (size_t)b.n_cand);  // the 8-byte seed on a 256-byte boundary
   L.total = L.seed + 256;
   return L;
 }
@@ -776,11 +952,16 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int* cnt_reach = cnt_retry + K * (R + 1);
   int* cnt_ik = cnt_reach + K * (R + 1);
   unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
-  const int n_counters = K * (R + 1);
+  const int n_counters = K * (R + 1) + 1;  // the last one is the chained kernel's
   int32_t* cand_t = reinterpret_cast<int32_t*>(sb + SL.cand_t);
   TmplInfo* tinfo = reinterpret_cast<TmplInfo*>(sb + SL.tinfo);
   float* edge_inv = reinterpret_cast<float*>(sb + SL.edge_inv);
+  uint8_t* alive = reinterpret_cast<uint8_t*>(sb + SL.alive);
   const unsigned long long* seed_dev = a.seed_dev;
+  const bool reach = a.arm != nullptr;
+  // objects [0, k_begin) carry reachability: one launch per (object, try)
+  // with the gate and IK between; the rest run in one chained launch
+  const int k_begin = reach ? (a.reach_objects < K ? a.reach_objects : K) : 0;
 
   int grid = 0;
   cudaError_t e;
@@ -796,7 +977,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     if (blocks < 1) blocks = 1;
     gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, L[0], counts, n_counts, counters, n_counters,
                                            reinterpret_cast<float4*>(a.poses), a.valid, a.band, a.tries, a.stats,
-                                           a.status);
+                                           a.status, alive, (uint8_t)(k_begin == 0 ? 1 : 0));
     int tb = ((b.n_cand > b.n_templates ? b.n_cand : b.n_templates) + 255) / 256;
     tb = tb < num_sms * 4 ? tb : num_sms * 4;
     gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv);
@@ -820,7 +1001,6 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.status = a.status;
   ReachArgs ra;
   std::memset(&ra, 0, sizeof(ra));
-  const bool reach = a.arm != nullptr;
   if (reach) {
     ra.b = b;
     ra.max_retries = R;
@@ -842,7 +1022,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int small_blocks = (n + 255) / 256;
   small_blocks = small_blocks < num_sms * 4 ? small_blocks : num_sms * 4;
   if (small_blocks < 1) small_blocks = 1;
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < k_begin; ++k) {
     g.k = k;
     g.list_next = L[(k + 1) & 1];
     g.n_next = cnt_list + k + 1;
@@ -888,6 +1068,25 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       if (a.timer) a.timer->end(s);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+  }
+  // ---- objects [k_begin, max_obj): one chained launch
+  if (k_begin < K) {
+    if (a.timer) a.timer->begin(0, s);
+    if (k_begin > 0) mark_alive_kernel<<<small_blocks, 256, 0, s>>>(L[k_begin & 1], cnt_list + k_begin, alive);
+    ChainArgs ca;
+    ca.order = a.order;
+    ca.n = n;
+    ca.k_begin = k_begin;
+    ca.alive = alive;
+    ca.counter = counters + K * (R + 1);
+    g.k = k_begin;
+    switch (cfg.a_per_lane) {
+      case 1: launch_chain<1>(g, ca, grid, cfg.threads, smem, s); break;
+      case 2: launch_chain<2>(g, ca, grid, cfg.threads, smem, s); break;
+      default: launch_chain<4>(g, ca, grid, cfg.threads, smem, s); break;
+    }
+    if (a.timer) a.timer->end(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
