@@ -100,43 +100,40 @@ __device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Tar
     e[4] += 0.5f * (rz * sx - rx * sz);
     e[5] += 0.5f * (rx * sy - ry * sx);
   }
-  float J[6][7];
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    const float ux = t[0] - p[i][0], uy = t[1] - p[i][1], uz = t[2] - p[i][2];
-    J[0][i] = z[i][1] * uz - z[i][2] * uy;
-    J[1][i] = z[i][2] * ux - z[i][0] * uz;
-    J[2][i] = z[i][0] * uy - z[i][1] * ux;
-    J[3][i] = z[i][0];
-    J[4][i] = z[i][1];
-    J[5][i] = z[i][2];
-  }
-  // A = J J^T + lambda^2 I, Cholesky A = L L^T (lower, in place)
+  // A = J J^T + lambda^2 I accumulated column by column (column i of J is
+  // j_i = (z_i x (t - p_i), z_i)); J itself is not kept, it is rebuilt for
+  // J^T y below, which keeps the register footprint small.
   float L[6][6];
 #pragma unroll
   for (int r = 0; r < 6; ++r)
 #pragma unroll
-    for (int c = 0; c <= r; ++c) {
-      float acc = (r == c) ? lambda2 : 0.f;
+    for (int c = 0; c <= r; ++c) L[r][c] = (r == c) ? lambda2 : 0.f;
 #pragma unroll
-      for (int i = 0; i < 7; ++i) acc = fmaf(J[r][i], J[c][i], acc);
-      L[r][c] = acc;
-    }
+  for (int i = 0; i < 7; ++i) {
+    const float ux = t[0] - p[i][0], uy = t[1] - p[i][1], uz = t[2] - p[i][2];
+    const float j[6] = {z[i][1] * uz - z[i][2] * uy, z[i][2] * ux - z[i][0] * uz, z[i][0] * uy - z[i][1] * ux,
+                        z[i][0], z[i][1], z[i][2]};
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) L[r][c] = fmaf(j[r], j[c], L[r][c]);
+  }
+  // Cholesky A = L L^T (lower, in place); 1 / L_jj from one reciprocal square root
   float inv_diag[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    float d = L[j][j];
+  for (int jc = 0; jc < 6; ++jc) {
+    float d = L[jc][jc];
 #pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    const float ljj = sqrtf(d);
-    inv_diag[j] = 1.f / ljj;
-    L[j][j] = ljj;
+    for (int k = 0; k < jc; ++k) d -= L[jc][k] * L[jc][k];
+    const float inv = rsqrtf(d);
+    inv_diag[jc] = inv;
+    L[jc][jc] = d * inv;
 #pragma unroll
-    for (int r = j + 1; r < 6; ++r) {
-      float v = L[r][j];
+    for (int r = jc + 1; r < 6; ++r) {
+      float v = L[r][jc];
 #pragma unroll
-      for (int k = 0; k < j; ++k) v -= L[r][k] * L[j][k];
-      L[r][j] = v * inv_diag[j];
+      for (int k = 0; k < jc; ++k) v -= L[r][k] * L[jc][k];
+      L[r][jc] = v * inv;
     }
   }
   float y[6];
@@ -155,10 +152,14 @@ __device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Tar
     y[r] = v * inv_diag[r];
   }
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    float dq = 0.f;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) dq = fmaf(J[r][i], y[r], dq);
+  for (int i = 0; i < 7; ++i) {  // dq = J^T y
+    const float ux = t[0] - p[i][0], uy = t[1] - p[i][1], uz = t[2] - p[i][2];
+    float dq = (z[i][1] * uz - z[i][2] * uy) * y[0];
+    dq = fmaf(z[i][2] * ux - z[i][0] * uz, y[1], dq);
+    dq = fmaf(z[i][0] * uy - z[i][1] * ux, y[2], dq);
+    dq = fmaf(z[i][0], y[3], dq);
+    dq = fmaf(z[i][1], y[4], dq);
+    dq = fmaf(z[i][2], y[5], dq);
     q[i] = fminf(fmaxf(q[i] + dq, A.qmin[i]), A.qmax[i]);
   }
 }
