@@ -542,15 +542,15 @@ def kernel_suite(sc, ctx, dev, peak_ops):
 
 
 def launches_per_step(db, args, reach, gate):
-    """Kernels one sc_generate call enqueues: init and tables; per (object, try)
-    of the objects with reachability a generation step and the reach stage
-    (grasp targets, [gate forward, gate split], IK); then the alive marks and
-    one chained launch for the remaining objects."""
+    """Kernels one sc_generate call enqueues: init and tables; per round of the
+    objects with reachability a generation step and the reach stage (grasp
+    targets, [gate forward, gate split], IK; rounds past the last candidate
+    exit at once); then one chained launch for the remaining objects."""
     K, R = db.c.max_obj, args.retries
-    per_try_reach = 4 if gate is not None else 2
+    per_round_reach = 4 if gate is not None else 2
     n_reach = min(4, K) if reach else 0
-    chained = (1 + (1 if n_reach > 0 else 0)) if n_reach < K else 0
-    return 2 + n_reach * (R + 1) * (1 + per_try_reach) + chained
+    rounds = 2 * n_reach * (R + 1)  # generate_rounds(): a try of a reach object spans two rounds
+    return 2 + rounds * (1 + per_round_reach) + (1 if n_reach < K else 0)
 
 
 def main():

@@ -24,6 +24,9 @@ struct sc_ctx {
   // grow-on-demand scratch of sc_generate (candidate lists and counters)
   void* gen_scratch = nullptr;
   size_t gen_scratch_bytes = 0;
+  // side streams and events of sc_generate's rounds (reach stages overlap generation)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> round_events;
   // sc_generate's launch sequence captured as a CUDA graph, and what it was captured for
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t gen_graph = nullptr;
@@ -159,6 +162,9 @@ void sc_ctx_destroy(sc_ctx* ctx) {
   if (ctx->gen_exec) cudaGraphExecDestroy(ctx->gen_exec);
   if (ctx->gen_graph) cudaGraphDestroy(ctx->gen_graph);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  for (cudaStream_t st : ctx->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->round_events) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
   delete ctx;
@@ -334,6 +340,9 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.reach_objects = 0;
   a.max_sph_obj = 0;
   a.timer = nullptr;
+  a.side[0] = a.side[1] = nullptr;
+  a.events = nullptr;
+  a.n_events = 0;
   if (ctx->timing) {
     ctx->timer.used = 0;
     a.timer = &ctx->timer;
@@ -352,6 +361,25 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     }
     a.reach_objects = want_reach ? ctx->reach_extent : 0;
     a.max_sph_obj = ctx->max_sph_obj;
+  }
+  if (a.reach_objects > 0) {  // side streams and events of the rounds
+    const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;
+    for (int j = 0; j < 2; ++j) {
+      if (!ctx->side[j]) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->side[j], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+      }
+    }
+    while (ctx->round_events.size() < need_ev) {
+      cudaEvent_t ev = nullptr;
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+      ctx->round_events.push_back(ev);
+    }
+    a.side[0] = ctx->side[0];
+    a.side[1] = ctx->side[1];
+    a.events = ctx->round_events.data();
+    a.n_events = (int)ctx->round_events.size();
   }
   ctx->seed_host = params->seed;
   cudaError_t e = cudaMemcpyAsync(seed_dev, &ctx->seed_host, 8, cudaMemcpyHostToDevice, ctx->stream);

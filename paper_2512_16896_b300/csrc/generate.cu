@@ -37,21 +37,30 @@ struct TmplInfo {
 };
 static_assert(sizeof(TmplInfo) == 64, "TmplInfo is four 16-byte loads");
 
+// Per-candidate progress of the rounds (objects with reachability): the
+// object a candidate is on and the try it makes next. A candidate sits in
+// exactly one list at a time, so only one kernel touches its state.
+struct CandState {
+  uint8_t* kc;     // [n_cand] current object
+  uint16_t* rc;    // [n_cand] next try of that object
+  uint8_t* alive;  // [n_cand] 1: starts the chained launch at object k_begin
+  int k_begin;     // objects [0, k_begin) run in rounds
+};
+
 struct GenStepArgs {
   sc_scene_batch b;
   const int32_t* cand_t;    // [n_cand] template of each candidate (-1: none)
   const TmplInfo* tinfo;    // [n_templates]
   const float* edge_inv;    // [n_verts] 1 / squared length of the edge ending at each vertex
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
-  int max_attempts, retry, max_retries, k, seg_len;
+  int max_attempts, max_retries, seg_len;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
-  const int32_t* list_in;
+  CandState st;
+  const int32_t* list_in;  // this round's candidates
   const int* n_in;
-  int32_t* list_retry;
-  int* n_retry;
-  int32_t* list_next;
-  int* n_next;
-  int32_t* list_reach;  // collision-free tries of reach-flagged objects (NULL: no reach stage)
+  int32_t* list_gen;       // the next round's candidates (retry, or the next object)
+  int* n_gen;
+  int32_t* list_reach;     // collision-free tries of reach-flagged objects (NULL: no reach stage)
   int* n_reach;
   float4* poses;
   uint8_t* valid;
@@ -453,18 +462,18 @@ __device__ __forceinline__ int check_object(const GenStepArgs& g, const TmplInfo
 }
 
 // Routing of a finished try (warp-uniform).
-enum Route : int { kRouteNone = 0, kRouteReach = 1, kRouteNext = 2, kRouteRetry = 3 };
+enum Route : int { kRouteNone = 0, kRouteReach = 1, kRouteGen = 2 };
 
 // Appends the warp's pending routed candidates (lane i holds entry i < npend)
 // to their lists: one atomic per list and flush instead of one per try.
 __device__ __forceinline__ void flush_routes(const GenStepArgs& g, int pend_c, int pend_r, int npend, int lane) {
 #pragma unroll
-  for (int d = kRouteReach; d <= kRouteRetry; ++d) {
+  for (int d = kRouteReach; d <= kRouteGen; ++d) {
     const bool mine = lane < npend && pend_r == d;
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, mine);
     if (!mask) continue;
-    int* cnt = d == kRouteReach ? g.n_reach : d == kRouteNext ? g.n_next : g.n_retry;
-    int32_t* list = d == kRouteReach ? g.list_reach : d == kRouteNext ? g.list_next : g.list_retry;
+    int* cnt = d == kRouteReach ? g.n_reach : g.n_gen;
+    int32_t* list = d == kRouteReach ? g.list_reach : g.list_gen;
     const int leader = __ffs(mask) - 1;
     int base = 0;
     if (lane == leader) base = atomicAdd(cnt, __popc(mask));
@@ -482,14 +491,18 @@ __device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCoun
   }
 }
 
-// One launch per (object k, try r) for the objects that carry reachability
-// (the gate and IK stages run between these launches): each warp takes one
-// listed candidate at a time and makes one try. Work distribution: warp w
-// takes item w first, then items claimed from the launch's counter (the
-// claim for the next item is issued before the current one is processed);
-// routed candidates are buffered per warp and appended 32 at a time.
+// One generation round for the objects that carry reachability: each warp
+// takes one listed candidate at a time and makes the try its state names
+// (object kc[c], try rc[c]). A collision-free try of a reach-flagged object
+// goes to this round's reach queue (its state is left for the reach stage);
+// otherwise the candidate advances (next try, or next object) into the next
+// round's list, to the chained launch (alive) once it reaches k_begin, or
+// ends (valid after its last object, invalid after its last try). Work
+// distribution: warp w takes item w first, then items claimed from the
+// round's counter (the claim for the next item is issued before the current
+// one is processed); routed candidates are appended 32 at a time.
 template <int APL>
-__global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
+__global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
   const WarpLayout WL = make_warp_layout(b.max_obj, g.max_sk, APL);
@@ -497,7 +510,6 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   const int n_items = *(volatile const int*)g.n_in;
-  const int k = g.k;
   const int warps_total = gridDim.x * warps_per_block;
   int item = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   if (item >= n_items) return;  // no atomic traffic from warps without work
@@ -512,6 +524,8 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
     const int t = (c >= 0 && c < b.n_cand) ? __ldg(&g.cand_t[c]) : -1;
     const TmplInfo& T = load_tmpl(g.tinfo, t, W.tmpl, lane);
     const int o0 = T.o0, nt = T.nt;
+    const int k = t >= 0 ? (int)g.st.kc[c] : 0;
+    const int r = t >= 0 ? (int)g.st.rc[c] : 0;
     int Sprev = 0, Sk = 0, rel = 0;
     if (t >= 0 && k < nt) {
       Sprev = __ldg(&b.obj_sph_off[o0 + k]) - T.s0;
@@ -537,18 +551,28 @@ __global__ void __launch_bounds__(256, 3) gen_warp_kernel(GenStepArgs g) {
 #pragma unroll 1
       for (int j = lane; j <= k + 1; j += 32) cp_async4(W.off + j, b.obj_sph_off + o0 + j);
       cp_async_commit();
-      const TryOut res =
-          gen_try<APL, true>(g, T, W, c, k, g.retry, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
-      if (res.pass) {
-        if (g.list_reach && (rel & SC_REL_REACH)) route = kRouteReach;
-        else if (k + 1 < nt) route = kRouteNext;
-      } else if (g.retry < g.max_retries) {
-        route = kRouteRetry;
+      const TryOut res = gen_try<APL, true>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
+      bool done = false;
+      if (res.pass && g.list_reach && (rel & SC_REL_REACH)) {
+        route = kRouteReach;
+      } else if (res.pass) {  // object k placed
+        done = k + 1 == nt;
+        if (!done) route = k + 1 < g.st.k_begin ? kRouteGen : kRouteNone;
+      } else if (r < g.max_retries) {
+        route = kRouteGen;
       }
       if (lane == 0) {
         if (res.band) g.band[c] = 1;
         atomicAdd(&g.tries[c], 1);
-        if (res.pass && route == kRouteNone) g.valid[c] = 1;  // object k was the last one
+        if (done) {
+          g.valid[c] = 1;
+        } else if (res.pass && route != kRouteReach) {
+          g.st.kc[c] = (uint8_t)(k + 1);
+          g.st.rc[c] = 0;
+          if (route == kRouteNone) g.st.alive[c] = 1;
+        } else if (!res.pass && route == kRouteGen) {
+          g.st.rc[c] = (uint16_t)(r + 1);
+        }
       }
     }
     if (route != kRouteNone) {
@@ -667,18 +691,19 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
 // unreachable back to retry; exact IK decides the rest.
 struct ReachArgs {
   sc_scene_batch b;
-  int k, retry, max_retries, gated;
+  const int32_t* cand_t;
+  const TmplInfo* tinfo;
+  int max_retries, gated;
   float tol_pos, tol_rot, tau;
-  const int32_t* list_reach;
+  CandState st;
+  const int32_t* list_reach;  // this round's reach queue
   const int* n_reach;
   float* targets;        // [cap][12]
   const float* logits;   // [cap]
   int32_t* list_ik;      // positions in the reach list the gate passed
   int* n_ik;
-  int32_t* list_retry;
-  int* n_retry;
-  int32_t* list_next;
-  int* n_next;
+  int32_t* list_gen;     // the round after next: retries and next objects
+  int* n_gen;
   const float4* poses;
   uint8_t* valid;
   uint8_t* band;
@@ -687,18 +712,38 @@ struct ReachArgs {
   ikc::IkArgs ik;
 };
 
-// Top-down grasp of object k: position = top centre of its box, tool z =
-// -world z, tool x along the object's yaw; expressed in the template's robot
-// base frame (x, y, z, yaw). R row-major, then p.
+// After the reach decision of try (k, r) of candidate c (one thread): the
+// next object (or valid after the last one, or the chained launch from
+// k_begin on) when it passed; the next try when it failed and tries remain.
+__device__ __forceinline__ void reach_advance(const ReachArgs& A, int c, int k, int r, int nt, bool pass) {
+  if (pass) {
+    if (k + 1 == nt) {
+      A.valid[c] = 1;
+      return;
+    }
+    A.st.kc[c] = (uint8_t)(k + 1);
+    A.st.rc[c] = 0;
+    if (k + 1 < A.st.k_begin) A.list_gen[atomicAdd(A.n_gen, 1)] = c;
+    else A.st.alive[c] = 1;
+  } else if (r < A.max_retries) {
+    A.st.rc[c] = (uint16_t)(r + 1);
+    A.list_gen[atomicAdd(A.n_gen, 1)] = c;
+  }
+}
+
+// Top-down grasp of the candidate's current object k: position = top centre
+// of its box, tool z = -world z, tool x along the object's yaw; expressed in
+// the template's robot base frame (x, y, z, yaw). R row-major, then p.
 __global__ void reach_targets_kernel(ReachArgs A) {
   const int n = *(volatile const int*)A.n_reach;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = A.list_reach[i];
-    const int t = template_of(A.b, c);
-    const int o0 = __ldg(&A.b.tmpl_obj_off[t]), nt = __ldg(&A.b.tmpl_obj_off[t + 1]) - o0;
-    const int64_t pbase = __ldg(&A.b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&A.b.cand_tmpl_off[t])) * nt;
-    const float4 p = A.poses[pbase + A.k];
-    const float hz = __ldg(&A.b.obj_half[4 * (o0 + A.k) + 2]);
+    const int t = __ldg(&A.cand_t[c]);
+    const TmplInfo& T = A.tinfo[t];
+    const int k = A.st.kc[c];
+    const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * T.nt;
+    const float4 p = A.poses[pbase + k];
+    const float hz = __ldg(&A.b.obj_half[4 * (T.o0 + k) + 2]);
     const float4 base = __ldg(reinterpret_cast<const float4*>(A.b.tmpl_base) + t);
     float sb, cb, sp, cp;
     sincosf(base.w, &sb, &cb);
@@ -723,7 +768,8 @@ __global__ void gate_split_kernel(ReachArgs A) {
       A.list_ik[atomicAdd(A.n_ik, 1)] = i;
     } else {
       ++rejected;
-      if (A.retry < A.max_retries) A.list_retry[atomicAdd(A.n_retry, 1)] = A.list_reach[i];
+      const int c = A.list_reach[i];
+      reach_advance(A, c, A.st.kc[c], A.st.rc[c], 0, false);
     }
   }
 #pragma unroll
@@ -739,28 +785,23 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
   for (int j = blockIdx.x * warps + (threadIdx.x >> 5); j < n; j += gridDim.x * warps) {
     const int i = A.gated ? A.list_ik[j] : j;
     const int c = A.list_reach[i];
+    const int k = A.st.kc[c], r = A.st.rc[c];
     const ikc::Target T = ikc::load_target(A.targets + 12 * (size_t)i);
     float q[7], pe2, sr, cr;
-    const ikc::Solve r = ikc::warp_solve(A.ik, T, (uint32_t)c, ((uint32_t)A.k << 16) | (uint32_t)A.retry, lane, q, pe2,
-                                         sr, cr);
+    const ikc::Solve s = ikc::warp_solve(A.ik, T, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, lane, q, pe2, sr, cr);
     ++solves;
-    seed_iters += (unsigned long long)(r.it + 1) * (unsigned long long)A.ik.seeds;
-    if (lane == r.winner) {
-      const int t = template_of(A.b, c);
-      const int o0 = __ldg(&A.b.tmpl_obj_off[t]), nt = __ldg(&A.b.tmpl_obj_off[t + 1]) - o0;
-      const int64_t pbase = __ldg(&A.b.tmpl_pose_off[t]) + (int64_t)(c - __ldg(&A.b.cand_tmpl_off[t])) * nt;
+    seed_iters += (unsigned long long)(s.it + 1) * (unsigned long long)A.ik.seeds;
+    __syncwarp();  // every lane has read the state before the winner updates it
+    if (lane == s.winner) {
+      const TmplInfo& Tm = A.tinfo[__ldg(&A.cand_t[c])];
+      const int64_t pbase = Tm.pose0 + (int64_t)(c - Tm.cand0) * Tm.nt;
       const float pe = sqrtf(pe2), ang = atan2f(sr, cr);
       if (fabsf(pe - A.tol_pos) <= kBand || fabsf(ang - A.tol_rot) <= kBand) A.band[c] = 1;
-      if (r.found) {
-        if (A.q_reach) {
+      if (s.found && A.q_reach) {
 #pragma unroll
-          for (int jq = 0; jq < 7; ++jq) A.q_reach[7 * (pbase + A.k) + jq] = q[jq];
-        }
-        if (A.k + 1 == nt) A.valid[c] = 1;
-        else A.list_next[atomicAdd(A.n_next, 1)] = c;
-      } else if (A.retry < A.max_retries) {
-        A.list_retry[atomicAdd(A.n_retry, 1)] = c;
+        for (int jq = 0; jq < 7; ++jq) A.q_reach[7 * (pbase + k) + jq] = q[jq];
       }
+      reach_advance(A, c, k, r, Tm.nt, s.found);
     }
   }
   if (lane == 0 && solves) {
@@ -819,28 +860,29 @@ __global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* t
   }
 }
 
-// First list = the caller's order (or 0..n-1); outputs of the listed
-// candidates cleared, their poses set to NaN until placed.
-// alive: 1 for every listed candidate when the chained kernel starts at
-// object 0, else 0 (set from the list of object k_begin later).
+// Initial state of the listed candidates: outputs cleared, poses NaN until
+// placed, object 0 / try 0, in round 0's list (the caller's order or
+// 0..n-1); alive = 1 when the chained launch starts at object 0. Counts are
+// zeroed except round 0's list length; work counters and statistics zeroed.
 __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, int32_t* list0, int* counts,
                                 int n_counts, unsigned int* counters, int n_counters, float4* poses, uint8_t* valid,
-                                uint8_t* band, int32_t* tries, unsigned long long* stats, int* status,
-                                uint8_t* alive, uint8_t alive_value) {
+                                uint8_t* band, int32_t* tries, unsigned long long* stats, int* status, CandState st) {
   const int stride = gridDim.x * blockDim.x;
   const float nan = __int_as_float(0x7FC00000);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int c = order ? order[i] : i;
     list0[i] = c;
     const int t = template_of(b, c);
-    if (t < 0) {  // the step kernel skips it too
+    if (t < 0) {  // the step kernels skip it too
       latch_error(status, kDevBadTemplate);
       continue;
     }
     valid[c] = 0;
     band[c] = 0;
     tries[c] = 0;
-    alive[c] = alive_value;
+    st.kc[c] = 0;
+    st.rc[c] = 0;
+    st.alive[c] = st.k_begin == 0 ? 1 : 0;
     const int o0 = b.tmpl_obj_off[t], nt = b.tmpl_obj_off[t + 1] - o0;
     const int64_t pbase = b.tmpl_pose_off[t] + (int64_t)(c - b.cand_tmpl_off[t]) * nt;
     for (int k = 0; k < nt; ++k) poses[pbase + k] = make_float4(nan, nan, nan, nan);
@@ -850,15 +892,9 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   if (blockIdx.x == 0 && threadIdx.x < 7 && stats) stats[threadIdx.x] = 0;
 }
 
-// Candidates listed for object k_begin are alive for the chained kernel.
-__global__ void mark_alive_kernel(const int32_t* list, const int* n_dev, uint8_t* alive) {
-  const int n = *(volatile const int*)n_dev;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alive[list[i]] = 1;
-}
-
 template <int APL>
 cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int num_sms, int* grid) {
-  auto kern = gen_warp_kernel<APL>;
+  auto kern = gen_round_kernel<APL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(gen_chain_kernel<APL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -872,8 +908,8 @@ cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int n
 }
 
 template <int APL>
-void launch_step(const GenStepArgs& g, int grid, int threads, size_t smem, cudaStream_t s) {
-  gen_warp_kernel<APL><<<grid, threads, smem, s>>>(g);
+void launch_round(const GenStepArgs& g, int grid, int threads, size_t smem, cudaStream_t s) {
+  gen_round_kernel<APL><<<grid, threads, smem, s>>>(g);
 }
 
 template <int APL>
@@ -892,28 +928,38 @@ cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host
   return cudaStreamSynchronize(s);
 }
 
-// Scratch: 6 int32 lists of n (next x2, retry x2, reach, gate-passed), the
-// grasp targets (12 floats) and logits of the reach list, counts
-// [K+1] + 3 x [K][R+1], work counters [K][R+1], the per-call tables
-// (candidate templates, TmplInfo records, inverse edge lengths), then the
-// seed scalar.
+int generate_rounds(int reach_objects, int max_retries) {
+  // a try of a reach-flagged object takes at most two rounds (generation,
+  // then the reach stage, whose outcome lands in the round after next)
+  return 2 * reach_objects * (max_retries + 1);
+}
+
+// Scratch: round lists G[3], reach queues Q[2] and gate-passed lists IK[2]
+// (int32 [n] each), two slots of grasp targets (12 floats) and logits; counts
+// (list lengths per round [NR + 2], reach queue and IK lengths per round
+// [NR] each); work counters (one per round + the chained launch); the
+// per-candidate state (object, try, alive); the per-call tables (candidate
+// templates, TmplInfo records, inverse edge lengths); then the seed scalar.
+// NR is bounded by generate_rounds(max_obj, max_retries).
 struct GenScratch {
-  size_t lists, counts, counters, cand_t, tinfo, edge_inv, alive, seed, total;
+  size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, seed, total;
 };
 
 static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int max_retries) {
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t n = (size_t)n_items;
-  const size_t K = (size_t)b.max_obj, R1 = (size_t)max_retries + 1;
+  const size_t NR = (size_t)generate_rounds(b.max_obj, max_retries);
   GenScratch L;
   L.lists = 0;
-  L.counts = up(L.lists + 6 * n * sizeof(int32_t) + 13 * n * sizeof(float));
-  L.counters = L.counts + ((K + 1) + 3 * K * R1) * sizeof(int);  // [K][R+1] + 1 (chained kernel)
-  L.cand_t = up(L.counters + (K * R1 + 1) * sizeof(unsigned int));
+  L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 13 * n * sizeof(float));
+  L.counters = up(L.counts + ((NR + 2) + 2 * NR) * sizeof(int));
+  L.kc = up(L.counters + (NR + 1) * sizeof(unsigned int));
+  L.rc = up(L.kc + (size_t)b.n_cand);
+  L.alive = up(L.rc + (size_t)b.n_cand * sizeof(uint16_t));
+  L.cand_t = up(L.alive + (size_t)b.n_cand);
   L.tinfo = up(L.cand_t + (size_t)b.n_cand * sizeof(int32_t));
   L.edge_inv = up(L.tinfo + (size_t)b.n_templates * sizeof(TmplInfo));
-  L.alive = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));
-  L.seed = up(L.alive + (size_t)b.n_cand);  // the 8-byte seed on a 256-byte boundary
+  L.seed = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));  // the 8-byte seed on a 256-byte boundary
   L.total = L.seed + 256;
   return L;
 }
@@ -936,32 +982,41 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   if (smem > 227 * 1024) { *why = "threads x per-warp shared memory exceeds one CTA's (lower threads)"; return cudaErrorInvalidValue; }
   const int n = a.n_items;
   const int K = b.max_obj, R = a.max_retries;
+  const bool reach = a.arm != nullptr;
+  // objects [0, k_begin) carry reachability and run in rounds (generation,
+  // then the gate and IK on two side streams, overlapping the next rounds);
+  // the rest run in one chained launch
+  const int k_begin = reach ? (a.reach_objects < K ? a.reach_objects : K) : 0;
+  const int NR = generate_rounds(k_begin, R);
+  if (k_begin > 0 && (a.n_events < 2 * NR + 1 || !a.side[0] || !a.side[1])) {
+    *why = "internal: too few events or side streams for the rounds";
+    return cudaErrorInvalidValue;
+  }
   const GenScratch SL = gen_scratch_layout(b, n, R);
   char* sb = static_cast<char*>(a.scratch);
   int32_t* ib = reinterpret_cast<int32_t*>(sb + SL.lists);
-  int32_t* L[2] = {ib, ib + n};
-  int32_t* Rl[2] = {ib + 2 * (size_t)n, ib + 3 * (size_t)n};
-  int32_t* list_reach = ib + 4 * (size_t)n;
-  int32_t* list_ik = ib + 5 * (size_t)n;
-  float* targets = reinterpret_cast<float*>(ib + 6 * (size_t)n);
-  float* logits = targets + 12 * (size_t)n;
+  int32_t* G[3] = {ib, ib + n, ib + 2 * (size_t)n};
+  int32_t* Q[2] = {ib + 3 * (size_t)n, ib + 4 * (size_t)n};
+  int32_t* IK[2] = {ib + 5 * (size_t)n, ib + 6 * (size_t)n};
+  float* fb = reinterpret_cast<float*>(ib + 7 * (size_t)n);
+  float* targets[2] = {fb, fb + 12 * (size_t)n};
+  float* logits[2] = {fb + 24 * (size_t)n, fb + 25 * (size_t)n};
+  const int NRmax = generate_rounds(K, R);
   int* counts = reinterpret_cast<int*>(sb + SL.counts);
-  const int n_counts = (K + 1) + 3 * K * (R + 1);
-  int* cnt_list = counts;
-  int* cnt_retry = counts + (K + 1);
-  int* cnt_reach = cnt_retry + K * (R + 1);
-  int* cnt_ik = cnt_reach + K * (R + 1);
+  const int n_counts = (NRmax + 2) + 2 * NRmax;
+  int* cnt_gen = counts;                  // [NR + 2]
+  int* cnt_reach = counts + (NRmax + 2);  // [NR]
+  int* cnt_ik = cnt_reach + NRmax;        // [NR]
   unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
-  const int n_counters = K * (R + 1) + 1;  // the last one is the chained kernel's
+  const int n_counters = NRmax + 1;  // one per round, the last one is the chained launch's
+  CandState st;
+  st.kc = reinterpret_cast<uint8_t*>(sb + SL.kc);
+  st.rc = reinterpret_cast<uint16_t*>(sb + SL.rc);
+  st.alive = reinterpret_cast<uint8_t*>(sb + SL.alive);
+  st.k_begin = k_begin;
   int32_t* cand_t = reinterpret_cast<int32_t*>(sb + SL.cand_t);
   TmplInfo* tinfo = reinterpret_cast<TmplInfo*>(sb + SL.tinfo);
   float* edge_inv = reinterpret_cast<float*>(sb + SL.edge_inv);
-  uint8_t* alive = reinterpret_cast<uint8_t*>(sb + SL.alive);
-  const unsigned long long* seed_dev = a.seed_dev;
-  const bool reach = a.arm != nullptr;
-  // objects [0, k_begin) carry reachability: one launch per (object, try)
-  // with the gate and IK between; the rest run in one chained launch
-  const int k_begin = reach ? (a.reach_objects < K ? a.reach_objects : K) : 0;
 
   int grid = 0;
   cudaError_t e;
@@ -975,24 +1030,26 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     int blocks = (n + 255) / 256;
     blocks = blocks < num_sms * 4 ? blocks : num_sms * 4;
     if (blocks < 1) blocks = 1;
-    gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, L[0], counts, n_counts, counters, n_counters,
+    gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, G[0], counts, n_counts, counters, n_counters,
                                            reinterpret_cast<float4*>(a.poses), a.valid, a.band, a.tries, a.stats,
-                                           a.status, alive, (uint8_t)(k_begin == 0 ? 1 : 0));
+                                           a.status, st);
     int tb = ((b.n_cand > b.n_templates ? b.n_cand : b.n_templates) + 255) / 256;
     tb = tb < num_sms * 4 ? tb : num_sms * 4;
     gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   GenStepArgs g;
+  std::memset(&g, 0, sizeof(g));
   g.b = b;
   g.cand_t = cand_t;
   g.tinfo = tinfo;
   g.edge_inv = edge_inv;
-  g.seed = seed_dev;
+  g.seed = a.seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
   g.max_sk = max_sk;
   g.seg_len = cfg.seg_len;
+  g.st = st;
   g.poses = reinterpret_cast<float4*>(a.poses);
   g.valid = a.valid;
   g.band = a.band;
@@ -1003,15 +1060,14 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   std::memset(&ra, 0, sizeof(ra));
   if (reach) {
     ra.b = b;
+    ra.cand_t = cand_t;
+    ra.tinfo = tinfo;
     ra.max_retries = R;
     ra.gated = a.gate != nullptr;
     ra.tol_pos = a.ik->tol_pos;
     ra.tol_rot = a.ik->tol_rot;
     ra.tau = a.tau;
-    ra.list_reach = list_reach;
-    ra.targets = targets;
-    ra.logits = logits;
-    ra.list_ik = list_ik;
+    ra.st = st;
     ra.poses = reinterpret_cast<const float4*>(a.poses);
     ra.valid = a.valid;
     ra.band = a.band;
@@ -1022,64 +1078,74 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int small_blocks = (n + 255) / 256;
   small_blocks = small_blocks < num_sms * 4 ? small_blocks : num_sms * 4;
   if (small_blocks < 1) small_blocks = 1;
-  for (int k = 0; k < k_begin; ++k) {
-    g.k = k;
-    g.list_next = L[(k + 1) & 1];
-    g.n_next = cnt_list + k + 1;
-    const bool reach_k = reach && k < a.reach_objects;
-    for (int r = 0; r <= R; ++r) {
-      g.retry = r;
-      g.list_in = r == 0 ? L[k & 1] : Rl[(r - 1) & 1];
-      g.n_in = r == 0 ? cnt_list + k : cnt_retry + k * (R + 1) + (r - 1);
-      g.list_retry = Rl[r & 1];
-      g.n_retry = cnt_retry + k * (R + 1) + r;
-      g.counter = counters + k * (R + 1) + r;
-      g.list_reach = reach_k ? list_reach : nullptr;
-      g.n_reach = reach_k ? cnt_reach + k * (R + 1) + r : nullptr;
-      if (a.timer) a.timer->begin(0, s);
-      switch (cfg.a_per_lane) {
-        case 1: launch_step<1>(g, grid, cfg.threads, smem, s); break;
-        case 2: launch_step<2>(g, grid, cfg.threads, smem, s); break;
-        default: launch_step<4>(g, grid, cfg.threads, smem, s); break;
-      }
-      if (a.timer) a.timer->end(s);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if (!reach_k) continue;
-      ra.k = k;
-      ra.retry = r;
-      ra.n_reach = g.n_reach;
-      ra.n_ik = cnt_ik + k * (R + 1) + r;
-      ra.list_retry = g.list_retry;
-      ra.n_retry = g.n_retry;
-      ra.list_next = g.list_next;
-      ra.n_next = g.n_next;
-      if (a.timer) a.timer->begin(1, s);
-      reach_targets_kernel<<<small_blocks, 256, 0, s>>>(ra);
-      if (ra.gated) {
-        e = mlp_infer_counted(a.gate, targets, ra.n_reach, n, logits, a.status, num_sms, s);
-        if (e != cudaSuccess) return e;
-        gate_split_kernel<<<small_blocks, 256, 0, s>>>(ra);
-      }
-      if (a.timer) {
-        a.timer->end(s);
-        a.timer->begin(2, s);
-      }
-      reach_ik_kernel<<<num_sms * 8, 128, 0, s>>>(ra);
-      if (a.timer) a.timer->end(s);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+  // ---- rounds. Round i: generation on s reads G[i % 3] (filled by round
+  // i-1's generation and round i-2's reach stage) and writes G[(i+1) % 3]
+  // and the reach queue Q[i % 2]; the reach stage of round i runs on side
+  // stream i % 2 after it and writes G[(i+2) % 3]. Generation of round i
+  // waits for the reach stage of round i-2, so reach stages overlap the next
+  // rounds' generation and each other.
+  cudaEvent_t* ev_gen = a.events + 1;
+  cudaEvent_t* ev_reach = a.events + 1 + NR;
+  if (NR > 0) {
+    if ((e = cudaEventRecord(a.events[0], s)) != cudaSuccess) return e;
+    for (int j = 0; j < 2; ++j)
+      if ((e = cudaStreamWaitEvent(a.side[j], a.events[0], 0)) != cudaSuccess) return e;
   }
+  for (int i = 0; i < NR; ++i) {
+    if (i >= 2 && (e = cudaStreamWaitEvent(s, ev_reach[i - 2], 0)) != cudaSuccess) return e;
+    g.list_in = G[i % 3];
+    g.n_in = cnt_gen + i;
+    g.list_gen = G[(i + 1) % 3];
+    g.n_gen = cnt_gen + i + 1;
+    g.list_reach = Q[i % 2];
+    g.n_reach = cnt_reach + i;
+    g.counter = counters + i;
+    if (a.timer) a.timer->begin(0, s);
+    switch (cfg.a_per_lane) {
+      case 1: launch_round<1>(g, grid, cfg.threads, smem, s); break;
+      case 2: launch_round<2>(g, grid, cfg.threads, smem, s); break;
+      default: launch_round<4>(g, grid, cfg.threads, smem, s); break;
+    }
+    if (a.timer) a.timer->end(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_gen[i], s)) != cudaSuccess) return e;
+    cudaStream_t sr = a.side[i % 2];
+    if ((e = cudaStreamWaitEvent(sr, ev_gen[i], 0)) != cudaSuccess) return e;
+    ra.list_reach = Q[i % 2];
+    ra.n_reach = cnt_reach + i;
+    ra.targets = targets[i % 2];
+    ra.logits = logits[i % 2];
+    ra.list_ik = IK[i % 2];
+    ra.n_ik = cnt_ik + i;
+    ra.list_gen = G[(i + 2) % 3];
+    ra.n_gen = cnt_gen + i + 2;
+    if (a.timer) a.timer->begin(1, sr);
+    reach_targets_kernel<<<small_blocks, 256, 0, sr>>>(ra);
+    if (ra.gated) {
+      e = mlp_infer_counted(a.gate, ra.targets, ra.n_reach, n, logits[i % 2], a.status, num_sms, sr);
+      if (e != cudaSuccess) return e;
+      gate_split_kernel<<<small_blocks, 256, 0, sr>>>(ra);
+    }
+    if (a.timer) {
+      a.timer->end(sr);
+      a.timer->begin(2, sr);
+    }
+    reach_ik_kernel<<<num_sms * 8, 128, 0, sr>>>(ra);
+    if (a.timer) a.timer->end(sr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_reach[i], sr)) != cudaSuccess) return e;
+  }
+  for (int i = NR - 2; i < NR; ++i)  // join the side streams
+    if (i >= 0 && (e = cudaStreamWaitEvent(s, ev_reach[i], 0)) != cudaSuccess) return e;
   // ---- objects [k_begin, max_obj): one chained launch
   if (k_begin < K) {
     if (a.timer) a.timer->begin(0, s);
-    if (k_begin > 0) mark_alive_kernel<<<small_blocks, 256, 0, s>>>(L[k_begin & 1], cnt_list + k_begin, alive);
     ChainArgs ca;
     ca.order = a.order;
     ca.n = n;
     ca.k_begin = k_begin;
-    ca.alive = alive;
-    ca.counter = counters + K * (R + 1);
-    g.k = k_begin;
+    ca.alive = st.alive;
+    ca.counter = counters + NRmax;
     switch (cfg.a_per_lane) {
       case 1: launch_chain<1>(g, ca, grid, cfg.threads, smem, s); break;
       case 2: launch_chain<2>(g, ca, grid, cfg.threads, smem, s); break;

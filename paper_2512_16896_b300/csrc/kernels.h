@@ -82,7 +82,16 @@ struct GenerateLaunch {
   int max_sph_obj;       // most spheres of one object in the batch (batch_scan)
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
   StageTimer* timer;     // NULL: no timing
+  // rounds of the objects with reachability: two side streams for the reach
+  // stages and 2 * generate_rounds(reach_objects, max_retries) + 1 events
+  cudaStream_t side[2];
+  cudaEvent_t* events;
+  int n_events;
 };
+
+// Upper bound on the rounds the objects with reachability take (a try of a
+// reach-flagged object spans two rounds).
+int generate_rounds(int reach_objects, int max_retries);
 
 size_t generate_scratch_bytes(const sc_scene_batch& b, int n_items, int max_retries);
 // Byte offset of the 8-byte seed scalar inside that scratch (256-aligned).
