@@ -361,13 +361,20 @@ typedef struct {
  * reach   optional reachability stage (NULL: none).
  * q_reach float [P][7] (may be NULL): for every reach-checked object that was
  *         placed, the IK solution that verified it (pose-slot layout).
+ * Schedule: objects before the last reach-flagged one run in rounds — each
+ * round one generation launch over the candidates due a try (each candidate
+ * carries its own object and try), then the reach stage of that round on one
+ * of two context-owned side streams, overlapping the next rounds (at most
+ * 2 x reach objects x (max_retries + 1) rounds; empty ones exit at once);
+ * the remaining objects run in one launch where a warp takes a candidate
+ * through all its later objects and tries. All of it is one graph launch
+ * when use_graph = 1 (the seed is read from device memory, so a replay with
+ * a new seed is not re-captured); the side streams are joined back into the
+ * caller's stream before the call's work ends.
  * The first call (or one with more candidates than before) allocates the
- * context's generation scratch (4 int32 lists of the candidates plus
- * counters); later calls reuse it. Enqueues 1 + max_obj * (max_retries + 1)
- * kernels (as one graph launch when use_graph = 1; the seed is read from
- * device memory, so a replay with a new seed is not re-captured); launches
- * whose list is empty exit at once. A call with use_graph = 1 must not itself
- * be issued inside another stream capture.
+ * context's generation scratch (candidate lists, per-candidate state,
+ * counters, per-call tables); later calls reuse it. A call with
+ * use_graph = 1 must not itself be issued inside another stream capture.
  * Errors: SC_ERR_INVALID (NULL outputs, max_attempts / max_retries out of
  * range, bad config, batch limits), SC_ERR_OOM, SC_ERR_CUDA. */
 sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_params* params, const int32_t* order,
@@ -381,8 +388,9 @@ typedef struct {
   int64_t ik_solves;           /* targets the exact IK solved */
   int64_t gate_rejections;     /* tries the learned gate sent back without IK */
   int64_t ik_seed_iterations;  /* sum over solves of seeds x (checks made) */
-  float ms_stage[3];           /* with timing on: device time of the generation-step launches,
-                                  the grasp-target + gate launches, and the IK launches */
+  float ms_stage[3];           /* with timing on: device time of the generation launches, the
+                                  grasp-target + gate launches, and the IK launches (stages run
+                                  concurrently on different streams, so these may overlap) */
   int32_t launches_stage[3];
   int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull */
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
