@@ -52,6 +52,7 @@ struct GenStepArgs {
   const int32_t* cand_t;    // [n_cand] template of each candidate (-1: none)
   const TmplInfo* tinfo;    // [n_templates]
   const float* edge_inv;    // [n_verts] 1 / squared length of the edge ending at each vertex
+  const float4* obb_tab;    // [n_obb][4] (R row 0 | cx), (R row 1 | cy), (R row 2 | cz), (hx, hy, hz, 0)
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, max_retries, seg_len;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
@@ -274,88 +275,53 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     __syncwarp();
   }
   a_bound = -warp_min(-a_bound);
-  // ---- object k's spheres (B side)
-  float r2 = 0.f;
+  // ---- object k's spheres (B side), one pass: world frame, world boxes
+  // (exact box SDF where the lower bound max(|p| - h) - r is within the
+  // band), cull against the kept objects' balls, compacted into Bs as they
+  // are produced
+  float r2 = 0.f, m = kFarSentinel;
+  int Sc = 0;  // B spheres kept
 #pragma unroll 1
-  for (int q = lane; q < Sk + kPad; q += 32) {
+  for (int q0 = 0; q0 < Sk; q0 += 32) {
+    const int q = q0 + lane;
+    bool keep = false;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    float bb = 0.f;
     if (q < Sk) {
       const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + s0 + Sprev + q);
       const float x = (pk.x - ref.x) + (kcs * l.x - skn * l.y);
       const float y = (pk.y - ref.y) + (skn * l.x + kcs * l.y);
       const float z = (pk.z - ref.z) + l.z;
       const float c2 = x * x + y * y + z * z;
-      W.Bs[q] = make_float4(x, y, z, l.w);
-      W.Bb[q] = c2 - l.w * l.w;
+      w = make_float4(x, y, z, l.w);
+      bb = c2 - l.w * l.w;
       r2 = fmaxf(r2, c2);
-    } else {
-      W.Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
-      W.Bb[q] = 3e12f;
-    }
-  }
-  __syncwarp();
-  float m = kFarSentinel;
-  // ---- object k vs world boxes
 #pragma unroll 1
-  for (int bi = 0; bi < nobb; ++bi) {
-    const float* o = b.obb + 12 * (bx0 + bi);
-    float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
-    const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
-    qx *= inv; qy *= inv; qz *= inv; qw *= inv;
-    // columns of R (R maps box frame to world)
-    const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
-    const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
-    const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
-    const float ox = __ldg(o + 0) - ref.x, oy = __ldg(o + 1) - ref.y, oz = __ldg(o + 2) - ref.z;
-    const float hx = __ldg(o + 8), hy = __ldg(o + 9), hz = __ldg(o + 10);
+      for (int bi = 0; bi < nobb; ++bi) {
+        const float4* o = g.obb_tab + 4 * (bx0 + bi);
+        const float4 R0 = __ldg(o), R1 = __ldg(o + 1), R2 = __ldg(o + 2), Hh = __ldg(o + 3);
+        // box frame: p = R^T (c - centre); rows of R^T are the columns of R,
+        // stored as the table's rows
+        const float vx = x - (R0.w - ref.x), vy = y - (R1.w - ref.y), vz = z - (R2.w - ref.z);
+        const float px = R0.x * vx + R0.y * vy + R0.z * vz;
+        const float py = R1.x * vx + R1.y * vy + R1.z * vz;
+        const float pz = R2.x * vx + R2.y * vy + R2.z * vz;
+        const float ex = fabsf(px) - Hh.x, ey = fabsf(py) - Hh.y, ez = fabsf(pz) - Hh.z;
+        const float em = fmaxf(ex, fmaxf(ey, ez));
+        if (em - l.w < kBand) {
+          const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
+          m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - l.w);
+        }
+      }
 #pragma unroll 1
-    for (int q = lane; q < Sk; q += 32) {
-      const float4 w = W.Bs[q];
-      const float vx = w.x - ox, vy = w.y - oy, vz = w.z - oz;
-      const float px = c00 * vx + c01 * vy + c02 * vz;
-      const float py = c10 * vx + c11 * vy + c12 * vz;
-      const float pz = c20 * vx + c21 * vy + c22 * vz;
-      const float ex = fabsf(px) - hx, ey = fabsf(py) - hy, ez = fabsf(pz) - hz;
-      const float em = fmaxf(ex, fmaxf(ey, ez));
-      if (em - w.w < kBand) {
-        const float ux = fmaxf(ex, 0.f), uy = fmaxf(ey, 0.f), uz = fmaxf(ez, 0.f);
-        m = fminf(m, sqrtf(ux * ux + uy * uy + uz * uz) + fminf(em, 0.f) - w.w);
+      for (int jj = 0; jj < nkeep && !keep; ++jj) {
+        const float4 kb = W.kball[jj];
+        const float dx = x - kb.x, dy = y - kb.y, dz = z - kb.z;
+        const float lim = kb.w + l.w + kBand + kBroadMargin;
+        keep = dx * dx + dy * dy + dz * dz <= lim * lim;
       }
     }
-  }
-  if (lane == 0) {
-    cnt.box += (unsigned long long)nobb * (unsigned long long)Sk;
-    cnt.exh += (unsigned long long)Sprev * (unsigned long long)Sk;
-  }
-  m = warp_min(m);
-  bool alive = !(m < -kBand);
-  r2 = -warp_min(-r2);
-  // ---- B cull against the kept objects' balls, compacted in place
-  unsigned keepbits = 0;  // bit u: sphere lane + 32 u is near a kept object
-#pragma unroll 1
-  for (int jj = 0; alive && jj < nkeep; ++jj) {
-    const float4 kb = W.kball[jj];
-#pragma unroll 1
-    for (int q = lane, u = 0; q < Sk; q += 32, ++u) {
-      const float4 w = W.Bs[q];
-      const float dx = w.x - kb.x, dy = w.y - kb.y, dz = w.z - kb.z;
-      const float lim = kb.w + w.w + kBand + kBroadMargin;
-      if (dx * dx + dy * dy + dz * dz <= lim * lim) keepbits |= 1u << u;
-    }
-  }
-  if (lane == 0) cnt.cull += (unsigned long long)Sk * (unsigned long long)nkeep;
-  int Sc = 0;  // B spheres kept
-#pragma unroll 1
-  for (int q0 = 0, u = 0; q0 < Sk; q0 += 32, ++u) {
-    const int q = q0 + lane;
-    const bool keep = (keepbits >> u) & 1u;
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    float bb = 0.f;
-    if (keep) {
-      w = W.Bs[q];
-      bb = W.Bb[q];
-    }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
-    __syncwarp();  // this chunk is read before it is overwritten
     if (keep) {
       const int pos = Sc + __popc(mask & ((1u << lane) - 1u));
       W.Bs[pos] = w;
@@ -368,6 +334,14 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     W.Bs[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
     W.Bb[q] = 3e12f;
   }
+  if (lane == 0) {
+    cnt.box += (unsigned long long)nobb * (unsigned long long)Sk;
+    cnt.exh += (unsigned long long)Sprev * (unsigned long long)Sk;
+    cnt.cull += (unsigned long long)Sk * (unsigned long long)nkeep;
+  }
+  m = warp_min(m);
+  bool alive = !(m < -kBand);
+  r2 = -warp_min(-r2);
   __syncwarp();
   // one tolerance for the whole try, from bounds on |a| and |b|
   const float eps = 1e-5f * (fmaxf(r2, a_bound * a_bound) + 0.01f);
@@ -828,8 +802,25 @@ __global__ void batch_scan_kernel(sc_scene_batch b, int* out) {
 // template (with the support polygon's bounding box) and the inverse squared
 // length of every polygon edge (edge i runs from vertex i-1 to vertex i,
 // cyclically within its polygon; 0 for a zero-length edge).
-__global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* tinfo, float* edge_inv) {
+__global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* tinfo, float* edge_inv,
+                                  float4* obb_tab) {
   const int stride = gridDim.x * blockDim.x;
+  // world boxes: the transpose of R (box frame -> world, from the normalised
+  // quaternion) row by row with the centre, then the half extents
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n_obb; i += stride) {
+    const float* o = b.obb + 12 * i;
+    float qx = o[4], qy = o[5], qz = o[6], qw = o[7];
+    const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx *= inv; qy *= inv; qz *= inv; qw *= inv;
+    // columns of R
+    const float c00 = 1.f - 2.f * (qy * qy + qz * qz), c01 = 2.f * (qx * qy + qz * qw), c02 = 2.f * (qx * qz - qy * qw);
+    const float c10 = 2.f * (qx * qy - qz * qw), c11 = 1.f - 2.f * (qx * qx + qz * qz), c12 = 2.f * (qy * qz + qx * qw);
+    const float c20 = 2.f * (qx * qz + qy * qw), c21 = 2.f * (qy * qz - qx * qw), c22 = 1.f - 2.f * (qx * qx + qy * qy);
+    obb_tab[4 * i + 0] = make_float4(c00, c01, c02, o[0]);
+    obb_tab[4 * i + 1] = make_float4(c10, c11, c12, o[1]);
+    obb_tab[4 * i + 2] = make_float4(c20, c21, c22, o[2]);
+    obb_tab[4 * i + 3] = make_float4(o[8], o[9], o[10], 0.f);
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b.n_cand; c += stride) cand_t[c] = template_of(b, c);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_templates; t += stride) {
     TmplInfo T;
@@ -942,7 +933,7 @@ int generate_rounds(int reach_objects, int max_retries) {
 // templates, TmplInfo records, inverse edge lengths); then the seed scalar.
 // NR is bounded by generate_rounds(max_obj, max_retries).
 struct GenScratch {
-  size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, seed, total;
+  size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, obb_tab, seed, total;
 };
 
 static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int max_retries) {
@@ -959,7 +950,8 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   L.cand_t = up(L.alive + (size_t)b.n_cand);
   L.tinfo = up(L.cand_t + (size_t)b.n_cand * sizeof(int32_t));
   L.edge_inv = up(L.tinfo + (size_t)b.n_templates * sizeof(TmplInfo));
-  L.seed = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));  // the 8-byte seed on a 256-byte boundary
+  L.obb_tab = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));
+  L.seed = up(L.obb_tab + (size_t)b.n_obb * 4 * sizeof(float4));  // the 8-byte seed on a 256-byte boundary
   L.total = L.seed + 256;
   return L;
 }
@@ -1017,6 +1009,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int32_t* cand_t = reinterpret_cast<int32_t*>(sb + SL.cand_t);
   TmplInfo* tinfo = reinterpret_cast<TmplInfo*>(sb + SL.tinfo);
   float* edge_inv = reinterpret_cast<float*>(sb + SL.edge_inv);
+  float4* obb_tab = reinterpret_cast<float4*>(sb + SL.obb_tab);
 
   int grid = 0;
   cudaError_t e;
@@ -1033,9 +1026,11 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, G[0], counts, n_counts, counters, n_counters,
                                            reinterpret_cast<float4*>(a.poses), a.valid, a.band, a.tries, a.stats,
                                            a.status, st);
-    int tb = ((b.n_cand > b.n_templates ? b.n_cand : b.n_templates) + 255) / 256;
+    int tmax = b.n_cand > b.n_templates ? b.n_cand : b.n_templates;
+    tmax = tmax > b.n_obb ? tmax : b.n_obb;
+    int tb = (tmax + 255) / 256;
     tb = tb < num_sms * 4 ? tb : num_sms * 4;
-    gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv);
+    gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv, obb_tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   GenStepArgs g;
@@ -1044,6 +1039,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.cand_t = cand_t;
   g.tinfo = tinfo;
   g.edge_inv = edge_inv;
+  g.obb_tab = obb_tab;
   g.seed = a.seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
