@@ -110,3 +110,41 @@ def test_trained_gate_emits_only_verified_scenes(sc, ctx):
     P, V, B, T, q = run(sc, ctx, db, b, seed=7, gate=gate)
     verify_emitted(b, P, V, q)
     gate.close()
+
+
+def _agree_and_verify(sc, ctx, b, seed, retries=10):
+    db = sc.DeviceBatch(b)
+    P, V, B, T, q = run(sc, ctx, db, b, seed=seed, retries=retries)
+    op, ov, ob, ot = oracle.generate(b, seed=seed, max_retries=retries, arm=ARM_O, ikp=oracle.ik_params(seed=seed))
+    gv = V.cpu().numpy()
+    assert np.mean(gv == ov) >= 0.95, np.mean(gv == ov)
+    if gv.sum():
+        verify_emitted(b, P, V, q)
+    return gv
+
+
+def test_reach_flags_not_a_prefix(sc, ctx):
+    """Objects 0 and 2 carry reachability, object 1 does not: object 1 is
+    placed inside the rounds without a reach stage."""
+    b = synth.ragged(seed=21, n_templates=12, cand_per_template=16, obj_range=(3, 9), n_reach=0)
+    for t in range(b.n_templates):
+        o0 = int(b.tmpl_obj_off[t])
+        for loc in (0, 2):
+            if loc < b.n_obj_of(t):
+                b.obj_rel[o0 + loc] |= synth.REL_REACH
+    gv = _agree_and_verify(sc, ctx, b, seed=8)
+    assert 0 < gv.sum() < len(gv)
+
+
+def test_every_object_reach_flagged(sc, ctx):
+    """All objects carry reachability: no chained launch, the rounds place everything."""
+    b = synth.ragged(seed=22, n_templates=8, cand_per_template=16, obj_range=(2, 5), n_reach=64)
+    assert all(b.obj_rel & synth.REL_REACH)
+    _agree_and_verify(sc, ctx, b, seed=9)
+
+
+def test_reach_without_retries(sc, ctx):
+    """max_retries = 0: one try per object, a failed reach ends the candidate."""
+    b = synth.ragged(seed=23, n_templates=12, cand_per_template=16, obj_range=(3, 8))
+    gv = _agree_and_verify(sc, ctx, b, seed=10, retries=0)
+    assert gv.sum() < len(gv)
