@@ -678,6 +678,7 @@ struct ReachArgs {
   int* n_ik;
   int32_t* list_gen;     // the round after next: retries and next objects
   int* n_gen;
+  unsigned int* claim;   // IK work counter of the round (zeroed at init)
   const float4* poses;
   uint8_t* valid;
   uint8_t* band;
@@ -752,11 +753,18 @@ __global__ void gate_split_kernel(ReachArgs A) {
 }
 
 // Exact IK, one warp per entry; seeds keyed by (candidate, object, try).
+// Entries cost from one check to 100 steps, so warps claim them one at a
+// time (first entry static, the claim for the next issued before solving the
+// current one) from a grid sized to the resident blocks.
 __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   const int n = A.gated ? *(volatile const int*)A.n_ik : *(volatile const int*)A.n_reach;
+  const int warps_total = gridDim.x * warps;
   unsigned long long solves = 0, seed_iters = 0;
-  for (int j = blockIdx.x * warps + (threadIdx.x >> 5); j < n; j += gridDim.x * warps) {
+  int j = blockIdx.x * warps + (threadIdx.x >> 5);
+  while (j < n) {
+    int next = 0;
+    if (lane == 0) next = warps_total + (int)atomicAdd(A.claim, 1u);
     const int i = A.gated ? A.list_ik[j] : j;
     const int c = A.list_reach[i];
     const int k = A.st.kc[c], r = A.st.rc[c];
@@ -777,6 +785,7 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
       }
       reach_advance(A, c, k, r, Tm.nt, s.found);
     }
+    j = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
   if (lane == 0 && solves) {
     atomicAdd(&A.stats[2], solves);
@@ -928,9 +937,10 @@ int generate_rounds(int reach_objects, int max_retries) {
 // Scratch: round lists G[3], reach queues Q[2] and gate-passed lists IK[2]
 // (int32 [n] each), two slots of grasp targets (12 floats) and logits; counts
 // (list lengths per round [NR + 2], reach queue and IK lengths per round
-// [NR] each); work counters (one per round + the chained launch); the
-// per-candidate state (object, try, alive); the per-call tables (candidate
-// templates, TmplInfo records, inverse edge lengths); then the seed scalar.
+// [NR] each); work counters (generation claims per round, the chained
+// launch's, IK claims per round); the per-candidate state (object, try,
+// alive); the per-call tables (candidate templates, TmplInfo records,
+// inverse edge lengths, world-box frames); then the seed scalar.
 // NR is bounded by generate_rounds(max_obj, max_retries).
 struct GenScratch {
   size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, obb_tab, seed, total;
@@ -944,7 +954,7 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   L.lists = 0;
   L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 13 * n * sizeof(float));
   L.counters = up(L.counts + ((NR + 2) + 2 * NR) * sizeof(int));
-  L.kc = up(L.counters + (NR + 1) * sizeof(unsigned int));
+  L.kc = up(L.counters + (2 * NR + 1) * sizeof(unsigned int));
   L.rc = up(L.kc + (size_t)b.n_cand);
   L.alive = up(L.rc + (size_t)b.n_cand * sizeof(uint16_t));
   L.cand_t = up(L.alive + (size_t)b.n_cand);
@@ -1000,7 +1010,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int* cnt_reach = counts + (NRmax + 2);  // [NR]
   int* cnt_ik = cnt_reach + NRmax;        // [NR]
   unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
-  const int n_counters = NRmax + 1;  // one per round, the last one is the chained launch's
+  const int n_counters = 2 * NRmax + 1;  // generation claims per round, the chained launch's, IK claims per round
   CandState st;
   st.kc = reinterpret_cast<uint8_t*>(sb + SL.kc);
   st.rc = reinterpret_cast<uint16_t*>(sb + SL.rc);
@@ -1074,6 +1084,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int small_blocks = (n + 255) / 256;
   small_blocks = small_blocks < num_sms * 4 ? small_blocks : num_sms * 4;
   if (small_blocks < 1) small_blocks = 1;
+  int ik_per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ik_per_sm, reach_ik_kernel, 128, 0)) != cudaSuccess) return e;
+  const int ik_blocks = num_sms * (ik_per_sm > 0 ? ik_per_sm : 1);
   // ---- rounds. Round i: generation on s reads G[i % 3] (filled by round
   // i-1's generation and round i-2's reach stage) and writes G[(i+1) % 3]
   // and the reach queue Q[i % 2]; the reach stage of round i runs on side
@@ -1115,6 +1128,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.n_ik = cnt_ik + i;
     ra.list_gen = G[(i + 2) % 3];
     ra.n_gen = cnt_gen + i + 2;
+    ra.claim = counters + NRmax + 1 + i;
     if (a.timer) a.timer->begin(1, sr);
     reach_targets_kernel<<<small_blocks, 256, 0, sr>>>(ra);
     if (ra.gated) {
@@ -1126,7 +1140,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       a.timer->end(sr);
       a.timer->begin(2, sr);
     }
-    reach_ik_kernel<<<num_sms * 8, 128, 0, sr>>>(ra);
+    reach_ik_kernel<<<ik_blocks, 128, 0, sr>>>(ra);
     if (a.timer) a.timer->end(sr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ev_reach[i], sr)) != cudaSuccess) return e;

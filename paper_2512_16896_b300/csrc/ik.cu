@@ -20,10 +20,17 @@ namespace {
 
 using namespace ikc;
 
+// Targets cost from one check to iters steps, so warps claim them one at a
+// time (first target static, the claim for the next issued before solving
+// the current one) from a grid sized to the resident blocks.
 __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
-  for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < K.n; i += gridDim.x * warps) {
+  const int warps_total = gridDim.x * warps;
+  int i = blockIdx.x * warps + (threadIdx.x >> 5);
+  while (i < K.n) {
+    int next = 0;
+    if (lane == 0) next = warps_total + (int)atomicAdd(K.claim, 1u);
     const Target T = load_target(K.targets + 12 * (size_t)i);
     const uint32_t tid = K.target_ids ? __ldg(&K.target_ids[i]) : (uint32_t)i;
     float q[7], pe2, s, c;
@@ -36,6 +43,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
       K.err[2 * (size_t)i + 1] = atan2f(s, c);
       if (K.iters_out) K.iters_out[i] = r.it;
     }
+    i = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
 }
 
@@ -64,10 +72,19 @@ __global__ void ik_step_kernel(ArmK arm, float lambda2, const float* targets, co
 
 }  // namespace
 
+int ik_resident_blocks(int num_sms) {
+  static int per_sm = 0;
+  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ik_kernel, 128, 0) != cudaSuccess)
+    per_sm = 4;
+  return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
-                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, int num_sms,
-                      cudaStream_t s) {
+                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, unsigned int* claim,
+                      int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(claim, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
   IkArgs K;
   fill_params(K, arm, P);
   K.targets = targets;
@@ -77,9 +94,10 @@ cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* tar
   K.q_out = q_out;
   K.err = err;
   K.iters_out = iters_out;
+  K.claim = claim;
   const int threads = 128, warps = threads / 32;
   int blocks = (n + warps - 1) / warps;
-  const int cap = num_sms * 16;
+  const int cap = ik_resident_blocks(num_sms);
   if (blocks > cap) blocks = cap;
   ik_kernel<<<blocks, threads, 0, s>>>(K);
   return cudaGetLastError();

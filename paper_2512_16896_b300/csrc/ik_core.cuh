@@ -26,6 +26,7 @@ struct IkArgs {
   float* q_out;
   float* err;
   int32_t* iters_out;
+  unsigned int* claim;  // work counter (zeroed before the launch): warps claim targets dynamically
 };
 
 // Forward kinematics; z[i], p[i] = z axis and origin of frame i (i = 0..6,

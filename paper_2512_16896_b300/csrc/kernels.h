@@ -103,9 +103,12 @@ cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
                              int num_sms, cudaStream_t s, const char** why);
 
+// claim: a device work counter, zeroed by the launcher on the stream.
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
-                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, int num_sms,
-                      cudaStream_t s);
+                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, unsigned int* claim,
+                      int num_sms, cudaStream_t s);
+// Blocks of 128 threads of the IK kernels that fit on the device at once.
+int ik_resident_blocks(int num_sms);
 cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets, const float* q_in, int n,
                            float* q_out, float* tool, int num_sms, cudaStream_t s);
 
