@@ -59,6 +59,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
   return x;
 }
 
+// sin and cos of x for moderate |x| (joint angles, yaw; |x| < 2^10): Cody
+// and Waite's additive range reduction x = j (pi/2) + r with pi/2 split into
+// its float value and the remainder, |r| <= pi/4, then the Taylor series of
+// sin r (through r^9) and cos r (through r^10), whose truncation errors on
+// that interval are below 2e-9 and 1.2e-10, and the quadrant rotation by j.
+// Absolute error about one float ulp of the result.
+__device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
+  const float j = rintf(x * 0.63661977236758134f);   // nearest multiple of pi/2
+  float r = fmaf(j, -1.57079637050628662f, x);       // float(pi/2) = pi/2 + 4.371139e-8
+  r = fmaf(j, 4.37113900630947700e-8f, r);
+  const float r2 = r * r;
+  float ps = 2.75573192239858907e-6f;                // 1/9!, -1/7!, 1/5!, -1/3!
+  ps = fmaf(ps, r2, -1.98412698412698413e-4f);
+  ps = fmaf(ps, r2, 8.33333333333333333e-3f);
+  ps = fmaf(ps, r2, -1.66666666666666667e-1f);
+  const float sn = fmaf(ps * r2, r, r);
+  float pc = -2.75573192239858907e-7f;               // -1/10!, 1/8!, -1/6!, 1/4!, -1/2!
+  pc = fmaf(pc, r2, 2.48015873015873016e-5f);
+  pc = fmaf(pc, r2, -1.38888888888888889e-3f);
+  pc = fmaf(pc, r2, 4.16666666666666667e-2f);
+  pc = fmaf(pc, r2, -0.5f);
+  const float cs = fmaf(pc, r2, 1.f);
+  const int q = (int)j;
+  const float s1 = (q & 1) ? cs : sn, c1 = (q & 1) ? sn : cs;
+  *s = (q & 2) ? -s1 : s1;
+  *c = ((q + 1) & 2) ? -c1 : c1;
+}
+
 // Uniform float in [0, 1) from the top 24 bits of a word (exact in FP32).
 __device__ __forceinline__ float unit_float(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
 

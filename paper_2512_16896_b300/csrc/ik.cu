@@ -64,7 +64,9 @@ __global__ void ik_step_kernel(ArmK arm, float lambda2, const float* targets, co
 #pragma unroll
       for (int j = 0; j < 3; ++j) tool[12 * (size_t)i + 9 + j] = t[j];
     }
-    dls_step(arm, lambda2, T, q, z, p, R, t);
+    float v[3], c;
+    rot_error(T, R, v, &c);
+    dls_step(arm, lambda2, T, q, z, p, R, t, v);
 #pragma unroll
     for (int j = 0; j < 7; ++j) q_out[7 * (size_t)i + j] = q[j];
   }

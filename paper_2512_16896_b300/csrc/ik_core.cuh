@@ -16,7 +16,7 @@ struct ArmK {
 
 struct IkArgs {
   ArmK arm;
-  float lambda2, tol_pos2, cos_tol, sin_tol;
+  float lambda2, tol_pos2, cos2_tol, sin2_tol;  // squared cosine / sine of the angle tolerance
   int iters, seeds;
   uint64_t seed;
   const float* targets;
@@ -42,7 +42,7 @@ __device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3
     z[i][0] = R[2]; z[i][1] = R[5]; z[i][2] = R[8];
     p[i][0] = t[0]; p[i][1] = t[1]; p[i][2] = t[2];
     float st, ct;
-    sincosf(q[i], &st, &ct);
+    sincos_cw(q[i], &st, &ct);
     const float ca = A.ca[i], sa = A.sa[i];
     // rotation part of Rz(q) Rx(alpha): columns c0 = (ct, st, 0), c1 = (-st ca, ct ca, sa), c2 = (st sa, -ct sa, ca)
     const float c1x = -st * ca, c1y = ct * ca, c2x = st * sa, c2y = -ct * sa;
@@ -63,44 +63,51 @@ struct Target {
   float R[9], p[3];
 };
 
-// Success test and errors of one configuration.
-__device__ __forceinline__ bool check(const IkArgs& K, const Target& T, const float R[9], const float t[3],
-                                      float* pos_err2, float* s_out, float* c_out) {
-  const float dx = T.p[0] - t[0], dy = T.p[1] - t[1], dz = T.p[2] - t[2];
-  const float pe2 = dx * dx + dy * dy + dz * dz;
-  // M = R^T R*; angle = atan2(|vee(M - M^T)| / 2, (tr M - 1) / 2)
+// Orientation error of R against the target's R*: with M = R^T R*, v =
+// vee(M - M^T) / 2 (tool frame; |v| = sin of the angle) and c = (tr M - 1) / 2
+// (its cosine).
+__device__ __forceinline__ void rot_error(const Target& T, const float R[9], float v[3], float* c) {
   float M[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) M[3 * r + c] = R[r] * T.R[c] + R[3 + r] * T.R[3 + c] + R[6 + r] * T.R[6 + c];
-  const float vx = 0.5f * (M[7] - M[5]), vy = 0.5f * (M[2] - M[6]), vz = 0.5f * (M[3] - M[1]);
-  const float s = sqrtf(vx * vx + vy * vy + vz * vz);
-  const float c = 0.5f * (M[0] + M[4] + M[8] - 1.f);
+    for (int cc = 0; cc < 3; ++cc) M[3 * r + cc] = R[r] * T.R[cc] + R[3 + r] * T.R[3 + cc] + R[6 + r] * T.R[6 + cc];
+  v[0] = 0.5f * (M[7] - M[5]);
+  v[1] = 0.5f * (M[2] - M[6]);
+  v[2] = 0.5f * (M[3] - M[1]);
+  *c = 0.5f * (M[0] + M[4] + M[8] - 1.f);
+}
+
+// Success test of one configuration; v, s2 = |v|^2 and c as rot_error.
+__device__ __forceinline__ bool check(const IkArgs& K, const Target& T, const float R[9], const float t[3],
+                                      float* pos_err2, float v[3], float* s2_out, float* c_out) {
+  const float dx = T.p[0] - t[0], dy = T.p[1] - t[1], dz = T.p[2] - t[2];
+  const float pe2 = dx * dx + dy * dy + dz * dz;
+  float c;
+  rot_error(T, R, v, &c);
+  const float s2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   *pos_err2 = pe2;
-  *s_out = s;
+  *s2_out = s2;
   *c_out = c;
-  // angle <= tol  <=>  s cos(tol) <= c sin(tol)   (angle in [0, pi], tol in (0, pi/2))
-  return pe2 <= K.tol_pos2 && s * K.cos_tol <= c * K.sin_tol;
+  // angle <= tol  <=>  s cos(tol) <= c sin(tol)  <=>  c >= 0 and s^2 cos^2(tol) <= c^2 sin^2(tol)
+  // (angle in [0, pi], s = |v| >= 0, tol in (0, pi/2))
+  return pe2 <= K.tol_pos2 && c >= 0.f && s2 * K.cos2_tol <= c * c * K.sin2_tol;
 }
 
 // One damped-least-squares step of q (in place) towards T, given the forward
-// kinematics (z, p, R, t) of q.
+// kinematics (z, p, R, t) of q and the tool-frame orientation error v of
+// rot_error. The world-frame orientation error 1/2 sum_k r_k x r*_k equals
+// R v (vee(R S R^T) = R vee(S) for a skew S, and R^T (R* R^T - R R*^T) R =
+// M - M^T).
 __device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Target& T, float q[7],
-                                         const float z[7][3], const float p[7][3], const float R[9], const float t[3]) {
+                                         const float z[7][3], const float p[7][3], const float R[9], const float t[3],
+                                         const float v[3]) {
   float e[6];
   e[0] = T.p[0] - t[0];
   e[1] = T.p[1] - t[1];
   e[2] = T.p[2] - t[2];
-  e[3] = e[4] = e[5] = 0.f;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {  // 1/2 sum_k r_k x r*_k (columns)
-    const float rx = R[k], ry = R[3 + k], rz = R[6 + k];
-    const float sx = T.R[k], sy = T.R[3 + k], sz = T.R[6 + k];
-    e[3] += 0.5f * (ry * sz - rz * sy);
-    e[4] += 0.5f * (rz * sx - rx * sz);
-    e[5] += 0.5f * (rx * sy - ry * sx);
-  }
+  for (int r = 0; r < 3; ++r) e[3 + r] = R[3 * r] * v[0] + R[3 * r + 1] * v[1] + R[3 * r + 2] * v[2];
   // A = J J^T + lambda^2 I accumulated column by column (column i of J is
   // j_i = (z_i x (t - p_i), z_i)); J itself is not kept, it is rebuilt for
   // J^T y below, which keeps the register footprint small.
@@ -196,21 +203,23 @@ __device__ __forceinline__ Solve warp_solve(const IkArgs& K, const Target& T, ui
   }
   Solve r{false, -1, 0};
   pe2 = 0.f;
-  s = 0.f;
+  float s2 = 0.f;
   c = 1.f;
   for (;; ++r.it) {
-    float z[7][3], p[7][3], R[9], t[3];
+    float z[7][3], p[7][3], R[9], t[3], v[3];
     fk(K.arm, q, z, p, R, t);
-    const bool ok = active && check(K, T, R, t, &pe2, &s, &c);
+    const bool ok = active && check(K, T, R, t, &pe2, v, &s2, &c);
     const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
     if (m) {
       r.winner = __ffs(m) - 1;
       r.found = true;
+      s = sqrtf(s2);
       return r;
     }
     if (r.it == K.iters) break;
-    if (active) dls_step(K.arm, K.lambda2, T, q, z, p, R, t);
+    if (active) dls_step(K.arm, K.lambda2, T, q, z, p, R, t, v);
   }
+  s = sqrtf(s2);
   // smallest position error, lowest index on ties
   float best = active ? pe2 : 3e38f;
   int who = lane;
@@ -242,8 +251,8 @@ inline void fill_params(IkArgs& K, const sc_arm& arm, const sc_ik_params& P) {
   K.arm = make_arm(arm);
   K.lambda2 = P.lambda * P.lambda;
   K.tol_pos2 = P.tol_pos * P.tol_pos;
-  K.cos_tol = (float)cos((double)P.tol_rot);
-  K.sin_tol = (float)sin((double)P.tol_rot);
+  K.cos2_tol = (float)(cos((double)P.tol_rot) * cos((double)P.tol_rot));
+  K.sin2_tol = (float)(sin((double)P.tol_rot) * sin((double)P.tol_rot));
   K.iters = P.iters;
   K.seeds = P.seeds;
   K.seed = P.seed;
