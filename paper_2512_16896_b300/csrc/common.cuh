@@ -59,7 +59,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
   return x;
 }
 
-// sin and cos of x for moderate |x| (joint angles, yaw; |x| < 2^10): Cody
+// sin and cos of a bounded angle (the callers pass yaws the sampler drew in
+// [0, 2 pi) and joint angles clamped to their limits; valid for |x| < 2^20): Cody
 // and Waite's additive range reduction x = j (pi/2) + r with pi/2 split into
 // its float value and the remainder, |r| <= pi/4, then the Taylor series of
 // sin r (through r^9) and cos r (through r^10), whose truncation errors on

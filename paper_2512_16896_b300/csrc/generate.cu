@@ -226,7 +226,7 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     for (int j = lane; j < k; j += 32) {
       const float4 p = W.opose[j], H = W.kball[j];
       float sn, cs;
-      sincosf(p.w, &sn, &cs);
+      sincos_cw(p.w, &sn, &cs);
       W.osc[j] = make_float2(sn, cs);
       W.orad[j] = sqrtf(H.x * H.x + H.y * H.y + H.z * H.z);
     }
@@ -238,7 +238,7 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
   const float4 pk = r.pose;
   const float rk = sqrtf(spec.H.x * spec.H.x + spec.H.y * spec.H.y + spec.H.z * spec.H.z);
   float skn, kcs;
-  sincosf(pk.w, &skn, &kcs);
+  sincos_cw(pk.w, &skn, &kcs);
   if (lane == 0) {
     W.opose[k] = pk;
     W.osc[k] = make_float2(skn, kcs);
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
         const float4 p = g.poses[pbase + j];
         const float4 H = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o0 + j);
         float sn, cs;
-        sincosf(p.w, &sn, &cs);
+        sincos_cw(p.w, &sn, &cs);
         W.opose[j] = p;
         W.osc[j] = make_float2(sn, cs);
         W.orad[j] = sqrtf(H.x * H.x + H.y * H.y + H.z * H.z);

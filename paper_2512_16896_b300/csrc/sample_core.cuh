@@ -167,7 +167,7 @@ __device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, con
     if (valid) {
       if (S.kind == SC_REL_NEXT_TO) {
         float sp, cp;
-        sincosf(kTwoPi * u.x, &sp, &cp);
+        sincos_cw(kTwoPi * u.x, &sp, &cp);
         const float r = rho_sum + RP.x + (RP.y - RP.x) * u.y;
         x = anchor.x + r * cp;
         y = anchor.y + r * sp;
