@@ -18,6 +18,7 @@
 #include "collide_core.cuh"
 #include "ik_core.cuh"
 #include "kernels.h"
+#include "mlp_tc_core.cuh"
 #include "sample_core.cuh"
 
 namespace sc {
@@ -673,7 +674,6 @@ struct ReachArgs {
   const int32_t* list_reach;  // this round's reach queue
   const int* n_reach;
   float* targets;        // [cap][12]
-  const float* logits;   // [cap]
   int32_t* list_ik;      // positions in the reach list the gate passed
   int* n_ik;
   int32_t* list_gen;     // the round after next: retries and next objects
@@ -706,50 +706,83 @@ __device__ __forceinline__ void reach_advance(const ReachArgs& A, int c, int k, 
   }
 }
 
+// Grasp target of the candidate's current object k (see reach_targets_kernel),
+// written to o[12].
+__device__ __forceinline__ void grasp_target(const ReachArgs& A, int c, float o[12]) {
+  const int t = __ldg(&A.cand_t[c]);
+  const TmplInfo& T = A.tinfo[t];
+  const int k = A.st.kc[c];
+  const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * T.nt;
+  const float4 p = A.poses[pbase + k];
+  const float hz = __ldg(&A.b.obj_half[4 * (T.o0 + k) + 2]);
+  const float4 base = __ldg(reinterpret_cast<const float4*>(A.b.tmpl_base) + t);
+  float sb, cb, sp, cp;
+  sincosf(base.w, &sb, &cb);
+  sincosf(p.w - base.w, &sp, &cp);
+  const float wx = p.x - base.x, wy = p.y - base.y, wz = p.z + hz - base.z;
+  o[0] = cp; o[1] = sp; o[2] = 0.f;
+  o[3] = sp; o[4] = -cp; o[5] = 0.f;
+  o[6] = 0.f; o[7] = 0.f; o[8] = -1.f;
+  o[9] = cb * wx + sb * wy;
+  o[10] = -sb * wx + cb * wy;
+  o[11] = wz;
+}
+
+// The learned gate's decision fused into the tensor-core forward pass: its
+// rows are the round's reach queue (grasp targets formed by
+// reach_targets_kernel), and each logit is decided at once — logit >= tau
+// goes to the IK list, the rest retries (or ends invalid); the appends are
+// aggregated per warp.
+struct GateIO {
+  ReachArgs A;
+  __device__ int rows() const { return *(volatile const int*)A.n_reach; }
+  __device__ void features(int row, float f[9]) const {
+    const float* t = A.targets + 12 * (size_t)row;
+    f[0] = __ldg(t + 9); f[1] = __ldg(t + 10); f[2] = __ldg(t + 11);
+    f[3] = __ldg(t + 0); f[4] = __ldg(t + 3); f[5] = __ldg(t + 6);
+    f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
+  }
+  __device__ void emit(int row, bool valid, float logit) const {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const bool pass = valid && logit >= A.tau;
+    const unsigned mp = __ballot_sync(0xFFFFFFFFu, pass);
+    if (mp) {
+      const int leader = __ffs(mp) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(A.n_ik, __popc(mp));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (pass) A.list_ik[base + __popc(mp & lt)] = row;
+    }
+    const bool rej = valid && !pass;
+    int c = 0;
+    bool retry = false;
+    if (rej) {
+      c = A.list_reach[row];
+      const int r = A.st.rc[c];
+      retry = r < A.max_retries;
+      if (retry) A.st.rc[c] = (uint16_t)(r + 1);
+    }
+    const unsigned mr = __ballot_sync(0xFFFFFFFFu, retry);
+    if (mr) {
+      const int leader = __ffs(mr) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(A.n_gen, __popc(mr));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (retry) A.list_gen[base + __popc(mr & lt)] = c;
+    }
+    const unsigned mj = __ballot_sync(0xFFFFFFFFu, rej);
+    if (lane == 0 && mj) atomicAdd(&A.stats[3], (unsigned long long)__popc(mj));
+  }
+};
+
 // Top-down grasp of the candidate's current object k: position = top centre
 // of its box, tool z = -world z, tool x along the object's yaw; expressed in
 // the template's robot base frame (x, y, z, yaw). R row-major, then p.
 __global__ void reach_targets_kernel(ReachArgs A) {
   const int n = *(volatile const int*)A.n_reach;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = A.list_reach[i];
-    const int t = __ldg(&A.cand_t[c]);
-    const TmplInfo& T = A.tinfo[t];
-    const int k = A.st.kc[c];
-    const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * T.nt;
-    const float4 p = A.poses[pbase + k];
-    const float hz = __ldg(&A.b.obj_half[4 * (T.o0 + k) + 2]);
-    const float4 base = __ldg(reinterpret_cast<const float4*>(A.b.tmpl_base) + t);
-    float sb, cb, sp, cp;
-    sincosf(base.w, &sb, &cb);
-    sincosf(p.w - base.w, &sp, &cp);
-    const float wx = p.x - base.x, wy = p.y - base.y, wz = p.z + hz - base.z;
-    float* o = A.targets + 12 * (size_t)i;
-    o[0] = cp; o[1] = sp; o[2] = 0.f;
-    o[3] = sp; o[4] = -cp; o[5] = 0.f;
-    o[6] = 0.f; o[7] = 0.f; o[8] = -1.f;
-    o[9] = cb * wx + sb * wy;
-    o[10] = -sb * wx + cb * wy;
-    o[11] = wz;
-  }
-}
-
-// Gate: logit >= tau goes on to IK, the rest retries (or ends invalid).
-__global__ void gate_split_kernel(ReachArgs A) {
-  const int n = *(volatile const int*)A.n_reach;
-  unsigned long long rejected = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (A.logits[i] >= A.tau) {
-      A.list_ik[atomicAdd(A.n_ik, 1)] = i;
-    } else {
-      ++rejected;
-      const int c = A.list_reach[i];
-      reach_advance(A, c, A.st.kc[c], A.st.rc[c], 0, false);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rejected += __shfl_xor_sync(0xFFFFFFFFu, rejected, o);
-  if ((threadIdx.x & 31) == 0 && rejected) atomicAdd(&A.stats[3], rejected);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    grasp_target(A, A.list_reach[i], A.targets + 12 * (size_t)i);
 }
 
 // Exact IK, one warp per entry; seeds keyed by (candidate, object, try).
@@ -935,7 +968,7 @@ int generate_rounds(int reach_objects, int max_retries) {
 }
 
 // Scratch: round lists G[3], reach queues Q[2] and gate-passed lists IK[2]
-// (int32 [n] each), two slots of grasp targets (12 floats) and logits; counts
+// (int32 [n] each), two slots of grasp targets (12 floats); counts
 // (list lengths per round [NR + 2], reach queue and IK lengths per round
 // [NR] each); work counters (generation claims per round, the chained
 // launch's, IK claims per round); the per-candidate state (object, try,
@@ -952,7 +985,7 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   const size_t NR = (size_t)generate_rounds(b.max_obj, max_retries);
   GenScratch L;
   L.lists = 0;
-  L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 13 * n * sizeof(float));
+  L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 12 * n * sizeof(float));
   L.counters = up(L.counts + ((NR + 2) + 2 * NR) * sizeof(int));
   L.kc = up(L.counters + (2 * NR + 1) * sizeof(unsigned int));
   L.rc = up(L.kc + (size_t)b.n_cand);
@@ -1002,7 +1035,6 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int32_t* IK[2] = {ib + 5 * (size_t)n, ib + 6 * (size_t)n};
   float* fb = reinterpret_cast<float*>(ib + 7 * (size_t)n);
   float* targets[2] = {fb, fb + 12 * (size_t)n};
-  float* logits[2] = {fb + 24 * (size_t)n, fb + 25 * (size_t)n};
   const int NRmax = generate_rounds(K, R);
   int* counts = reinterpret_cast<int*>(sb + SL.counts);
   const int n_counts = (NRmax + 2) + 2 * NRmax;
@@ -1084,6 +1116,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int small_blocks = (n + 255) / 256;
   small_blocks = small_blocks < num_sms * 4 ? small_blocks : num_sms * 4;
   if (small_blocks < 1) small_blocks = 1;
+  const MlpTcWeights gate_w = a.gate ? mlp_tc_weights(a.gate) : MlpTcWeights{};
   int ik_per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ik_per_sm, reach_ik_kernel, 128, 0)) != cudaSuccess) return e;
   const int ik_blocks = num_sms * (ik_per_sm > 0 ? ik_per_sm : 1);
@@ -1123,7 +1156,6 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.list_reach = Q[i % 2];
     ra.n_reach = cnt_reach + i;
     ra.targets = targets[i % 2];
-    ra.logits = logits[i % 2];
     ra.list_ik = IK[i % 2];
     ra.n_ik = cnt_ik + i;
     ra.list_gen = G[(i + 2) % 3];
@@ -1131,10 +1163,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.claim = counters + NRmax + 1 + i;
     if (a.timer) a.timer->begin(1, sr);
     reach_targets_kernel<<<small_blocks, 256, 0, sr>>>(ra);
-    if (ra.gated) {
-      e = mlp_infer_counted(a.gate, ra.targets, ra.n_reach, n, logits[i % 2], a.status, num_sms, sr);
+    if (ra.gated) {  // gate forward pass and decision in one launch
+      e = launch_mlp_tc(gate_w, GateIO{ra}, n, a.status, num_sms, sr);
       if (e != cudaSuccess) return e;
-      gate_split_kernel<<<small_blocks, 256, 0, sr>>>(ra);
     }
     if (a.timer) {
       a.timer->end(sr);

@@ -127,6 +127,8 @@ struct MlpTcWeights {
   const float* inv_sigma;  // [9]
   int off_b1, off_b2, off_b3, off_b4;
 };
+// The tensor-core view of a surrogate's weights.
+MlpTcWeights mlp_tc_weights(const MlpState* S);
 // Logits of n rows of targets (or min(n, *n_dev) when n_dev is set) on
 // tcgen05; a wait that gives up latches kDevTimeout into *status.
 cudaError_t mlp_forward_tc(const MlpTcWeights& w, const float* targets, int n, const int* n_dev, float* logits,

@@ -565,6 +565,9 @@ static cudaError_t smem_opt_in() {
   return e;
 }
 
+static MlpTcWeights tc_view(const MlpState& S);
+MlpTcWeights mlp_tc_weights(const MlpState* S) { return tc_view(*S); }
+
 static MlpTcWeights tc_view(const MlpState& S) {
   MlpTcWeights w;
   w.params = S.params;

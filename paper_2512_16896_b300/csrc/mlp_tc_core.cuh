@@ -1,0 +1,357 @@
+#pragma once
+// Surrogate forward pass on the 5th-generation tensor cores (tcgen05 + TMEM):
+// logits of the MLP 9 -> 256 -> 256 -> 256 -> 1 (SiLU) with BF16 operands and
+// FP32 accumulation, rounded at the same points as the training forward pass
+// (standardised input, every SiLU output and the weight copies in bf16;
+// biases FP32), for the learned reachability gate of Sec. IV-E. The SiLU uses
+// the SFU's approximate exponential and reciprocal (relative error ~1e-6).
+//
+// One persistent CTA of 8 warps per SM works through tiles of 128 rows:
+//   layer 1  A = features [128 x 16],  B = W1 [256 x 16]   -> TMEM D [128 x 256] f32
+//   layer 2  A = h1 [128 x 256],       B = W2 [256 x 256]  -> TMEM D
+//   layer 3  A = h2,                   B = W3              -> TMEM D
+// D row i lives in TMEM lane i. Warp w reads lanes 32 (w % 4) .. + 31 and
+// columns 128 (w / 4) .. + 127 (tcgen05.ld), adds the bias, applies SiLU,
+// rounds to bf16 and writes the next layer's A operand; after layer 3 it
+// forms its half of W4 . h3 and the two halves are summed through shared
+// memory. Operands sit in shared memory in the canonical no-swizzle K-major
+// layout of core matrices (8 rows x 16 bytes): core matrices adjacent in K are
+// 128 bytes apart (leading byte offset), 8-row groups K / 8 * 128 bytes apart
+// (stride byte offset). W2 and W3 arrive by 1-D bulk copies (cp.async.bulk)
+// from weight copies kept in that layout, the copy of the next weights
+// overlapping the current epilogue. One thread issues the MMAs and commits
+// them to an mbarrier. Every wait is bounded: on timeout the CTA latches
+// kDevTimeout, waits (bounded) for its own copies and MMAs still in flight,
+// frees TMEM and returns.
+//
+// Core of the tensor-core surrogate forward pass (tcgen05 + TMEM), templated
+// on where its rows come from and where their logits go; included by the
+// plain inference (mlp_tc.cu) and by the generation loop's fused gate.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sc {
+
+namespace {
+
+constexpr int H = 256;
+constexpr int TILE = 128;
+constexpr int THREADS = 256;
+constexpr int SM_W1 = 0;                      // [256][16] bf16 canonical, 8 KB
+constexpr int SM_W = SM_W1 + 8192;            // [256][256] bf16 canonical, 128 KB
+constexpr int SM_A = SM_W + 131072;           // [128][256] bf16 canonical, 64 KB
+constexpr int SM_BIAS = SM_A + 65536;         // b1 b2 b3 W4 as f32, 4 KB
+constexpr int SM_PART = SM_BIAS + 4 * H * 4;  // [128] partial logits of the second column half
+constexpr int SM_BAR = SM_PART + TILE * 4;    // 2 mbarriers
+constexpr int SM_TMEM = SM_BAR + 16;          // TMEM base address written by tcgen05.alloc
+constexpr int SM_TOTAL = SM_TMEM + 16;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start, leading and stride byte offsets
+// (all >> 4), descriptor version 1, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Waits until the phase with parity `parity` of the mbarrier has completed;
+// false when the cycle budget runs out first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Arrives on `bar` once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Global -> shared bulk copy of `bytes` (a multiple of 16; 16-byte aligned
+// ends) in 32 KB pieces, completing on `bar` (one arrival + the byte count).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  for (uint32_t off = 0; off < bytes; off += 32768) {
+    const uint32_t n = bytes - off < 32768 ? bytes - off : 32768;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst + off),
+        "l"(static_cast<const char*>(src) + off), "r"(n), "r"(bar)
+        : "memory");
+  }
+}
+
+// 32 consecutive f32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// SiLU a / (1 + e^-a) on the special-function unit: the approximate base-2
+// exponential and reciprocal (__expf, __fdividef) keep the relative error
+// near 1e-6, far below the bf16 rounding that follows, at two SFU operations
+// and a few FMA-pipe operations per activation. For a < -87 the denominator
+// overflows and the result is -0 (the exact value is below 1e-36 in magnitude).
+__device__ __forceinline__ float silu_f(float a) { return __fdividef(a, 1.f + __expf(-a)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+
+// Epilogue of layers 1 and 2 for one thread's row and column half:
+// TMEM -> + bias -> SiLU -> bf16 -> next A operand (canonical, K = 256).
+__device__ __forceinline__ void epilogue_to_a(uint32_t taddr, const float* bias, uint8_t* sa, int row, int col0) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < H / 2; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + c0, r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = col0 + c0 + q * 8 + 2 * j;
+        w[j] = pack_bf16(silu_f(__uint_as_float(r[q * 8 + 2 * j]) + bias[c]),
+                         silu_f(__uint_as_float(r[q * 8 + 2 * j + 1]) + bias[c + 1]));
+      }
+      *reinterpret_cast<uint4*>(sa + canon_offset(row, col0 + c0 + q * 8, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// IO supplies the rows: rows() (the row count, read once), features(row, f)
+// (the 9 raw features of a row < rows(), called by one thread per row) and
+// emit(row, valid, logit) (called by every thread of warps 0..3, one row
+// each, valid = row < rows(), so warp collectives may be used).
+template <class IO>
+__global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = io.rows();
+  const int ntiles = (n + TILE - 1) / TILE;
+  if ((int)blockIdx.x >= ntiles) return;  // uniform for the CTA, before any allocation
+
+  uint8_t* sw1 = smem + SM_W1;
+  uint8_t* sw = smem + SM_W;
+  uint8_t* sa = smem + SM_A;
+  float* sbias = reinterpret_cast<float*>(smem + SM_BIAS);  // b1 | b2 | b3 | W4
+  float* spart = reinterpret_cast<float*>(smem + SM_PART);
+  const uint32_t bar_w = smem_u32(smem + SM_BAR), bar_m = bar_w + 8;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TMEM);
+
+  if (tid == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_m, 1);
+  }
+  for (int i = tid; i < 8192 / 16; i += THREADS)
+    reinterpret_cast<uint4*>(sw1)[i] = __ldg(reinterpret_cast<const uint4*>(w.W1c) + i);
+  for (int i = tid; i < H; i += THREADS) {
+    sbias[i] = __ldg(w.params + w.off_b1 + i);
+    sbias[H + i] = __ldg(w.params + w.off_b2 + i);
+    sbias[2 * H + i] = __ldg(w.params + w.off_b3 + i);
+    sbias[3 * H + i] = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(w.W4)[i]);
+  }
+  const float b4 = __ldg(w.params + w.off_b4);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(H)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int trow = quarter * 32 + lane;  // this thread's row in the tile (= TMEM lane)
+  const int col0 = half * (H / 2);       // this thread's column half
+  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+  constexpr uint32_t idesc = make_idesc(TILE, H);
+
+  uint32_t ph_w = 0, ph_m = 0;
+  bool w_pending = true, m_pending = false, ok = true;
+  if (tid == 0) bulk_load(smem_u32(sw), w.W2c, 131072, bar_w);
+
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // ---- layer-1 operand: standardised features, bf16, K padded to 16
+    if (tid < TILE) {
+      const int row = tile * TILE + tid;
+      float x[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = 0.f;
+      if (row < n) {
+        float f[9];
+        io.features(row, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x[i] = (f[i] - __ldg(w.mu + i)) * __ldg(w.inv_sigma + i);
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        *reinterpret_cast<uint4*>(sa + canon_offset(tid, q * 8, 16)) =
+            make_uint4(pack_bf16(x[q * 8], x[q * 8 + 1]), pack_bf16(x[q * 8 + 2], x[q * 8 + 3]),
+                       pack_bf16(x[q * 8 + 4], x[q * 8 + 5]), pack_bf16(x[q * 8 + 6], x[q * 8 + 7]));
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      tc_mma(tmem, make_desc(smem_u32(sa), 128, 256), make_desc(smem_u32(sw1), 128, 256), idesc, 0);
+      tc_commit(bar_m);
+    }
+    m_pending = true;
+    ok = mbar_wait(bar_m, ph_m);
+    if (ok) {
+      ph_m ^= 1;
+      m_pending = false;
+    }
+    tc_fence_after();
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    epilogue_to_a(taddr, sbias, sa, trow, col0);
+
+    // ---- layers 2 and 3
+    for (int layer = 0; layer < 2; ++layer) {
+      fence_proxy_async();
+      tc_fence_before();
+      ok = mbar_wait(bar_w, ph_w);  // this layer's weights have landed
+      if (ok) {
+        ph_w ^= 1;
+        w_pending = false;
+      }
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int s = 0; s < H / 16; ++s)
+          tc_mma(tmem, make_desc(smem_u32(sa) + 256 * s, 128, 4096), make_desc(smem_u32(sw) + 256 * s, 128, 4096),
+                 idesc, s > 0);
+        tc_commit(bar_m);
+      }
+      m_pending = true;
+      ok = mbar_wait(bar_m, ph_m);
+      if (ok) {
+        ph_m ^= 1;
+        m_pending = false;
+      }
+      tc_fence_after();
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      // The MMAs have read the weight buffer: bring in the next weights (W3,
+      // or the next tile's W2) while the epilogue runs.
+      if (layer == 0 || tile + (int)gridDim.x < ntiles) {
+        if (tid == 0) bulk_load(smem_u32(sw), layer == 0 ? w.W3c : w.W2c, 131072, bar_w);
+        w_pending = true;
+      }
+      if (layer == 0) {
+        epilogue_to_a(taddr, sbias + H, sa, trow, col0);
+      } else {
+        // h3 = bf16(SiLU(acc + b3)); logit = W4 . h3 + b4
+        const float* b3 = sbias + 2 * H + col0;
+        const float* w4 = sbias + 3 * H + col0;
+        float z = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < H / 2; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(taddr + c0, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float h = __bfloat162float(__float2bfloat16_rn(silu_f(__uint_as_float(r[j]) + b3[c0 + j])));
+            z = fmaf(h, w4[c0 + j], z);
+          }
+        }
+        if (half == 1) spart[trow] = z;
+        tc_fence_before();
+        __syncthreads();  // TMEM reads done before the next tile's MMA; partials visible
+        const int row = tile * TILE + trow;
+        if (half == 0) io.emit(row, row < n, (z + spart[trow]) + b4);
+      }
+    }
+  }
+  if (!ok) {
+    if (tid == 0) latch_error(status, kDevTimeout);
+    // Drain what this CTA still has in flight before its TMEM and shared memory go away.
+    if (w_pending) mbar_wait(bar_w, ph_w);
+    if (m_pending) mbar_wait(bar_m, ph_m);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H) : "memory");
+  }
+}
+
+}  // namespace
+
+// Launches mlp_tc_kernel<IO> over at most n_cap rows (the kernel reads the
+// actual count from io.rows()).
+template <class IO>
+cudaError_t launch_mlp_tc(const MlpTcWeights& w, const IO& io, int n_cap, int* status, int num_sms, cudaStream_t s) {
+  if (n_cap <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
+  if (e) return e;
+  const int tiles = (n_cap + TILE - 1) / TILE;
+  const int grid = tiles < num_sms ? tiles : num_sms;
+  mlp_tc_kernel<IO><<<grid, THREADS, SM_TOTAL, s>>>(w, io, status);
+  return cudaGetLastError();
+}
+
+}  // namespace sc
