@@ -163,19 +163,31 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash(name: str) -> str:
-    p = os.path.join(ROOT, "paper_2512_16896_b300", "csrc", name)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+# Sources each measured kernel is compiled from (a traffic record is valid
+# only for the exact sources it was captured on).
+KERNEL_SOURCES = {
+    "reach_ik_kernel": ("generate.cu", "ik_core.cuh", "common.cuh", "kernels.h"),
+    "gen_chain_kernel": ("generate.cu", "collide_core.cuh", "sample_core.cuh", "common.cuh", "kernels.h"),
+}
 
 
-def measured_traffic(kernel_file: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel; else None."""
+def kernel_source_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2512_16896_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + written) per launch from profiles/traffic.json, if
+    they were captured on the current sources of the kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(f"{kernel_file}:{workload}")
-    if not d or d.get("source_hash") != kernel_source_hash(kernel_file):
+    with open(p) as f:
+        d = json.load(f).get(f"{kernel}:{workload}")
+    if not d or d.get("source_hash") != kernel_source_hash(kernel):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -435,7 +447,7 @@ def run_ours(args, wl):
 
     gen_rf, ik_rf = stage_roofline(main)
     dom = gen_rf if gen_rf["ms_per_step"] >= ik_rf["ms_per_step"] else ik_rf
-    dom_file = "generate.cu" if dom is gen_rf else "ik_core.cuh"
+    dom_kernel = "gen_chain_kernel" if dom is gen_rf else "reach_ik_kernel"
     clk = clocks.summary()
     cpu = None
     if world == 1 and args.cpu_budget_s > 0:
@@ -478,7 +490,7 @@ def run_ours(args, wl):
                    "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"],
                    "gen_exhaustive_equivalent_frac": gen_rf["exhaustive_equivalent_frac"]},
         "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": peak_ops / 1e12,
-                     "unit": "Tops/s", "frac": dom["frac"], "traffic": measured_traffic(dom_file, args.workload),
+                     "unit": "Tops/s", "frac": dom["frac"], "traffic": measured_traffic(dom_kernel, args.workload),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "
                                     f"({peak_src} max clock)",
                      "ms_per_step_in_kernel": dom["ms_per_step"], "launches_per_step": dom["launches_per_step"]},
