@@ -57,6 +57,7 @@ import synth  # noqa: E402
 # Algorithmic FP32-pipe operations per evaluated pair ("Rooflines"):
 OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 1 FADD + 4 FFMA
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
+OPS_PER_SPHERE_BOX_COLLIDE = 15  # collision kernel: box frame (9 FFMA), |p| - h (3 FADD), bound (2 FMNMX + FSETP)
 OPS_PER_CULL_TEST = 10     # sphere vs bounding ball: 3 FADD, FMUL + 2 FFMA, 2 FADD (limit), FMUL, FSETP
 OPS_PER_EXHAUSTIVE_PAIR = 9  # one pair of an uncalled exhaustive check (3 FADD, FMUL + 2 FFMA, FADD, FMUL, FSETP)
 OPS_PER_IK_SEED_ITER = 720  # one check + DLS step: FK 280, check 40, error 21, J 63, J J^T 147, Cholesky 50,
@@ -510,14 +511,28 @@ def run_ours(args, wl):
     return 0
 
 
-def kernel_suite(sc, ctx, dev, peak_ops):
-    """Each row's kernel alone, timed with CUDA events on the context's stream."""
+def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
+    """Each row's kernel alone, timed with CUDA events on the context's stream.
+    only: regular expression on the row names (None: every row)."""
+    import re
     import torch
     stream = ctx.stream
     out = {}
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    # exact-minimum collision, shelf batch (65,536 x 32 objects x 64 spheres, 20 boxes)
-    shelf = synth.shelf(seed=1)
+    want = lambda key: only is None or re.search(only, key) is not None
+    if want("collide_exact_min_shelf") or want("collide_decide_shelf"):
+        kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand)
+    if want("ik_topdown_262144") or want("gate_infer_262144") or want("gate_train_epoch_262144"):
+        kernel_suite_ik_gate(sc, ctx, dev, out, want)
+    return out
+
+
+def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
+    import torch
+    stream = ctx.stream
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    # collision, shelf batch (65,536 x 32 objects x 64 spheres, 20 boxes), both modes
+    shelf = synth.shelf(seed=1, n_cand=shelf_cand)
     db = sc.DeviceBatch(shelf, device=dev)
     order = torch.from_numpy(sc.order_by_work(shelf)).to(dev)
     poses, _, _ = sc.sample_poses(ctx, db, seed=1)
@@ -525,7 +540,11 @@ def kernel_suite(sc, ctx, dev, peak_ops):
     md = torch.empty(shelf.n_cand, dtype=torch.float32, device=dev)
     cb = torch.empty(shelf.n_cand, dtype=torch.uint8, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    box_all = shelf.n_cand * int(np.diff(shelf.obj_sph_off)[0:32].sum()) * int(np.diff(shelf.tmpl_obb_off)[0])
     for mode in (0, 1):
+        key = "collide_exact_min_shelf" if mode == 0 else "collide_decide_shelf"
+        if not want(key):
+            continue
         ms, work = [], []
         for i in range(5):
             with torch.cuda.stream(stream):
@@ -537,53 +556,82 @@ def kernel_suite(sc, ctx, dev, peak_ops):
             work.append(sc.collide_last_work(ctx))
             if i >= 2:
                 ms.append(a.elapsed_time(b))
-        ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX for p, q in work[2:]])
-        key = "collide_exact_min_shelf" if mode == 0 else "collide_decide_shelf"
+        ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE for p, q in work[2:]])
         out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": shelf.n_cand / (np.mean(ms) / 1e3),
                     "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
                     "box_pairs": float(np.mean([w[1] for w in work[2:]])),
                     "exhaustive_pairs": float(shelf.n_cand * 496 * 64 * 64),
-                    "roofline_frac": float(ops / (np.mean(ms) / 1e3) / peak_ops)}
+                    "exhaustive_box_pairs": float(box_all),
+                    "roofline_frac": float(ops / (np.mean(ms) / 1e3) / peak_ops),
+                    # every sphere against every box at the same rate: the work the
+                    # per-(object, box) ball cull saves, as a fraction of the FP32 peak
+                    "box_exhaustive_equivalent_frac": float(box_all * OPS_PER_SPHERE_BOX_COLLIDE /
+                                                            (np.mean(ms) / 1e3) / peak_ops)}
     del db, poses, col, md, cb
-    # IK: 262,144 top-down grasp targets over the tabletop region, 32 seeds x 100 iterations
-    arm = sc.make_arm(*synth.arm_arrays())
+
+
+def kernel_suite_ik_gate(sc, ctx, dev, out, want):
+    import torch
+    stream = ctx.stream
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     tg = torch.from_numpy(synth.topdown_targets(seed=3, n=262144)).to(dev)
-    ms = []
-    for i in range(4):
-        a, b = ev()
-        a.record(stream)
-        r, q, err = sc.ik_reach(ctx, arm, sc.ik_params(seed=3), tg)
-        b.record(stream)
-        b.synchronize()
-        if i >= 1:
-            ms.append(a.elapsed_time(b))
-    out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / (np.mean(ms) / 1e3),
-                                "reachable": float(r.float().mean().item())}
+    if want("ik_topdown_262144"):
+        # IK: 262,144 top-down grasp targets over the tabletop region, 32 seeds x 100 iterations
+        arm = sc.make_arm(*synth.arm_arrays())
+        ms = []
+        for i in range(4):
+            a, b = ev()
+            a.record(stream)
+            r, q, err = sc.ik_reach(ctx, arm, sc.ik_params(seed=3), tg)
+            b.record(stream)
+            b.synchronize()
+            if i >= 1:
+                ms.append(a.elapsed_time(b))
+        out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / (np.mean(ms) / 1e3),
+                                    "reachable": float(r.float().mean().item())}
+    if not (want("gate_infer_262144") or want("gate_train_epoch_262144")):
+        return
     # gate inference and one training epoch
     net = sc.Surrogate(ctx, seed=1)
-    ms = []
-    for i in range(4):
+    flops = 2.0 * 262144 * (9 * 256 + 2 * 256 * 256 + 256)
+    if want("gate_infer_262144"):
+        ms = []
+        for i in range(4):
+            a, b = ev()
+            a.record(stream)
+            net.infer(tg)
+            b.record(stream)
+            b.synchronize()
+            if i >= 1:
+                ms.append(a.elapsed_time(b))
+        out["gate_infer_262144"] = {"ms": float(np.mean(ms)), "samples_per_s": 262144 / (np.mean(ms) / 1e3),
+                                    "tflops": flops / (np.mean(ms) / 1e3) / 1e12}
+    if want("gate_train_epoch_262144"):
+        y = (torch.rand(262144, device=dev) < 0.5).to(torch.uint8)
         a, b = ev()
         a.record(stream)
-        net.infer(tg)
+        net.train(tg, y, sc.train_params(epochs=1, batch=4096))
         b.record(stream)
         b.synchronize()
-        if i >= 1:
-            ms.append(a.elapsed_time(b))
-    flops = 2.0 * 262144 * (9 * 256 + 2 * 256 * 256 + 256)
-    out["gate_infer_262144"] = {"ms": float(np.mean(ms)), "samples_per_s": 262144 / (np.mean(ms) / 1e3),
-                                "tflops": flops / (np.mean(ms) / 1e3) / 1e12}
-    y = (torch.rand(262144, device=dev) < 0.5).to(torch.uint8)
-    a, b = ev()
-    a.record(stream)
-    net.train(tg, y, sc.train_params(epochs=1, batch=4096))
-    b.record(stream)
-    b.synchronize()
-    t = a.elapsed_time(b)
-    out["gate_train_epoch_262144"] = {"ms": t, "samples_per_s": 262144 / (t / 1e3),
-                                      "tflops": 3 * flops / (t / 1e3) / 1e12}
+        t = a.elapsed_time(b)
+        out["gate_train_epoch_262144"] = {"ms": t, "samples_per_s": 262144 / (t / 1e3),
+                                          "tflops": 3 * flops / (t / 1e3) / 1e12}
     net.close()
-    return out
+
+
+def run_kernels(args):
+    """The per-kernel rows alone, on one GPU (profiling entry point)."""
+    import torch
+    import paper_2512_16896_b300 as sc
+    torch.cuda.set_device(0)
+    ctx = sc.Context(0)
+    peaks, _ = read_peaks()
+    peak_ops = ctx.num_sms * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6
+    out = kernel_suite(sc, ctx, torch.device("cuda", 0), peak_ops, only=args.kernel_filter, shelf_cand=args.shelf_cand)
+    ctx.synchronize()
+    print(json.dumps({"kernels": out, "shelf_cand": args.shelf_cand}))
+    ctx.close()
+    return 0
 
 
 def launches_per_step(db, args, reach, gate):
@@ -620,6 +668,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain (eager, ungated) comparison run")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel measurements")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the per-kernel measurements (one JSON line; profiling)")
+    ap.add_argument("--kernel-filter", type=str, default=None, help="regular expression on the kernel row names")
+    ap.add_argument("--shelf-cand", type=int, default=65536, help="shelf candidates of the collision rows")
     ap.add_argument("--train-labels", type=int, default=4194304)
     ap.add_argument("--train-epochs", type=int, default=2)
     args = ap.parse_args()
@@ -630,6 +682,8 @@ def main():
         wl["desc"] = wl["desc"].replace("4096 templates", f"{T} templates")
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.kernels_only:
+        return run_kernels(args)
     return run_ours(args, wl)
 
 

@@ -170,9 +170,10 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
  * ctas_per_sm: resident CTAs per SM the grid is sized for (1..8).
  * decide_only: 0 = exact minimum distance for every candidate; 1 = decide
  * only: a candidate stops at its first pair closer than -1e-5 m (a certain
- * collision); collide and band are the same as in mode 0, and min_dist is the
- * exact minimum only where it is <= 1e-5 m (elsewhere some distance > 1e-5 m
- * or FLT_MAX). */
+ * collision); collide and band are the same as in mode 0. min_dist is the
+ * exact minimum inside the band (|d| <= 1e-5 m); a certain collision reports
+ * some distance below -1e-5 m, a clear candidate some distance above 1e-5 m
+ * or FLT_MAX. */
 typedef struct {
   int32_t threads, a_per_lane, seg_len, ctas_per_sm;
   int32_t decide_only;

@@ -1,7 +1,17 @@
-// Collision kernel of sc_collide / sc_collide_ex: persistent CTAs take
+// Collision kernel of sc_collide / sc_collide_ex (Sec. IV-B one transform
+// per instance, Sec. IV-D batched collision checking). Persistent CTAs take
 // candidates from the caller's list through a global atomic counter (list the
-// heaviest first) and reduce each candidate's minimum signed distance with
-// the device core in collide_core.cuh (exact minimum, or decide-only mode).
+// heaviest first); one CTA reduces one candidate's minimum signed distance
+// (exact minimum, or decide-only mode) at a time:
+//  * stage_*: the candidate's objects [0, n) are moved to shared memory once,
+//    spheres in the world frame relative to the position of object 0, with
+//    each object's bounding ball, and the template's world boxes;
+//  * box_units: sphere vs world box, culled per (object, box) by the ball;
+//  * build_units / pair_units: the pair set {(i, j): obj(i) < obj(j),
+//    obj(j) >= f} is cut into units (A block of 32*APL consecutive spheres,
+//    one per lane per slot) x (B segment of up to seg_len spheres); warps
+//    pull units from a CTA-local counter and sweep them with the prune test
+//    of collide_core.cuh.
 #include "collide_core.cuh"
 #include "kernels.h"
 
@@ -11,14 +21,357 @@ namespace {
 
 using namespace core;
 
+struct Layout {
+  int W, beta, oid, off, opose, osc, obb, blk_lo, blk_mend, blk_pref, total, nb_max, cap;
+};
+
+__host__ __device__ inline Layout make_layout(int max_sph, int max_obj, int apl) {
+  Layout L;
+  L.cap = ((max_sph + kPad + 7) / 8) * 8;
+  L.nb_max = L.cap / (32 * apl) + 2;
+  L.W = 0;
+  L.beta = align16(L.W + 16 * L.cap);
+  L.oid = align16(L.beta + 4 * L.cap);
+  L.off = align16(L.oid + L.cap);
+  L.opose = align16(L.off + 4 * (max_obj + 1));
+  L.osc = align16(L.opose + 16 * max_obj);
+  L.obb = align16(L.osc + 8 * max_obj);
+  L.blk_lo = align16(L.obb + 4 * 16 * kMaxObbPerTemplate);
+  L.blk_mend = align16(L.blk_lo + 4 * L.nb_max);
+  L.blk_pref = align16(L.blk_mend + 4 * L.nb_max);
+  L.total = align16(L.blk_pref + 4 * (L.nb_max + 1));
+  return L;
+}
+
+struct Smem {
+  float4* W;
+  float* beta;
+  uint8_t* oid;
+  int* off;
+  float4* opose;
+  float2* osc;  // sin, cos of each object's yaw; once the spheres are staged,
+                // (radius of its bounding ball about its position, 0)
+  float* obbd;
+  int* blk_lo;
+  int* blk_mend;
+  int* blk_pref;
+};
+
+__device__ __forceinline__ Smem smem_view(unsigned char* base, const Layout& L) {
+  Smem s;
+  s.W = reinterpret_cast<float4*>(base + L.W);
+  s.beta = reinterpret_cast<float*>(base + L.beta);
+  s.oid = base + L.oid;
+  s.off = reinterpret_cast<int*>(base + L.off);
+  s.opose = reinterpret_cast<float4*>(base + L.opose);
+  s.osc = reinterpret_cast<float2*>(base + L.osc);
+  s.obbd = reinterpret_cast<float*>(base + L.obb);
+  s.blk_lo = reinterpret_cast<int*>(base + L.blk_lo);
+  s.blk_mend = reinterpret_cast<int*>(base + L.blk_mend);
+  s.blk_pref = reinterpret_cast<int*>(base + L.blk_pref);
+  return s;
+}
+
+// CTA-wide scalars (a static __shared__ object of the kernel).
+struct CtaShared {
+  int item;
+  int unit_next, total_units, nb;
+  int best_key;            // MIN: CTA-wide running minimum (float_key)
+  int r2max_key, rmax_key;
+  int hit;                 // DECIDE: a certain collision was found
+  float warp_min[32];
+};
+
+// largest k in [0, n) with arr[k] <= v, for non-decreasing arr with arr[0] <= v
+__device__ __forceinline__ int upper_index(const int* arr, int n, int v) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (arr[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Poses, sin/cos of yaw and sphere offsets of objects [0, n).
+__device__ __forceinline__ void stage_objects(const sc_scene_batch& b, const float4* poses, int64_t pbase, int o0,
+                                              int s0, int n, const Smem& sm, int tid, int nthr) {
+  for (int k = tid; k < n; k += nthr) {
+    const float4 p = poses[pbase + k];
+    float sn, cs;
+    sincosf(p.w, &sn, &cs);
+    sm.opose[k] = p;
+    sm.osc[k] = make_float2(sn, cs);
+    sm.off[k] = __ldg(&b.obj_sph_off[o0 + k]) - s0;
+  }
+  if (tid == 0) sm.off[n] = __ldg(&b.obj_sph_off[o0 + n]) - s0;
+}
+
+// Spheres [0, S) of the staged objects in the world frame relative to object
+// 0's position, plus |c|^2 - r^2; kPad far-away dummies after them; and each
+// object's bounding-ball radius about its position, max |l| + r over its
+// local spheres l, in place of its (no longer needed) sin/cos. Groups of gl lanes (8, 16 or 32, from the mean spheres
+// per object) take one object at a time, so a sphere's object needs no search
+// and each object's pose is read once per group.
+__device__ __forceinline__ void stage_spheres(const sc_scene_batch& b, int s0, int n, int S, const Smem& sm,
+                                              CtaShared& sh, int tid, int nthr, int lane) {
+  const float4 ref = sm.opose[0];
+  float r2max = 0.f, rmx = 0.f;
+  const int mean = S / n;
+  const int gl = mean > 16 ? 32 : mean > 8 ? 16 : 8;
+  const int ngrp = nthr / gl;
+  const float4* local = reinterpret_cast<const float4*>(b.sph_local) + s0;
+#pragma unroll 1
+  for (int k0 = 0; k0 < n; k0 += ngrp) {  // same trip count in every lane (group shuffles below)
+    const int k = k0 + tid / gl;
+    float rad = 0.f;
+    if (k < n) {
+      const int lo = sm.off[k], hi = sm.off[k + 1];
+      const float4 p = sm.opose[k];
+      const float2 sc2 = sm.osc[k];
+      const float tx = p.x - ref.x, ty = p.y - ref.y, tz = p.z - ref.z;
+#pragma unroll 2
+      for (int q = lo + (tid & (gl - 1)); q < hi; q += gl) {
+        const float4 l = __ldg(local + q);
+        const float x = tx + (sc2.y * l.x - sc2.x * l.y);
+        const float y = ty + (sc2.x * l.x + sc2.y * l.y);
+        const float z = tz + l.z;
+        const float c2 = x * x + y * y + z * z;
+        sm.W[q] = make_float4(x, y, z, l.w);
+        sm.beta[q] = c2 - l.w * l.w;
+        sm.oid[q] = (uint8_t)k;
+        r2max = fmaxf(r2max, c2);
+        rmx = fmaxf(rmx, l.w);
+        rad = fmaxf(rad, sqrtf(l.x * l.x + l.y * l.y + l.z * l.z) + l.w);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      if (o < gl) rad = fmaxf(rad, __shfl_xor_sync(0xFFFFFFFFu, rad, o));
+    // the group's lanes read osc[k] before the shuffles above
+    if (k < n && (tid & (gl - 1)) == 0) sm.osc[k] = make_float2(rad, 0.f);
+  }
+  for (int q = S + tid; q < S + kPad; q += nthr) {
+    sm.W[q] = make_float4(1e6f, 1e6f, 1e6f, 0.f);
+    sm.beta[q] = 3e12f;
+    sm.oid[q] = 255;
+  }
+  r2max = -warp_min(-r2max);
+  rmx = -warp_min(-rmx);
+  if (lane == 0) {
+    atomicMax(&sh.r2max_key, __float_as_int(r2max));  // non-negative floats order as ints
+    atomicMax(&sh.rmax_key, __float_as_int(rmx));
+  }
+}
+
+// World boxes: columns of R, minus R^T (centre - object 0's position), half
+// extents. A sphere centre w (relative to object 0) has box-frame
+// coordinates p = R^T w - R^T (centre - ref): three FMAs per axis.
+__device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int bx0, int nobb, const Smem& sm, int tid,
+                                            int nthr) {
+  const float4 ref = sm.opose[0];
+  for (int k = tid; k < nobb; k += nthr) {
+    const float* o = b.obb + 12 * (bx0 + k);
+    float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
+    const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx *= inv; qy *= inv; qz *= inv; qw *= inv;
+    float* d = sm.obbd + 16 * k;
+    // R (row-major) of the unit quaternion; stored by columns
+    d[0] = 1.f - 2.f * (qy * qy + qz * qz); d[1] = 2.f * (qx * qy + qz * qw); d[2] = 2.f * (qx * qz - qy * qw);
+    d[3] = 2.f * (qx * qy - qz * qw); d[4] = 1.f - 2.f * (qx * qx + qz * qz); d[5] = 2.f * (qy * qz + qx * qw);
+    d[6] = 2.f * (qx * qz + qy * qw); d[7] = 2.f * (qy * qz - qx * qw); d[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    const float cx = __ldg(o + 0) - ref.x, cy = __ldg(o + 1) - ref.y, cz = __ldg(o + 2) - ref.z;
+    d[9] = -(d[0] * cx + d[1] * cy + d[2] * cz);
+    d[10] = -(d[3] * cx + d[4] * cy + d[5] * cz);
+    d[11] = -(d[6] * cx + d[7] * cy + d[8] * cz);
+    d[12] = __ldg(o + 8); d[13] = __ldg(o + 9); d[14] = __ldg(o + 10); d[15] = 0.f;
+  }
+}
+
+// Thread 0: work units for pairs (i, j), obj(i) < obj(j), obj(j) in [f, n).
+__device__ __forceinline__ void build_units(int f, int n, int S, int BA, int seg_len, const Smem& sm, CtaShared& sh) {
+  int total = 0, nb = 0;
+  if (f < n) {
+    const int B_lo = sm.off[f];
+    const int A_end = sm.off[n - 1];
+    if (A_end > 0) {
+      nb = (A_end + BA - 1) / BA;
+      for (int bk = 0; bk < nb; ++bk) {
+        const int i0 = bk * BA, i1 = min(i0 + BA, A_end);
+        const int lo = max(B_lo, sm.off[sm.oid[i0] + 1]);
+        const int mend = max(lo, max(B_lo, sm.off[sm.oid[i1 - 1] + 1]));
+        sm.blk_lo[bk] = lo;
+        sm.blk_mend[bk] = mend;
+        sm.blk_pref[bk] = total;
+        if (S > lo) total += (S - lo + seg_len - 1) / seg_len;
+      }
+    }
+  }
+  sm.blk_pref[nb] = total;
+  sh.total_units = total;
+  sh.nb = nb;
+  sh.unit_next = 0;
+}
+
+// Box-frame excess q = |R^T (c - centre)| - h of a point c (relative to
+// object 0) against a staged box (c0..c3, see stage_boxes), and its largest
+// component: a lower bound on the box's signed distance, 1-Lipschitz in c.
+struct BoxQ {
+  float x, y, z, m;
+};
+
+__device__ __forceinline__ BoxQ box_q(const float4& c0, const float4& c1, const float4& c2, const float4& c3,
+                                      float wx, float wy, float wz) {
+  // c0 = R col 0 | col 1 x; c1 = col 1 yz | col 2 xy; c2 = col 2 z | -R^T centre; c3 = half extents
+  const float px = fmaf(c0.x, wx, fmaf(c0.y, wy, fmaf(c0.z, wz, c2.y)));
+  const float py = fmaf(c0.w, wx, fmaf(c1.x, wy, fmaf(c1.y, wz, c2.z)));
+  const float pz = fmaf(c1.z, wx, fmaf(c1.w, wy, fmaf(c2.x, wz, c2.w)));
+  BoxQ q;
+  q.x = fabsf(px) - c3.x;
+  q.y = fabsf(py) - c3.y;
+  q.z = fabsf(pz) - c3.z;
+  q.m = fmaxf(q.x, fmaxf(q.y, q.z));
+  return q;
+}
+
+// Sphere vs world box for the objects [f, n), one (object, box) unit at a
+// time. Broad phase: the object's bounding ball (centre c, radius R) gives
+// L = max(q(c)) - R, below every sphere's max(q) - r and hence below every
+// sphere's distance to the box; a unit is skipped when L (with kBroadMargin
+// for FP32 rounding) cannot reach the threshold. Narrow phase: the warp's
+// lanes take the object's spheres; the exact box SDF minus r is computed
+// where max(q) - r beats the threshold thr (m in MIN, the band in DECIDE),
+// tested as max(q) < t with t = thr + r rounded up: a computed distance is
+// never below the computed max(q) - r (the sqrt of a sum holding max(q)^2 is
+// at least max(q); rounding is monotone), so a skipped pair cannot beat thr.
+// PASS 0 (DECIDE): units with L < band; stops at the first certain collision
+// (below -band), its own or one another warp raised in `hit`.
+// PASS 1 (MIN): units whose balls come within kBroadMargin of the box, which
+// is where a collision's depth is found. PASS 2 (MIN): the other units with L below the
+// CTA-wide minimum so far (read once per 32 units).
+template <int PASS>
+__device__ __forceinline__ float box_units(const Smem& sm, CtaShared& sh, int f, int n, int nobb, float m, int lane,
+                                           int warp, int nwarps, unsigned long long& my_box) {
+  constexpr bool DECIDE = PASS == 0;
+  const float4* bd = reinterpret_cast<const float4*>(sm.obbd);
+  const float4 ref = sm.opose[0];
+  const int nu = (n - f) * nobb;
+#pragma unroll 1
+  for (int u0 = warp * 32; u0 < nu; u0 += nwarps * 32) {
+    float lim = (DECIDE ? kBand : 0.f) + kBroadMargin;
+    if (PASS == 2) lim = fminf(m, key_float(*(volatile int*)&sh.best_key)) + kBroadMargin;
+    const int u = u0 + lane;
+    bool need = false;
+    if (u < nu) {
+      const int o = f + u / nobb, k = u - (o - f) * nobb;
+      const float4 p = sm.opose[o];
+      const BoxQ q = box_q(bd[4 * k], bd[4 * k + 1], bd[4 * k + 2], bd[4 * k + 3], p.x - ref.x, p.y - ref.y,
+                           p.z - ref.z);
+      const float L = q.m - sm.osc[o].x;
+      need = PASS == 2 ? (L >= kBroadMargin && L < lim) : L < lim;
+    }
+    unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
+#pragma unroll 1
+    while (mask) {
+      const int uu = u0 + __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int o = f + uu / nobb, k = uu - (o - f) * nobb;
+      const float4 c0 = bd[4 * k], c1 = bd[4 * k + 1], c2 = bd[4 * k + 2], c3 = bd[4 * k + 3];
+      const int lo = sm.off[o], hi = sm.off[o + 1];
+#pragma unroll 2
+      for (int i = lo + lane; i < hi; i += 32) {
+        const float4 w = sm.W[i];
+        const BoxQ q = box_q(c0, c1, c2, c3, w.x, w.y, w.z);
+        if (q.m < __fadd_ru(DECIDE ? kBand : m, w.w)) {
+          const float ox = fmaxf(q.x, 0.f), oy = fmaxf(q.y, 0.f), oz = fmaxf(q.z, 0.f);
+          m = fminf(m, sqrtf(ox * ox + oy * oy + oz * oz) + fminf(q.m, 0.f) - w.w);
+        }
+      }
+      if (lane == 0) my_box += (unsigned long long)(hi - lo);
+      if (DECIDE) {
+        if (__any_sync(0xFFFFFFFFu, m < -kBand)) {
+          if (lane == 0) *(volatile int*)&sh.hit = 1;
+          return m;
+        }
+        // another warp's certain collision (the vote keeps the exit warp-uniform)
+        if (__any_sync(0xFFFFFFFFu, *(volatile int*)&sh.hit != 0)) return m;
+      }
+    }
+    if (DECIDE && __any_sync(0xFFFFFFFFu, *(volatile int*)&sh.hit != 0)) return m;
+    if (PASS == 2) {
+      const float wm = warp_min(m);
+      if (lane == 0 && wm < kFarSentinel) atomicMin(&sh.best_key, float_key(wm));
+    }
+  }
+  return m;
+}
+
+// Warps pull units until none are left; returns the warp's result (MIN: its
+// running minimum; DECIDE: the minimum of the exact distances it computed).
+template <int APL, bool DECIDE>
+__device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f, int n, int S, int seg_len, float m,
+                                            float rmax, float eps, int lane, unsigned long long& my_pairs) {
+  constexpr int BA = 32 * APL;
+  const int B_lo = sm.off[f];
+  const int A_end = sm.off[n - 1];
+  const int total_units = sh.total_units;
+  const int nb = sh.nb;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&sh.unit_next, 1);
+    u = __shfl_sync(0xFFFFFFFFu, u, 0);
+    if (u >= total_units) break;
+    {  // CTA-wide state, broadcast so m stays warp-uniform
+      int key = 0;
+      if (lane == 0) key = DECIDE ? *(volatile int*)&sh.hit : *(volatile int*)&sh.best_key;
+      key = __shfl_sync(0xFFFFFFFFu, key, 0);
+      if (DECIDE) {
+        if (key) break;
+      } else {
+        m = fminf(m, key_float(key));
+      }
+    }
+    const int bk = upper_index(sm.blk_pref, nb + 1, u);
+    const int seg = u - sm.blk_pref[bk];
+    const int i0 = bk * BA, i1 = min(i0 + BA, A_end);
+    const int lo = sm.blk_lo[bk], mend = sm.blk_mend[bk];
+    const int j0 = lo + seg * seg_len;
+    const int j1 = min(j0 + seg_len, S);
+    ABlock<APL> A;
+#pragma unroll
+    for (int s = 0; s < APL; ++s) {
+      const int i = i0 + s * 32 + lane;
+      const bool valid = i < i1;
+      const float4 w = valid ? sm.W[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      A.ax[s] = -2.f * w.x; A.ay[s] = -2.f * w.y; A.az[s] = -2.f * w.z;
+      A.a2[s] = w.x * w.x + w.y * w.y + w.z * w.z;
+      A.r[s] = w.w;
+      A.bst[s] = valid ? max(B_lo, sm.off[sm.oid[i] + 1]) : INT_MAX;
+    }
+    bool alive = refresh<APL, DECIDE>(A, m, rmax, eps);
+    if (!alive) continue;
+#pragma unroll
+    for (int s = 0; s < APL; ++s)
+      if (A.act[s]) my_pairs += (unsigned long long)max(0, j1 - max(j0, A.bst[s]));
+    const int jm = min(j1, mend);
+    if (j0 < jm) sweep<APL, true, DECIDE>(A, sm.W, sm.beta, j0, jm, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
+    if (alive && max(j0, mend) < j1)
+      sweep<APL, false, DECIDE>(A, sm.W, sm.beta, max(j0, mend), j1, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
+    if (DECIDE && !alive) break;
+  }
+  return m;
+}
+
 struct KArgs {
   sc_scene_batch b;
   CollideLaunch a;
   int seg_len;
 };
 
-template <int APL, int MAXT, bool DECIDE>
-__global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
+// MINB = 2 caps a 512-thread instantiation at 64 registers (four 256-thread
+// CTAs per SM where shared memory allows); MINB = 1 leaves the pair sweep its
+// registers where shared memory holds one or two CTAs per SM anyway.
+template <int APL, int MAXT, int MINB, bool DECIDE>
+__global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CtaShared sh;
   const sc_scene_batch& b = K.b;
@@ -28,11 +381,15 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   unsigned long long my_pairs = 0, my_box = 0;
 
+  // the next candidate is claimed while this one is reduced: thread 0 stores
+  // it in sh.item just before the candidate's last barrier
+  if (tid == 0) sh.item = (int)atomicAdd(a.counter, 1u);
+  __syncthreads();
   for (;;) {
-    if (tid == 0) sh.item = (int)atomicAdd(a.counter, 1u);
-    __syncthreads();
     const int item = sh.item;
     if (item >= a.n_items) break;
+    int next = 0;
+    if (tid == 0) next = (int)atomicAdd(a.counter, 1u);
     const int c = a.active ? __ldg(&a.active[item]) : item;
     const int t = template_of(b, c);
     int o0 = 0, nt = 0, s0 = 0, S = 0, nobb = 0, bx0 = 0;
@@ -57,6 +414,8 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
         a.min_dist[item] = __int_as_float(0x7FC00000);
         a.band[item] = 1;
       }
+      __syncthreads();  // every thread has read sh.item
+      if (tid == 0) sh.item = next;
       __syncthreads();
       continue;
     }
@@ -72,16 +431,35 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
     stage_spheres(b, s0, nt, S, sm, sh, tid, nthr, lane);
     stage_boxes(b, bx0, nobb, sm, tid, nthr);
     __syncthreads();
-    if (tid == 0) build_units(f, nt, S, 32 * APL, K.seg_len, sm, sh);
-    __syncthreads();
     const float rmax = __int_as_float(sh.rmax_key);
     const float eps = 1e-5f * (__int_as_float(sh.r2max_key) + 0.01f);
     float m = kFarSentinel;
-    if (f < nt) {
-      if (nobb > 0) m = box_phase<DECIDE>(sm, nobb, sm.off[f], S, m, tid, nthr, my_box);
+    bool pairs = f < nt;
+    if (pairs && nobb > 0) {
+      if (DECIDE) {
+        m = box_units<0>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+      } else {
+        m = box_units<1>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        const float wm = warp_min(m);
+        if (lane == 0 && wm < kFarSentinel) atomicMin(&sh.best_key, float_key(wm));
+        __syncthreads();
+        // a unit left for pass 2 has L >= kBroadMargin: it can only matter
+        // while the minimum so far is positive
+        if (key_float(*(volatile int*)&sh.best_key) > 0.f)
+          m = box_units<2>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+      }
       m = warp_min(m);
       if (!DECIDE && lane == 0 && m < kFarSentinel) atomicMin(&sh.best_key, float_key(m));
       if (DECIDE && lane == 0 && m < -kBand) *(volatile int*)&sh.hit = 1;
+      __syncthreads();
+      // A computed sphere-pair distance is never below -(r_i + r_j) >= -2 rmax
+      // (rounding is monotone), so a box distance under that already is the
+      // minimum; a certain collision already is the decision.
+      pairs = DECIDE ? !*(volatile int*)&sh.hit : key_float(*(volatile int*)&sh.best_key) >= -2.f * rmax;
+    }
+    if (pairs) {
+      if (tid == 0) build_units(f, nt, S, 32 * APL, K.seg_len, sm, sh);
+      __syncthreads();
       m = pair_units<APL, DECIDE>(sm, sh, f, nt, S, K.seg_len, m, rmax, eps, lane, my_pairs);
     }
     m = warp_min(m);
@@ -94,6 +472,7 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
       a.min_dist[item] = out;
       a.collide[item] = out < 0.f;
       a.band[item] = fabsf(out) <= kBand;
+      sh.item = next;
     }
     __syncthreads();
   }
@@ -109,9 +488,9 @@ __global__ void __launch_bounds__(MAXT) collide_kernel(KArgs K) {
   }
 }
 
-template <int APL, int MAXT, bool DECIDE>
+template <int APL, int MAXT, int MINB, bool DECIDE>
 cudaError_t launch_t(const KArgs& K, const sc_collide_config& cfg, size_t smem, int num_sms, cudaStream_t s) {
-  auto kern = collide_kernel<APL, MAXT, DECIDE>;
+  auto kern = collide_kernel<APL, MAXT, MINB, DECIDE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -127,9 +506,11 @@ cudaError_t launch_t(const KArgs& K, const sc_collide_config& cfg, size_t smem, 
 template <bool DECIDE>
 cudaError_t launch_mode(const KArgs& K, const sc_collide_config& cfg, size_t smem, int num_sms, cudaStream_t s) {
   switch (cfg.a_per_lane) {
-    case 1: return launch_t<1, 1024, DECIDE>(K, cfg, smem, num_sms, s);
-    case 2: return launch_t<2, 1024, DECIDE>(K, cfg, smem, num_sms, s);
-    default: return launch_t<4, 512, DECIDE>(K, cfg, smem, num_sms, s);
+    case 1: return launch_t<1, 1024, 1, DECIDE>(K, cfg, smem, num_sms, s);
+    case 2: return launch_t<2, 1024, 1, DECIDE>(K, cfg, smem, num_sms, s);
+    default:
+      return 3 * (smem + 1024) <= 228 * 1024 ? launch_t<4, 512, 2, DECIDE>(K, cfg, smem, num_sms, s)
+                                              : launch_t<4, 512, 1, DECIDE>(K, cfg, smem, num_sms, s);
   }
 }
 

@@ -134,6 +134,67 @@ def test_collide_random_poses(sc, ctx, make):
     check_collide(gcol, gmd, gband, ocol, omd, oband)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: synth.tabletop(seed=0, n_cand=1024),
+    lambda: synth.shelf(seed=1, n_cand=97, n_obj=32, n_sph=64, n_obb=20),
+    lambda: synth.shelf(seed=3, n_cand=64, n_obj=12, n_sph=100, n_obb=6),
+    lambda: synth.ragged(seed=2, n_templates=24, cand_per_template=3, obj_range=(2, 40), sph_range=(1, 130)),
+])
+def test_collide_decide_only(sc, ctx, make):
+    """Decide-only mode (Sec. IV-D, a yes/no per candidate): the decision and
+    band agree with the oracle; min_dist is above the band (FLT_MAX when no
+    pair was close enough to evaluate) for a clear candidate, below -band for
+    a certain collision, and the exact minimum (bit-identical to the
+    exact-minimum mode) inside the band."""
+    b = make()
+    db = sc.DeviceBatch(b)
+    poses = synth.random_poses(b, seed=5, spread=0.5)
+    pt = torch.from_numpy(poses).cuda()
+    ecol, emd, eband = (x.cpu().numpy() for x in sc.collide(ctx, db, pt))
+    dcol, dmd, dband = (x.cpu().numpy() for x in sc.collide(ctx, db, pt, config=(0, 0, 0, 0, 1)))
+    ctx.synchronize()
+    ocol, omd, oband = oracle.collide(b, poses)
+    band = dband.astype(bool) | oband.astype(bool)
+    assert band.mean() <= 0.01
+    assert np.array_equal(dcol[~band], ocol[~band])
+    clear = ~band & (ocol == 0)
+    assert np.all(dmd[clear] > 1e-5)
+    hit = ~band & (ocol == 1)
+    assert np.all(dmd[hit] < -1e-5)
+    inside = eband.astype(bool) & (np.abs(emd) < 0.999e-5)
+    assert np.array_equal(dband[inside], eband[inside]) and np.array_equal(dmd[inside], emd[inside])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_collide_boxes_near_and_far(sc, ctx, mode):
+    """World boxes at every range from the objects: most candidates clear
+    (the minimum is the distance to the nearest box or pair, including boxes
+    whose distance only a later pass of the per-(object, box) ball cull
+    reaches), some grazing, some inside a box."""
+    rng = np.random.default_rng(31)
+    objs = [[(float(x), float(y), float(z), float(r)) for x, y, z, r in
+             np.c_[rng.uniform(-0.08, 0.08, (n, 3)), rng.uniform(0.01, 0.04, n)]] for n in (40, 7, 70, 1, 33)]
+    obbs = []
+    for i in range(9):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        c = rng.uniform([-1.5, -1.5, 0.0], [1.5, 1.5, 1.0])
+        obbs.append([*c, 0, *q, *rng.uniform(0.02, 0.4, 3), 0])
+    b = tiny_batch(objs, obbs=obbs, n_cand=600)
+    poses = synth.random_poses(b, seed=32, spread=1.6)
+    g = sc.collide(ctx, sc.DeviceBatch(b), torch.from_numpy(poses).cuda(), config=(0, 0, 0, 0, mode))
+    ctx.synchronize()
+    ocol, omd, oband = oracle.collide(b, poses)
+    gcol, gmd, gband = (x.cpu().numpy() for x in g)
+    band = gband.astype(bool) | oband.astype(bool)
+    assert np.array_equal(gcol[~band], ocol[~band])
+    assert 0.2 < ocol.mean() < 0.8, ocol.mean()
+    if mode == 0:
+        check_collide(*g, ocol, omd, oband)
+    else:
+        assert np.all(gmd[~band & (ocol == 0)] > 1e-5) and np.all(gmd[~band & (ocol == 1)] < -1e-5)
+
+
 @pytest.mark.parametrize("first_new", [0, 1, 5, 7, 8, 100])
 def test_collide_first_new(sc, ctx, first_new):
     b = synth.tabletop(seed=6, n_cand=333)
