@@ -520,54 +520,74 @@ def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
     out = {}
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     want = lambda key: only is None or re.search(only, key) is not None
-    if want("collide_exact_min_shelf") or want("collide_decide_shelf"):
+    if any(want(f"collide_{m}_{w}") for m in ("exact_min", "decide") for w in ("shelf", "ragged")):
         kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand)
     if want("ik_topdown_262144") or want("gate_infer_262144") or want("gate_train_epoch_262144"):
         kernel_suite_ik_gate(sc, ctx, dev, out, want)
     return out
 
 
+def exhaustive_work(batch):
+    """Sphere pairs between different objects and sphere-box pairs of every
+    candidate of a batch (the all-pairs check the culls stand in for)."""
+    so, to, bo = batch.obj_sph_off, batch.tmpl_obj_off, batch.tmpl_obb_off
+    ncand = np.diff(batch.cand_tmpl_off)
+    pairs = boxes = 0
+    for t in range(len(to) - 1):
+        n_o = np.diff(so[to[t]:to[t + 1] + 1]).astype(np.int64)
+        S = int(n_o.sum())
+        pairs += int(ncand[t]) * (S * S - int((n_o * n_o).sum())) // 2
+        boxes += int(ncand[t]) * S * int(bo[t + 1] - bo[t])
+    return pairs, boxes
+
+
 def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
+    """Whole-scene collision on sampled poses, both modes: the shelf batch
+    (65,536 x 32 objects x 64 spheres, 20 boxes) and the ragged batch."""
     import torch
     stream = ctx.stream
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    # collision, shelf batch (65,536 x 32 objects x 64 spheres, 20 boxes), both modes
-    shelf = synth.shelf(seed=1, n_cand=shelf_cand)
-    db = sc.DeviceBatch(shelf, device=dev)
-    order = torch.from_numpy(sc.order_by_work(shelf)).to(dev)
-    poses, _, _ = sc.sample_poses(ctx, db, seed=1)
-    col = torch.empty(shelf.n_cand, dtype=torch.uint8, device=dev)
-    md = torch.empty(shelf.n_cand, dtype=torch.float32, device=dev)
-    cb = torch.empty(shelf.n_cand, dtype=torch.uint8, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    box_all = shelf.n_cand * int(np.diff(shelf.obj_sph_off)[0:32].sum()) * int(np.diff(shelf.tmpl_obb_off)[0])
-    for mode in (0, 1):
-        key = "collide_exact_min_shelf" if mode == 0 else "collide_decide_shelf"
-        if not want(key):
+    for name, make in (("shelf", lambda: synth.shelf(seed=1, n_cand=shelf_cand)), ("ragged", lambda: synth.ragged(seed=2))):
+        keys = {0: f"collide_exact_min_{name}", 1: f"collide_decide_{name}"}
+        if not any(want(k) for k in keys.values()):
             continue
-        ms, work = [], []
-        for i in range(5):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            a, b = ev()
-            a.record(stream)
-            sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=(0, 0, 0, 0, mode))
-            b.record(stream)
-            work.append(sc.collide_last_work(ctx))
-            if i >= 2:
-                ms.append(a.elapsed_time(b))
-        ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE for p, q in work[2:]])
-        out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": shelf.n_cand / (np.mean(ms) / 1e3),
-                    "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
-                    "box_pairs": float(np.mean([w[1] for w in work[2:]])),
-                    "exhaustive_pairs": float(shelf.n_cand * 496 * 64 * 64),
-                    "exhaustive_box_pairs": float(box_all),
-                    "roofline_frac": float(ops / (np.mean(ms) / 1e3) / peak_ops),
-                    # every sphere against every box at the same rate: the work the
-                    # per-(object, box) ball cull saves, as a fraction of the FP32 peak
-                    "box_exhaustive_equivalent_frac": float(box_all * OPS_PER_SPHERE_BOX_COLLIDE /
-                                                            (np.mean(ms) / 1e3) / peak_ops)}
-    del db, poses, col, md, cb
+        batch = make()
+        db = sc.DeviceBatch(batch, device=dev)
+        order = torch.from_numpy(sc.order_by_work(batch)).to(dev)
+        poses, _, _ = sc.sample_poses(ctx, db, seed=1)
+        col = torch.empty(batch.n_cand, dtype=torch.uint8, device=dev)
+        md = torch.empty(batch.n_cand, dtype=torch.float32, device=dev)
+        cb = torch.empty(batch.n_cand, dtype=torch.uint8, device=dev)
+        pairs_all, box_all = exhaustive_work(batch)
+        for mode, key in keys.items():
+            if not want(key):
+                continue
+            ms, work = [], []
+            for i in range(5):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                a, b = ev()
+                a.record(stream)
+                sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=(0, 0, 0, 0, mode))
+                b.record(stream)
+                work.append(sc.collide_last_work(ctx))
+                if i >= 2:
+                    ms.append(a.elapsed_time(b))
+            t = np.mean(ms) / 1e3
+            ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE for p, q in work[2:]])
+            out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": batch.n_cand / t,
+                        "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
+                        "box_pairs": float(np.mean([w[1] for w in work[2:]])),
+                        "exhaustive_pairs": float(pairs_all),
+                        "exhaustive_box_pairs": float(box_all),
+                        "collide_frac": float(col.float().mean().item()),
+                        "roofline_frac": float(ops / t / peak_ops),
+                        # every pair at the same rate: the work the bounding-ball
+                        # culls save, as a fraction of the FP32 issue peak
+                        "exhaustive_equivalent_frac": float((pairs_all * OPS_PER_EXHAUSTIVE_PAIR + box_all *
+                                                             OPS_PER_SPHERE_BOX_COLLIDE) / t / peak_ops)}
+        del db, poses, col, md, cb
 
 
 def kernel_suite_ik_gate(sc, ctx, dev, out, want):

@@ -22,7 +22,7 @@ namespace {
 using namespace core;
 
 struct Layout {
-  int W, beta, oid, off, opose, osc, obb, blk_lo, blk_mend, blk_pref, total, nb_max, cap;
+  int W, beta, oid, off, opose, osc, obb, blk_lo, blk_pref, total, nb_max, cap;
 };
 
 __host__ __device__ inline Layout make_layout(int max_sph, int max_obj, int apl) {
@@ -37,8 +37,7 @@ __host__ __device__ inline Layout make_layout(int max_sph, int max_obj, int apl)
   L.osc = align16(L.opose + 16 * max_obj);
   L.obb = align16(L.osc + 8 * max_obj);
   L.blk_lo = align16(L.obb + 4 * 16 * kMaxObbPerTemplate);
-  L.blk_mend = align16(L.blk_lo + 4 * L.nb_max);
-  L.blk_pref = align16(L.blk_mend + 4 * L.nb_max);
+  L.blk_pref = align16(L.blk_lo + 4 * L.nb_max);
   L.total = align16(L.blk_pref + 4 * (L.nb_max + 1));
   return L;
 }
@@ -53,7 +52,6 @@ struct Smem {
                 // (radius of its bounding ball about its position, 0)
   float* obbd;
   int* blk_lo;
-  int* blk_mend;
   int* blk_pref;
 };
 
@@ -67,7 +65,6 @@ __device__ __forceinline__ Smem smem_view(unsigned char* base, const Layout& L) 
   s.osc = reinterpret_cast<float2*>(base + L.osc);
   s.obbd = reinterpret_cast<float*>(base + L.obb);
   s.blk_lo = reinterpret_cast<int*>(base + L.blk_lo);
-  s.blk_mend = reinterpret_cast<int*>(base + L.blk_mend);
   s.blk_pref = reinterpret_cast<int*>(base + L.blk_pref);
   return s;
 }
@@ -196,11 +193,8 @@ __device__ __forceinline__ void build_units(int f, int n, int S, int BA, int seg
     if (A_end > 0) {
       nb = (A_end + BA - 1) / BA;
       for (int bk = 0; bk < nb; ++bk) {
-        const int i0 = bk * BA, i1 = min(i0 + BA, A_end);
-        const int lo = max(B_lo, sm.off[sm.oid[i0] + 1]);
-        const int mend = max(lo, max(B_lo, sm.off[sm.oid[i1 - 1] + 1]));
+        const int lo = max(B_lo, sm.off[sm.oid[bk * BA] + 1]);
         sm.blk_lo[bk] = lo;
-        sm.blk_mend[bk] = mend;
         sm.blk_pref[bk] = total;
         if (S > lo) total += (S - lo + seg_len - 1) / seg_len;
       }
@@ -307,6 +301,11 @@ __device__ __forceinline__ float box_units(const Smem& sm, CtaShared& sh, int f,
 
 // Warps pull units until none are left; returns the warp's result (MIN: its
 // running minimum; DECIDE: the minimum of the exact distances it computed).
+// A unit's B segment is swept one B object ob at a time, each A slot taking
+// part only where its object oa comes before ob and the two bounding balls
+// can reach the threshold: |c_a - c_b| - R_a - R_b (below every sphere pair's
+// distance between the two objects) under thr + kBroadMargin. A B object no
+// slot of the warp reaches is skipped.
 template <int APL, bool DECIDE>
 __device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f, int n, int S, int seg_len, float m,
                                             float rmax, float eps, int lane, unsigned long long& my_pairs) {
@@ -333,10 +332,11 @@ __device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f
     const int bk = upper_index(sm.blk_pref, nb + 1, u);
     const int seg = u - sm.blk_pref[bk];
     const int i0 = bk * BA, i1 = min(i0 + BA, A_end);
-    const int lo = sm.blk_lo[bk], mend = sm.blk_mend[bk];
+    const int lo = sm.blk_lo[bk];
     const int j0 = lo + seg * seg_len;
     const int j1 = min(j0 + seg_len, S);
     ABlock<APL> A;
+    int oa[APL];  // object of each A slot (-1: padding)
 #pragma unroll
     for (int s = 0; s < APL; ++s) {
       const int i = i0 + s * 32 + lane;
@@ -345,17 +345,47 @@ __device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f
       A.ax[s] = -2.f * w.x; A.ay[s] = -2.f * w.y; A.az[s] = -2.f * w.z;
       A.a2[s] = w.x * w.x + w.y * w.y + w.z * w.z;
       A.r[s] = w.w;
-      A.bst[s] = valid ? max(B_lo, sm.off[sm.oid[i] + 1]) : INT_MAX;
+      oa[s] = valid ? (int)sm.oid[i] : -1;
+      A.bst[s] = valid ? max(B_lo, sm.off[oa[s] + 1]) : INT_MAX;
     }
     bool alive = refresh<APL, DECIDE>(A, m, rmax, eps);
     if (!alive) continue;
+    for (int j = max(j0, lo); j < j1;) {
+      const int ob = sm.oid[j];
+      const int je = min(j1, sm.off[ob + 1]);
+      const float4 pb = sm.opose[ob];
+      const float rb = sm.osc[ob].x;
+      const float lim = (DECIDE ? kBand : m) + kBroadMargin + rb;
+      bool any = false, cut = false;
 #pragma unroll
-    for (int s = 0; s < APL; ++s)
-      if (A.act[s]) my_pairs += (unsigned long long)max(0, j1 - max(j0, A.bst[s]));
-    const int jm = min(j1, mend);
-    if (j0 < jm) sweep<APL, true, DECIDE>(A, sm.W, sm.beta, j0, jm, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
-    if (alive && max(j0, mend) < j1)
-      sweep<APL, false, DECIDE>(A, sm.W, sm.beta, max(j0, mend), j1, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
+      for (int s = 0; s < APL; ++s) {
+        if (!A.act[s]) continue;
+        bool near = false;
+        if (oa[s] < ob) {
+          // |c_a - c_b| < thr + margin + R_a + R_b, squared (false if the right side is <= 0)
+          const float4 pa = sm.opose[oa[s]];
+          const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+          const float t = lim + sm.osc[oa[s]].x;
+          near = t > 0.f && dx * dx + dy * dy + dz * dz < t * t;
+        }
+        if (near) {
+          my_pairs += (unsigned long long)(je - j);
+          any = true;
+        } else {
+          A.al[s] = kRetired;  // left out of this B object only
+          cut = true;
+        }
+      }
+      bool fresh = false;  // every slot's threshold already re-derived
+      if (__any_sync(0xFFFFFFFFu, any)) {
+        const float m0 = m;
+        sweep<APL, false, DECIDE>(A, sm.W, sm.beta, j, je, S, m, rmax, eps, &sh.best_key, &sh.hit, alive);
+        if (!alive) break;  // DECIDE: a certain collision; MIN: every slot retired
+        fresh = !DECIDE && m != m0;  // MIN re-derives the thresholds when m drops
+      }
+      if (!fresh && __any_sync(0xFFFFFFFFu, cut)) alive = refresh<APL, DECIDE>(A, m, rmax, eps);
+      j = je;
+    }
     if (DECIDE && !alive) break;
   }
   return m;
