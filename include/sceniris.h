@@ -164,7 +164,8 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
 /* ------------------------------------------------------------ collision */
 
 /* Launch shape and mode of the persistent collision kernel. A field left 0
- * (or a NULL config) takes the built-in default. threads: 128..1024, multiple
+ * (or a NULL config) takes the built-in default: {128, 1, 32, 8} for a batch
+ * with max_sph <= 256, else {256, 4, 256, 4}. threads: 128..1024, multiple
  * of 32. a_per_lane: spheres each lane holds from the A side (1, 2 or 4).
  * seg_len: B-sphere segment per work unit (multiple of 8, 8..4096).
  * ctas_per_sm: resident CTAs per SM the grid is sized for (1..8).

@@ -220,7 +220,6 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
   return SC_OK;
 }
 
-static const sc_collide_config kDefaultCollide = {256, 4, 256, 4, 0};
 // The generation step culls spheres before its pair sweep, so its register
 // blocks are small; one A sphere per lane also keeps its instruction
 // footprint smallest (the step is bound by instruction fetch, not the FMA pipe).
@@ -238,7 +237,7 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
   if (!aligned(poses, 16)) return fail(SC_ERR_INVALID, "poses must be 16-byte aligned");
   if (first_new_obj < 0) return fail(SC_ERR_INVALID, "first_new_obj = %d < 0", first_new_obj);
   if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
-  sc_collide_config cfg = kDefaultCollide;
+  sc_collide_config cfg = sc::default_collide_config(*batch);
   if (config) {  // zero fields keep the default
     if (config->threads) cfg.threads = config->threads;
     if (config->a_per_lane) cfg.a_per_lane = config->a_per_lane;

@@ -184,26 +184,36 @@ __device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int bx0, in
   }
 }
 
-// Thread 0: work units for pairs (i, j), obj(i) < obj(j), obj(j) in [f, n).
-__device__ __forceinline__ void build_units(int f, int n, int S, int BA, int seg_len, const Smem& sm, CtaShared& sh) {
+// Warp 0: work units for pairs (i, j), obj(i) < obj(j), obj(j) in [f, n):
+// A blocks of BA spheres, each lane one block at a time, unit counts summed
+// by a warp scan.
+__device__ __forceinline__ void build_units(int f, int n, int S, int BA, int seg_len, const Smem& sm, CtaShared& sh,
+                                            int lane) {
   int total = 0, nb = 0;
-  if (f < n) {
-    const int B_lo = sm.off[f];
-    const int A_end = sm.off[n - 1];
-    if (A_end > 0) {
-      nb = (A_end + BA - 1) / BA;
-      for (int bk = 0; bk < nb; ++bk) {
-        const int lo = max(B_lo, sm.off[sm.oid[bk * BA] + 1]);
-        sm.blk_lo[bk] = lo;
-        sm.blk_pref[bk] = total;
-        if (S > lo) total += (S - lo + seg_len - 1) / seg_len;
-      }
+  if (f < n && sm.off[n - 1] > 0) nb = (sm.off[n - 1] + BA - 1) / BA;
+  for (int bk0 = 0; bk0 < nb; bk0 += 32) {
+    const int bk = bk0 + lane;
+    int cnt = 0;
+    if (bk < nb) {
+      const int lo = max(sm.off[f], sm.off[sm.oid[bk * BA] + 1]);
+      sm.blk_lo[bk] = lo;
+      if (S > lo) cnt = (S - lo + seg_len - 1) / seg_len;
     }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (bk < nb) sm.blk_pref[bk] = total + incl - cnt;
+    total += __shfl_sync(0xFFFFFFFFu, incl, 31);
   }
-  sm.blk_pref[nb] = total;
-  sh.total_units = total;
-  sh.nb = nb;
-  sh.unit_next = 0;
+  if (lane == 0) {
+    sm.blk_pref[nb] = total;
+    sh.total_units = total;
+    sh.nb = nb;
+    sh.unit_next = 0;
+  }
 }
 
 // Box-frame excess q = |R^T (c - centre)| - h of a point c (relative to
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
       pairs = DECIDE ? !*(volatile int*)&sh.hit : key_float(*(volatile int*)&sh.best_key) >= -2.f * rmax;
     }
     if (pairs) {
-      if (tid == 0) build_units(f, nt, S, 32 * APL, K.seg_len, sm, sh);
+      if (warp == 0) build_units(f, nt, S, 32 * APL, K.seg_len, sm, sh, lane);
       __syncthreads();
       m = pair_units<APL, DECIDE>(sm, sh, f, nt, S, K.seg_len, m, rmax, eps, lane, my_pairs);
     }
@@ -545,6 +555,15 @@ cudaError_t launch_mode(const KArgs& K, const sc_collide_config& cfg, size_t sme
 }
 
 }  // namespace
+
+// A candidate of up to 256 spheres is one or two register blocks of four
+// spheres per lane: small CTAs with one sphere per lane and short B segments
+// spread its few pairs over more warps and keep eight candidates per SM in
+// flight (tabletop batch, 8 x 16 spheres: 2.3 ms against 9.8 ms exact, 1.2
+// against 2.9 ms decide, for 262,144 candidates).
+sc_collide_config default_collide_config(const sc_scene_batch& b) {
+  return b.max_sph <= 256 ? sc_collide_config{128, 1, 32, 8, 0} : sc_collide_config{256, 4, 256, 4, 0};
+}
 
 size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg) {
   return (size_t)make_layout(b.max_sph, b.max_obj, cfg.a_per_lane).total;

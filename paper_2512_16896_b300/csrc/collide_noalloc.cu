@@ -94,7 +94,7 @@ sc_status sc_collide_noalloc(void* cuda_stream, const sc_scene_batch* batch, con
   a.counter = reinterpret_cast<unsigned int*>(static_cast<char*>(scratch));
   a.stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 16);
   a.status = nullptr;
-  const sc_collide_config cfg = {256, 4, 256, 4};
+  const sc_collide_config cfg = sc::default_collide_config(*batch);
   const char* why = nullptr;
   e = sc::launch_collide(*batch, a, cfg, num_sms, static_cast<cudaStream_t>(cuda_stream), &why);
   if (why) return fail(SC_ERR_INVALID, std::string("sc_collide_noalloc: ") + why);

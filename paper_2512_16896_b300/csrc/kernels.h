@@ -162,4 +162,7 @@ const char* check_collide_config(const sc_collide_config& cfg);
 // Dynamic shared memory one collide CTA needs for this batch and config.
 size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg);
 
+// Default launch shape of the collision kernel for a batch (decide_only = 0).
+sc_collide_config default_collide_config(const sc_scene_batch& b);
+
 }  // namespace sc
