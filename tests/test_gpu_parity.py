@@ -208,6 +208,41 @@ def test_collide_first_new(sc, ctx, first_new):
         assert np.all(g[1].cpu().numpy() == FLT_MAX) and not g[0].any()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("first_new", [0, 3, 9])
+def test_collide_offset_spheres_culls(sc, ctx, mode, first_new):
+    """Objects whose spheres sit far from the object origin (the bounding
+    balls are centred on the origin, so their radii are large and lopsided),
+    objects of one sphere, of many spheres and world boxes, in both modes and
+    with earlier objects already placed: the per-(object, box) and
+    per-object-pair ball culls must not drop a pair that decides."""
+    rng = np.random.default_rng(41)
+    objs = []
+    for n in (1, 90, 5, 33, 1, 140, 12, 64, 2, 40, 7, 20):
+        off = rng.uniform(-0.25, 0.25, 3)
+        c = off + rng.uniform(-0.05, 0.05, (n, 3))
+        objs.append([(float(x), float(y), float(z), float(r)) for (x, y, z), r in zip(c, rng.uniform(0.005, 0.05, n))])
+    obbs = []
+    for i in range(5):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        obbs.append([*rng.uniform([-0.8, -0.8, 0.0], [0.8, 0.8, 0.5]), 0, *q, *rng.uniform(0.02, 0.3, 3), 0])
+    b = tiny_batch(objs, obbs=obbs, n_cand=500)
+    poses = synth.random_poses(b, seed=42, spread=0.9)
+    g = sc.collide(ctx, sc.DeviceBatch(b), torch.from_numpy(poses).cuda(), first_new=first_new,
+                   config=(0, 0, 0, 0, mode))
+    ctx.synchronize()
+    ocol, omd, oband = oracle.collide(b, poses, first_new=first_new)
+    gcol, gmd, gband = (x.cpu().numpy() for x in g)
+    band = gband.astype(bool) | oband.astype(bool)
+    assert np.array_equal(gcol[~band], ocol[~band])
+    assert 0.05 < ocol.mean() < 0.95, ocol.mean()
+    if mode == 0:
+        check_collide(*g, ocol, omd, oband)
+    else:
+        assert np.all(gmd[~band & (ocol == 0)] > 1e-5) and np.all(gmd[~band & (ocol == 1)] < -1e-5)
+
+
 @pytest.mark.parametrize("cfg", [(128, 1, 8, 1), (1024, 2, 64, 1), (512, 4, 4096, 2), (256, 4, 256, 4), (96 * 4, 2, 24, 3)])
 def test_collide_configs_bit_identical(sc, ctx, cfg):
     """Every launch shape reduces the same per-pair values: min_dist bit-identical."""
