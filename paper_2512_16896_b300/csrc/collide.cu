@@ -309,6 +309,34 @@ __device__ __forceinline__ float box_units(const Smem& sm, CtaShared& sh, int f,
   return m;
 }
 
+// Seed pairs: the first two spheres of every object against those of every
+// later object (the later one new, obj >= f), before the pair sweep. They
+// are real pairs, so their minimum is an upper bound on the result that the
+// sweep's culls use from its first unit; where two objects overlap it is
+// usually close to the final minimum (decide mode: usually already a certain
+// collision). Warps take the later object, lanes the earlier one. Returns
+// the thread's minimum.
+__device__ __forceinline__ float seed_pairs(const Smem& sm, int f, int n, float m, int lane, int warp, int nwarps) {
+#pragma unroll 1
+  for (int b = f + warp; b < n; b += nwarps) {
+    const int b0 = sm.off[b], nb = sm.off[b + 1] - b0;
+    if (nb == 0) continue;
+    const float4 wb0 = sm.W[b0], wb1 = sm.W[b0 + (nb > 1)];
+#pragma unroll 1
+    for (int a = lane; a < b; a += 32) {
+      const int a0 = sm.off[a], na = sm.off[a + 1] - a0;
+      if (na == 0) continue;
+      const float4 wa0 = sm.W[a0], wa1 = sm.W[a0 + (na > 1)];
+      // with one sphere on a side its "second" is the first again: a repeat, not a wrong pair
+      m = fminf(m, sphere_distance(wa0.x, wa0.y, wa0.z, wa0.w, wb0));
+      m = fminf(m, sphere_distance(wa0.x, wa0.y, wa0.z, wa0.w, wb1));
+      m = fminf(m, sphere_distance(wa1.x, wa1.y, wa1.z, wa1.w, wb0));
+      m = fminf(m, sphere_distance(wa1.x, wa1.y, wa1.z, wa1.w, wb1));
+    }
+  }
+  return m;
+}
+
 // Warps pull units until none are left; returns the warp's result (MIN: its
 // running minimum; DECIDE: the minimum of the exact distances it computed).
 // A unit's B segment is swept one B object ob at a time, each A slot taking
@@ -498,6 +526,12 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
       pairs = DECIDE ? !*(volatile int*)&sh.hit : key_float(*(volatile int*)&sh.best_key) >= -2.f * rmax;
     }
     if (pairs) {
+      m = seed_pairs(sm, f, nt, m, lane, warp, nwarps);
+      m = warp_min(m);
+      if (lane == 0) {
+        if (!DECIDE && m < kFarSentinel) atomicMin(&sh.best_key, float_key(m));
+        if (DECIDE && m < -kBand) *(volatile int*)&sh.hit = 1;
+      }
       if (warp == 0) build_units(f, nt, S, 32 * APL, K.seg_len, sm, sh, lane);
       __syncthreads();
       m = pair_units<APL, DECIDE>(sm, sh, f, nt, S, K.seg_len, m, rmax, eps, lane, my_pairs);

@@ -58,6 +58,13 @@ __device__ __forceinline__ bool refresh(ABlock<APL>& A, float m, float rmax, flo
   return __any_sync(0xFFFFFFFFu, any);
 }
 
+// Signed distance of two spheres (centre (ax, ay, az), radius ar; b): the
+// exact value every prune hit is settled with.
+__device__ __forceinline__ float sphere_distance(float ax, float ay, float az, float ar, const float4& b) {
+  const float dx = ax - b.x, dy = ay - b.y, dz = az - b.z;
+  return sqrtf(dx * dx + dy * dy + dz * dz) - ar - b.w;
+}
+
 // Exact distances of the A block against B spheres [j, j + kGroup) (only the
 // pairs allowed for each A sphere, only real B spheres), folded into m.
 template <int APL>
@@ -70,11 +77,8 @@ __device__ __forceinline__ float slow_group(const ABlock<APL>& A, const float4* 
     const float4 B = W[jj];
 #pragma unroll
     for (int s = 0; s < APL; ++s) {
-      if (jj >= A.bst[s]) {
-        const float dx = -0.5f * A.ax[s] - B.x, dy = -0.5f * A.ay[s] - B.y, dz = -0.5f * A.az[s] - B.z;
-        const float d = sqrtf(dx * dx + dy * dy + dz * dz) - A.r[s] - B.w;
-        mloc = fminf(mloc, d);
-      }
+      if (jj >= A.bst[s])  // -ax / 2 is the centre again (scaling by powers of two is exact)
+        mloc = fminf(mloc, sphere_distance(-0.5f * A.ax[s], -0.5f * A.ay[s], -0.5f * A.az[s], A.r[s], B));
     }
   }
   return warp_min(mloc);
