@@ -7,11 +7,13 @@
 //    spheres in the world frame relative to the position of object 0, with
 //    each object's bounding ball, and the template's world boxes;
 //  * box_units: sphere vs world box, culled per (object, box) by the ball;
+//  * seed_pairs: the first two spheres of every object pair, a first upper
+//    bound on the minimum;
 //  * build_units / pair_units: the pair set {(i, j): obj(i) < obj(j),
 //    obj(j) >= f} is cut into units (A block of 32*APL consecutive spheres,
 //    one per lane per slot) x (B segment of up to seg_len spheres); warps
-//    pull units from a CTA-local counter and sweep them with the prune test
-//    of collide_core.cuh.
+//    pull units from a CTA-local counter and sweep them one B object at a
+//    time (object-pair ball cull) with the prune test of collide_core.cuh.
 #include "collide_core.cuh"
 #include "kernels.h"
 
