@@ -298,6 +298,7 @@ def run_ours(args, wl):
     # ---- surrogate gate (untimed set-up: IK labels, training, threshold)
     gate = None
     gate_info = None
+    rmap = None
     if reach and not args.no_gate:
         t0 = time.perf_counter()
         box = ((-0.2, 2.2), (-1.3, 1.3), (0.0, 0.8))  # base-frame region of the workload's grasp targets
@@ -317,20 +318,21 @@ def run_ours(args, wl):
                      "heldout_reachable": float(yho.float().mean().item()),
                      "label_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
                      "train_samples_per_s": int(args.train_epochs * tr.shape[0] / max(t2 - t1, 1e-9))}
+        gate_info["vs_reach_map"], rmap = compare_gates(sc, ctx, gate, tr, ytr, ho, yho, recall, pass_rate)
         del tr, ho, ytr, yho
 
-    def enqueue(step_seed, use_gate=True, use_graph=True):
+    def enqueue(step_seed, use_gate=True, use_graph=True, use_map=False):
         sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
                     out=(valid, band, tries), use_graph=use_graph and not args.no_graph,
-                    arm=arm if reach else None, ik=ikp, gate=gate if use_gate else None,
-                    q_reach=q_reach if reach else None)
+                    arm=arm if reach else None, ik=ikp, gate=gate if use_gate and not use_map else None,
+                    q_reach=q_reach if reach else None, rmap=rmap if use_map else None)
 
-    def timed(label, use_gate, use_graph, steps, warmup):
+    def timed(label, use_gate, use_graph, steps, warmup, use_map=False):
         ctx.set_timing(True)
         for i in range(warmup):
             with torch.cuda.stream(stream):
                 flush.zero_()
-            enqueue(seed * 7919 + i, use_gate, use_graph)
+            enqueue(seed * 7919 + i, use_gate, use_graph, use_map)
         ctx.synchronize()
         if world > 1:
             dist.barrier()
@@ -340,7 +342,7 @@ def run_ours(args, wl):
             with torch.cuda.stream(stream):
                 flush.zero_()  # evict L2 between timed steps (not timed)
             ev[i][0].record(stream)
-            enqueue(seed * 7919 + 1000 + i, use_gate, use_graph)
+            enqueue(seed * 7919 + 1000 + i, use_gate, use_graph, use_map)
             ev[i][1].record(stream)
             stats.append(ctx.generate_stats())  # synchronises after the step
             vals.append(int(valid.sum().item()))
@@ -355,6 +357,10 @@ def run_ours(args, wl):
     plain = None
     if reach and not args.no_plain:
         plain = timed("plain", False, False, args.plain_steps, min(args.warmup, 3))
+    map_run = None
+    if rmap is not None and args.map_steps > 0:
+        map_run = timed("batched+map", False, True, args.map_steps, min(args.warmup, 3), use_map=True)
+        rmap.close()
 
     # ---- end to end through the C ABI with host buffers. Two contexts with
     # their own device buffers alternate, so one step's copies (the batch in
@@ -462,6 +468,16 @@ def run_ours(args, wl):
         plain_line = {"value": sum(plain["valid"]) / p_s, "unit": "scenes/s", "ms_per_step": 1000 * p_s / len(plain["ms"]),
                       "steps": len(plain["ms"]), "valid_per_step": sum(plain["valid"]) / len(plain["valid"]),
                       "ik_solves_per_step": p_ik["ik_solves"], "launch": "eager", "gate": None}
+    map_line = None
+    if map_run:
+        m_s = sum(map_run["ms"]) / 1000.0
+        m_st = map_run["stats"][-1]
+        map_line = {"value": sum(map_run["valid"]) / m_s, "unit": "scenes/s",
+                    "ms_per_step": 1000 * m_s / len(map_run["ms"]), "steps": len(map_run["ms"]),
+                    "valid_per_step": sum(map_run["valid"]) / len(map_run["valid"]),
+                    "ik_solves_per_step": m_st["ik_solves"], "gate_rejections_per_step": m_st["gate_rejections"],
+                    "launch": "CUDA graph replay",
+                    "gate": "4D reachability map from the same IK labels, recall >= 0.99 on the held-out targets"}
     line = {
         "metric": "verified collision-free scenes/sec",
         "value": total_valid / total_s,
@@ -482,6 +498,7 @@ def run_ours(args, wl):
                    "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
                    "parallelism": f"replicas x{world}"},
         "plain": plain_line,
+        "map_gated": map_line,
         "stages": {"gen_ms_per_step": gen_rf["ms_per_step"], "ik_ms_per_step": ik_rf["ms_per_step"],
                    "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
                    "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
@@ -654,6 +671,44 @@ def run_kernels(args):
     return 0
 
 
+def compare_gates(sc, ctx, gate, tr, ytr, ho, yho, gate_recall, gate_pass_rate):
+    """The RM4D-style 4D reachability map (the paper's kind of reachability
+    check, Sec. IV-E) built from the same IK labels as the learned gate, tuned
+    to the same recall on the same held-out targets: recall, pass rate and
+    device time per query of each, and the map's build time."""
+    import torch
+    stream = ctx.stream
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(fn, reps=5):
+        ms = []
+        for i in range(reps + 1):
+            a, b = ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if i:
+                ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    m = sc.ReachMap(ctx)
+    a, b = ev()
+    a.record(stream)
+    m.build(tr, ytr)
+    b.record(stream)
+    b.synchronize()
+    build_ms = a.elapsed_time(b)
+    tau, rec, pr = m.tune_threshold(ho, yho, 0.99)
+    score = torch.empty(ho.shape[0], dtype=torch.uint16, device=ho.device)
+    map_ms = timed(lambda: m.query(ho, out=score))
+    gate_ms = timed(lambda: gate.infer(ho))
+    out = {"queries": int(ho.shape[0]), "map_cells": m.cells, "map_build_ms": round(build_ms, 3),
+           "map_tau": tau, "map_recall": rec, "map_pass_rate": pr, "map_query_ms": round(map_ms, 4),
+           "gate_recall": gate_recall, "gate_pass_rate": gate_pass_rate, "gate_infer_ms": round(gate_ms, 4)}
+    return out, m
+
+
 def launches_per_step(db, args, reach, gate):
     """Kernels one sc_generate call enqueues: init and tables; per round of the
     objects with reachability a generation step and the reach stage (grasp
@@ -687,6 +742,7 @@ def main():
     ap.add_argument("--no-gate", action="store_true", help="no learned gate (exact IK on every try)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain (eager, ungated) comparison run")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--map-steps", type=int, default=3, help="steps of the map-gated comparison run (0: none)")
     ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel measurements")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the per-kernel measurements (one JSON line; profiling)")

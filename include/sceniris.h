@@ -313,6 +313,61 @@ sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* mlp, const float* tar
 sc_status sc_mlp_save(sc_ctx* ctx, const sc_mlp* mlp, const char* path);
 sc_status sc_mlp_load(sc_ctx* ctx, const char* path, sc_mlp** out);
 
+/* ---------------------------------------------- 4D reachability map */
+
+/* A reachability map in the manner of RM4D, the map the paper queries for
+ * its reachability check (Sec. IV-E), built here from labelled IK outcomes
+ * (sc_ik_reach) instead of the paper's precomputed map. A target (R, p) in
+ * the base frame ([12] floats: R row-major, then p) falls in one cell of a
+ * 4D grid over
+ *   - its height p_z, in [z_lo, z_hi), nz bins;
+ *   - the cosine a_z of its approach axis a = R e_z, in [-1, 1], nc bins
+ *     (the top bin closed);
+ *   - its position (x*, y*) in the frame turned about the base z axis until
+ *     the azimuth reference h lies on +x, each in [-r_max, r_max), nxy bins.
+ *     h = the horizontal direction of a, or, for a vertical approach
+ *     (a_x^2 + a_y^2 <= 1e-6), of the tool x axis R e_x.
+ * Every key step is one IEEE-rounded FP32 operation in a fixed order:
+ *   u = tilted ? (a_x, a_y) : ((R e_x)_x, (R e_x)_y); n2 = u_x u_x + u_y u_y;
+ *   inv = 1 / sqrt(n2); h = u inv; x* = p_x h_x + p_y h_y; y* = p_y h_x - p_x h_y;
+ *   bin = floor((v - lo) s) with s = nz / (z_hi - z_lo), nc / 2, nxy / (2 r_max)
+ * (each s one FP32 division on the host). A target outside the grid, or
+ * with n2 = 0 or a NaN, has no cell. Each cell holds two counts (uint32):
+ * reachable labels and labels. */
+typedef struct {
+  int32_t nz, nc, nxy;   /* bins; nz * nc * nxy^2 <= 2^27 */
+  float z_lo, z_hi;      /* height range (metres), z_hi > z_lo */
+  float r_max;           /* half-width of the x*, y* range (metres), > 0 */
+} sc_rmap_params;
+
+typedef struct sc_rmap sc_rmap;
+
+/* New map with zero counts and threshold 1 (a target passes when its score
+ * is >= the threshold). SC_ERR_INVALID for bad params, SC_ERR_OOM. */
+sc_status sc_rmap_create(sc_ctx* ctx, const sc_rmap_params* params, sc_rmap** out);
+void sc_rmap_destroy(sc_rmap* map);
+/* Number of cells (0 for NULL). */
+int64_t sc_rmap_cells(const sc_rmap* map);
+/* Add n labelled targets (device: targets float [n][12], labels u8 [n], 1 =
+ * reachable) to the counts; targets without a cell are skipped. Counts are
+ * integers, so the result does not depend on the order of the additions. */
+sc_status sc_rmap_build(sc_ctx* ctx, sc_rmap* map, const float* targets, const uint8_t* labels, int32_t n);
+/* score[i] (device u16 [n]) = floor(65535 * reachable / labels) of target
+ * i's cell; 65535 for a cell without labels (no evidence there, and a gate
+ * must not reject without it); 0 for a target without a cell (choose the
+ * grid to cover the arm's workspace). */
+sc_status sc_rmap_query(sc_ctx* ctx, const sc_rmap* map, const float* targets, int32_t n, uint16_t* score);
+/* Set the threshold to the largest tau whose recall on these labelled
+ * targets is >= min_recall (ties included: pass when score >= tau) and report
+ * the recall and the fraction of targets that pass. Synchronises. */
+sc_status sc_rmap_tune_threshold(sc_ctx* ctx, sc_rmap* map, const float* targets, const uint8_t* labels, int32_t n,
+                                 float min_recall, int32_t* tau, float* recall, float* pass_rate);
+/* Set the threshold directly (0 passes every target, 65536 none). */
+sc_status sc_rmap_set_threshold(sc_rmap* map, int32_t tau);
+/* Counts to HOST memory, uint32 [cells][2] = (reachable, labels) per cell
+ * in the order cell = ((iz * nc + ic) * nxy + ix) * nxy + iy. Synchronises. */
+sc_status sc_rmap_get_counts(sc_ctx* ctx, const sc_rmap* map, uint32_t* counts);
+
 /* ----------------------------------------------------------- generation */
 
 typedef struct {
@@ -333,11 +388,15 @@ typedef struct {
  * collision. Exact IK (sc_ik_reach semantics, seeds keyed by (candidate,
  * seed, block, object << 16 | try)) then decides; an unreachable grasp
  * retries too. Every emitted scene is thus verified by exact collision and
- * exact IK decisions; the gate only skips IK on tries it predicts to fail. */
+ * exact IK decisions; the gate only skips IK on tries it predicts to fail.
+ * A 4D reachability map (sc_rmap) can gate instead of the surrogate: the
+ * grasp target's map score must reach the map's threshold
+ * (sc_rmap_tune_threshold), decided where the target is formed. */
 typedef struct {
   const sc_arm* arm;       /* NULL: no reachability stage */
   const sc_ik_params* ik;  /* exact IK settings */
   const sc_mlp* gate;      /* NULL: exact IK on every collision-free try */
+  const sc_rmap* map;      /* map gate instead (at most one of gate and map) */
 } sc_gen_reach;
 
 /* Generate scenes: the paper's placement loop (Sec. IV-A, Fig. 2) over the

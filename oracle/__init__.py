@@ -7,7 +7,8 @@ imported by it. Inputs are duck-typed scene batches (any object with the CSR
 arrays documented in ``synth.SceneBatch``).
 
 ``sceniris_oracle.cpp`` holds the geometry, sampling, collision, generation
-and IK definitions; ``mlp.py`` holds the surrogate network (numpy, FP64).
+and IK definitions; ``mlp.py`` holds the surrogate network (numpy, FP64);
+``rmap.py`` the 4D reachability map (cell keys in FP32, counts as integers).
 """
 from __future__ import annotations
 

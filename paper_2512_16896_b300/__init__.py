@@ -22,6 +22,8 @@ from ._native import (  # noqa: F401
     make_arm,
     ik_params,
     Surrogate,
+    ReachMap,
+    RMAP_DEFAULT,
     train_params,
     order_by_work,
 )

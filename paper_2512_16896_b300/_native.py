@@ -54,8 +54,13 @@ class ScGenStats(ctypes.Structure):
                 "exhaustive_pairs": self.exhaustive_pairs}
 
 
+class ScRmapParams(ctypes.Structure):
+    _fields_ = [("nz", I32), ("nc", I32), ("nxy", I32), ("z_lo", ctypes.c_float), ("z_hi", ctypes.c_float),
+                ("r_max", ctypes.c_float)]
+
+
 class ScGenReach(ctypes.Structure):
-    _fields_ = [("arm", P), ("ik", P), ("gate", P)]
+    _fields_ = [("arm", P), ("ik", P), ("gate", P), ("map", P)]
 
 
 class ScGenParams(ctypes.Structure):
@@ -131,6 +136,14 @@ SIGNATURES = {
     "sc_generate_stats": (ctypes.c_int, [P, ctypes.POINTER(ScGenStats)]),
     "sc_ctx_set_timing": (ctypes.c_int, [P, I32]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
+    "sc_rmap_create": (ctypes.c_int, [P, ctypes.POINTER(ScRmapParams), ctypes.POINTER(P)]),
+    "sc_rmap_destroy": (None, [P]),
+    "sc_rmap_cells": (I64, [P]),
+    "sc_rmap_build": (ctypes.c_int, [P, P, P, P, I32]),
+    "sc_rmap_query": (ctypes.c_int, [P, P, P, I32, P]),
+    "sc_rmap_tune_threshold": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, P]),
+    "sc_rmap_get_counts": (ctypes.c_int, [P, P, P]),
+    "sc_rmap_set_threshold": (ctypes.c_int, [P, I32]),
 }
 
 
@@ -304,10 +317,12 @@ def collide(ctx: Context, db: DeviceBatch, poses: torch.Tensor, active: torch.Te
 
 def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, max_retries: int = 10,
              order: torch.Tensor | None = None, config=None, poses: torch.Tensor | None = None, out=None,
-             use_graph: bool = True, arm=None, ik=None, gate=None, q_reach: torch.Tensor | None = None):
+             use_graph: bool = True, arm=None, ik=None, gate=None, q_reach: torch.Tensor | None = None,
+             rmap=None):
     """sc_generate. Returns (poses [P,4] f32, valid [n_cand] u8, band [n_cand] u8, tries [n_cand] i32).
     With `arm` (and `ik`), designated objects must also be reachable; `gate` (a
-    Surrogate) filters tries before IK; q_reach [P,7] receives the IK solutions."""
+    Surrogate) or `rmap` (a ReachMap) filters tries before IK; q_reach [P,7]
+    receives the IK solutions."""
     dev = torch.device("cuda", ctx.device)
     poses = db.new_poses(dev) if poses is None else poses
     if out is None:
@@ -325,7 +340,7 @@ def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, m
     if arm is not None:
         ik = ik if ik is not None else ik_params()
         reach = ScGenReach(ctypes.cast(ctypes.pointer(arm), P), ctypes.cast(ctypes.pointer(ik), P),
-                           None if gate is None else gate.handle)
+                           None if gate is None else gate.handle, None if rmap is None else rmap.handle)
     _check(lib().sc_generate(ctx.handle, ctypes.byref(db.c), ctypes.byref(p), _active_ptr(order), n,
                              None if cfg is None else ctypes.byref(cfg), None if reach is None else ctypes.byref(reach),
                              _ptr(poses), _ptr(valid), _ptr(band), _ptr(tries), _ptr(q_reach)))
@@ -420,6 +435,67 @@ class Surrogate:
     def close(self):
         if getattr(self, "handle", None):
             lib().sc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+RMAP_DEFAULT = (64, 16, 64, -1.1, 1.5, 1.4)  # nz, nc, nxy, z_lo, z_hi, r_max: 4 cm cells around the arm
+
+
+class ReachMap:
+    """An sc_rmap handle: the 4D reachability map (RM4D-style) built from
+    labelled IK outcomes; score >= tau passes."""
+
+    def __init__(self, ctx: Context, params=RMAP_DEFAULT):
+        self.ctx = ctx
+        self.params = tuple(params)
+        h = P()
+        _check(lib().sc_rmap_create(ctx.handle, ctypes.byref(ScRmapParams(*params)), ctypes.byref(h)))
+        self.handle = h
+        self.tau = 1
+
+    @property
+    def cells(self) -> int:
+        return lib().sc_rmap_cells(self.handle)
+
+    def build(self, targets: torch.Tensor, labels: torch.Tensor):
+        assert targets.dtype == torch.float32 and targets.is_contiguous() and targets.shape[1] == 12
+        assert labels.dtype == torch.uint8 and labels.shape[0] == targets.shape[0]
+        _check(lib().sc_rmap_build(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels), targets.shape[0]))
+
+    def query(self, targets: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        assert targets.dtype == torch.float32 and targets.is_contiguous() and targets.shape[1] == 12
+        n = targets.shape[0]
+        score = torch.empty(n, dtype=torch.uint16, device=targets.device) if out is None else out
+        _check(lib().sc_rmap_query(self.ctx.handle, self.handle, _ptr(targets), n, _ptr(score)))
+        return score
+
+    def tune_threshold(self, targets: torch.Tensor, labels: torch.Tensor, min_recall: float = 0.99):
+        tau, rec, pr = I32(), ctypes.c_float(), ctypes.c_float()
+        _check(lib().sc_rmap_tune_threshold(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels),
+                                            targets.shape[0], float(min_recall), ctypes.byref(tau),
+                                            ctypes.byref(rec), ctypes.byref(pr)))
+        self.tau = tau.value
+        return tau.value, rec.value, pr.value
+
+    def set_threshold(self, tau: int):
+        _check(lib().sc_rmap_set_threshold(self.handle, int(tau)))
+        self.tau = int(tau)
+
+    def counts(self) -> np.ndarray:
+        """uint32 [cells][2] = (reachable, labels) per cell."""
+        c = np.zeros((self.cells, 2), np.uint32)
+        _check(lib().sc_rmap_get_counts(self.ctx.handle, self.handle, _ptr(c)))
+        return c
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sc_rmap_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

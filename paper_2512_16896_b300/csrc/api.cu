@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "rmap.h"
 
 struct sc_ctx {
   int device = 0;
@@ -53,6 +54,13 @@ struct sc_mlp {
   int32_t* index = nullptr;  // epoch permutation scratch
   int index_cap = 0;
   float* loss_dev = nullptr;
+};
+
+struct sc_rmap {
+  int device = 0;
+  sc::RmapGrid g{};
+  uint2* counts = nullptr;
+  int32_t tau = 1;
 };
 
 namespace {
@@ -288,6 +296,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   const bool want_reach = reach && reach->arm;
   if (want_reach) {
     if (!reach->ik) return fail(SC_ERR_INVALID, "reach->ik is NULL");
+    if (reach->gate && reach->map) return fail(SC_ERR_INVALID, "reach->gate and reach->map are both set");
     if (!batch->tmpl_base) return fail(SC_ERR_INVALID, "a reachability stage needs batch->tmpl_base");
     const sc_ik_params& P = *reach->ik;
     if (P.seeds < 1 || P.seeds > 32 || P.iters < 0 || !(P.tol_pos > 0.f) || !(P.tol_rot > 0.f) ||
@@ -335,6 +344,9 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.ik = want_reach ? reach->ik : nullptr;
   a.gate = (want_reach && reach->gate) ? reach->gate->st : nullptr;
   a.tau = (want_reach && reach->gate) ? reach->gate->tau : 0.f;
+  a.map_counts = (want_reach && reach->map) ? reach->map->counts : nullptr;
+  a.map_grid = (want_reach && reach->map) ? reach->map->g : sc::RmapGrid{};
+  a.map_tau = (want_reach && reach->map) ? reach->map->tau : 0;
   a.q_reach = want_reach ? q_reach : nullptr;
   a.reach_objects = 0;
   a.max_sph_obj = 0;
@@ -406,6 +418,8 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     sc_ik_params ik;
     const void* gate;
     float tau;
+    const void* map;
+    int32_t map_tau;
     float* q_reach;
     int reach_objects;
     int max_sph_obj;
@@ -430,6 +444,8 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   }
   key.gate = a.gate;
   key.tau = a.tau;
+  key.map = a.map_counts;
+  key.map_tau = a.map_tau;
   key.q_reach = a.q_reach;
   key.reach_objects = a.reach_objects;
   key.max_sph_obj = a.max_sph_obj;
@@ -711,6 +727,136 @@ sc_status sc_surrogate_tune_threshold(sc_ctx* ctx, sc_mlp* m, const float* targe
   if (tau_out) *tau_out = tau;
   if (recall_out) *recall_out = (float)tp / pos.size();
   if (pass_rate_out) *pass_rate_out = (float)pass / n;
+  return SC_OK;
+}
+
+// ---- 4D reachability map
+
+sc_status sc_rmap_create(sc_ctx* ctx, const sc_rmap_params* p, sc_rmap** out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!p || !out) return fail(SC_ERR_INVALID, "params or out is NULL");
+  *out = nullptr;
+  if (p->nz < 1 || p->nc < 1 || p->nxy < 1) return fail(SC_ERR_INVALID, "bin counts must be >= 1");
+  const double cells = (double)p->nz * p->nc * (double)p->nxy * p->nxy;
+  if (cells > (double)(1 << 27)) return fail(SC_ERR_INVALID, "nz * nc * nxy^2 = %.0f cells > 2^27", cells);
+  if (!(std::isfinite(p->z_lo) && std::isfinite(p->z_hi) && p->z_hi > p->z_lo))
+    return fail(SC_ERR_INVALID, "need finite z_lo < z_hi");
+  if (!(std::isfinite(p->r_max) && p->r_max > 0.f)) return fail(SC_ERR_INVALID, "need a finite r_max > 0");
+  sc::RmapGrid g;
+  g.nz = p->nz;
+  g.nc = p->nc;
+  g.nxy = p->nxy;
+  g.z_lo = p->z_lo;
+  const float span = p->z_hi - p->z_lo;  // FP32 operations, as the key definition states
+  g.sz = (float)p->nz / span;
+  g.sc = (float)p->nc / 2.f;
+  g.r_max = p->r_max;
+  g.sxy = (float)p->nxy / (2.f * p->r_max);
+  g.cells = (size_t)cells;
+  if (!(std::isfinite(g.sz) && std::isfinite(g.sxy))) return fail(SC_ERR_INVALID, "grid scale is not finite");
+  DeviceGuard gd(ctx->device);
+  sc_rmap* m = new (std::nothrow) sc_rmap;
+  if (!m) return fail(SC_ERR_OOM, "host allocation failed");
+  m->device = ctx->device;
+  m->g = g;
+  cudaError_t e = cudaMalloc(&m->counts, g.cells * sizeof(uint2));
+  if (e) { delete m; return fail(SC_ERR_OOM, "map counts (%zu cells): %s", g.cells, cudaGetErrorString(e)); }
+  e = cudaMemsetAsync(m->counts, 0, g.cells * sizeof(uint2), ctx->stream);
+  if (e) { sc_rmap_destroy(m); return cuda_fail(e, "map clear"); }
+  *out = m;
+  return SC_OK;
+}
+
+void sc_rmap_destroy(sc_rmap* m) {
+  if (!m) return;
+  DeviceGuard g(m->device);
+  cudaDeviceSynchronize();
+  if (m->counts) cudaFree(m->counts);
+  delete m;
+}
+
+int64_t sc_rmap_cells(const sc_rmap* m) { return m ? (int64_t)m->g.cells : 0; }
+
+sc_status sc_rmap_build(sc_ctx* ctx, sc_rmap* m, const float* targets, const uint8_t* labels, int32_t n) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "map is NULL");
+  if (n < 0) return fail(SC_ERR_INVALID, "n < 0");
+  if (n == 0) return SC_OK;
+  if (!targets || !labels) return fail(SC_ERR_INVALID, "targets or labels is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::rmap_build(m->g, m->counts, targets, labels, n, ctx->num_sms, ctx->stream);
+  if (e) return cuda_fail(e, "rmap_build_kernel launch");
+  return SC_OK;
+}
+
+sc_status sc_rmap_query(sc_ctx* ctx, const sc_rmap* m, const float* targets, int32_t n, uint16_t* score) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "map is NULL");
+  if (n < 0) return fail(SC_ERR_INVALID, "n < 0");
+  if (n == 0) return SC_OK;
+  if (!targets || !score) return fail(SC_ERR_INVALID, "targets or score is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::rmap_query(m->g, m->counts, targets, n, score, ctx->num_sms, ctx->stream);
+  if (e) return cuda_fail(e, "rmap_query_kernel launch");
+  return SC_OK;
+}
+
+sc_status sc_rmap_tune_threshold(sc_ctx* ctx, sc_rmap* m, const float* targets, const uint8_t* labels, int32_t n,
+                                 float min_recall, int32_t* tau_out, float* recall_out, float* pass_rate_out) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "map is NULL");
+  if (n < 1 || !targets || !labels) return fail(SC_ERR_INVALID, "need n >= 1 targets and labels");
+  if (!(min_recall > 0.f && min_recall <= 1.f)) return fail(SC_ERR_INVALID, "min_recall must be in (0, 1]");
+  DeviceGuard g(ctx->device);
+  uint16_t* dscore = nullptr;
+  cudaError_t e = cudaMalloc(&dscore, (size_t)n * 2);
+  if (e) return fail(SC_ERR_OOM, "score buffer: %s", cudaGetErrorString(e));
+  e = sc::rmap_query(m->g, m->counts, targets, n, dscore, ctx->num_sms, ctx->stream);
+  std::vector<uint16_t> z(n);
+  std::vector<uint8_t> y(n);
+  if (!e) e = cudaMemcpyAsync(z.data(), dscore, (size_t)n * 2, cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaMemcpyAsync(y.data(), labels, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dscore);
+  if (e) return cuda_fail(e, "map threshold tuning");
+  // largest tau with recall >= min_recall: the ceil(min_recall * P)-th largest positive score
+  std::vector<int32_t> pos;
+  for (int i = 0; i < n; ++i)
+    if (y[i]) pos.push_back(z[i]);
+  if (pos.empty()) return fail(SC_ERR_INVALID, "no positive labels");
+  std::sort(pos.begin(), pos.end(), std::greater<int32_t>());
+  const size_t need = (size_t)std::ceil((double)min_recall * pos.size());
+  const int32_t tau = pos[std::min(pos.size(), std::max<size_t>(need, 1)) - 1];
+  size_t tp = 0, pass = 0;
+  for (int i = 0; i < n; ++i)
+    if (z[i] >= tau) { ++pass; tp += y[i] ? 1 : 0; }
+  m->tau = tau;
+  if (tau_out) *tau_out = tau;
+  if (recall_out) *recall_out = (float)tp / pos.size();
+  if (pass_rate_out) *pass_rate_out = (float)pass / n;
+  return SC_OK;
+}
+
+sc_status sc_rmap_set_threshold(sc_rmap* m, int32_t tau) {
+  g_err.clear();
+  if (!m) return fail(SC_ERR_INVALID, "map is NULL");
+  if (tau < 0 || tau > 65536) return fail(SC_ERR_INVALID, "tau = %d outside 0..65536", tau);
+  m->tau = tau;
+  return SC_OK;
+}
+
+sc_status sc_rmap_get_counts(sc_ctx* ctx, const sc_rmap* m, uint32_t* counts) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m || !counts) return fail(SC_ERR_INVALID, "map or counts is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (!e) e = cudaMemcpy(counts, m->counts, m->g.cells * sizeof(uint2), cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(e, "map read-back");
   return SC_OK;
 }
 

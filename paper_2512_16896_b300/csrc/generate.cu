@@ -679,6 +679,9 @@ struct ReachArgs {
   int32_t* list_gen;     // the round after next: retries and next objects
   int* n_gen;
   unsigned int* claim;   // IK work counter of the round (zeroed at init)
+  const uint2* map_counts;  // 4D reachability map gate (NULL: the surrogate or none)
+  RmapGrid map_grid;
+  int map_tau;
   const float4* poses;
   uint8_t* valid;
   uint8_t* band;
@@ -728,11 +731,45 @@ __device__ __forceinline__ void grasp_target(const ReachArgs& A, int c, float o[
   o[11] = wz;
 }
 
+// A gate's decision on reach-queue entry `row` (warp-uniform call; `valid`
+// false on lanes past the queue): a pass goes to the IK list, a rejection
+// retries (or ends invalid); appends aggregated per warp.
+__device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool valid, bool pass) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  pass = valid && pass;
+  const unsigned mp = __ballot_sync(0xFFFFFFFFu, pass);
+  if (mp) {
+    const int leader = __ffs(mp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(A.n_ik, __popc(mp));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pass) A.list_ik[base + __popc(mp & lt)] = row;
+  }
+  const bool rej = valid && !pass;
+  int c = 0;
+  bool retry = false;
+  if (rej) {
+    c = A.list_reach[row];
+    const int r = A.st.rc[c];
+    retry = r < A.max_retries;
+    if (retry) A.st.rc[c] = (uint16_t)(r + 1);
+  }
+  const unsigned mr = __ballot_sync(0xFFFFFFFFu, retry);
+  if (mr) {
+    const int leader = __ffs(mr) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(A.n_gen, __popc(mr));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (retry) A.list_gen[base + __popc(mr & lt)] = c;
+  }
+  const unsigned mj = __ballot_sync(0xFFFFFFFFu, rej);
+  if (lane == 0 && mj) atomicAdd(&A.stats[3], (unsigned long long)__popc(mj));
+}
+
 // The learned gate's decision fused into the tensor-core forward pass: its
 // rows are the round's reach queue (grasp targets formed by
-// reach_targets_kernel), and each logit is decided at once — logit >= tau
-// goes to the IK list, the rest retries (or ends invalid); the appends are
-// aggregated per warp.
+// reach_targets_kernel), and each logit is decided at once (logit >= tau).
 struct GateIO {
   ReachArgs A;
   __device__ int rows() const { return *(volatile const int*)A.n_reach; }
@@ -742,47 +779,36 @@ struct GateIO {
     f[3] = __ldg(t + 0); f[4] = __ldg(t + 3); f[5] = __ldg(t + 6);
     f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
   }
-  __device__ void emit(int row, bool valid, float logit) const {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const bool pass = valid && logit >= A.tau;
-    const unsigned mp = __ballot_sync(0xFFFFFFFFu, pass);
-    if (mp) {
-      const int leader = __ffs(mp) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(A.n_ik, __popc(mp));
-      base = __shfl_sync(0xFFFFFFFFu, base, leader);
-      if (pass) A.list_ik[base + __popc(mp & lt)] = row;
-    }
-    const bool rej = valid && !pass;
-    int c = 0;
-    bool retry = false;
-    if (rej) {
-      c = A.list_reach[row];
-      const int r = A.st.rc[c];
-      retry = r < A.max_retries;
-      if (retry) A.st.rc[c] = (uint16_t)(r + 1);
-    }
-    const unsigned mr = __ballot_sync(0xFFFFFFFFu, retry);
-    if (mr) {
-      const int leader = __ffs(mr) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(A.n_gen, __popc(mr));
-      base = __shfl_sync(0xFFFFFFFFu, base, leader);
-      if (retry) A.list_gen[base + __popc(mr & lt)] = c;
-    }
-    const unsigned mj = __ballot_sync(0xFFFFFFFFu, rej);
-    if (lane == 0 && mj) atomicAdd(&A.stats[3], (unsigned long long)__popc(mj));
-  }
+  __device__ void emit(int row, bool valid, float logit) const { gate_route(A, row, valid, logit >= A.tau); }
 };
 
 // Top-down grasp of the candidate's current object k: position = top centre
 // of its box, tool z = -world z, tool x along the object's yaw; expressed in
 // the template's robot base frame (x, y, z, yaw). R row-major, then p.
+// With a map gate, each target's map score is decided here as well (score
+// >= the map's threshold), warps walking the queue 32 entries at a time.
 __global__ void reach_targets_kernel(ReachArgs A) {
   const int n = *(volatile const int*)A.n_reach;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    grasp_target(A, A.list_reach[i], A.targets + 12 * (size_t)i);
+  if (!A.map_counts) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      grasp_target(A, A.list_reach[i], A.targets + 12 * (size_t)i);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + lane;
+    const bool valid = i < n;
+    bool pass = false;
+    if (valid) {
+      float o[12];
+      grasp_target(A, A.list_reach[i], o);
+      float* t = A.targets + 12 * (size_t)i;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) t[j] = o[j];
+      pass = (int)rmap_score(A.map_counts, rmap_cell(A.map_grid, o)) >= A.map_tau;
+    }
+    gate_route(A, i, valid, pass);
+  }
 }
 
 // Exact IK, one warp per entry; seeds keyed by (candidate, object, try).
@@ -1101,7 +1127,10 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.cand_t = cand_t;
     ra.tinfo = tinfo;
     ra.max_retries = R;
-    ra.gated = a.gate != nullptr;
+    ra.gated = a.gate != nullptr || a.map_counts != nullptr;
+    ra.map_counts = a.map_counts;
+    ra.map_grid = a.map_grid;
+    ra.map_tau = a.map_tau;
     ra.tol_pos = a.ik->tol_pos;
     ra.tol_rot = a.ik->tol_rot;
     ra.tau = a.tau;
@@ -1163,7 +1192,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.claim = counters + NRmax + 1 + i;
     if (a.timer) a.timer->begin(1, sr);
     reach_targets_kernel<<<small_blocks, 256, 0, sr>>>(ra);
-    if (ra.gated) {  // gate forward pass and decision in one launch
+    if (a.gate) {  // gate forward pass and decision in one launch
       e = launch_mlp_tc(gate_w, GateIO{ra}, n, a.status, num_sms, sr);
       if (e != cudaSuccess) return e;
     }

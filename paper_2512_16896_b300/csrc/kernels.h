@@ -6,6 +6,7 @@
 
 #include <string>
 
+#include "rmap.h"
 #include "sceniris.h"
 
 namespace sc {
@@ -78,6 +79,9 @@ struct GenerateLaunch {
   const sc_ik_params* ik;
   const MlpState* gate;  // NULL: exact IK on every candidate
   float tau;
+  const uint2* map_counts;  // 4D reachability map gate instead of the surrogate (NULL: none)
+  RmapGrid map_grid;
+  int map_tau;
   int reach_objects;     // object indices < reach_objects may carry the reach flag
   int max_sph_obj;       // most spheres of one object in the batch (batch_scan)
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)

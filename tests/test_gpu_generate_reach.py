@@ -37,12 +37,12 @@ def ctx(sc):
     c.close()
 
 
-def run(sc, ctx, db, b, seed, gate=None, retries=10):
+def run(sc, ctx, db, b, seed, gate=None, retries=10, rmap=None):
     q = torch.full((db.n_poses, 7), float("nan"), device="cuda")
     order = torch.from_numpy(sc.order_by_work(b)).cuda()
     arm = sc.make_arm(*synth.arm_arrays())
     P, V, B, T = sc.generate(ctx, db, seed=seed, max_retries=retries, order=order, arm=arm,
-                             ik=sc.ik_params(seed=seed), gate=gate, q_reach=q)
+                             ik=sc.ik_params(seed=seed), gate=gate, q_reach=q, rmap=rmap)
     ctx.synchronize()
     return [x.clone() for x in (P, V, B, T, q)]
 
@@ -158,3 +158,51 @@ def test_reach_without_retries(sc, ctx):
     b = synth.ragged(seed=23, n_templates=12, cand_per_template=16, obj_range=(3, 8))
     gv = _agree_and_verify(sc, ctx, b, seed=10, retries=0)
     assert gv.sum() < len(gv)
+
+
+def test_map_gate_extremes(sc, ctx):
+    """A map gate that passes every try reproduces the plain run bit for bit;
+    one that passes nothing places no designated object."""
+    b = synth.ragged(seed=13, n_templates=24, cand_per_template=12, obj_range=(2, 12))
+    db = sc.DeviceBatch(b)
+    plain = run(sc, ctx, db, b, seed=6)
+    m = sc.ReachMap(ctx)
+    m.set_threshold(0)
+    open_ = run(sc, ctx, db, b, seed=6, rmap=m)
+    for x, y in zip(plain, open_):
+        assert torch.equal(torch.nan_to_num(x, 5.0), torch.nan_to_num(y, 5.0))
+    m.set_threshold(65536)
+    shut = run(sc, ctx, db, b, seed=6, rmap=m)
+    assert shut[1].sum().item() == 0
+    m.close()
+
+
+def test_map_gate_emits_only_verified_scenes(sc, ctx):
+    """The 4D reachability map built from IK labels and tuned to recall 0.99
+    gates like the surrogate: only verified scenes, fewer IK solves than the
+    plain run; a surrogate and a map together are refused."""
+    arm = sc.make_arm(*synth.arm_arrays())
+    box = ((-0.2, 1.6), (-1.0, 1.0), (-0.05, 0.6))
+    tr = torch.from_numpy(synth.topdown_targets(seed=4, n=262144, box=box)).cuda()
+    ho = torch.from_numpy(synth.topdown_targets(seed=5, n=65536, box=box)).cuda()
+    ytr, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=4), tr)
+    yho, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=5), ho)
+    m = sc.ReachMap(ctx, (32, 16, 32, -1.1, 1.5, 1.4))
+    m.build(tr, ytr)
+    tau, rec, pr = m.tune_threshold(ho, yho, 0.99)
+    assert rec >= 0.99 and tau >= 1
+    b = synth.ragged(seed=14, n_templates=32, cand_per_template=16, obj_range=(3, 14))
+    db = sc.DeviceBatch(b)
+    _, Vp, _, _, _ = run(sc, ctx, db, b, seed=7)
+    plain = ctx.generate_stats()
+    P, V, B, T, q = run(sc, ctx, db, b, seed=7, rmap=m)
+    gated = ctx.generate_stats()
+    verify_emitted(b, P, V, q)
+    assert gated["gate_rejections"] > 0
+    assert gated["ik_solves"] < 0.8 * plain["ik_solves"], (gated["ik_solves"], plain["ik_solves"])
+    assert V.sum().item() >= 0.9 * Vp.sum().item(), (V.sum().item(), Vp.sum().item())
+    gate = sc.Surrogate(ctx, seed=1)
+    with pytest.raises(sc.SceniError):
+        run(sc, ctx, db, b, seed=7, gate=gate, rmap=m)
+    gate.close()
+    m.close()

@@ -551,3 +551,81 @@ def test_adam_first_step_closed_form():
     w1, m, v = mlp.adam_step(w0, g, np.zeros(4), np.zeros(4), 1)
     assert np.allclose(w1 - w0, -1e-3 * g / (np.abs(g) + 1e-8), atol=1e-15)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+# --------------------------------------------------------------------------- 4D reachability map
+
+from oracle import rmap  # noqa: E402
+
+RM_P = (10, 4, 10, 0.0, 1.0, 1.0)  # nz, nc, nxy, z_lo, z_hi, r_max: 0.1 m / 0.5 (cosine) / 0.2 m bins
+
+
+def _target(R, p):
+    return np.concatenate([np.asarray(R, np.float64).reshape(9), p]).astype(np.float32)
+
+
+def _topdown(p, yaw):
+    """Tool z down, tool x at angle yaw in the horizontal plane (rotation matrix by hand)."""
+    c, s = math.cos(yaw), math.sin(yaw)
+    return _target([[c, s, 0], [s, -c, 0], [0, 0, -1]], p)
+
+
+def test_rmap_cell_hand_computed():
+    """Top-down grasp at p = (0.55, 0, 0.25), tool x along +x: the reference
+    direction is the tool x axis, so x* = 0.55, y* = 0, tilt cosine -1: bins
+    (iz, ic, ix, iy) = (2, 0, 7, 5) by hand -> ((2*4 + 0)*10 + 7)*10 + 5."""
+    assert rmap.cells(RM_P, _topdown([0.55, 0.0, 0.25], 0.0)[None])[0] == 875
+    # tool x along +y: the frame turns by 90 deg, the same point lies on y* = -0.55
+    # (ix = floor(1.0 * 5) = 5, iy = floor(0.45 * 5) = 2)
+    assert rmap.cells(RM_P, _topdown([0.55, 0.0, 0.25], math.pi / 2)[None])[0] == ((2 * 4 + 0) * 10 + 5) * 10 + 2
+    # approach tilted 90 deg (horizontal, along +y): a_z = 0 -> tilt bin 2; the
+    # reference is a itself: x* = p.y, y* = -p.x
+    R = Rotation.from_euler("x", -90, degrees=True).as_matrix()  # maps e_z to +y
+    assert np.allclose(R @ [0, 0, 1], [0, 1, 0])
+    t = _target(R, [0.1, 0.3, 0.65])
+    assert rmap.cells(RM_P, t[None])[0] == ((6 * 4 + 2) * 10 + 6) * 10 + 4
+
+
+def test_rmap_cell_turn_about_base_z_invariant():
+    """Turning the whole target by 90 deg about the base z axis is exact in
+    FP32 (a swap and a sign), and the key is built to be invariant under any
+    such turn: the same cell, for random orientations."""
+    rng = np.random.default_rng(3)
+    Rs = Rotation.random(500, random_state=rng).as_matrix()
+    ps = rng.uniform([-0.9, -0.9, 0.0], [0.9, 0.9, 1.0], (500, 3))
+    t = np.stack([_target(R, p) for R, p in zip(Rs, ps)])
+    Q = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]], np.float64)
+    t2 = np.stack([_target(Q @ R, Q @ p) for R, p in zip(Rs, ps)])
+    c1, c2 = rmap.cells(RM_P, t), rmap.cells(RM_P, t2)
+    assert (c1 >= 0).sum() > 300
+    assert np.array_equal(c1, c2)
+
+
+def test_rmap_outside_and_degenerate_have_no_cell():
+    bad = np.stack([_topdown([0.0, 0.0, 1.2], 0.0), _topdown([1.5, 0.0, 0.5], 0.0), _topdown([0.0, 0.0, -0.01], 0.0),
+                    np.zeros(12, np.float32), np.full(12, np.nan, np.float32)])
+    assert np.all(rmap.cells(RM_P, bad) == -1)
+
+
+def test_rmap_counts_and_scores():
+    """Counts conserve the in-grid labels; a cell's score is floor(65535 p / n)
+    (1 of 3 -> 21845), 65535 without labels, 0 outside the grid; every reachable training target
+    passes tau = 1 when no cell holds more than 65535 labels, so tuning for
+    recall 1 on the build set gives recall 1."""
+    rng = np.random.default_rng(4)
+    n = 4000
+    t = np.stack([_topdown(p, y) for p, y in zip(rng.uniform([-1.1, -1.1, -0.1], [1.1, 1.1, 1.1], (n, 3)),
+                                                 rng.uniform(0, 2 * math.pi, n))])
+    y = (rng.uniform(size=n) < 0.4).astype(np.uint8)
+    c = rmap.cells(RM_P, t)
+    counts = rmap.build(RM_P, t, y)
+    assert counts[:, 1].sum() == (c >= 0).sum() and counts[:, 0].sum() == ((c >= 0) & (y == 1)).sum()
+    s = rmap.score(RM_P, counts, t)
+    assert np.all(s[(c >= 0) & (y == 1)] >= 1) and np.all(s[c < 0] == 0)
+    inside = c >= 0
+    tau, rec, pr = rmap.tune(s[inside], y[inside], 1.0)
+    assert tau >= 1 and rec == 1.0 and pr < 1.0
+    one = np.zeros((rmap.n_cells(RM_P), 2), np.uint32)
+    one[875] = (1, 3)
+    assert rmap.score(RM_P, one, _topdown([0.55, 0.0, 0.25], 0.0)[None])[0] == 21845
+    assert rmap.score(RM_P, one, _topdown([0.15, 0.0, 0.25], 0.0)[None])[0] == 65535  # an empty cell
