@@ -539,7 +539,8 @@ def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
     want = lambda key: only is None or re.search(only, key) is not None
     if any(want(f"collide_{m}_{w}") for m in ("exact_min", "decide") for w in ("shelf", "ragged")):
         kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand)
-    if want("ik_topdown_262144") or want("gate_infer_262144") or want("gate_train_epoch_262144"):
+    if any(want(k) for k in ("ik_topdown_262144", "gate_infer_262144", "gate_train_epoch_262144",
+                              "rmap_build_262144", "rmap_query_262144")):
         kernel_suite_ik_gate(sc, ctx, dev, out, want)
     return out
 
@@ -612,7 +613,7 @@ def kernel_suite_ik_gate(sc, ctx, dev, out, want):
     stream = ctx.stream
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     tg = torch.from_numpy(synth.topdown_targets(seed=3, n=262144)).to(dev)
-    if want("ik_topdown_262144"):
+    if want("ik_topdown_262144") or want("rmap_build_262144") or want("rmap_query_262144"):
         # IK: 262,144 top-down grasp targets over the tabletop region, 32 seeds x 100 iterations
         arm = sc.make_arm(*synth.arm_arrays())
         ms = []
@@ -626,6 +627,29 @@ def kernel_suite_ik_gate(sc, ctx, dev, out, want):
                 ms.append(a.elapsed_time(b))
         out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / (np.mean(ms) / 1e3),
                                     "reachable": float(r.float().mean().item())}
+        # 4D reachability map from these labels: build, then query the same targets
+        m = sc.ReachMap(ctx)
+        bms, qms = [], []
+        score = torch.empty(262144, dtype=torch.uint16, device=dev)
+        for i in range(4):
+            a, b = ev()
+            a.record(stream)
+            m.build(tg, r)
+            b.record(stream)
+            c, d = ev()
+            c.record(stream)
+            m.query(tg, out=score)
+            d.record(stream)
+            d.synchronize()
+            if i >= 1:
+                bms.append(a.elapsed_time(b))
+                qms.append(c.elapsed_time(d))
+        q_ms = float(np.mean(qms))
+        out["rmap_build_262144"] = {"ms": float(np.mean(bms)), "labels_per_s": 262144 / (np.mean(bms) / 1e3)}
+        out["rmap_query_262144"] = {"ms": q_ms, "queries_per_s": 262144 / (q_ms / 1e3),
+                                    "hbm_gbs": 262144 * 58 / (q_ms / 1e3) / 1e9,
+                                    "bytes_per_query": "48 in + 8 gathered + 2 out"}
+        m.close()
     if not (want("gate_infer_262144") or want("gate_train_epoch_262144")):
         return
     # gate inference and one training epoch
