@@ -67,8 +67,18 @@ int32_t sc_ctx_num_sms(const sc_ctx* ctx);
 
 /* ---------------------------------------------------------- scene batch */
 
-/* Relation kinds stored in obj_rel (low 4 bits), see sc_sample_poses. */
-enum { SC_REL_FREE = 0, SC_REL_ON_TOP = 1, SC_REL_NEXT_TO = 2, SC_REL_KIND_MASK = 0xF, SC_REL_REACH = 0x10 };
+/* Relation kinds stored in obj_rel (low 4 bits) and flags, see sc_sample_poses. */
+enum {
+  SC_REL_FREE = 0,
+  SC_REL_ON_TOP = 1,
+  SC_REL_NEXT_TO = 2,
+  SC_REL_DIRECTIONAL = 3, /* one anchor, partial annulus (direction, half-angle, radii) */
+  SC_REL_MIDDLE = 4,      /* two or more anchors: inside the polygon of their positions */
+  SC_REL_KIND_MASK = 0xF,
+  SC_REL_REACH = 0x10,    /* reachability check (sc_generate) */
+  SC_REL_LOCAL = 0x20,    /* DIRECTIONAL: direction angle in the anchor's frame */
+  SC_REL_FACE_TO = 0x40   /* yaw faces the reference object instead of a uniform draw */
+};
 
 /* A batch of scene templates and the candidates (scene variations) drawn
  * from them, CSR-packed (Sec. IV-B: one transform per instance per edge; here
@@ -85,9 +95,17 @@ enum { SC_REL_FREE = 0, SC_REL_ON_TOP = 1, SC_REL_NEXT_TO = 2, SC_REL_KIND_MASK 
  *                             radius of its xy bounding circle. The box must contain
  *                             every sphere of the object: sc_generate skips pairs of
  *                             objects whose bounding balls (radius |H|) are apart.
- *  obj_rel       int32 [O]    kind | SC_REL_REACH flag | (reference local index << 8);
- *                             the reference (parent / anchor) is an EARLIER object.
- *  obj_rel_param float [O][4] (dmin, dmax, ratio_on_support, unused).
+ *  obj_rel       int32 [O]    kind | flags | (reference local index << 8); the
+ *                             reference (parent / anchor / faced object) is an EARLIER
+ *                             object.
+ *  obj_rel_param float [O][4] (dmin, dmax, ratio_on_support, unused); DIRECTIONAL:
+ *                             (min_r, max_r, ratio_on_support, theta), max_r may be +inf.
+ *  obj_rel_dir   float [O]    DIRECTIONAL: direction angle of v (radians); may be NULL
+ *                             when no object is DIRECTIONAL.
+ *  obj_anchor_off int32 [O+1], obj_anchor int32 [A]: MIDDLE: the anchors (2..16
+ *                             template-local indices of earlier objects, polygon order)
+ *                             of object o are obj_anchor[obj_anchor_off[o] ..
+ *                             obj_anchor_off[o+1]); may be NULL when no object is MIDDLE.
  *  tmpl_poly_off int32 [T+1], poly_verts float [V][2]: support polygon of template t
  *                             (closed, any orientation, >= 3 vertices) on the plane
  *                             z = tmpl_support_z[t].
@@ -121,6 +139,9 @@ typedef struct {
   const int32_t* cand_tmpl_off;
   const int64_t* tmpl_pose_off;
   const float* tmpl_base;
+  const float* obj_rel_dir;
+  const int32_t* obj_anchor_off;
+  const int32_t* obj_anchor;
 } sc_scene_batch;
 
 /* ------------------------------------------------------------- sampling */
@@ -144,17 +165,31 @@ typedef struct {
  *           (dmax - dmin) u1 (the annulus between min_r and max_r of Sec. IV-F, v = Null);
  *   ON_TOP  xy uniform in the parent's top face (its frame) moved by the parent's pose,
  *           z = parent z + parent Hz + Hz; accepted at attempt 0 (may overhang).
- * FREE / NEXT_TO proposals are accepted when inside the support polygon and at
- * least e = ratio_on_support * min(Hx, Hy) from its boundary; z = support + Hz.
- * yaw = 2 pi u2. The first accepted attempt wins; if none is accepted the pose
- * of the last attempt is written and the object counts as failed.
+ *   DIRECTIONAL (one anchor, the partial annulus S_r of Sec. IV-F): area-uniform
+ *           in the sector of half-angle theta around phi = dir (+ the anchor's yaw
+ *           with SC_REL_LOCAL) between radii min_r and R = min(max_r, largest
+ *           distance from the anchor to a corner of the support's bounding box):
+ *           r = sqrt(min_r^2 + (R^2 - min_r^2) u0), angle phi + theta (2 u1 - 1),
+ *           measured from the anchor's position;
+ *   MIDDLE  (anchors A_1..A_n, Sec. IV-F 'middle'): n = 2: A_1 + u0 (A_2 - A_1);
+ *           n >= 3: uniform in the anchors' bounding box, kept only inside the
+ *           polygon A_1..A_n (crossing number, boundary inside).
+ * FREE / NEXT_TO / DIRECTIONAL / MIDDLE proposals are accepted when inside the
+ * support polygon and at least e = ratio_on_support * min(Hx, Hy) from its
+ * boundary (S' = S_r n S); z = support + Hz. yaw = 2 pi u2, or with
+ * SC_REL_FACE_TO the direction from the object towards the reference object,
+ * atan2(y_ref - y, x_ref - x). The first accepted attempt wins; if none is
+ * accepted the pose of the last attempt is written and the object counts as
+ * failed. A relation that names a later object, a missing array, or a MIDDLE
+ * object without 2..16 anchors latches a device error and is sampled free.
  * poses   float [P][4] (x, y, z, yaw), CSR layout of the batch; read (earlier
  *         objects) and written (sampled objects).
  * active  int32 [n_active] candidate indices to sample, or NULL for all n_cand
  *         (then n_active is ignored). Duplicates are not allowed.
  * sample_ok [n] u8: 1 if every sampled object of the candidate was accepted.
  * band      [n] u8: 1 if an accept/reject decision that fixed the outcome lay
- *           within 1e-5 m of the polygon boundary or of the erosion distance.
+ *           within 1e-5 m of the polygon boundary or of the erosion distance (or,
+ *           for MIDDLE, of the anchor polygon's boundary).
  * Errors: SC_ERR_INVALID for NULL outputs, max_attempts outside 1..1024,
  * retry < 0, n_obj < 0 or sizes beyond the limits of sc_scene_batch. */
 sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sample_params* params,

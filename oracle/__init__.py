@@ -47,7 +47,8 @@ class _Scene(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("n_templates", "n_objects", "n_spheres", "n_verts", "n_obb", "n_cand")] + [
         (n, ctypes.c_void_p) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel",
                                        "obj_rel_param", "tmpl_poly_off", "poly_verts", "tmpl_support_z",
-                                       "tmpl_obb_off", "obb", "cand_tmpl_off", "tmpl_base")]
+                                       "tmpl_obb_off", "obb", "cand_tmpl_off", "tmpl_base", "obj_rel_dir",
+                                       "obj_anchor_off", "obj_anchor")]
 
 
 class _Arm(ctypes.Structure):
@@ -116,6 +117,12 @@ class Scene:
             "obb": _c(batch.obb, np.float32).reshape(-1, 12), "cand_tmpl_off": _c(batch.cand_tmpl_off, np.int32),
             "tmpl_base": _c(batch.tmpl_base, np.float32).reshape(-1, 4),
         }
+        # optional relation arrays (None: no object uses them)
+        for name, dt in (("obj_rel_dir", np.float32), ("obj_anchor_off", np.int32), ("obj_anchor", np.int32)):
+            a = getattr(batch, name, None)
+            self.keep[name] = None if a is None or np.asarray(a).size == 0 else _c(a, dt)
+        if self.keep["obj_anchor"] is None:
+            self.keep["obj_anchor_off"] = None
         k = self.keep
         self.n_cand = int(k["cand_tmpl_off"][-1])
         self.c = _Scene(len(k["tmpl_obj_off"]) - 1, len(k["obj_half"]), len(k["sph_local"]), len(k["poly_verts"]),

@@ -177,9 +177,15 @@ typedef struct {
   const float* obb;              // [n_obb][12] centre(x,y,z,-), quaternion(x,y,z,w), half(x,y,z,-)
   const int32_t* cand_tmpl_off;  // [T+1] candidates of template t: [off[t], off[t+1])
   const float* tmpl_base;        // [T][4] robot base pose x,y,z,yaw (reachability only; may be NULL)
+  const float* obj_rel_dir;      // [O] direction angle of a DIRECTIONAL relation (may be NULL)
+  const int32_t* obj_anchor_off; // [O+1] anchors of a MIDDLE relation (may be NULL)
+  const int32_t* obj_anchor;     // [A] template-local indices of earlier objects
 } or_scene;
 
-enum { REL_FREE = 0, REL_ON_TOP = 1, REL_NEXT_TO = 2, REL_KIND_MASK = 0xF, REL_REACH = 0x10 };
+enum {
+  REL_FREE = 0, REL_ON_TOP = 1, REL_NEXT_TO = 2, REL_DIRECTIONAL = 3, REL_MIDDLE = 4, REL_KIND_MASK = 0xF,
+  REL_REACH = 0x10, REL_LOCAL = 0x20, REL_FACE_TO = 0x40
+};
 
 static const double BAND = 1e-5;         // decision band of the parity contract (metres)
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -232,11 +238,41 @@ static bool support_accept(const or_scene* s, int t, double x, double y, double 
 //   NEXT_TO : Sec. IV-F one-anchor relation with v = Null: the annulus between
 //             min_r = contact + dmin and max_r = contact + dmax around the anchor,
 //             intersected with the support polygon S (S' = S_r n S) by rejection.
+//   DIRECTIONAL : Sec. IV-F one anchor with a direction v and angle threshold
+//             theta: the partial annulus between min_r and max_r (from the
+//             distance type; max_r may be infinite) around the anchor's
+//             position, v turned by the anchor's yaw when LOCAL; points drawn
+//             uniformly over its area (radius from the area fraction, angle
+//             uniform in v +- theta) with max_r cut at the support's farthest
+//             bounding-box corner, then S' = S_r n S by rejection.
+//   MIDDLE  : Sec. IV-F two or more anchors: the polygon of their positions
+//             (for two, the segment between them), proposals uniform over it
+//             (over its bounding box, kept when inside), then S by rejection.
+//   FACE_TO : the yaw points from the object to the reference object.
+// A relation naming a later object, a missing array or a MIDDLE object
+// without 2..16 earlier anchors is sampled as a free object.
 static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int max_attempts, uint64_t seed,
                           double (*pose)[4], bool* band_out) {
   int o = s->tmpl_obj_off[t] + k;
   int rel = s->obj_rel[o];
-  int kind = rel & REL_KIND_MASK, ref = rel >> 8;
+  int kind = rel & REL_KIND_MASK, ref = (rel >> 8) & 0xFF;
+  bool face_to = (rel & REL_FACE_TO) != 0;
+  std::vector<int> anchors;
+  bool bad = (kind != REL_FREE || face_to) && ref >= k;
+  bad = bad || kind > REL_MIDDLE || (kind == REL_DIRECTIONAL && !s->obj_rel_dir);
+  if (kind == REL_MIDDLE) {
+    if (!s->obj_anchor_off) {
+      bad = true;
+    } else {
+      for (int i = s->obj_anchor_off[o]; i < s->obj_anchor_off[o + 1]; ++i) anchors.push_back(s->obj_anchor[i]);
+      bad = bad || anchors.size() < 2 || anchors.size() > 16;
+      for (int j : anchors) bad = bad || j < 0 || j >= k;
+    }
+  }
+  if (bad) {
+    kind = REL_FREE;
+    face_to = false;
+  }
   const float* H = &s->obj_half[4 * o];
   const float* P = &s->obj_rel_param[4 * o];
   double Hx = H[0], Hy = H[1], Hz = H[2], rho = H[3];
@@ -267,11 +303,43 @@ static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int
     xmin = std::min(xmin, vx); xmax = std::max(xmax, vx);
     ymin = std::min(ymin, vy); ymax = std::max(ymax, vy);
   }
+  // DIRECTIONAL: direction and outer radius; MIDDLE: the anchors' polygon and bounding box
+  double dir = 0.0, r1 = 0.0;
+  if (kind == REL_DIRECTIONAL) {
+    dir = (double)s->obj_rel_dir[o] + ((rel & REL_LOCAL) ? pose[ref][3] : 0.0);
+    double dx = std::max(std::fabs(xmin - pose[ref][0]), std::fabs(xmax - pose[ref][0]));
+    double dy = std::max(std::fabs(ymin - pose[ref][1]), std::fabs(ymax - pose[ref][1]));
+    r1 = std::min((double)P[1], std::sqrt(dx * dx + dy * dy));
+  }
+  std::vector<double> ax, ay;
+  double bx0 = INFINITY, bx1 = -INFINITY, by0 = INFINITY, by1 = -INFINITY;
+  for (int j : anchors) {
+    ax.push_back(pose[j][0]);
+    ay.push_back(pose[j][1]);
+    bx0 = std::min(bx0, pose[j][0]); bx1 = std::max(bx1, pose[j][0]);
+    by0 = std::min(by0, pose[j][1]); by1 = std::max(by1, pose[j][1]);
+  }
   for (int a = 0; a < max_attempts; ++a) {
     double u[4];
     draw4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, (uint32_t)a, u);
     double x, y;
-    if (kind == REL_NEXT_TO) {
+    bool in_rel = true, rel_band = false;
+    if (kind == REL_DIRECTIONAL) {
+      double r0 = P[0], th = P[3];
+      double rr = std::sqrt(std::max(0.0, r0 * r0 + (r1 * r1 - r0 * r0) * u[0]));
+      double phi = dir + th * (2.0 * u[1] - 1.0);
+      x = pose[ref][0] + rr * std::cos(phi);
+      y = pose[ref][1] + rr * std::sin(phi);
+    } else if (kind == REL_MIDDLE && anchors.size() == 2) {
+      x = ax[0] + u[0] * (ax[1] - ax[0]);
+      y = ay[0] + u[0] * (ay[1] - ay[0]);
+    } else if (kind == REL_MIDDLE) {
+      x = bx0 + (bx1 - bx0) * u[0];
+      y = by0 + (by1 - by0) * u[1];
+      double d;
+      in_rel = or_point_in_polygon(ax.data(), ay.data(), (int)ax.size(), x, y, &d) != 0;
+      rel_band = d <= BAND;
+    } else if (kind == REL_NEXT_TO) {
       int ao = s->tmpl_obj_off[t] + ref;
       double rho_a = s->obj_half[4 * ao + 3];
       double phi = TWO_PI * u[0];
@@ -283,12 +351,12 @@ static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int
       y = ymin + (ymax - ymin) * u[1];
     }
     bool b;
-    bool ok = support_accept(s, t, x, y, e, &b);
-    band = band || b;
+    bool ok = support_accept(s, t, x, y, e, &b) && in_rel;
+    band = band || b || rel_band;
     pose[k][0] = x;
     pose[k][1] = y;
     pose[k][2] = zs + Hz;
-    pose[k][3] = TWO_PI * u[2];
+    pose[k][3] = face_to ? std::atan2(pose[ref][1] - y, pose[ref][0] - x) : TWO_PI * u[2];
     if (ok) { *band_out = band; return true; }
   }
   *band_out = band;

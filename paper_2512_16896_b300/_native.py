@@ -34,7 +34,7 @@ class ScSceneBatch(ctypes.Structure):
                                    "max_sph")] + [
         (n, P) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel", "obj_rel_param",
                          "tmpl_poly_off", "poly_verts", "tmpl_support_z", "tmpl_obb_off", "obb", "cand_tmpl_off",
-                         "tmpl_pose_off", "tmpl_base")]
+                         "tmpl_pose_off", "tmpl_base", "obj_rel_dir", "obj_anchor_off", "obj_anchor")]
 
 
 class ScSampleParams(ctypes.Structure):
@@ -226,6 +226,7 @@ class DeviceBatch:
               "tmpl_poly_off": torch.int32, "poly_verts": torch.float32, "tmpl_support_z": torch.float32,
               "tmpl_obb_off": torch.int32, "obb": torch.float32, "cand_tmpl_off": torch.int32,
               "tmpl_base": torch.float32}
+    OPTIONAL = {"obj_rel_dir": torch.float32, "obj_anchor_off": torch.int32, "obj_anchor": torch.int32}
 
     def __init__(self, batch, device: int | str | torch.device = "cuda", pinned_host: bool = False):
         self.t = {}
@@ -235,6 +236,13 @@ class DeviceBatch:
             if x.numel() == 0:
                 x = torch.zeros(16, dtype=dt)  # keep a valid aligned pointer for empty arrays
             self.t[name] = x.to(device) if not pinned_host else x.pin_memory()
+        for name, dt in self.OPTIONAL.items():  # relation arrays a batch may leave out (NULL)
+            a = getattr(batch, name, None)
+            if a is not None and np.asarray(a).size:
+                self.t[name] = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
+                self.t[name] = self.t[name].to(device) if not pinned_host else self.t[name].pin_memory()
+        if "obj_anchor" not in self.t:  # no MIDDLE object: neither anchor array
+            self.t.pop("obj_anchor_off", None)
         tpo = np.concatenate([[0], np.cumsum(np.diff(batch.cand_tmpl_off).astype(np.int64) *
                                              np.diff(batch.tmpl_obj_off).astype(np.int64))]).astype(np.int64)
         self.t["tmpl_pose_off"] = torch.from_numpy(tpo).to(device)
@@ -249,7 +257,7 @@ class DeviceBatch:
         self.c = ScSceneBatch(
             n_t, len(batch.obj_half), len(batch.sph_local), len(batch.poly_verts), len(batch.obb), self.n_cand,
             int(nobj.max()), int(nsph.max()),
-            *[_ptr(self.t[n]) for n, _ in ScSceneBatch._fields_[8:]])
+            *[_ptr(self.t.get(n)) for n, _ in ScSceneBatch._fields_[8:]])
         if len(batch.obb) == 0:
             self.c.obb = None
 

@@ -45,6 +45,7 @@ struct sc_ctx {
   const void* scan_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int reach_extent = -1;
   int max_sph_obj = -1;
+  int ext_rel = 0;
 };
 
 struct sc_mlp {
@@ -114,6 +115,10 @@ sc_status check_batch(const sc_scene_batch* b) {
   if (!aligned(b->sph_local, 16) || !aligned(b->obj_half, 16) || !aligned(b->obj_rel_param, 16) ||
       !aligned(b->poly_verts, 8) || (b->obb && !aligned(b->obb, 16)) || (b->tmpl_base && !aligned(b->tmpl_base, 16)))
     return fail(SC_ERR_INVALID, "float4 / float2 batch arrays must be 16 / 8 byte aligned");
+  if (!b->obj_anchor_off != !b->obj_anchor) return fail(SC_ERR_INVALID, "obj_anchor_off and obj_anchor go together");
+  if ((b->obj_rel_dir && !aligned(b->obj_rel_dir, 4)) || (b->obj_anchor_off && !aligned(b->obj_anchor_off, 4)) ||
+      (b->obj_anchor && !aligned(b->obj_anchor, 4)))
+    return fail(SC_ERR_INVALID, "relation arrays must be 4-byte aligned");
   return SC_OK;
 }
 
@@ -350,6 +355,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
   a.q_reach = want_reach ? q_reach : nullptr;
   a.reach_objects = 0;
   a.max_sph_obj = 0;
+  a.ext_rel = 0;
   a.timer = nullptr;
   a.side[0] = a.side[1] = nullptr;
   a.events = nullptr;
@@ -363,15 +369,18 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
                           reinterpret_cast<const void*>((intptr_t)batch->n_templates),
                           reinterpret_cast<const void*>((intptr_t)batch->n_objects)};
     if (ctx->reach_extent < 0 || std::memcmp(key, ctx->scan_key, sizeof(key))) {
-      int out[2] = {0, 0};
-      cudaError_t e = sc::batch_scan(*batch, ctx->d_status + 2, out, ctx->stream);
+      int out[3] = {0, 0, 0};
+      int* scan_scratch = reinterpret_cast<int*>(static_cast<char*>(ctx->scratch) + 96);  // past the stats
+      cudaError_t e = sc::batch_scan(*batch, scan_scratch, out, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(e, "batch scan");
       std::memcpy(ctx->scan_key, key, sizeof(key));
       ctx->reach_extent = out[0];
       ctx->max_sph_obj = out[1];
+      ctx->ext_rel = out[2];
     }
     a.reach_objects = want_reach ? ctx->reach_extent : 0;
     a.max_sph_obj = ctx->max_sph_obj;
+    a.ext_rel = ctx->ext_rel;
   }
   if (a.reach_objects > 0) {  // side streams and events of the rounds
     const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;

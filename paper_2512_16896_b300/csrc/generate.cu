@@ -195,7 +195,7 @@ struct TryOut {
 // sphere pair within the band. Sphere-level cull (exact, same argument): a B
 // sphere farther than band + margin from every kept object's ball, or an A
 // sphere that far from object k's ball, has no pair within the band.
-template <int APL, bool PREFETCHED>
+template <int APL, bool PREFETCHED, bool EXT>
 __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& T, const WarpState& W, int c, int k,
                                           int retry, int rel, int Sprev, int Sk, int64_t pbase, uint64_t seed,
                                           const float4* ref_poses, int lane, TryCounters& cnt) {
@@ -209,13 +209,13 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
   sup.ok = T.nv >= 3 && T.nv <= kMaxPolyVerts;
   sup.z = T.z;
   sup.xmin = T.xmin; sup.xmax = T.xmax; sup.ymin = T.ymin; sup.ymax = T.ymax;
-  const ObjectSpec spec = load_object_spec(b, o0, k, rel, ref_poses, 0, g.status, lane);
+  const ObjectSpec spec = load_object_spec<EXT>(b, o0, k, rel, ref_poses, 0, g.status, lane);
   SampleResult r;
   r.placed = false;
   r.band = true;
   r.pose = make_float4(0.f, 0.f, 0.f, 0.f);
   if (sup.ok) {
-    r = warp_sample_spec(sup, spec, seed, g.max_attempts, retry, c, k, lane);
+    r = warp_sample_spec<EXT>(sup, spec, seed, g.max_attempts, retry, c, k, lane, b.obj_anchor, ref_poses);
   } else if (lane == 0) {
     latch_error(g.status, kDevBadPolygon);
   }
@@ -476,7 +476,7 @@ __device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCoun
 // distribution: warp w takes item w first, then items claimed from the
 // round's counter (the claim for the next item is issued before the current
 // one is processed); routed candidates are appended 32 at a time.
-template <int APL>
+template <int APL, bool EXT>
 __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
 #pragma unroll 1
       for (int j = lane; j <= k + 1; j += 32) cp_async4(W.off + j, b.obj_sph_off + o0 + j);
       cp_async_commit();
-      const TryOut res = gen_try<APL, true>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
+      const TryOut res =
+          gen_try<APL, true, EXT>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
       bool done = false;
       if (res.pass && g.list_reach && (rel & SC_REL_REACH)) {
         route = kRouteReach;
@@ -581,7 +582,7 @@ struct ChainArgs {
   unsigned int* counter;
 };
 
-template <int APL>
+template <int APL, bool EXT>
 __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainArgs ca) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
 #pragma unroll 1
         for (int r = 0; r <= g.max_retries && !placed; ++r) {
           const TryOut res =
-              gen_try<APL, false>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
+              gen_try<APL, false, EXT>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
           ++ntries;
           band = band || res.band;
           placed = res.pass;
@@ -853,7 +854,9 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
 }
 
 // out[0]: 1 + the largest template-local index of an object carrying the
-// reach flag; out[1]: the most spheres of one object.
+// reach flag; out[1]: the most spheres of one object; out[2]: 1 if an object
+// uses a relation beyond FREE / ON_TOP / NEXT_TO (a DIRECTIONAL or MIDDLE
+// kind, or the LOCAL or FACE_TO flag).
 __global__ void batch_scan_kernel(sc_scene_batch b, int* out) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_templates; t += gridDim.x * blockDim.x) {
     const int o0 = b.tmpl_obj_off[t], o1 = b.tmpl_obj_off[t + 1];
@@ -862,8 +865,11 @@ __global__ void batch_scan_kernel(sc_scene_batch b, int* out) {
       if (b.obj_rel[o] & SC_REL_REACH) ext = o - o0 + 1;
     if (ext) atomicMax(out, ext);
   }
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < b.n_objects; o += gridDim.x * blockDim.x)
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < b.n_objects; o += gridDim.x * blockDim.x) {
     atomicMax(out + 1, b.obj_sph_off[o + 1] - b.obj_sph_off[o]);
+    const int rel = b.obj_rel[o];
+    if ((rel & SC_REL_KIND_MASK) > SC_REL_NEXT_TO || (rel & (SC_REL_LOCAL | SC_REL_FACE_TO))) atomicMax(out + 2, 1);
+  }
 }
 
 // Per-call tables: the template of every candidate, one TmplInfo record per
@@ -951,12 +957,12 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   if (blockIdx.x == 0 && threadIdx.x < 7 && stats) stats[threadIdx.x] = 0;
 }
 
-template <int APL>
+template <int APL, bool EXT>
 cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int num_sms, int* grid) {
-  auto kern = gen_round_kernel<APL>;
+  auto kern = gen_round_kernel<APL, EXT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gen_chain_kernel<APL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(gen_chain_kernel<APL, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -967,23 +973,26 @@ cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int n
 }
 
 template <int APL>
-void launch_round(const GenStepArgs& g, int grid, int threads, size_t smem, cudaStream_t s) {
-  gen_round_kernel<APL><<<grid, threads, smem, s>>>(g);
+void launch_round(const GenStepArgs& g, bool ext, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (ext) gen_round_kernel<APL, true><<<grid, threads, smem, s>>>(g);
+  else gen_round_kernel<APL, false><<<grid, threads, smem, s>>>(g);
 }
 
 template <int APL>
-void launch_chain(const GenStepArgs& g, const ChainArgs& ca, int grid, int threads, size_t smem, cudaStream_t s) {
-  gen_chain_kernel<APL><<<grid, threads, smem, s>>>(g, ca);
+void launch_chain(const GenStepArgs& g, const ChainArgs& ca, bool ext, int grid, int threads, size_t smem,
+                  cudaStream_t s) {
+  if (ext) gen_chain_kernel<APL, true><<<grid, threads, smem, s>>>(g, ca);
+  else gen_chain_kernel<APL, false><<<grid, threads, smem, s>>>(g, ca);
 }
 
 }  // namespace
 
-cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host2, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(scratch_int2, 0, 2 * sizeof(int), s);
+cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int3, int* out_host3, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(scratch_int3, 0, 3 * sizeof(int), s);
   if (e) return e;
-  batch_scan_kernel<<<64, 256, 0, s>>>(b, scratch_int2);
+  batch_scan_kernel<<<64, 256, 0, s>>>(b, scratch_int3);
   if ((e = cudaGetLastError())) return e;
-  if ((e = cudaMemcpyAsync(out_host2, scratch_int2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaMemcpyAsync(out_host3, scratch_int3, 3 * sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
   return cudaStreamSynchronize(s);
 }
 
@@ -1082,9 +1091,18 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   int grid = 0;
   cudaError_t e;
   switch (cfg.a_per_lane) {
-    case 1: e = prepare_step_kernel<1>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
-    case 2: e = prepare_step_kernel<2>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
-    default: e = prepare_step_kernel<4>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid); break;
+    case 1:
+      e = a.ext_rel ? prepare_step_kernel<1, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                    : prepare_step_kernel<1, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      break;
+    case 2:
+      e = a.ext_rel ? prepare_step_kernel<2, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                    : prepare_step_kernel<2, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      break;
+    default:
+      e = a.ext_rel ? prepare_step_kernel<4, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                    : prepare_step_kernel<4, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      break;
   }
   if (e != cudaSuccess) return e;
   {
@@ -1173,9 +1191,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     g.counter = counters + i;
     if (a.timer) a.timer->begin(0, s);
     switch (cfg.a_per_lane) {
-      case 1: launch_round<1>(g, grid, cfg.threads, smem, s); break;
-      case 2: launch_round<2>(g, grid, cfg.threads, smem, s); break;
-      default: launch_round<4>(g, grid, cfg.threads, smem, s); break;
+      case 1: launch_round<1>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
+      case 2: launch_round<2>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
+      default: launch_round<4>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
     }
     if (a.timer) a.timer->end(s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1217,9 +1235,9 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ca.alive = st.alive;
     ca.counter = counters + NRmax;
     switch (cfg.a_per_lane) {
-      case 1: launch_chain<1>(g, ca, grid, cfg.threads, smem, s); break;
-      case 2: launch_chain<2>(g, ca, grid, cfg.threads, smem, s); break;
-      default: launch_chain<4>(g, ca, grid, cfg.threads, smem, s); break;
+      case 1: launch_chain<1>(g, ca, a.ext_rel, grid, cfg.threads, smem, s); break;
+      case 2: launch_chain<2>(g, ca, a.ext_rel, grid, cfg.threads, smem, s); break;
+      default: launch_chain<4>(g, ca, a.ext_rel, grid, cfg.threads, smem, s); break;
     }
     if (a.timer) a.timer->end(s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

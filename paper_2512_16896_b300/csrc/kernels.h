@@ -84,6 +84,7 @@ struct GenerateLaunch {
   int map_tau;
   int reach_objects;     // object indices < reach_objects may carry the reach flag
   int max_sph_obj;       // most spheres of one object in the batch (batch_scan)
+  int ext_rel;           // some object uses DIRECTIONAL / MIDDLE / LOCAL / FACE_TO (batch_scan)
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
   StageTimer* timer;     // NULL: no timing
   // rounds of the objects with reachability: two side streams for the reach
@@ -100,9 +101,10 @@ int generate_rounds(int reach_objects, int max_retries);
 size_t generate_scratch_bytes(const sc_scene_batch& b, int n_items, int max_retries);
 // Byte offset of the 8-byte seed scalar inside that scratch (256-aligned).
 size_t generate_seed_offset(const sc_scene_batch& b, int n_items, int max_retries);
-// out_host2[0]: 1 + largest object index with the reach flag; out_host2[1]:
-// most spheres of one object (uses 2 device ints; synchronises the stream).
-cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int2, int* out_host2, cudaStream_t s);
+// out_host3[0]: 1 + largest object index with the reach flag; [1]: most
+// spheres of one object; [2]: 1 if some object uses a relation beyond FREE /
+// ON_TOP / NEXT_TO (uses 3 device ints; synchronises the stream).
+cudaError_t batch_scan(const sc_scene_batch& b, int* scratch_int3, int* out_host3, cudaStream_t s);
 // Enqueues the whole generation (init + one launch per object and try).
 cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, const sc_collide_config& cfg,
                              int num_sms, cudaStream_t s, const char** why);

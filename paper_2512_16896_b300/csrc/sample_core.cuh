@@ -90,47 +90,100 @@ struct SampleResult {
   bool band;
 };
 
+constexpr int kMaxAnchors = 16;
+
 // What sampling object k needs besides the support: its relation, half
 // extents (w: rho), relation parameters and, for a relation, the reference
-// object's pose and half extents. Loaded by load_object_spec so a caller can
-// issue these loads early.
+// object's pose and half extents; for DIRECTIONAL the direction angle (the
+// anchor's yaw added under SC_REL_LOCAL), for MIDDLE where its anchors are.
+// Loaded by load_object_spec so a caller can issue these loads early.
 struct ObjectSpec {
-  int kind, ref;
+  int kind, ref, face_to;
   float4 H, RP;
   float4 ref_pose, ref_half;
+  float dir;      // DIRECTIONAL: direction angle
+  int an0, n_an;  // MIDDLE: anchors obj_anchor[an0 .. an0 + n_an)
 };
 
-// Relation of template-local object k (a relation must refer to an earlier
-// object: otherwise kDevBadRelation is latched and the object is sampled as
-// free). The reference pose is read from poses[pbase + ref], written before
-// this call (the caller orders the accesses).
+// Relation of template-local object k. A reference (parent, anchor, faced
+// object) must be an earlier object, a DIRECTIONAL object needs obj_rel_dir, a
+// MIDDLE one 2..16 earlier anchors: otherwise kDevBadRelation is latched and
+// the object is sampled as free. The reference pose is read from
+// poses[pbase + ref], written before this call (the caller orders the
+// accesses). EXT = false compiles only FREE / ON_TOP / NEXT_TO (any other
+// kind or flag is refused the same way) for batches known to use no more.
+template <bool EXT = true>
 __device__ __forceinline__ ObjectSpec load_object_spec(const sc_scene_batch& b, int o0, int k, int rel,
                                                        const float4* poses, int64_t pbase, int* status, int lane) {
   ObjectSpec S;
   const int o = o0 + k;
   S.kind = rel & SC_REL_KIND_MASK;
-  S.ref = rel >> 8;
-  if (S.kind != SC_REL_FREE && (S.ref < 0 || S.ref >= k || S.kind > SC_REL_NEXT_TO)) {
+  S.face_to = EXT && (rel & SC_REL_FACE_TO) != 0;
+  S.ref = (rel >> 8) & 0xFF;
+  S.an0 = 0;
+  S.n_an = 0;
+  S.dir = 0.f;
+  bool bad = (S.kind != SC_REL_FREE || S.face_to) && S.ref >= k;
+  bad = bad || S.kind > (EXT ? SC_REL_MIDDLE : SC_REL_NEXT_TO) || (EXT && S.kind == SC_REL_DIRECTIONAL && !b.obj_rel_dir);
+  if (EXT && S.kind == SC_REL_MIDDLE) {
+    if (!b.obj_anchor_off) {
+      bad = true;
+    } else {
+      S.an0 = __ldg(&b.obj_anchor_off[o]);
+      S.n_an = __ldg(&b.obj_anchor_off[o + 1]) - S.an0;
+      bool ok = S.n_an >= 2 && S.n_an <= kMaxAnchors;
+      if (ok) {
+        const int j = lane < S.n_an ? __ldg(&b.obj_anchor[S.an0 + lane]) : 0;
+        ok = __all_sync(0xFFFFFFFFu, j >= 0 && j < k);
+      }
+      bad = bad || !ok;
+    }
+  }
+  if (bad) {
     if (lane == 0) latch_error(status, kDevBadRelation);
     S.kind = SC_REL_FREE;
+    S.face_to = 0;
   }
   S.H = __ldg(reinterpret_cast<const float4*>(b.obj_half) + o);
   S.RP = __ldg(reinterpret_cast<const float4*>(b.obj_rel_param) + o);
   S.ref_pose = make_float4(0.f, 0.f, 0.f, 0.f);
   S.ref_half = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (S.kind != SC_REL_FREE) {
+  if (S.kind != SC_REL_FREE || S.face_to) {
     S.ref_pose = poses[pbase + S.ref];
     S.ref_half = __ldg(reinterpret_cast<const float4*>(b.obj_half) + (o0 + S.ref));
   }
+  if (EXT && S.kind == SC_REL_DIRECTIONAL)
+    S.dir = __ldg(&b.obj_rel_dir[o]) + ((rel & SC_REL_LOCAL) ? S.ref_pose.w : 0.f);
   return S;
 }
 
-// Sample object k (spec S) of candidate c for try `retry`; the whole warp
-// calls this (uniform arguments). Attempts run one per lane; the lowest
-// accepted attempt wins, which equals trying them in order. Every lane gets
-// the same result.
-__device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, const ObjectSpec& S, uint64_t seed,
-                                                        int max_attempts, int retry, int c, int k, int lane) {
+// Lowest accepted attempt of a 32-attempt chunk (or the chunk's last attempt
+// when none is accepted), folded into R: placed, band of the deciding
+// attempts, and the chosen attempt's x, y, yaw.
+__device__ __forceinline__ void take_attempt(SampleResult& R, bool acc, bool bnd, float x, float y, float yaw,
+                                             int max_attempts, int a0) {
+  const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, acc);
+  const unsigned bnd_mask = __ballot_sync(0xFFFFFFFFu, bnd);
+  int src;
+  if (acc_mask) {
+    src = __ffs(acc_mask) - 1;
+    const unsigned upto = (src == 31) ? 0xFFFFFFFFu : ((2u << src) - 1u);
+    R.band = R.band || (bnd_mask & upto);
+    R.placed = true;
+  } else {
+    R.band = R.band || bnd_mask;
+    src = min(31, max_attempts - 1 - a0);  // last attempt of this chunk
+  }
+  R.pose.x = __shfl_sync(0xFFFFFFFFu, x, src);
+  R.pose.y = __shfl_sync(0xFFFFFFFFu, y, src);
+  R.pose.w = __shfl_sync(0xFFFFFFFFu, yaw, src);
+}
+
+// FREE, NEXT_TO and ON_TOP objects (Sec. III, IV-C, IV-F). Attempts run one
+// per lane; the lowest accepted attempt wins, which equals trying them in
+// order. Every lane gets the same result.
+__device__ __forceinline__ SampleResult warp_sample_basic(const Support& sup, const ObjectSpec& S, uint64_t seed,
+                                                         int max_attempts, int retry, int c, int k, int lane) {
   SampleResult R;
   R.band = false;
   R.placed = false;
@@ -181,23 +234,124 @@ __device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, con
       acc = inside && dist >= e;
       bnd = dist <= kBand || (inside && fabsf(dist - e) <= kBand);
     }
-    const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, acc);
-    const unsigned bnd_mask = __ballot_sync(0xFFFFFFFFu, bnd);
-    int src;
-    if (acc_mask) {
-      src = __ffs(acc_mask) - 1;
-      const unsigned upto = (src == 31) ? 0xFFFFFFFFu : ((2u << src) - 1u);
-      R.band = R.band || (bnd_mask & upto);
-      R.placed = true;
-    } else {
-      R.band = R.band || bnd_mask;
-      src = min(31, max_attempts - 1 - a0);  // last attempt of this chunk
-    }
-    R.pose.x = __shfl_sync(0xFFFFFFFFu, x, src);
-    R.pose.y = __shfl_sync(0xFFFFFFFFu, y, src);
-    R.pose.w = __shfl_sync(0xFFFFFFFFu, yaw, src);
+    take_attempt(R, acc, bnd, x, y, yaw, max_attempts, a0);
   }
   R.pose.z = sup.z + H.z;
+  return R;
+}
+
+// Position of object j of the candidate (anchors of a MIDDLE relation).
+__device__ __forceinline__ float2 object_xy(const float4* poses, int j) {
+  const float4 p = poses[j];
+  return make_float2(p.x, p.y);
+}
+
+// DIRECTIONAL and MIDDLE objects (Sec. IV-F), out of line so the common
+// kinds do not carry this code. Attempts as in warp_sample_spec, with the
+// proposal:
+//   DIRECTIONAL: area-uniform in the sector of half-angle RP.w around S.dir
+//     between radii RP.x and min(RP.y, the farthest support-box corner from
+//     the anchor), measured from the anchor's position;
+//   MIDDLE: on the segment between two anchors, or uniform in the bounding
+//     box of 3+ anchors and kept inside their polygon (crossing number,
+//     boundary inside; within the band of its boundary flags the attempt).
+// anchors: the batch's obj_anchor; poses: the candidate's object poses.
+static __device__ __noinline__ SampleResult warp_sample_special(const Support& sup, const ObjectSpec& S, uint64_t seed,
+                                                                int max_attempts, int retry, int c, int k, int lane,
+                                                                const int32_t* anchors, const float4* poses) {
+  SampleResult R;
+  R.band = false;
+  R.placed = false;
+  R.pose = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 H = S.H, RP = S.RP;
+  const float e = RP.z * fminf(H.x, H.y);  // ratio_on_support erosion
+  const bool directional = S.kind == SC_REL_DIRECTIONAL;
+  const int n = S.n_an;
+  const int32_t* an = anchors + S.an0;
+  float r1 = 0.f;
+  float4 box = make_float4(3e38f, -3e38f, 3e38f, -3e38f);
+  if (directional) {
+    const float dx = fmaxf(fabsf(sup.xmin - S.ref_pose.x), fabsf(sup.xmax - S.ref_pose.x));
+    const float dy = fmaxf(fabsf(sup.ymin - S.ref_pose.y), fabsf(sup.ymax - S.ref_pose.y));
+    r1 = fminf(RP.y, sqrtf(dx * dx + dy * dy));
+  } else {
+    for (int i = 0; i < n; ++i) {
+      const float2 a = object_xy(poses, __ldg(&an[i]));
+      box.x = fminf(box.x, a.x); box.y = fmaxf(box.y, a.x);
+      box.z = fminf(box.z, a.y); box.w = fmaxf(box.w, a.y);
+    }
+  }
+  for (int a0 = 0; a0 < max_attempts && !R.placed; a0 += 32) {
+    const int a = a0 + lane;
+    const float4 u = draw_uniform4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, (uint32_t)a);
+    float x = 0.f, y = 0.f;
+    bool acc = false, bnd = false;
+    if (a < max_attempts) {
+      bool in_rel = true;
+      if (directional) {
+        const float r0 = RP.x;
+        const float rho = sqrtf(fmaxf(0.f, r0 * r0 + (r1 * r1 - r0 * r0) * u.x));
+        float sn, cs;
+        sincosf(S.dir + RP.w * (2.f * u.y - 1.f), &sn, &cs);
+        x = S.ref_pose.x + rho * cs;
+        y = S.ref_pose.y + rho * sn;
+      } else if (n == 2) {
+        const float2 p = object_xy(poses, __ldg(&an[0])), q = object_xy(poses, __ldg(&an[1]));
+        x = p.x + u.x * (q.x - p.x);
+        y = p.y + u.x * (q.y - p.y);
+      } else {
+        x = box.x + (box.y - box.x) * u.x;
+        y = box.z + (box.w - box.z) * u.y;
+        bool odd = false;
+        float d2 = 3.0e38f;
+        float2 p = object_xy(poses, __ldg(&an[n - 1]));
+        for (int i = 0; i < n; ++i) {
+          const float2 q = object_xy(poses, __ldg(&an[i]));
+          const float ex = q.x - p.x, ey = q.y - p.y, wx = x - p.x, wy = y - p.y;
+          const float len2 = ex * ex + ey * ey;
+          float t = len2 > 0.f ? (wx * ex + wy * ey) / len2 : 0.f;
+          t = fminf(fmaxf(t, 0.f), 1.f);
+          const float qx = wx - t * ex, qy = wy - t * ey;
+          d2 = fminf(d2, qx * qx + qy * qy);
+          if ((p.y > y) != (q.y > y)) {
+            const float lhs = wx * ey, rhs = wy * ex;
+            if (ey > 0.f ? lhs < rhs : lhs > rhs) odd = !odd;
+          }
+          p = q;
+        }
+        in_rel = odd || d2 == 0.f;
+        bnd = sqrtf(d2) <= kBand;
+      }
+      float dist;
+      const bool inside = pip_with_distance(sup.P, x, y, &dist);
+      acc = in_rel && inside && dist >= e;
+      bnd = bnd || dist <= kBand || (inside && fabsf(dist - e) <= kBand);
+    }
+    take_attempt(R, acc, bnd, x, y, kTwoPi * u.z, max_attempts, a0);
+  }
+  R.pose.z = sup.z + H.z;
+  return R;
+}
+
+// Sample object k (spec S) of candidate c for try `retry`; the whole warp
+// calls this (uniform arguments). Attempts run one per lane; the lowest
+// accepted attempt wins, which equals trying them in order. Every lane gets
+// the same result. With SC_REL_FACE_TO the yaw of the chosen attempt faces
+// the reference object (the yaw takes no part in acceptance). anchors: the
+// batch's obj_anchor; poses: the candidate's object poses (MIDDLE anchors).
+// EXT = false: the basic kinds only (see load_object_spec).
+template <bool EXT = true>
+__device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, const ObjectSpec& S, uint64_t seed,
+                                                        int max_attempts, int retry, int c, int k, int lane,
+                                                        const int32_t* anchors, const float4* poses) {
+  if (!EXT) return warp_sample_basic(sup, S, seed, max_attempts, retry, c, k, lane);
+  SampleResult R;
+  if (S.kind >= SC_REL_DIRECTIONAL) {
+    R = warp_sample_special(sup, S, seed, max_attempts, retry, c, k, lane, anchors, poses);
+  } else {
+    R = warp_sample_basic(sup, S, seed, max_attempts, retry, c, k, lane);
+  }
+  if (S.face_to && S.kind != SC_REL_ON_TOP) R.pose.w = atan2f(S.ref_pose.y - R.pose.y, S.ref_pose.x - R.pose.x);
   return R;
 }
 
@@ -208,7 +362,7 @@ __device__ __forceinline__ SampleResult warp_sample_object(const sc_scene_batch&
                                                           int o0, const float4* poses, int64_t pbase, int* status,
                                                           int lane) {
   const ObjectSpec S = load_object_spec(b, o0, k, __ldg(&b.obj_rel[o0 + k]), poses, pbase, status, lane);
-  return warp_sample_spec(sup, S, seed, max_attempts, retry, c, k, lane);
+  return warp_sample_spec(sup, S, seed, max_attempts, retry, c, k, lane, b.obj_anchor, poses + pbase);
 }
 
 }  // namespace sc

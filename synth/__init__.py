@@ -29,8 +29,8 @@ import math
 
 import numpy as np
 
-REL_FREE, REL_ON_TOP, REL_NEXT_TO = 0, 1, 2
-REL_REACH = 0x10
+REL_FREE, REL_ON_TOP, REL_NEXT_TO, REL_DIRECTIONAL, REL_MIDDLE = 0, 1, 2, 3, 4
+REL_REACH, REL_LOCAL, REL_FACE_TO = 0x10, 0x20, 0x40
 
 # 7-DoF arm used by the reachability workload: standard DH parameters.
 ARM_D = (0.333, 0.0, 0.316, 0.0, 0.384, 0.0, 0.107)
@@ -48,8 +48,10 @@ class SceneBatch:
       obj_sph_off   int32 [O+1]  spheres of object o
       sph_local     f32 [S,4]    (x, y, z, r) in the object frame
       obj_half      f32 [O,4]    (Hx, Hy, Hz, rho_xy)
-      obj_rel       int32 [O]    kind | REL_REACH flag | (reference local index << 8)
-      obj_rel_param f32 [O,4]    (dmin, dmax, ratio_on_support, 0)
+      obj_rel       int32 [O]    kind | flags (REL_REACH, REL_LOCAL, REL_FACE_TO) | (reference local index << 8)
+      obj_rel_param f32 [O,4]    (dmin, dmax, ratio_on_support, 0); directional: (min_r, max_r, ratio, theta)
+      obj_rel_dir   f32 [O]      direction angle of a directional relation (radians)
+      obj_anchor_off int32 [O+1]; obj_anchor int32 [A]: anchors (local indices) of a middle relation
       tmpl_poly_off int32 [T+1]; poly_verts f32 [V,2] (CCW)
       tmpl_support_z f32 [T]
       tmpl_obb_off  int32 [T+1]; obb f32 [n_obb,12] centre(x,y,z,0) quat(x,y,z,w) half(x,y,z,0)
@@ -70,6 +72,9 @@ class SceneBatch:
     obb: np.ndarray
     cand_tmpl_off: np.ndarray
     tmpl_base: np.ndarray
+    obj_rel_dir: np.ndarray = None
+    obj_anchor_off: np.ndarray = None
+    obj_anchor: np.ndarray = None
     name: str = ""
 
     @property
@@ -117,9 +122,11 @@ class SceneBatch:
             s0, s1 = int(self.obj_sph_off[o0]), int(self.obj_sph_off[o1])
             v0, v1 = int(self.tmpl_poly_off[t]), int(self.tmpl_poly_off[t + 1])
             b0, b1 = int(self.tmpl_obb_off[t]), int(self.tmpl_obb_off[t + 1])
+            anchors = [list(self.obj_anchor[self.obj_anchor_off[o]:self.obj_anchor_off[o + 1]]) for o in range(o0, o1)]
             parts.append(dict(
                 sph=self.sph_local[s0:s1], nsph=np.diff(self.obj_sph_off[o0:o1 + 1]),
                 half=self.obj_half[o0:o1], rel=self.obj_rel[o0:o1], relp=self.obj_rel_param[o0:o1],
+                dir=self.obj_rel_dir[o0:o1], anchors=anchors,
                 poly=self.poly_verts[v0:v1], z=self.tmpl_support_z[t], obb=self.obb[b0:b1],
                 ncand=int(self.cand_tmpl_off[t + 1] - self.cand_tmpl_off[t]), base=self.tmpl_base[t]))
         return _pack(parts, name=f"{self.name}[subset {len(templates)}]")
@@ -131,6 +138,7 @@ def _pack(parts, name="") -> SceneBatch:
 
     nobj = [len(p["half"]) for p in parts]
     nsph = np.concatenate([p["nsph"] for p in parts]).astype(np.int64)
+    anchors = [list(a) for p in parts for a in p.get("anchors", [[]] * len(p["half"]))]
     return SceneBatch(
         tmpl_obj_off=off(nobj),
         obj_sph_off=off(nsph),
@@ -145,6 +153,10 @@ def _pack(parts, name="") -> SceneBatch:
         obb=np.ascontiguousarray(np.concatenate([p["obb"] for p in parts]).astype(np.float32).reshape(-1, 12)),
         cand_tmpl_off=off([p["ncand"] for p in parts]),
         tmpl_base=np.ascontiguousarray(np.array([p["base"] for p in parts], dtype=np.float32).reshape(-1, 4)),
+        obj_rel_dir=np.ascontiguousarray(np.concatenate([p.get("dir", np.zeros(len(p["half"]))) for p in parts])
+                                         .astype(np.float32)),
+        obj_anchor_off=off([len(a) for a in anchors]),
+        obj_anchor=np.array([i for a in anchors for i in a], dtype=np.int32),
         name=name,
     )
 
@@ -184,6 +196,56 @@ def draw_relations(rng: np.random.Generator, n: int, n_reach: int = 0):
     return rel.astype(np.int32)
 
 
+def draw_relations_hard(rng: np.random.Generator, n: int, n_reach: int = 0):
+    """The full relation set of Sec. IV-F: object 0 free; of objects 1..n-1
+    (random permutation) about 15% on-top, 15% next-to, 30% directional
+    (one anchor: a partial annulus around it, direction +-x / +-y or a random
+    angle, in the world or the anchor's frame, half-angle pi/8, pi/4 or pi/2,
+    distance 'greater' [d, inf), 'less' [0, d] or 'equal' [d - 0.02, d + 0.02]
+    with d ~ U(0.2, 0.6) m measured between positions), 15% middle (2 to 4
+    earlier anchors) and the rest free; a quarter of the non-on-top objects
+    face a random earlier object. Returns (rel, relp, dir, anchors)."""
+    kinds = np.zeros(n, dtype=np.int32)
+    refs = np.zeros(n, dtype=np.int32)
+    relp = np.tile(np.array([0.05, 0.2, 0.0, 0.0], dtype=np.float32), (n, 1))
+    dirs = np.zeros(n, dtype=np.float32)
+    flags = np.zeros(n, dtype=np.int32)
+    anchors = [[] for _ in range(n)]
+    perm = rng.permutation(np.arange(1, n))
+    m = len(perm)
+    cut = np.cumsum([int(round(f * m)) for f in (0.15, 0.15, 0.30, 0.15)])
+    kinds[perm[:cut[0]]] = REL_ON_TOP
+    kinds[perm[cut[0]:cut[1]]] = REL_NEXT_TO
+    kinds[perm[cut[1]:cut[2]]] = REL_DIRECTIONAL
+    kinds[perm[cut[2]:cut[3]]] = REL_MIDDLE
+    for k in range(1, n):
+        refs[k] = rng.integers(0, k)
+        if kinds[k] == REL_DIRECTIONAL:
+            choice = rng.integers(0, 5)
+            dirs[k] = [0.0, math.pi, 0.5 * math.pi, -0.5 * math.pi, 0.0][choice]
+            if choice == 4:
+                dirs[k] = rng.uniform(-math.pi, math.pi)
+            if rng.uniform() < 0.5:
+                flags[k] |= REL_LOCAL
+            theta = [math.pi / 8, math.pi / 4, math.pi / 2][rng.integers(0, 3)]
+            d = rng.uniform(0.2, 0.6)
+            dt = rng.integers(0, 3)
+            lo, hi = [(d, math.inf), (0.0, d), (d - 0.02, d + 0.02)][dt]
+            relp[k] = [lo, hi, 0.0, theta]
+        elif kinds[k] == REL_MIDDLE:
+            na = min(k, int(rng.integers(2, 5)))
+            if na < 2:
+                kinds[k] = REL_FREE
+            else:
+                anchors[k] = sorted(rng.choice(k, size=na, replace=False).tolist())
+                refs[k] = anchors[k][0]
+        if kinds[k] != REL_ON_TOP and rng.uniform() < 0.25:
+            flags[k] |= REL_FACE_TO
+    rel = kinds | flags | (refs << 8)
+    rel[: min(n_reach, n)] |= REL_REACH
+    return rel.astype(np.int32), relp, dirs, anchors
+
+
 def rect_polygon(lx: float, ly: float) -> np.ndarray:
     return np.array([[-lx / 2, -ly / 2], [lx / 2, -ly / 2], [lx / 2, ly / 2], [-lx / 2, ly / 2]], dtype=np.float32)
 
@@ -221,17 +283,22 @@ def make_template(rng, n_obj, sph_counts, poly, support_z=0.75, n_obb=0, relatio
         sph.append(s)
         nsph.append(len(s))
         half.append([h[0], h[1], h[2], rho])
-    if relations:
+    dirs = np.zeros(n_obj, dtype=np.float32)
+    anchors = [[] for _ in range(n_obj)]
+    relp = np.tile(np.array([0.05, 0.2, ratio_on_support, 0.0], dtype=np.float32), (n_obj, 1))
+    if relations == "hard":
+        rel, relp, dirs, anchors = draw_relations_hard(rng, n_obj, n_reach)
+        relp[:, 2] = ratio_on_support
+    elif relations:
         rel = draw_relations(rng, n_obj, n_reach)
     else:
         rel = np.zeros(n_obj, dtype=np.int32)
         rel[: min(n_reach, n_obj)] |= REL_REACH
-    relp = np.tile(np.array([0.05, 0.2, ratio_on_support, 0.0], dtype=np.float32), (n_obj, 1))
     obb = random_obbs(rng, n_obb) if n_obb else np.zeros((0, 12), np.float32)
     if base is None:  # robot at the middle of the support's -x side, facing +x
         base = [float(poly[:, 0].min()), 0.0, support_z, 0.0]
     return dict(sph=np.concatenate(sph), nsph=np.array(nsph), half=np.array(half, np.float32), rel=rel, relp=relp,
-                poly=poly, z=support_z, obb=obb, base=np.array(base, np.float32))
+                dir=dirs, anchors=anchors, poly=poly, z=support_z, obb=obb, base=np.array(base, np.float32))
 
 
 def tabletop(seed: int = 0, n_cand: int = 1024, n_obj: int = 8, n_sph: int = 16) -> SceneBatch:
@@ -265,6 +332,23 @@ def ragged(seed: int = 2, n_templates: int = 4096, cand_per_template: int = 64, 
         p["ncand"] = cand_per_template
         parts.append(p)
     return _pack(parts, name=f"ragged T={n_templates}x{cand_per_template}")
+
+
+def hard(seed: int = 5, n_templates: int = 256, cand_per_template: int = 64, obj_range=(6, 24),
+         sph_range=(8, 64), n_reach: int = 0) -> SceneBatch:
+    """Relation-heavy workload, a stand-in for the paper's harder benchmark
+    scenes (Sec. V-A): every template uses the full relation set
+    (draw_relations_hard) on a convex 4..10-gon support of area 1..3 m^2."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_templates):
+        n = int(rng.integers(obj_range[0], obj_range[1] + 1))
+        counts = rng.integers(sph_range[0], sph_range[1] + 1, size=n)
+        poly = convex_polygon(rng, int(rng.integers(4, 11)), float(rng.uniform(1.0, 3.0)))
+        p = make_template(rng, n, counts, poly, relations="hard", n_reach=n_reach)
+        p["ncand"] = cand_per_template
+        parts.append(p)
+    return _pack(parts, name=f"hard T={n_templates}x{cand_per_template}")
 
 
 def random_poses(batch: SceneBatch, seed: int, spread: float = 0.6) -> np.ndarray:

@@ -4,13 +4,19 @@ import numpy as np
 import synth
 
 
-def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_cand=1, rel=None):
-    """objects: list of sphere lists [(x,y,z,r), ...] in object frames."""
+def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_cand=1, rel=None, relp=None,
+               dirs=None, anchors=None):
+    """objects: list of sphere lists [(x,y,z,r), ...] in object frames; rel,
+    relp, dirs, anchors: per-object relation fields (defaults: all free)."""
+    n = len(objects)
     parts = dict(
         sph=np.array([s for o in objects for s in o], np.float32), nsph=np.array([len(o) for o in objects]),
-        half=np.array([[0.1, 0.1, 0.1, 0.15]] * len(objects), np.float32),
-        rel=np.zeros(len(objects), np.int32) if rel is None else np.array(rel, np.int32),
-        relp=np.tile(np.array([0.05, 0.2, 0.0, 0.0], np.float32), (len(objects), 1)),
+        half=np.array([[0.1, 0.1, 0.1, 0.15]] * n, np.float32),
+        rel=np.zeros(n, np.int32) if rel is None else np.array(rel, np.int32),
+        relp=np.tile(np.array([0.05, 0.2, 0.0, 0.0], np.float32), (n, 1)) if relp is None
+        else np.array(relp, np.float32).reshape(n, 4),
+        dir=np.zeros(n, np.float32) if dirs is None else np.array(dirs, np.float32),
+        anchors=[[] for _ in range(n)] if anchors is None else [list(a) for a in anchors],
         poly=np.array(poly, np.float32), z=0.0, obb=np.array(obbs, np.float32).reshape(-1, 12), ncand=n_cand,
         base=np.zeros(4, np.float32))
     return synth._pack([parts])

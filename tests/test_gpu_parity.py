@@ -84,6 +84,52 @@ def test_sample_all_objects(sc, ctx, make, seed):
     assert d[rows].max() <= TOL_POSE, d[rows].max(axis=0)
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_sample_relation_set(sc, ctx, seed):
+    """The full relation set of Sec. IV-F (on-top, next-to, directional in the
+    world and the anchor's frame with finite and open radii, middle of 2..4
+    anchors, face-to), chained through earlier objects' poses."""
+    b = synth.hard(seed=seed, n_templates=48, cand_per_template=16)
+    kinds = b.obj_rel & 0xF
+    assert (kinds == synth.REL_DIRECTIONAL).any() and (kinds == synth.REL_MIDDLE).any()
+    assert (b.obj_rel & synth.REL_FACE_TO).any() and (b.obj_rel & synth.REL_LOCAL).any()
+    db = sc.DeviceBatch(b)
+    gp, gok, gband = sc.sample_poses(ctx, db, seed=seed)
+    ctx.synchronize()
+    op, ook, oband = oracle.sample_poses(b, seed=seed)
+    band, d = check_samples(gp, gok, gband, op, ook, oband, max_band_frac=0.02)
+    # a face-to yaw is the direction to the reference: compare the aimed point,
+    # i.e. the yaw difference times the distance to the reference (metres)
+    offs, t_of = oracle.pose_offsets(b), b.cand_template()
+    for c in range(b.n_cand):
+        o0 = b.tmpl_obj_off[t_of[c]]
+        for k in range(b.n_obj_of(t_of[c])):
+            rel = int(b.obj_rel[o0 + k])
+            if rel & synth.REL_FACE_TO and (rel & 0xF) != synth.REL_ON_TOP:
+                row, ref = offs[c] + k, offs[c] + ((rel >> 8) & 0xFF)
+                d[row, 3] *= np.hypot(*(op[ref, :2] - op[row, :2]))
+    rows = pose_rows(b, np.nonzero(~band)[0])
+    assert d[rows].max() <= TOL_POSE, d[rows].max(axis=0)
+    assert 0.05 < ook.mean() < 0.95
+
+
+def test_relation_arrays_validated(sc, ctx):
+    """A batch with anchors but no anchor offsets is refused on the host; a
+    MIDDLE object whose anchors name itself latches a device error."""
+    b = synth.hard(seed=3, n_templates=4, cand_per_template=4)
+    db = sc.DeviceBatch(b)
+    db.c.obj_anchor_off = None
+    with pytest.raises(sc.SceniError):
+        sc.sample_poses(ctx, db, seed=1)
+    rel = [0, 0, synth.REL_MIDDLE]
+    bad = tiny_batch([[(0, 0, 0, 0.01)]] * 3, n_cand=4, rel=rel, anchors=[[], [], [0, 2]])
+    sc.sample_poses(ctx, sc.DeviceBatch(bad), seed=1)
+    with pytest.raises(sc.SceniError) as ei:
+        ctx.synchronize()
+    assert ei.value.status == 6
+    ctx.synchronize()
+
+
 def test_sample_active_list_retry_and_object_range(sc, ctx):
     """A subset of candidates, retry index 3, objects 2..5 only, with objects
     0..1 sampled by an earlier call on each side."""

@@ -629,3 +629,102 @@ def test_rmap_counts_and_scores():
     one[875] = (1, 3)
     assert rmap.score(RM_P, one, _topdown([0.55, 0.0, 0.25], 0.0)[None])[0] == 21845
     assert rmap.score(RM_P, one, _topdown([0.15, 0.0, 0.25], 0.0)[None])[0] == 65535  # an empty cell
+
+
+# --------------------------------------------------------------------------- Sec. IV-F relation set
+
+BIG = ((-50, -50), (50, -50), (50, 50), (-50, 50))  # a support no proposal leaves
+ONE = [(0.0, 0.0, 0.0, 0.01)]
+
+
+def _fixed_anchor_samples(rel, relp, dirs, n_cand, anchors=None, n_obj=2, anchor_poses=None, poly=BIG, seed=21):
+    """Sample the last object of a tiny template with the earlier objects
+    placed at anchor_poses (x, y, z, yaw) in every candidate."""
+    b = tiny_batch([ONE] * n_obj, poly=poly, n_cand=n_cand, rel=rel, relp=relp, dirs=dirs, anchors=anchors)
+    poses = np.zeros((b.n_poses(), 4))
+    for k, p in enumerate(anchor_poses):
+        poses[k::n_obj] = p
+    p, ok, band = oracle.sample_poses(b, seed=seed, first_obj=n_obj - 1, n_obj=1, poses=poses)
+    return p[n_obj - 1::n_obj], ok, band
+
+
+def test_directional_sector_area_uniform():
+    """DIRECTIONAL with v at 40 deg in the anchor's frame (anchor yaw 30 deg),
+    theta = 25 deg, radii [0.3, 0.9] m on a support no proposal leaves: every
+    point lies in the sector, r^2 is uniform on [0.09, 0.81] and the angle
+    uniform on v +- theta (area-uniform over the partial annulus)."""
+    th, yaw_a, v = math.radians(25), math.radians(30), math.radians(40)
+    rel = [0, synth.REL_DIRECTIONAL | synth.REL_LOCAL]
+    relp = [[0.05, 0.2, 0, 0], [0.3, 0.9, 0, th]]
+    p, ok, band = _fixed_anchor_samples(rel, relp, [0, v], 4000, anchor_poses=[(1.0, -2.0, 0.0, yaw_a)])
+    assert ok.all() and not band.any()
+    d = p[:, :2] - [1.0, -2.0]
+    r2 = (d ** 2).sum(1)
+    ang = np.arctan2(d[:, 1], d[:, 0]) - (v + yaw_a)
+    assert r2.min() >= 0.09 - 1e-12 and r2.max() <= 0.81 + 1e-12 and np.abs(ang).max() <= th + 1e-12
+    assert stats.kstest(r2, stats.uniform(0.09, 0.72).cdf).pvalue > 1e-3
+    assert stats.kstest(ang, stats.uniform(-th, 2 * th).cdf).pvalue > 1e-3
+
+
+def test_directional_greater_is_cut_at_the_support():
+    """max_r = inf ('greater'): the radius range ends at the support box's
+    farthest corner from the anchor, and the support decides the rest."""
+    sq = ((-1, -1), (1, -1), (1, 1), (-1, 1))
+    rel = [0, synth.REL_DIRECTIONAL]
+    relp = [[0.05, 0.2, 0, 0], [0.5, math.inf, 0, math.pi]]
+    p, ok, band = _fixed_anchor_samples(rel, relp, [0, 0.0], 3000, anchor_poses=[(0.2, 0.0, 0.0, 0.0)], poly=sq)
+    d = np.hypot(p[:, 0] - 0.2, p[:, 1])
+    assert d.min() >= 0.5 - 1e-12 and d.max() <= math.hypot(1.2, 1.0) + 1e-12
+    acc = ok.astype(bool)
+    assert acc.mean() > 0.9
+    assert np.all(np.abs(p[acc, :2]) <= 1.0 + 1e-12)
+
+
+def test_middle_triangle_and_segment():
+    """MIDDLE of three anchors: every accepted point is inside the triangle and
+    the points are uniform over it (the first barycentric coordinate of a
+    uniform point has CDF 1 - (1 - x)^2); of two anchors: on the segment,
+    with the position along it uniform."""
+    A = np.array([[0.0, 0.0], [1.0, 0.2], [0.3, 0.9]])
+    rel = [0, 0, 0, synth.REL_MIDDLE]
+    anchors = [[], [], [], [0, 1, 2]]
+    p, ok, band = _fixed_anchor_samples(rel, None, None, 4000, anchors=anchors, n_obj=4,
+                                        anchor_poses=[(*A[0], 0, 0), (*A[1], 0, 0), (*A[2], 0, 0)])
+    acc = ok.astype(bool) & ~band.astype(bool)
+    assert acc.mean() > 0.95
+    T = np.array([A[1] - A[0], A[2] - A[0]]).T
+    lam = np.linalg.solve(T, (p[acc, :2] - A[0]).T).T
+    l0 = 1 - lam.sum(1)
+    assert lam.min() >= -1e-9 and l0.min() >= -1e-9
+    assert stats.kstest(l0, lambda x: 1 - (1 - np.clip(x, 0, 1)) ** 2).pvalue > 1e-3
+    rel2, anchors2 = [0, 0, synth.REL_MIDDLE], [[], [], [1, 0]]
+    q, ok2, _ = _fixed_anchor_samples(rel2, None, None, 3000, anchors=anchors2, n_obj=3,
+                                      anchor_poses=[(0.5, 0.5, 0, 0), (-0.5, 0.1, 0, 0)])
+    t = (q[:, 0] - (-0.5)) / 1.0
+    assert ok2.all()
+    assert np.allclose(q[:, 1], 0.1 + t * 0.4, atol=1e-12)
+    assert stats.kstest(t, stats.uniform(0, 1).cdf).pvalue > 1e-3
+
+
+def test_face_to_points_at_the_reference():
+    """FACE_TO on a free object: its yaw points from it to the reference."""
+    rel = [0, synth.REL_FACE_TO | (0 << 8)]
+    p, ok, _ = _fixed_anchor_samples(rel, None, None, 500, anchor_poses=[(0.3, -0.4, 0.0, 1.0)],
+                                     poly=((-1, -1), (1, -1), (1, 1), (-1, 1)))
+    d = np.array([0.3, -0.4]) - p[:, :2]
+    u = np.stack([np.cos(p[:, 3]), np.sin(p[:, 3])], 1)
+    assert np.allclose((u * d).sum(1), np.hypot(d[:, 0], d[:, 1]), atol=1e-12)
+
+
+def test_bad_relations_sample_free():
+    """A MIDDLE object with one anchor, or one naming a later object, and a
+    DIRECTIONAL one referring forward are sampled as free objects (the same
+    draws as a free object)."""
+    free, _, _ = _fixed_anchor_samples([0, 0, 0], None, None, 50, n_obj=3, anchor_poses=[(0, 0, 0, 0), (0.5, 0, 0, 0)],
+                                       poly=((-1, -1), (1, -1), (1, 1), (-1, 1)))
+    for rel, anchors in (([0, 0, synth.REL_MIDDLE], [[], [], [0]]), ([0, 0, synth.REL_MIDDLE], [[], [], [0, 2]]),
+                         ([0, 0, synth.REL_DIRECTIONAL | (2 << 8)], None)):
+        p, _, _ = _fixed_anchor_samples(rel, None, [0, 0, 0.5], 50, anchors=anchors, n_obj=3,
+                                        anchor_poses=[(0, 0, 0, 0), (0.5, 0, 0, 0)],
+                                        poly=((-1, -1), (1, -1), (1, 1), (-1, 1)))
+        assert np.array_equal(p, free)
