@@ -74,6 +74,9 @@ WORKLOADS = {
                    desc="ragged 4096 templates x 64 candidates, 4-64 objects, 8-128 spheres/object, convex 4-10-gon supports"),
     "shelf": dict(make=lambda seed: synth.shelf(seed=seed), seed=1,
                   desc="shelf 65536 candidates x 32 objects x 64 spheres, 25% on-top / 25% next-to, 20 world OBBs"),
+    "hard": dict(make=lambda seed: synth.hard(seed=seed, n_templates=4096, n_reach=4), seed=5,
+                 desc="relation-heavy 4096 templates x 64 candidates, 6-24 objects, 8-64 spheres/object, "
+                      "on-top / next-to / directional / middle / face-to, convex 4-10-gon supports of 1-3 m^2"),
     "tabletop": dict(make=lambda seed: synth.tabletop(seed=seed), seed=0,
                      desc="tabletop 1024 candidates x 8 objects x 16 spheres on a 1.2 x 0.8 m table"),
 }
