@@ -74,6 +74,7 @@ enum {
   SC_REL_NEXT_TO = 2,
   SC_REL_DIRECTIONAL = 3, /* one anchor, partial annulus (direction, half-angle, radii) */
   SC_REL_MIDDLE = 4,      /* two or more anchors: inside the polygon of their positions */
+  SC_REL_INSIDE = 5,      /* on the inside support of an articulated part (reference = part index) */
   SC_REL_KIND_MASK = 0xF,
   SC_REL_REACH = 0x10,    /* reachability check (sc_generate) */
   SC_REL_LOCAL = 0x20,    /* DIRECTIONAL: direction angle in the anchor's frame */
@@ -106,12 +107,27 @@ enum {
  *                             template-local indices of earlier objects, polygon order)
  *                             of object o are obj_anchor[obj_anchor_off[o] ..
  *                             obj_anchor_off[o+1]); may be NULL when no object is MIDDLE.
+ *  Articulated parts (prismatic, e.g. drawers; all NULL / 0 when there are none):
+ *  tmpl_part_off int32 [T+1]  parts of template t: [tmpl_part_off[t], tmpl_part_off[t+1]), at
+ *                             most 16 per template; template-local part j is part
+ *                             tmpl_part_off[t] + j.
+ *  part_param    float [n_parts][12]  (ax, ay, az, qmin), (qmax, cx, cy, cz), (hx, hy, yaw, -):
+ *                             joint axis (unit, template frame) and range; the part's
+ *                             inside support at q = 0, a rectangle of half extents hx, hy
+ *                             turned by yaw about z, centred at (cx, cy) on the plane z = cz.
+ *                             At joint value q the part and its support move by q * axis.
+ *  obb_part      int32 [n_obb] template-local part a world box moves with (-1: static).
+ *  part_q        float [n_cand][max_parts] joint value of every part per candidate
+ *                             (sc_sample_parts writes them); read by sampling (INSIDE),
+ *                             collision and generation.
  *  tmpl_poly_off int32 [T+1], poly_verts float [V][2]: support polygon of template t
  *                             (closed, any orientation, >= 3 vertices) on the plane
  *                             z = tmpl_support_z[t].
- *  tmpl_obb_off  int32 [T+1], obb float [n_obb][12]: static world boxes of template t,
+ *  tmpl_obb_off  int32 [T+1], obb float [n_obb][12]: world boxes of template t,
  *                             each (cx, cy, cz, -, qx, qy, qz, qw, hx, hy, hz, -); the
- *                             quaternion need not be normalised.
+ *                             quaternion need not be normalised. A box of an articulated
+ *                             part (obb_part >= 0) is centred at c + q * axis for each
+ *                             candidate's joint value q of that part.
  *  cand_tmpl_off int32 [T+1]  candidates of template t: [cand_tmpl_off[t], cand_tmpl_off[t+1]);
  *                             the global candidate index is the Philox counter word 0.
  *  tmpl_pose_off int64 [T+1]  start of template t's block in the pose array; candidate
@@ -142,6 +158,11 @@ typedef struct {
   const float* obj_rel_dir;
   const int32_t* obj_anchor_off;
   const int32_t* obj_anchor;
+  int32_t n_parts, max_parts;
+  const int32_t* tmpl_part_off;
+  const float* part_param;
+  const int32_t* obb_part;
+  const float* part_q;
 } sc_scene_batch;
 
 /* ------------------------------------------------------------- sampling */
@@ -174,6 +195,10 @@ typedef struct {
  *   MIDDLE  (anchors A_1..A_n, Sec. IV-F 'middle'): n = 2: A_1 + u0 (A_2 - A_1);
  *           n >= 3: uniform in the anchors' bounding box, kept only inside the
  *           polygon A_1..A_n (crossing number, boundary inside).
+ *   INSIDE  (Sec. IV-F 'inside', reference = part j): like ON_TOP on the part's
+ *           inside support at the candidate's joint value (the rectangle shrunk
+ *           by e = ratio_on_support * min(Hx, Hy) on each side), z = its plane + Hz;
+ *           accepted at attempt 0.
  * FREE / NEXT_TO / DIRECTIONAL / MIDDLE proposals are accepted when inside the
  * support polygon and at least e = ratio_on_support * min(Hx, Hy) from its
  * boundary (S' = S_r n S); z = support + Hz. yaw = 2 pi u2, or with
@@ -195,6 +220,16 @@ typedef struct {
 sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sample_params* params,
                           const int32_t* active, int32_t n_active, float* poses, uint8_t* sample_ok,
                           uint8_t* band);
+
+/* Joint value of every articulated part of the listed candidates (the
+ * paper's randomised articulation states, e.g. how far each drawer is open):
+ * part_q[c * max_parts + j] = qmin + (qmax - qmin) u0 with
+ * u = Philox(seed; c, 0xFFFF0000 + j, 0, 0), u0 as in sc_sample_poses.
+ * part_q: device float [n_cand][max_parts]; entries of other candidates and
+ * of j >= the template's part count are left unchanged. Errors:
+ * SC_ERR_INVALID (NULL part_q, a batch without parts). */
+sc_status sc_sample_parts(sc_ctx* ctx, const sc_scene_batch* batch, uint64_t seed, const int32_t* active,
+                          int32_t n_active, float* part_q);
 
 /* ------------------------------------------------------------ collision */
 

@@ -48,7 +48,9 @@ class _Scene(ctypes.Structure):
         (n, ctypes.c_void_p) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel",
                                        "obj_rel_param", "tmpl_poly_off", "poly_verts", "tmpl_support_z",
                                        "tmpl_obb_off", "obb", "cand_tmpl_off", "tmpl_base", "obj_rel_dir",
-                                       "obj_anchor_off", "obj_anchor")]
+                                       "obj_anchor_off", "obj_anchor")] + [
+        ("n_parts", ctypes.c_int32), ("max_parts", ctypes.c_int32)] + [
+        (n, ctypes.c_void_p) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")]
 
 
 class _Arm(ctypes.Structure):
@@ -90,6 +92,7 @@ def _declare(L):
     L.or_ik_reach.argtypes = [P, P, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int]
     L.or_grasp_target.argtypes = [P, ctypes.c_double, P, P]
     L.or_generate.argtypes = [P, P, P, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int]
+    L.or_sample_parts.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int, P]
 
 
 def _ptr(a):
@@ -123,10 +126,28 @@ class Scene:
             self.keep[name] = None if a is None or np.asarray(a).size == 0 else _c(a, dt)
         if self.keep["obj_anchor"] is None:
             self.keep["obj_anchor_off"] = None
+        # articulated parts and the candidates' joint values (None: no parts)
+        self.max_parts = 0
+        pp = getattr(batch, "part_param", None)
+        if pp is not None and np.asarray(pp).size:
+            self.keep["tmpl_part_off"] = _c(batch.tmpl_part_off, np.int32)
+            self.keep["part_param"] = _c(pp, np.float32).reshape(-1, 12)
+            op = getattr(batch, "obb_part", None)
+            self.keep["obb_part"] = None if op is None or np.asarray(op).size == 0 else _c(op, np.int32)
+            self.max_parts = int(np.diff(self.keep["tmpl_part_off"]).max())
+            self.keep["part_q"] = _c(batch.part_q, np.float32).reshape(-1, self.max_parts)
+        else:
+            for name in ("tmpl_part_off", "part_param", "obb_part", "part_q"):
+                self.keep[name] = None
         k = self.keep
         self.n_cand = int(k["cand_tmpl_off"][-1])
         self.c = _Scene(len(k["tmpl_obj_off"]) - 1, len(k["obj_half"]), len(k["sph_local"]), len(k["poly_verts"]),
-                        len(k["obb"]), self.n_cand, *[_ptr(k[n]) for n, _ in _Scene._fields_[6:]])
+                        len(k["obb"]), self.n_cand)
+        for n, _ in _Scene._fields_[6:]:
+            if n not in ("n_parts", "max_parts"):
+                setattr(self.c, n, _ptr(k[n]))
+        self.c.n_parts = 0 if k["part_param"] is None else len(k["part_param"])
+        self.c.max_parts = self.max_parts
         sizes = np.diff(k["cand_tmpl_off"]).astype(np.int64) * np.diff(k["tmpl_obj_off"]).astype(np.int64)
         self.n_poses = int(sizes.sum())
 
@@ -185,6 +206,19 @@ def sample_poses(batch, seed, max_attempts=16, retry=0, first_obj=0, n_obj=1 << 
     lib().or_sample_poses(sc.ref(), seed, max_attempts, retry, first_obj, n_obj, _ptr(act), n, _ptr(poses), _ptr(ok),
                           _ptr(band), threads or default_threads())
     return poses, ok, band
+
+
+def sample_parts(batch, seed, active=None):
+    """Joint values of every part of the listed candidates, float64
+    [n_cand][max_parts] (entries of unlisted candidates and unused slots 0)."""
+    sc = batch if isinstance(batch, Scene) else Scene(batch)
+    if sc.max_parts == 0:
+        raise ValueError("the batch has no articulated parts")
+    q = np.zeros((sc.n_cand, sc.max_parts), np.float64)
+    act = None if active is None else _c(active, np.int32)
+    n = sc.n_cand if act is None else len(act)
+    lib().or_sample_parts(sc.ref(), seed, _ptr(act), n, _ptr(q))
+    return q
 
 
 def collide(batch, poses, active=None, first_new=0, threads=None):

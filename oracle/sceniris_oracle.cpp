@@ -180,10 +180,16 @@ typedef struct {
   const float* obj_rel_dir;      // [O] direction angle of a DIRECTIONAL relation (may be NULL)
   const int32_t* obj_anchor_off; // [O+1] anchors of a MIDDLE relation (may be NULL)
   const int32_t* obj_anchor;     // [A] template-local indices of earlier objects
+  int32_t n_parts, max_parts;    // articulated (prismatic) parts; 0 when there are none
+  const int32_t* tmpl_part_off;  // [T+1] parts of template t
+  const float* part_param;       // [n_parts][12] axis, qmin | qmax, support centre | half x, y, yaw, -
+  const int32_t* obb_part;       // [n_obb] template-local part a box moves with, -1 static (may be NULL)
+  const float* part_q;           // [n_cand][max_parts] joint values
 } or_scene;
 
 enum {
-  REL_FREE = 0, REL_ON_TOP = 1, REL_NEXT_TO = 2, REL_DIRECTIONAL = 3, REL_MIDDLE = 4, REL_KIND_MASK = 0xF,
+  REL_FREE = 0, REL_ON_TOP = 1, REL_NEXT_TO = 2, REL_DIRECTIONAL = 3, REL_MIDDLE = 4, REL_INSIDE = 5,
+  REL_KIND_MASK = 0xF,
   REL_REACH = 0x10, REL_LOCAL = 0x20, REL_FACE_TO = 0x40
 };
 
@@ -208,6 +214,16 @@ static int64_t pose_offset(const or_scene* s, int c, int t) {
 }
 
 int64_t or_pose_offset(const or_scene* s, int c) { return pose_offset(s, c, template_of(s, c)); }
+
+// Number of articulated parts of template t (0 without parts).
+static int parts_of(const or_scene* s, int t) {
+  if (s->n_parts <= 0 || !s->tmpl_part_off) return 0;
+  return s->tmpl_part_off[t + 1] - s->tmpl_part_off[t];
+}
+
+// Joint value of template-local part j of candidate c (a prismatic joint:
+// the part translates by q along its axis).
+static double part_value(const or_scene* s, int c, int j) { return s->part_q[(int64_t)c * s->max_parts + j]; }
 
 // Support-polygon acceptance for a sampled xy (Sec. III position sampling +
 // Sec. IV-F ratio_on_support): inside the polygon and at least e from its
@@ -248,9 +264,19 @@ static bool support_accept(const or_scene* s, int t, double x, double y, double 
 //   MIDDLE  : Sec. IV-F two or more anchors: the polygon of their positions
 //             (for two, the segment between them), proposals uniform over it
 //             (over its bounding box, kept when inside), then S by rejection.
-//   FACE_TO : the yaw points from the object to the reference object.
+//   INSIDE  : Sec. IV-F 'inside': the support is the inside floor of an
+//             articulated part (a drawer), a rectangle given at joint value 0
+//             and translated by q * axis at the candidate's joint value q; the
+//             position is uniform in the rectangle shrunk by the erosion e on
+//             every side (to a line or point when e exceeds a half extent),
+//             z = the moved floor + half height, yaw uniform, and the
+//             placement is accepted at once, like ON_TOP; the walls are left
+//             to the collision check.
+//   FACE_TO : the yaw points from the object to the reference object (not
+//             for ON_TOP or INSIDE).
 // A relation naming a later object, a missing array or a MIDDLE object
-// without 2..16 earlier anchors is sampled as a free object.
+// without 2..16 earlier anchors, or an INSIDE object naming a part its
+// template lacks, is sampled as a free object.
 static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int max_attempts, uint64_t seed,
                           double (*pose)[4], bool* band_out) {
   int o = s->tmpl_obj_off[t] + k;
@@ -258,8 +284,10 @@ static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int
   int kind = rel & REL_KIND_MASK, ref = (rel >> 8) & 0xFF;
   bool face_to = (rel & REL_FACE_TO) != 0;
   std::vector<int> anchors;
-  bool bad = (kind != REL_FREE || face_to) && ref >= k;
-  bad = bad || kind > REL_MIDDLE || (kind == REL_DIRECTIONAL && !s->obj_rel_dir);
+  if (kind == REL_INSIDE) face_to = false;
+  bool bad = (kind != REL_FREE || face_to) && kind != REL_INSIDE && ref >= k;
+  bad = bad || kind > REL_INSIDE || (kind == REL_DIRECTIONAL && !s->obj_rel_dir);
+  bad = bad || (kind == REL_INSIDE && (!s->part_param || !s->part_q || ref >= parts_of(s, t) || ref >= s->max_parts));
   if (kind == REL_MIDDLE) {
     if (!s->obj_anchor_off) {
       bad = true;
@@ -279,6 +307,23 @@ static bool sample_object(const or_scene* s, int t, int c, int k, int retry, int
   double e = (double)P[2] * std::min(Hx, Hy);  // ratio_on_support erosion
   double zs = s->tmpl_support_z[t];
   bool band = false;
+
+  if (kind == REL_INSIDE) {
+    double u[4];
+    draw4(seed, (uint32_t)c, (uint32_t)k, (uint32_t)retry, 0u, u);
+    const float* pp = &s->part_param[12 * (s->tmpl_part_off[t] + ref)];
+    double q = part_value(s, c, ref);
+    double cx = pp[5] + q * pp[0], cy0 = pp[6] + q * pp[1], cz = pp[7] + q * pp[2];
+    double hx = std::max((double)pp[8] - e, 0.0), hy = std::max((double)pp[9] - e, 0.0), yaw = pp[10];
+    double xl = hx * (2.0 * u[0] - 1.0), yl = hy * (2.0 * u[1] - 1.0);
+    double cs = std::cos(yaw), sn = std::sin(yaw);
+    pose[k][0] = cx + cs * xl - sn * yl;
+    pose[k][1] = cy0 + sn * xl + cs * yl;
+    pose[k][2] = cz + Hz;
+    pose[k][3] = TWO_PI * u[2];
+    *band_out = false;
+    return true;
+  }
 
   if (kind == REL_ON_TOP) {
     double u[4];
@@ -408,6 +453,24 @@ int or_sample_poses(const or_scene* s, uint64_t seed, int max_attempts, int retr
   return 0;
 }
 
+// Randomised articulation (Sec. IV-F 'inside' needs the parts' states): the
+// joint value of part j of candidate c is uniform in [qmin, qmax], drawn from
+// the Philox counter (c, 0xFFFF0000 + j, 0, 0), which no pose draw uses.
+int or_sample_parts(const or_scene* s, uint64_t seed, const int32_t* active, int n_active, double* part_q) {
+  int n = active ? n_active : s->n_cand;
+  for (int i = 0; i < n; ++i) {
+    int c = active ? active[i] : i;
+    int t = template_of(s, c);
+    for (int j = 0; j < parts_of(s, t); ++j) {
+      const float* pp = &s->part_param[12 * (s->tmpl_part_off[t] + j)];
+      double u[4];
+      draw4(seed, (uint32_t)c, 0xFFFF0000u + (uint32_t)j, 0u, 0u, u);
+      part_q[(int64_t)c * s->max_parts + j] = (double)pp[3] + ((double)pp[4] - (double)pp[3]) * u[0];
+    }
+  }
+  return 0;
+}
+
 // ---------------------------------------------------------------------------
 // Collision (Sec. IV-D): per-object sphere sets moved by the object's pose
 // (Sec. IV-B: one transform per instance), sphere-sphere signed distance
@@ -439,12 +502,16 @@ static void quat_to_matrix(const double q_in[4], double R[9]) {
   R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-// Signed distance from sphere (c, r) to the oriented box (12 floats as in or_scene.obb).
-double or_sphere_obb(const double* sphere, const float* box) {
+// Signed distance from sphere (c, r) to the oriented box (12 floats as in
+// or_scene.obb) whose centre is moved by `shift` (NULL: not moved).
+static double sphere_obb_moved(const double* sphere, const float* box, const double* shift) {
   double q[4] = {box[4], box[5], box[6], box[7]};
   double R[9];
   quat_to_matrix(q, R);
-  double d[3] = {sphere[0] - box[0], sphere[1] - box[1], sphere[2] - box[2]};
+  double ctr[3] = {box[0], box[1], box[2]};
+  if (shift)
+    for (int i = 0; i < 3; ++i) ctr[i] += shift[i];
+  double d[3] = {sphere[0] - ctr[0], sphere[1] - ctr[1], sphere[2] - ctr[2]};
   double p[3];  // R^T d: the sphere centre in the box frame
   for (int i = 0; i < 3; ++i) p[i] = R[0 + i] * d[0] + R[3 + i] * d[1] + R[6 + i] * d[2];
   double h[3] = {box[8], box[9], box[10]};
@@ -455,10 +522,25 @@ double or_sphere_obb(const double* sphere, const float* box) {
   return outside + inside - sphere[3];
 }
 
+double or_sphere_obb(const double* sphere, const float* box) { return sphere_obb_moved(sphere, box, nullptr); }
+
+// Where world box `ob` of candidate c (template t) sits: a box of an
+// articulated part is moved by q * axis, q the candidate's joint value of it.
+static void box_shift(const or_scene* s, int t, int c, int ob, double shift[3]) {
+  shift[0] = shift[1] = shift[2] = 0.0;
+  if (!s->obb_part || s->n_parts <= 0) return;
+  int j = s->obb_part[ob];
+  if (j < 0 || j >= parts_of(s, t) || j >= s->max_parts) return;
+  const float* pp = &s->part_param[12 * (s->tmpl_part_off[t] + j)];
+  double q = part_value(s, c, j);
+  for (int i = 0; i < 3; ++i) shift[i] = q * pp[i];
+}
+
 // Minimum signed distance of candidate c whose poses are pose[0..n_t):
 // sphere pairs (i in object a, j in object b, a < b, b >= first_new) and
 // (sphere in object >= first_new, world OBB). Empty set: +FLT_MAX.
-static double candidate_min_dist(const or_scene* s, int t, const double (*pose)[4], int first_new, int last_obj) {
+static double candidate_min_dist(const or_scene* s, int t, int c, const double (*pose)[4], int first_new,
+                                 int last_obj) {
   int o0 = s->tmpl_obj_off[t];
   int nt = std::min(s->tmpl_obj_off[t + 1] - o0, last_obj);
   // world-frame spheres of every object, per object
@@ -478,8 +560,11 @@ static double candidate_min_dist(const or_scene* s, int t, const double (*pose)[
         for (auto& sj : W[b]) m = std::min(m, or_sphere_sphere(si.data(), sj.data()));
   for (int b = std::max(first_new, 0); b < nt; ++b)
     for (auto& sj : W[b])
-      for (int ob = s->tmpl_obb_off[t]; ob < s->tmpl_obb_off[t + 1]; ++ob)
-        m = std::min(m, or_sphere_obb(sj.data(), &s->obb[12 * ob]));
+      for (int ob = s->tmpl_obb_off[t]; ob < s->tmpl_obb_off[t + 1]; ++ob) {
+        double sh[3];
+        box_shift(s, t, c, ob, sh);
+        m = std::min(m, sphere_obb_moved(sj.data(), &s->obb[12 * ob], sh));
+      }
   return m;
 }
 
@@ -492,7 +577,7 @@ int or_collide(const or_scene* s, const double* poses, const int32_t* active, in
     int c = active ? active[i] : i;
     int t = template_of(s, c);
     const double(*pose)[4] = (const double(*)[4]) & poses[4 * pose_offset(s, c, t)];
-    double m = candidate_min_dist(s, t, pose, first_new, 1 << 30);
+    double m = candidate_min_dist(s, t, c, pose, first_new, 1 << 30);
     min_dist[i] = m;
     collide[i] = m < 0.0;
     band[i] = std::fabs(m) <= BAND;
@@ -784,7 +869,7 @@ int or_generate(const or_scene* s, const or_gen_params* G, const or_arm* arm, co
         bool ok = sample_object(s, t, c, k, r, G->max_attempts, G->seed, pose, &b);
         any_band = any_band || b;
         if (!ok) continue;
-        double m = candidate_min_dist(s, t, pose, k, k + 1);
+        double m = candidate_min_dist(s, t, c, pose, k, k + 1);
         any_band = any_band || std::fabs(m) <= BAND;
         if (m < 0.0) continue;
         if (arm && (s->obj_rel[o0 + k] & REL_REACH)) {

@@ -14,6 +14,7 @@ from ._native import (  # noqa: F401
     CollideConfig,
     lib,
     sample_poses,
+    sample_parts,
     collide,
     collide_last_work,
     generate,

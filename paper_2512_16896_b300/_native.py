@@ -34,7 +34,8 @@ class ScSceneBatch(ctypes.Structure):
                                    "max_sph")] + [
         (n, P) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel", "obj_rel_param",
                          "tmpl_poly_off", "poly_verts", "tmpl_support_z", "tmpl_obb_off", "obb", "cand_tmpl_off",
-                         "tmpl_pose_off", "tmpl_base", "obj_rel_dir", "obj_anchor_off", "obj_anchor")]
+                         "tmpl_pose_off", "tmpl_base", "obj_rel_dir", "obj_anchor_off", "obj_anchor")] + [
+        ("n_parts", I32), ("max_parts", I32)] + [(n, P) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")]
 
 
 class ScSampleParams(ctypes.Structure):
@@ -136,6 +137,7 @@ SIGNATURES = {
     "sc_generate_stats": (ctypes.c_int, [P, ctypes.POINTER(ScGenStats)]),
     "sc_ctx_set_timing": (ctypes.c_int, [P, I32]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
+    "sc_sample_parts": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.c_uint64, P, I32, P]),
     "sc_rmap_create": (ctypes.c_int, [P, ctypes.POINTER(ScRmapParams), ctypes.POINTER(P)]),
     "sc_rmap_destroy": (None, [P]),
     "sc_rmap_cells": (I64, [P]),
@@ -226,7 +228,8 @@ class DeviceBatch:
               "tmpl_poly_off": torch.int32, "poly_verts": torch.float32, "tmpl_support_z": torch.float32,
               "tmpl_obb_off": torch.int32, "obb": torch.float32, "cand_tmpl_off": torch.int32,
               "tmpl_base": torch.float32}
-    OPTIONAL = {"obj_rel_dir": torch.float32, "obj_anchor_off": torch.int32, "obj_anchor": torch.int32}
+    OPTIONAL = {"obj_rel_dir": torch.float32, "obj_anchor_off": torch.int32, "obj_anchor": torch.int32,
+                "tmpl_part_off": torch.int32, "part_param": torch.float32, "obb_part": torch.int32}
 
     def __init__(self, batch, device: int | str | torch.device = "cuda", pinned_host: bool = False):
         self.t = {}
@@ -243,6 +246,18 @@ class DeviceBatch:
                 self.t[name] = self.t[name].to(device) if not pinned_host else self.t[name].pin_memory()
         if "obj_anchor" not in self.t:  # no MIDDLE object: neither anchor array
             self.t.pop("obj_anchor_off", None)
+        # articulated parts: their per-candidate joint values live next to the batch
+        part_off = getattr(batch, "tmpl_part_off", None)
+        n_parts_t = np.diff(part_off) if part_off is not None and len(part_off) > 1 else np.zeros(1, np.int64)
+        self.max_parts = int(n_parts_t.max()) if "part_param" in self.t else 0
+        if self.max_parts > 0:  # the batch's joint values, or zeros for sample_parts to fill
+            q0 = getattr(batch, "part_q", None)
+            q = (torch.from_numpy(np.ascontiguousarray(q0, np.float32)).reshape(-1) if q0 is not None else
+                 torch.zeros(int(batch.cand_tmpl_off[-1]) * self.max_parts, dtype=torch.float32))
+            self.t["part_q"] = q.to(device) if not pinned_host else q.pin_memory()
+        else:
+            for name in ("tmpl_part_off", "part_param", "obb_part"):
+                self.t.pop(name, None)
         tpo = np.concatenate([[0], np.cumsum(np.diff(batch.cand_tmpl_off).astype(np.int64) *
                                              np.diff(batch.tmpl_obj_off).astype(np.int64))]).astype(np.int64)
         self.t["tmpl_pose_off"] = torch.from_numpy(tpo).to(device)
@@ -254,12 +269,22 @@ class DeviceBatch:
         nsph = self.obj_sph_off[self.tmpl_obj_off[1:]] - self.obj_sph_off[self.tmpl_obj_off[:-1]]
         self.n_poses = int(tpo[-1])
         self.n_cand = int(self.cand_tmpl_off[-1])
+        ptrs = {n: _ptr(self.t.get(n)) for n, _ in ScSceneBatch._fields_[8:] if n not in ("n_parts", "max_parts")}
         self.c = ScSceneBatch(
             n_t, len(batch.obj_half), len(batch.sph_local), len(batch.poly_verts), len(batch.obb), self.n_cand,
-            int(nobj.max()), int(nsph.max()),
-            *[_ptr(self.t.get(n)) for n, _ in ScSceneBatch._fields_[8:]])
+            int(nobj.max()), int(nsph.max()))
+        for n, v in ptrs.items():
+            setattr(self.c, n, v)
+        self.c.n_parts = len(batch.part_param) if self.max_parts else 0
+        self.c.max_parts = self.max_parts
         if len(batch.obb) == 0:
             self.c.obb = None
+
+    @property
+    def part_q(self) -> torch.Tensor | None:
+        """Joint values of the articulated parts, float [n_cand][max_parts] (None without parts)."""
+        q = self.t.get("part_q")
+        return None if q is None else q.view(self.n_cand, self.max_parts)
 
     def new_poses(self, device="cuda") -> torch.Tensor:
         return torch.zeros((self.n_poses, 4), dtype=torch.float32, device=device)
@@ -511,6 +536,15 @@ class ReachMap:
             self.close()
         except Exception:
             pass
+
+
+def sample_parts(ctx: Context, db: DeviceBatch, seed: int, active: torch.Tensor | None = None) -> torch.Tensor:
+    """sc_sample_parts into the batch's joint-value array; returns it [n_cand][max_parts]."""
+    if db.max_parts == 0:
+        raise ValueError("the batch has no articulated parts")
+    n = _n_items(db, active)
+    _check(lib().sc_sample_parts(ctx.handle, ctypes.byref(db.c), seed, _active_ptr(active), n, _ptr(db.t["part_q"])))
+    return db.part_q
 
 
 def collide_last_work(ctx: Context):

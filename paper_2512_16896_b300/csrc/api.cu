@@ -32,7 +32,7 @@ struct sc_ctx {
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t gen_graph = nullptr;
   cudaGraphExec_t gen_exec = nullptr;
-  unsigned char gen_key[512] = {};
+  unsigned char gen_key[768] = {};
   size_t gen_key_len = 0;
   unsigned long long seed_host = 0;
   // stage timing (sc_ctx_set_timing)
@@ -119,6 +119,16 @@ sc_status check_batch(const sc_scene_batch* b) {
   if ((b->obj_rel_dir && !aligned(b->obj_rel_dir, 4)) || (b->obj_anchor_off && !aligned(b->obj_anchor_off, 4)) ||
       (b->obj_anchor && !aligned(b->obj_anchor, 4)))
     return fail(SC_ERR_INVALID, "relation arrays must be 4-byte aligned");
+  if (b->n_parts < 0 || b->max_parts < 0 || b->max_parts > sc::kMaxParts || (b->n_parts > 0) != (b->max_parts > 0))
+    return fail(SC_ERR_INVALID, "n_parts = %d, max_parts = %d: both 0, or n_parts > 0 and max_parts in 1..%d",
+                b->n_parts, b->max_parts, sc::kMaxParts);
+  if (b->n_parts > 0) {
+    if (!b->tmpl_part_off || !b->part_param || !b->part_q)
+      return fail(SC_ERR_INVALID, "a batch with parts needs tmpl_part_off, part_param and part_q");
+    if (!aligned(b->part_param, 16) || !aligned(b->tmpl_part_off, 4) || !aligned(b->part_q, 4) ||
+        (b->obb_part && !aligned(b->obb_part, 4)))
+      return fail(SC_ERR_INVALID, "part_param must be 16-byte aligned, the other part arrays 4-byte aligned");
+  }
   return SC_OK;
 }
 
@@ -205,7 +215,7 @@ sc_status sc_ctx_synchronize(sc_ctx* ctx) {
     cudaMemset(ctx->d_status, 0, sizeof(int));
     if (st == sc::kDevTimeout) return fail(SC_ERR_TIMEOUT, "a bounded tensor-core wait gave up (device code 7)");
     return fail(SC_ERR_DEVICE, "a kernel latched device error code %d (1 bad template, 2 too many spheres, "
-                "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation)", st);
+                "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation, 8 bad part)", st);
   }
   return SC_OK;
 }
@@ -230,6 +240,22 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
   cudaError_t e = sc::launch_sample(*batch, *params, active, n, poses, sample_ok, band, ctx->d_status, ctx->num_sms,
                                     ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sample_kernel launch");
+  return SC_OK;
+}
+
+sc_status sc_sample_parts(sc_ctx* ctx, const sc_scene_batch* batch, uint64_t seed, const int32_t* active,
+                          int32_t n_active, float* part_q) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (sc_status s = check_batch(batch)) return s;
+  if (batch->n_parts == 0) return fail(SC_ERR_INVALID, "the batch has no articulated parts");
+  if (!part_q || !aligned(part_q, 4)) return fail(SC_ERR_INVALID, "part_q is NULL or not 4-byte aligned");
+  if (active && n_active < 0) return fail(SC_ERR_INVALID, "n_active < 0");
+  const int n = active ? n_active : batch->n_cand;
+  if (n == 0) return SC_OK;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::launch_sample_parts(*batch, seed, active, n, part_q, ctx->d_status, ctx->num_sms, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sample_parts_kernel launch");
   return SC_OK;
 }
 
@@ -380,7 +406,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     }
     a.reach_objects = want_reach ? ctx->reach_extent : 0;
     a.max_sph_obj = ctx->max_sph_obj;
-    a.ext_rel = ctx->ext_rel;
+    a.ext_rel = ctx->ext_rel || batch->n_parts > 0;  // parts move boxes and carry INSIDE supports
   }
   if (a.reach_objects > 0) {  // side streams and events of the rounds
     const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;

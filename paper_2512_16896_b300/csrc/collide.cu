@@ -165,10 +165,11 @@ __device__ __forceinline__ void stage_spheres(const sc_scene_batch& b, int s0, i
 // World boxes: columns of R, minus R^T (centre - object 0's position), half
 // extents. A sphere centre w (relative to object 0) has box-frame
 // coordinates p = R^T w - R^T (centre - ref): three FMAs per axis.
-__device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int bx0, int nobb, const Smem& sm, int tid,
-                                            int nthr) {
+__device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int t, int c, int bx0, int nobb, const Smem& sm,
+                                            int tid, int nthr, int* status) {
   const float4 ref = sm.opose[0];
   for (int k = tid; k < nobb; k += nthr) {
+    const float3 sh = box_shift(b, t, c, bx0 + k, status);  // an articulated part's box moves with its joint
     const float* o = b.obb + 12 * (bx0 + k);
     float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
     const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
@@ -178,7 +179,8 @@ __device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int bx0, in
     d[0] = 1.f - 2.f * (qy * qy + qz * qz); d[1] = 2.f * (qx * qy + qz * qw); d[2] = 2.f * (qx * qz - qy * qw);
     d[3] = 2.f * (qx * qy - qz * qw); d[4] = 1.f - 2.f * (qx * qx + qz * qz); d[5] = 2.f * (qy * qz + qx * qw);
     d[6] = 2.f * (qx * qz + qy * qw); d[7] = 2.f * (qy * qz - qx * qw); d[8] = 1.f - 2.f * (qx * qx + qy * qy);
-    const float cx = __ldg(o + 0) - ref.x, cy = __ldg(o + 1) - ref.y, cz = __ldg(o + 2) - ref.z;
+    const float cx = (__ldg(o + 0) + sh.x) - ref.x, cy = (__ldg(o + 1) + sh.y) - ref.y,
+                cz = (__ldg(o + 2) + sh.z) - ref.z;
     d[9] = -(d[0] * cx + d[1] * cy + d[2] * cz);
     d[10] = -(d[3] * cx + d[4] * cy + d[5] * cz);
     d[11] = -(d[6] * cx + d[7] * cy + d[8] * cz);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
     }
     __syncthreads();
     stage_spheres(b, s0, nt, S, sm, sh, tid, nthr, lane);
-    stage_boxes(b, bx0, nobb, sm, tid, nthr);
+    stage_boxes(b, t, c, bx0, nobb, sm, tid, nthr, a.status);
     __syncthreads();
     const float rmax = __int_as_float(sh.rmax_key);
     const float eps = 1e-5f * (__int_as_float(sh.r2max_key) + 0.01f);

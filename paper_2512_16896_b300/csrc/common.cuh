@@ -17,6 +17,7 @@ constexpr int kMaxSph = 8192;                        // spheres of one template
 constexpr int kMaxSphPerObj = 256;                   // spheres of one object (generation)
 constexpr int kMaxPolyVerts = 64;
 constexpr int kMaxObbPerTemplate = 64;
+constexpr int kMaxParts = 16;                        // articulated parts of one template
 
 // Device status codes latched into the context's status word (first error wins).
 enum DeviceError : int {
@@ -28,6 +29,7 @@ enum DeviceError : int {
   kDevBadPolygon = 5,
   kDevBadRelation = 6,  // relation refers to itself or a later object
   kDevTimeout = 7,      // a bounded wait on a tensor-core MMA or bulk copy gave up
+  kDevBadPart = 8,      // a box or an INSIDE relation names a part its template does not have
 };
 
 // Byte offset of element (r, k) of a [rows][K] bf16 matrix in the canonical
@@ -105,6 +107,28 @@ __device__ __forceinline__ int template_of(const sc_scene_batch& b, int c) {
     if (__ldg(&b.cand_tmpl_off[mid]) <= c) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Displacement q * axis of world box `box` (a batch index) for candidate c of
+// template t: nonzero only for a box of an articulated part (obb_part >= 0),
+// q being that part's joint value of the candidate. A part index outside the
+// template's parts latches kDevBadPart and leaves the box where it is.
+__device__ __forceinline__ float3 box_shift(const sc_scene_batch& b, int t, int c, int box, int* status) {
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  if (!b.obb_part || b.max_parts <= 0) return s;
+  const int p = __ldg(&b.obb_part[box]);
+  if (p < 0) return s;
+  const int p0 = __ldg(&b.tmpl_part_off[t]);
+  if (p >= __ldg(&b.tmpl_part_off[t + 1]) - p0 || p >= b.max_parts) {
+    latch_error(status, kDevBadPart);
+    return s;
+  }
+  const float q = __ldg(&b.part_q[(int64_t)c * b.max_parts + p]);
+  const float* a = b.part_param + 12 * (int64_t)(p0 + p);
+  s.x = q * __ldg(a);
+  s.y = q * __ldg(a + 1);
+  s.z = q * __ldg(a + 2);
+  return s;
 }
 
 // Order-preserving map of a float onto a signed int (for atomicMin on floats).

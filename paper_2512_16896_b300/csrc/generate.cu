@@ -196,7 +196,7 @@ struct TryOut {
 // sphere farther than band + margin from every kept object's ball, or an A
 // sphere that far from object k's ball, has no pair within the band.
 template <int APL, bool PREFETCHED, bool EXT>
-__device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& T, const WarpState& W, int c, int k,
+__device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& T, const WarpState& W, int t, int c, int k,
                                           int retry, int rel, int Sprev, int Sk, int64_t pbase, uint64_t seed,
                                           const float4* ref_poses, int lane, TryCounters& cnt) {
   const sc_scene_batch& b = g.b;
@@ -209,7 +209,7 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
   sup.ok = T.nv >= 3 && T.nv <= kMaxPolyVerts;
   sup.z = T.z;
   sup.xmin = T.xmin; sup.xmax = T.xmax; sup.ymin = T.ymin; sup.ymax = T.ymax;
-  const ObjectSpec spec = load_object_spec<EXT>(b, o0, k, rel, ref_poses, 0, g.status, lane);
+  const ObjectSpec spec = load_object_spec<EXT>(b, o0, k, rel, ref_poses, 0, g.status, lane, t, c);
   SampleResult r;
   r.placed = false;
   r.band = true;
@@ -301,9 +301,12 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
       for (int bi = 0; bi < nobb; ++bi) {
         const float4* o = g.obb_tab + 4 * (bx0 + bi);
         const float4 R0 = __ldg(o), R1 = __ldg(o + 1), R2 = __ldg(o + 2), Hh = __ldg(o + 3);
+        // an articulated part's box moves with the candidate's joint value
+        const float3 sh = EXT ? box_shift(b, t, c, bx0 + bi, g.status) : make_float3(0.f, 0.f, 0.f);
         // box frame: p = R^T (c - centre); rows of R^T are the columns of R,
         // stored as the table's rows
-        const float vx = x - (R0.w - ref.x), vy = y - (R1.w - ref.y), vz = z - (R2.w - ref.z);
+        const float vx = x - ((R0.w + sh.x) - ref.x), vy = y - ((R1.w + sh.y) - ref.y),
+                    vz = z - ((R2.w + sh.z) - ref.z);
         const float px = R0.x * vx + R0.y * vy + R0.z * vz;
         const float py = R1.x * vx + R1.y * vy + R1.z * vz;
         const float pz = R2.x * vx + R2.y * vy + R2.z * vz;
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
       for (int j = lane; j <= k + 1; j += 32) cp_async4(W.off + j, b.obj_sph_off + o0 + j);
       cp_async_commit();
       const TryOut res =
-          gen_try<APL, true, EXT>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
+          gen_try<APL, true, EXT>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
       bool done = false;
       if (res.pass && g.list_reach && (rel & SC_REL_REACH)) {
         route = kRouteReach;
@@ -640,7 +643,7 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
 #pragma unroll 1
         for (int r = 0; r <= g.max_retries && !placed; ++r) {
           const TryOut res =
-              gen_try<APL, false, EXT>(g, T, W, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
+              gen_try<APL, false, EXT>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
           ++ntries;
           band = band || res.band;
           placed = res.pass;

@@ -11,6 +11,8 @@
 
 namespace sc {
 
+cudaError_t launch_sample_parts(const sc_scene_batch& b, uint64_t seed, const int32_t* active, int n_items,
+                               float* part_q, int* status, int num_sms, cudaStream_t s);
 cudaError_t launch_sample(const sc_scene_batch& b, const sc_sample_params& p, const int32_t* active, int n_items,
                           float* poses, uint8_t* ok, uint8_t* band, int* status, int num_sms, cudaStream_t s);
 

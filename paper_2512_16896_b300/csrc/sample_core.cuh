@@ -105,16 +105,21 @@ struct ObjectSpec {
   int an0, n_an;  // MIDDLE: anchors obj_anchor[an0 .. an0 + n_an)
 };
 
-// Relation of template-local object k. A reference (parent, anchor, faced
-// object) must be an earlier object, a DIRECTIONAL object needs obj_rel_dir, a
-// MIDDLE one 2..16 earlier anchors: otherwise kDevBadRelation is latched and
+// Relation of template-local object k of candidate c (template t). A
+// reference (parent, anchor, faced object) must be an earlier object, a
+// DIRECTIONAL object needs obj_rel_dir, a MIDDLE one 2..16 earlier anchors, an
+// INSIDE one a part of its template: otherwise kDevBadRelation is latched and
 // the object is sampled as free. The reference pose is read from
 // poses[pbase + ref], written before this call (the caller orders the
-// accesses). EXT = false compiles only FREE / ON_TOP / NEXT_TO (any other
-// kind or flag is refused the same way) for batches known to use no more.
+// accesses). INSIDE becomes ON_TOP of a flat reference: the part's support
+// rectangle moved by q * axis, its half extents shrunk by the erosion e (not
+// below 0), the face-to flag dropped as for ON_TOP. EXT = false compiles only
+// FREE / ON_TOP / NEXT_TO (any other kind or flag is refused the same way) for
+// batches known to use no more.
 template <bool EXT = true>
 __device__ __forceinline__ ObjectSpec load_object_spec(const sc_scene_batch& b, int o0, int k, int rel,
-                                                       const float4* poses, int64_t pbase, int* status, int lane) {
+                                                       const float4* poses, int64_t pbase, int* status, int lane,
+                                                       int t, int c) {
   ObjectSpec S;
   const int o = o0 + k;
   S.kind = rel & SC_REL_KIND_MASK;
@@ -123,8 +128,20 @@ __device__ __forceinline__ ObjectSpec load_object_spec(const sc_scene_batch& b, 
   S.an0 = 0;
   S.n_an = 0;
   S.dir = 0.f;
-  bool bad = (S.kind != SC_REL_FREE || S.face_to) && S.ref >= k;
-  bad = bad || S.kind > (EXT ? SC_REL_MIDDLE : SC_REL_NEXT_TO) || (EXT && S.kind == SC_REL_DIRECTIONAL && !b.obj_rel_dir);
+  const bool inside = EXT && S.kind == SC_REL_INSIDE;
+  int part0 = 0;
+  if (inside) {
+    S.face_to = 0;
+    bool ok = b.part_param && b.part_q && b.tmpl_part_off && b.max_parts > 0;
+    if (ok) {
+      part0 = __ldg(&b.tmpl_part_off[t]);
+      ok = S.ref < __ldg(&b.tmpl_part_off[t + 1]) - part0 && S.ref < b.max_parts;
+    }
+    if (!ok && lane == 0) latch_error(status, kDevBadPart);
+    if (!ok) S.kind = SC_REL_FREE;
+  }
+  bool bad = (S.kind != SC_REL_FREE || S.face_to) && S.ref >= k && !inside;
+  bad = bad || S.kind > (EXT ? SC_REL_INSIDE : SC_REL_NEXT_TO) || (EXT && S.kind == SC_REL_DIRECTIONAL && !b.obj_rel_dir);
   if (EXT && S.kind == SC_REL_MIDDLE) {
     if (!b.obj_anchor_off) {
       bad = true;
@@ -148,7 +165,16 @@ __device__ __forceinline__ ObjectSpec load_object_spec(const sc_scene_batch& b, 
   S.RP = __ldg(reinterpret_cast<const float4*>(b.obj_rel_param) + o);
   S.ref_pose = make_float4(0.f, 0.f, 0.f, 0.f);
   S.ref_half = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (S.kind != SC_REL_FREE || S.face_to) {
+  if (EXT && S.kind == SC_REL_INSIDE) {
+    // part_param rows: (axis, qmin), (qmax, centre), (half extents, yaw, -)
+    const float4* pp = reinterpret_cast<const float4*>(b.part_param) + 3 * (int64_t)(part0 + S.ref);
+    const float4 ax = __ldg(pp), ce = __ldg(pp + 1), hh = __ldg(pp + 2);
+    const float q = __ldg(&b.part_q[(int64_t)c * b.max_parts + S.ref]);
+    const float e = S.RP.z * fminf(S.H.x, S.H.y);
+    S.ref_pose = make_float4(ce.y + q * ax.x, ce.z + q * ax.y, ce.w + q * ax.z, hh.z);
+    S.ref_half = make_float4(fmaxf(hh.x - e, 0.f), fmaxf(hh.y - e, 0.f), 0.f, 0.f);
+    S.kind = SC_REL_ON_TOP;
+  } else if (S.kind != SC_REL_FREE || S.face_to) {
     S.ref_pose = poses[pbase + S.ref];
     S.ref_half = __ldg(reinterpret_cast<const float4*>(b.obj_half) + (o0 + S.ref));
   }
@@ -360,8 +386,8 @@ __device__ __forceinline__ SampleResult warp_sample_spec(const Support& sup, con
 __device__ __forceinline__ SampleResult warp_sample_object(const sc_scene_batch& b, const Support& sup,
                                                           uint64_t seed, int max_attempts, int retry, int c, int k,
                                                           int o0, const float4* poses, int64_t pbase, int* status,
-                                                          int lane) {
-  const ObjectSpec S = load_object_spec(b, o0, k, __ldg(&b.obj_rel[o0 + k]), poses, pbase, status, lane);
+                                                          int lane, int t) {
+  const ObjectSpec S = load_object_spec(b, o0, k, __ldg(&b.obj_rel[o0 + k]), poses, pbase, status, lane, t, c);
   return warp_sample_spec(sup, S, seed, max_attempts, retry, c, k, lane, b.obj_anchor, poses + pbase);
 }
 

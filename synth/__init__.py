@@ -29,7 +29,7 @@ import math
 
 import numpy as np
 
-REL_FREE, REL_ON_TOP, REL_NEXT_TO, REL_DIRECTIONAL, REL_MIDDLE = 0, 1, 2, 3, 4
+REL_FREE, REL_ON_TOP, REL_NEXT_TO, REL_DIRECTIONAL, REL_MIDDLE, REL_INSIDE = 0, 1, 2, 3, 4, 5
 REL_REACH, REL_LOCAL, REL_FACE_TO = 0x10, 0x20, 0x40
 
 # 7-DoF arm used by the reachability workload: standard DH parameters.
@@ -57,6 +57,10 @@ class SceneBatch:
       tmpl_obb_off  int32 [T+1]; obb f32 [n_obb,12] centre(x,y,z,0) quat(x,y,z,w) half(x,y,z,0)
       cand_tmpl_off int32 [T+1]  candidates of template t
       tmpl_base     f32 [T,4]    robot base (x, y, z, yaw)
+      tmpl_part_off int32 [T+1]; part_param f32 [n_parts,12]: articulated (prismatic) parts,
+                                 (axis, qmin), (qmax, support centre), (support half x, y, yaw, 0)
+      obb_part      int32 [n_obb] template-local part a box moves with (-1: static)
+      part_q        f32 [B, max_parts] joint value of every part per candidate (drawn here)
     """
 
     tmpl_obj_off: np.ndarray
@@ -75,6 +79,10 @@ class SceneBatch:
     obj_rel_dir: np.ndarray = None
     obj_anchor_off: np.ndarray = None
     obj_anchor: np.ndarray = None
+    tmpl_part_off: np.ndarray = None
+    part_param: np.ndarray = None
+    obb_part: np.ndarray = None
+    part_q: np.ndarray = None
     name: str = ""
 
     @property
@@ -123,7 +131,13 @@ class SceneBatch:
             v0, v1 = int(self.tmpl_poly_off[t]), int(self.tmpl_poly_off[t + 1])
             b0, b1 = int(self.tmpl_obb_off[t]), int(self.tmpl_obb_off[t + 1])
             anchors = [list(self.obj_anchor[self.obj_anchor_off[o]:self.obj_anchor_off[o + 1]]) for o in range(o0, o1)]
-            parts.append(dict(
+            extra = {}
+            if self.part_param is not None:
+                p0, p1 = int(self.tmpl_part_off[t]), int(self.tmpl_part_off[t + 1])
+                c0, c1 = int(self.cand_tmpl_off[t]), int(self.cand_tmpl_off[t + 1])
+                extra = dict(parts=self.part_param[p0:p1], obb_part=self.obb_part[b0:b1],
+                             part_q=self.part_q[c0:c1, :p1 - p0])
+            parts.append(dict(**extra,
                 sph=self.sph_local[s0:s1], nsph=np.diff(self.obj_sph_off[o0:o1 + 1]),
                 half=self.obj_half[o0:o1], rel=self.obj_rel[o0:o1], relp=self.obj_rel_param[o0:o1],
                 dir=self.obj_rel_dir[o0:o1], anchors=anchors,
@@ -158,14 +172,37 @@ def _pack(parts, name="") -> SceneBatch:
         obj_anchor_off=off([len(a) for a in anchors]),
         obj_anchor=np.array([i for a in anchors for i in a], dtype=np.int32),
         name=name,
+        **_pack_parts(parts),
     )
 
 
-def draw_object(rng: np.random.Generator, n_spheres: int):
+def _pack_parts(parts) -> dict:
+    """CSR arrays of the articulated parts (empty dict when no template has any)."""
+    if not any(len(p.get("parts", ())) for p in parts):
+        return {}
+    n_parts = [len(p.get("parts", ())) for p in parts]
+    max_parts = max(n_parts)
+    q = np.zeros((sum(p["ncand"] for p in parts), max_parts), np.float32)
+    row = 0
+    for p, n in zip(parts, n_parts):
+        if n:
+            q[row:row + p["ncand"], :n] = p["part_q"]
+        row += p["ncand"]
+    return dict(
+        tmpl_part_off=np.concatenate([[0], np.cumsum(n_parts)]).astype(np.int32),
+        part_param=np.ascontiguousarray(np.concatenate([np.asarray(p.get("parts", np.zeros((0, 12))), np.float32)
+                                                        .reshape(-1, 12) for p in parts])),
+        obb_part=np.concatenate([np.asarray(p.get("obb_part", -np.ones(len(p["obb"]))), np.int32)
+                                 for p in parts]).astype(np.int32),
+        part_q=q,
+    )
+
+
+def draw_object(rng: np.random.Generator, n_spheres: int, h_range=(0.05, 0.15), r_range=(0.01, 0.05)):
     """One object asset: (spheres [n,4] in the AABB-centred frame, half extents (Hx,Hy,Hz), rho)."""
-    h = rng.uniform(0.05, 0.15, size=3)
+    h = rng.uniform(h_range[0], h_range[1], size=3)
     c = rng.uniform(-h, h, size=(n_spheres, 3))
-    r = rng.uniform(0.01, 0.05, size=n_spheres)
+    r = rng.uniform(r_range[0], r_range[1], size=n_spheres)
     lo = (c - r[:, None]).min(axis=0)
     hi = (c + r[:, None]).max(axis=0)
     centre = 0.5 * (lo + hi)
@@ -349,6 +386,73 @@ def hard(seed: int = 5, n_templates: int = 256, cand_per_template: int = 64, obj
         p["ncand"] = cand_per_template
         parts.append(p)
     return _pack(parts, name=f"hard T={n_templates}x{cand_per_template}")
+
+
+def _box(c, h):
+    """One axis-aligned world box row: centre c, identity quaternion, half extents h."""
+    return [c[0], c[1], c[2], 0.0, 0.0, 0.0, 0.0, 1.0, h[0], h[1], h[2], 0.0]
+
+
+def cabinet_template(rng, n_counter, n_drawers, inside_per_drawer, n_sph, q_max=0.35, counter_z=0.9):
+    """A kitchen counter over a column of drawers (stand-in for the paper's
+    cabinet with drawers, Sec. V-A). Counter: a 0.6 x 1.6 m support at
+    z = counter_z with n_counter objects related as in draw_relations, its
+    plate 1 mm below. Static carcass: the plate, two side panels and a back
+    panel. Drawer j (prismatic, axis -x, q in [0, q_max]): floor plane at
+    z = 0.04 + 0.28 j, inside support 0.49 x 0.55 m centred on the cabinet's
+    axis at q = 0, a floor box 1 mm below it and four 13 cm walls 1 cm thick
+    (5 boxes that move with the drawer). After the counter objects,
+    inside_per_drawer objects per drawer with the INSIDE relation (erosion
+    ratio 1), smaller assets (half extents U(0.03, 0.07), radii U(0.01, 0.03)).
+    Joint values of the candidates are drawn later (uniform in the range)."""
+    p = make_template(rng, n_counter, [n_sph] * n_counter, rect_polygon(0.6, 1.6), support_z=counter_z,
+                      base=[-0.9, 0.0, counter_z, 0.0])
+    obb = [_box((0.0, 0.0, counter_z - 0.016), (0.3, 0.8, 0.015)),
+           _box((0.0, 0.31, 0.44), (0.3, 0.01, 0.42)), _box((0.0, -0.31, 0.44), (0.3, 0.01, 0.42)),
+           _box((0.29, 0.0, 0.44), (0.01, 0.3, 0.42))]
+    obb_part = [-1] * len(obb)
+    parts = []
+    for j in range(n_drawers):
+        zf = 0.04 + 0.28 * j
+        parts.append([-1.0, 0.0, 0.0, 0.0, q_max, 0.0, 0.0, zf, 0.245, 0.275, 0.0, 0.0])
+        obb += [_box((0.0, 0.0, zf - 0.006), (0.26, 0.29, 0.005)),
+                _box((-0.255, 0.0, zf + 0.06), (0.005, 0.29, 0.065)), _box((0.255, 0.0, zf + 0.06), (0.005, 0.29, 0.065)),
+                _box((0.0, 0.285, zf + 0.06), (0.25, 0.005, 0.065)), _box((0.0, -0.285, zf + 0.06), (0.25, 0.005, 0.065))]
+        obb_part += [j] * 5
+    sph, nsph, half, rel, relp = [p["sph"]], list(p["nsph"]), list(p["half"]), list(p["rel"]), list(p["relp"])
+    for j in range(n_drawers):
+        for _ in range(inside_per_drawer):
+            s, h, rho = draw_object(rng, n_sph, h_range=(0.03, 0.07), r_range=(0.01, 0.03))
+            sph.append(s)
+            nsph.append(len(s))
+            half.append([h[0], h[1], h[2], rho])
+            rel.append(REL_INSIDE | (j << 8))
+            relp.append([0.0, 0.0, 1.0, 0.0])
+    n = len(half)
+    p.update(sph=np.concatenate(sph), nsph=np.array(nsph), half=np.array(half, np.float32),
+             rel=np.array(rel, np.int32), relp=np.array(relp, np.float32), dir=np.zeros(n, np.float32),
+             anchors=[[] for _ in range(n)], obb=np.array(obb, np.float32), obb_part=np.array(obb_part, np.int32),
+             parts=np.array(parts, np.float32))
+    return p
+
+
+def cabinet(seed: int = 6, n_templates: int = 64, cand_per_template: int = 64, counter_range=(4, 10),
+            drawer_range=(2, 3), inside_per_drawer: int = 2, n_sph: int = 16) -> SceneBatch:
+    """Articulated workload: cabinet_template with 2..3 drawers and 4..10
+    counter objects per template; every candidate draws each drawer's joint
+    value uniformly in its range (seeded numpy, the same values for the
+    library and the oracle)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_templates):
+        nd = int(rng.integers(drawer_range[0], drawer_range[1] + 1))
+        nc = int(rng.integers(counter_range[0], counter_range[1] + 1))
+        p = cabinet_template(rng, nc, nd, inside_per_drawer, n_sph)
+        p["ncand"] = cand_per_template
+        lo, hi = p["parts"][:, 3], p["parts"][:, 4]
+        p["part_q"] = (lo + (hi - lo) * rng.uniform(size=(cand_per_template, nd))).astype(np.float32)
+        parts.append(p)
+    return _pack(parts, name=f"cabinet T={n_templates}x{cand_per_template}")
 
 
 def random_poses(batch: SceneBatch, seed: int, spread: float = 0.6) -> np.ndarray:

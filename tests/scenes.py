@@ -5,10 +5,12 @@ import synth
 
 
 def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_cand=1, rel=None, relp=None,
-               dirs=None, anchors=None):
+               dirs=None, anchors=None, parts=None, obb_part=None, part_q=None):
     """objects: list of sphere lists [(x,y,z,r), ...] in object frames; rel,
-    relp, dirs, anchors: per-object relation fields (defaults: all free)."""
+    relp, dirs, anchors: per-object relation fields (defaults: all free);
+    parts [n][12], obb_part [n_obb], part_q [n_cand][n]: articulated parts."""
     n = len(objects)
+    part_rows = parts
     parts = dict(
         sph=np.array([s for o in objects for s in o], np.float32), nsph=np.array([len(o) for o in objects]),
         half=np.array([[0.1, 0.1, 0.1, 0.15]] * n, np.float32),
@@ -19,4 +21,10 @@ def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_ca
         anchors=[[] for _ in range(n)] if anchors is None else [list(a) for a in anchors],
         poly=np.array(poly, np.float32), z=0.0, obb=np.array(obbs, np.float32).reshape(-1, 12), ncand=n_cand,
         base=np.zeros(4, np.float32))
+    if part_rows is not None:
+        parts["parts"] = np.array(part_rows, np.float32).reshape(-1, 12)
+        parts["obb_part"] = (-np.ones(len(parts["obb"]), np.int32) if obb_part is None
+                             else np.array(obb_part, np.int32))
+        parts["part_q"] = (np.zeros((n_cand, len(parts["parts"])), np.float32) if part_q is None
+                           else np.array(part_q, np.float32).reshape(n_cand, -1))
     return synth._pack([parts])

@@ -728,3 +728,107 @@ def test_bad_relations_sample_free():
                                         anchor_poses=[(0, 0, 0, 0), (0.5, 0, 0, 0)],
                                         poly=((-1, -1), (1, -1), (1, 1), (-1, 1)))
         assert np.array_equal(p, free)
+
+
+# --------------------------------------------------------------------------- articulated parts
+
+# One prismatic part: axis (0.6, 0, 0.8) (a unit vector with a vertical
+# component, so a dropped or swapped axis component shows), q in [0, 1], inside
+# support centred at (0.2, -0.1) on z = 0.3, half extents (0.3, 0.15), yaw 0.5.
+_PART = [0.6, 0.0, 0.8, 0.0, 1.0, 0.2, -0.1, 0.3, 0.3, 0.15, 0.5, 0.0]
+
+
+def _inside_batch(n, ratio, q):
+    return tiny_batch([[(0.0, 0.0, 0.0, 0.05)], [(0.0, 0.0, 0.0, 0.05)]], n_cand=n,
+                      rel=[0, synth.REL_INSIDE | (0 << 8)], relp=[[0.05, 0.2, 0.0, 0.0], [0.0, 0.0, ratio, 0.0]],
+                      parts=[_PART], part_q=np.asarray(q, np.float32).reshape(n, 1))
+
+
+def test_inside_places_on_the_moved_shrunk_support():
+    """INSIDE (Sec. IV-F 'inside'): the position is uniform in the part's
+    support rectangle moved by q * axis and shrunk by e = ratio * min(Hx, Hy)
+    (tiny_batch objects have Hx = Hy = Hz = 0.1, so e = 0.05 at ratio 0.5),
+    turned by the part's yaw; z = the moved floor + Hz; accepted at once."""
+    n = 4000
+    q = np.random.default_rng(0).uniform(0.0, 1.0, n).astype(np.float32)
+    b = _inside_batch(n, 0.5, q)
+    p, ok, band = oracle.sample_poses(b, seed=11)
+    assert ok.all() and not band.any()
+    p = p.reshape(n, 2, 4)[:, 1]
+    qd = q.astype(np.float64)
+    cx, cy, cz = 0.2 + 0.6 * qd, -0.1 + 0.0 * qd, 0.3 + 0.8 * qd
+    yaw = np.float32(0.5)
+    local = Rotation.from_euler("z", -float(yaw)).apply(np.stack([p[:, 0] - cx, p[:, 1] - cy, 0 * cx], 1))
+    assert np.abs(local[:, 0]).max() <= 0.25 + 1e-9 and np.abs(local[:, 1]).max() <= 0.10 + 1e-9
+    assert stats.kstest(local[:, 0] / 0.25, stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    assert stats.kstest(local[:, 1] / 0.10, stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    assert np.allclose(p[:, 2], cz + np.float32(0.1), atol=1e-7)
+    # an erosion beyond the half extents leaves the moved centre
+    p2, ok2, _ = oracle.sample_poses(_inside_batch(n, 4.0, q), seed=11)
+    p2 = p2.reshape(n, 2, 4)[:, 1]
+    assert ok2.all() and np.allclose(p2[:, 0], cx, atol=1e-7) and np.allclose(p2[:, 1], cy, atol=1e-7)
+
+
+def test_inside_naming_a_missing_part_samples_free():
+    """An INSIDE object whose part index is not a part of its template is
+    sampled with the draws of a free object."""
+    n = 64
+    q = np.full(n, 0.5, np.float32)
+    free = tiny_batch([[(0.0, 0.0, 0.0, 0.05)], [(0.0, 0.0, 0.0, 0.05)]], n_cand=n, parts=[_PART],
+                      part_q=q.reshape(n, 1))
+    bad = tiny_batch([[(0.0, 0.0, 0.0, 0.05)], [(0.0, 0.0, 0.0, 0.05)]], n_cand=n,
+                     rel=[0, synth.REL_INSIDE | (1 << 8)], parts=[_PART], part_q=q.reshape(n, 1))
+    pf, _, _ = oracle.sample_poses(free, seed=4)
+    pb, _, _ = oracle.sample_poses(bad, seed=4)
+    assert np.array_equal(pf, pb)
+
+
+def test_part_boxes_move_with_their_joint():
+    """Translation invariance: a box of part j at joint value q is the static
+    box with its centre moved by q * axis_j. Two parts with different axes and
+    values (a swapped part index or value shows) and a static box that must
+    not move; the static-box distance itself is pinned above."""
+    parts = [[0.6, 0.8, 0.0, 0.0, 1.0, 0, 0, 0, 0.1, 0.1, 0, 0], [0.0, 0.0, 1.0, -1.0, 1.0, 0, 0, 0, 0.1, 0.1, 0, 0]]
+    boxes = [[0.1, 0.0, 0.2, 0, 0, 0, 0.3826834, 0.9238795, 0.1, 0.2, 0.05, 0],
+             [-0.3, 0.2, 0.1, 0, 0.2, 0.1, 0.0, 0.9746794, 0.05, 0.1, 0.1, 0],
+             [0.5, -0.5, 0.0, 0, 0, 0, 0, 1, 0.2, 0.2, 0.2, 0]]
+    obb_part = [1, 0, -1]
+    q = np.array([[0.35, -0.4], [0.9, 0.25], [0.0, 0.0]], np.float32)
+    obj = [[(0.0, 0.0, 0.0, 0.05), (0.05, 0.02, 0.0, 0.03)]]
+    poses = synth.random_poses(tiny_batch(obj, n_cand=3), seed=3, spread=0.5)
+    moving = tiny_batch(obj, obbs=boxes, n_cand=3, parts=parts, obb_part=obb_part, part_q=q)
+    _, md, _ = oracle.collide(moving, poses)
+    for c in range(3):
+        moved = np.array(boxes, np.float64)
+        for i, j in enumerate(obb_part):
+            if j >= 0:
+                moved[i, :3] += np.float64(q[c, j]) * np.array(parts[j][:3], np.float32)
+        ref = [oracle.sphere_obb(oracle.sphere_world(s, poses[c]), moved[i].astype(np.float32))
+               for s in obj[0] for i in range(3)]
+        # the moved centres are rounded to FP32 in the reference: 1e-7 slack
+        assert abs(md[c] - min(ref)) <= 1e-6, (c, md[c], min(ref))
+    # the joint values matter: candidates 0 and 1 differ from the unmoved boxes
+    _, md_static, _ = oracle.collide(tiny_batch(obj, obbs=boxes, n_cand=3), poses)
+    assert md[2] == md_static[2] and md[0] != md_static[0] and md[1] != md_static[1]
+
+
+def test_sample_parts_counter_and_range():
+    """Joint values: uniform in [qmin, qmax] from the Philox counter
+    (c, 0xFFFF0000 + j, 0, 0) (pinned to numpy's Philox through the shared
+    round code above); slots past a template's part count stay 0."""
+    b = synth.cabinet(seed=1, n_templates=6, cand_per_template=400)
+    q = oracle.sample_parts(b, seed=9)
+    nparts = np.diff(b.tmpl_part_off)[b.cand_template()]
+    for c in (0, 5, 1234, b.n_cand - 1):
+        for j in range(q.shape[1]):
+            if j >= nparts[c]:
+                assert q[c, j] == 0.0
+                continue
+            u0 = oracle.uniform4(9, c, 0xFFFF0000 + j, 0, 0)[0]
+            assert abs(q[c, j] - np.float64(np.float32(0.35)) * u0) < 1e-15
+    live = q[:, :2].ravel()
+    assert live.min() >= 0.0 and live.max() < np.float32(0.35)
+    assert stats.kstest(live / np.float64(np.float32(0.35)), stats.uniform(0, 1).cdf).pvalue > 1e-3
+    act = np.array([3, 7], np.int32)
+    qa = oracle.sample_parts(b, seed=9, active=act)
+    assert np.array_equal(qa[act], q[act]) and not np.delete(qa, act, axis=0).any()
