@@ -77,6 +77,10 @@ WORKLOADS = {
     "hard": dict(make=lambda seed: synth.hard(seed=seed, n_templates=4096, n_reach=4), seed=5,
                  desc="relation-heavy 4096 templates x 64 candidates, 6-24 objects, 8-64 spheres/object, "
                       "on-top / next-to / directional / middle / face-to, convex 4-10-gon supports of 1-3 m^2"),
+    "cabinet": dict(make=lambda seed: synth.cabinet(seed=seed, n_templates=4096), seed=6,
+                    desc="articulated 4096 templates x 64 candidates: a counter with 4-10 objects over 2-3 drawers "
+                         "(prismatic, joint values drawn every step), 2 objects inside each drawer, 16 spheres "
+                         "per object, 14-19 world boxes of which 10-15 move with the drawers"),
     "tabletop": dict(make=lambda seed: synth.tabletop(seed=seed), seed=0,
                      desc="tabletop 1024 candidates x 8 objects x 16 spheres on a 1.2 x 0.8 m table"),
 }
@@ -325,6 +329,8 @@ def run_ours(args, wl):
         del tr, ho, ytr, yho
 
     def enqueue(step_seed, use_gate=True, use_graph=True, use_map=False):
+        if db.max_parts:  # a new articulation state per step, then the scenes around it
+            sc.sample_parts(ctx, db, seed=step_seed)
         sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=order, config=cfg, poses=poses,
                     out=(valid, band, tries), use_graph=use_graph and not args.no_graph,
                     arm=arm if reach else None, ik=ikp, gate=gate if use_gate and not use_map else None,
@@ -405,6 +411,8 @@ def run_ours(args, wl):
             if i >= 2:
                 stream.wait_event(ev_out[i - 2])  # slot j's results of step i-2 are out
             P_, V_, B_, T_, Q_ = outs[j]
+            if dbs[j].max_parts:
+                sc.sample_parts(ctxs[j], dbs[j], seed=seed * 7919 + 5000 + i)
             sc.generate(ctxs[j], dbs[j], seed=seed * 7919 + 5000 + i, max_retries=args.retries, order=order,
                         config=cfg, poses=P_, out=(V_, B_, T_), use_graph=not args.no_graph,
                         arm=arm if reach else None, ik=ikp, gate=gate, q_reach=Q_ if reach else None)
@@ -745,7 +753,8 @@ def launches_per_step(db, args, reach, gate):
     per_round_reach = 4 if gate is not None else 2
     n_reach = min(4, K) if reach else 0
     rounds = 2 * n_reach * (R + 1)  # generate_rounds(): a try of a reach object spans two rounds
-    return 2 + rounds * (1 + per_round_reach) + (1 if n_reach < K else 0)
+    parts = 1 if db.max_parts else 0  # sc_sample_parts before the generation call
+    return parts + 2 + rounds * (1 + per_round_reach) + (1 if n_reach < K else 0)
 
 
 def main():
