@@ -128,6 +128,14 @@ enum {
  *                             quaternion need not be normalised. A box of an articulated
  *                             part (obb_part >= 0) is centred at c + q * axis for each
  *                             candidate's joint value q of that part.
+ *  World meshes (NULL / 0 when there are none):
+ *  tmpl_tri_off  int32 [T+1], tri float [n_tri][12]: triangles of template t's world
+ *                             meshes, (ax, ay, az, -, bx, by, bz, -, cx, cy, cz, -) in the
+ *                             world frame, at most 65,536 per template; 16-byte aligned.
+ *                             A mesh is a surface: a sphere's distance to it is the
+ *                             distance from its centre to the nearest point of any
+ *                             triangle, minus r (unsigned; a sphere wholly inside a
+ *                             closed mesh does not touch it).
  *  cand_tmpl_off int32 [T+1]  candidates of template t: [cand_tmpl_off[t], cand_tmpl_off[t+1]);
  *                             the global candidate index is the Philox counter word 0.
  *  tmpl_pose_off int64 [T+1]  start of template t's block in the pose array; candidate
@@ -163,6 +171,9 @@ typedef struct {
   const float* part_param;
   const int32_t* obb_part;
   const float* part_q;
+  int32_t n_tri;
+  const int32_t* tmpl_tri_off;
+  const float* tri;
 } sc_scene_batch;
 
 /* ------------------------------------------------------------- sampling */
@@ -251,13 +262,16 @@ typedef struct {
 } sc_collide_config;
 
 /* Collision check of the listed candidates (Sec. IV-D; the paper uses cuRobo
- * meshes, this build per-object sphere sets and oriented boxes). Each sphere
+ * meshes, this build per-object sphere sets against oriented boxes and world
+ * triangle meshes). Each sphere
  * is moved by its object's pose (rotation about z by yaw, then translation),
  * and the minimum signed distance
  *   min( |c_i - c_j| - r_i - r_j  over spheres i of object a, j of object b,
  *                                  a < b, b >= first_new_obj,
  *        sdf_box(c_i) - r_i       over spheres of objects >= first_new_obj and
- *                                  the template's world boxes )
+ *                                  the template's world boxes,
+ *        dist_tri(c_i) - r_i      over the same spheres and the template's
+ *                                  world triangles (unsigned distance) )
  * is reduced per candidate; the empty set gives FLT_MAX. Touching (d = 0) is
  * free: collide = min_dist < 0. band = |min_dist| <= 1e-5 m.
  * first_new_obj = 0 checks the whole scene; k re-checks object k (and later)
@@ -279,6 +293,8 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
  * loop, read back after the call completes (synchronises the stream). Pairs
  * that the kernel proved unable to change the result are not counted. */
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs);
+/* Exact sphere-triangle distances of the last collision call (synchronises). */
+sc_status sc_collide_last_tri_work(sc_ctx* ctx, int64_t* sphere_tri_pairs);
 
 /* --------------------------------------------------------- reachability */
 
@@ -526,6 +542,7 @@ typedef struct {
   int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull */
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
                                   spheres x all spheres of the objects placed before it) */
+  int64_t sphere_tri_pairs;    /* exact sphere-triangle distances (after the ball cull) */
 } sc_gen_stats;
 sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured

@@ -50,7 +50,8 @@ class _Scene(ctypes.Structure):
                                        "tmpl_obb_off", "obb", "cand_tmpl_off", "tmpl_base", "obj_rel_dir",
                                        "obj_anchor_off", "obj_anchor")] + [
         ("n_parts", ctypes.c_int32), ("max_parts", ctypes.c_int32)] + [
-        (n, ctypes.c_void_p) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")]
+        (n, ctypes.c_void_p) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")] + [
+        ("n_tri", ctypes.c_int32), ("tmpl_tri_off", ctypes.c_void_p), ("tri", ctypes.c_void_p)]
 
 
 class _Arm(ctypes.Structure):
@@ -93,6 +94,10 @@ def _declare(L):
     L.or_grasp_target.argtypes = [P, ctypes.c_double, P, P]
     L.or_generate.argtypes = [P, P, P, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int]
     L.or_sample_parts.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int, P]
+    L.or_point_triangle.argtypes = [P, P, P, P]
+    L.or_point_triangle.restype = ctypes.c_double
+    L.or_sphere_triangle.argtypes = [P, P]
+    L.or_sphere_triangle.restype = ctypes.c_double
 
 
 def _ptr(a):
@@ -143,9 +148,17 @@ class Scene:
         self.n_cand = int(k["cand_tmpl_off"][-1])
         self.c = _Scene(len(k["tmpl_obj_off"]) - 1, len(k["obj_half"]), len(k["sph_local"]), len(k["poly_verts"]),
                         len(k["obb"]), self.n_cand)
+        # world meshes (None: no triangles)
+        tr = getattr(batch, "tri", None)
+        if tr is not None and np.asarray(tr).size:
+            k["tmpl_tri_off"] = _c(batch.tmpl_tri_off, np.int32)
+            k["tri"] = _c(tr, np.float32).reshape(-1, 12)
+        else:
+            k["tmpl_tri_off"] = k["tri"] = None
         for n, _ in _Scene._fields_[6:]:
-            if n not in ("n_parts", "max_parts"):
+            if n not in ("n_parts", "max_parts", "n_tri"):
                 setattr(self.c, n, _ptr(k[n]))
+        self.c.n_tri = 0 if k["tri"] is None else len(k["tri"])
         self.c.n_parts = 0 if k["part_param"] is None else len(k["part_param"])
         self.c.max_parts = self.max_parts
         sizes = np.diff(k["cand_tmpl_off"]).astype(np.int64) * np.diff(k["tmpl_obj_off"]).astype(np.int64)
@@ -193,6 +206,15 @@ def sphere_sphere(a, b):
 
 def sphere_obb(sphere, box12):
     return lib().or_sphere_obb(_ptr(_c(sphere, np.float64)), _ptr(_c(box12, np.float32)))
+
+
+def point_triangle(p, a, b, c):
+    """Distance from point p to the filled triangle abc (FP64)."""
+    return lib().or_point_triangle(*[_ptr(_c(x, np.float64)) for x in (p, a, b, c)])
+
+
+def sphere_triangle(sphere, tri12):
+    return lib().or_sphere_triangle(_ptr(_c(sphere, np.float64)), _ptr(_c(tri12, np.float32)))
 
 
 def sample_poses(batch, seed, max_attempts=16, retry=0, first_obj=0, n_obj=1 << 30, active=None, poses=None,

@@ -185,6 +185,9 @@ typedef struct {
   const float* part_param;       // [n_parts][12] axis, qmin | qmax, support centre | half x, y, yaw, -
   const int32_t* obb_part;       // [n_obb] template-local part a box moves with, -1 static (may be NULL)
   const float* part_q;           // [n_cand][max_parts] joint values
+  int32_t n_tri;                 // world mesh triangles; 0 when there are none
+  const int32_t* tmpl_tri_off;   // [T+1] triangles of template t
+  const float* tri;              // [n_tri][12] vertices a | b | c (x, y, z, -)
 } or_scene;
 
 enum {
@@ -524,6 +527,46 @@ static double sphere_obb_moved(const double* sphere, const float* box, const dou
 
 double or_sphere_obb(const double* sphere, const float* box) { return sphere_obb_moved(sphere, box, nullptr); }
 
+// Distance from point p to segment [a, b]: the nearest point a + t (b - a)
+// with t the projection parameter clamped to [0, 1].
+static double point_segment(const double* p, const double* a, const double* b) {
+  double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double l2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+  double t = l2 > 0.0 ? (ap[0] * ab[0] + ap[1] * ab[1] + ap[2] * ab[2]) / l2 : 0.0;
+  t = std::min(1.0, std::max(0.0, t));
+  double d[3] = {ap[0] - t * ab[0], ap[1] - t * ab[1], ap[2] - t * ab[2]};
+  return std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+// Distance from point p to the (closed, filled) triangle abc: the distance
+// to its plane when p's orthogonal projection falls inside the triangle (all
+// three barycentric coordinates >= 0), else the distance to the nearest of
+// its three edges. A zero-area triangle is its edges.
+double or_point_triangle(const double* p, const double* a, const double* b, const double* c) {
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  double edges = std::min(point_segment(p, a, b), std::min(point_segment(p, b, c), point_segment(p, c, a)));
+  if (!(nn > 0.0)) return edges;
+  double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double h = (ap[0] * n[0] + ap[1] * n[1] + ap[2] * n[2]) / nn;  // signed height over |n|^2
+  double q[3] = {ap[0] - h * n[0], ap[1] - h * n[1], ap[2] - h * n[2]};  // projection, relative to a
+  // barycentric coordinates of the projection: q = s e1 + t e2
+  double d11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], d22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+  double d12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+  double q1 = q[0] * e1[0] + q[1] * e1[1] + q[2] * e1[2], q2 = q[0] * e2[0] + q[1] * e2[1] + q[2] * e2[2];
+  double det = d11 * d22 - d12 * d12;
+  double s = (q1 * d22 - q2 * d12) / det, t = (q2 * d11 - q1 * d12) / det;
+  if (s >= 0.0 && t >= 0.0 && s + t <= 1.0) return std::fabs(h) * std::sqrt(nn);
+  return edges;
+}
+
+// Signed distance of sphere (c, r) to triangle `t` (12 floats as in or_scene.tri).
+double or_sphere_triangle(const double* sphere, const float* t) {
+  double a[3] = {t[0], t[1], t[2]}, b[3] = {t[4], t[5], t[6]}, c[3] = {t[8], t[9], t[10]};
+  return or_point_triangle(sphere, a, b, c) - sphere[3];
+}
+
 // Where world box `ob` of candidate c (template t) sits: a box of an
 // articulated part is moved by q * axis, q the candidate's joint value of it.
 static void box_shift(const or_scene* s, int t, int c, int ob, double shift[3]) {
@@ -565,6 +608,11 @@ static double candidate_min_dist(const or_scene* s, int t, int c, const double (
         box_shift(s, t, c, ob, sh);
         m = std::min(m, sphere_obb_moved(sj.data(), &s->obb[12 * ob], sh));
       }
+  if (s->n_tri > 0 && s->tmpl_tri_off && s->tri)
+    for (int b = std::max(first_new, 0); b < nt; ++b)
+      for (auto& sj : W[b])
+        for (int q = s->tmpl_tri_off[t]; q < s->tmpl_tri_off[t + 1]; ++q)
+          m = std::min(m, or_sphere_triangle(sj.data(), &s->tri[12 * q]));
   return m;
 }
 

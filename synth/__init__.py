@@ -61,6 +61,7 @@ class SceneBatch:
                                  (axis, qmin), (qmax, support centre), (support half x, y, yaw, 0)
       obb_part      int32 [n_obb] template-local part a box moves with (-1: static)
       part_q        f32 [B, max_parts] joint value of every part per candidate (drawn here)
+      tmpl_tri_off  int32 [T+1]; tri f32 [n_tri,12]: world mesh triangles a | b | c (x, y, z, 0)
     """
 
     tmpl_obj_off: np.ndarray
@@ -83,6 +84,8 @@ class SceneBatch:
     part_param: np.ndarray = None
     obb_part: np.ndarray = None
     part_q: np.ndarray = None
+    tmpl_tri_off: np.ndarray = None
+    tri: np.ndarray = None
     name: str = ""
 
     @property
@@ -137,6 +140,8 @@ class SceneBatch:
                 c0, c1 = int(self.cand_tmpl_off[t]), int(self.cand_tmpl_off[t + 1])
                 extra = dict(parts=self.part_param[p0:p1], obb_part=self.obb_part[b0:b1],
                              part_q=self.part_q[c0:c1, :p1 - p0])
+            if self.tri is not None:
+                extra["tri"] = self.tri[int(self.tmpl_tri_off[t]):int(self.tmpl_tri_off[t + 1])]
             parts.append(dict(**extra,
                 sph=self.sph_local[s0:s1], nsph=np.diff(self.obj_sph_off[o0:o1 + 1]),
                 half=self.obj_half[o0:o1], rel=self.obj_rel[o0:o1], relp=self.obj_rel_param[o0:o1],
@@ -173,7 +178,17 @@ def _pack(parts, name="") -> SceneBatch:
         obj_anchor=np.array([i for a in anchors for i in a], dtype=np.int32),
         name=name,
         **_pack_parts(parts),
+        **_pack_meshes(parts),
     )
+
+
+def _pack_meshes(parts) -> dict:
+    """CSR arrays of the world triangles (empty dict when no template has any)."""
+    if not any(len(p.get("tri", ())) for p in parts):
+        return {}
+    tris = [np.asarray(p.get("tri", np.zeros((0, 12))), np.float32).reshape(-1, 12) for p in parts]
+    return dict(tmpl_tri_off=np.concatenate([[0], np.cumsum([len(t) for t in tris])]).astype(np.int32),
+                tri=np.ascontiguousarray(np.concatenate(tris)))
 
 
 def _pack_parts(parts) -> dict:
@@ -453,6 +468,82 @@ def cabinet(seed: int = 6, n_templates: int = 64, cand_per_template: int = 64, c
         p["part_q"] = (lo + (hi - lo) * rng.uniform(size=(cand_per_template, nd))).astype(np.float32)
         parts.append(p)
     return _pack(parts, name=f"cabinet T={n_templates}x{cand_per_template}")
+
+
+def _tri_rows(v, faces):
+    """Triangle rows (a, 0, b, 0, c, 0) of faces [m,3] over vertices v [n,3]."""
+    out = np.zeros((len(faces), 12), np.float64)
+    for i in range(3):
+        out[:, 4 * i:4 * i + 3] = v[np.asarray(faces)[:, i]]
+    return out
+
+
+def box_mesh(centre, rot, half):
+    """The 12 triangles of a box surface: half extents `half`, rotation matrix
+    `rot` (3x3), centre `centre`."""
+    s = np.array([[x, y, z] for x in (-1, 1) for y in (-1, 1) for z in (-1, 1)], np.float64)
+    v = (s * np.asarray(half)) @ np.asarray(rot).T + np.asarray(centre)
+    faces = [(0, 1, 3), (0, 3, 2), (4, 6, 7), (4, 7, 5), (0, 4, 5), (0, 5, 1),
+             (2, 3, 7), (2, 7, 6), (0, 2, 6), (0, 6, 4), (1, 5, 7), (1, 7, 3)]
+    return _tri_rows(v, faces)
+
+
+def sphere_mesh(centre, radius, n_lat=8, n_lon=12):
+    """A latitude-longitude sphere surface: 2 n_lon (n_lat - 1) triangles."""
+    v = [[0.0, 0.0, 1.0]]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2 * math.pi * j / n_lon
+            v.append([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    v.append([0.0, 0.0, -1.0])
+    v = np.array(v) * radius + np.asarray(centre)
+    ring = lambda i, j: 1 + (i - 1) * n_lon + (j % n_lon)
+    faces = [(0, ring(1, j), ring(1, j + 1)) for j in range(n_lon)]
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            faces += [(ring(i, j), ring(i + 1, j), ring(i + 1, j + 1)), (ring(i, j), ring(i + 1, j + 1), ring(i, j + 1))]
+    last = len(v) - 1
+    faces += [(last, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)) for j in range(n_lon)]
+    return _tri_rows(v, faces)
+
+
+def _rot_z_tilt(rng):
+    """A random rotation: yaw U(0, 2 pi) then a tilt U(-0.3, 0.3) rad about x."""
+    a, b = rng.uniform(0, 2 * math.pi), rng.uniform(-0.3, 0.3)
+    rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    return rz @ rx
+
+
+def meshes(seed: int = 7, n_templates: int = 4096, cand_per_template: int = 64, obj_range=(4, 24),
+           sph_range=(8, 64), box_range=(2, 6), ball_range=(1, 3)) -> SceneBatch:
+    """World-mesh workload (stand-in for the paper's mesh worlds checked by
+    cuRobo, Sec. IV-D): the ragged recipe's objects (relations as in
+    draw_relations) on convex 4..10-gon supports of 1..3 m^2 at z = 0.75,
+    cluttered by U{2..6} box meshes (12 triangles; half extents U(0.03, 0.25),
+    a random yaw and a tilt within 0.3 rad) and U{1..3} sphere meshes
+    (192 triangles, radius U(0.05, 0.2)), centres uniform over the support's
+    bounding box at heights U(0.70, 1.10)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_templates):
+        n = int(rng.integers(obj_range[0], obj_range[1] + 1))
+        counts = rng.integers(sph_range[0], sph_range[1] + 1, size=n)
+        poly = convex_polygon(rng, int(rng.integers(4, 11)), float(rng.uniform(1.0, 3.0)))
+        p = make_template(rng, n, counts, poly)
+        lo, hi = poly.min(axis=0), poly.max(axis=0)
+        tris = []
+        for _ in range(int(rng.integers(box_range[0], box_range[1] + 1))):
+            c = [rng.uniform(lo[0], hi[0]), rng.uniform(lo[1], hi[1]), rng.uniform(0.70, 1.10)]
+            tris.append(box_mesh(c, _rot_z_tilt(rng), rng.uniform(0.03, 0.25, 3)))
+        for _ in range(int(rng.integers(ball_range[0], ball_range[1] + 1))):
+            c = [rng.uniform(lo[0], hi[0]), rng.uniform(lo[1], hi[1]), rng.uniform(0.70, 1.10)]
+            tris.append(sphere_mesh(c, rng.uniform(0.05, 0.2)))
+        p["tri"] = np.concatenate(tris).astype(np.float32)
+        p["ncand"] = cand_per_template
+        parts.append(p)
+    return _pack(parts, name=f"meshes T={n_templates}x{cand_per_template}")
 
 
 def random_poses(batch: SceneBatch, seed: int, spread: float = 0.6) -> np.ndarray:

@@ -832,3 +832,73 @@ def test_sample_parts_counter_and_range():
     act = np.array([3, 7], np.int32)
     qa = oracle.sample_parts(b, seed=9, active=act)
     assert np.array_equal(qa[act], q[act]) and not np.delete(qa, act, axis=0).any()
+
+
+# --------------------------------------------------------------------------- world meshes
+
+
+def test_point_triangle_closed_forms():
+    """Over the interior: the height above the plane; beyond a vertex: the
+    distance to it; beside an edge: the distance to that edge's line; a
+    collinear (zero-area) triangle is the segment between its extremes."""
+    a, b, c = np.array([0.0, 0, 0]), np.array([2.0, 0, 0]), np.array([0.0, 1.0, 0])
+    assert oracle.point_triangle([0.3, 0.2, -0.7], a, b, c) == pytest.approx(0.7, abs=1e-15)
+    assert oracle.point_triangle([-1.0, -1.0, 1.0], a, b, c) == pytest.approx(math.sqrt(3), abs=1e-15)
+    assert oracle.point_triangle([1.0, -0.5, 0.0], a, b, c) == pytest.approx(0.5, abs=1e-15)
+    # beside the hypotenuse b-c (line x + 2y = 2): distance |x + 2y - 2| / sqrt(5)
+    p = np.array([1.5, 1.0, 0.25])
+    assert oracle.point_triangle(p, a, b, c) == pytest.approx(math.hypot(1.5 / math.sqrt(5), 0.25), abs=1e-14)
+    assert oracle.point_triangle([3.0, 1.0, 0.0], a, b, [1.0, 0, 0]) == pytest.approx(math.sqrt(2), abs=1e-15)
+
+
+def test_point_triangle_brute_force():
+    """Against the minimum over a dense barycentric grid of the triangle (a
+    brute-force distance: never below the true one, above it by at most the
+    grid's spacing), on random triangles and points."""
+    rng = np.random.default_rng(3)
+    k = 200
+    s, t = np.meshgrid(np.arange(k + 1) / k, np.arange(k + 1) / k)
+    keep = s + t <= 1
+    s, t = s[keep], t[keep]
+    for _ in range(40):
+        a, b, c = rng.normal(size=(3, 3))
+        pts = a + s[:, None] * (b - a) + t[:, None] * (c - a)
+        spacing = max(np.linalg.norm(b - a), np.linalg.norm(c - a)) / k
+        p = rng.normal(size=3) * 1.5
+        d = oracle.point_triangle(p, a, b, c)
+        brute = np.min(np.linalg.norm(pts - p, axis=1))
+        assert d <= brute + 1e-12 and brute - d <= spacing
+
+
+def test_box_mesh_distance_is_the_box_sdf():
+    """The distance to the 12-triangle surface of a box equals the box's SDF
+    (pinned above) outside it and minus the SDF inside it."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        q = Rotation.random(random_state=rng)
+        c, h = rng.uniform(-1, 1, 3), rng.uniform(0.05, 0.5, 3)
+        box = np.concatenate([c, [0], q.as_quat(), h, [0]]).astype(np.float32)
+        # the box from the rounded float32 values both sides see
+        cb, qb, hb = box[:3].astype(np.float64), box[4:8].astype(np.float64), box[8:11].astype(np.float64)
+        tris = synth.box_mesh(cb, Rotation.from_quat(qb).as_matrix(), hb).astype(np.float32)
+        for p in rng.uniform(-1.5, 1.5, (10, 3)):
+            sdf = oracle.sphere_obb(np.concatenate([p, [0.0]]), box)
+            d = min(oracle.sphere_triangle(np.concatenate([p, [0.0]]), t) for t in tris)
+            assert d == pytest.approx(abs(sdf), abs=2e-6)
+
+
+def test_collide_counts_the_nearest_triangle():
+    """A one-sphere object over a triangle: min_dist is the plane height minus
+    r (closed form), a collision once the sphere dips through the surface, and
+    triangles only count for objects >= first_new."""
+    tri = [[0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0]]
+    b = tiny_batch([[(0.0, 0.0, 0.0, 0.05)], [(0.0, 0.0, 0.0, 0.05)]], n_cand=3)
+    b.tmpl_tri_off, b.tri = np.array([0, 1], np.int32), np.array(tri, np.float32)
+    poses = np.array([[5, 5, 5, 0], [0.2, 0.2, 0.30, 1.0],
+                      [5, 5, 5, 0], [0.2, 0.2, 0.03, 0.0],
+                      [0.2, 0.2, 0.03, 0.0], [-5, -5, 5, 0]], np.float32)
+    col, md, _ = oracle.collide(b, poses)
+    assert md[0] == pytest.approx(np.float64(np.float32(0.30)) - np.float64(np.float32(0.05)), abs=1e-12)
+    assert col[1] == 1 and md[1] == pytest.approx(np.float64(np.float32(0.03)) - np.float64(np.float32(0.05)))
+    col2, md2, _ = oracle.collide(b, poses, first_new=1)
+    assert col2[2] == 0 and md2[2] > 1.0  # object 0 dips through the triangle but is not new
