@@ -81,6 +81,10 @@ WORKLOADS = {
                     desc="articulated 4096 templates x 64 candidates: a counter with 4-10 objects over 2-3 drawers "
                          "(prismatic, joint values drawn every step), 2 objects inside each drawer, 16 spheres "
                          "per object, 14-19 world boxes of which 10-15 move with the drawers"),
+    "meshes": dict(make=lambda seed: synth.meshes(seed=seed, n_templates=4096), seed=7,
+                   desc="world-mesh 4096 templates x 64 candidates, 4-24 objects, 8-64 spheres/object, convex "
+                        "4-10-gon supports of 1-3 m^2 cluttered by 2-6 box meshes (12 triangles) and 1-3 sphere "
+                        "meshes (192 triangles), 216-1152 triangles per template"),
     "tabletop": dict(make=lambda seed: synth.tabletop(seed=seed), seed=0,
                      desc="tabletop 1024 candidates x 8 objects x 16 spheres on a 1.2 x 0.8 m table"),
 }

@@ -17,6 +17,7 @@ from ._native import (  # noqa: F401
     sample_parts,
     collide,
     collide_last_work,
+    collide_last_tri_work,
     generate,
     ik_reach,
     ik_dls_step,

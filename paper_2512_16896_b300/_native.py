@@ -35,7 +35,8 @@ class ScSceneBatch(ctypes.Structure):
         (n, P) for n in ("tmpl_obj_off", "obj_sph_off", "sph_local", "obj_half", "obj_rel", "obj_rel_param",
                          "tmpl_poly_off", "poly_verts", "tmpl_support_z", "tmpl_obb_off", "obb", "cand_tmpl_off",
                          "tmpl_pose_off", "tmpl_base", "obj_rel_dir", "obj_anchor_off", "obj_anchor")] + [
-        ("n_parts", I32), ("max_parts", I32)] + [(n, P) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")]
+        ("n_parts", I32), ("max_parts", I32)] + [(n, P) for n in ("tmpl_part_off", "part_param", "obb_part", "part_q")] + [
+        ("n_tri", I32), ("tmpl_tri_off", P), ("tri", P)]
 
 
 class ScSampleParams(ctypes.Structure):
@@ -45,14 +46,14 @@ class ScSampleParams(ctypes.Structure):
 class ScGenStats(ctypes.Structure):
     _fields_ = [("sphere_pairs", I64), ("sphere_box_pairs", I64), ("ik_solves", I64), ("gate_rejections", I64),
                 ("ik_seed_iterations", I64), ("ms_stage", ctypes.c_float * 3), ("launches_stage", I32 * 3),
-                ("cull_tests", I64), ("exhaustive_pairs", I64)]
+                ("cull_tests", I64), ("exhaustive_pairs", I64), ("sphere_tri_pairs", I64)]
 
     def as_dict(self):
         return {"sphere_pairs": self.sphere_pairs, "sphere_box_pairs": self.sphere_box_pairs,
                 "ik_solves": self.ik_solves, "gate_rejections": self.gate_rejections,
                 "ik_seed_iterations": self.ik_seed_iterations, "ms_stage": list(self.ms_stage),
                 "launches_stage": list(self.launches_stage), "cull_tests": self.cull_tests,
-                "exhaustive_pairs": self.exhaustive_pairs}
+                "exhaustive_pairs": self.exhaustive_pairs, "sphere_tri_pairs": self.sphere_tri_pairs}
 
 
 class ScRmapParams(ctypes.Structure):
@@ -117,6 +118,7 @@ SIGNATURES = {
     "sc_collide_ex": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, ctypes.POINTER(CollideConfig), P,
                                      P, P]),
     "sc_collide_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    "sc_collide_last_tri_work": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
     "sc_generate": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScGenParams), P, I32,
                                    ctypes.POINTER(CollideConfig), ctypes.POINTER(ScGenReach), P, P, P, P, P]),
@@ -229,7 +231,8 @@ class DeviceBatch:
               "tmpl_obb_off": torch.int32, "obb": torch.float32, "cand_tmpl_off": torch.int32,
               "tmpl_base": torch.float32}
     OPTIONAL = {"obj_rel_dir": torch.float32, "obj_anchor_off": torch.int32, "obj_anchor": torch.int32,
-                "tmpl_part_off": torch.int32, "part_param": torch.float32, "obb_part": torch.int32}
+                "tmpl_part_off": torch.int32, "part_param": torch.float32, "obb_part": torch.int32,
+                "tmpl_tri_off": torch.int32, "tri": torch.float32}
 
     def __init__(self, batch, device: int | str | torch.device = "cuda", pinned_host: bool = False):
         self.t = {}
@@ -269,7 +272,10 @@ class DeviceBatch:
         nsph = self.obj_sph_off[self.tmpl_obj_off[1:]] - self.obj_sph_off[self.tmpl_obj_off[:-1]]
         self.n_poses = int(tpo[-1])
         self.n_cand = int(self.cand_tmpl_off[-1])
-        ptrs = {n: _ptr(self.t.get(n)) for n, _ in ScSceneBatch._fields_[8:] if n not in ("n_parts", "max_parts")}
+        if "tri" not in self.t:  # no world meshes: neither triangle array
+            self.t.pop("tmpl_tri_off", None)
+        ptrs = {n: _ptr(self.t.get(n)) for n, _ in ScSceneBatch._fields_[8:]
+                if n not in ("n_parts", "max_parts", "n_tri")}
         self.c = ScSceneBatch(
             n_t, len(batch.obj_half), len(batch.sph_local), len(batch.poly_verts), len(batch.obb), self.n_cand,
             int(nobj.max()), int(nsph.max()))
@@ -277,6 +283,7 @@ class DeviceBatch:
             setattr(self.c, n, v)
         self.c.n_parts = len(batch.part_param) if self.max_parts else 0
         self.c.max_parts = self.max_parts
+        self.c.n_tri = self.t["tri"].numel() // 12 if "tri" in self.t else 0
         if len(batch.obb) == 0:
             self.c.obb = None
 
@@ -552,6 +559,13 @@ def collide_last_work(ctx: Context):
     a, b = I64(), I64()
     _check(lib().sc_collide_last_work(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def collide_last_tri_work(ctx: Context) -> int:
+    """Exact sphere-triangle distances of the last collide call (synchronises)."""
+    a = I64()
+    _check(lib().sc_collide_last_tri_work(ctx.handle, ctypes.byref(a)))
+    return a.value
 
 
 def order_by_work(batch) -> np.ndarray:

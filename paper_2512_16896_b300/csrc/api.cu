@@ -21,7 +21,7 @@ struct sc_ctx {
   void* scratch = nullptr;
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;
-  unsigned long long* d_stats = nullptr;  // [7] (generation); [2] (collision)
+  unsigned long long* d_stats = nullptr;  // [8] (generation); [0..1] and [7] (collision)
   // grow-on-demand scratch of sc_generate (candidate lists and counters)
   void* gen_scratch = nullptr;
   size_t gen_scratch_bytes = 0;
@@ -129,6 +129,11 @@ sc_status check_batch(const sc_scene_batch* b) {
         (b->obb_part && !aligned(b->obb_part, 4)))
       return fail(SC_ERR_INVALID, "part_param must be 16-byte aligned, the other part arrays 4-byte aligned");
   }
+  if (b->n_tri < 0) return fail(SC_ERR_INVALID, "n_tri = %d < 0", b->n_tri);
+  if (b->n_tri > 0 && (!b->tmpl_tri_off || !b->tri))
+    return fail(SC_ERR_INVALID, "a batch with triangles needs tmpl_tri_off and tri");
+  if (b->n_tri > 0 && (!aligned(b->tri, 16) || !aligned(b->tmpl_tri_off, 4)))
+    return fail(SC_ERR_INVALID, "tri must be 16-byte aligned, tmpl_tri_off 4-byte aligned");
   return SC_OK;
 }
 
@@ -215,7 +220,8 @@ sc_status sc_ctx_synchronize(sc_ctx* ctx) {
     cudaMemset(ctx->d_status, 0, sizeof(int));
     if (st == sc::kDevTimeout) return fail(SC_ERR_TIMEOUT, "a bounded tensor-core wait gave up (device code 7)");
     return fail(SC_ERR_DEVICE, "a kernel latched device error code %d (1 bad template, 2 too many spheres, "
-                "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation, 8 bad part)", st);
+                "3 too many objects, 4 too many boxes, 5 bad polygon, 6 bad relation, 8 bad part, "
+                "9 too many triangles)", st);
   }
   return SC_OK;
 }
@@ -406,7 +412,8 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     }
     a.reach_objects = want_reach ? ctx->reach_extent : 0;
     a.max_sph_obj = ctx->max_sph_obj;
-    a.ext_rel = ctx->ext_rel || batch->n_parts > 0;  // parts move boxes and carry INSIDE supports
+    // parts move boxes and carry INSIDE supports; triangles are checked there too
+    a.ext_rel = ctx->ext_rel || batch->n_parts > 0 || batch->n_tri > 0;
   }
   if (a.reach_objects > 0) {  // side streams and events of the rounds
     const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;
@@ -987,7 +994,7 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   if (sc_status s = check_ctx(ctx)) return s;
   if (!out) return fail(SC_ERR_INVALID, "out is NULL");
   DeviceGuard g(ctx->device);
-  unsigned long long h[7] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
   if (!e) e = cudaStreamSynchronize(ctx->stream);
   if (e) return cuda_fail(e, "stats read");
@@ -999,6 +1006,7 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   out->ik_seed_iterations = (int64_t)h[4];
   out->cull_tests = (int64_t)h[5];
   out->exhaustive_pairs = (int64_t)h[6];
+  out->sphere_tri_pairs = (int64_t)h[7];
   if (ctx->timing) {
     for (int i = 0; i < ctx->timer.used; ++i) {
       float ms = 0.f;
@@ -1024,6 +1032,18 @@ sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphe
   if (e != cudaSuccess) return cuda_fail(e, "stats read");
   if (sphere_pairs) *sphere_pairs = (int64_t)h[0];
   if (sphere_box_pairs) *sphere_box_pairs = (int64_t)h[1];
+  return SC_OK;
+}
+
+sc_status sc_collide_last_tri_work(sc_ctx* ctx, int64_t* sphere_tri_pairs) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  DeviceGuard g(ctx->device);
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->d_stats + 7, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stats read");
+  if (sphere_tri_pairs) *sphere_tri_pairs = (int64_t)h;
   return SC_OK;
 }
 

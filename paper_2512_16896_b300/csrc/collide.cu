@@ -16,6 +16,7 @@
 //    time (object-pair ball cull) with the prune test of collide_core.cuh.
 #include "collide_core.cuh"
 #include "kernels.h"
+#include "tri_core.cuh"
 
 namespace sc {
 
@@ -313,6 +314,63 @@ __device__ __forceinline__ float box_units(const Smem& sm, CtaShared& sh, int f,
   return m;
 }
 
+// Sphere vs world triangle for the objects [f, n), one (object, triangle)
+// unit at a time, the passes and thresholds of box_units: the unit's bound is
+// L = dist(ball centre, triangle) - R, below every sphere's distance to the
+// triangle minus its radius (the triangle is a convex set, its distance
+// 1-Lipschitz), with kBroadMargin for FP32 rounding; the narrow phase
+// computes each sphere's exact distance. tri: the template's first triangle.
+template <int PASS>
+__device__ __forceinline__ float tri_units(const Smem& sm, CtaShared& sh, const float* tri, int f, int n, int ntri,
+                                           float m, int lane, int warp, int nwarps, unsigned long long& my_tri) {
+  constexpr bool DECIDE = PASS == 0;
+  const float4 r4 = sm.opose[0];
+  const float3 ref = make_float3(r4.x, r4.y, r4.z);
+  const int nu = (n - f) * ntri;
+#pragma unroll 1
+  for (int u0 = warp * 32; u0 < nu; u0 += nwarps * 32) {
+    float lim = (DECIDE ? kBand : 0.f) + kBroadMargin;
+    if (PASS == 2) lim = fminf(m, key_float(*(volatile int*)&sh.best_key)) + kBroadMargin;
+    const int u = u0 + lane;
+    bool need = false;
+    if (u < nu) {
+      const int o = f + u / ntri, k = u - (o - f) * ntri;
+      const float4 p = sm.opose[o];
+      const Tri T = load_tri(tri, k, ref);
+      const float L = sqrtf(point_tri_d2(make_float3(p.x - ref.x, p.y - ref.y, p.z - ref.z), T)) - sm.osc[o].x;
+      need = PASS == 2 ? (L >= kBroadMargin && L < lim) : L < lim;
+    }
+    unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
+#pragma unroll 1
+    while (mask) {
+      const int uu = u0 + __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int o = f + uu / ntri, k = uu - (o - f) * ntri;
+      const Tri T = load_tri(tri, k, ref);
+      const int lo = sm.off[o], hi = sm.off[o + 1];
+#pragma unroll 1
+      for (int i = lo + lane; i < hi; i += 32) {
+        const float4 w = sm.W[i];
+        m = fminf(m, sqrtf(point_tri_d2(make_float3(w.x, w.y, w.z), T)) - w.w);
+      }
+      if (lane == 0) my_tri += (unsigned long long)(hi - lo);
+      if (DECIDE) {
+        if (__any_sync(0xFFFFFFFFu, m < -kBand)) {
+          if (lane == 0) *(volatile int*)&sh.hit = 1;
+          return m;
+        }
+        if (__any_sync(0xFFFFFFFFu, *(volatile int*)&sh.hit != 0)) return m;
+      }
+    }
+    if (DECIDE && __any_sync(0xFFFFFFFFu, *(volatile int*)&sh.hit != 0)) return m;
+    if (PASS == 2) {
+      const float wm = warp_min(m);
+      if (lane == 0 && wm < kFarSentinel) atomicMin(&sh.best_key, float_key(wm));
+    }
+  }
+  return m;
+}
+
 // Seed pairs: the first two spheres of every object against those of every
 // later object (the later one new, obj >= f), before the pair sweep. They
 // are real pairs, so their minimum is an upper bound on the result that the
@@ -451,7 +509,7 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
   const Layout L = make_layout(b.max_sph, b.max_obj, APL);
   const Smem sm = smem_view(smem, L);
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  unsigned long long my_pairs = 0, my_box = 0;
+  unsigned long long my_pairs = 0, my_box = 0, my_tri = 0;
 
   // the next candidate is claimed while this one is reduced: thread 0 stores
   // it in sh.item just before the candidate's last barrier
@@ -464,8 +522,14 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
     if (tid == 0) next = (int)atomicAdd(a.counter, 1u);
     const int c = a.active ? __ldg(&a.active[item]) : item;
     const int t = template_of(b, c);
-    int o0 = 0, nt = 0, s0 = 0, S = 0, nobb = 0, bx0 = 0;
+    int o0 = 0, nt = 0, s0 = 0, S = 0, nobb = 0, bx0 = 0, ntri = 0;
+    const float* tri = nullptr;
     int64_t pbase = 0;
+    if (t >= 0 && b.n_tri > 0) {
+      const int q0 = __ldg(&b.tmpl_tri_off[t]);
+      ntri = __ldg(&b.tmpl_tri_off[t + 1]) - q0;
+      tri = b.tri + 12 * (int64_t)q0;
+    }
     if (t >= 0) {
       o0 = __ldg(&b.tmpl_obj_off[t]);
       nt = __ldg(&b.tmpl_obj_off[t + 1]) - o0;
@@ -478,7 +542,8 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
     const int err = t < 0 ? kDevBadTemplate
                     : (S > b.max_sph || S + kPad > L.cap) ? kDevTooManySpheres
                     : (nt > b.max_obj || nt > kMaxObj || nt < 1) ? kDevTooManyObjects
-                    : (nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes : kDevOk;
+                    : (nobb > kMaxObbPerTemplate) ? kDevTooManyBoxes
+                    : (ntri < 0 || ntri > kMaxTriPerTemplate) ? kDevTooManyTriangles : kDevOk;
     if (err != kDevOk) {
       if (tid == 0) {
         latch_error(a.status, err);
@@ -507,18 +572,23 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
     const float eps = 1e-5f * (__int_as_float(sh.r2max_key) + 0.01f);
     float m = kFarSentinel;
     bool pairs = f < nt;
-    if (pairs && nobb > 0) {
+    if (pairs && (nobb > 0 || ntri > 0)) {
       if (DECIDE) {
-        m = box_units<0>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        if (nobb > 0) m = box_units<0>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        if (ntri > 0 && !__any_sync(0xFFFFFFFFu, *(volatile int*)&sh.hit != 0))
+          m = tri_units<0>(sm, sh, tri, f, nt, ntri, m, lane, warp, nwarps, my_tri);
       } else {
-        m = box_units<1>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        if (nobb > 0) m = box_units<1>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        if (ntri > 0) m = tri_units<1>(sm, sh, tri, f, nt, ntri, m, lane, warp, nwarps, my_tri);
         const float wm = warp_min(m);
         if (lane == 0 && wm < kFarSentinel) atomicMin(&sh.best_key, float_key(wm));
         __syncthreads();
         // a unit left for pass 2 has L >= kBroadMargin: it can only matter
         // while the minimum so far is positive
-        if (key_float(*(volatile int*)&sh.best_key) > 0.f)
-          m = box_units<2>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+        if (key_float(*(volatile int*)&sh.best_key) > 0.f) {
+          if (nobb > 0) m = box_units<2>(sm, sh, f, nt, nobb, m, lane, warp, nwarps, my_box);
+          if (ntri > 0) m = tri_units<2>(sm, sh, tri, f, nt, ntri, m, lane, warp, nwarps, my_tri);
+        }
       }
       m = warp_min(m);
       if (!DECIDE && lane == 0 && m < kFarSentinel) atomicMin(&sh.best_key, float_key(m));
@@ -559,10 +629,12 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
   for (int o = 16; o > 0; o >>= 1) {
     my_pairs += __shfl_xor_sync(0xFFFFFFFFu, my_pairs, o);
     my_box += __shfl_xor_sync(0xFFFFFFFFu, my_box, o);
+    my_tri += __shfl_xor_sync(0xFFFFFFFFu, my_tri, o);
   }
   if (lane == 0 && a.stats) {
     atomicAdd(&a.stats[0], my_pairs);
     atomicAdd(&a.stats[1], my_box);
+    atomicAdd(&a.stats[7], my_tri);
   }
 }
 
@@ -627,6 +699,7 @@ cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, cons
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   if (a.stats && (e = cudaMemsetAsync(a.stats, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if (a.stats && (e = cudaMemsetAsync(a.stats + 7, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if (a.n_items <= 0) return cudaSuccess;
   KArgs K{b, a, cfg.seg_len};
   return cfg.decide_only ? launch_mode<true>(K, cfg, smem, num_sms, s) : launch_mode<false>(K, cfg, smem, num_sms, s);

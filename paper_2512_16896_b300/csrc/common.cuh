@@ -30,6 +30,7 @@ enum DeviceError : int {
   kDevBadRelation = 6,  // relation refers to itself or a later object
   kDevTimeout = 7,      // a bounded wait on a tensor-core MMA or bulk copy gave up
   kDevBadPart = 8,      // a box or an INSIDE relation names a part its template does not have
+  kDevTooManyTriangles = 9,
 };
 
 // Byte offset of element (r, k) of a [rows][K] bf16 matrix in the canonical

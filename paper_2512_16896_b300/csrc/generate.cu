@@ -20,6 +20,7 @@
 #include "kernels.h"
 #include "mlp_tc_core.cuh"
 #include "sample_core.cuh"
+#include "tri_core.cuh"
 
 namespace sc {
 
@@ -173,7 +174,7 @@ __device__ __forceinline__ void sweep_block(const float4* astage, int fill, cons
 
 // Work counted by lane 0 of a warp.
 struct TryCounters {
-  unsigned long long pairs = 0, box = 0, cull = 0, exh = 0;
+  unsigned long long pairs = 0, box = 0, cull = 0, exh = 0, tri = 0;
 };
 
 struct TryOut {
@@ -181,10 +182,47 @@ struct TryOut {
   bool band;  // a decision of the try lay within the band
 };
 
+// Object k (position pk, yaw sine/cosine skn/kcs, ball radius rk, spheres
+// [sph0, sph0 + Sk) of the batch) against the world triangles of template t,
+// coordinates relative to ref: lanes take triangles and keep those within the
+// band of object k's ball (distance minus its radius, with kBroadMargin for
+// rounding), then each kept triangle's exact distance to every sphere of
+// object k. Returns this lane's minimum.
+__device__ __forceinline__ float world_tri_min(const sc_scene_batch& b, int t, float4 pk, float4 ref, float rk,
+                                                float skn, float kcs, int sph0, int Sk, int lane,
+                                                unsigned long long& tri_cnt) {
+  float m = kFarSentinel;
+  const int tq0 = __ldg(&b.tmpl_tri_off[t]), ntri = __ldg(&b.tmpl_tri_off[t + 1]) - tq0;
+  const float3 r3 = make_float3(ref.x, ref.y, ref.z);
+  const float3 ck = make_float3(pk.x - ref.x, pk.y - ref.y, pk.z - ref.z);
+#pragma unroll 1
+  for (int j0 = 0; j0 < ntri; j0 += 32) {
+    bool near = false;
+    if (j0 + lane < ntri)
+      near = sqrtf(point_tri_d2(ck, load_tri(b.tri, tq0 + j0 + lane, r3))) - rk < kBand + kBroadMargin;
+    unsigned mask = __ballot_sync(0xFFFFFFFFu, near);
+#pragma unroll 1
+    while (mask) {
+      const Tri Tj = load_tri(b.tri, tq0 + j0 + __ffs(mask) - 1, r3);
+      mask &= mask - 1;
+#pragma unroll 1
+      for (int q = lane; q < Sk; q += 32) {
+        const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + sph0 + q);
+        const float3 w = make_float3((pk.x - ref.x) + (kcs * l.x - skn * l.y), (pk.y - ref.y) + (skn * l.x + kcs * l.y),
+                                     (pk.z - ref.z) + l.z);
+        m = fminf(m, sqrtf(point_tri_d2(w, Tj)) - l.w);
+      }
+      if (lane == 0) tri_cnt += (unsigned long long)Sk;
+    }
+  }
+  return m;
+}
+
 // One try (Sec. IV-A, Fig. 2) of template-local object k of candidate c:
 // sample its pose (the pose is written to poses[pbase + k] whatever the
-// outcome), then decide it against the kept earlier objects and the world
-// boxes. On entry the warp state holds objects 0..k-1 (opose, osc, orad,
+// outcome), then decide it against the kept earlier objects, the world
+// boxes and (relation-enabled instances) the world triangles. On entry the
+// warp state holds objects 0..k-1 (opose, osc, orad,
 // off[0..k]); with PREFETCHED, their poses, half extents (in kball) and
 // offsets are cp.async copies still in flight, completed here after the
 // sampling, and osc / orad are derived from them. On return, when the pose
@@ -343,6 +381,9 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     cnt.exh += (unsigned long long)Sprev * (unsigned long long)Sk;
     cnt.cull += (unsigned long long)Sk * (unsigned long long)nkeep;
   }
+  // ---- object k against the world triangles (relation-enabled instances)
+  if (EXT && b.n_tri > 0 && !__any_sync(0xFFFFFFFFu, m < -kBand))
+    m = fminf(m, world_tri_min(b, t, pk, ref, rk, skn, kcs, s0 + Sprev, Sk, lane, cnt.tri));
   m = warp_min(m);
   bool alive = !(m < -kBand);
   r2 = -warp_min(-r2);
@@ -466,6 +507,7 @@ __device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCoun
     atomicAdd(&g.stats[1], cnt.box);
     atomicAdd(&g.stats[5], cnt.cull);
     atomicAdd(&g.stats[6], cnt.exh);
+    if (cnt.tri) atomicAdd(&g.stats[7], cnt.tri);
   }
 }
 
@@ -957,7 +999,7 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += stride) counts[i] = (i == 0) ? n : 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counters; i += stride) counters[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x < 7 && stats) stats[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 8 && stats) stats[threadIdx.x] = 0;
 }
 
 template <int APL, bool EXT>
