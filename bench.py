@@ -58,6 +58,9 @@ import synth  # noqa: E402
 OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 1 FADD + 4 FFMA
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
 OPS_PER_SPHERE_BOX_COLLIDE = 15  # collision kernel: box frame (9 FFMA), |p| - h (3 FADD), bound (2 FMNMX + FSETP)
+OPS_PER_POINT_TRI = 77     # point-triangle distance, face region: edges and offsets 15 FADD, six dot products 18,
+                           # area terms 8, 2 divisions 8, nearest point 6 FFMA, |q|^2 3, sqrt 4, - r 1,
+                           # region tests 12 FSETP, world position of the sphere 2 (FADD)
 OPS_PER_CULL_TEST = 10     # sphere vs bounding ball: 3 FADD, FMUL + 2 FFMA, 2 FADD (limit), FMUL, FSETP
 OPS_PER_EXHAUSTIVE_PAIR = 9  # one pair of an uncalled exhaustive check (3 FADD, FMUL + 2 FFMA, FADD, FMUL, FSETP)
 OPS_PER_IK_SEED_ITER = 720  # one check + DLS step: FK 280, check 40, error 21, J 63, J J^T 147, Cholesky 50,
@@ -454,6 +457,7 @@ def run_ours(args, wl):
         ms_ik = sum(s["ms_stage"][2] for s in st)
         ops_gen = sum(s["sphere_pairs"] for s in st) * OPS_PER_SPHERE_PAIR + \
             sum(s["sphere_box_pairs"] for s in st) * OPS_PER_SPHERE_BOX + \
+            sum(s["sphere_tri_pairs"] for s in st) * OPS_PER_POINT_TRI + \
             sum(s["cull_tests"] for s in st) * OPS_PER_CULL_TEST
         ops_exh = sum(s["exhaustive_pairs"] for s in st) * OPS_PER_EXHAUSTIVE_PAIR
         ops_ik = sum(s["ik_seed_iterations"] for s in st) * OPS_PER_IK_SEED_ITER
@@ -518,6 +522,7 @@ def run_ours(args, wl):
                    "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
                    "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
                    "sphere_pairs_per_step": st0["sphere_pairs"], "cull_tests_per_step": st0["cull_tests"],
+                   "point_triangle_per_step": st0["sphere_tri_pairs"],
                    "exhaustive_pairs_per_step": st0["exhaustive_pairs"],
                    "ik_seed_iterations_per_step": st0["ik_seed_iterations"],
                    "gen_roofline_frac": gen_rf["frac"], "ik_roofline_frac": ik_rf["frac"],

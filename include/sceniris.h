@@ -293,7 +293,8 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
  * loop, read back after the call completes (synchronises the stream). Pairs
  * that the kernel proved unable to change the result are not counted. */
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs);
-/* Exact sphere-triangle distances of the last collision call (synchronises). */
+/* Point-triangle distances (ball culls and exact sphere distances) of the
+ * last sc_collide / sc_collide_ex / sc_generate call (synchronises). */
 sc_status sc_collide_last_tri_work(sc_ctx* ctx, int64_t* sphere_tri_pairs);
 
 /* --------------------------------------------------------- reachability */
@@ -542,7 +543,7 @@ typedef struct {
   int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull */
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
                                   spheres x all spheres of the objects placed before it) */
-  int64_t sphere_tri_pairs;    /* exact sphere-triangle distances (after the ball cull) */
+  int64_t sphere_tri_pairs;    /* point-triangle distances: ball culls and exact sphere distances */
 } sc_gen_stats;
 sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured

@@ -340,6 +340,7 @@ __device__ __forceinline__ float tri_units(const Smem& sm, CtaShared& sh, const 
       const float L = sqrtf(point_tri_d2(make_float3(p.x - ref.x, p.y - ref.y, p.z - ref.z), T)) - sm.osc[o].x;
       need = PASS == 2 ? (L >= kBroadMargin && L < lim) : L < lim;
     }
+    if (lane == 0) my_tri += (unsigned long long)min(32, nu - u0);
     unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
 #pragma unroll 1
     while (mask) {

@@ -200,6 +200,7 @@ __device__ __forceinline__ float world_tri_min(const sc_scene_batch& b, int t, f
     bool near = false;
     if (j0 + lane < ntri)
       near = sqrtf(point_tri_d2(ck, load_tri(b.tri, tq0 + j0 + lane, r3))) - rk < kBand + kBroadMargin;
+    if (lane == 0) tri_cnt += (unsigned long long)min(32, ntri - j0);
     unsigned mask = __ballot_sync(0xFFFFFFFFu, near);
 #pragma unroll 1
     while (mask) {
