@@ -557,7 +557,7 @@ def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
     out = {}
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     want = lambda key: only is None or re.search(only, key) is not None
-    if any(want(f"collide_{m}_{w}") for m in ("exact_min", "decide") for w in ("shelf", "ragged")):
+    if any(want(f"collide_{m}_{w}") for m in ("exact_min", "decide") for w in ("shelf", "ragged", "meshes")):
         kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand)
     if any(want(k) for k in ("ik_topdown_262144", "gate_infer_262144", "gate_train_epoch_262144",
                               "rmap_build_262144", "rmap_query_262144")):
@@ -569,24 +569,28 @@ def exhaustive_work(batch):
     """Sphere pairs between different objects and sphere-box pairs of every
     candidate of a batch (the all-pairs check the culls stand in for)."""
     so, to, bo = batch.obj_sph_off, batch.tmpl_obj_off, batch.tmpl_obb_off
+    tro = batch.tmpl_tri_off if batch.tri is not None else np.zeros(len(to), np.int64)
     ncand = np.diff(batch.cand_tmpl_off)
-    pairs = boxes = 0
+    pairs = boxes = tris = 0
     for t in range(len(to) - 1):
         n_o = np.diff(so[to[t]:to[t + 1] + 1]).astype(np.int64)
         S = int(n_o.sum())
         pairs += int(ncand[t]) * (S * S - int((n_o * n_o).sum())) // 2
         boxes += int(ncand[t]) * S * int(bo[t + 1] - bo[t])
-    return pairs, boxes
+        tris += int(ncand[t]) * S * int(tro[t + 1] - tro[t])
+    return pairs, boxes, tris
 
 
 def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
     """Whole-scene collision on sampled poses, both modes: the shelf batch
-    (65,536 x 32 objects x 64 spheres, 20 boxes) and the ragged batch."""
+    (65,536 x 32 objects x 64 spheres, 20 boxes), the ragged batch and the
+    world-mesh batch."""
     import torch
     stream = ctx.stream
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    for name, make in (("shelf", lambda: synth.shelf(seed=1, n_cand=shelf_cand)), ("ragged", lambda: synth.ragged(seed=2))):
+    for name, make in (("shelf", lambda: synth.shelf(seed=1, n_cand=shelf_cand)), ("ragged", lambda: synth.ragged(seed=2)),
+                       ("meshes", lambda: synth.meshes(seed=7))):
         keys = {0: f"collide_exact_min_{name}", 1: f"collide_decide_{name}"}
         if not any(want(k) for k in keys.values()):
             continue
@@ -597,7 +601,7 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
         col = torch.empty(batch.n_cand, dtype=torch.uint8, device=dev)
         md = torch.empty(batch.n_cand, dtype=torch.float32, device=dev)
         cb = torch.empty(batch.n_cand, dtype=torch.uint8, device=dev)
-        pairs_all, box_all = exhaustive_work(batch)
+        pairs_all, box_all, tri_all = exhaustive_work(batch)
         for mode, key in keys.items():
             if not want(key):
                 continue
@@ -609,22 +613,26 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
                 a.record(stream)
                 sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=(0, 0, 0, 0, mode))
                 b.record(stream)
-                work.append(sc.collide_last_work(ctx))
+                work.append(sc.collide_last_work(ctx) + (sc.collide_last_tri_work(ctx),))
                 if i >= 2:
                     ms.append(a.elapsed_time(b))
             t = np.mean(ms) / 1e3
-            ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE for p, q in work[2:]])
+            ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE + r * OPS_PER_POINT_TRI
+                           for p, q, r in work[2:]])
             out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": batch.n_cand / t,
                         "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
                         "box_pairs": float(np.mean([w[1] for w in work[2:]])),
                         "exhaustive_pairs": float(pairs_all),
                         "exhaustive_box_pairs": float(box_all),
+                        "point_triangle": float(np.mean([w[2] for w in work[2:]])),
+                        "exhaustive_sphere_triangle": float(tri_all),
                         "collide_frac": float(col.float().mean().item()),
                         "roofline_frac": float(ops / t / peak_ops),
                         # every pair at the same rate: the work the bounding-ball
                         # culls save, as a fraction of the FP32 issue peak
                         "exhaustive_equivalent_frac": float((pairs_all * OPS_PER_EXHAUSTIVE_PAIR + box_all *
-                                                             OPS_PER_SPHERE_BOX_COLLIDE) / t / peak_ops)}
+                                                             OPS_PER_SPHERE_BOX_COLLIDE + tri_all *
+                                                             OPS_PER_POINT_TRI) / t / peak_ops)}
         del db, poses, col, md, cb
 
 
