@@ -540,7 +540,8 @@ typedef struct {
                                   grasp-target + gate launches, and the IK launches (stages run
                                   concurrently on different streams, so these may overlap) */
   int32_t launches_stage[3];
-  int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull */
+  int64_t cull_tests;          /* sphere-vs-bounding-ball tests of the exact sphere-level cull
+                                  (and triangle-chunk ball tests) */
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
                                   spheres x all spheres of the objects placed before it) */
   int64_t sphere_tri_pairs;    /* point-triangle distances: ball culls and exact sphere distances */

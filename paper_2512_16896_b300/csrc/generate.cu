@@ -55,6 +55,7 @@ struct GenStepArgs {
   const TmplInfo* tinfo;    // [n_templates]
   const float* edge_inv;    // [n_verts] 1 / squared length of the edge ending at each vertex
   const float4* obb_tab;    // [n_obb][4] (R row 0 | cx), (R row 1 | cy), (R row 2 | cz), (hx, hy, hz, 0)
+  const float4* tri_chunk;  // [tri_chunk_slots] bounding ball (centre, radius) of 32 triangles (world frame)
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, max_retries, seg_len;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
@@ -184,36 +185,59 @@ struct TryOut {
 
 // Object k (position pk, yaw sine/cosine skn/kcs, ball radius rk, spheres
 // [sph0, sph0 + Sk) of the batch) against the world triangles of template t,
-// coordinates relative to ref: lanes take triangles and keep those within the
-// band of object k's ball (distance minus its radius, with kBroadMargin for
-// rounding), then each kept triangle's exact distance to every sphere of
-// object k. Returns this lane's minimum.
-__device__ __forceinline__ float world_tri_min(const sc_scene_batch& b, int t, float4 pk, float4 ref, float rk,
-                                                float skn, float kcs, int sph0, int Sk, int lane,
-                                                unsigned long long& tri_cnt) {
+// coordinates relative to ref, in three exact culls: chunks of 32 triangles
+// whose bounding balls (chunks, world frame) come within the band of object
+// k's ball; their triangles within the band of the ball (distance minus its
+// radius); each kept triangle's exact distance to every sphere of object k.
+// kBroadMargin absorbs FP32 rounding at both cull levels. Chunk tests count
+// as ball cull tests (cull_cnt), point-triangle distances in tri_cnt.
+// Returns this lane's minimum.
+__device__ __forceinline__ float world_tri_min(const sc_scene_batch& b, const float4* chunks, int t, float4 pk,
+                                                float4 ref, float rk, float skn, float kcs, int sph0, int Sk,
+                                                int lane, unsigned long long& tri_cnt,
+                                                unsigned long long& cull_cnt) {
   float m = kFarSentinel;
   const int tq0 = __ldg(&b.tmpl_tri_off[t]), ntri = __ldg(&b.tmpl_tri_off[t + 1]) - tq0;
+  const int nch = (ntri + 31) >> 5;
   const float3 r3 = make_float3(ref.x, ref.y, ref.z);
   const float3 ck = make_float3(pk.x - ref.x, pk.y - ref.y, pk.z - ref.z);
+  const float3 cw = make_float3(pk.x, pk.y, pk.z);
 #pragma unroll 1
-  for (int j0 = 0; j0 < ntri; j0 += 32) {
-    bool near = false;
-    if (j0 + lane < ntri)
-      near = sqrtf(point_tri_d2(ck, load_tri(b.tri, tq0 + j0 + lane, r3))) - rk < kBand + kBroadMargin;
-    if (lane == 0) tri_cnt += (unsigned long long)min(32, ntri - j0);
-    unsigned mask = __ballot_sync(0xFFFFFFFFu, near);
+  for (int c0 = 0; c0 < nch; c0 += 32) {
+    // chunk level: lanes take chunks; a chunk whose ball is farther from
+    // object k's ball than the band holds no triangle that matters
+    bool chunk_near = false;
+    if (c0 + lane < nch) {
+      const float4 cb = __ldg(&chunks[tri_chunk_slot(tq0, t, c0 + lane)]);
+      const float dx = cw.x - cb.x, dy = cw.y - cb.y, dz = cw.z - cb.z;
+      const float lim = cb.w + rk + kBand + kBroadMargin;
+      chunk_near = dx * dx + dy * dy + dz * dz <= lim * lim;
+    }
+    if (lane == 0) cull_cnt += (unsigned long long)min(32, nch - c0);
+    unsigned cmask = __ballot_sync(0xFFFFFFFFu, chunk_near);
 #pragma unroll 1
-    while (mask) {
-      const Tri Tj = load_tri(b.tri, tq0 + j0 + __ffs(mask) - 1, r3);
-      mask &= mask - 1;
+    while (cmask) {
+      const int j0 = (c0 + __ffs(cmask) - 1) * 32;
+      cmask &= cmask - 1;
+      // triangle level: lanes take the chunk's triangles
+      bool near = false;
+      if (j0 + lane < ntri)
+        near = sqrtf(point_tri_d2(ck, load_tri(b.tri, tq0 + j0 + lane, r3))) - rk < kBand + kBroadMargin;
+      if (lane == 0) tri_cnt += (unsigned long long)min(32, ntri - j0);
+      unsigned mask = __ballot_sync(0xFFFFFFFFu, near);
 #pragma unroll 1
-      for (int q = lane; q < Sk; q += 32) {
-        const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + sph0 + q);
-        const float3 w = make_float3((pk.x - ref.x) + (kcs * l.x - skn * l.y), (pk.y - ref.y) + (skn * l.x + kcs * l.y),
-                                     (pk.z - ref.z) + l.z);
-        m = fminf(m, sqrtf(point_tri_d2(w, Tj)) - l.w);
+      while (mask) {
+        const Tri Tj = load_tri(b.tri, tq0 + j0 + __ffs(mask) - 1, r3);
+        mask &= mask - 1;
+#pragma unroll 1
+        for (int q = lane; q < Sk; q += 32) {
+          const float4 l = __ldg(reinterpret_cast<const float4*>(b.sph_local) + sph0 + q);
+          const float3 w = make_float3((pk.x - ref.x) + (kcs * l.x - skn * l.y),
+                                       (pk.y - ref.y) + (skn * l.x + kcs * l.y), (pk.z - ref.z) + l.z);
+          m = fminf(m, sqrtf(point_tri_d2(w, Tj)) - l.w);
+        }
+        if (lane == 0) tri_cnt += (unsigned long long)Sk;
       }
-      if (lane == 0) tri_cnt += (unsigned long long)Sk;
     }
   }
   return m;
@@ -384,7 +408,7 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
   }
   // ---- object k against the world triangles (relation-enabled instances)
   if (EXT && b.n_tri > 0 && !__any_sync(0xFFFFFFFFu, m < -kBand))
-    m = fminf(m, world_tri_min(b, t, pk, ref, rk, skn, kcs, s0 + Sprev, Sk, lane, cnt.tri));
+    m = fminf(m, world_tri_min(b, g.tri_chunk, t, pk, ref, rk, skn, kcs, s0 + Sprev, Sk, lane, cnt.tri, cnt.cull));
   m = warp_min(m);
   bool alive = !(m < -kBand);
   r2 = -warp_min(-r2);
@@ -923,8 +947,44 @@ __global__ void batch_scan_kernel(sc_scene_batch b, int* out) {
 // length of every polygon edge (edge i runs from vertex i-1 to vertex i,
 // cyclically within its polygon; 0 for a zero-length edge).
 __global__ void gen_tables_kernel(sc_scene_batch b, int32_t* cand_t, TmplInfo* tinfo, float* edge_inv,
-                                  float4* obb_tab) {
+                                  float4* obb_tab, float4* tri_chunk) {
   const int stride = gridDim.x * blockDim.x;
+  // triangle chunks (one warp per template): the centre of the chunk's
+  // bounding box and the largest vertex distance from it, rounded up by a
+  // relative 1e-6 and 1e-6 m so the ball holds every vertex despite FP32
+  if (b.n_tri > 0) {
+    const int lane = threadIdx.x & 31, nwarp = stride >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < b.n_templates; t += nwarp) {
+      const int tq0 = b.tmpl_tri_off[t], ntri = b.tmpl_tri_off[t + 1] - tq0;
+      for (int j = 0; j * 32 < ntri; ++j) {
+        const bool has = j * 32 + lane < ntri;
+        float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+        float v[9];
+        if (has) {
+          const float* q = b.tri + 12 * (int64_t)(tq0 + j * 32 + lane);
+          for (int i = 0; i < 3; ++i)
+            for (int d = 0; d < 3; ++d) {
+              v[3 * i + d] = q[4 * i + d];
+              lo[d] = fminf(lo[d], v[3 * i + d]);
+              hi[d] = fmaxf(hi[d], v[3 * i + d]);
+            }
+        }
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = warp_min(lo[d]);
+          hi[d] = -warp_min(-hi[d]);
+        }
+        const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]), cz = 0.5f * (lo[2] + hi[2]);
+        float r2 = 0.f;
+        if (has)
+          for (int i = 0; i < 3; ++i) {
+            const float dx = v[3 * i] - cx, dy = v[3 * i + 1] - cy, dz = v[3 * i + 2] - cz;
+            r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+          }
+        r2 = -warp_min(-r2);
+        if (lane == 0) tri_chunk[tri_chunk_slot(tq0, t, j)] = make_float4(cx, cy, cz, sqrtf(r2) * 1.000001f + 1e-6f);
+      }
+    }
+  }
   // world boxes: the transpose of R (box frame -> world, from the normalised
   // quaternion) row by row with the centre, then the half extents
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n_obb; i += stride) {
@@ -1054,10 +1114,11 @@ int generate_rounds(int reach_objects, int max_retries) {
 // [NR] each); work counters (generation claims per round, the chained
 // launch's, IK claims per round); the per-candidate state (object, try,
 // alive); the per-call tables (candidate templates, TmplInfo records,
-// inverse edge lengths, world-box frames); then the seed scalar.
+// inverse edge lengths, world-box frames, triangle chunk balls); then the
+// seed scalar.
 // NR is bounded by generate_rounds(max_obj, max_retries).
 struct GenScratch {
-  size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, obb_tab, seed, total;
+  size_t lists, counts, counters, kc, rc, alive, cand_t, tinfo, edge_inv, obb_tab, tri_chunk, seed, total;
 };
 
 static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int max_retries) {
@@ -1075,7 +1136,8 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   L.tinfo = up(L.cand_t + (size_t)b.n_cand * sizeof(int32_t));
   L.edge_inv = up(L.tinfo + (size_t)b.n_templates * sizeof(TmplInfo));
   L.obb_tab = up(L.edge_inv + (size_t)b.n_verts * sizeof(float));
-  L.seed = up(L.obb_tab + (size_t)b.n_obb * 4 * sizeof(float4));  // the 8-byte seed on a 256-byte boundary
+  L.tri_chunk = up(L.obb_tab + (size_t)b.n_obb * 4 * sizeof(float4));
+  L.seed = up(L.tri_chunk + tri_chunk_slots(b) * sizeof(float4));  // the 8-byte seed on a 256-byte boundary
   L.total = L.seed + 256;
   return L;
 }
@@ -1133,6 +1195,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   TmplInfo* tinfo = reinterpret_cast<TmplInfo*>(sb + SL.tinfo);
   float* edge_inv = reinterpret_cast<float*>(sb + SL.edge_inv);
   float4* obb_tab = reinterpret_cast<float4*>(sb + SL.obb_tab);
+  float4* tri_chunk = reinterpret_cast<float4*>(sb + SL.tri_chunk);
 
   int grid = 0;
   cudaError_t e;
@@ -1162,7 +1225,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     tmax = tmax > b.n_obb ? tmax : b.n_obb;
     int tb = (tmax + 255) / 256;
     tb = tb < num_sms * 4 ? tb : num_sms * 4;
-    gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv, obb_tab);
+    gen_tables_kernel<<<tb < 1 ? 1 : tb, 256, 0, s>>>(b, cand_t, tinfo, edge_inv, obb_tab, tri_chunk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   GenStepArgs g;
@@ -1172,6 +1235,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.tinfo = tinfo;
   g.edge_inv = edge_inv;
   g.obb_tab = obb_tab;
+  g.tri_chunk = tri_chunk;
   g.seed = a.seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;

@@ -12,6 +12,17 @@ struct Tri {
   float3 a, b, c;
 };
 
+// Triangles are also grouped per template in chunks of 32 consecutive ones;
+// chunk j of template t (first triangle tq0) has the table slot
+// tq0 / 32 + t + j, a layout without collisions in at most
+// n_tri / 32 + n_templates + 1 slots (template t's chunks touch at most as
+// many 32-aligned blocks as they cover, so its last slot stays below the
+// next template's first).
+__host__ __device__ __forceinline__ int tri_chunk_slot(int tq0, int t, int j) { return tq0 / 32 + t + j; }
+__host__ __device__ __forceinline__ size_t tri_chunk_slots(const sc_scene_batch& b) {
+  return b.n_tri > 0 ? (size_t)b.n_tri / 32 + (size_t)b.n_templates + 1 : 0;
+}
+
 // Triangle q of the batch, its vertices relative to `ref`.
 __device__ __forceinline__ Tri load_tri(const float* tri, int q, float3 ref) {
   const float4* t = reinterpret_cast<const float4*>(tri) + 3 * (int64_t)q;

@@ -540,7 +540,7 @@ def meshes(seed: int = 7, n_templates: int = 4096, cand_per_template: int = 64, 
         for _ in range(int(rng.integers(ball_range[0], ball_range[1] + 1))):
             c = [rng.uniform(lo[0], hi[0]), rng.uniform(lo[1], hi[1]), rng.uniform(0.70, 1.10)]
             tris.append(sphere_mesh(c, rng.uniform(0.05, 0.2)))
-        p["tri"] = np.concatenate(tris).astype(np.float32)
+        p["tri"] = np.concatenate(tris).astype(np.float32) if tris else np.zeros((0, 12), np.float32)
         p["ncand"] = cand_per_template
         parts.append(p)
     return _pack(parts, name=f"meshes T={n_templates}x{cand_per_template}")

@@ -73,8 +73,8 @@ def test_triangle_cases_and_work(sc, ctx):
     """One sphere against single triangles in every Voronoi region (above the
     face, beside each edge, beyond each vertex) and against zero-area
     triangles (collinear, a point): distances within 1e-6 of the oracle; the
-    point-triangle distances the kernel reports are at most a ball cull and
-    an exact distance per candidate."""
+    point-triangle distances the kernel reports are at most a ball cull per
+    pass (two in exact-minimum mode) and an exact distance per candidate."""
     tris = [[0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0],       # right triangle in z = 0
             [0, 0, 0, 0, 1, 1, 0, 0, 2, 2, 0, 0],       # collinear
             [0.3, 0.3, 0.3, 0, 0.3, 0.3, 0.3, 0, 0.3, 0.3, 0.3, 0]]  # a point
@@ -89,7 +89,7 @@ def test_triangle_cases_and_work(sc, ctx):
         work = sc.collide_last_tri_work(ctx)
         _, omd, _ = oracle.collide(b, poses)
         assert np.max(np.abs(gmd.cpu().numpy() - omd)) <= 1e-6
-        assert 0 < work <= 2 * len(pts)
+        assert 0 < work <= 3 * len(pts)
 
 
 def test_mesh_arrays_validated(sc, ctx):
