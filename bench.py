@@ -54,7 +54,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-# Algorithmic FP32-pipe operations per evaluated pair ("Rooflines"):
+# Algorithmic FP32-pipe operations per evaluated pair:
 OPS_PER_SPHERE_PAIR = 5    # prune test |a|^2 - q^2 + |b|^2 - r^2 - 2a.b - 2qr: 1 FADD + 4 FFMA
 OPS_PER_SPHERE_BOX = 18    # box frame (3 FADD + 3 FMUL + 6 FFMA), |p| - h (3 FADD), bound (3 FMNMX)
 OPS_PER_SPHERE_BOX_COLLIDE = 15  # collision kernel: box frame (9 FFMA), |p| - h (3 FADD), bound (2 FMNMX + FSETP)
