@@ -182,7 +182,8 @@ class ClockSampler:
 # only for the exact sources it was captured on).
 KERNEL_SOURCES = {
     "reach_ik_kernel": ("generate.cu", "ik_core.cuh", "common.cuh", "kernels.h"),
-    "gen_chain_kernel": ("generate.cu", "collide_core.cuh", "sample_core.cuh", "common.cuh", "kernels.h"),
+    "gen_chain_kernel": ("generate.cu", "collide_core.cuh", "sample_core.cuh", "tri_core.cuh", "common.cuh",
+                         "kernels.h"),
 }
 
 
