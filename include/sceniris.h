@@ -232,8 +232,9 @@ sc_status sc_sample_poses(sc_ctx* ctx, const sc_scene_batch* batch, const sc_sam
                           const int32_t* active, int32_t n_active, float* poses, uint8_t* sample_ok,
                           uint8_t* band);
 
-/* Joint value of every articulated part of the listed candidates (the
- * paper's randomised articulation states, e.g. how far each drawer is open):
+/* Joint value of every articulated part of the listed candidates (Sec. IV-B:
+ * a batched forward kinematics sets each instance's articulation, e.g. how
+ * far each drawer is open; a prismatic part's FK is the translation q * axis):
  * part_q[c * max_parts + j] = qmin + (qmax - qmin) u0 with
  * u = Philox(seed; c, 0xFFFF0000 + j, 0, 0), u0 as in sc_sample_poses.
  * part_q: device float [n_cand][max_parts]; entries of other candidates and

@@ -456,7 +456,8 @@ int or_sample_poses(const or_scene* s, uint64_t seed, int max_attempts, int retr
   return 0;
 }
 
-// Randomised articulation (Sec. IV-F 'inside' needs the parts' states): the
+// Randomised articulation (Sec. IV-B batched forward kinematics; the 'inside'
+// supports of Sec. IV-F sit on the parts): the
 // joint value of part j of candidate c is uniform in [qmin, qmax], drawn from
 // the Philox counter (c, 0xFFFF0000 + j, 0, 0), which no pose draw uses.
 int or_sample_parts(const or_scene* s, uint64_t seed, const int32_t* active, int n_active, double* part_q) {

@@ -100,3 +100,22 @@ def test_mesh_arrays_validated(sc, ctx):
     with pytest.raises(sc.SceniError):
         sc.collide(ctx, db, db.new_poses())
     ctx.synchronize()
+
+
+def test_triangle_limit_latches_device_code_9(sc, ctx):
+    """A template with more than 65,536 triangles: the collision kernel
+    latches device code 9 for its candidates and reports them as band."""
+    n = 65537
+    tri = np.zeros((n, 12), np.float32)
+    tri[:, 0:3] = [5.0, 5.0, 5.0]
+    tri[:, 4:7] = [5.1, 5.0, 5.0]
+    tri[:, 8:11] = [5.0, 5.1, 5.0]
+    b = tiny_batch([[(0.0, 0.0, 0.0, 0.01)]], n_cand=2)
+    b.tmpl_tri_off, b.tri = np.array([0, n], np.int32), tri
+    db = sc.DeviceBatch(b)
+    _, _, band = sc.collide(ctx, db, db.new_poses())
+    with pytest.raises(sc.SceniError) as ei:
+        ctx.synchronize()
+    assert "device error code 9" in str(ei.value)
+    assert band.cpu().numpy().all()
+    ctx.synchronize()

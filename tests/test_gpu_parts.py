@@ -134,3 +134,12 @@ def test_part_arrays_validated(sc, ctx):
         ctx.synchronize()
     assert "device error code 8" in str(ei.value)
     ctx.synchronize()
+
+
+def test_part_count_limit_refused(sc, ctx):
+    """More than 16 parts in a template (max_parts > 16) is refused on the host."""
+    part = [[1.0, 0.0, 0.0, 0.0, 0.2, 0.0, 0.0, 0.0, 0.2, 0.2, 0.0, 0.0]] * 17
+    b = tiny_batch([[(0, 0, 0, 0.01)]], n_cand=2, parts=part)
+    with pytest.raises(sc.SceniError):
+        sc.sample_poses(ctx, sc.DeviceBatch(b), seed=1)
+    ctx.synchronize()
