@@ -311,21 +311,28 @@ __global__ void __launch_bounds__(128) mlp_backward_act_kernel(MlpDev M, const f
   }
 }
 
-// dW[n][k] = sum_s daT[n][s] hT[k][s] for one layer; one warp per 16 x 64
-// tile (n0, k0); K = batch rows, padded to a multiple of 16 with zeros.
-__global__ void __launch_bounds__(128) mlp_weight_grad_kernel(const __nv_bfloat16* daT, const __nv_bfloat16* hT,
-                                                              int n_out, int n_in, int B, int Bpad, float* dW,
-                                                              int dW_stride, int n_in_store) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, warps = blockDim.x >> 5;
+// dW[n][k] = sum_s daT[n][s] hT[k][s] for one layer; one CTA per 16 x 64
+// tile (n0, k0), K = batch rows padded to a multiple of 16 with zeros. The
+// CTA's kWgSplit warps take every kWgSplit-th 16-row step of the batch, so a
+// tile's serial chain is kWgSplit times shorter; their partial sums are added
+// in warp order through shared memory (the same order on every run).
+constexpr int kWgSplit = 8;
+
+__global__ void __launch_bounds__(32 * kWgSplit) mlp_weight_grad_kernel(const __nv_bfloat16* daT,
+                                                                         const __nv_bfloat16* hT, int n_out, int n_in,
+                                                                         int B, int Bpad, float* dW, int dW_stride,
+                                                                         int n_in_store) {
+  __shared__ float part[kWgSplit][16 * 64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const int tiles_n = n_out / 16, tiles_k = (n_in + 63) / 64;
-  for (int tile = blockIdx.x * warps + w; tile < tiles_n * tiles_k; tile += gridDim.x * warps) {
+  for (int tile = blockIdx.x; tile < tiles_n * tiles_k; tile += gridDim.x) {
     const int n0 = (tile / tiles_k) * 16, k0 = (tile % tiles_k) * 64;
     const int nk = min(64, n_in - k0) / 8;  // n-tiles of 8 in this chunk (n_in is a multiple of 8)
     float c[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
-    for (int s0 = 0; s0 < Bpad; s0 += 16) {
+    for (int s0 = w * 16; s0 < Bpad; s0 += 16 * kWgSplit) {
       uint32_t a[4];
       a[0] = ld32(daT + (size_t)(n0 + g) * B + s0 + 2 * t4);
       a[1] = ld32(daT + (size_t)(n0 + g + 8) * B + s0 + 2 * t4);
@@ -342,14 +349,21 @@ __global__ void __launch_bounds__(128) mlp_weight_grad_kernel(const __nv_bfloat1
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (j < nk) {
-        const int col = k0 + j * 8 + 2 * t4;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int r = n0 + g + (h >> 1) * 8, cc = col + (h & 1);
-          if (cc < n_in_store) dW[(size_t)r * dW_stride + cc] = c[j][h];
-        }
+        for (int h = 0; h < 4; ++h) part[w][(g + (h >> 1) * 8) * 64 + j * 8 + 2 * t4 + (h & 1)] = c[j][h];
       }
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+      const int r = e >> 6, cc = e & 63;
+      if (cc < nk * 8 && k0 + cc < n_in_store) {
+        float v = part[0][e];
+#pragma unroll
+        for (int q = 1; q < kWgSplit; ++q) v += part[q][e];
+        dW[(size_t)(n0 + r) * dW_stride + k0 + cc] = v;
+      }
+    }
+    __syncthreads();  // part is reused by the CTA's next tile
   }
 }
 
@@ -665,9 +679,14 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
                                                                             v.tc, v.bo);
   const int ld = S->Bcap;
   // dW1 [256][9] from da1T . x16T, dW2, dW3
-  mlp_weight_grad_kernel<<<64, 128, 0, s>>>(v.bo.da1T, v.tc.x16T, H, KIN, ld, Bpad, S->grads + OFF_W1, 9, 9);
-  mlp_weight_grad_kernel<<<64, 128, 0, s>>>(v.bo.da2T, v.tc.h1T, H, H, ld, Bpad, S->grads + OFF_W2, H, H);
-  mlp_weight_grad_kernel<<<64, 128, 0, s>>>(v.bo.da3T, v.tc.h2T, H, H, ld, Bpad, S->grads + OFF_W3, H, H);
+  // one CTA per 16 x 64 tile of each weight gradient
+  const int wg_tiles_1 = (H / 16) * ((KIN + 63) / 64), wg_tiles_h = (H / 16) * ((H + 63) / 64);
+  mlp_weight_grad_kernel<<<wg_tiles_1, 32 * kWgSplit, 0, s>>>(v.bo.da1T, v.tc.x16T, H, KIN, ld, Bpad,
+                                                              S->grads + OFF_W1, 9, 9);
+  mlp_weight_grad_kernel<<<wg_tiles_h, 32 * kWgSplit, 0, s>>>(v.bo.da2T, v.tc.h1T, H, H, ld, Bpad,
+                                                              S->grads + OFF_W2, H, H);
+  mlp_weight_grad_kernel<<<wg_tiles_h, 32 * kWgSplit, 0, s>>>(v.bo.da3T, v.tc.h2T, H, H, ld, Bpad,
+                                                              S->grads + OFF_W3, H, H);
   mlp_bias_grad_kernel<<<64, 256, 0, s>>>(v.bo.da1T, v.bo.da2T, v.bo.da3T, v.tc.h3T, v.bo.dz, B, ld, S->grads);
   return cudaGetLastError();
 }
