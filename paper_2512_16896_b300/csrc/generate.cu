@@ -339,6 +339,18 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     __syncwarp();
   }
   a_bound = -warp_min(-a_bound);
+  // boxes of articulated parts: the candidate's shifts q * axis, one per box,
+  // staged in the A area (unused until the sweep) so the box loop reads them
+  // from shared memory instead of a chain of dependent global loads
+  const bool shifted = EXT && b.max_parts > 0 && b.obb_part != nullptr;
+  if (shifted) {
+#pragma unroll 1
+    for (int bi = lane; bi < nobb; bi += 32) {
+      const float3 sh = box_shift(b, t, c, bx0 + bi, g.status);
+      W.astage[bi] = make_float4(sh.x, sh.y, sh.z, 0.f);
+    }
+    __syncwarp();
+  }
   // ---- object k's spheres (B side), one pass: world frame, world boxes
   // (exact box SDF where the lower bound max(|p| - h) - r is within the
   // band), cull against the kept objects' balls, compacted into Bs as they
@@ -365,7 +377,7 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
         const float4* o = g.obb_tab + 4 * (bx0 + bi);
         const float4 R0 = __ldg(o), R1 = __ldg(o + 1), R2 = __ldg(o + 2), Hh = __ldg(o + 3);
         // an articulated part's box moves with the candidate's joint value
-        const float3 sh = EXT ? box_shift(b, t, c, bx0 + bi, g.status) : make_float3(0.f, 0.f, 0.f);
+        const float4 sh = shifted ? W.astage[bi] : make_float4(0.f, 0.f, 0.f, 0.f);
         // box frame: p = R^T (c - centre); rows of R^T are the columns of R,
         // stored as the table's rows
         const float vx = x - ((R0.w + sh.x) - ref.x), vy = y - ((R1.w + sh.y) - ref.y),
