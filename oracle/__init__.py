@@ -141,6 +141,8 @@ class Scene:
             self.keep["obb_part"] = None if op is None or np.asarray(op).size == 0 else _c(op, np.int32)
             self.max_parts = int(np.diff(self.keep["tmpl_part_off"]).max())
             self.keep["part_q"] = _c(batch.part_q, np.float32).reshape(-1, self.max_parts)
+            if len(self.keep["part_q"]) != int(self.keep["cand_tmpl_off"][-1]):
+                raise ValueError("part_q needs one row of max_parts values per candidate")
         else:
             for name in ("tmpl_part_off", "part_param", "obb_part", "part_q"):
                 self.keep[name] = None

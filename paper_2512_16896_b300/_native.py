@@ -249,14 +249,31 @@ class DeviceBatch:
                 self.t[name] = self.t[name].to(device) if not pinned_host else self.t[name].pin_memory()
         if "obj_anchor" not in self.t:  # no MIDDLE object: neither anchor array
             self.t.pop("obj_anchor_off", None)
+        # CSR consistency of the optional arrays (the library reads them on the
+        # device, where it cannot check their lengths)
+        n_t_ = len(batch.tmpl_obj_off) - 1
+        tro, tri = getattr(batch, "tmpl_tri_off", None), getattr(batch, "tri", None)
+        if tri is not None and np.asarray(tri).size and (
+                tro is None or len(tro) != n_t_ + 1 or int(tro[-1]) != np.asarray(tri).reshape(-1, 12).shape[0]):
+            raise ValueError("tmpl_tri_off must have n_templates + 1 entries ending at the triangle count")
+        po, pp = getattr(batch, "tmpl_part_off", None), getattr(batch, "part_param", None)
+        if pp is not None and np.asarray(pp).size:
+            if po is None or len(po) != n_t_ + 1 or int(po[-1]) != np.asarray(pp).reshape(-1, 12).shape[0]:
+                raise ValueError("tmpl_part_off must have n_templates + 1 entries ending at the part count")
+            ob = getattr(batch, "obb_part", None)
+            if ob is not None and np.asarray(ob).size and len(ob) != len(batch.obb):
+                raise ValueError("obb_part needs one entry per world box")
         # articulated parts: their per-candidate joint values live next to the batch
         part_off = getattr(batch, "tmpl_part_off", None)
         n_parts_t = np.diff(part_off) if part_off is not None and len(part_off) > 1 else np.zeros(1, np.int64)
         self.max_parts = int(n_parts_t.max()) if "part_param" in self.t else 0
         if self.max_parts > 0:  # the batch's joint values, or zeros for sample_parts to fill
             q0 = getattr(batch, "part_q", None)
+            n_q = int(batch.cand_tmpl_off[-1]) * self.max_parts
             q = (torch.from_numpy(np.ascontiguousarray(q0, np.float32)).reshape(-1) if q0 is not None else
-                 torch.zeros(int(batch.cand_tmpl_off[-1]) * self.max_parts, dtype=torch.float32))
+                 torch.zeros(n_q, dtype=torch.float32))
+            if q.numel() != n_q:  # the library reads part_q[c * max_parts + j] for every candidate
+                raise ValueError(f"part_q has {q.numel()} values, the batch needs n_cand x max_parts = {n_q}")
             self.t["part_q"] = q.to(device) if not pinned_host else q.pin_memory()
         else:
             for name in ("tmpl_part_off", "part_param", "obb_part"):

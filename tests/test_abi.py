@@ -67,3 +67,35 @@ def test_order_by_work_is_lpt():
     work = 0.5 * (S * S - sq)
     w = work[t_of[order]]
     assert np.all(np.diff(w) <= 0)
+
+
+def test_device_batch_checks_joint_value_shape():
+    """The binding refuses joint values that do not cover every candidate's
+    part slots (the library would read past them); no GPU needed: the check
+    runs before any copy."""
+    import numpy as np
+    import pytest
+    import synth
+    from paper_2512_16896_b300 import _native
+    b = synth.cabinet(seed=1, n_templates=2, cand_per_template=3)
+    b.part_q = np.zeros((b.n_cand - 1, b.part_q.shape[1]), np.float32)
+    with pytest.raises(ValueError):
+        _native.DeviceBatch(b, device="cpu")
+
+
+def test_device_batch_checks_mesh_and_part_offsets():
+    """Triangle and part offsets must end at their array's length, obb_part
+    must cover every box (checked in the binding before any copy)."""
+    import numpy as np
+    import pytest
+    import synth
+    from paper_2512_16896_b300 import _native
+    m = synth.meshes(seed=1, n_templates=2, cand_per_template=2)
+    m.tmpl_tri_off = m.tmpl_tri_off.copy()
+    m.tmpl_tri_off[-1] += 1
+    with pytest.raises(ValueError):
+        _native.DeviceBatch(m, device="cpu")
+    c = synth.cabinet(seed=1, n_templates=2, cand_per_template=2)
+    c.obb_part = c.obb_part[:-1]
+    with pytest.raises(ValueError):
+        _native.DeviceBatch(c, device="cpu")
