@@ -339,11 +339,26 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     __syncwarp();
   }
   a_bound = -warp_min(-a_bound);
-  // boxes of articulated parts: the candidate's shifts q * axis, one per box,
-  // staged in the A area (unused until the sweep) so the box loop reads them
-  // from shared memory instead of a chain of dependent global loads
+  // world boxes in the A area (unused until the sweep; relation-enabled
+  // instances): the template's box rows with each part box's centre moved by
+  // the candidate's q * axis when they fit (4 rows per box), else the shifts
+  // alone, so the box loop reads shared memory instead of global loads (and
+  // no chain of dependent loads for a part box)
   const bool shifted = EXT && b.max_parts > 0 && b.obb_part != nullptr;
-  if (shifted) {
+  const bool staged = EXT && nobb > 0 && 4 * nobb <= 32 * APL + 64;
+  if (staged) {
+#pragma unroll 1
+    for (int e = lane; e < 4 * nobb; e += 32) {
+      const int bi = e >> 2, row = e & 3;
+      float4 v = __ldg(g.obb_tab + 4 * (bx0 + bi) + row);
+      if (shifted && row < 3) {
+        const float3 sh = box_shift(b, t, c, bx0 + bi, g.status);
+        v.w = v.w + (row == 0 ? sh.x : row == 1 ? sh.y : sh.z);
+      }
+      W.astage[e] = v;
+    }
+    __syncwarp();
+  } else if (shifted) {
 #pragma unroll 1
     for (int bi = lane; bi < nobb; bi += 32) {
       const float3 sh = box_shift(b, t, c, bx0 + bi, g.status);
@@ -374,10 +389,17 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
       r2 = fmaxf(r2, c2);
 #pragma unroll 1
       for (int bi = 0; bi < nobb; ++bi) {
-        const float4* o = g.obb_tab + 4 * (bx0 + bi);
-        const float4 R0 = __ldg(o), R1 = __ldg(o + 1), R2 = __ldg(o + 2), Hh = __ldg(o + 3);
+        float4 R0, R1, R2, Hh;
         // an articulated part's box moves with the candidate's joint value
-        const float4 sh = shifted ? W.astage[bi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (staged) {  // rows with the moved centres
+          const float4* o = W.astage + 4 * bi;
+          R0 = o[0]; R1 = o[1]; R2 = o[2]; Hh = o[3];
+        } else {
+          const float4* o = g.obb_tab + 4 * (bx0 + bi);
+          R0 = __ldg(o); R1 = __ldg(o + 1); R2 = __ldg(o + 2); Hh = __ldg(o + 3);
+          if (shifted) sh = W.astage[bi];
+        }
         // box frame: p = R^T (c - centre); rows of R^T are the columns of R,
         // stored as the table's rows
         const float vx = x - ((R0.w + sh.x) - ref.x), vy = y - ((R1.w + sh.y) - ref.y),
