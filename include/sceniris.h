@@ -491,8 +491,11 @@ typedef struct {
  * listed candidates. Objects are placed in template order. For object k each
  * candidate still alive tries r = 0..max_retries: sample object k's pose with
  * try index r (exactly sc_sample_poses for that object), then check object k
- * against objects 0..k-1 and the world boxes (the decision of sc_collide with
+ * against objects 0..k-1, the world boxes (part boxes at the candidate's
+ * joint values) and the world triangles (the decision of sc_collide with
  * first_new_obj = k; only the scenes that retry are re-checked, Sec. IV-D).
+ * Joint values are read from batch->part_q, written before the call (for
+ * example by sc_sample_parts).
  * The first try whose proposal is accepted and collision-free fixes the
  * pose; a candidate that exhausts its tries is invalid (Sec. V-A) and its
  * later objects are not placed.
