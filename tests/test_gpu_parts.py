@@ -143,3 +143,37 @@ def test_part_count_limit_refused(sc, ctx):
     with pytest.raises(sc.SceniError):
         sc.sample_poses(ctx, sc.DeviceBatch(b), seed=1)
     ctx.synchronize()
+
+
+def test_random_parts_rotated_boxes_match_oracle(sc, ctx):
+    """Parts with random unit axes (vertical components included), yawed
+    inside supports and rotated boxes owned by them, random joint values per
+    candidate: INSIDE sampling and whole-scene collision against the oracle."""
+    rng = np.random.default_rng(12)
+    n_cand, n_parts = 400, 3
+    parts = []
+    for j in range(n_parts):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        parts.append([*ax, -0.2, 0.3, rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), rng.uniform(0.0, 0.4),
+                      rng.uniform(0.1, 0.3), rng.uniform(0.1, 0.3), rng.uniform(-np.pi, np.pi), 0.0])
+    boxes = synth.random_obbs(rng, 6)
+    obb_part = [0, 1, 2, 0, -1, 2]
+    objects = [[(0.0, 0.0, 0.0, 0.05), (0.04, 0.0, 0.02, 0.03)] for _ in range(5)]
+    rel = [0, synth.REL_INSIDE | (0 << 8), synth.REL_INSIDE | (1 << 8), synth.REL_INSIDE | (2 << 8),
+           synth.REL_ON_TOP | (1 << 8)]
+    relp = [[0.05, 0.2, 0.0, 0.0], [0, 0, 0.5, 0], [0, 0, 1.0, 0], [0, 0, 0.0, 0], [0.05, 0.2, 0.0, 0.0]]
+    q = rng.uniform(-0.2, 0.3, (n_cand, n_parts)).astype(np.float32)
+    b = tiny_batch(objects, obbs=boxes, n_cand=n_cand, rel=rel, relp=relp, parts=parts, obb_part=obb_part, part_q=q)
+    db = sc.DeviceBatch(b)
+    gp, gok, gband = sc.sample_poses(ctx, db, seed=21)
+    ctx.synchronize()
+    op, ook, oband = oracle.sample_poses(b, seed=21)
+    band, d = check_samples(gp, gok, gband, op, ook, oband)
+    assert d[pose_rows(b, np.nonzero(~band)[0])].max() <= TOL_POSE
+    poses = op.astype(np.float32)
+    gcol, gmd, gcb = sc.collide(ctx, db, torch.from_numpy(poses).cuda())
+    ctx.synchronize()
+    ocol, omd, ocb = oracle.collide(b, poses)
+    check_collide(gcol, gmd, gcb, ocol, omd, ocb)
+    assert 0.05 < ocol.mean() < 1.0
