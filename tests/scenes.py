@@ -28,3 +28,22 @@ def tiny_batch(objects, poly=((-1, -1), (1, -1), (1, 1), (-1, 1)), obbs=(), n_ca
         parts["part_q"] = (np.zeros((n_cand, len(parts["parts"])), np.float32) if part_q is None
                            else np.array(part_q, np.float32).reshape(n_cand, -1))
     return synth._pack([parts])
+
+
+def cabinet_with_meshes(seed=11, n_templates=16, cand_per_template=8):
+    """Cabinet templates (parts, INSIDE objects, part boxes) with a sphere
+    mesh and a box mesh on the counter: every world feature in one batch."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_templates):
+        p = synth.cabinet_template(rng, int(rng.integers(3, 7)), int(rng.integers(2, 4)), 1, 12)
+        c1 = [rng.uniform(-0.25, 0.25), rng.uniform(-0.7, 0.7), 0.9 + rng.uniform(0.05, 0.2)]
+        c2 = [rng.uniform(-0.25, 0.25), rng.uniform(-0.7, 0.7), 0.95]
+        p["tri"] = np.concatenate([synth.sphere_mesh(c1, rng.uniform(0.05, 0.12)),
+                                   synth.box_mesh(c2, np.eye(3), rng.uniform(0.03, 0.1, 3))]).astype(np.float32)
+        p["ncand"] = cand_per_template
+        nd = len(p["parts"])
+        p["part_q"] = (p["parts"][:, 3] + (p["parts"][:, 4] - p["parts"][:, 3]) *
+                       rng.uniform(size=(cand_per_template, nd))).astype(np.float32)
+        parts.append(p)
+    return synth._pack(parts, name="cabinet+meshes")

@@ -11,6 +11,7 @@ import torch
 
 import oracle
 import synth
+from scenes import cabinet_with_meshes
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,7 @@ def compare(b, gp, gv, gb, gt, op, ov, ob, ot, cands, max_band=0.02):
     (lambda: synth.cabinet(seed=8, n_templates=24, cand_per_template=8), 6, 10),
     (lambda: synth.meshes(seed=9, n_templates=24, cand_per_template=8), 7, 10),
     (lambda: synth.meshes(seed=10, n_templates=30, cand_per_template=6, box_range=(0, 3), ball_range=(0, 2)), 8, 10),
+    (lambda: cabinet_with_meshes(), 9, 10),
 ])
 def test_generate_matches_oracle(sc, ctx, make, seed, retries):
     b = make()
