@@ -110,6 +110,31 @@ def test_generate_full_ragged_sampled(sc, ctx):
     assert gv.sum().item() > 0
 
 
+@pytest.mark.parametrize("make,seed", [(lambda: synth.cabinet(seed=6, n_templates=4096), 6),
+                                       (lambda: synth.meshes(seed=7, n_templates=4096), 7)])
+def test_generate_full_cabinet_and_meshes_sampled(sc, ctx, make, seed):
+    """The benchmark's articulated and world-mesh batches (4096 templates x 64
+    candidates), graph replay: sc_sample_parts's joint values checked against
+    the oracle's own draw, then scenes generated on both sides from the
+    oracle's values; 96 random candidates compared."""
+    b = make()
+    db = sc.DeviceBatch(b)
+    if db.max_parts:  # the benchmark's per-step joint values, checked against the oracle's draw first
+        q = sc.sample_parts(ctx, db, seed=seed).cpu().numpy()
+        oq = oracle.sample_parts(b, seed=seed)
+        live = oq != 0
+        assert np.max(np.abs(q[live] - oq[live])) <= 1e-7
+        b.part_q = oq.astype(np.float32)  # the oracle's own values (FP64 rounded to FP32)
+        db = sc.DeviceBatch(b)
+    order = torch.from_numpy(sc.order_by_work(b)).cuda()
+    gp, gv, gb, gt = sc.generate(ctx, db, seed=seed, order=order)
+    ctx.synchronize()
+    pick = np.sort(np.random.default_rng(4).choice(b.n_cand, 96, replace=False)).astype(np.int32)
+    op, ov, ob, ot = oracle.generate(b, seed=seed, active=pick)
+    compare(b, gp, gv, gb, gt, op, ov, ob, ot, pick, max_band=0.05)
+    assert gv.sum().item() > 0
+
+
 def test_graph_replay_equals_eager_and_takes_new_seeds(sc, ctx):
     """use_graph=1 captures once and replays; a new seed (read from device
     memory by the kernels) changes the result exactly as an eager run does."""
