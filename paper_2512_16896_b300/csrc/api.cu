@@ -412,8 +412,9 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     }
     a.reach_objects = want_reach ? ctx->reach_extent : 0;
     a.max_sph_obj = ctx->max_sph_obj;
-    // parts move boxes and carry INSIDE supports; triangles are checked there too
-    a.ext_rel = ctx->ext_rel || batch->n_parts > 0 || batch->n_tri > 0;
+    // instances: 2 with parts (boxes moved, INSIDE supports) or triangles,
+    // 1 with the full relation set, 0 with free / on-top / next-to only
+    a.ext_rel = (batch->n_parts > 0 || batch->n_tri > 0) ? 2 : ctx->ext_rel ? 1 : 0;
   }
   if (a.reach_objects > 0) {  // side streams and events of the rounds
     const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;

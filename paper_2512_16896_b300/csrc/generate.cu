@@ -258,10 +258,13 @@ __device__ __forceinline__ float world_tri_min(const sc_scene_batch& b, const fl
 // sphere pair within the band. Sphere-level cull (exact, same argument): a B
 // sphere farther than band + margin from every kept object's ball, or an A
 // sphere that far from object k's ball, has no pair within the band.
-template <int APL, bool PREFETCHED, bool EXT>
+// MODE 0: free / on-top / next-to objects only; 1: the full relation set;
+// 2: the full relation set with articulated parts and world triangles.
+template <int APL, bool PREFETCHED, int MODE>
 __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& T, const WarpState& W, int t, int c, int k,
                                           int retry, int rel, int Sprev, int Sk, int64_t pbase, uint64_t seed,
                                           const float4* ref_poses, int lane, TryCounters& cnt) {
+  constexpr bool EXT = MODE >= 1, WORLD = MODE == 2;
   const sc_scene_batch& b = g.b;
   const int o0 = T.o0, s0 = T.s0, nobb = T.nobb, bx0 = T.bx0;
   // ---- sample object k
@@ -339,13 +342,13 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     __syncwarp();
   }
   a_bound = -warp_min(-a_bound);
-  // world boxes in the A area (unused until the sweep; relation-enabled
-  // instances): the template's box rows with each part box's centre moved by
+  // world boxes in the A area (unused until the sweep; instances with
+  // parts and triangles): the template's box rows with each part box's centre moved by
   // the candidate's q * axis when they fit (4 rows per box), else the shifts
   // alone, so the box loop reads shared memory instead of global loads (and
   // no chain of dependent loads for a part box)
-  const bool shifted = EXT && b.max_parts > 0 && b.obb_part != nullptr;
-  const bool staged = EXT && nobb > 0 && 4 * nobb <= 32 * APL + 64;
+  const bool shifted = WORLD && b.max_parts > 0 && b.obb_part != nullptr;
+  const bool staged = WORLD && nobb > 0 && 4 * nobb <= 32 * APL + 64;
   if (staged) {
 #pragma unroll 1
     for (int e = lane; e < 4 * nobb; e += 32) {
@@ -440,8 +443,8 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
     cnt.exh += (unsigned long long)Sprev * (unsigned long long)Sk;
     cnt.cull += (unsigned long long)Sk * (unsigned long long)nkeep;
   }
-  // ---- object k against the world triangles (relation-enabled instances)
-  if (EXT && b.n_tri > 0 && !__any_sync(0xFFFFFFFFu, m < -kBand))
+  // ---- object k against the world triangles (instances with world features)
+  if (WORLD && b.n_tri > 0 && !__any_sync(0xFFFFFFFFu, m < -kBand))
     m = fminf(m, world_tri_min(b, g.tri_chunk, t, pk, ref, rk, skn, kcs, s0 + Sprev, Sk, lane, cnt.tri, cnt.cull));
   m = warp_min(m);
   bool alive = !(m < -kBand);
@@ -580,7 +583,7 @@ __device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCoun
 // distribution: warp w takes item w first, then items claimed from the
 // round's counter (the claim for the next item is issued before the current
 // one is processed); routed candidates are appended 32 at a time.
-template <int APL, bool EXT>
+template <int APL, int MODE>
 __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
       for (int j = lane; j <= k + 1; j += 32) cp_async4(W.off + j, b.obj_sph_off + o0 + j);
       cp_async_commit();
       const TryOut res =
-          gen_try<APL, true, EXT>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
+          gen_try<APL, true, MODE>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
       bool done = false;
       if (res.pass && g.list_reach && (rel & SC_REL_REACH)) {
         route = kRouteReach;
@@ -686,7 +689,7 @@ struct ChainArgs {
   unsigned int* counter;
 };
 
-template <int APL, bool EXT>
+template <int APL, int MODE>
 __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainArgs ca) {
   extern __shared__ __align__(16) unsigned char smem[];
   const sc_scene_batch& b = g.b;
@@ -744,7 +747,7 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
 #pragma unroll 1
         for (int r = 0; r <= g.max_retries && !placed; ++r) {
           const TryOut res =
-              gen_try<APL, false, EXT>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
+              gen_try<APL, false, MODE>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, W.opose, lane, cnt);
           ++ntries;
           band = band || res.band;
           placed = res.pass;
@@ -1097,12 +1100,12 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   if (blockIdx.x == 0 && threadIdx.x < 8 && stats) stats[threadIdx.x] = 0;
 }
 
-template <int APL, bool EXT>
+template <int APL, int MODE>
 cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int num_sms, int* grid) {
-  auto kern = gen_round_kernel<APL, EXT>;
+  auto kern = gen_round_kernel<APL, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gen_chain_kernel<APL, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(gen_chain_kernel<APL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -1113,16 +1116,18 @@ cudaError_t prepare_step_kernel(size_t smem, int threads, int ctas_per_sm, int n
 }
 
 template <int APL>
-void launch_round(const GenStepArgs& g, bool ext, int grid, int threads, size_t smem, cudaStream_t s) {
-  if (ext) gen_round_kernel<APL, true><<<grid, threads, smem, s>>>(g);
-  else gen_round_kernel<APL, false><<<grid, threads, smem, s>>>(g);
+void launch_round(const GenStepArgs& g, int mode, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (mode == 2) gen_round_kernel<APL, 2><<<grid, threads, smem, s>>>(g);
+  else if (mode == 1) gen_round_kernel<APL, 1><<<grid, threads, smem, s>>>(g);
+  else gen_round_kernel<APL, 0><<<grid, threads, smem, s>>>(g);
 }
 
 template <int APL>
-void launch_chain(const GenStepArgs& g, const ChainArgs& ca, bool ext, int grid, int threads, size_t smem,
+void launch_chain(const GenStepArgs& g, const ChainArgs& ca, int mode, int grid, int threads, size_t smem,
                   cudaStream_t s) {
-  if (ext) gen_chain_kernel<APL, true><<<grid, threads, smem, s>>>(g, ca);
-  else gen_chain_kernel<APL, false><<<grid, threads, smem, s>>>(g, ca);
+  if (mode == 2) gen_chain_kernel<APL, 2><<<grid, threads, smem, s>>>(g, ca);
+  else if (mode == 1) gen_chain_kernel<APL, 1><<<grid, threads, smem, s>>>(g, ca);
+  else gen_chain_kernel<APL, 0><<<grid, threads, smem, s>>>(g, ca);
 }
 
 }  // namespace
@@ -1235,16 +1240,19 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   cudaError_t e;
   switch (cfg.a_per_lane) {
     case 1:
-      e = a.ext_rel ? prepare_step_kernel<1, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
-                    : prepare_step_kernel<1, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      e = a.ext_rel == 2   ? prepare_step_kernel<1, 2>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+          : a.ext_rel == 1 ? prepare_step_kernel<1, 1>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                           : prepare_step_kernel<1, 0>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
       break;
     case 2:
-      e = a.ext_rel ? prepare_step_kernel<2, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
-                    : prepare_step_kernel<2, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      e = a.ext_rel == 2   ? prepare_step_kernel<2, 2>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+          : a.ext_rel == 1 ? prepare_step_kernel<2, 1>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                           : prepare_step_kernel<2, 0>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
       break;
     default:
-      e = a.ext_rel ? prepare_step_kernel<4, true>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
-                    : prepare_step_kernel<4, false>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
+      e = a.ext_rel == 2   ? prepare_step_kernel<4, 2>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+          : a.ext_rel == 1 ? prepare_step_kernel<4, 1>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid)
+                           : prepare_step_kernel<4, 0>(smem, cfg.threads, cfg.ctas_per_sm, num_sms, &grid);
       break;
   }
   if (e != cudaSuccess) return e;

@@ -86,7 +86,8 @@ struct GenerateLaunch {
   int map_tau;
   int reach_objects;     // object indices < reach_objects may carry the reach flag
   int max_sph_obj;       // most spheres of one object in the batch (batch_scan)
-  int ext_rel;           // some object uses DIRECTIONAL / MIDDLE / LOCAL / FACE_TO (batch_scan)
+  int ext_rel;           // generation instance: 0 basic relations, 1 DIRECTIONAL / MIDDLE / LOCAL /
+                         // FACE_TO in use (batch_scan), 2 also parts or world triangles
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
   StageTimer* timer;     // NULL: no timing
   // rounds of the objects with reachability: two side streams for the reach
