@@ -330,10 +330,16 @@ typedef struct {
  * target_ids uint32 [n] Philox counter word of each target, or NULL (= index).
  * reachable  u8 [n]; q_out float [n][7]; err float [n][2] = (position error,
  *            rotation angle) of the returned configuration.
+ * band       u8 [n] or NULL: 1 when a success check of some seed, at any
+ *            check up to the one that ended the target, could flip under a
+ *            perturbation of 1e-5 (both errors at most 1e-5 above their
+ *            tolerances and one within 1e-5 of its tolerance). FP32 and FP64
+ *            solvers can decide such targets differently.
  * Errors: SC_ERR_INVALID (NULL pointers, seeds outside 1..32, iters < 0,
  * non-positive tolerances or tol_rot >= pi/2). */
 sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params, const float* targets,
-                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err);
+                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err,
+                      uint8_t* band);
 
 /* One damped-least-squares step (the update of sc_ik_reach, including the
  * clamp) for n independent (target, configuration) pairs: q_out[i] = step of
@@ -507,8 +513,9 @@ typedef struct {
  * poses   float [P][4] CSR pose layout; objects never placed are NaN.
  * valid   u8 [n_cand]: 1 when every object was placed.
  * band    u8 [n_cand]: 1 when any decision on the candidate's path (a support
- *         test of an attempt that fixed an outcome, or a minimum distance)
- *         lay within 1e-5 m of its threshold.
+ *         test of an attempt that fixed an outcome, a minimum distance, or
+ *         an IK success check as sc_ik_reach's band) lay within 1e-5 of its
+ *         threshold.
  * tries   int32 [n_cand]: tries spent over all objects.
  * reach   optional reachability stage (NULL: none).
  * q_reach float [P][7] (may be NULL): for every reach-checked object that was

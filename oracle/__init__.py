@@ -90,7 +90,7 @@ def _declare(L):
     L.or_dls_step.argtypes = [P, ctypes.c_double, P, P, P]
     L.or_ik_error.argtypes = [P, P, P, P, P]
     L.or_ik_seed.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, P]
-    L.or_ik_reach.argtypes = [P, P, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int]
+    L.or_ik_reach.argtypes = [P, P, P, P, ctypes.c_int, P, P, P, P, P, ctypes.c_int]
     L.or_grasp_target.argtypes = [P, ctypes.c_double, P, P]
     L.or_generate.argtypes = [P, P, P, P, P, ctypes.c_int, P, P, P, P, ctypes.c_int]
     L.or_sample_parts.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int, P]
@@ -306,15 +306,17 @@ def ik_seed(arm, seed, target, s):
     return q
 
 
-def ik_reach(arm, params, targets, target_ids=None, threads=None):
-    """Returns (reach [n] u8, q [n,7], err [n,2], iters [n])."""
+def ik_reach(arm, params, targets, target_ids=None, threads=None, with_band=False):
+    """Returns (reach [n] u8, q [n,7], err [n,2], iters [n]), plus band [n] u8
+    (a success check of some seed within 1e-5 of a tolerance) if with_band."""
     t = _c(targets, np.float32).reshape(-1, 12)
     n = len(t)
     ids = None if target_ids is None else _c(target_ids, np.uint32)
     reach = np.zeros(n, np.uint8); q = np.zeros((n, 7)); err = np.zeros((n, 2)); it = np.zeros(n, np.int32)
+    band = np.zeros(n, np.uint8)
     lib().or_ik_reach(ctypes.byref(arm), ctypes.byref(params), _ptr(t), _ptr(ids), n, _ptr(reach), _ptr(q), _ptr(err),
-                      _ptr(it), threads or default_threads())
-    return reach, q, err, it
+                      _ptr(it), _ptr(band), threads or default_threads())
+    return (reach, q, err, it, band) if with_band else (reach, q, err, it)
 
 
 def grasp_target(pose, hz, base):

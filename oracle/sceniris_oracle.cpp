@@ -41,8 +41,9 @@ extern "C" {
 // and the 64-bit word widths so that the 64-bit instance can be checked against
 // numpy.random.Philox (a library implementation of Philox4x64-10): the round
 // structure, the S-box permutation and the key schedule are shared code.
-// Pinned by: 4x64 instance == numpy.random.Philox outputs; 4x32 instance by
-// uniformity / independence statistics (no third-party 4x32 vector is used).
+// Pinned by: 4x64 instance == numpy.random.Philox outputs; 4x32 instance ==
+// the published Philox4x32-10 known-answer vectors (tests/golden), plus
+// uniformity / independence statistics.
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
@@ -655,9 +656,16 @@ extern "C" {
 //   All seeds of a target iterate in lock step; the target is reachable at the
 //   first check where any seed succeeds and returns the lowest such seed index;
 //   otherwise it returns the seed with the smallest position error at the end.
+//   Band: a check of some seed whose position error or angle lies within
+//   1e-5 of its tolerance (the other not failing by more than 1e-5) could
+//   flip under FP32 rounding; the target is then flagged.
 // Pinned by: FK at q = 0 against a hand-multiplied DH chain, Jacobian against
-// central differences, the push-through identity of the damped inverse, and
-// the reach bound (targets beyond sum |d_i| + |a_i| never succeed).
+// central differences, the push-through identity of the damped inverse, the
+// reach bound (targets beyond sum |d_i| + |a_i| never succeed), the seed
+// draw against an independent Philox4x32-10 checked on its known answers,
+// and the selection rule at zero iterations (the lowest seed whose own FK,
+// from scipy, is the target wins; else the seed of least scipy-FK position
+// error); the band flag by targets placed at tol_pos +- 5e-6 and +- 2e-5.
 // ---------------------------------------------------------------------------
 typedef struct {
   float dh_d[7], dh_a[7], dh_alpha[7], qmin[7], qmax[7];
@@ -815,11 +823,23 @@ void or_ik_seed(const or_arm* arm, uint64_t seed, uint32_t target, uint32_t s, d
   ik_seed_words(arm, seed, target, 0u, s, q);
 }
 
+// Is one seed's success decision at one check within the band? The decision
+// is (position error <= tol_pos) and (angle <= tol_rot); it could flip under
+// a perturbation of BAND when one error lies within BAND of its tolerance
+// while the other does not fail by more than BAND.
+static bool ik_check_banded(double pe, double re, const or_ik_params* P) {
+  const double tp = P->tol_pos, tr = P->tol_rot;
+  return (std::fabs(pe - tp) <= BAND && re <= tr + BAND) || (std::fabs(re - tr) <= BAND && pe <= tp + BAND);
+}
+
 // IK for one target (12 floats: R row-major, p). Returns reachable; q_out[7],
 // err[2] = (position error, rotation angle) of the returned configuration,
-// *iter_out = the check index at which it ended.
+// *iter_out = the check index at which it ended, *band_out = 1 if any check
+// of any seed up to that one was within the band (ik_check_banded): every
+// such check took part in deciding the outcome, since the seeds move in lock
+// step and the first success ends all of them.
 static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target, uint32_t tid, uint32_t tid_hi,
-                  double* q_out, double* err, int* iter_out) {
+                  double* q_out, double* err, int* iter_out, int* band_out) {
   double Rt[9], pt[3];
   for (int i = 0; i < 9; ++i) Rt[i] = target[i];
   for (int i = 0; i < 3; ++i) pt[i] = target[9 + i];
@@ -827,10 +847,12 @@ static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target,
   std::vector<double> q(7 * S);
   for (int s = 0; s < S; ++s) ik_seed_words(arm, P->seed, tid, tid_hi, (uint32_t)s, &q[7 * s]);
   std::vector<double> pe(S), re(S);
+  int banded = 0;
   for (int it = 0; it <= P->iters; ++it) {
     int hit = -1;
     for (int s = 0; s < S; ++s) {
       or_pose_error(arm, &q[7 * s], Rt, pt, &pe[s], &re[s]);
+      if (ik_check_banded(pe[s], re[s], P)) banded = 1;
       if (hit < 0 && pe[s] <= (double)P->tol_pos && re[s] <= (double)P->tol_rot) hit = s;
     }
     if (hit >= 0) {
@@ -838,6 +860,7 @@ static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target,
       err[0] = pe[hit];
       err[1] = re[hit];
       *iter_out = it;
+      *band_out = banded;
       return 1;
     }
     if (it == P->iters) break;
@@ -850,17 +873,20 @@ static int ik_one(const or_arm* arm, const or_ik_params* P, const float* target,
   err[0] = pe[best];
   err[1] = re[best];
   *iter_out = P->iters;
+  *band_out = banded;
   return 0;
 }
 
-// target_ids: Philox counter index of each target (NULL: 0..n-1).
+// target_ids: Philox counter index of each target (NULL: 0..n-1). band
+// (optional) receives ik_one's band flag of each target.
 int or_ik_reach(const or_arm* arm, const or_ik_params* P, const float* targets, const uint32_t* target_ids, int n,
-                uint8_t* reach, double* q_out, double* err, int32_t* iters, int nthreads) {
+                uint8_t* reach, double* q_out, double* err, int32_t* iters, uint8_t* band, int nthreads) {
   parallel_for(n, nthreads, [&](int i) {
-    int it;
+    int it, b;
     reach[i] = (uint8_t)ik_one(arm, P, targets + 12 * i, target_ids ? target_ids[i] : (uint32_t)i, 0u, q_out + 7 * i,
-                               err + 2 * i, &it);
+                               err + 2 * i, &it, &b);
     if (iters) iters[i] = it;
+    if (band) band[i] = (uint8_t)b;
   });
   return 0;
 }
@@ -890,8 +916,14 @@ void or_grasp_target(const double* pose, double Hz, const float* base, double* o
 // and an arm is given) solve IK for its top-down grasp. The first try that
 // passes every check fixes the pose; if none does the scene is invalid and its
 // remaining objects are not placed.
-// band[c] = some decision on the candidate's path was within 1e-5 m.
+// band[c] = some decision on the candidate's path was within 1e-5 m (a
+// support test, a collision minimum or an IK success check).
 // tries[c] = total tries spent.
+// Pinned by: valid scenes re-checked collision-free, zero retries equal to a
+// whole-scene check, and for the reachability branch: tolerances every seed
+// meets at once give the scenes of the run without an arm; a base from which
+// every grasp lies beyond the arm's reach spends all max_retries + 1 tries on
+// the first designated object and places nothing after it.
 // ---------------------------------------------------------------------------
 typedef struct {
   uint64_t seed;
@@ -927,9 +959,11 @@ int or_generate(const or_scene* s, const or_gen_params* G, const or_arm* arm, co
           float tf[12];
           for (int q = 0; q < 12; ++q) tf[q] = (float)tgt[q];
           double qo[7], e2[2];
-          int it;
+          int it, ikb;
           // IK seeds of this try: counter (candidate, seed, block, object << 16 | try)
-          if (!ik_one(arm, ikp, tf, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, qo, e2, &it)) continue;
+          const int reach_ok = ik_one(arm, ikp, tf, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, qo, e2, &it, &ikb);
+          any_band = any_band || ikb;
+          if (!reach_ok) continue;
         }
         placed = true;
       }

@@ -122,7 +122,7 @@ SIGNATURES = {
     "sc_order_by_work": (ctypes.c_int, [I32, P, P, P, P]),
     "sc_generate": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.POINTER(ScGenParams), P, I32,
                                    ctypes.POINTER(CollideConfig), ctypes.POINTER(ScGenReach), P, P, P, P, P]),
-    "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P]),
+    "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P, P]),
     "sc_ik_dls_step": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.c_float, P, P, I32, P, P]),
     "sc_mlp_param_count": (I32, []),
     "sc_mlp_create": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(P)]),
@@ -404,16 +404,19 @@ def generate(ctx: Context, db: DeviceBatch, seed: int, max_attempts: int = 16, m
     return poses, valid, band, tries
 
 
-def ik_reach(ctx: Context, arm: ScArm, params: ScIkParams, targets: torch.Tensor, target_ids=None):
-    """sc_ik_reach. targets [n,12] f32 (device). Returns (reach u8 [n], q f32 [n,7], err f32 [n,2])."""
+def ik_reach(ctx: Context, arm: ScArm, params: ScIkParams, targets: torch.Tensor, target_ids=None,
+             with_band: bool = False):
+    """sc_ik_reach. targets [n,12] f32 (device). Returns (reach u8 [n], q f32 [n,7], err f32 [n,2]),
+    plus band u8 [n] if with_band."""
     dev = torch.device("cuda", ctx.device)
     n = targets.shape[0]
     reach = torch.empty(n, dtype=torch.uint8, device=dev)
     q = torch.empty((n, 7), dtype=torch.float32, device=dev)
     err = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    band = torch.empty(n, dtype=torch.uint8, device=dev) if with_band else None
     _check(lib().sc_ik_reach(ctx.handle, ctypes.byref(arm), ctypes.byref(params), _ptr(targets), _ptr(target_ids), n,
-                             _ptr(reach), _ptr(q), _ptr(err)))
-    return reach, q, err
+                             _ptr(reach), _ptr(q), _ptr(err), _ptr(band)))
+    return (reach, q, err, band) if with_band else (reach, q, err)
 
 
 def ik_dls_step(ctx: Context, arm: ScArm, lam: float, targets: torch.Tensor, q_in: torch.Tensor):

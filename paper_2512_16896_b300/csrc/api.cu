@@ -525,7 +525,8 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
 }
 
 sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params, const float* targets,
-                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err) {
+                      const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err,
+                      uint8_t* band) {
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;
   if (!arm || !params) return fail(SC_ERR_INVALID, "arm or params is NULL");
@@ -537,8 +538,8 @@ sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params
   if (!(params->tol_pos > 0.f) || !(params->tol_rot > 0.f) || !(params->tol_rot < 1.5707963f) || !(params->lambda >= 0.f))
     return fail(SC_ERR_INVALID, "tolerances must be positive, tol_rot < pi/2, lambda >= 0");
   DeviceGuard g(ctx->device);
-  cudaError_t e = sc::launch_ik(*arm, *params, targets, target_ids, n, reachable, q_out, err, nullptr, ctx->d_counter,
-                                ctx->num_sms, ctx->stream);
+  cudaError_t e = sc::launch_ik(*arm, *params, targets, target_ids, n, reachable, q_out, err, nullptr, band,
+                                ctx->d_counter, ctx->num_sms, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "ik_kernel launch");
   return SC_OK;
 }

@@ -777,7 +777,7 @@ struct ReachArgs {
   const int32_t* cand_t;
   const TmplInfo* tinfo;
   int max_retries, gated;
-  float tol_pos, tol_rot, tau;
+  float tau;
   CandState st;
   const int32_t* list_reach;  // this round's reach queue
   const int* n_reach;
@@ -944,8 +944,7 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
     if (lane == s.winner) {
       const TmplInfo& Tm = A.tinfo[__ldg(&A.cand_t[c])];
       const int64_t pbase = Tm.pose0 + (int64_t)(c - Tm.cand0) * Tm.nt;
-      const float pe = sqrtf(pe2), ang = atan2f(sr, cr);
-      if (fabsf(pe - A.tol_pos) <= kBand || fabsf(ang - A.tol_rot) <= kBand) A.band[c] = 1;
+      if (s.band) A.band[c] = 1;
       if (s.found && A.q_reach) {
 #pragma unroll
         for (int jq = 0; jq < 7; ++jq) A.q_reach[7 * (pbase + k) + jq] = q[jq];
@@ -1301,8 +1300,6 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.map_counts = a.map_counts;
     ra.map_grid = a.map_grid;
     ra.map_tau = a.map_tau;
-    ra.tol_pos = a.ik->tol_pos;
-    ra.tol_rot = a.ik->tol_rot;
     ra.tau = a.tau;
     ra.st = st;
     ra.poses = reinterpret_cast<const float4*>(a.poses);

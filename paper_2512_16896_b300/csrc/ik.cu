@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
       K.err[2 * (size_t)i] = sqrtf(pe2);
       K.err[2 * (size_t)i + 1] = atan2f(s, c);
       if (K.iters_out) K.iters_out[i] = r.it;
+      if (K.band) K.band[i] = r.band;
     }
     i = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
@@ -82,8 +83,8 @@ int ik_resident_blocks(int num_sms) {
 }
 
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
-                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, unsigned int* claim,
-                      int num_sms, cudaStream_t s) {
+                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, uint8_t* band,
+                      unsigned int* claim, int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(claim, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
@@ -96,6 +97,7 @@ cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* tar
   K.q_out = q_out;
   K.err = err;
   K.iters_out = iters_out;
+  K.band = band;
   K.claim = claim;
   const int threads = 128, warps = threads / 32;
   int blocks = (n + warps - 1) / warps;

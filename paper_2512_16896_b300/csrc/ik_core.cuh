@@ -17,6 +17,9 @@ struct ArmK {
 struct IkArgs {
   ArmK arm;
   float lambda2, tol_pos2, cos2_tol, sin2_tol;  // squared cosine / sine of the angle tolerance
+  // band of the success decision: squared position bounds (tol_pos -+ 1e-5)^2
+  // and squared cosine / sine of the angles tol_rot -+ 1e-5 (see check_banded)
+  float pos_lo2, pos_hi2, cos2_lo, sin2_lo, cos2_hi, sin2_hi;
   int iters, seeds;
   uint64_t seed;
   const float* targets;
@@ -26,6 +29,7 @@ struct IkArgs {
   float* q_out;
   float* err;
   int32_t* iters_out;
+  uint8_t* band;        // optional: band flag of each target (Solve::band)
   unsigned int* claim;  // work counter (zeroed before the launch): warps claim targets dynamically
 };
 
@@ -92,6 +96,19 @@ __device__ __forceinline__ bool check(const IkArgs& K, const Target& T, const fl
   // angle <= tol  <=>  s cos(tol) <= c sin(tol)  <=>  c >= 0 and s^2 cos^2(tol) <= c^2 sin^2(tol)
   // (angle in [0, pi], s = |v| >= 0, tol in (0, pi/2))
   return pe2 <= K.tol_pos2 && c >= 0.f && s2 * K.cos2_tol <= c * c * K.sin2_tol;
+}
+
+// Could this success decision flip under a perturbation of 1e-5? It could
+// when both errors are within 1e-5 above their tolerances at most and one of
+// them lies within 1e-5 of its tolerance:
+//   pe <= tol_pos + b  and  angle <= tol_rot + b  and
+//   (pe >= tol_pos - b  or  angle >= tol_rot - b),   b = 1e-5,
+// in squared form as check (angle <= x  <=>  c >= 0 and s^2 cos^2 x <= c^2 sin^2 x).
+__device__ __forceinline__ bool check_banded(const IkArgs& K, float pe2, float s2, float c) {
+  const float c2 = c * c;
+  const bool rot_hi = c >= 0.f && s2 * K.cos2_hi <= c2 * K.sin2_hi;
+  const bool rot_below_lo = c > 0.f && s2 * K.cos2_lo < c2 * K.sin2_lo;
+  return pe2 <= K.pos_hi2 && rot_hi && (pe2 >= K.pos_lo2 || !rot_below_lo);
 }
 
 // One damped-least-squares step of q (in place) towards T, given the forward
@@ -184,6 +201,7 @@ __device__ __forceinline__ Target load_target(const float* tg) {
 
 struct Solve {
   bool found;
+  bool band;   // some seed's check up to the last one was within the band (check_banded)
   int winner;  // lane holding the returned configuration
   int it;      // check index at which the solve ended
 };
@@ -201,24 +219,28 @@ __device__ __forceinline__ Solve warp_solve(const IkArgs& K, const Target& T, ui
 #pragma unroll
     for (int j = 0; j < 7; ++j) q[j] = K.arm.qmin[j] + (K.arm.qmax[j] - K.arm.qmin[j]) * u[j];
   }
-  Solve r{false, -1, 0};
+  Solve r{false, false, -1, 0};
   pe2 = 0.f;
   float s2 = 0.f;
   c = 1.f;
+  bool near = false;
   for (;; ++r.it) {
     float z[7][3], p[7][3], R[9], t[3], v[3];
     fk(K.arm, q, z, p, R, t);
     const bool ok = active && check(K, T, R, t, &pe2, v, &s2, &c);
+    near = near || (active && check_banded(K, pe2, s2, c));
     const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
     if (m) {
       r.winner = __ffs(m) - 1;
       r.found = true;
+      r.band = __any_sync(0xFFFFFFFFu, near);
       s = sqrtf(s2);
       return r;
     }
     if (r.it == K.iters) break;
     if (active) dls_step(K.arm, K.lambda2, T, q, z, p, R, t, v);
   }
+  r.band = __any_sync(0xFFFFFFFFu, near);
   s = sqrtf(s2);
   // smallest position error, lowest index on ties
   float best = active ? pe2 : 3e38f;
@@ -253,6 +275,14 @@ inline void fill_params(IkArgs& K, const sc_arm& arm, const sc_ik_params& P) {
   K.tol_pos2 = P.tol_pos * P.tol_pos;
   K.cos2_tol = (float)(cos((double)P.tol_rot) * cos((double)P.tol_rot));
   K.sin2_tol = (float)(sin((double)P.tol_rot) * sin((double)P.tol_rot));
+  const double b = 1e-5, tp = P.tol_pos, tr = P.tol_rot, half_pi = 1.5707963267948966;
+  K.pos_lo2 = tp > b ? (float)((tp - b) * (tp - b)) : -1.f;  // -1: no position is below the band
+  K.pos_hi2 = (float)((tp + b) * (tp + b));
+  const double lo = tr - b, hi = tr + b;
+  K.cos2_lo = lo > 0.0 ? (float)(cos(lo) * cos(lo)) : 1.f;  // (1, 0): no angle is below the band
+  K.sin2_lo = lo > 0.0 ? (float)(sin(lo) * sin(lo)) : 0.f;
+  K.cos2_hi = hi < half_pi ? (float)(cos(hi) * cos(hi)) : 0.f;  // (0, 1): every angle <= pi/2 passes
+  K.sin2_hi = hi < half_pi ? (float)(sin(hi) * sin(hi)) : 1.f;
   K.iters = P.iters;
   K.seeds = P.seeds;
   K.seed = P.seed;

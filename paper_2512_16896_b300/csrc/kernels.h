@@ -114,8 +114,8 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
 
 // claim: a device work counter, zeroed by the launcher on the stream.
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
-                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, unsigned int* claim,
-                      int num_sms, cudaStream_t s);
+                      int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, uint8_t* band,
+                      unsigned int* claim, int num_sms, cudaStream_t s);
 // Blocks of 128 threads of the IK kernels that fit on the device at once.
 int ik_resident_blocks(int num_sms);
 cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets, const float* q_in, int n,

@@ -1,14 +1,19 @@
 """Generation with the reachability stage (collision, then gate, then exact
 IK), through the C ABI.
 
-IK is an FP32 iteration, so its decisions agree with the FP64 oracle on most
-but not all tries; the checks are: (1) plain generation agrees with the
-oracle's loop on >= 95% of candidates; (2) every scene the GPU emits is
-verified: collision-free in the whole-scene check and, for every designated
-object, the returned IK solution reaches the top-down grasp target in FP64
-forward kinematics; (3) a gate that passes everything reproduces the plain
-run bit for bit, a gate that passes nothing places no designated object;
-(4) a trained gate emits only verified scenes and skips IK on some tries.
+With zero IK iterations the seeds alone decide every reach check, and the
+FP32 and FP64 seeds differ by rounding only: outside the decision band (a
+support test, a collision minimum or an IK success check within 1e-5 of its
+threshold) valid flags and try counts must equal the oracle's exactly. With
+100 iterations the FP32 and FP64 trajectories drift apart, so the checks
+are: (1) the banded fraction is reported and bounded, and the unbanded
+candidates agree with the oracle's loop on a stated fraction; (2) every
+scene the GPU emits is verified: collision-free in the whole-scene check
+and, for every designated object, the returned IK solution reaches the
+top-down grasp target in FP64 forward kinematics; (3) a gate that passes
+everything reproduces the plain run bit for bit, a gate that passes nothing
+places no designated object; (4) a trained gate emits only verified scenes
+and skips IK on some tries.
 """
 import numpy as np
 import pytest
@@ -37,17 +42,17 @@ def ctx(sc):
     c.close()
 
 
-def run(sc, ctx, db, b, seed, gate=None, retries=10, rmap=None):
+def run(sc, ctx, db, b, seed, gate=None, retries=10, rmap=None, ik=None):
     q = torch.full((db.n_poses, 7), float("nan"), device="cuda")
     order = torch.from_numpy(sc.order_by_work(b)).cuda()
     arm = sc.make_arm(*synth.arm_arrays())
     P, V, B, T = sc.generate(ctx, db, seed=seed, max_retries=retries, order=order, arm=arm,
-                             ik=sc.ik_params(seed=seed), gate=gate, q_reach=q, rmap=rmap)
+                             ik=sc.ik_params(seed=seed) if ik is None else ik, gate=gate, q_reach=q, rmap=rmap)
     ctx.synchronize()
     return [x.clone() for x in (P, V, B, T, q)]
 
 
-def verify_emitted(b, P, V, q):
+def verify_emitted(b, P, V, q, tol_pos=5e-3, tol_rot=0.05):
     """Every valid scene: whole-scene collision-free and reach-verified in FP64."""
     P, V, q = P.cpu().numpy().astype(np.float64), V.cpu().numpy(), q.cpu().numpy().astype(np.float64)
     sel = np.nonzero(V)[0].astype(np.int32)
@@ -65,7 +70,7 @@ def verify_emitted(b, P, V, q):
                 row = offs[c] + k
                 tgt = oracle.grasp_target(P[row], float(b.obj_half[o0 + k, 2]), b.tmpl_base[t])
                 pe, re = oracle.pose_error(ARM_O, q[row], tgt)
-                assert pe <= 5e-3 + 1e-5 and re <= 0.05 + 1e-5, (c, k, pe, re)
+                assert pe <= tol_pos + 1e-5 and re <= tol_rot + 1e-5, (c, k, pe, re)
                 assert np.all(np.abs(q[row]) <= 2.8 + 1e-6)
                 checked += 1
     assert checked >= len(sel)
@@ -77,10 +82,48 @@ def test_plain_reach_generation_matches_oracle_and_is_verified(sc, ctx):
     P, V, B, T, q = run(sc, ctx, db, b, seed=5)
     op, ov, ob, ot = oracle.generate(b, seed=5, arm=ARM_O, ikp=oracle.ik_params(seed=5))
     gv = V.cpu().numpy()
-    agree = np.mean(gv == ov)
-    assert agree >= 0.95, agree
+    banded, agree = band_report(V, B, T, ov, ob, ot, "tabletop 100 iterations")
+    assert banded <= 0.08, banded  # measured 0.023
+    assert agree >= 0.985, agree  # measured 0.995
     assert 0.05 < gv.mean() < 0.95
     verify_emitted(b, P, V, q)
+
+
+def band_report(V, B, T, ov, ob, ot, what):
+    """Fraction of candidates either side bands, and the fraction of the others
+    whose valid flag and try count equal the oracle's."""
+    gv, gb, gt = V.cpu().numpy(), B.cpu().numpy().astype(bool), T.cpu().numpy()
+    band = gb | ob.astype(bool)
+    keep = ~band
+    agree = float(np.mean((gv[keep] == ov[keep]) & (gt[keep] == ot[keep]))) if keep.any() else 1.0
+    print(f"{what}: banded {band.mean():.4f} of {len(band)}, unbanded agreement {agree:.4f}")
+    return float(band.mean()), agree
+
+
+ZERO_ITER = dict(tol_pos=0.3, tol_rot=1.2, iters=0, seeds=32)
+
+
+@pytest.mark.parametrize("make,seed", [
+    (lambda: synth.ragged(seed=41, n_templates=24, cand_per_template=16, obj_range=(2, 12)), 11),
+    (lambda: synth.hard(seed=42, n_templates=16, cand_per_template=16, obj_range=(3, 8), n_reach=2), 12),
+])
+def test_reach_decisions_exact_at_zero_iterations(sc, ctx, make, seed):
+    """iters = 0 (the seeds decide), tolerances 0.3 m / 1.2 rad so that about
+    one try in eight reaches: valid flags and try counts equal the oracle's on
+    every candidate neither side bands, and emitted scenes are verified."""
+    b = make()
+    db = sc.DeviceBatch(b)
+    P, V, B, T, q = run(sc, ctx, db, b, seed=seed, ik=sc.ik_params(seed=seed, **ZERO_ITER))
+    op, ov, ob, ot = oracle.generate(b, seed=seed, arm=ARM_O, ikp=oracle.ik_params(seed=seed, **ZERO_ITER))
+    gv, gt = V.cpu().numpy(), T.cpu().numpy()
+    band = B.cpu().numpy().astype(bool) | ob.astype(bool)
+    keep = ~band
+    assert band.mean() <= 0.05, band.mean()
+    assert np.array_equal(gv[keep], ov[keep]), np.nonzero(gv[keep] != ov[keep])
+    assert np.array_equal(gt[keep], ot[keep]), np.nonzero(gt[keep] != ot[keep])
+    assert ov[keep].sum() >= 5 and ov[keep].mean() < 0.98, ov[keep].mean()  # both outcomes occur
+    if gv.sum():
+        verify_emitted(b, P, V, q, tol_pos=0.3, tol_rot=1.2)
 
 
 def test_gate_extremes(sc, ctx):
@@ -127,7 +170,15 @@ def _agree_and_verify(sc, ctx, b, seed, retries=10):
     P, V, B, T, q = run(sc, ctx, db, b, seed=seed, retries=retries)
     op, ov, ob, ot = oracle.generate(b, seed=seed, max_retries=retries, arm=ARM_O, ikp=oracle.ik_params(seed=seed))
     gv = V.cpu().numpy()
-    assert np.mean(gv == ov) >= 0.95, np.mean(gv == ov)
+    banded, agree = band_report(V, B, T, ov, ob, ot, f"ragged seed {seed}, 100 iterations")
+    assert banded <= 0.08, banded  # measured <= 0.016
+    assert agree >= 0.98, agree  # measured 1.0
+    # at zero iterations the same schedule is exact outside the band
+    Z = run(sc, ctx, db, b, seed=seed, retries=retries, ik=sc.ik_params(seed=seed, **ZERO_ITER))
+    _, zv, zb, zt = oracle.generate(b, seed=seed, max_retries=retries, arm=ARM_O,
+                                    ikp=oracle.ik_params(seed=seed, **ZERO_ITER))
+    keep = ~(Z[2].cpu().numpy().astype(bool) | zb.astype(bool))
+    assert np.array_equal(Z[1].cpu().numpy()[keep], zv[keep]) and np.array_equal(Z[3].cpu().numpy()[keep], zt[keep])
     if gv.sum():
         verify_emitted(b, P, V, q)
     return gv

@@ -5,6 +5,7 @@ by someone else (numpy's Philox4x64, scipy's rotations, torch's bfloat16
 conversion, numpy.linalg), an invariance, or brute force on hand-made cases.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -35,6 +36,26 @@ def test_philox4x64_matches_numpy(key, ctr):
             c[1] = (c[1] + 1) % 2**64
         outs += [int(x) for x in oracle.philox4x64(c, key)]
     assert raw == outs
+
+
+def _kat_rows():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows.append([int(x, 16) for x in line])
+    return rows
+
+
+def test_philox4x32_known_answers():
+    """The published Philox4x32-10 known-answer vectors (tests/golden, from the
+    Random123 distribution of Salmon et al., SC'11): they fix the multipliers,
+    the Weyl key increments and the round count that only statistics covered."""
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for r in rows:
+        assert [int(x) for x in oracle.philox4x32(r[0:4], r[4:6])] == r[6:10]
 
 
 def test_philox4x32_statistics():
@@ -469,6 +490,135 @@ def test_ik_reaches_fk_targets_and_never_beyond_reach():
     assert np.all(np.linalg.norm(far[:, 9:], axis=1) > bound)
     reach, _, _, _ = oracle.ik_reach(ARM, P, far)
     assert reach.sum() == 0
+
+
+def _seed_q(seed, target, s, hi=0):
+    """Seed s of a target as the documented draw: q_j = qmin + (qmax - qmin) u_j,
+    u = (w >> 8) 2^-24 of Philox4x32-10 word j % 4 at counter (target, s, j / 4,
+    hi), key = (seed low, seed high); the generator is pinned by its known
+    answers above."""
+    q = np.zeros(7)
+    for b in range(2):
+        w = oracle.philox4x32([target, s, b, hi], [seed & 0xFFFFFFFF, seed >> 32])
+        for j in range(4):
+            if 4 * b + j < 7:
+                q[4 * b + j] = -2.8 + 5.6 * float(np.float32(float(int(w[j]) >> 8) * 2.0**-24))
+    return q
+
+
+def test_ik_seed_draw_matches_its_definition():
+    for seed, target, s in [(3, 0, 0), (3, 17, 31), (2**40 + 5, 123456, 7)]:
+        assert np.allclose(oracle.ik_seed(ARM, seed, target, s), _seed_q(seed, target, s), atol=1e-12)
+
+
+def _target_of(T):
+    return np.concatenate([T[:3, :3].ravel(), T[:3, 3]]).astype(np.float32)
+
+
+def test_ik_selection_at_zero_iterations():
+    """With no step the seeds alone decide. A target made (by scipy's DH chain)
+    from seed s's own configuration is reached by the lowest seed whose
+    scipy-FK pose meets the tolerances (normally s itself), and its q is
+    returned; an unreachable target returns the seed of least scipy-FK
+    position error."""
+    rng = np.random.default_rng(12)
+    P = oracle.ik_params(seeds=8, iters=0, seed=9)
+    n = 24
+    chosen = rng.integers(0, 8, n)
+    seeds = [[_seed_q(9, i, s) for s in range(8)] for i in range(n)]
+    tg = np.array([_target_of(_dh_scipy(seeds[i][chosen[i]])) for i in range(n)])
+    # the last quarter: moved 0.3 m away, so no seed meets 5 mm
+    tg[18:, 9] += 0.3
+    reach, qo, err, it = oracle.ik_reach(ARM, P, tg)
+    assert np.all(it == 0)
+    for i in range(n):
+        pes, res = [], []
+        for s in range(8):
+            T = _dh_scipy(seeds[i][s])
+            pes.append(np.linalg.norm(T[:3, 3] - tg[i, 9:].astype(np.float64)))
+            Rt = tg[i, :9].astype(np.float64).reshape(3, 3)
+            res.append(Rotation.from_matrix(T[:3, :3].T @ Rt).magnitude())
+        ok = [s for s in range(8) if pes[s] <= 5e-3 and res[s] <= 0.05]
+        if i < 18:
+            assert ok and ok[0] <= chosen[i]
+            assert reach[i] == 1 and np.allclose(qo[i], seeds[i][ok[0]], atol=1e-12)
+        else:
+            assert not ok and reach[i] == 0
+            assert np.allclose(qo[i], seeds[i][int(np.argmin(pes))], atol=1e-12)
+            assert err[i, 0] == pytest.approx(min(pes), abs=1e-6)  # float32 DH lengths in the oracle
+    # loose tolerances: several seeds succeed at once; the lowest index wins,
+    # not the most accurate one
+    P2 = oracle.ik_params(seeds=8, iters=0, seed=9, tol_pos=0.7, tol_rot=1.5)
+    reach2, qo2, _, _ = oracle.ik_reach(ARM, P2, tg)
+    informative = 0
+    for i in range(n):
+        pes, oks = [], []
+        for s in range(8):
+            T = _dh_scipy(seeds[i][s])
+            pe = np.linalg.norm(T[:3, 3] - tg[i, 9:].astype(np.float64))
+            re = Rotation.from_matrix(T[:3, :3].T @ tg[i, :9].astype(np.float64).reshape(3, 3)).magnitude()
+            pes.append(pe)
+            if pe <= 0.7 and re <= 1.5:
+                oks.append(s)
+        assert reach2[i] == (len(oks) > 0)
+        if oks:
+            assert np.allclose(qo2[i], seeds[i][oks[0]], atol=1e-12)
+            informative += len(oks) > 1 and oks[int(np.argmin([pes[s] for s in oks]))] != oks[0]
+    assert informative >= 2
+
+
+def test_ik_band_flag_at_the_position_tolerance():
+    """A target whose position lies tol_pos +- 5e-6 from seed 0's tool point
+    (same rotation) is banded; at +- 2e-5 it is not, and the decision follows
+    the side of the tolerance."""
+    P = oracle.ik_params(seeds=4, iters=0, seed=21)
+    rows, expect = [], []
+    for i, (dr, banded) in enumerate([(-5e-6, 1), (5e-6, 1), (-2e-5, 0), (2e-5, 0)]):
+        T = _dh_scipy(_seed_q(21, i, 0))
+        u = np.array([0.6, -0.48, 0.64])
+        tgt = T[:3, 3] + (5e-3 + dr) * u
+        rows.append(np.concatenate([T[:3, :3].ravel(), tgt]).astype(np.float32))
+        expect.append((int(dr < 0), banded))
+    reach, _, err, _, band = oracle.ik_reach(ARM, P, np.array(rows), with_band=True)
+    for i, (r, b) in enumerate(expect):
+        assert (reach[i], band[i]) == (r, b), (i, reach[i], band[i], err[i])
+
+
+def _reach_batch():
+    return synth.ragged(seed=31, n_templates=6, cand_per_template=12, obj_range=(2, 7), n_reach=4)
+
+
+def test_generate_reach_branch_with_tolerances_every_seed_meets():
+    """tol_pos = 10 m, tol_rot = pi: IK succeeds at its first check on every
+    try, so generation with the arm equals generation without it."""
+    b = _reach_batch()
+    ikp = oracle.ik_params(tol_pos=10.0, tol_rot=math.pi, iters=5, seeds=4, seed=2)
+    p0, v0, b0, t0 = oracle.generate(b, seed=4)
+    p1, v1, b1, t1 = oracle.generate(b, seed=4, arm=ARM, ikp=ikp)
+    assert 0 < v0.sum() < len(v0)
+    assert np.array_equal(v0, v1) and np.array_equal(t0, t1)
+    assert np.array_equal(p0, p1, equal_nan=True)
+    assert np.all(b1 >= b0)
+
+
+def test_generate_reach_branch_with_every_grasp_out_of_reach():
+    """Base 3 m beyond the support: every grasp lies farther than
+    sum |d_i| + |a_i| = 1.393 m, so object 0 (designated, free, no world to
+    hit) fails IK on every try, spends exactly max_retries + 1 tries, the
+    candidate is invalid and no later object is placed."""
+    b = _reach_batch()
+    b.tmpl_base[:, 0] -= 3.0
+    ikp = oracle.ik_params(iters=3, seeds=4, seed=2)
+    for retries in (0, 3):
+        poses, v, _, tries = oracle.generate(b, seed=4, max_retries=retries, arm=ARM, ikp=ikp)
+        assert v.sum() == 0
+        assert np.all(tries == retries + 1)
+        offs = oracle.pose_offsets(b)
+        t_of = b.cand_template()
+        for c in range(b.n_cand):
+            n = b.n_obj_of(t_of[c])
+            assert np.all(np.isfinite(poses[offs[c]]))
+            assert np.all(np.isnan(poses[offs[c] + 1: offs[c] + n]))
 
 
 def test_grasp_target_frame():
