@@ -63,8 +63,11 @@ OPS_PER_POINT_TRI = 77     # point-triangle distance, face region: edges and off
                            # region tests 12 FSETP, world position of the sphere 2 (FADD)
 OPS_PER_CULL_TEST = 10     # sphere vs bounding ball: 3 FADD, FMUL + 2 FFMA, 2 FADD (limit), FMUL, FSETP
 OPS_PER_EXHAUSTIVE_PAIR = 9  # one pair of an uncalled exhaustive check (3 FADD, FMUL + 2 FFMA, FADD, FMUL, FSETP)
-OPS_PER_IK_SEED_ITER = 720  # one check + DLS step: FK 280, check 40, error 21, J 63, J J^T 147, Cholesky 50,
-                            # solves 60, J^T y 42, clamp 14 (FP32-pipe operations, sincos counted once)
+OPS_PER_IK_SEED_ITER = 1000  # one check + DLS step, the scope table's algorithmic unit: FK ~315, J ~63,
+                             # J J^T 147, Cholesky ~60 + 6 sqrt, solves 72, J^T y 42, error + check ~80 (FP32
+                             # instructions; the 14 MUFU of the sin / cos pairs on top). The kernel's own
+                             # count of the same work is ~720 (FK 280, check 40, error 21, J 63, J J^T 147,
+                             # Cholesky 50, solves 60, J^T y 42, clamp 14) plus its sin / cos polynomials.
 L2_BYTES = 126 * 1024 * 1024
 
 PATHS = {
@@ -336,6 +339,21 @@ def run_ours(args, wl):
         gate_info["vs_reach_map"], rmap = compare_gates(sc, ctx, gate, tr, ytr, ho, yho, recall, pass_rate)
         del tr, ho, ytr, yho
 
+    # launch shape of the generation kernels: the project's autotuner times
+    # whole graph-replayed calls of this workload over its search space
+    # (untimed set-up) unless a shape is given
+    shape_info = None
+    if cfg is None and not args.no_tune:
+        from paper_2512_16896_b300 import autotune
+        t0 = time.perf_counter()
+        cfg, tune = autotune.tune_generate(ctx, db, batch, order, seed=seed * 7919 + 7, max_retries=args.retries,
+                                           arm=arm if reach else None, ik=ikp, gate=gate, verbose=args.tune_verbose)
+        shape_info = {"threads": cfg[0], "a_per_lane": cfg[1], "ctas_per_sm": cfg[3], "tuned": True,
+                      "tune_ms_best": round(tune["ms"], 3), "tune_seconds": round(time.perf_counter() - t0, 1),
+                      "top": tune["top"][:4]}
+    elif cfg is not None:
+        shape_info = {"threads": cfg[0], "a_per_lane": cfg[1], "ctas_per_sm": cfg[3], "tuned": False}
+
     def enqueue(step_seed, use_gate=True, use_graph=True, use_map=False):
         if db.max_parts:  # a new articulation state per step, then the scenes around it
             sc.sample_parts(ctx, db, seed=step_seed)
@@ -363,6 +381,11 @@ def run_ours(args, wl):
             ev[i][1].record(stream)
             stats.append(ctx.generate_stats())  # synchronises after the step
             vals.append(int(valid.sum().item()))
+            if args.trace and i == steps - 1 and label.startswith("batched"):
+                st_, a_, b_ = ctx.generate_trace()
+                with open(args.trace, "w") as f:
+                    json.dump({"label": label, "stage": st_.tolist(), "start_ms": a_.tolist(),
+                               "end_ms": b_.tolist()}, f)
         torch.cuda.synchronize()
         ctx.synchronize()
         ms = [a.elapsed_time(b) for a, b in ev]
@@ -374,6 +397,10 @@ def run_ours(args, wl):
     plain = None
     if reach and not args.no_plain:
         plain = timed("plain", False, False, args.plain_steps, min(args.warmup, 3))
+    per_tmpl = None
+    if reach and not args.no_plain and args.per_template_s > 0:
+        per_tmpl = plain_per_template(sc, ctx, db, batch, args, arm, ikp, seed, poses, valid, band, tries,
+                                      q_reach, args.per_template_s)
     map_run = None
     if rmap is not None and args.map_steps > 0:
         map_run = timed("batched+map", False, True, args.map_steps, min(args.warmup, 3), use_map=True)
@@ -498,6 +525,18 @@ def run_ours(args, wl):
                     "ik_solves_per_step": m_st["ik_solves"], "gate_rejections_per_step": m_st["gate_rejections"],
                     "launch": "CUDA graph replay",
                     "gate": "4D reachability map from the same IK labels, recall >= 0.99 on the held-out targets"}
+    cfg_block = {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
+                 "reachability": reach_desc if reach else None,
+                 "gate": gate_info, "launch": "eager" if args.no_graph else "CUDA graph replay",
+                 "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
+                 "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
+                 "parallelism": f"replicas x{world}",
+                 "launch_shape": shape_info,
+                 # the metric's own comparison as scalars: the plain paths and the gate's quality
+                 "plain_value": plain_line["value"] if plain_line else None,
+                 "plain_per_template_value": per_tmpl["value"] if per_tmpl else None,
+                 "gate_heldout_recall": gate_info["heldout_recall"] if gate_info else None,
+                 "gate_pass_rate": gate_info["heldout_pass_rate"] if gate_info else None}
     line = {
         "metric": "verified collision-free scenes/sec",
         "value": total_valid / total_s,
@@ -511,13 +550,9 @@ def run_ours(args, wl):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "path": PATHS[args.path], "retries": args.retries,
-                   "reachability": reach_desc if reach else None,
-                   "gate": gate_info, "launch": "eager" if args.no_graph else "CUDA graph replay",
-                   "candidates_per_gpu": n, "valid_per_step": total_valid / args.steps / world,
-                   "l2": "flushed between timed steps (256 MB write, untimed); inputs exceed L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": cfg_block,
         "plain": plain_line,
+        "plain_per_template": per_tmpl,
         "map_gated": map_line,
         "stages": {"gen_ms_per_step": gen_rf["ms_per_step"], "ik_ms_per_step": ik_rf["ms_per_step"],
                    "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
@@ -549,6 +584,48 @@ def run_ours(args, wl):
     return 0
 
 
+def plain_per_template(sc, ctx, db, batch, args, arm, ikp, seed, poses, valid, band, tries, q_reach, budget_s):
+    """The scope table's plain arm: the same placement loop with exact IK on
+    every try, launched eagerly once per template (no batching across
+    templates, no graph, no gate), over templates taken in a seeded random
+    order until about budget_s seconds have run. Returns verified scenes/s
+    over the candidates of the templates it ran."""
+    import torch
+    dev = poses.device
+    rng = np.random.default_rng(seed + 77)
+    order_t = rng.permutation(batch.n_templates)
+    off = batch.cand_tmpl_off
+    lists = [torch.arange(int(off[t]), int(off[t + 1]), dtype=torch.int32, device=dev) for t in order_t[:8]]
+
+    def one(t_list, step_seed):
+        sc.generate(ctx, db, seed=step_seed, max_retries=args.retries, order=t_list, poses=poses,
+                    out=(valid, band, tries), use_graph=False, arm=arm, ik=ikp, gate=None, q_reach=q_reach)
+
+    for i, t_list in enumerate(lists[:4]):  # warm-up
+        one(t_list, seed * 7919 + 9000 + i)
+    ctx.synchronize()
+    valid.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(ctx.stream)
+    t0 = time.perf_counter()
+    done = []
+    for t in order_t:
+        t_list = torch.arange(int(off[t]), int(off[t + 1]), dtype=torch.int32, device=dev)
+        one(t_list, seed * 7919 + 9100)
+        done.append(t_list)
+        if len(done) % 16 == 0:
+            ctx.synchronize()
+            if time.perf_counter() - t0 > budget_s:
+                break
+    b.record(ctx.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    cand = torch.cat(done)
+    n_valid = int(valid[cand].sum().item())
+    return {"value": n_valid / (ms / 1e3), "unit": "scenes/s", "templates": len(done), "candidates": int(cand.numel()),
+            "valid": n_valid, "ms": ms, "launch": "eager, one sc_generate call per template, exact IK on every try"}
+
+
 def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
     """Each row's kernel alone, timed with CUDA events on the context's stream.
     only: regular expression on the row names (None: every row)."""
@@ -562,8 +639,63 @@ def kernel_suite(sc, ctx, dev, peak_ops, only=None, shelf_cand=65536):
         kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand)
     if any(want(k) for k in ("ik_topdown_262144", "gate_infer_262144", "gate_train_epoch_262144",
                               "rmap_build_262144", "rmap_query_262144")):
-        kernel_suite_ik_gate(sc, ctx, dev, out, want)
+        kernel_suite_ik_gate(sc, ctx, dev, out, want, peak_ops)
+    if want("tabletop_graph_1024"):
+        out["tabletop_graph_1024"] = tabletop_graph(sc, ctx, dev)
     return out
+
+
+def tabletop_graph(sc, ctx, dev, replays=1000):
+    """The small plain case: one tabletop template, 1024 candidates x 8
+    objects x 16 spheres. One batch = sample every object's pose, then the
+    whole-scene collision check (exact minimum); captured once into a CUDA
+    graph and replayed `replays` times back to back: microseconds per batch
+    (launch latency bound), next to the same two calls launched eagerly."""
+    import torch
+    stream = torch.cuda.Stream(dev)  # graphs are captured on a non-default stream
+    ctx = sc.Context(dev.index if dev.index is not None else torch.cuda.current_device(), stream=stream)
+    b = synth.tabletop(seed=0, n_cand=1024)
+    db = sc.DeviceBatch(b, device=dev)
+    poses = db.new_poses(dev)
+    n = b.n_cand
+    ok, sband = torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.uint8, device=dev)
+    col, md, cband = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
+                      torch.empty(n, dtype=torch.uint8, device=dev))
+
+    def batch_once():
+        sc.sample_poses(ctx, db, seed=0, poses=poses, out=(ok, sband))
+        sc.collide(ctx, db, poses, out=(col, md, cband))
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            batch_once()
+    ctx.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch_once()
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with torch.cuda.stream(stream):
+        for _ in range(10):
+            g.replay()
+        a, z = ev()
+        a.record(stream)
+        for _ in range(replays):
+            g.replay()
+        z.record(stream)
+        z.synchronize()
+        c, d = ev()
+        c.record(stream)
+        for _ in range(replays):
+            batch_once()
+        d.record(stream)
+        d.synchronize()
+    ctx.synchronize()
+    free = int(((col == 0) & (ok == 1)).sum().item())
+    ctx.close()
+    us = a.elapsed_time(z) * 1e3 / replays
+    return {"us_per_batch_graph": us, "us_per_batch_eager": c.elapsed_time(d) * 1e3 / replays, "replays": replays,
+            "candidates": n, "collision_free": free,
+            "candidates_per_s": n / (us / 1e6)}
 
 
 def exhaustive_work(batch):
@@ -587,6 +719,7 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
     (65,536 x 32 objects x 64 spheres, 20 boxes), the ragged batch and the
     world-mesh batch."""
     import torch
+    from paper_2512_16896_b300 import autotune
     stream = ctx.stream
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -606,21 +739,34 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
         for mode, key in keys.items():
             if not want(key):
                 continue
-            ms, work = [], []
-            for i in range(5):
-                with torch.cuda.stream(stream):
-                    flush.zero_()
-                a, b = ev()
-                a.record(stream)
-                sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=(0, 0, 0, 0, mode))
-                b.record(stream)
-                work.append(sc.collide_last_work(ctx) + (sc.collide_last_tri_work(ctx),))
-                if i >= 2:
-                    ms.append(a.elapsed_time(b))
+            # the project's autotuner picks the launch shape on a strided sample
+            # of the LPT list (untimed); the default shape is timed beside it
+            shape, tune = autotune.tune_collide(ctx, db, batch, poses, order, decide=bool(mode))
+            cfg = tuple(shape) + (mode,)
+
+            def timed_collide(config):
+                ms_, work_ = [], []
+                for i in range(5):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                    a, b = ev()
+                    a.record(stream)
+                    sc.collide(ctx, db, poses, active=order, out=(col, md, cb), config=config)
+                    b.record(stream)
+                    work_.append(sc.collide_last_work(ctx) + (sc.collide_last_tri_work(ctx),))
+                    if i >= 2:
+                        ms_.append(a.elapsed_time(b))
+                return ms_, work_
+
+            ms_def, _ = timed_collide((0, 0, 0, 0, mode))
+            ms, work = timed_collide(cfg)
             t = np.mean(ms) / 1e3
             ops = np.mean([p * OPS_PER_SPHERE_PAIR + q * OPS_PER_SPHERE_BOX_COLLIDE + r * OPS_PER_POINT_TRI
                            for p, q, r in work[2:]])
             out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": batch.n_cand / t,
+                        "launch_shape": {"threads": shape[0], "a_per_lane": shape[1], "seg_len": shape[2],
+                                         "ctas_per_sm": shape[3], "tuned_on": tune["sample"]},
+                        "ms_default_shape": float(np.mean(ms_def)),
                         "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
                         "box_pairs": float(np.mean([w[1] for w in work[2:]])),
                         "exhaustive_pairs": float(pairs_all),
@@ -637,7 +783,7 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
         del db, poses, col, md, cb
 
 
-def kernel_suite_ik_gate(sc, ctx, dev, out, want):
+def kernel_suite_ik_gate(sc, ctx, dev, out, want, peak_ops):
     import torch
     stream = ctx.stream
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -654,8 +800,12 @@ def kernel_suite_ik_gate(sc, ctx, dev, out, want):
             b.synchronize()
             if i >= 1:
                 ms.append(a.elapsed_time(b))
-        out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / (np.mean(ms) / 1e3),
-                                    "reachable": float(r.float().mean().item())}
+        seed_iters = sc.ik_last_work(ctx)
+        t_ik = float(np.mean(ms)) / 1e3
+        out["ik_topdown_262144"] = {"ms": float(np.mean(ms)), "targets_per_s": 262144 / t_ik,
+                                    "reachable": float(r.float().mean().item()), "seed_iterations": seed_iters,
+                                    "ops_per_seed_iteration": OPS_PER_IK_SEED_ITER,
+                                    "roofline_frac": seed_iters * OPS_PER_IK_SEED_ITER / t_ik / peak_ops}
         # 4D reachability map from these labels: build, then query the same targets
         m = sc.ReachMap(ctx)
         bms, qms = [], []
@@ -790,7 +940,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--templates", type=int, default=4096, help="ragged workload: number of templates (profiling)")
-    ap.add_argument("--no-tune", action="store_true", help="use the library's default collide launch shape")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the library's default launch shape for generation (skip the autotuner)")
     ap.add_argument("--collide-config", type=str, default="", help="threads,a_per_lane,seg_len,ctas_per_sm")
     ap.add_argument("--tune-verbose", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the generation steps eagerly")
@@ -803,6 +954,10 @@ def main():
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the per-kernel measurements (one JSON line; profiling)")
     ap.add_argument("--kernel-filter", type=str, default=None, help="regular expression on the kernel row names")
+    ap.add_argument("--per-template-s", type=float, default=3.0,
+                    help="seconds of the one-launch-per-template plain arm (0: skip)")
+    ap.add_argument("--trace", type=str, default=None,
+                    help="write the per-launch stage trace of the last timed gated step to this JSON file")
     ap.add_argument("--shelf-cand", type=int, default=65536, help="shelf candidates of the collision rows")
     ap.add_argument("--train-labels", type=int, default=4194304)
     ap.add_argument("--train-epochs", type=int, default=2)

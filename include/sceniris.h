@@ -281,8 +281,12 @@ typedef struct {
  * through an atomic counter, so list the heaviest candidates first (see
  * sc_order_by_work) for ragged batches.
  * Outputs [n]: collide u8, min_dist float, band u8 (n = n_active, or n_cand
- * when active is NULL). Errors: SC_ERR_INVALID (NULL outputs, first_new_obj < 0,
- * bad config, limits of sc_scene_batch). */
+ * when active is NULL). A candidate the kernel cannot check (its template,
+ * sphere, object, box or triangle counts beyond the limits, or a world box
+ * naming a part its template lacks) gets collide = 0, min_dist = NaN and
+ * band = 1, and the device error is latched into the context's status word.
+ * Errors: SC_ERR_INVALID (NULL outputs, first_new_obj < 0, bad config, limits
+ * of sc_scene_batch). */
 sc_status sc_collide(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
                      int32_t n_active, int32_t first_new_obj, uint8_t* collide, float* min_dist, uint8_t* band);
 sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
@@ -340,6 +344,11 @@ typedef struct {
 sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params, const float* targets,
                       const uint32_t* target_ids, int32_t n, uint8_t* reachable, float* q_out, float* err,
                       uint8_t* band);
+
+/* Seed-iterations (checks evaluated x seeds, summed over targets) of the
+ * last sc_ik_reach call on this context, read back after the call completes
+ * (synchronises the stream). */
+sc_status sc_ik_last_work(sc_ctx* ctx, int64_t* seed_iterations);
 
 /* One damped-least-squares step (the update of sc_ik_reach, including the
  * clamp) for n independent (target, configuration) pairs: q_out[i] = step of
@@ -561,6 +570,11 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured
  * with one setting is re-captured for the other). */
 sc_status sc_ctx_set_timing(sc_ctx* ctx, int32_t on);
+/* Per-launch trace of the last timed sc_generate call (timing on): for each
+ * timed launch i < *n (at most cap are written), stage[i] (0 generation,
+ * 1 grasp targets + gate, 2 exact IK), start_ms[i] and end_ms[i] relative to
+ * the first recorded event. HOST arrays [cap]. Synchronises the stream. */
+sc_status sc_generate_trace(sc_ctx* ctx, int32_t cap, int32_t* n, int32_t* stage, float* start_ms, float* end_ms);
 
 /* Host helper: order candidates heaviest first (LPT) by their exhaustive
  * pair count. HOST arrays: tmpl_obj_off [T+1], obj_sph_off [O+1],
@@ -570,7 +584,9 @@ sc_status sc_order_by_work(int32_t n_templates, const int32_t* tmpl_obj_off, con
 
 /* ------------------------------------------------- allocation-free variant */
 
-/* Largest candidate list one sc_collide_noalloc call accepts. */
+/* Largest candidate list one sc_collide_noalloc call accepts: CTAs claim
+ * candidates through a 32-bit work counter that runs past the end by up to
+ * the grid size, and the kernel reads it as a signed index. */
 #define SC_NOALLOC_MAX_ITEMS (1 << 30)
 
 /* The collision check of sc_collide for callers that cannot allocate device
@@ -586,7 +602,10 @@ sc_status sc_order_by_work(int32_t n_templates, const int32_t* tmpl_obj_off, con
  *    NULL = legacy default stream).
  *  - The first call on a device looks up that array's device address
  *    (cudaGetSymbolAddress) and the SM count; make that first call before any
- *    stream capture on that device.
+ *    stream capture on that device. The address is kept for the life of the
+ *    process: do not call this entry point on a device after a
+ *    cudaDeviceReset of it (the library's module, and the array with it, is
+ *    loaded again at a new address).
  *  - Every call shares the one array per device; the launch zeroes the work
  *    counter before the kernel runs. Calls that overlap on the GPU (on two
  *    streams, or from two host threads at once) race on it and must not be

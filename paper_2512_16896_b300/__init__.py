@@ -18,6 +18,7 @@ from ._native import (  # noqa: F401
     collide,
     collide_last_work,
     collide_last_tri_work,
+    ik_last_work,
     generate,
     ik_reach,
     ik_dls_step,

@@ -124,6 +124,7 @@ SIGNATURES = {
                                    ctypes.POINTER(CollideConfig), ctypes.POINTER(ScGenReach), P, P, P, P, P]),
     "sc_ik_reach": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.POINTER(ScIkParams), P, P, I32, P, P, P, P]),
     "sc_ik_dls_step": (ctypes.c_int, [P, ctypes.POINTER(ScArm), ctypes.c_float, P, P, I32, P, P]),
+    "sc_ik_last_work": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
     "sc_mlp_param_count": (I32, []),
     "sc_mlp_create": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(P)]),
     "sc_mlp_destroy": (None, [P]),
@@ -138,6 +139,7 @@ SIGNATURES = {
     "sc_mlp_load": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.POINTER(P)]),
     "sc_generate_stats": (ctypes.c_int, [P, ctypes.POINTER(ScGenStats)]),
     "sc_ctx_set_timing": (ctypes.c_int, [P, I32]),
+    "sc_generate_trace": (ctypes.c_int, [P, I32, ctypes.POINTER(I32), P, P, P]),
     "sc_collide_noalloc": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), P, P, I32, I32, P, P, P]),
     "sc_sample_parts": (ctypes.c_int, [P, ctypes.POINTER(ScSceneBatch), ctypes.c_uint64, P, I32, P]),
     "sc_rmap_create": (ctypes.c_int, [P, ctypes.POINTER(ScRmapParams), ctypes.POINTER(P)]),
@@ -204,6 +206,18 @@ class Context:
         st = ScGenStats()
         _check(lib().sc_generate_stats(self.handle, ctypes.byref(st)))
         return st.as_dict()
+
+    def generate_trace(self, cap: int = 8192):
+        """Per-launch trace of the last timed generate call: (stage, start_ms, end_ms) numpy arrays."""
+        import numpy as np
+        n = I32()
+        stage = np.zeros(cap, np.int32)
+        t0 = np.zeros(cap, np.float32)
+        t1 = np.zeros(cap, np.float32)
+        _check(lib().sc_generate_trace(self.handle, cap, ctypes.byref(n), stage.ctypes.data, t0.ctypes.data,
+                                       t1.ctypes.data))
+        m = min(n.value, cap)
+        return stage[:m], t0[:m], t1[:m]
 
     @property
     def num_sms(self) -> int:
@@ -579,6 +593,13 @@ def collide_last_work(ctx: Context):
     a, b = I64(), I64()
     _check(lib().sc_collide_last_work(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ik_last_work(ctx: Context) -> int:
+    """Seed-iterations (checks x seeds) of the last ik_reach call (synchronises)."""
+    a = I64()
+    _check(lib().sc_ik_last_work(ctx.handle, ctypes.byref(a)))
+    return a.value
 
 
 def collide_last_tri_work(ctx: Context) -> int:

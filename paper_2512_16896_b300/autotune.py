@@ -1,11 +1,17 @@
-"""Launch-shape autotuner for the persistent collision kernel.
+"""Launch-shape autotuner for the persistent collision kernel and the
+generation kernels.
 
-Times sc_collide_ex over a grid of launch shapes (threads per CTA, A spheres
-per lane, B-segment length, CTAs per SM) on a bounded sample of the batch's
-candidates (kept in the batch's LPT order, so the sample has the batch's mix
-of heavy and light candidates), and returns the fastest. Results are cached in
-a JSON file keyed by the device name and a histogram of the batch's per-template
-sphere counts, so a workload of the same shape reuses the choice.
+tune_collide times sc_collide_ex over a grid of launch shapes (threads per
+CTA, A spheres per lane, B-segment length, CTAs per SM) on a bounded sample
+of the batch's candidates (kept in the batch's LPT order, so the sample has
+the batch's mix of heavy and light candidates). tune_generate times whole
+sc_generate calls (CUDA-graph replays, the reachability stage included when
+an arm is given) over the generation kernels' shapes (threads per CTA, A
+spheres per lane, CTAs per SM). Each returns the fastest shape. Results are
+cached in a JSON file keyed by the device name, the call and histograms of the
+batch's per-template sphere and object counts, so a workload of the same
+shape reuses the choice. Every shape computes the same results (the launch
+shape changes only how the work is spread), which the tests check.
 """
 from __future__ import annotations
 
@@ -30,6 +36,14 @@ DEFAULT_SPACE = [
 ]
 
 
+GENERATE_SPACE = [
+    (t, apl, 256, cps)
+    for t in (128, 256)
+    for apl in (1, 2)
+    for cps in (2, 3, 4, 6)
+]
+
+
 def shape_key(batch, first_new: int) -> str:
     nsph = np.asarray(batch.obj_sph_off[np.asarray(batch.tmpl_obj_off)[1:]] -
                       batch.obj_sph_off[np.asarray(batch.tmpl_obj_off)[:-1]])
@@ -40,6 +54,10 @@ def shape_key(batch, first_new: int) -> str:
     frac = lambda x: tuple(np.round(x / max(1, x.sum()), 2).tolist())
     raw = json.dumps([frac(h), frac(o), nobb > 0, first_new > 0])
     return hashlib.sha1(raw.encode()).hexdigest()[:16]
+
+
+def generate_key(batch, retries: int, reach: bool, gated: bool) -> str:
+    return f"generate|{shape_key(batch, 0)}|r{retries}|{'reach' if reach else 'plain'}|{'gate' if gated else 'nogate'}"
 
 
 def _load():
@@ -53,10 +71,11 @@ def _load():
 
 def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tensor, order: torch.Tensor,
                  first_new: int = 0, space=None, sample: int = 16384, reps: int = 2, use_cache: bool = True,
-                 verbose: bool = False):
-    """Best (threads, a_per_lane, seg_len, ctas_per_sm) for this batch shape."""
+                 verbose: bool = False, decide: bool = False):
+    """Best (threads, a_per_lane, seg_len, ctas_per_sm) for this batch shape, in
+    exact-minimum mode or (decide) decide-only mode."""
     dev = torch.cuda.get_device_name(ctx.device)
-    key = f"{dev}|{shape_key(batch, first_new)}"
+    key = f"{dev}|{shape_key(batch, first_new)}|{'decide' if decide else 'exact'}"
     cache = _load()
     if use_cache and key in cache:
         return tuple(cache[key]["config"]), cache[key]
@@ -70,12 +89,13 @@ def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tens
     results = []
     for cfg in space:
         try:
-            nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=cfg)  # warm
+            full = tuple(cfg) + (1 if decide else 0,)
+            nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)  # warm
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(ctx.stream)
             for _ in range(reps):
-                nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=cfg)
+                nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)
             e1.record(ctx.stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1) / reps
@@ -84,9 +104,15 @@ def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tens
         results.append((ms, cfg))
         if verbose:
             print(f"  {cfg}: {ms:.3f} ms", flush=True)
+    return _store(cache, key, results, int(sub.numel()))
+
+
+def _store(cache, key, results, sample):
+    if not results:
+        raise nat.SceniError("no launch shape of the search space could run this batch")
     results.sort()
     best_ms, best = results[0]
-    entry = {"config": list(best), "ms": best_ms, "sample": int(sub.numel()),
+    entry = {"config": list(best), "ms": best_ms, "sample": sample,
              "top": [[round(m, 4), list(c)] for m, c in results[:8]], "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     cache[key] = entry
     try:
@@ -94,4 +120,43 @@ def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tens
             json.dump(cache, f, indent=1, sort_keys=True)
     except OSError:
         pass
-    return best, entry
+    return tuple(best), entry
+
+
+def tune_generate(ctx: nat.Context, db: nat.DeviceBatch, batch, order: torch.Tensor, seed: int = 1,
+                  max_retries: int = 10, arm=None, ik=None, gate=None, space=None, reps: int = 2,
+                  use_cache: bool = True, verbose: bool = False):
+    """Best (threads, a_per_lane, seg_len, ctas_per_sm) of sc_generate for this
+    batch shape: each shape's call is captured once into a CUDA graph, warmed
+    and replayed `reps` times on the whole batch (the generation kernels'
+    balance depends on the whole candidate list, so no sample is taken)."""
+    dev = torch.cuda.get_device_name(ctx.device)
+    key = f"{dev}|{generate_key(batch, max_retries, arm is not None, gate is not None)}"
+    cache = _load()
+    if use_cache and key in cache:
+        return tuple(cache[key]["config"]), cache[key]
+    space = space or GENERATE_SPACE
+    poses = db.new_poses(order.device)
+    n = db.n_cand
+    outs = (torch.zeros(n, dtype=torch.uint8, device=poses.device), torch.zeros(n, dtype=torch.uint8, device=poses.device),
+            torch.zeros(n, dtype=torch.int32, device=poses.device))
+    results = []
+    for cfg in space:
+        try:
+            call = lambda: nat.generate(ctx, db, seed=seed, max_retries=max_retries, order=order, config=cfg,
+                                        poses=poses, out=outs, use_graph=True, arm=arm, ik=ik, gate=gate)
+            call()  # capture and warm
+            ctx.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            for _ in range(reps):
+                call()
+            e1.record(ctx.stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        except nat.SceniError:
+            continue  # shape not launchable for this batch (shared memory, occupancy)
+        results.append((ms, cfg))
+        if verbose:
+            print(f"  {cfg}: {ms:.3f} ms", flush=True)
+    return _store(cache, key, results, n)

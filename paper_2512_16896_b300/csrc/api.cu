@@ -539,7 +539,7 @@ sc_status sc_ik_reach(sc_ctx* ctx, const sc_arm* arm, const sc_ik_params* params
     return fail(SC_ERR_INVALID, "tolerances must be positive, tol_rot < pi/2, lambda >= 0");
   DeviceGuard g(ctx->device);
   cudaError_t e = sc::launch_ik(*arm, *params, targets, target_ids, n, reachable, q_out, err, nullptr, band,
-                                ctx->d_counter, ctx->num_sms, ctx->stream);
+                                ctx->d_counter, ctx->d_stats + 4, ctx->num_sms, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "ik_kernel launch");
   return SC_OK;
 }
@@ -656,7 +656,7 @@ sc_status sc_surrogate_grads(sc_ctx* ctx, sc_mlp* m, const float* targets, const
   DeviceGuard g(ctx->device);
   cudaError_t e = sc::mlp_reserve(m->st, n);
   if (e) return fail(SC_ERR_OOM, "surrogate training buffers: %s", cudaGetErrorString(e));
-  e = sc::mlp_gradients(m->st, targets, labels, nullptr, n, m->loss_dev, ctx->num_sms, ctx->stream);
+  e = sc::mlp_gradients(m->st, targets, labels, nullptr, n, m->loss_dev, ctx->d_status, ctx->num_sms, ctx->stream);
   if (!e && grads)
     e = cudaMemcpyAsync(grads, sc::mlp_grads_ptr(m->st), sc::mlp_param_count() * 4, cudaMemcpyDeviceToDevice,
                         ctx->stream);
@@ -721,7 +721,7 @@ sc_status sc_surrogate_train(sc_ctx* ctx, sc_mlp* m, const float* targets, const
     float loss_acc = 0.f;
     for (int bi = 0; bi < nb; ++bi) {
       e = sc::mlp_gradients(m->st, targets, labels, m->index + (size_t)bi * p->batch, p->batch, m->loss_dev,
-                            ctx->num_sms, ctx->stream);
+                            ctx->d_status, ctx->num_sms, ctx->stream);
       if (!e) e = sc::mlp_adam(m->st, p->lr, p->beta1, p->beta2, p->eps, ctx->stream);
       if (e) return cuda_fail(e, "training step");
       if (loss_per_epoch && bi == nb - 1) {  // the epoch's last batch reports its mean BCE
@@ -1024,6 +1024,29 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   return SC_OK;
 }
 
+sc_status sc_generate_trace(sc_ctx* ctx, int32_t cap, int32_t* n, int32_t* stage, float* start_ms, float* end_ms) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!n || cap < 0 || (cap > 0 && (!stage || !start_ms || !end_ms)))
+    return fail(SC_ERR_INVALID, "NULL output or negative cap");
+  DeviceGuard g(ctx->device);
+  *n = ctx->timing ? ctx->timer.used : 0;
+  if (*n == 0) return SC_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e) return cuda_fail(e, "synchronize");
+  const int m = *n < cap ? *n : cap;
+  for (int i = 0; i < m; ++i) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, ctx->tev[0], ctx->tev[2 * i]);
+    if (!e) e = cudaEventElapsedTime(&b, ctx->tev[0], ctx->tev[2 * i + 1]);
+    if (e) return cuda_fail(e, "cudaEventElapsedTime");
+    stage[i] = ctx->tcls[i];
+    start_ms[i] = a;
+    end_ms[i] = b;
+  }
+  return SC_OK;
+}
+
 sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphere_box_pairs) {
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;
@@ -1034,6 +1057,19 @@ sc_status sc_collide_last_work(sc_ctx* ctx, int64_t* sphere_pairs, int64_t* sphe
   if (e != cudaSuccess) return cuda_fail(e, "stats read");
   if (sphere_pairs) *sphere_pairs = (int64_t)h[0];
   if (sphere_box_pairs) *sphere_box_pairs = (int64_t)h[1];
+  return SC_OK;
+}
+
+sc_status sc_ik_last_work(sc_ctx* ctx, int64_t* seed_iterations) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!seed_iterations) return fail(SC_ERR_INVALID, "seed_iterations is NULL");
+  DeviceGuard g(ctx->device);
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->d_stats + 4, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stats read");
+  *seed_iterations = (int64_t)h;
   return SC_OK;
 }
 

@@ -79,6 +79,7 @@ struct CtaShared {
   int best_key;            // MIN: CTA-wide running minimum (float_key)
   int r2max_key, rmax_key;
   int hit;                 // DECIDE: a certain collision was found
+  int bad_box;             // a staged box names a part its template lacks
   float warp_min[32];
 };
 
@@ -167,10 +168,12 @@ __device__ __forceinline__ void stage_spheres(const sc_scene_batch& b, int s0, i
 // extents. A sphere centre w (relative to object 0) has box-frame
 // coordinates p = R^T w - R^T (centre - ref): three FMAs per axis.
 __device__ __forceinline__ void stage_boxes(const sc_scene_batch& b, int t, int c, int bx0, int nobb, const Smem& sm,
-                                            int tid, int nthr, int* status) {
+                                            int tid, int nthr, int* status, int* bad_box) {
   const float4 ref = sm.opose[0];
   for (int k = tid; k < nobb; k += nthr) {
-    const float3 sh = box_shift(b, t, c, bx0 + k, status);  // an articulated part's box moves with its joint
+    bool bad = false;
+    const float3 sh = box_shift(b, t, c, bx0 + k, status, &bad);  // an articulated part's box moves with its joint
+    if (bad) *(volatile int*)bad_box = 1;
     const float* o = b.obb + 12 * (bx0 + k);
     float qx = __ldg(o + 4), qy = __ldg(o + 5), qz = __ldg(o + 6), qw = __ldg(o + 7);
     const float inv = rsqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
@@ -564,11 +567,23 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
       sh.r2max_key = 0;
       sh.rmax_key = 0;
       sh.hit = 0;
+      sh.bad_box = 0;
     }
     __syncthreads();
     stage_spheres(b, s0, nt, S, sm, sh, tid, nthr, lane);
-    stage_boxes(b, t, c, bx0, nobb, sm, tid, nthr, a.status);
+    stage_boxes(b, t, c, bx0, nobb, sm, tid, nthr, a.status, &sh.bad_box);
     __syncthreads();
+    if (*(volatile int*)&sh.bad_box) {  // a malformed part box: no verdict, marked like the checks above
+      __syncthreads();  // every thread has read the flag
+      if (tid == 0) {
+        a.collide[item] = 0;
+        a.min_dist[item] = __int_as_float(0x7FC00000);
+        a.band[item] = 1;
+        sh.item = next;
+      }
+      __syncthreads();
+      continue;
+    }
     const float rmax = __int_as_float(sh.rmax_key);
     const float eps = 1e-5f * (__int_as_float(sh.r2max_key) + 0.01f);
     float m = kFarSentinel;

@@ -22,8 +22,10 @@
 namespace {
 
 // Scratch of one call: [0, 4) work counter (u32, zeroed by the launcher before
-// each launch), [16, 32) pair statistics (2 x u64, zeroed likewise). Status is
-// not latched here: candidates the kernel's own checks reject come back with
+// each launch); work statistics as u64 words from byte 16: sphere pairs at
+// [16, 24), sphere-box pairs at [24, 32) and point-triangle distances at
+// [72, 80) (word 7), zeroed likewise; the rest is unused. Status is not
+// latched here: candidates the kernel's own checks reject come back with
 // min_dist = NaN and band = 1.
 constexpr size_t kScratchBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -53,8 +55,9 @@ sc_status sc_collide_noalloc(void* cuda_stream, const sc_scene_batch* batch, con
   const int64_t n_items = active ? n_active : batch->n_cand;
   if (n_items > SC_NOALLOC_MAX_ITEMS)
     return fail(SC_ERR_INVALID, "sc_collide_noalloc: " + std::to_string(n_items) +
-                                    " candidates exceed the fixed scratch's limit of " +
-                                    std::to_string(SC_NOALLOC_MAX_ITEMS) + " per call");
+                                    " candidates exceed the per-call limit of " +
+                                    std::to_string(SC_NOALLOC_MAX_ITEMS) +
+                                    " (the 32-bit work counter runs past the end by up to the grid size)");
   if (n_items == 0) return SC_OK;
   if (!poses || !collide || !min_dist || !band)
     return fail(SC_ERR_INVALID, "sc_collide_noalloc: an input or output pointer is NULL");

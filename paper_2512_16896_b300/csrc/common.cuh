@@ -113,8 +113,10 @@ __device__ __forceinline__ int template_of(const sc_scene_batch& b, int c) {
 // Displacement q * axis of world box `box` (a batch index) for candidate c of
 // template t: nonzero only for a box of an articulated part (obb_part >= 0),
 // q being that part's joint value of the candidate. A part index outside the
-// template's parts latches kDevBadPart and leaves the box where it is.
-__device__ __forceinline__ float3 box_shift(const sc_scene_batch& b, int t, int c, int box, int* status) {
+// template's parts latches kDevBadPart (when status is given), sets *bad
+// (when given) and leaves the box where it is.
+__device__ __forceinline__ float3 box_shift(const sc_scene_batch& b, int t, int c, int box, int* status,
+                                            bool* bad = nullptr) {
   float3 s = make_float3(0.f, 0.f, 0.f);
   if (!b.obb_part || b.max_parts <= 0) return s;
   const int p = __ldg(&b.obb_part[box]);
@@ -122,6 +124,7 @@ __device__ __forceinline__ float3 box_shift(const sc_scene_batch& b, int t, int 
   const int p0 = __ldg(&b.tmpl_part_off[t]);
   if (p >= __ldg(&b.tmpl_part_off[t + 1]) - p0 || p >= b.max_parts) {
     latch_error(status, kDevBadPart);
+    if (bad) *bad = true;
     return s;
   }
   const float q = __ldg(&b.part_q[(int64_t)c * b.max_parts + p]);

@@ -879,6 +879,8 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
 // rows are the round's reach queue (grasp targets formed by
 // reach_targets_kernel), and each logit is decided at once (logit >= tau).
 struct GateIO {
+  static constexpr int kColGroups = 4;
+  static constexpr bool kStores = false;
   ReachArgs A;
   __device__ int rows() const { return *(volatile const int*)A.n_reach; }
   __device__ void features(int row, float f[9]) const {
@@ -888,6 +890,10 @@ struct GateIO {
     f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
   }
   __device__ void emit(int row, bool valid, float logit) const { gate_route(A, row, valid, logit >= A.tau); }
+  __device__ void store_input(int, const uint32_t*) const {}
+  __device__ void store_grad(int, int, int, const float*) const {}
+  __device__ uint16_t* act_out(int) const { return nullptr; }
+  __device__ int act_ld() const { return 0; }
 };
 
 // Top-down grasp of the candidate's current object k: position = top centre
@@ -939,7 +945,7 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
     float q[7], pe2, sr, cr;
     const ikc::Solve s = ikc::warp_solve(A.ik, T, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, lane, q, pe2, sr, cr);
     ++solves;
-    seed_iters += (unsigned long long)(s.it + 1) * (unsigned long long)A.ik.seeds;
+    seed_iters += (unsigned long long)s.checks * (unsigned long long)A.ik.seeds;
     __syncwarp();  // every lane has read the state before the winner updates it
     if (lane == s.winner) {
       const TmplInfo& Tm = A.tinfo[__ldg(&A.cand_t[c])];

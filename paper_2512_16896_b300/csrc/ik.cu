@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
   const int warps_total = gridDim.x * warps;
+  unsigned long long seed_iters = 0;
   int i = blockIdx.x * warps + (threadIdx.x >> 5);
   while (i < K.n) {
     int next = 0;
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
     const uint32_t tid = K.target_ids ? __ldg(&K.target_ids[i]) : (uint32_t)i;
     float q[7], pe2, s, c;
     const Solve r = warp_solve(K, T, tid, 0u, lane, q, pe2, s, c);
+    seed_iters += (unsigned long long)r.checks * (unsigned long long)K.seeds;
     if (lane == r.winner) {
       K.reach[i] = r.found;
 #pragma unroll
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
     }
     i = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
+  if (lane == 0 && seed_iters && K.seed_iters) atomicAdd(K.seed_iters, seed_iters);
 }
 
 // One DLS step for each (target, configuration) pair: the building block the
@@ -84,9 +87,10 @@ int ik_resident_blocks(int num_sms) {
 
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
                       int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, uint8_t* band,
-                      unsigned int* claim, int num_sms, cudaStream_t s) {
+                      unsigned int* claim, unsigned long long* seed_iters, int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(claim, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess && seed_iters) e = cudaMemsetAsync(seed_iters, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   IkArgs K;
   fill_params(K, arm, P);
@@ -98,6 +102,7 @@ cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* tar
   K.err = err;
   K.iters_out = iters_out;
   K.band = band;
+  K.seed_iters = seed_iters;
   K.claim = claim;
   const int threads = 128, warps = threads / 32;
   int blocks = (n + warps - 1) / warps;

@@ -30,11 +30,15 @@ struct IkArgs {
   float* err;
   int32_t* iters_out;
   uint8_t* band;        // optional: band flag of each target (Solve::band)
+  unsigned long long* seed_iters;  // optional: checks evaluated x seeds, summed (zeroed before the launch)
   unsigned int* claim;  // work counter (zeroed before the launch): warps claim targets dynamically
 };
 
 // Forward kinematics; z[i], p[i] = z axis and origin of frame i (i = 0..6,
-// the frame joint i+1 rotates about); R, t = tool frame.
+// the frame joint i+1 rotates about); R, t = tool frame (R row-major).
+// T_i = Rz(q_i) Tz(d_i) Tx(a_i) Rx(alpha_i) acts on the frame's columns
+// c0, c1, c2 in three steps: Rz turns c0, c1 by q; the translation adds
+// a c0 + d c2; Rx turns c1, c2 by alpha (4 + 2 + 4 multiply-adds per row).
 __device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3], float p[7][3], float R[9],
                                    float t[3]) {
   R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
@@ -47,18 +51,16 @@ __device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3
     p[i][0] = t[0]; p[i][1] = t[1]; p[i][2] = t[2];
     float st, ct;
     sincos_cw(q[i], &st, &ct);
-    const float ca = A.ca[i], sa = A.sa[i];
-    // rotation part of Rz(q) Rx(alpha): columns c0 = (ct, st, 0), c1 = (-st ca, ct ca, sa), c2 = (st sa, -ct sa, ca)
-    const float c1x = -st * ca, c1y = ct * ca, c2x = st * sa, c2y = -ct * sa;
-    // translation Rz(q) (a, 0, d) = (a ct, a st, d) in the current frame
-    const float lx = A.a[i] * ct, ly = A.a[i] * st, lz = A.d[i];
+    const float ca = A.ca[i], sa = A.sa[i], a = A.a[i], d = A.d[i];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
-      t[r] += r0 * lx + r1 * ly + r2 * lz;
-      R[3 * r] = r0 * ct + r1 * st;
-      R[3 * r + 1] = r0 * c1x + r1 * c1y + r2 * sa;
-      R[3 * r + 2] = r0 * c2x + r1 * c2y + r2 * ca;
+      const float n0 = fmaf(r1, st, r0 * ct);   // Rz: c0' = ct c0 + st c1
+      const float n1 = fmaf(r1, ct, -r0 * st);  //     c1' = ct c1 - st c0
+      t[r] = fmaf(n0, a, fmaf(r2, d, t[r]));    // Tz Tx: t += a c0' + d c2
+      R[3 * r] = n0;
+      R[3 * r + 1] = fmaf(r2, sa, n1 * ca);     // Rx: c1'' = ca c1' + sa c2
+      R[3 * r + 2] = fmaf(r2, ca, -n1 * sa);    //     c2'' = ca c2 - sa c1'
     }
   }
 }
@@ -67,22 +69,29 @@ struct Target {
   float R[9], p[3];
 };
 
-// Orientation error of R against the target's R*: with M = R^T R*, v =
-// vee(M - M^T) / 2 (tool frame; |v| = sin of the angle) and c = (tr M - 1) / 2
-// (its cosine).
-__device__ __forceinline__ void rot_error(const Target& T, const float R[9], float v[3], float* c) {
-  float M[9];
+// Orientation error of R against the target's R*, in the world frame: w =
+// 1/2 sum_k r_k x r*_k over the columns (|w| = sine of the angle of R^T R*,
+// since w = R vee(M - M^T) / 2 with M = R^T R*), and c = (tr(R^T R*) - 1) / 2
+// = (sum_ij R_ij R*_ij - 1) / 2 (its cosine).
+__device__ __forceinline__ void rot_error(const Target& T, const float R[9], float w[3], float* c) {
+  float wx = 0.f, wy = 0.f, wz = 0.f, tr = -1.f;
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) M[3 * r + cc] = R[r] * T.R[cc] + R[3 + r] * T.R[3 + cc] + R[6 + r] * T.R[6 + cc];
-  v[0] = 0.5f * (M[7] - M[5]);
-  v[1] = 0.5f * (M[2] - M[6]);
-  v[2] = 0.5f * (M[3] - M[1]);
-  *c = 0.5f * (M[0] + M[4] + M[8] - 1.f);
+  for (int k = 0; k < 3; ++k) {
+    const float ax = R[k], ay = R[3 + k], az = R[6 + k];        // column k of R
+    const float bx = T.R[k], by = T.R[3 + k], bz = T.R[6 + k];  // column k of R*
+    wx = fmaf(ay, bz, fmaf(-az, by, wx));
+    wy = fmaf(az, bx, fmaf(-ax, bz, wy));
+    wz = fmaf(ax, by, fmaf(-ay, bx, wz));
+    tr = fmaf(ax, bx, fmaf(ay, by, fmaf(az, bz, tr)));
+  }
+  w[0] = 0.5f * wx;
+  w[1] = 0.5f * wy;
+  w[2] = 0.5f * wz;
+  *c = 0.5f * tr;
 }
 
-// Success test of one configuration; v, s2 = |v|^2 and c as rot_error.
+// Success test of one configuration; v (world-frame error), s2 = |v|^2 and c
+// as rot_error.
 __device__ __forceinline__ bool check(const IkArgs& K, const Target& T, const float R[9], const float t[3],
                                       float* pos_err2, float v[3], float* s2_out, float* c_out) {
   const float dx = T.p[0] - t[0], dy = T.p[1] - t[1], dz = T.p[2] - t[2];
@@ -112,10 +121,8 @@ __device__ __forceinline__ bool check_banded(const IkArgs& K, float pe2, float s
 }
 
 // One damped-least-squares step of q (in place) towards T, given the forward
-// kinematics (z, p, R, t) of q and the tool-frame orientation error v of
-// rot_error. The world-frame orientation error 1/2 sum_k r_k x r*_k equals
-// R v (vee(R S R^T) = R vee(S) for a skew S, and R^T (R* R^T - R R*^T) R =
-// M - M^T).
+// kinematics (z, p, R, t) of q and the world-frame orientation error v =
+// 1/2 sum_k r_k x r*_k of rot_error.
 __device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Target& T, float q[7],
                                          const float z[7][3], const float p[7][3], const float R[9], const float t[3],
                                          const float v[3]) {
@@ -123,8 +130,9 @@ __device__ __forceinline__ void dls_step(const ArmK& A, float lambda2, const Tar
   e[0] = T.p[0] - t[0];
   e[1] = T.p[1] - t[1];
   e[2] = T.p[2] - t[2];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) e[3 + r] = R[3 * r] * v[0] + R[3 * r + 1] * v[1] + R[3 * r + 2] * v[2];
+  e[3] = v[0];
+  e[4] = v[1];
+  e[5] = v[2];
   // A = J J^T + lambda^2 I accumulated column by column (column i of J is
   // j_i = (z_i x (t - p_i), z_i)); J itself is not kept, it is rebuilt for
   // J^T y below, which keeps the register footprint small.
@@ -204,6 +212,7 @@ struct Solve {
   bool band;   // some seed's check up to the last one was within the band (check_banded)
   int winner;  // lane holding the returned configuration
   int it;      // check index at which the solve ended
+  int checks;  // checks evaluated (it + 1)
 };
 
 // Lock-step solve of one target by the whole warp (seed = lane). Returns the
@@ -219,7 +228,7 @@ __device__ __forceinline__ Solve warp_solve(const IkArgs& K, const Target& T, ui
 #pragma unroll
     for (int j = 0; j < 7; ++j) q[j] = K.arm.qmin[j] + (K.arm.qmax[j] - K.arm.qmin[j]) * u[j];
   }
-  Solve r{false, false, -1, 0};
+  Solve r{false, false, -1, 0, 0};
   pe2 = 0.f;
   float s2 = 0.f;
   c = 1.f;
@@ -230,6 +239,7 @@ __device__ __forceinline__ Solve warp_solve(const IkArgs& K, const Target& T, ui
     const bool ok = active && check(K, T, R, t, &pe2, v, &s2, &c);
     near = near || (active && check_banded(K, pe2, s2, c));
     const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+    r.checks = r.it + 1;
     if (m) {
       r.winner = __ffs(m) - 1;
       r.found = true;

@@ -115,7 +115,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
 // claim: a device work counter, zeroed by the launcher on the stream.
 cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* targets, const uint32_t* target_ids,
                       int n, uint8_t* reach, float* q_out, float* err, int32_t* iters_out, uint8_t* band,
-                      unsigned int* claim, int num_sms, cudaStream_t s);
+                      unsigned int* claim, unsigned long long* seed_iters, int num_sms, cudaStream_t s);
 // Blocks of 128 threads of the IK kernels that fit on the device at once.
 int ik_resident_blocks(int num_sms);
 cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets, const float* q_in, int n,
@@ -153,7 +153,38 @@ cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int
                               int* status, int num_sms, cudaStream_t s);
 cudaError_t mlp_reserve(MlpState* S, int Bcap);
 cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
-                          float* loss_dev, int num_sms, cudaStream_t s);
+                          float* loss_dev, int* status, int num_sms, cudaStream_t s);
+// One training step's contractions on tcgen05 (mlp_train_tc.cu): the
+// forward pass with its caches, the backward pass through the activations
+// and the weight gradients dW1..dW3 (bias and last-layer gradients are
+// summed by the caller). Feature-major arrays have row stride ld.
+struct TrainTcLaunch {
+  MlpTcWeights w;
+  const void* W2tc;  // bf16 canonical [in][out] copies (B operands of dH = dA W)
+  const void* W3tc;
+  const float* targets;
+  const uint8_t* labels;
+  const int32_t* index;  // batch row -> target / label (NULL: identity)
+  int n, ld;
+  float* logits;         // [n]
+  uint16_t* x16T;        // [16][ld]
+  uint16_t* hT[3];       // [256][ld]
+  float4* g[3];          // SiLU'(z): [64][ld] float4 blocks of 4 features
+  uint16_t* daT[3];      // [256][ld]
+  float* dz;             // [n]
+  float* loss_sum;       // zeroed by the caller
+  float* wg_part;        // mlp_train_tc_part_bytes(ld)
+  float* dW1;            // [256][9]
+  float* dW2;            // [256][256]
+  float* dW3;
+  float* db[3];          // [256] bias gradients
+  float* dW4;            // [256]
+  float* db4;            // [1]
+  int* status;
+};
+int mlp_train_tc_splits(int rows);
+size_t mlp_train_tc_part_bytes(int Bcap);
+cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s);
 cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t mlp_epoch_index(int n, uint64_t seed, int epoch, int32_t* index, cudaStream_t s);
 float* mlp_params_ptr(MlpState* S);

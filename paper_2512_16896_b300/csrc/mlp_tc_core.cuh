@@ -38,13 +38,13 @@ namespace {
 
 constexpr int H = 256;
 constexpr int TILE = 128;
-constexpr int THREADS = 256;
+constexpr int THREADS = 256;  // the training kernels' CTA; the forward pass takes 128 x IO::kColGroups
 constexpr int SM_W1 = 0;                      // [256][16] bf16 canonical, 8 KB
 constexpr int SM_W = SM_W1 + 8192;            // [256][256] bf16 canonical, 128 KB
 constexpr int SM_A = SM_W + 131072;           // [128][256] bf16 canonical, 64 KB
 constexpr int SM_BIAS = SM_A + 65536;         // b1 b2 b3 W4 as f32, 4 KB
-constexpr int SM_PART = SM_BIAS + 4 * H * 4;  // [128] partial logits of the second column half
-constexpr int SM_BAR = SM_PART + TILE * 4;    // 2 mbarriers
+constexpr int SM_PART = SM_BIAS + 4 * H * 4;  // [3][128] partial logits of column groups 1..3
+constexpr int SM_BAR = SM_PART + 3 * TILE * 4;  // 2 mbarriers
 constexpr int SM_TMEM = SM_BAR + 16;          // TMEM base address written by tcgen05.alloc
 constexpr int SM_TOTAL = SM_TMEM + 16;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz per wait
@@ -121,6 +121,20 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
   }
 }
 
+// 32 consecutive f32 columns of this thread's TMEM lane, without waiting
+// (tmem_wait_ld completes every load issued before it).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 32 consecutive f32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
   asm volatile(
@@ -140,6 +154,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
 // and a few FMA-pipe operations per activation. For a < -87 the denominator
 // overflows and the result is -0 (the exact value is below 1e-36 in magnitude).
 __device__ __forceinline__ float silu_f(float a) { return __fdividef(a, 1.f + __expf(-a)); }
+// The same logistic (for training, which also keeps SiLU'(a) = s (1 + a (1 - s))).
+__device__ __forceinline__ float sigmoid_f(float a) { return __fdividef(1.f, 1.f + __expf(-a)); }
+__device__ __forceinline__ float silu_grad_from(float a, float s) { return s * fmaf(a, 1.f - s, 1.f); }
+
+// Copies a 128 x 256 bf16 operand in the canonical K-major layout (K = 256)
+// out feature-major: dstT[k][row0 + r] (row stride ld), one 8 x 8 core matrix
+// per step: eight 16-byte shared loads, a register transpose, eight 16-byte
+// global stores. Row groups at or past `rows` are skipped (ld, a multiple of
+// 16, covers every row group below it).
+__device__ __forceinline__ void copy_out_transposed(const uint8_t* sa, uint16_t* dstT, int ld, int row0, int rows,
+                                                    int tid, int nthreads) {
+  for (int cm = tid; cm < (TILE / 8) * (H / 8); cm += nthreads) {
+    const int rg = cm / (H / 8), kg = cm % (H / 8);
+    if (rg * 8 >= rows) continue;
+    const uint8_t* src = sa + rg * (H / 8) * 128 + kg * 128;  // core matrix (rg, kg): 8 rows x 16 bytes
+    uint32_t w[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * r);
+      w[r][0] = v.x; w[r][1] = v.y; w[r][2] = v.z; w[r][3] = v.w;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {  // columns 2p, 2p + 1 of the core matrix
+      uint32_t lo[4], hi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // rows 2q, 2q + 1
+        lo[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x5410);
+        hi[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x7632);
+      }
+      const size_t base = (size_t)(kg * 8 + 2 * p) * ld + row0 + rg * 8;
+      *reinterpret_cast<uint4*>(dstT + base) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(dstT + base + ld) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    }
+  }
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -147,34 +196,66 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 
-// Epilogue of layers 1 and 2 for one thread's row and column half:
-// TMEM -> + bias -> SiLU -> bf16 -> next A operand (canonical, K = 256).
-__device__ __forceinline__ void epilogue_to_a(uint32_t taddr, const float* bias, uint8_t* sa, int row, int col0) {
-#pragma unroll 1
-  for (int c0 = 0; c0 < H / 2; c0 += 32) {
-    uint32_t r[32];
-    tmem_ld32(taddr + c0, r);
+// Epilogue of layers 1 and 2 for one thread's row and its CW columns:
+// TMEM -> + bias -> SiLU -> bf16 -> next A operand (canonical, K = 256); the
+// next 32 columns are loaded from TMEM while the current ones are computed.
+// A training IO (IO::kStores) also keeps every pre-activation and bf16
+// activation of batch row `grow` (io.store, only when `valid`).
+template <class IO, int CW>
+__device__ __forceinline__ void epilogue_to_a(const IO& io, int layer, uint32_t taddr, const float* bias, uint8_t* sa,
+                                              int row, int col0, int grow, bool valid) {
+  uint32_t r[2][32];
+  tmem_ld32_async(taddr, r[0]);
+  tmem_wait_ld();
+#pragma unroll
+  for (int c0 = 0; c0 < CW; c0 += 32) {
+    const int cur = (c0 / 32) & 1;
+    if (c0 + 32 < CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t w[4];
+      float g[8];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = col0 + c0 + q * 8 + 2 * j;
-        w[j] = pack_bf16(silu_f(__uint_as_float(r[q * 8 + 2 * j]) + bias[c]),
-                         silu_f(__uint_as_float(r[q * 8 + 2 * j + 1]) + bias[c + 1]));
+        const float p0 = __uint_as_float(r[cur][q * 8 + 2 * j]) + bias[c];
+        const float p1 = __uint_as_float(r[cur][q * 8 + 2 * j + 1]) + bias[c + 1];
+        if constexpr (IO::kStores) {
+          const float s0 = sigmoid_f(p0), s1 = sigmoid_f(p1);
+          w[j] = pack_bf16(p0 * s0, p1 * s1);
+          g[2 * j] = silu_grad_from(p0, s0);
+          g[2 * j + 1] = silu_grad_from(p1, s1);
+        } else {
+          w[j] = pack_bf16(silu_f(p0), silu_f(p1));
+        }
+      }
+      if constexpr (IO::kStores) {
+        if (valid) io.store_grad(layer, grow, col0 + c0 + q * 8, g);
       }
       *reinterpret_cast<uint4*>(sa + canon_offset(row, col0 + c0 + q * 8, H)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
+    if (c0 + 32 < CW) tmem_wait_ld();
   }
 }
 
 // IO supplies the rows: rows() (the row count, read once), features(row, f)
 // (the 9 raw features of a row < rows(), called by one thread per row) and
 // emit(row, valid, logit) (called by every thread of warps 0..3, one row
-// each, valid = row < rows(), so warp collectives may be used).
+// each, valid = row < rows(), so warp collectives may be used), and
+// IO::kColGroups (2 or 4): the CTA has 4 x kColGroups warps, warp w handling
+// TMEM lanes 32 (w % 4) .. + 31 and columns (w / 4) H / kColGroups .. (more
+// warps hide more of the epilogue's latency; the training IO keeps 2 for its
+// register budget). With
+// IO::kStores it also receives store_input(row, x16 as 8 packed bf16 pairs),
+// store_grad(layer, row, col8, SiLU'(z) of 8 columns) for layers 0..2 and
+// act_out(layer), the feature-major destination ([256][act_ld]) each
+// layer's bf16 activations are copied to from the shared operand while the
+// next contraction runs (training keeps them for the backward pass).
 template <class IO>
-__global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
+__global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int CG = IO::kColGroups, NT = 128 * CG, CW = H / CG;
+  static_assert(CG == 2 || CG == 4, "two or four column groups");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = io.rows();
   const int ntiles = (n + TILE - 1) / TILE;
@@ -192,9 +273,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
     mbar_init(bar_w, 1);
     mbar_init(bar_m, 1);
   }
-  for (int i = tid; i < 8192 / 16; i += THREADS)
+  for (int i = tid; i < 8192 / 16; i += NT)
     reinterpret_cast<uint4*>(sw1)[i] = __ldg(reinterpret_cast<const uint4*>(w.W1c) + i);
-  for (int i = tid; i < H; i += THREADS) {
+  for (int i = tid; i < H; i += NT) {
     sbias[i] = __ldg(w.params + w.off_b1 + i);
     sbias[H + i] = __ldg(w.params + w.off_b2 + i);
     sbias[2 * H + i] = __ldg(w.params + w.off_b3 + i);
@@ -212,9 +293,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, cg = warp >> 2;
   const int trow = quarter * 32 + lane;  // this thread's row in the tile (= TMEM lane)
-  const int col0 = half * (H / 2);       // this thread's column half
+  const int col0 = cg * CW;              // this thread's columns
   const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
   constexpr uint32_t idesc = make_idesc(TILE, H);
 
@@ -235,11 +316,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
 #pragma unroll
         for (int i = 0; i < 9; ++i) x[i] = (f[i] - __ldg(w.mu + i)) * __ldg(w.inv_sigma + i);
       }
+      uint32_t xb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xb[i] = pack_bf16(x[2 * i], x[2 * i + 1]);
 #pragma unroll
       for (int q = 0; q < 2; ++q)
         *reinterpret_cast<uint4*>(sa + canon_offset(tid, q * 8, 16)) =
-            make_uint4(pack_bf16(x[q * 8], x[q * 8 + 1]), pack_bf16(x[q * 8 + 2], x[q * 8 + 3]),
-                       pack_bf16(x[q * 8 + 4], x[q * 8 + 5]), pack_bf16(x[q * 8 + 6], x[q * 8 + 7]));
+            make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
+      if constexpr (IO::kStores) {
+        if (row < n) io.store_input(row, xb);
+      }
     }
     fence_proxy_async();
     tc_fence_before();
@@ -260,7 +346,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
       ok = false;
       break;
     }
-    epilogue_to_a(taddr, sbias, sa, trow, col0);
+    const int grow = tile * TILE + trow;
+    epilogue_to_a<IO, CW>(io, 0, taddr, sbias, sa, trow, col0, grow, grow < n);
 
     // ---- layers 2 and 3
     for (int layer = 0; layer < 2; ++layer) {
@@ -283,6 +370,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
                  idesc, s > 0);
         tc_commit(bar_m);
       }
+      if constexpr (IO::kStores)  // h1 / h2 out while the tensor cores read the same operand
+        copy_out_transposed(sa, io.act_out(layer), io.act_ld(), tile * TILE, n - tile * TILE, tid, NT);
       m_pending = true;
       ok = mbar_wait(bar_m, ph_m);
       if (ok) {
@@ -301,27 +390,61 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(MlpTcWeights w, IO i
         w_pending = true;
       }
       if (layer == 0) {
-        epilogue_to_a(taddr, sbias + H, sa, trow, col0);
+        epilogue_to_a<IO, CW>(io, 1, taddr, sbias + H, sa, trow, col0, grow, grow < n);
       } else {
         // h3 = bf16(SiLU(acc + b3)); logit = W4 . h3 + b4
         const float* b3 = sbias + 2 * H + col0;
         const float* w4 = sbias + 3 * H + col0;
         float z = 0.f;
-#pragma unroll 1
-        for (int c0 = 0; c0 < H / 2; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(taddr + c0, r);
+        uint32_t r[2][32];
+        tmem_ld32_async(taddr, r[0]);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float h = __bfloat162float(__float2bfloat16_rn(silu_f(__uint_as_float(r[j]) + b3[c0 + j])));
-            z = fmaf(h, w4[c0 + j], z);
+        for (int c0 = 0; c0 < CW; c0 += 32) {
+          const int cur = (c0 / 32) & 1;
+          if (c0 + 32 < CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
+#pragma unroll
+          for (int j8 = 0; j8 < 32; j8 += 8) {
+            uint32_t hw[4];
+            float g[8];
+#pragma unroll
+            for (int j = j8; j < j8 + 8; j += 2) {
+              const float p0 = __uint_as_float(r[cur][j]) + b3[c0 + j];
+              const float p1 = __uint_as_float(r[cur][j + 1]) + b3[c0 + j + 1];
+              uint32_t hb;
+              if constexpr (IO::kStores) {
+                const float s0 = sigmoid_f(p0), s1 = sigmoid_f(p1);
+                hb = pack_bf16(p0 * s0, p1 * s1);
+                g[j - j8] = silu_grad_from(p0, s0);
+                g[j - j8 + 1] = silu_grad_from(p1, s1);
+              } else {
+                hb = pack_bf16(silu_f(p0), silu_f(p1));
+              }
+              hw[(j - j8) / 2] = hb;
+              z = fmaf(__uint_as_float(hb << 16), w4[c0 + j], z);
+              z = fmaf(__uint_as_float(hb & 0xFFFF0000u), w4[c0 + j + 1], z);
+            }
+            if constexpr (IO::kStores) {  // h3 into the (free) operand buffer, SiLU'(z3) out
+              if (grow < n) io.store_grad(2, grow, col0 + c0 + j8, g);
+              *reinterpret_cast<uint4*>(sa + canon_offset(trow, col0 + c0 + j8, H)) =
+                  make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            }
           }
+          if (c0 + 32 < CW) tmem_wait_ld();
         }
-        if (half == 1) spart[trow] = z;
+        if (cg > 0) spart[(cg - 1) * TILE + trow] = z;
         tc_fence_before();
         __syncthreads();  // TMEM reads done before the next tile's MMA; partials visible
+        if constexpr (IO::kStores) {
+          copy_out_transposed(sa, io.act_out(2), io.act_ld(), tile * TILE, n - tile * TILE, tid, NT);
+          __syncthreads();  // the operand is read before the next tile's features overwrite it
+        }
         const int row = tile * TILE + trow;
-        if (half == 0) io.emit(row, row < n, (z + spart[trow]) + b4);
+        if (cg == 0) {  // column groups summed in order
+#pragma unroll
+          for (int g = 1; g < CG; ++g) z += spart[(g - 1) * TILE + trow];
+          io.emit(row, row < n, z + b4);
+        }
       }
     }
   }
@@ -350,7 +473,7 @@ cudaError_t launch_mlp_tc(const MlpTcWeights& w, const IO& io, int n_cap, int* s
   if (e) return e;
   const int tiles = (n_cap + TILE - 1) / TILE;
   const int grid = tiles < num_sms ? tiles : num_sms;
-  mlp_tc_kernel<IO><<<grid, THREADS, SM_TOTAL, s>>>(w, io, status);
+  mlp_tc_kernel<IO><<<grid, 128 * IO::kColGroups, SM_TOTAL, s>>>(w, io, status);
   return cudaGetLastError();
 }
 

@@ -75,12 +75,16 @@ def test_forward_matches_oracle(sc, ctx, n):
     net.close()
 
 
-def test_gradients_match_oracle(sc, ctx):
+# one 4096-row batch (32 tiles); a ragged batch (a partial tile and a
+# partial 64-row chunk of the weight-gradient reduction); more tiles than
+# CTAs (each CTA reloads the W^T copies between its tiles)
+@pytest.mark.parametrize("n", [4096, 1000, 2 * 148 * 128 + 77])
+def test_gradients_match_oracle(sc, ctx, n):
     P = random_net(2)
     net = sc.Surrogate(ctx, seed=0)
     net.set(pack(P), P.mu, P.sigma, 0.0)
-    tg = synth.topdown_targets(seed=12, n=4096)
-    y = (np.random.default_rng(3).uniform(size=4096) < 0.5).astype(np.uint8)
+    tg = synth.topdown_targets(seed=12, n=n)
+    y = (np.random.default_rng(3).uniform(size=n) < 0.5).astype(np.uint8)
     g, loss = net.grads(torch.from_numpy(tg).cuda(), torch.from_numpy(y).cuda())
     g = g.cpu().numpy().astype(np.float64)
     L, dW, db = omlp.backward(P, tg, y.astype(np.float64), bf16=True)

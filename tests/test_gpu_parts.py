@@ -124,10 +124,12 @@ def test_part_arrays_validated(sc, ctx):
     bad_box = tiny_batch([[(0, 0, 0, 0.01)]], obbs=[[0.5, 0, 0, 0, 0, 0, 0, 1, 0.1, 0.1, 0.1, 0]], n_cand=2,
                          parts=part, obb_part=[3])
     dbb = sc.DeviceBatch(bad_box)
-    sc.collide(ctx, dbb, dbb.new_poses())
+    col, md, band = sc.collide(ctx, dbb, dbb.new_poses())
     with pytest.raises(sc.SceniError) as ei:
         ctx.synchronize()
     assert "device error code 8" in str(ei.value)
+    # and the candidates carry no verdict: NaN, banded, not colliding
+    assert torch.isnan(md).all() and (band == 1).all() and (col == 0).all()
     bad_rel = tiny_batch([[(0, 0, 0, 0.01)]] * 2, n_cand=2, rel=[0, synth.REL_INSIDE | (2 << 8)], parts=part)
     sc.sample_poses(ctx, sc.DeviceBatch(bad_rel), seed=1)
     with pytest.raises(sc.SceniError) as ei:

@@ -77,7 +77,7 @@ def test_noalloc_matches_collide_twice(sc):
 
 
 def test_noalloc_rejects_oversized_list(sc):
-    """More candidates than the fixed scratch is sized for: refused on the host."""
+    """More candidates than the per-call limit (the 32-bit work counter): refused on the host."""
     L = sc.lib()
     b = synth.tabletop(seed=0, n_cand=4)
     db = sc.DeviceBatch(b)
@@ -87,3 +87,23 @@ def test_noalloc_rejects_oversized_list(sc):
     st = L.sc_collide_noalloc(None, ctypes.byref(db.c), p, ctypes.c_void_p(dummy.data_ptr()), (1 << 30) + 1, 0, p, p, p)
     assert st == 1
     assert b"limit" in L.sc_last_error()
+
+
+def test_noalloc_marks_a_malformed_part_box(sc):
+    """A world box naming a part its template lacks: there is no status word
+    here, so the candidate itself must say it has no verdict (NaN, band 1,
+    not colliding), and the next call on well-formed input is unaffected."""
+    from scenes import tiny_batch
+    part = [[1.0, 0.0, 0.0, 0.0, 0.2, 0.0, 0.0, 0.0, 0.2, 0.2, 0.0, 0.0]]
+    bad = tiny_batch([[(0, 0, 0, 0.01)]], obbs=[[0.5, 0, 0, 0, 0, 0, 0, 1, 0.1, 0.1, 0.1, 0]], n_cand=3,
+                     parts=part, obb_part=[3])
+    db = sc.DeviceBatch(bad)
+    col, md, band = _noalloc(sc, db, db.new_poses())
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(md.cpu().numpy())) and np.all(band.cpu().numpy() == 1) and np.all(col.cpu().numpy() == 0)
+    good = tiny_batch([[(0, 0, 0, 0.01)]], obbs=[[0.5, 0, 0, 0, 0, 0, 0, 1, 0.1, 0.1, 0.1, 0]], n_cand=3,
+                      parts=part, obb_part=[0])
+    dg = sc.DeviceBatch(good)
+    col, md, band = _noalloc(sc, dg, dg.new_poses())
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(md.cpu().numpy())) and np.all(band.cpu().numpy() == 0)
