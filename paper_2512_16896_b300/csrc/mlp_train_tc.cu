@@ -32,7 +32,7 @@ namespace {
 // [64 column blocks][ld rows], so a warp's 32 consecutive rows touch 512
 // contiguous bytes.
 struct TrainIO {
-  static constexpr int kColGroups = 2;
+  static constexpr int kColGroups = 4;
   static constexpr bool kStores = true;
   const float* targets;
   const int32_t* index;  // batch row -> target (NULL: identity)
@@ -86,6 +86,8 @@ struct BwdArgs {
   int ld;
 };
 
+constexpr int BW_THREADS = 512;              // 16 warps: TMEM lane quarter x 4 column groups of 64
+constexpr int BW_CW = H / 4;
 constexpr int BW_W = 0;                      // [256][256] bf16 canonical weights, 128 KB
 constexpr int BW_A = BW_W + 131072;          // [128][256] bf16 canonical dA operand, 64 KB
 constexpr int BW_W4 = BW_A + 65536;          // W4 as f32, 1 KB
@@ -94,7 +96,7 @@ constexpr int BW_BAR = BW_DZ + 4 * TILE;     // 2 mbarriers
 constexpr int BW_TMEM = BW_BAR + 16;
 constexpr int BW_TOTAL = BW_TMEM + 16;
 
-// Epilogue of one backward contraction for one thread's row and column half:
+// Epilogue of one backward contraction for one thread's row and 64 columns:
 // dA = bf16(TMEM * SiLU'(z)) (zero on rows past the batch) into the shared
 // operand buffer, from where it is copied out feature-major.
 __device__ __forceinline__ void bwd_epilogue(uint32_t taddr, const float4* g, int ld, uint8_t* sa, int trow, int col0,
@@ -103,9 +105,9 @@ __device__ __forceinline__ void bwd_epilogue(uint32_t taddr, const float4* g, in
   tmem_ld32_async(taddr, r[0]);
   tmem_wait_ld();
 #pragma unroll
-  for (int c0 = 0; c0 < H / 2; c0 += 32) {
+  for (int c0 = 0; c0 < BW_CW; c0 += 32) {
     const int cur = (c0 / 32) & 1;
-    if (c0 + 32 < H / 2) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
+    if (c0 + 32 < BW_CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = col0 + c0 + q * 8;
@@ -119,16 +121,16 @@ __device__ __forceinline__ void bwd_epilogue(uint32_t taddr, const float4* g, in
                                  pack_bf16(v[4] * gb.x, v[5] * gb.y), pack_bf16(v[6] * gb.z, v[7] * gb.w));
       *reinterpret_cast<uint4*>(sa + canon_offset(trow, c, H)) = w;
     }
-    if (c0 + 32 < H / 2) tmem_wait_ld();
+    if (c0 + 32 < BW_CW) tmem_wait_ld();
   }
 }
 
-// Backward through the activations, one persistent CTA of 8 warps per SM over
+// Backward through the activations, one persistent CTA of 16 warps per SM over
 // 128-row tiles: dz = (sigmoid(z) - y) / n and the loss; dA3 = bf16(bf16(dz)
 // W4 * SiLU'(z3)) formed by the threads into the A operand; dH2 = dA3 W3 and
 // dH1 = dA2 W2 on the tensor cores (the W^T copies arrive by bulk copy, the
 // next one overlapping the epilogue).
-__global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* status) {
+__global__ void __launch_bounds__(BW_THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = A.n;
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* 
     mbar_init(bar_w, 1);
     mbar_init(bar_m, 1);
   }
-  for (int i = tid; i < H; i += THREADS) sw4[i] = __uint_as_float((uint32_t)__ldg(&A.W4[i]) << 16);
+  for (int i = tid; i < H; i += BW_THREADS) sw4[i] = __uint_as_float((uint32_t)__ldg(&A.W4[i]) << 16);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(H)
                  : "memory");
@@ -156,9 +158,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, cg = warp >> 2;
   const int trow = quarter * 32 + lane;
-  const int col0 = half * (H / 2);
+  const int col0 = cg * BW_CW;
   const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
   constexpr uint32_t idesc = make_idesc(TILE, H);
 
@@ -184,14 +186,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* 
       if (lane == 0) atomicAdd(A.loss_sum, loss * A.inv_n);
     }
     __syncthreads();
-    // ---- dA3 = bf16(bf16(dz) W4 * SiLU'(z3)): thread (row, column half)
+    // ---- dA3 = bf16(bf16(dz) W4 * SiLU'(z3)): thread (row, 64 columns)
     {
-      const int r = tid & (TILE - 1), cb = (tid >> 7) * (H / 2);
+      const int r = tid & (TILE - 1), cb = (tid >> 7) * BW_CW;
       const int grow = tile * TILE + r;
       const bool valid = grow < n;
       const float d = sdz[r];
 #pragma unroll 4
-      for (int c = cb; c < cb + H / 2; c += 8) {
+      for (int c = cb; c < cb + BW_CW; c += 8) {
         float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
         if (valid) {
           ga = A.g[2][(size_t)(c / 4) * A.ld + grow];
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* 
                  idesc, s > 0);
         tc_commit(bar_m);
       }
-      copy_out_transposed(sa, A.daT[2 - layer], A.ld, tile * TILE, n - tile * TILE, tid, THREADS);
+      copy_out_transposed(sa, A.daT[2 - layer], A.ld, tile * TILE, n - tile * TILE, tid, BW_THREADS);
       m_pending = true;
       ok = mbar_wait(bar_m, ph_m);
       if (ok) {
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* 
       __syncthreads();  // TMEM read and the operand written before the next MMA or copy
     }
     if (!ok) break;
-    copy_out_transposed(sa, A.daT[0], A.ld, tile * TILE, n - tile * TILE, tid, THREADS);
+    copy_out_transposed(sa, A.daT[0], A.ld, tile * TILE, n - tile * TILE, tid, BW_THREADS);
     __syncthreads();  // the operand is read before the next tile's dA3 overwrites it
   }
   if (!ok) {
@@ -481,8 +483,12 @@ __global__ void mlp_grad_finish_kernel(WgArgs G, FinishArgs F) {
       const float* part = jb == 0 ? G.job[0].part : jb == 1 ? G.job[1].part : G.job[2].part;
       const int o = idx / N, i = idx % N;
       if (jb == 0 && i >= 9) continue;
+      float v[16];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) v[s] = s < G.S ? part[((size_t)s * H + o) * N + i] : 0.f;  // loads in flight together
       float acc = 0.f;
-      for (int s = 0; s < G.S; ++s) acc += part[((size_t)s * H + o) * N + i];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) acc += v[s];  // split order
       if (jb == 0) F.dW[0][o * 9 + i] = acc;
       else F.dW[jb][o * H + i] = acc;
     }
@@ -578,7 +584,7 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     A.ld = L.ld;
     if ((e = cudaFuncSetAttribute(mlp_tc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BW_TOTAL))) return e;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
-    mlp_tc_bwd_kernel<<<grid, THREADS, BW_TOTAL, s>>>(A, L.status);
+    mlp_tc_bwd_kernel<<<grid, BW_THREADS, BW_TOTAL, s>>>(A, L.status);
     if ((e = cudaGetLastError())) return e;
   }
   // ---- weight gradients: dW1 = dA1^T X, dW2 = dA2^T H1, dW3 = dA3^T H2
@@ -608,7 +614,7 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     F.db4 = L.db4;
     F.h3T = L.hT[2];
     F.dz = L.dz;
-    F.red_blocks = num_sms;
+    F.red_blocks = 2 * num_sms;
     const int bias_blocks = (4 * H + 1 + 7) / 8;  // one warp per output, 8 warps per block
     mlp_grad_finish_kernel<<<F.red_blocks + bias_blocks, 256, 0, s>>>(G, F);
     if ((e = cudaGetLastError())) return e;
