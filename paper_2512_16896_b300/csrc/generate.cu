@@ -879,7 +879,7 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
 // rows are the round's reach queue (grasp targets formed by
 // reach_targets_kernel), and each logit is decided at once (logit >= tau).
 struct GateIO {
-  static constexpr int kColGroups = 4;
+  static constexpr int kColGroups = 2;  // 8 warps: leaves room on the SM for the IK blocks of the other side stream
   static constexpr bool kStores = false;
   ReachArgs A;
   __device__ int rows() const { return *(volatile const int*)A.n_reach; }
