@@ -755,7 +755,7 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
             # the project's autotuner picks the launch shape on a strided sample
             # of the LPT list (untimed); the default shape is timed beside it
             shape, tune = autotune.tune_collide(ctx, db, batch, poses, order, decide=bool(mode))
-            cfg = tuple(shape) + (mode,)
+            cfg = tuple(shape)  # (threads, a_per_lane, seg_len, ctas_per_sm, decide_only, stage_bulk)
 
             def timed_collide(config):
                 ms_, work_ = [], []
@@ -778,7 +778,8 @@ def kernel_suite_collide(sc, ctx, dev, peak_ops, out, want, shelf_cand):
                            for p, q, r in work[2:]])
             out[key] = {"ms": float(np.mean(ms)), "candidates_per_s": batch.n_cand / t,
                         "launch_shape": {"threads": shape[0], "a_per_lane": shape[1], "seg_len": shape[2],
-                                         "ctas_per_sm": shape[3], "tuned_on": tune["sample"]},
+                                         "ctas_per_sm": shape[3], "stage_bulk": shape[5], "tuned_on": tune["sample"],
+                                         "top": tune["top"][:4]},
                         "ms_default_shape": float(np.mean(ms_def)),
                         "evaluated_pairs": float(np.mean([w[0] for w in work[2:]])),
                         "box_pairs": float(np.mean([w[1] for w in work[2:]])),

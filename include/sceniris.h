@@ -256,10 +256,17 @@ sc_status sc_sample_parts(sc_ctx* ctx, const sc_scene_batch* batch, uint64_t see
  * collision); collide and band are the same as in mode 0. min_dist is the
  * exact minimum inside the band (|d| <= 1e-5 m); a certain collision reports
  * some distance below -1e-5 m, a clear candidate some distance above 1e-5 m
- * or FLT_MAX. */
+ * or FLT_MAX.
+ * stage_bulk: 0 = each lane loads the local spheres it transforms; 1 = one
+ * thread copies the candidate's whole local sphere block (contiguous per
+ * template) into shared memory with a bulk asynchronous copy
+ * (cp.async.bulk, completion on an mbarrier) and the lanes transform it in
+ * place. Results are identical; only the time differs (sc_collide only;
+ * sc_generate ignores it). */
 typedef struct {
   int32_t threads, a_per_lane, seg_len, ctas_per_sm;
   int32_t decide_only;
+  int32_t stage_bulk;
 } sc_collide_config;
 
 /* Collision check of the listed candidates (Sec. IV-D; the paper uses cuRobo

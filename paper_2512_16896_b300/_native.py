@@ -97,10 +97,11 @@ def train_params(epochs=4, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8
 
 
 class CollideConfig(ctypes.Structure):
-    _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32), ("decide_only", I32)]
+    _fields_ = [("threads", I32), ("a_per_lane", I32), ("seg_len", I32), ("ctas_per_sm", I32), ("decide_only", I32),
+                ("stage_bulk", I32)]
 
     def as_tuple(self):
-        return (self.threads, self.a_per_lane, self.seg_len, self.ctas_per_sm, self.decide_only)
+        return (self.threads, self.a_per_lane, self.seg_len, self.ctas_per_sm, self.decide_only, self.stage_bulk)
 
 
 # name -> (restype, argtypes); mirrors include/sceniris.h

@@ -72,8 +72,12 @@ def _load():
 def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tensor, order: torch.Tensor,
                  first_new: int = 0, space=None, sample: int = 16384, reps: int = 2, use_cache: bool = True,
                  verbose: bool = False, decide: bool = False):
-    """Best (threads, a_per_lane, seg_len, ctas_per_sm) for this batch shape, in
-    exact-minimum mode or (decide) decide-only mode."""
+    """Best launch configuration for this batch shape, in exact-minimum mode
+    or (decide) decide-only mode: the fastest (threads, a_per_lane, seg_len,
+    ctas_per_sm) of the space, then that shape with the local spheres staged
+    by per-lane loads or by one bulk copy, whichever is faster. Returns the
+    full sc_collide_config tuple (threads, a_per_lane, seg_len, ctas_per_sm,
+    decide_only, stage_bulk) and the cache entry."""
     dev = torch.cuda.get_device_name(ctx.device)
     key = f"{dev}|{shape_key(batch, first_new)}|{'decide' if decide else 'exact'}"
     cache = _load()
@@ -86,24 +90,39 @@ def tune_collide(ctx: nat.Context, db: nat.DeviceBatch, batch, poses: torch.Tens
         sub = order[idx].contiguous()
     else:
         sub = order
+    mode = 1 if decide else 0
+
+    def time_cfg(full):
+        nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     results = []
     for cfg in space:
+        full = tuple(cfg)[:4] + (mode, 0)
         try:
-            full = tuple(cfg) + (1 if decide else 0,)
-            nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)  # warm
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(ctx.stream)
-            for _ in range(reps):
-                nat.collide(ctx, db, poses, active=sub, first_new=first_new, config=full)
-            e1.record(ctx.stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / reps
+            ms = time_cfg(full)
         except nat.SceniError:
             continue  # shape not launchable for this batch (e.g. shared memory)
-        results.append((ms, cfg))
+        results.append((ms, full))
         if verbose:
-            print(f"  {cfg}: {ms:.3f} ms", flush=True)
+            print(f"  {full}: {ms:.3f} ms", flush=True)
+    if results:
+        best = min(results)[1]
+        bulk = best[:5] + (1,)
+        try:
+            ms = time_cfg(bulk)
+            results.append((ms, bulk))
+            if verbose:
+                print(f"  {bulk}: {ms:.3f} ms", flush=True)
+        except nat.SceniError:
+            pass
     return _store(cache, key, results, int(sub.numel()))
 
 

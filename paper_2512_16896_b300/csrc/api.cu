@@ -268,7 +268,7 @@ sc_status sc_sample_parts(sc_ctx* ctx, const sc_scene_batch* batch, uint64_t see
 // The generation step culls spheres before its pair sweep, so its register
 // blocks are small; one A sphere per lane also keeps its instruction
 // footprint smallest (the step is bound by instruction fetch, not the FMA pipe).
-static const sc_collide_config kDefaultGenerate = {256, 1, 256, 4, 1};
+static const sc_collide_config kDefaultGenerate = {256, 1, 256, 4, 1, 0};
 
 sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* poses, const int32_t* active,
                         int32_t n_active, int32_t first_new_obj, const sc_collide_config* config, uint8_t* collide,
@@ -289,6 +289,7 @@ sc_status sc_collide_ex(sc_ctx* ctx, const sc_scene_batch* batch, const float* p
     if (config->seg_len) cfg.seg_len = config->seg_len;
     if (config->ctas_per_sm) cfg.ctas_per_sm = config->ctas_per_sm;
     cfg.decide_only = config->decide_only;
+    cfg.stage_bulk = config->stage_bulk;
   }
   sc::CollideLaunch a;
   a.poses = poses;

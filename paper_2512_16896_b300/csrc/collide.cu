@@ -80,6 +80,7 @@ struct CtaShared {
   int r2max_key, rmax_key;
   int hit;                 // DECIDE: a certain collision was found
   int bad_box;             // a staged box names a part its template lacks
+  unsigned long long bar;  // mbarrier of the bulk copy of the local spheres
   float warp_min[32];
 };
 
@@ -114,13 +115,15 @@ __device__ __forceinline__ void stage_objects(const sc_scene_batch& b, const flo
 // per object) take one object at a time, so a sphere's object needs no search
 // and each object's pose is read once per group.
 __device__ __forceinline__ void stage_spheres(const sc_scene_batch& b, int s0, int n, int S, const Smem& sm,
-                                              CtaShared& sh, int tid, int nthr, int lane) {
+                                              CtaShared& sh, int tid, int nthr, int lane, bool in_smem) {
   const float4 ref = sm.opose[0];
   float r2max = 0.f, rmx = 0.f;
   const int mean = S / n;
   const int gl = mean > 16 ? 32 : mean > 8 ? 16 : 8;
   const int ngrp = nthr / gl;
-  const float4* local = reinterpret_cast<const float4*>(b.sph_local) + s0;
+  // the local spheres: in global memory, or already copied into W (in_smem;
+  // each sphere is then read and overwritten by the same lane)
+  const float4* local = in_smem ? sm.W : reinterpret_cast<const float4*>(b.sph_local) + s0;
 #pragma unroll 1
   for (int k0 = 0; k0 < n; k0 += ngrp) {  // same trip count in every lane (group shuffles below)
     const int k = k0 + tid / gl;
@@ -132,7 +135,7 @@ __device__ __forceinline__ void stage_spheres(const sc_scene_batch& b, int s0, i
       const float tx = p.x - ref.x, ty = p.y - ref.y, tz = p.z - ref.z;
 #pragma unroll 2
       for (int q = lo + (tid & (gl - 1)); q < hi; q += gl) {
-        const float4 l = __ldg(local + q);
+        const float4 l = in_smem ? local[q] : __ldg(local + q);
         const float x = tx + (sc2.y * l.x - sc2.x * l.y);
         const float y = ty + (sc2.x * l.x + sc2.y * l.y);
         const float z = tz + l.z;
@@ -495,10 +498,41 @@ __device__ __forceinline__ float pair_units(const Smem& sm, CtaShared& sh, int f
   return m;
 }
 
+// Bulk asynchronous copy of the local sphere block into shared memory: one
+// thread arms the mbarrier with the byte count and issues the copy; every
+// thread waits for the phase with a cycle budget (false: it ran out).
+__device__ __forceinline__ void bulk_stage_issue(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  for (uint32_t off = 0; off < bytes; off += 32768) {
+    const uint32_t n = bytes - off < 32768 ? bytes - off : 32768;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d + off),
+                 "l"(static_cast<const char*>(src) + off), "r"(n), "r"(b)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ bool bulk_stage_wait(unsigned long long* bar, uint32_t parity) {
+  const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 4000000000LL) return false;  // about 2 s
+  }
+}
+
 struct KArgs {
   sc_scene_batch b;
   CollideLaunch a;
   int seg_len;
+  int stage_bulk;  // the local sphere block arrives by one bulk copy
 };
 
 // MINB = 2 caps a 512-thread instantiation at 64 registers (four 256-thread
@@ -517,8 +551,17 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
 
   // the next candidate is claimed while this one is reduced: thread 0 stores
   // it in sh.item just before the candidate's last barrier
-  if (tid == 0) sh.item = (int)atomicAdd(a.counter, 1u);
+  if (tid == 0) {
+    sh.item = (int)atomicAdd(a.counter, 1u);
+    if (K.stage_bulk) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(&sh.bar)))
+                   : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   __syncthreads();
+  uint32_t bulk_phase = 0;
   for (;;) {
     const int item = sh.item;
     if (item >= a.n_items) break;
@@ -561,6 +604,9 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
       continue;
     }
     const int f = a.first_new;
+    // this thread's generic accesses of W (the previous candidate) are
+    // ordered before the bulk copy that overwrites it (issued after a barrier)
+    if (K.stage_bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     stage_objects(b, reinterpret_cast<const float4*>(a.poses), pbase, o0, s0, nt, sm, tid, nthr);
     if (tid == 0) {
       sh.best_key = float_key(kFarSentinel);
@@ -570,7 +616,22 @@ __global__ void __launch_bounds__(MAXT, MINB) collide_kernel(KArgs K) {
       sh.bad_box = 0;
     }
     __syncthreads();
-    stage_spheres(b, s0, nt, S, sm, sh, tid, nthr, lane);
+    if (K.stage_bulk) {
+      if (tid == 0) bulk_stage_issue(sm.W, reinterpret_cast<const float4*>(b.sph_local) + s0, 16u * (uint32_t)S, &sh.bar);
+      const bool landed = bulk_stage_wait(&sh.bar, bulk_phase);
+      if (!__syncthreads_and(landed)) {  // the copy did not arrive: no verdict, stop this CTA
+        if (tid == 0) {
+          latch_error(a.status, kDevTimeout);
+          a.collide[item] = 0;
+          a.min_dist[item] = __int_as_float(0x7FC00000);
+          a.band[item] = 1;
+        }
+        bulk_stage_wait(&sh.bar, bulk_phase);  // do not leave the copy in flight into freed shared memory
+        break;
+      }
+      bulk_phase ^= 1u;
+    }
+    stage_spheres(b, s0, nt, S, sm, sh, tid, nthr, lane, K.stage_bulk != 0);
     stage_boxes(b, t, c, bx0, nobb, sm, tid, nthr, a.status, &sh.bad_box);
     __syncthreads();
     if (*(volatile int*)&sh.bad_box) {  // a malformed part box: no verdict, marked like the checks above
@@ -688,7 +749,7 @@ cudaError_t launch_mode(const KArgs& K, const sc_collide_config& cfg, size_t sme
 // flight (tabletop batch, 8 x 16 spheres: 2.3 ms against 9.8 ms exact, 1.2
 // against 2.9 ms decide, for 262,144 candidates).
 sc_collide_config default_collide_config(const sc_scene_batch& b) {
-  return b.max_sph <= 256 ? sc_collide_config{128, 1, 32, 8, 0} : sc_collide_config{256, 4, 256, 4, 0};
+  return b.max_sph <= 256 ? sc_collide_config{128, 1, 32, 8, 0, 0} : sc_collide_config{256, 4, 256, 4, 0, 0};
 }
 
 size_t collide_smem_bytes(const sc_scene_batch& b, const sc_collide_config& cfg) {
@@ -703,6 +764,7 @@ const char* check_collide_config(const sc_collide_config& cfg) {
   if (cfg.seg_len < 8 || cfg.seg_len > 4096 || cfg.seg_len % 8) return "seg_len must be a multiple of 8 in 8..4096";
   if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 8) return "ctas_per_sm must be in 1..8";
   if (cfg.decide_only != 0 && cfg.decide_only != 1) return "decide_only must be 0 or 1";
+  if (cfg.stage_bulk != 0 && cfg.stage_bulk != 1) return "stage_bulk must be 0 or 1";
   return nullptr;
 }
 
@@ -717,7 +779,7 @@ cudaError_t launch_collide(const sc_scene_batch& b, const CollideLaunch& a, cons
   if (a.stats && (e = cudaMemsetAsync(a.stats, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if (a.stats && (e = cudaMemsetAsync(a.stats + 7, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if (a.n_items <= 0) return cudaSuccess;
-  KArgs K{b, a, cfg.seg_len};
+  KArgs K{b, a, cfg.seg_len, cfg.stage_bulk};
   return cfg.decide_only ? launch_mode<true>(K, cfg, smem, num_sms, s) : launch_mode<false>(K, cfg, smem, num_sms, s);
 }
 

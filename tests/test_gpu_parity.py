@@ -301,6 +301,28 @@ def test_collide_configs_bit_identical(sc, ctx, cfg):
     assert torch.equal(ref[1], got[1]) and torch.equal(ref[0], got[0]) and torch.equal(ref[2], got[2])
 
 
+@pytest.mark.parametrize("make,first_new", [
+    (lambda: synth.shelf(seed=12, n_cand=300, n_obj=12, n_sph=40, n_obb=6), 0),
+    (lambda: synth.ragged(seed=13, n_templates=24, cand_per_template=5), 2),
+    (lambda: synth.tabletop(seed=14, n_cand=200), 0),
+])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_collide_bulk_staging_bit_identical(sc, ctx, make, first_new, mode):
+    """The local spheres copied in one bulk asynchronous copy per candidate
+    (stage_bulk = 1) give exactly what per-lane loads give, in both modes,
+    over consecutive candidates of one template and of different ones."""
+    b = make()
+    db = sc.DeviceBatch(b)
+    poses = torch.from_numpy(synth.random_poses(b, seed=15, spread=0.5)).cuda()
+    order = torch.from_numpy(sc.order_by_work(b)).cuda()
+    for shape in ((0, 0, 0, 0), (128, 2, 64, 2)):
+        ref = sc.collide(ctx, db, poses, active=order, first_new=first_new, config=shape + (mode, 0))
+        got = sc.collide(ctx, db, poses, active=order, first_new=first_new, config=shape + (mode, 1))
+        ctx.synchronize()
+        for x, y in zip(ref, got):
+            assert torch.equal(x, y)
+
+
 def test_collide_lpt_active_list_and_empty(sc, ctx):
     b = synth.ragged(seed=10, n_templates=30, cand_per_template=5)
     db = sc.DeviceBatch(b)
