@@ -65,6 +65,7 @@ struct GenStepArgs {
   int32_t* list_gen;       // the next round's candidates (retry, or the next object)
   int* n_gen;
   int32_t* list_reach;     // collision-free tries of reach-flagged objects (NULL: no reach stage)
+  float* targets;          // [cap][12] their grasp targets, by position in list_reach
   int* n_reach;
   float4* poses;
   uint8_t* valid;
@@ -545,8 +546,35 @@ __device__ __forceinline__ int check_object(const GenStepArgs& g, const TmplInfo
 // Routing of a finished try (warp-uniform).
 enum Route : int { kRouteNone = 0, kRouteReach = 1, kRouteGen = 2 };
 
+// Top-down grasp of candidate c's current object k = kc[c] (Sec. IV-E):
+// position = top centre of its box, tool z = -world z, tool x along the
+// object's yaw; expressed in the template's robot base frame (x, y, z, yaw).
+// R row-major, then p, into o[12].
+__device__ __forceinline__ void grasp_target_at(const sc_scene_batch& b, const int32_t* cand_t, const TmplInfo* tinfo,
+                                                const uint8_t* kc, const float4* poses, int c, float o[12]) {
+  const int t = __ldg(&cand_t[c]);
+  const TmplInfo& T = tinfo[t];
+  const int k = kc[c];
+  const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * T.nt;
+  const float4 p = poses[pbase + k];
+  const float hz = __ldg(&b.obj_half[4 * (T.o0 + k) + 2]);
+  const float4 base = __ldg(reinterpret_cast<const float4*>(b.tmpl_base) + t);
+  float sb, cb, sp, cp;
+  sincosf(base.w, &sb, &cb);
+  sincosf(p.w - base.w, &sp, &cp);
+  const float wx = p.x - base.x, wy = p.y - base.y, wz = p.z + hz - base.z;
+  o[0] = cp; o[1] = sp; o[2] = 0.f;
+  o[3] = sp; o[4] = -cp; o[5] = 0.f;
+  o[6] = 0.f; o[7] = 0.f; o[8] = -1.f;
+  o[9] = cb * wx + sb * wy;
+  o[10] = -sb * wx + cb * wy;
+  o[11] = wz;
+}
+
 // Appends the warp's pending routed candidates (lane i holds entry i < npend)
-// to their lists: one atomic per list and flush instead of one per try.
+// to their lists: one atomic per list and flush instead of one per try. A
+// candidate sent to the reach queue also gets its grasp target at the same
+// position (its pose was written by this warp before the flush).
 __device__ __forceinline__ void flush_routes(const GenStepArgs& g, int pend_c, int pend_r, int npend, int lane) {
 #pragma unroll
   for (int d = kRouteReach; d <= kRouteGen; ++d) {
@@ -559,7 +587,18 @@ __device__ __forceinline__ void flush_routes(const GenStepArgs& g, int pend_c, i
     int base = 0;
     if (lane == leader) base = atomicAdd(cnt, __popc(mask));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (mine) list[base + __popc(mask & ((1u << lane) - 1u))] = pend_c;
+    if (mine) {
+      const int row = base + __popc(mask & ((1u << lane) - 1u));
+      list[row] = pend_c;
+      if (d == kRouteReach) {
+        float o[12];
+        grasp_target_at(g.b, g.cand_t, g.tinfo, g.st.kc, g.poses, pend_c, o);
+        float4* dst = reinterpret_cast<float4*>(g.targets + 12 * (size_t)row);
+        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+      }
+    }
   }
 }
 
@@ -817,27 +856,6 @@ __device__ __forceinline__ void reach_advance(const ReachArgs& A, int c, int k, 
   }
 }
 
-// Grasp target of the candidate's current object k (see reach_targets_kernel),
-// written to o[12].
-__device__ __forceinline__ void grasp_target(const ReachArgs& A, int c, float o[12]) {
-  const int t = __ldg(&A.cand_t[c]);
-  const TmplInfo& T = A.tinfo[t];
-  const int k = A.st.kc[c];
-  const int64_t pbase = T.pose0 + (int64_t)(c - T.cand0) * T.nt;
-  const float4 p = A.poses[pbase + k];
-  const float hz = __ldg(&A.b.obj_half[4 * (T.o0 + k) + 2]);
-  const float4 base = __ldg(reinterpret_cast<const float4*>(A.b.tmpl_base) + t);
-  float sb, cb, sp, cp;
-  sincosf(base.w, &sb, &cb);
-  sincosf(p.w - base.w, &sp, &cp);
-  const float wx = p.x - base.x, wy = p.y - base.y, wz = p.z + hz - base.z;
-  o[0] = cp; o[1] = sp; o[2] = 0.f;
-  o[3] = sp; o[4] = -cp; o[5] = 0.f;
-  o[6] = 0.f; o[7] = 0.f; o[8] = -1.f;
-  o[9] = cb * wx + sb * wy;
-  o[10] = -sb * wx + cb * wy;
-  o[11] = wz;
-}
 
 // A gate's decision on reach-queue entry `row` (warp-uniform call; `valid`
 // false on lanes past the queue): a pass goes to the IK list, a rejection
@@ -876,8 +894,8 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
 }
 
 // The learned gate's decision fused into the tensor-core forward pass: its
-// rows are the round's reach queue (grasp targets formed by
-// reach_targets_kernel), and each logit is decided at once (logit >= tau).
+// rows are the round's reach queue (grasp targets written by the generation
+// round), and each logit is decided at once (logit >= tau).
 struct GateIO {
   static constexpr int kColGroups = 2;  // 8 warps: leaves room on the SM for the IK blocks of the other side stream
   static constexpr bool kStores = false;
@@ -896,18 +914,11 @@ struct GateIO {
   __device__ int act_ld() const { return 0; }
 };
 
-// Top-down grasp of the candidate's current object k: position = top centre
-// of its box, tool z = -world z, tool x along the object's yaw; expressed in
-// the template's robot base frame (x, y, z, yaw). R row-major, then p.
-// With a map gate, each target's map score is decided here as well (score
-// >= the map's threshold), warps walking the queue 32 entries at a time.
-__global__ void reach_targets_kernel(ReachArgs A) {
+// The 4D reachability map's decision on the round's reach queue (the grasp
+// targets were written by the generation round): score >= the map's
+// threshold passes to IK, warps walking the queue 32 entries at a time.
+__global__ void reach_map_gate_kernel(ReachArgs A) {
   const int n = *(volatile const int*)A.n_reach;
-  if (!A.map_counts) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      grasp_target(A, A.list_reach[i], A.targets + 12 * (size_t)i);
-    return;
-  }
   const int lane = threadIdx.x & 31;
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + lane;
@@ -915,10 +926,9 @@ __global__ void reach_targets_kernel(ReachArgs A) {
     bool pass = false;
     if (valid) {
       float o[12];
-      grasp_target(A, A.list_reach[i], o);
-      float* t = A.targets + 12 * (size_t)i;
+      const float* t = A.targets + 12 * (size_t)i;
 #pragma unroll
-      for (int j = 0; j < 12; ++j) t[j] = o[j];
+      for (int j = 0; j < 12; ++j) o[j] = t[j];
       pass = (int)rmap_score(A.map_counts, rmap_cell(A.map_grid, o)) >= A.map_tau;
     }
     gate_route(A, i, valid, pass);
@@ -1343,6 +1353,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     g.n_gen = cnt_gen + i + 1;
     g.list_reach = Q[i % 2];
     g.n_reach = cnt_reach + i;
+    g.targets = targets[i % 2];  // free: this round waited for the reach stage of round i - 2
     g.counter = counters + i;
     if (a.timer) a.timer->begin(0, s);
     switch (cfg.a_per_lane) {
@@ -1364,7 +1375,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.n_gen = cnt_gen + i + 2;
     ra.claim = counters + NRmax + 1 + i;
     if (a.timer) a.timer->begin(1, sr);
-    reach_targets_kernel<<<small_blocks, 256, 0, sr>>>(ra);
+    if (a.map_counts) reach_map_gate_kernel<<<small_blocks, 256, 0, sr>>>(ra);
     if (a.gate) {  // gate forward pass and decision in one launch
       e = launch_mlp_tc(gate_w, GateIO{ra}, n, a.status, num_sms, sr);
       if (e != cudaSuccess) return e;

@@ -39,30 +39,36 @@ struct IkArgs {
 // T_i = Rz(q_i) Tz(d_i) Tx(a_i) Rx(alpha_i) acts on the frame's columns
 // c0, c1, c2 in three steps: Rz turns c0, c1 by q; the translation adds
 // a c0 + d c2; Rx turns c1, c2 by alpha (4 + 2 + 4 multiply-adds per row).
+// Rows 0 and 1 go through the packed two-lane FP32 instructions (each
+// multiply-add above is one instruction for both rows), row 2 is scalar;
+// every product rounds as its scalar form.
 __device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3], float p[7][3], float R[9],
                                    float t[3]) {
-  R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
-  R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
-  R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
-  t[0] = t[1] = t[2] = 0.f;
+  float2 c0 = make_float2(1.f, 0.f), c1 = make_float2(0.f, 1.f), c2 = make_float2(0.f, 0.f), t01 = make_float2(0.f, 0.f);
+  float c0z = 0.f, c1z = 0.f, c2z = 1.f, tz = 0.f;  // row 2
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
-    z[i][0] = R[2]; z[i][1] = R[5]; z[i][2] = R[8];
-    p[i][0] = t[0]; p[i][1] = t[1]; p[i][2] = t[2];
+    z[i][0] = c2.x; z[i][1] = c2.y; z[i][2] = c2z;
+    p[i][0] = t01.x; p[i][1] = t01.y; p[i][2] = tz;
     float st, ct;
     sincos_cw(q[i], &st, &ct);
     const float ca = A.ca[i], sa = A.sa[i], a = A.a[i], d = A.d[i];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
-      const float n0 = fmaf(r1, st, r0 * ct);   // Rz: c0' = ct c0 + st c1
-      const float n1 = fmaf(r1, ct, -r0 * st);  //     c1' = ct c1 - st c0
-      t[r] = fmaf(n0, a, fmaf(r2, d, t[r]));    // Tz Tx: t += a c0' + d c2
-      R[3 * r] = n0;
-      R[3 * r + 1] = fmaf(r2, sa, n1 * ca);     // Rx: c1'' = ca c1' + sa c2
-      R[3 * r + 2] = fmaf(r2, ca, -n1 * sa);    //     c2'' = ca c2 - sa c1'
-    }
+    const float2 n0 = __ffma2_rn(c1, make_float2(st, st), __fmul2_rn(c0, make_float2(ct, ct)));
+    const float2 n1 = __ffma2_rn(c1, make_float2(ct, ct), __fmul2_rn(c0, make_float2(-st, -st)));
+    t01 = __ffma2_rn(n0, make_float2(a, a), __ffma2_rn(c2, make_float2(d, d), t01));
+    c0 = n0;
+    c1 = __ffma2_rn(c2, make_float2(sa, sa), __fmul2_rn(n1, make_float2(ca, ca)));
+    c2 = __ffma2_rn(c2, make_float2(ca, ca), __fmul2_rn(n1, make_float2(-sa, -sa)));
+    const float m0 = fmaf(c1z, st, c0z * ct), m1 = fmaf(c1z, ct, -c0z * st);
+    tz = fmaf(m0, a, fmaf(c2z, d, tz));
+    c0z = m0;
+    c1z = fmaf(c2z, sa, m1 * ca);
+    c2z = fmaf(c2z, ca, -m1 * sa);
   }
+  R[0] = c0.x; R[1] = c1.x; R[2] = c2.x;
+  R[3] = c0.y; R[4] = c1.y; R[5] = c2.y;
+  R[6] = c0z; R[7] = c1z; R[8] = c2z;
+  t[0] = t01.x; t[1] = t01.y; t[2] = tz;
 }
 
 struct Target {
