@@ -169,7 +169,6 @@ struct TrainTcLaunch {
   float* logits;         // [n]
   uint16_t* x16T;        // [16][ld]
   uint16_t* hT[3];       // [256][ld]
-  float4* g[3];          // SiLU'(z): [64][ld] float4 blocks of 4 features
   uint16_t* daT[3];      // [256][ld]
   float* dz;             // [n]
   float* loss_sum;       // zeroed by the caller

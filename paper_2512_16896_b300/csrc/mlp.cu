@@ -247,13 +247,12 @@ cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int
 }
 
 // Batch buffers of Bcap rows: the forward caches (standardised input and
-// activations feature-major, SiLU'(z) in blocks of 4 features), the dL/da
-// (feature-major), dz, logits, the loss word and the weight gradients'
-// partial sums.
+// activations, feature-major), the dL/da (feature-major), dz, logits, the
+// loss word and the weight gradients' partial sums. (SiLU'(z) stays in the
+// tensor memory of the fused forward-backward kernel.)
 struct TrainViews {
   uint16_t* x16T;   // [KIN][Bcap]
   uint16_t* hT[3];  // [H][Bcap]
-  float4* g[3];     // SiLU'(z): [H / 4][Bcap]
   uint16_t* daT[3]; // [H][Bcap]
   float* dz;        // [Bcap]
   float* logits;    // [Bcap]
@@ -265,7 +264,7 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 static size_t train_bytes(int Bcap) {
   const size_t Bp = (size_t)Bcap;
-  return align256(Bp * KIN * 2) + 3 * align256(Bp * H * 2) + 3 * align256(Bp * H * 4) + 3 * align256(Bp * H * 2) +
+  return align256(Bp * KIN * 2) + 3 * align256(Bp * H * 2) + 3 * align256(Bp * H * 2) +
          2 * align256(Bp * 4) + 256 + align256(mlp_train_tc_part_bytes(Bcap));
 }
 
@@ -275,7 +274,6 @@ static TrainViews carve(MlpState* S, int Bcap) {
   TrainViews v;
   v.x16T = reinterpret_cast<uint16_t*>(take((size_t)Bcap * KIN * 2));
   for (int l = 0; l < 3; ++l) v.hT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
-  for (int l = 0; l < 3; ++l) v.g[l] = reinterpret_cast<float4*>(take((size_t)Bcap * H * 4));
   for (int l = 0; l < 3; ++l) v.daT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
   v.dz = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.logits = reinterpret_cast<float*>(take((size_t)Bcap * 4));
@@ -320,7 +318,6 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
   L.x16T = v.x16T;
   for (int l = 0; l < 3; ++l) {
     L.hT[l] = v.hT[l];
-    L.g[l] = v.g[l];
     L.daT[l] = v.daT[l];
   }
   L.dz = v.dz;

@@ -3,17 +3,15 @@
 // gate of Sec. IV-E, as three contractions per layer, all bf16 x bf16 -> f32
 // in TMEM with operands in the canonical no-swizzle K-major layout:
 //
-//   forward   Z_l  = H_{l-1} W_l^T        mlp_tc_kernel<TrainIO> (the inference
-//                                          kernel, which here also keeps SiLU'(Z_l)
-//                                          and, feature-major, every bf16
-//                                          activation)
-//   backward  dH_l = dA_{l+1} W_{l+1}     mlp_tc_bwd_kernel, B = W^T copies
-//             dA_l = bf16(dH_l * SiLU'(Z_l))
+//   forward   Z_l  = H_{l-1} W_l^T        mlp_train_fb_kernel, one cluster of
+//   backward  dH_l = dA_{l+1} W_{l+1}     four CTAs per 128-row tile, each CTA
+//             dA_l = bf16(dH_l * SiLU'(Z_l))   64 of the 256 features; B = W^T
+//                                          copies in the backward pass
 //   weights   dW_l = dA_l^T H_{l-1}       mlp_tc_wgrad_kernel: M = output
 //                                          features (two 128-row tiles), N = input
 //                                          features, K = the batch, split over
 //                                          CTAs; partial sums added in split
-//                                          order by mlp_wgrad_reduce_kernel
+//                                          order by mlp_grad_finish_kernel
 //
 // Rounding points as in the FP64 reference: standardised input, SiLU outputs,
 // weight copies, dL/dz before it meets W4 and every dL/da in bf16; biases,
@@ -26,244 +24,448 @@ namespace sc {
 
 namespace {
 
-// Forward rows of a training batch: targets through an index, and the caches
-// the backward pass and the weight gradients read.
-// SiLU'(z) of every activation in a tile layout: float4 blocks of 4 columns,
-// [64 column blocks][ld rows], so a warp's 32 consecutive rows touch 512
-// contiguous bytes.
-struct TrainIO {
-  static constexpr int kColGroups = 4;
-  static constexpr bool kStores = true;
-  const float* targets;
-  const int32_t* index;  // batch row -> target (NULL: identity)
-  int n;
-  float* logits;         // [n]
-  uint16_t* x16T;        // [16][ld] standardised input, bf16, feature-major
-  uint16_t* hT[3];       // [256][ld] h1, h2, h3, bf16, feature-major
-  float4* g[3];          // [64][ld] SiLU'(z1), SiLU'(z2), SiLU'(z3)
-  int ld;
-  __device__ int rows() const { return n; }
-  __device__ void features(int row, float f[9]) const {
-    const int ti = index ? __ldg(&index[row]) : row;
-    const float* t = targets + 12 * (size_t)ti;
-    f[0] = __ldg(t + 9); f[1] = __ldg(t + 10); f[2] = __ldg(t + 11);
-    f[3] = __ldg(t + 0); f[4] = __ldg(t + 3); f[5] = __ldg(t + 6);
-    f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
-  }
-  __device__ void emit(int row, bool valid, float logit) const {
-    if (valid) logits[row] = logit;
-  }
-  __device__ void store_input(int row, const uint32_t* xb) const {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) x16T[(size_t)i * ld + row] = (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
-  }
-  __device__ void store_grad(int layer, int row, int col8, const float* gg) const {
-    g[layer][(size_t)(col8 / 4) * ld + row] = make_float4(gg[0], gg[1], gg[2], gg[3]);
-    g[layer][(size_t)(col8 / 4 + 1) * ld + row] = make_float4(gg[4], gg[5], gg[6], gg[7]);
-  }
-  __device__ uint16_t* act_out(int layer) const { return hT[layer]; }
-  __device__ int act_ld() const { return ld; }
-};
-
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float sigmoid_acc(float a) { return 1.f / (1.f + expf(-a)); }
+__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
 
-// ------------------------------------------------------------ backward pass
+// ------------------------------------------- forward and backward, fused
+//
+// One 128-row tile per cluster of FB_CTAS CTAs. CTA rank j of the cluster owns
+// hidden features [64 j, 64 j + 64) of every layer: its contractions are
+// M = 128 (rows) x N = 64 (its features) x K = 256, with B = its 64-row slice
+// of the weight copy (contiguous in the canonical layout). The A operands
+// (h1, h2, dA3, dA2) are kept as four 16 KB blocks of 64 features, each in
+// the canonical K-major layout with K = 64; a CTA writes its own block and
+// sends it to the other CTAs of the cluster with one bulk shared-to-shared
+// copy each (cp.async.bulk.shared::cluster), which completes on the
+// receiver's mbarrier. Two operand buffers alternate, and a CTA sends the
+// next layer's block only after it has received every block of the current
+// one, so no block is overwritten while it is read. SiLU'(z) of the CTA's
+// features stays in TMEM between the forward and the backward pass. The
+// logit is the in-order sum of the four CTAs' partial dot products W4 . h3,
+// exchanged the same way. Cluster barriers only bracket the kernel (every
+// CTA has initialised its mbarriers before it is sent anything; none leaves
+// while its copies may still be read), and every CTA passes both, whatever
+// its bounded waits did.
+constexpr int FB_CTAS = 4;
+constexpr int FB_NS = H / FB_CTAS;                     // features per CTA
+constexpr int FB_BLK = TILE * FB_NS * 2;               // one CTA's block of an operand, 16 KB
+constexpr int FB_THREADS = 256;                        // 8 warps: TMEM lane quarter x 2 column halves
+constexpr int FB_CW = FB_NS * TILE / FB_THREADS;       // 32 columns per thread
+constexpr int FB_A0 = 0;                               // [4 blocks][128][64] bf16 operand, 64 KB
+constexpr int FB_A1 = FB_A0 + FB_CTAS * FB_BLK;        // the other operand buffer
+constexpr int FB_X = FB_A1 + FB_CTAS * FB_BLK;         // [128][16] bf16 canonical layer-1 operand
+constexpr int FB_W1 = FB_X + TILE * 16 * 2;            // [64][16] slice of W1
+constexpr int FB_WA = FB_W1 + FB_NS * 16 * 2;          // [64][256] slice of W2, then of W3^T
+constexpr int FB_WB = FB_WA + FB_NS * H * 2;           // [64][256] slice of W3, then of W2^T
+constexpr int FB_BIAS = FB_WB + FB_NS * H * 2;         // b1 b2 b3 W4 slices as f32
+constexpr int FB_PART = FB_BIAS + 4 * FB_NS * 4;       // [FB_CTAS][128] partial logits
+constexpr int FB_HALF = FB_PART + FB_CTAS * TILE * 4;  // [128] partial logit of column half 1
+constexpr int FB_DZ = FB_HALF + TILE * 4;              // [128] bf16-rounded dz of the tile
+constexpr int FB_BAR = FB_DZ + TILE * 4;               // 6 mbarriers
+constexpr int FB_TMEM = FB_BAR + 48;
+constexpr int FB_TOTAL = FB_TMEM + 16;
+constexpr uint32_t FB_TCOLS = 4 * FB_NS;               // TMEM: accumulator, SiLU'(z1), SiLU'(z2), SiLU'(z3)
+constexpr uint32_t FB_RECV = (FB_CTAS - 1) * FB_BLK;   // operand bytes received per layer
+static_assert(FB_CW == 32, "one 32-column TMEM access per thread and epilogue");
+static_assert(FB_TOTAL <= 227 * 1024, "shared memory of one CTA");
 
-struct BwdArgs {
-  const void* W3tc;        // bf16 [256 in][256 out] canonical: B operand of dH2 = dA3 W3
-  const void* W2tc;        // bf16 canonical: B operand of dH1 = dA2 W2
-  const uint16_t* W4;      // bf16 [256]
-  const float* logits;     // [n]
-  const uint8_t* labels;   // [targets], through index
-  const int32_t* index;
-  int n;
+struct FbArgs {
+  MlpTcWeights w;         // forward weights (W1c, W2c, W3c canonical [out][in]), biases, standardisation
+  const void* W2tc;       // bf16 canonical [in][out]: B operand of dH1 = dA2 W2
+  const void* W3tc;       // B operand of dH2 = dA3 W3
+  const float* targets;
+  const uint8_t* labels;  // [targets], through index
+  const int32_t* index;   // batch row -> target / label (NULL: identity)
+  int n, ld;
   float inv_n;
-  const float4* g[3];      // SiLU'(z1), SiLU'(z2), SiLU'(z3) in TrainIO's tile layout
-  uint16_t* daT[3];        // dL/da1, da2, da3, bf16 [256][ld]
-  float* dz;               // [n] dL/dz
-  float* loss_sum;         // mean BCE (sum / n)
-  int ld;
+  float* logits;          // [n]
+  uint16_t* x16T;         // [16][ld] standardised input, bf16, feature-major
+  uint16_t* hT[3];        // [256][ld] h1, h2, h3, bf16, feature-major
+  uint16_t* daT[3];       // [256][ld] dL/da1, da2, da3, bf16, feature-major
+  float* dz;              // [n] dL/dz
+  float* loss_sum;        // mean BCE (sum / n)
 };
 
-constexpr int BW_THREADS = 512;              // 16 warps: TMEM lane quarter x 4 column groups of 64
-constexpr int BW_CW = H / 4;
-constexpr int BW_W = 0;                      // [256][256] bf16 canonical weights, 128 KB
-constexpr int BW_A = BW_W + 131072;          // [128][256] bf16 canonical dA operand, 64 KB
-constexpr int BW_W4 = BW_A + 65536;          // W4 as f32, 1 KB
-constexpr int BW_DZ = BW_W4 + 4 * H;         // [128] bf16-rounded dz of the tile
-constexpr int BW_BAR = BW_DZ + 4 * TILE;     // 2 mbarriers
-constexpr int BW_TMEM = BW_BAR + 16;
-constexpr int BW_TOTAL = BW_TMEM + 16;
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
 
-// Epilogue of one backward contraction for one thread's row and 64 columns:
-// dA = bf16(TMEM * SiLU'(z)) (zero on rows past the batch) into the shared
-// operand buffer, from where it is copied out feature-major.
-__device__ __forceinline__ void bwd_epilogue(uint32_t taddr, const float4* g, int ld, uint8_t* sa, int trow, int col0,
-                                             int grow, bool valid) {
-  uint32_t r[2][32];
-  tmem_ld32_async(taddr, r[0]);
-  tmem_wait_ld();
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_shared_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// `bytes` at shared address `local` to the same address in every other CTA
+// of the cluster, each copy completing on that CTA's mbarrier `bar` (one
+// thread; the bytes were written before a proxy fence and a CTA barrier).
+__device__ __forceinline__ void fb_send(uint32_t local, uint32_t bytes, uint32_t bar, uint32_t rank) {
 #pragma unroll
-  for (int c0 = 0; c0 < BW_CW; c0 += 32) {
-    const int cur = (c0 / 32) & 1;
-    if (c0 + 32 < BW_CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = col0 + c0 + q * 8;
-      float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
-      if (valid) {
-        ga = g[(size_t)(c / 4) * ld + grow];
-        gb = g[(size_t)(c / 4 + 1) * ld + grow];
-      }
-      const float* v = reinterpret_cast<const float*>(&r[cur][q * 8]);
-      const uint4 w = make_uint4(pack_bf16(v[0] * ga.x, v[1] * ga.y), pack_bf16(v[2] * ga.z, v[3] * ga.w),
-                                 pack_bf16(v[4] * gb.x, v[5] * gb.y), pack_bf16(v[6] * gb.z, v[7] * gb.w));
-      *reinterpret_cast<uint4*>(sa + canon_offset(trow, c, H)) = w;
-    }
-    if (c0 + 32 < BW_CW) tmem_wait_ld();
+  for (uint32_t r = 0; r < FB_CTAS; ++r) {
+    if (r == rank) continue;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            map_shared_rank(local, r)),
+        "r"(local), "r"(bytes), "r"(map_shared_rank(bar, r))
+        : "memory");
   }
 }
 
-// Backward through the activations, one persistent CTA of 16 warps per SM over
-// 128-row tiles: dz = (sigmoid(z) - y) / n and the loss; dA3 = bf16(bf16(dz)
-// W4 * SiLU'(z3)) formed by the threads into the A operand; dH2 = dA3 W3 and
-// dH1 = dA2 W2 on the tensor cores (the W^T copies arrive by bulk copy, the
-// next one overlapping the epilogue).
-__global__ void __launch_bounds__(BW_THREADS, 1) mlp_tc_bwd_kernel(BwdArgs A, int* status) {
+// One arrival on `bar` that also expects `bytes` of copies for its phase.
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// One 64-feature block ([128][64] bf16, canonical K-major, K = 64) out
+// feature-major: dstT[f0 + k][row0 + r] (row stride ld), one 8 x 8 core
+// matrix per step (eight 16-byte shared loads, a register transpose, eight
+// 16-byte global stores). Row groups at or past `rows` are skipped (ld, a
+// multiple of 16, covers every row group below it).
+__device__ __forceinline__ void copy_out_block(const uint8_t* blk, uint16_t* dstT, int ld, int row0, int rows, int f0,
+                                               int tid) {
+  for (int cm = tid; cm < (TILE / 8) * (FB_NS / 8); cm += FB_THREADS) {
+    const int rg = cm / (FB_NS / 8), kg = cm % (FB_NS / 8);
+    if (rg * 8 >= rows) continue;
+    const uint8_t* src = blk + rg * (FB_NS / 8) * 128 + kg * 128;  // core matrix (rg, kg): 8 rows x 16 bytes
+    uint32_t w[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * r);
+      w[r][0] = v.x; w[r][1] = v.y; w[r][2] = v.z; w[r][3] = v.w;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {  // columns 2p, 2p + 1 of the core matrix
+      uint32_t lo[4], hi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // rows 2q, 2q + 1
+        lo[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x5410);
+        hi[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x7632);
+      }
+      const size_t base = (size_t)(f0 + kg * 8 + 2 * p) * ld + row0 + rg * 8;
+      *reinterpret_cast<uint4*>(dstT + base) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(dstT + base + ld) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    }
+  }
+}
+
+// The 16 MMAs (K = 16 each) of D[128 x 64] = A[128 x 256] B[64 x 256]^T, A
+// in four 64-feature blocks, committed to `bar`; one thread.
+__device__ __forceinline__ void fb_mma_k256(uint32_t tmem, uint32_t a, uint32_t b, uint32_t bar) {
+  constexpr uint32_t idesc = make_idesc(TILE, FB_NS);
+  tc_fence_after();
+#pragma unroll 1
+  for (int s = 0; s < H / 16; ++s)
+    tc_mma(tmem, make_desc(a + (s >> 2) * FB_BLK + (s & 3) * 256, 128, FB_NS / 8 * 128),
+           make_desc(b + 256 * s, 128, 4096), idesc, s > 0);
+  tc_commit(bar);
+}
+
+// 32 bf16 values (16 packed pairs) of row `row`, block features [c0, c0 + 32),
+// into the block at shared address `blk`.
+__device__ __forceinline__ void fb_put_row(uint32_t blk, int row, int c0, const uint32_t hw[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(blk + canon_offset(row, c0 + 8 * q, FB_NS)),
+                 "r"(hw[4 * q]), "r"(hw[4 * q + 1]), "r"(hw[4 * q + 2]), "r"(hw[4 * q + 3])
+                 : "memory");
+}
+
+// Forward and backward of one 128-row tile, dz and the loss, for a cluster of
+// FB_CTAS CTAs (see above). Writes the standardised input, h1..h3 and
+// dA1..dA3 feature-major for the weight gradients, the logits and dz.
+__global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = A.n;
-  const int ntiles = (n + TILE - 1) / TILE;
-  if ((int)blockIdx.x >= ntiles) return;
-  uint8_t* sw = smem + BW_W;
-  uint8_t* sa = smem + BW_A;
-  float* sw4 = reinterpret_cast<float*>(smem + BW_W4);
-  float* sdz = reinterpret_cast<float*>(smem + BW_DZ);
-  const uint32_t bar_w = smem_u32(smem + BW_BAR), bar_m = bar_w + 8;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + BW_TMEM);
+  const int row0 = (int)(blockIdx.x / FB_CTAS) * TILE;
+  const uint32_t rank = cluster_ctarank();
+  const int fs = (int)rank * FB_NS;  // first feature of this CTA
+  float* sbias = reinterpret_cast<float*>(smem + FB_BIAS);  // b1 | b2 | b3 | W4 of this CTA's features
+  float* spart = reinterpret_cast<float*>(smem + FB_PART);
+  float* shalf = reinterpret_cast<float*>(smem + FB_HALF);
+  float* sdz = reinterpret_cast<float*>(smem + FB_DZ);
+  const uint32_t s0 = smem_u32(smem);
+  const uint32_t bar_a = s0 + FB_BAR, bar_b = bar_a + 8, bar_m = bar_a + 16;  // weights, weights, MMAs
+  const uint32_t bar_x0 = bar_a + 24, bar_x1 = bar_a + 32, bar_p = bar_a + 40;  // received: A0, A1, logits
+  const uint32_t own0 = s0 + FB_A0 + rank * FB_BLK, own1 = s0 + FB_A1 + rank * FB_BLK;  // this CTA's blocks
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + FB_TMEM);
+  const char* W2c = static_cast<const char*>(A.w.W2c) + (size_t)fs * H * 2;  // 64-row slices
+  const char* W3c = static_cast<const char*>(A.w.W3c) + (size_t)fs * H * 2;
+  const char* W2t = static_cast<const char*>(A.W2tc) + (size_t)fs * H * 2;
+  const char* W3t = static_cast<const char*>(A.W3tc) + (size_t)fs * H * 2;
+
   if (tid == 0) {
-    mbar_init(bar_w, 1);
-    mbar_init(bar_m, 1);
+    for (int i = 0; i < 6; ++i) mbar_init(bar_a + 8 * i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < H; i += BW_THREADS) sw4[i] = __uint_as_float((uint32_t)__ldg(&A.W4[i]) << 16);
+  __syncthreads();
+  // phases issued and completed on each mbarrier (the same in every thread)
+  int iss_a = 1, iss_b = 1, iss_m = 0, iss_x0 = 1, iss_x1 = 1, iss_p = 1;
+  int got_a = 0, got_b = 0, got_m = 0, got_x0 = 0, got_x1 = 0, got_p = 0;
+  if (tid == 0) {
+    mbar_expect(bar_x0, FB_RECV);
+    mbar_expect(bar_x1, FB_RECV);
+    mbar_expect(bar_p, (FB_CTAS - 1) * TILE * 4);
+    bulk_load(s0 + FB_WA, W2c, FB_NS * H * 2, bar_a);
+    bulk_load(s0 + FB_WB, W3c, FB_NS * H * 2, bar_b);
+  }
+  cluster_arrive();  // this CTA's mbarriers are ready for the others' copies
+  for (int i = tid; i < FB_NS * 16 * 2 / 16; i += FB_THREADS)
+    reinterpret_cast<uint4*>(smem + FB_W1)[i] =
+        __ldg(reinterpret_cast<const uint4*>(static_cast<const char*>(A.w.W1c) + (size_t)fs * 16 * 2) + i);
+  for (int i = tid; i < FB_NS; i += FB_THREADS) {
+    sbias[i] = __ldg(A.w.params + A.w.off_b1 + fs + i);
+    sbias[FB_NS + i] = __ldg(A.w.params + A.w.off_b2 + fs + i);
+    sbias[2 * FB_NS + i] = __ldg(A.w.params + A.w.off_b3 + fs + i);
+    sbias[3 * FB_NS + i] = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(A.w.W4)[fs + i]);
+  }
+  const float b4 = __ldg(A.w.params + A.w.off_b4);
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(H)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(FB_TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // ---- layer-1 operand: standardised features, bf16, K padded to 16 (every
+  // CTA forms all of it; rank 0 keeps it for dW1); each row's label
+  float y = 0.f;
+  if (tid < TILE) {
+    const int row = row0 + tid;
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = 0.f;
+    if (row < n) {
+      const int ti = A.index ? __ldg(&A.index[row]) : row;
+      const float* t = A.targets + 12 * (size_t)ti;
+      const float f[9] = {__ldg(t + 9), __ldg(t + 10), __ldg(t + 11), __ldg(t + 0), __ldg(t + 3),
+                          __ldg(t + 6), __ldg(t + 1), __ldg(t + 4), __ldg(t + 7)};
+      y = __ldg(&A.labels[ti]) ? 1.f : 0.f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) x[i] = (f[i] - __ldg(A.w.mu + i)) * __ldg(A.w.inv_sigma + i);
+    }
+    uint32_t xb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xb[i] = pack_bf16(x[2 * i], x[2 * i + 1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      *reinterpret_cast<uint4*>(smem + FB_X + canon_offset(tid, q * 8, 16)) =
+          make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
+    if (rank == 0 && row < n) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) A.x16T[(size_t)i * A.ld + row] = (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
+    }
+  }
   fence_proxy_async();
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int quarter = warp & 3, cg = warp >> 2;
-  const int trow = quarter * 32 + lane;
-  const int col0 = cg * BW_CW;
-  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
-  constexpr uint32_t idesc = make_idesc(TILE, H);
+  const int quarter = warp & 3, half = warp >> 2;
+  const int trow = quarter * 32 + lane;  // this thread's row (= TMEM lane)
+  const int cb = half * FB_CW;           // its first column among the CTA's features
+  const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+  const uint32_t tacc = tl + (uint32_t)cb;  // accumulator
+  const uint32_t tg1 = tacc + FB_NS, tg2 = tacc + 2 * FB_NS, tg3 = tacc + 3 * FB_NS;  // SiLU'(z1..z3)
+  bool ok = true;
 
-  uint32_t ph_w = 0, ph_m = 0;
-  bool w_pending = true, m_pending = false, ok = true;
-  if (tid == 0) bulk_load(smem_u32(sw), A.W3tc, 131072, bar_w);
+  // the next phase of an mbarrier, the outcome agreed by the CTA
+  auto wait_bar = [&](uint32_t bar, int& got) {
+    const bool w = mbar_wait(bar, (uint32_t)(got & 1));
+    if (w) ++got;
+    ok = __syncthreads_and(ok && w) != 0;
+    tc_fence_after();
+  };
+  auto issue = [&](uint32_t a, uint32_t b) {  // D = A B^T, K = 256
+    if (tid == 0) fb_mma_k256(tmem, s0 + a, s0 + b, bar_m);
+    ++iss_m;
+  };
+  auto reload = [&](uint32_t dst, const char* src, uint32_t bar, int& iss) {
+    if (tid == 0) bulk_load(s0 + dst, src, FB_NS * H * 2, bar);
+    ++iss;
+  };
+  // this CTA's block written (by every thread): visible to the copies and
+  // the tensor cores, then sent to the other CTAs
+  auto publish = [&](uint32_t blk, uint32_t bytes, uint32_t bar) {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) fb_send(blk, bytes, bar, rank);
+  };
+  // forward epilogue of layer l: bias, SiLU, SiLU' into TMEM, the bf16 h_l
+  // block into `blk` (and, for l = 2, the partial logit of these features)
+  auto fwd_epilogue = [&](int l, uint32_t blk) {
+    uint32_t v[32], gw[32], hw[16];
+    tmem_ld32(tacc, v);
+    const float* bias = sbias + l * FB_NS + cb;
+    const float* w4 = sbias + 3 * FB_NS + cb;
+    float z = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+      const float p0 = __uint_as_float(v[i]) + bias[i];
+      const float p1 = __uint_as_float(v[i + 1]) + bias[i + 1];
+      const float q0 = sigmoid_f(p0), q1 = sigmoid_f(p1);
+      hw[i / 2] = pack_bf16(p0 * q0, p1 * q1);
+      gw[i] = __float_as_uint(silu_grad_from(p0, q0));
+      gw[i + 1] = __float_as_uint(silu_grad_from(p1, q1));
+      if (l == 2) {
+        z = fmaf(bf16_lo(hw[i / 2]), w4[i], z);
+        z = fmaf(bf16_hi(hw[i / 2]), w4[i + 1], z);
+      }
+    }
+    tmem_st32(l == 0 ? tg1 : l == 1 ? tg2 : tg3, gw);
+    fb_put_row(blk, trow, cb, hw);
+    return z;
+  };
+  // backward epilogue: the dA = bf16(dH * SiLU'(z)) block into `blk`
+  auto bwd_epilogue = [&](uint32_t tg, uint32_t blk) {
+    uint32_t v[32], g[32], hw[16];
+    tmem_ld32_async(tacc, v);
+    tmem_ld32_async(tg, g);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; i += 2)
+      hw[i / 2] = pack_bf16(__uint_as_float(v[i]) * __uint_as_float(g[i]),
+                            __uint_as_float(v[i + 1]) * __uint_as_float(g[i + 1]));
+    fb_put_row(blk, trow, cb, hw);
+  };
 
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // ---- dz and the loss (one thread per row)
-    if (tid < TILE) {
-      const int row = tile * TILE + tid;
-      float dz = 0.f, loss = 0.f;
-      if (row < n) {
-        const float z = A.logits[row];
-        const float y = A.labels[A.index ? __ldg(&A.index[row]) : row] ? 1.f : 0.f;
-        dz = (sigmoid_acc(z) - y) * A.inv_n;
-        loss = fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
+  // ---- forward. z1 = X W1^T (K = 16)
+  if (tid == 0) {
+    tc_mma(tmem, make_desc(s0 + FB_X, 128, 256), make_desc(s0 + FB_W1, 128, 256), make_idesc(TILE, FB_NS), 0);
+    tc_commit(bar_m);
+  }
+  iss_m = 1;
+  wait_bar(bar_m, got_m);
+  if (ok) fwd_epilogue(0, own0);
+  cluster_wait();  // every CTA's mbarriers are ready
+  if (ok) publish(own0, FB_BLK, bar_x0);
+  // z2 = h1 W2^T once every block of h1 is here; this CTA's h1 out meanwhile
+  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.hT[0], A.ld, row0, n - row0, fs, tid);
+  if (ok) wait_bar(bar_x0, got_x0);
+  if (ok && tid == 0) mbar_expect(bar_x0, FB_RECV);  // dA2 arrives in A0
+  if (ok) ++iss_x0;
+  if (ok) wait_bar(bar_a, got_a);
+  if (ok) issue(FB_A0, FB_WA);
+  if (ok) wait_bar(bar_m, got_m);
+  if (ok) reload(FB_WA, W3t, bar_a, iss_a);  // the MMAs have read W2: bring in W3^T
+  if (ok) fwd_epilogue(1, own1);
+  if (ok) publish(own1, FB_BLK, bar_x1);
+  // z3 = h2 W3^T
+  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.hT[1], A.ld, row0, n - row0, fs, tid);
+  if (ok) wait_bar(bar_x1, got_x1);
+  if (ok && tid == 0) mbar_expect(bar_x1, FB_RECV);  // dA3 arrives in A1
+  if (ok) ++iss_x1;
+  if (ok) wait_bar(bar_b, got_b);
+  if (ok) issue(FB_A1, FB_WB);
+  if (ok) wait_bar(bar_m, got_m);
+  if (ok) reload(FB_WB, W2t, bar_b, iss_b);  // W3 read: bring in W2^T
+  if (ok) {
+    // h3 into this CTA's block of A0 (the others' blocks of h1 there stay
+    // until dA2 replaces them); the partial logit of its features
+    float z = fwd_epilogue(2, own0);
+    if (half == 1) shalf[trow] = z;
+    __syncthreads();
+    if (half == 0) spart[rank * TILE + trow] = z + shalf[trow];
+    publish(s0 + FB_PART + rank * TILE * 4, TILE * 4, bar_p);
+  }
+  // ---- logits, dz = (sigmoid(z) - y) / n, the loss; h3 out
+  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.hT[2], A.ld, row0, n - row0, fs, tid);
+  if (ok) wait_bar(bar_p, got_p);
+  if (tid < TILE) {
+    const int row = row0 + tid;
+    float dz = 0.f, loss = 0.f;
+    if (ok && row < n) {
+      float z = spart[tid];
+#pragma unroll
+      for (int r = 1; r < FB_CTAS; ++r) z += spart[r * TILE + tid];  // in rank order
+      z += b4;
+      dz = (sigmoid_acc(z) - y) * A.inv_n;
+      loss = fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
+      if (rank == 0) {
+        A.logits[row] = z;
         A.dz[row] = dz;
       }
-      sdz[tid] = bf16_round(dz);
+    }
+    sdz[tid] = bf16_round(dz);
+    if (rank == 0) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
       if (lane == 0) atomicAdd(A.loss_sum, loss * A.inv_n);
     }
-    __syncthreads();
-    // ---- dA3 = bf16(bf16(dz) W4 * SiLU'(z3)): thread (row, 64 columns)
-    {
-      const int r = tid & (TILE - 1), cb = (tid >> 7) * BW_CW;
-      const int grow = tile * TILE + r;
-      const bool valid = grow < n;
-      const float d = sdz[r];
-#pragma unroll 4
-      for (int c = cb; c < cb + BW_CW; c += 8) {
-        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
-        if (valid) {
-          ga = A.g[2][(size_t)(c / 4) * A.ld + grow];
-          gb = A.g[2][(size_t)(c / 4 + 1) * A.ld + grow];
-        }
-        const float* w4 = sw4 + c;
-        *reinterpret_cast<uint4*>(sa + canon_offset(r, c, H)) =
-            make_uint4(pack_bf16(d * w4[0] * ga.x, d * w4[1] * ga.y), pack_bf16(d * w4[2] * ga.z, d * w4[3] * ga.w),
-                       pack_bf16(d * w4[4] * gb.x, d * w4[5] * gb.y), pack_bf16(d * w4[6] * gb.z, d * w4[7] * gb.w));
-      }
-    }
-    // ---- dH2 = dA3 W3 -> dA2; dH1 = dA2 W2 -> dA1. Each dA is copied out
-    // feature-major from the operand buffer (dA3, dA2 while the tensor cores
-    // read them; dA1 after the last contraction).
-    const int grow = tile * TILE + trow;
-    for (int layer = 0; layer < 2; ++layer) {
-      fence_proxy_async();
-      tc_fence_before();
-      ok = mbar_wait(bar_w, ph_w);
-      if (ok) {
-        ph_w ^= 1;
-        w_pending = false;
-      }
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll 1
-        for (int s = 0; s < H / 16; ++s)
-          tc_mma(tmem, make_desc(smem_u32(sa) + 256 * s, 128, 4096), make_desc(smem_u32(sw) + 256 * s, 128, 4096),
-                 idesc, s > 0);
-        tc_commit(bar_m);
-      }
-      copy_out_transposed(sa, A.daT[2 - layer], A.ld, tile * TILE, n - tile * TILE, tid, BW_THREADS);
-      m_pending = true;
-      ok = mbar_wait(bar_m, ph_m);
-      if (ok) {
-        ph_m ^= 1;
-        m_pending = false;
-      }
-      tc_fence_after();
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      // the MMAs have read the weights and the operand; the copy is done
-      if (layer == 0 || tile + (int)gridDim.x < ntiles) {
-        if (tid == 0) bulk_load(smem_u32(sw), layer == 0 ? A.W2tc : A.W3tc, 131072, bar_w);
-        w_pending = true;
-      }
-      bwd_epilogue(taddr, A.g[1 - layer], A.ld, sa, trow, col0, grow, grow < n);
-      tc_fence_before();
-      __syncthreads();  // TMEM read and the operand written before the next MMA or copy
-    }
-    if (!ok) break;
-    copy_out_transposed(sa, A.daT[0], A.ld, tile * TILE, n - tile * TILE, tid, BW_THREADS);
-    __syncthreads();  // the operand is read before the next tile's dA3 overwrites it
   }
+  __syncthreads();
+  // ---- backward. dA3 = bf16(bf16(dz) W4 * SiLU'(z3)) into A1
+  if (ok) {
+    uint32_t g[32], hw[16];
+    tmem_ld32(tg3, g);
+    const float d = sdz[trow];
+    const float* w4 = sbias + 3 * FB_NS + cb;
+#pragma unroll
+    for (int i = 0; i < 32; i += 2)
+      hw[i / 2] = pack_bf16(d * w4[i] * __uint_as_float(g[i]), d * w4[i + 1] * __uint_as_float(g[i + 1]));
+    fb_put_row(own1, trow, cb, hw);
+    publish(own1, FB_BLK, bar_x1);
+  }
+  // dH2 = dA3 W3 -> dA2 into A0
+  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.daT[2], A.ld, row0, n - row0, fs, tid);
+  if (ok) wait_bar(bar_x1, got_x1);
+  if (ok) wait_bar(bar_a, got_a);
+  if (ok) issue(FB_A1, FB_WA);
+  if (ok) wait_bar(bar_m, got_m);
+  if (ok) {
+    bwd_epilogue(tg2, own0);
+    publish(own0, FB_BLK, bar_x0);
+  }
+  // dH1 = dA2 W2 -> dA1 into this CTA's block of A1 (dA3 there is read)
+  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.daT[1], A.ld, row0, n - row0, fs, tid);
+  if (ok) wait_bar(bar_x0, got_x0);
+  if (ok) wait_bar(bar_b, got_b);
+  if (ok) issue(FB_A0, FB_WB);
+  if (ok) wait_bar(bar_m, got_m);
+  if (ok) bwd_epilogue(tg1, own1);
+  __syncthreads();
+  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.daT[0], A.ld, row0, n - row0, fs, tid);
+
   if (!ok) {
     if (tid == 0) latch_error(status, kDevTimeout);
-    if (w_pending) mbar_wait(bar_w, ph_w);
-    if (m_pending) mbar_wait(bar_m, ph_m);
+    // drain what is still in flight into this CTA (bounded)
+    while (got_a < iss_a && mbar_wait(bar_a, (uint32_t)(got_a & 1))) ++got_a;
+    while (got_b < iss_b && mbar_wait(bar_b, (uint32_t)(got_b & 1))) ++got_b;
+    while (got_m < iss_m && mbar_wait(bar_m, (uint32_t)(got_m & 1))) ++got_m;
+    while (got_x0 < iss_x0 && mbar_wait(bar_x0, (uint32_t)(got_x0 & 1))) ++got_x0;
+    while (got_x1 < iss_x1 && mbar_wait(bar_x1, (uint32_t)(got_x1 & 1))) ++got_x1;
+    while (got_p < iss_p && mbar_wait(bar_p, (uint32_t)(got_p & 1))) ++got_p;
   }
+  // every CTA has received what this one sent before any of them leaves
+  cluster_arrive();
+  cluster_wait();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FB_TCOLS) : "memory");
   }
 }
 
@@ -470,9 +672,6 @@ struct FinishArgs {
   int red_blocks;
 };
 
-__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
-
 __global__ void mlp_grad_finish_kernel(WgArgs G, FinishArgs F) {
   if ((int)blockIdx.x < F.red_blocks) {
     const int n1 = H * 16, n2 = H * H;
@@ -549,43 +748,41 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
   if (L.n <= 0) return cudaSuccess;
   const int ntiles = (L.n + TILE - 1) / TILE;
   cudaError_t e;
-  // ---- forward with caches
+  // ---- forward and backward through the activations, a cluster per tile
   {
-    TrainIO io;
-    io.targets = L.targets;
-    io.index = L.index;
-    io.n = L.n;
-    io.logits = L.logits;
-    io.x16T = L.x16T;
-    for (int l = 0; l < 3; ++l) {
-      io.hT[l] = L.hT[l];
-      io.g[l] = L.g[l];
-    }
-    io.ld = L.ld;
-    if ((e = launch_mlp_tc(L.w, io, L.n, L.status, num_sms, s))) return e;
-  }
-  // ---- backward through the activations
-  {
-    BwdArgs A;
-    A.W3tc = L.W3tc;
+    FbArgs A;
+    A.w = L.w;
     A.W2tc = L.W2tc;
-    A.W4 = static_cast<const uint16_t*>(L.w.W4);
-    A.logits = L.logits;
+    A.W3tc = L.W3tc;
+    A.targets = L.targets;
     A.labels = L.labels;
     A.index = L.index;
     A.n = L.n;
+    A.ld = L.ld;
     A.inv_n = 1.f / (float)L.n;
+    A.logits = L.logits;
+    A.x16T = L.x16T;
     for (int l = 0; l < 3; ++l) {
-      A.g[l] = L.g[l];
+      A.hT[l] = L.hT[l];
       A.daT[l] = L.daT[l];
     }
     A.dz = L.dz;
     A.loss_sum = L.loss_sum;
-    A.ld = L.ld;
-    if ((e = cudaFuncSetAttribute(mlp_tc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BW_TOTAL))) return e;
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
-    mlp_tc_bwd_kernel<<<grid, BW_THREADS, BW_TOTAL, s>>>(A, L.status);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaFuncSetAttribute(mlp_train_fb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_TOTAL)))
+      return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(FB_CTAS * ntiles));
+    cfg.blockDim = dim3(FB_THREADS);
+    cfg.dynamicSmemBytes = FB_TOTAL;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = FB_CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, mlp_train_fb_kernel, A, L.status))) return e;
   }
   // ---- weight gradients: dW1 = dA1^T X, dW2 = dA2^T H1, dW3 = dA3^T H2
   {
