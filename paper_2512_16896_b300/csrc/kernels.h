@@ -168,11 +168,11 @@ struct TrainTcLaunch {
   int n, ld;
   float* logits;         // [n]
   uint16_t* x16T;        // [16][ld]
-  uint16_t* hT[3];       // [256][ld]
+  uint16_t* hT[2];       // [256][ld] h1, h2
   uint16_t* daT[3];      // [256][ld]
   float* dz;             // [n]
   float* loss_sum;       // zeroed by the caller
-  float* wg_part;        // mlp_train_tc_part_bytes(ld)
+  float* wg_part;        // mlp_train_tc_part_bytes(ld): per-tile sums of dz h3 and dz
   float* dW1;            // [256][9]
   float* dW2;            // [256][256]
   float* dW3;
@@ -181,7 +181,6 @@ struct TrainTcLaunch {
   float* db4;            // [1]
   int* status;
 };
-int mlp_train_tc_splits(int rows);
 size_t mlp_train_tc_part_bytes(int Bcap);
 cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s);
 cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s);

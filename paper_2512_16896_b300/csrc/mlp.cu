@@ -246,25 +246,25 @@ cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int
   return mlp_forward_tc(tc_view(*S), targets, n_cap, n_dev, logits, status, num_sms, s);
 }
 
-// Batch buffers of Bcap rows: the forward caches (standardised input and
-// activations, feature-major), the dL/da (feature-major), dz, logits, the
-// loss word and the weight gradients' partial sums. (SiLU'(z) stays in the
-// tensor memory of the fused forward-backward kernel.)
+// Batch buffers of Bcap rows: the standardised input and h1, h2 (feature-
+// major) for the weight gradients, the dL/da (feature-major), dz, logits,
+// the loss word and the per-tile sums of dz h3 and dz. (SiLU'(z) stays in
+// the tensor memory of the fused forward-backward kernel.)
 struct TrainViews {
   uint16_t* x16T;   // [KIN][Bcap]
-  uint16_t* hT[3];  // [H][Bcap]
+  uint16_t* hT[2];  // [H][Bcap] h1, h2
   uint16_t* daT[3]; // [H][Bcap]
   float* dz;        // [Bcap]
   float* logits;    // [Bcap]
   float* loss_sum;
-  float* part;      // mlp_train_tc_part_bytes(Bcap)
+  float* part;      // mlp_train_tc_part_bytes(Bcap): per-tile sums
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 static size_t train_bytes(int Bcap) {
   const size_t Bp = (size_t)Bcap;
-  return align256(Bp * KIN * 2) + 3 * align256(Bp * H * 2) + 3 * align256(Bp * H * 2) +
+  return align256(Bp * KIN * 2) + 2 * align256(Bp * H * 2) + 3 * align256(Bp * H * 2) +
          2 * align256(Bp * 4) + 256 + align256(mlp_train_tc_part_bytes(Bcap));
 }
 
@@ -273,7 +273,7 @@ static TrainViews carve(MlpState* S, int Bcap) {
   auto take = [&](size_t bytes) { char* r = p; p += align256(bytes); return r; };
   TrainViews v;
   v.x16T = reinterpret_cast<uint16_t*>(take((size_t)Bcap * KIN * 2));
-  for (int l = 0; l < 3; ++l) v.hT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
+  for (int l = 0; l < 2; ++l) v.hT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
   for (int l = 0; l < 3; ++l) v.daT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
   v.dz = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.logits = reinterpret_cast<float*>(take((size_t)Bcap * 4));
@@ -316,10 +316,8 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
   L.ld = S->Bcap;
   L.logits = v.logits;
   L.x16T = v.x16T;
-  for (int l = 0; l < 3; ++l) {
-    L.hT[l] = v.hT[l];
-    L.daT[l] = v.daT[l];
-  }
+  for (int l = 0; l < 2; ++l) L.hT[l] = v.hT[l];
+  for (int l = 0; l < 3; ++l) L.daT[l] = v.daT[l];
   L.dz = v.dz;
   L.loss_sum = loss;
   L.wg_part = v.part;

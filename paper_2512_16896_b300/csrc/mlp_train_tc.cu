@@ -8,10 +8,11 @@
 //             dA_l = bf16(dH_l * SiLU'(Z_l))   64 of the 256 features; B = W^T
 //                                          copies in the backward pass
 //   weights   dW_l = dA_l^T H_{l-1}       mlp_tc_wgrad_kernel: M = output
-//                                          features (two 128-row tiles), N = input
-//                                          features, K = the batch, split over
-//                                          CTAs; partial sums added in split
-//                                          order by mlp_grad_finish_kernel
+//   biases    db_l = dA_l^T 1             features (two 128-row tiles), N = input
+//                                          features and a row of ones, K = the
+//                                          batch split over the CTAs of a cluster,
+//                                          the partials added in split order over
+//                                          distributed shared memory
 //
 // Rounding points as in the FP64 reference: standardised input, SiLU outputs,
 // weight copies, dL/dz before it meets W4 and every dL/da in bf16; biases,
@@ -63,7 +64,9 @@ constexpr int FB_BIAS = FB_WB + FB_NS * H * 2;         // b1 b2 b3 W4 slices as 
 constexpr int FB_PART = FB_BIAS + 4 * FB_NS * 4;       // [FB_CTAS][128] partial logits
 constexpr int FB_HALF = FB_PART + FB_CTAS * TILE * 4;  // [128] partial logit of column half 1
 constexpr int FB_DZ = FB_HALF + TILE * 4;              // [128] bf16-rounded dz of the tile
-constexpr int FB_BAR = FB_DZ + TILE * 4;               // 6 mbarriers
+constexpr int FB_DZF = FB_DZ + TILE * 4;               // [128] dz of the tile
+constexpr int FB_RED = FB_DZF + TILE * 4;              // [4][64] partial sums of dW4
+constexpr int FB_BAR = FB_RED + 4 * FB_NS * 4;         // 6 mbarriers
 constexpr int FB_TMEM = FB_BAR + 48;
 constexpr int FB_TOTAL = FB_TMEM + 16;
 constexpr uint32_t FB_TCOLS = 4 * FB_NS;               // TMEM: accumulator, SiLU'(z1), SiLU'(z2), SiLU'(z3)
@@ -82,10 +85,11 @@ struct FbArgs {
   float inv_n;
   float* logits;          // [n]
   uint16_t* x16T;         // [16][ld] standardised input, bf16, feature-major
-  uint16_t* hT[3];        // [256][ld] h1, h2, h3, bf16, feature-major
+  uint16_t* hT[2];        // [256][ld] h1, h2, bf16, feature-major
   uint16_t* daT[3];       // [256][ld] dL/da1, da2, da3, bf16, feature-major
   float* dz;              // [n] dL/dz
   float* loss_sum;        // mean BCE (sum / n)
+  float* tsum;            // [tiles][257] over each tile's rows: dW4 = sum dz h3 (256), db4 = sum dz
 };
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -193,8 +197,9 @@ __device__ __forceinline__ void fb_put_row(uint32_t blk, int row, int c0, const 
 }
 
 // Forward and backward of one 128-row tile, dz and the loss, for a cluster of
-// FB_CTAS CTAs (see above). Writes the standardised input, h1..h3 and
-// dA1..dA3 feature-major for the weight gradients, the logits and dz.
+// FB_CTAS CTAs (see above). Writes the standardised input, h1, h2 and
+// dA1..dA3 feature-major for the weight gradients, the logits, dz and the
+// tile's sums of dz h3 and dz.
 __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -206,6 +211,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   float* spart = reinterpret_cast<float*>(smem + FB_PART);
   float* shalf = reinterpret_cast<float*>(smem + FB_HALF);
   float* sdz = reinterpret_cast<float*>(smem + FB_DZ);
+  float* sdzf = reinterpret_cast<float*>(smem + FB_DZF);
+  float* sred = reinterpret_cast<float*>(smem + FB_RED);
+  const int tile = row0 / TILE;
   const uint32_t s0 = smem_u32(smem);
   const uint32_t bar_a = s0 + FB_BAR, bar_b = bar_a + 8, bar_m = bar_a + 16;  // weights, weights, MMAs
   const uint32_t bar_x0 = bar_a + 24, bar_x1 = bar_a + 32, bar_p = bar_a + 40;  // received: A0, A1, logits
@@ -390,8 +398,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     if (half == 0) spart[rank * TILE + trow] = z + shalf[trow];
     publish(s0 + FB_PART + rank * TILE * 4, TILE * 4, bar_p);
   }
-  // ---- logits, dz = (sigmoid(z) - y) / n, the loss; h3 out
-  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.hT[2], A.ld, row0, n - row0, fs, tid);
+  // ---- logits, dz = (sigmoid(z) - y) / n, the loss
   if (ok) wait_bar(bar_p, got_p);
   if (tid < TILE) {
     const int row = row0 + tid;
@@ -409,6 +416,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
       }
     }
     sdz[tid] = bf16_round(dz);
+    sdzf[tid] = dz;
     if (rank == 0) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
@@ -428,8 +436,46 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     fb_put_row(own1, trow, cb, hw);
     publish(own1, FB_BLK, bar_x1);
   }
-  // dH2 = dA3 W3 -> dA2 into A0
   if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.daT[2], A.ld, row0, n - row0, fs, tid);
+  // dW4 = sum dz h3 and db4 = sum dz over the tile's rows, this CTA's
+  // features of h3 (its block of A0): thread (row group set, 8 features,
+  // row in group) with 16-byte loads, the 8 rows of a group added across
+  // lanes, the 4 row-group sets in order
+  if (ok) {
+    const int kg = (lane >> 3) + 4 * (warp & 1), rl = lane & 7;
+    const uint8_t* blk = smem + FB_A0 + rank * FB_BLK;
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rg = (warp >> 1) + 4 * i;
+      const uint4 v = *reinterpret_cast<const uint4*>(blk + rg * (FB_NS / 8) * 128 + kg * 128 + rl * 16);
+      const float d = sdzf[rg * 8 + rl];
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[2 * j] = fmaf(bf16_lo(w[j]), d, acc[2 * j]);
+        acc[2 * j + 1] = fmaf(bf16_hi(w[j]), d, acc[2 * j + 1]);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xFFFFFFFFu, acc[j], o);
+    if (rl == 0)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sred[(warp >> 1) * FB_NS + kg * 8 + j] = acc[j];
+    __syncthreads();
+    float* ts = A.tsum + (size_t)tile * (H + 1);
+    if (tid < FB_NS) ts[fs + tid] = ((sred[tid] + sred[FB_NS + tid]) + sred[2 * FB_NS + tid]) + sred[3 * FB_NS + tid];
+    if (rank == 0 && tid == FB_NS) {
+      float t = 0.f;
+      for (int r = 0; r < TILE; ++r) t += sdzf[r];
+      ts[H] = t;
+    }
+  }
+  // dH2 = dA3 W3 -> dA2 into A0 (h3 there is read)
   if (ok) wait_bar(bar_x1, got_x1);
   if (ok) wait_bar(bar_a, got_a);
   if (ok) issue(FB_A1, FB_WA);
@@ -470,28 +516,51 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
 }
 
 // -------------------------------------------------------- weight gradients
+//
+// dW_l = dA_l^T H_{l-1} and db_l = dA_l^T 1 as one contraction per output
+// tile: M = 128 output features, K = the batch, and N = the input features
+// followed by a row of ones over the batch (bf16 1.0 for rows < n, so the
+// bias gradient is the sum of dA in FP32 on the tensor cores): for the first
+// layer the ones take input slot 9 (slots 9..15 pad the 9 inputs to 16); for
+// the others they are row 256 of a 16-row block, contracted by a second MMA
+// of N = 16 (N stops at 256). The batch is split over the S CTAs of a
+// cluster; each CTA accumulates its split in TMEM, copies it to its shared
+// memory, and after a cluster barrier sums one slice of rows over all S
+// partials in split order (distributed shared-memory loads), writing dW and
+// db directly. Thread block (0) also adds the fused kernel's per-tile sums
+// of dW4 and db4 in tile order.
 
 struct WgJob {
   const uint16_t* A;  // dL/da feature-major [256][ld]: A operand rows = output features
   const uint16_t* B;  // activations feature-major [N][ld]: B operand rows = input features
-  int N;              // 256, or 16 for the first layer (inputs padded to 16)
-  float* part;        // [S][256][N] partial sums
+  int N;              // 256, or 16 for the first layer (9 inputs padded to 16)
+  float* dW;          // [256][256], or [256][9]
+  float* db;          // [256]
 };
 
 struct WgArgs {
   WgJob job[3];
   int n;         // batch rows
   int ld;
-  int S;         // K splits
+  int S;         // K splits = CTAs per cluster
   int chunks;    // 64-row chunks per split
+  const float* tsum;  // [tiles][257] per-tile sums of dz h3 | dz
+  int tiles;
+  float* dW4;    // [256]
+  float* db4;    // [1]
 };
 
-constexpr int WG_CHUNK = 64;                       // batch rows per staged chunk (K)
-constexpr int WG_STAGE_A = 128 * WG_CHUNK * 2;     // 16 KB
-constexpr int WG_STAGE = WG_STAGE_A + H * WG_CHUNK * 2;  // + 32 KB
-constexpr int WG_BAR = 2 * WG_STAGE;               // 2 mbarriers
+constexpr int WG_CHUNK = 64;                            // batch rows per staged chunk (K)
+constexpr int WG_NB = H + 16;                           // B rows staged: inputs, then the ones block
+constexpr int WG_STAGE_A = 128 * WG_CHUNK * 2;          // 16 KB
+constexpr int WG_STAGE = WG_STAGE_A + WG_NB * WG_CHUNK * 2;  // + 34 KB
+constexpr int WG_LD = WG_NB + 4;                        // floats per row of a CTA's partial (padded)
+constexpr int WG_RED = TILE * WG_LD * 4;                // the partial, over the stages once they are read
+constexpr int WG_BAR = (2 * WG_STAGE > WG_RED ? 2 * WG_STAGE : WG_RED);  // 2 mbarriers
 constexpr int WG_TMEM = WG_BAR + 16;
 constexpr int WG_TOTAL = WG_TMEM + 16;
+constexpr int WG_MAX_S = 16;
+static_assert(WG_TOTAL <= 227 * 1024, "shared memory of one CTA");
 
 // 16 consecutive f32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
@@ -503,15 +572,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
 // Rows [row0, row0 + rows) x batch columns [k0, k0 + 64) of a feature-major
 // bf16 matrix into the canonical K-major layout (K = 64) by asynchronous
 // 16-byte copies (cp.async; whole vectors past n are zero-filled by the copy,
 // a vector that straddles n is assembled by the thread); batch columns at or
-// past n read as zero.
+// past n read as zero. Row `skip` (if in range) is left to the caller.
 __device__ __forceinline__ void stage_chunk_async(uint8_t* dst, const uint16_t* src, int row0, int rows, int k0,
-                                                  int n, int ld, int tid) {
+                                                  int n, int ld, int tid, int skip) {
   for (int v = tid; v < rows * (WG_CHUNK / 8); v += THREADS) {
     const int r = v >> 3, kv = (v & 7) * 8;
+    if (r == skip) continue;
     const int k = k0 + kv;
     const uint16_t* p = src + (size_t)(row0 + r) * ld + k;
     uint8_t* d = dst + canon_offset(r, kv, WG_CHUNK);
@@ -531,18 +610,37 @@ __device__ __forceinline__ void stage_chunk_async(uint8_t* dst, const uint16_t* 
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// dW (one 128-row tile of output features) over one split of the batch:
-// 64-row chunks staged in two buffers, the next chunk loading while the
-// tensor cores work on the current one.
+// Rows [r0, r0 + rows) of a staged B chunk: row `ones` holds bf16 1.0 for
+// batch columns < n (0 past n), the others zero.
+__device__ __forceinline__ void stage_ones(uint8_t* dst, int r0, int rows, int ones, int k0, int n, int tid) {
+  for (int v = tid; v < rows * (WG_CHUNK / 8); v += THREADS) {
+    const int r = r0 + (v >> 3), kv = (v & 7) * 8;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (r == ones)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k0 + kv + j < n) w[j >> 1] |= 0x3F80u << (16 * (j & 1));
+    *reinterpret_cast<uint4*>(dst + canon_offset(r, kv, WG_CHUNK)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// One (layer, 128-row tile of output features) per cluster of G.S CTAs, CTA
+// rank = split of the batch (see above).
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int per_job = 2 * G.S;
-  const int jb = blockIdx.x / per_job, mt = (blockIdx.x / G.S) % 2, split = blockIdx.x % G.S;
+  const int S = G.S;
+  const int jb = blockIdx.x / (2 * S), mt = (blockIdx.x / S) % 2;
+  const int split = (int)cluster_ctarank();
   const WgJob J = G.job[jb];
-  const int N = J.N;
-  const uint32_t ncols = N >= 32 ? (uint32_t)N : 32u;  // TMEM columns (a power of two >= 32)
-  const uint32_t bar0 = smem_u32(smem + WG_BAR);
+  const bool wide = J.N == H;
+  const int NB = wide ? WG_NB : 16;                // B rows staged
+  const int ones = wide ? H : 9;                   // the row of ones
+  const uint32_t ncols = wide ? 512u : 32u;        // TMEM columns (a power of two >= NB)
+  const int LDr = NB + 4;                          // row stride of the partial in shared memory
+  const uint32_t s0 = smem_u32(smem);
+  const uint32_t bar0 = s0 + WG_BAR;
+  float* red = reinterpret_cast<float*>(smem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + WG_TMEM);
   if (tid == 0) {
     mbar_init(bar0, 1);
@@ -559,7 +657,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc(TILE, N);
+  constexpr uint32_t idesc_w = make_idesc(TILE, H), idesc_n = make_idesc(TILE, 16);
   const int c_first = split * G.chunks;
   const int c_end = min(c_first + G.chunks, (G.n + WG_CHUNK - 1) / WG_CHUNK);
   uint32_t commits[2] = {0u, 0u};  // MMA commits issued to each stage's barrier
@@ -570,8 +668,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   // while the tensor cores work on chunk c
   auto stage = [&](int cix) {
     uint8_t* sa = smem + ((cix - c_first) & 1) * WG_STAGE;
-    stage_chunk_async(sa, J.A, mt * TILE, TILE, cix * WG_CHUNK, G.n, G.ld, tid);
-    stage_chunk_async(sa + WG_STAGE_A, J.B, 0, N, cix * WG_CHUNK, G.n, G.ld, tid);
+    uint8_t* sb = sa + WG_STAGE_A;
+    const int k0 = cix * WG_CHUNK;
+    stage_chunk_async(sa, J.A, mt * TILE, TILE, k0, G.n, G.ld, tid, -1);
+    if (wide) {
+      stage_chunk_async(sb, J.B, 0, H, k0, G.n, G.ld, tid, -1);
+      stage_ones(sb, H, 16, ones, k0, G.n, tid);
+    } else {
+      stage_chunk_async(sb, J.B, 0, 16, k0, G.n, G.ld, tid, ones);
+      stage_ones(sb, ones, 1, ones, k0, G.n, tid);
+    }
   };
   if (c_first < c_end) stage(c_first);
   for (int cix = c_first; cix < c_end && ok; ++cix) {
@@ -596,14 +702,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
-    uint8_t* sa = smem + s * WG_STAGE;
-    uint8_t* sb = sa + WG_STAGE_A;
+    const uint32_t sa = s0 + s * WG_STAGE, sb = sa + WG_STAGE_A;
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int k = 0; k < WG_CHUNK / 16; ++k)
-        tc_mma(tmem, make_desc(smem_u32(sa) + 256 * k, 128, WG_CHUNK / 8 * 128),
-               make_desc(smem_u32(sb) + 256 * k, 128, WG_CHUNK / 8 * 128), idesc, (issued > 0 || k > 0) ? 1u : 0u);
+      for (int k = 0; k < WG_CHUNK / 16; ++k) {
+        const uint64_t ad = make_desc(sa + 256 * k, 128, WG_CHUNK / 8 * 128);
+        const uint32_t acc = (issued > 0 || k > 0) ? 1u : 0u;
+        if (wide) {
+          tc_mma(tmem, ad, make_desc(sb + 256 * k, 128, WG_CHUNK / 8 * 128), idesc_w, acc);
+          tc_mma(tmem + H, ad, make_desc(sb + H / 8 * 1024 + 256 * k, 128, WG_CHUNK / 8 * 128), idesc_n, acc);
+        } else {
+          tc_mma(tmem, ad, make_desc(sb + 256 * k, 128, WG_CHUNK / 8 * 128), idesc_n, acc);
+        }
+      }
       tc_commit(bar0 + 8 * s);
     }
     ++commits[s];
@@ -618,35 +730,86 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
     }
   tc_fence_after();
   ok = __syncthreads_and(ok) != 0;
-  if (!ok) {
-    if (tid == 0) latch_error(status, kDevTimeout);
-  } else {
-    // D row = output feature mt * 128 + lane quarter; columns = input features
+  // this split's partial [128][NB] into shared memory (over the stages)
+  if (ok) {
     const int quarter = warp & 3, half = warp >> 2;
-    const int o = mt * TILE + quarter * 32 + lane;
-    float* dst = J.part + ((size_t)split * H + o) * N;
+    const int row = quarter * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
-    if (N == H) {
+    float* dst = red + row * LDr;
+    auto put = [&](int c0, const uint32_t* r, int cnt) {
+      for (int j = 0; j < cnt; j += 4)
+        *reinterpret_cast<float4*>(dst + c0 + j) =
+            issued ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                 __uint_as_float(r[j + 3]))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    if (wide) {
 #pragma unroll 1
       for (int c0 = half * (H / 2); c0 < (half + 1) * (H / 2); c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tq + (uint32_t)c0, r);
-        if (issued == 0) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                  __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+        put(c0, r, 32);
       }
-    } else if (half == 0) {  // N = 16
+      if (half == 1) {
+        uint32_t r[16];
+        tmem_ld16(tq + (uint32_t)H, r);
+        put(H, r, 16);
+      }
+    } else if (half == 0) {
       uint32_t r[16];
       tmem_ld16(tq, r);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) dst[j] = issued ? __uint_as_float(r[j]) : 0.f;
+      put(0, r, 16);
     }
   }
+  // every split's partial is in its CTA's shared memory
+  tc_fence_before();
+  cluster_arrive();
+  cluster_wait();
+  // rows [split R, split R + R) of the tile: the S partials added in split order
+  if (ok) {
+    const int R = (TILE + S - 1) / S;
+    const int q4 = NB / 4;
+    for (int e = tid; e < R * q4; e += THREADS) {
+      const int row = split * R + e / q4, c = (e % q4) * 4;
+      if (row >= TILE) break;
+      const uint32_t a = s0 + (uint32_t)(row * LDr + c) * 4u;
+      float4 v[WG_MAX_S];
+#pragma unroll
+      for (int q = 0; q < WG_MAX_S; ++q)
+        if (q < S) v[q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
+      float4 t = v[0];
+#pragma unroll
+      for (int q = 1; q < WG_MAX_S; ++q)
+        if (q < S) {
+          t.x += v[q].x; t.y += v[q].y; t.z += v[q].z; t.w += v[q].w;
+        }
+      const int o = mt * TILE + row;
+      const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = c + j;
+        if (wide) {
+          if (cj < H) J.dW[(size_t)o * H + cj] = tv[j];
+          else if (cj == H) J.db[o] = tv[j];
+        } else {
+          if (cj < 9) J.dW[o * 9 + cj] = tv[j];
+          else if (cj == 9) J.db[o] = tv[j];
+        }
+      }
+    }
+  }
+  // no CTA leaves while another may still read its shared memory
+  cluster_arrive();
+  cluster_wait();
+  if (!ok && tid == 0) latch_error(status, kDevTimeout);
+  // the last layer: dW4 and db4 from the per-tile sums, in tile order
+  if (blockIdx.x == 0)
+    for (int o = tid; o <= H; o += THREADS) {
+      float t = 0.f;
+      for (int i = 0; i < G.tiles; ++i) t += G.tsum[(size_t)i * (H + 1) + o];
+      if (o < H) G.dW4[o] = t;
+      else *G.db4 = t;
+    }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -655,94 +818,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   }
 }
 
-// The rest of the gradients, one launch: the weight gradients as sums over
-// the splits in split order (dW1 [256][9], inputs 9..15 dropped; dW2, dW3
-// [256][256]), from blocks [0, red_blocks); then, one warp per output, the
-// bias gradients (sums of dA over the batch), dW4 = sum dz h3 and
-// db4 = sum dz, four bf16 per lane and load (rows are 32-byte aligned: ld is a
-// multiple of 16), four independent partial sums per lane.
-struct FinishArgs {
-  float* dW[3];
-  float* db[3];
-  float* dW4;
-  float* db4;
-  const uint16_t* daT[3];
-  const uint16_t* h3T;
-  const float* dz;
-  int red_blocks;
-};
-
-__global__ void mlp_grad_finish_kernel(WgArgs G, FinishArgs F) {
-  if ((int)blockIdx.x < F.red_blocks) {
-    const int n1 = H * 16, n2 = H * H;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + 2 * n2; e += F.red_blocks * blockDim.x) {
-      const int jb = e < n1 ? 0 : e < n1 + n2 ? 1 : 2;
-      const int idx = jb == 0 ? e : jb == 1 ? e - n1 : e - n1 - n2;
-      const int N = jb == 0 ? 16 : H;
-      const float* part = jb == 0 ? G.job[0].part : jb == 1 ? G.job[1].part : G.job[2].part;
-      const int o = idx / N, i = idx % N;
-      if (jb == 0 && i >= 9) continue;
-      float v[16];
-#pragma unroll
-      for (int s = 0; s < 16; ++s) v[s] = s < G.S ? part[((size_t)s * H + o) * N + i] : 0.f;  // loads in flight together
-      float acc = 0.f;
-#pragma unroll
-      for (int s = 0; s < 16; ++s) acc += v[s];  // split order
-      if (jb == 0) F.dW[0][o * 9 + i] = acc;
-      else F.dW[jb][o * H + i] = acc;
-    }
-    return;
-  }
-  // rows 0..H-1: db1, H..2H-1: db2, 2H..3H-1: db3, 3H..4H-1: dW4, 4H: db4
-  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  const int w = ((int)blockIdx.x - F.red_blocks) * warps + (threadIdx.x >> 5);
-  const int B = G.n, B4 = G.n & ~3;
-  for (int row = w; row <= 4 * H; row += ((int)gridDim.x - F.red_blocks) * warps) {
-    float acc = 0.f;
-    if (row < 4 * H) {
-      const bool dot = row >= 3 * H;
-      const uint16_t* src = row < H ? F.daT[0] : row < 2 * H ? F.daT[1] : row < 3 * H ? F.daT[2] : F.h3T;
-      const uint16_t* p = src + (size_t)(row % H) * G.ld;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      for (int s = 4 * lane; s < B4; s += 128) {
-        const uint2 v = *reinterpret_cast<const uint2*>(p + s);
-        if (dot) {
-          const float4 d = *reinterpret_cast<const float4*>(F.dz + s);
-          a0 = fmaf(bf16_lo(v.x), d.x, a0); a1 = fmaf(bf16_hi(v.x), d.y, a1);
-          a2 = fmaf(bf16_lo(v.y), d.z, a2); a3 = fmaf(bf16_hi(v.y), d.w, a3);
-        } else {
-          a0 += bf16_lo(v.x); a1 += bf16_hi(v.x); a2 += bf16_lo(v.y); a3 += bf16_hi(v.y);
-        }
-      }
-      for (int s = B4 + lane; s < B; s += 32) {
-        const float x = __uint_as_float((uint32_t)p[s] << 16);
-        a0 = dot ? fmaf(x, F.dz[s], a0) : a0 + x;
-      }
-      acc = (a0 + a1) + (a2 + a3);
-    } else {
-      for (int s = lane; s < B; s += 32) acc += F.dz[s];
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-    if (lane == 0) {
-      if (row < 3 * H) F.db[row / H][row % H] = acc;
-      else if (row < 4 * H) F.dW4[row - 3 * H] = acc;
-      else *F.db4 = acc;
-    }
-  }
-}
-
 }  // namespace
 
-size_t mlp_train_tc_part_bytes(int Bcap) {
-  const int S = mlp_train_tc_splits(Bcap);
-  return (size_t)S * H * (16 + 2 * H) * 4;
-}
-
-int mlp_train_tc_splits(int Bcap) {
-  const int chunks = (Bcap + WG_CHUNK - 1) / WG_CHUNK;
-  return chunks < 16 ? chunks : 16;
-}
+size_t mlp_train_tc_part_bytes(int Bcap) { return (size_t)((Bcap + TILE - 1) / TILE) * (H + 1) * 4; }
 
 cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s) {
   if (L.n <= 0) return cudaSuccess;
@@ -762,12 +840,11 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     A.inv_n = 1.f / (float)L.n;
     A.logits = L.logits;
     A.x16T = L.x16T;
-    for (int l = 0; l < 3; ++l) {
-      A.hT[l] = L.hT[l];
-      A.daT[l] = L.daT[l];
-    }
+    for (int l = 0; l < 3; ++l) A.daT[l] = L.daT[l];
+    for (int l = 0; l < 2; ++l) A.hT[l] = L.hT[l];
     A.dz = L.dz;
     A.loss_sum = L.loss_sum;
+    A.tsum = L.wg_part;
     if ((e = cudaFuncSetAttribute(mlp_train_fb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_TOTAL)))
       return e;
     cudaLaunchConfig_t cfg = {};
@@ -784,37 +861,46 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     cfg.numAttrs = 1;
     if ((e = cudaLaunchKernelEx(&cfg, mlp_train_fb_kernel, A, L.status))) return e;
   }
-  // ---- weight gradients: dW1 = dA1^T X, dW2 = dA2^T H1, dW3 = dA3^T H2
+  // ---- weight and bias gradients, split-K over the CTAs of a cluster
   {
     WgArgs G;
     G.n = L.n;
     G.ld = L.ld;
-    G.S = mlp_train_tc_splits(L.n);
     const int chunks = (L.n + WG_CHUNK - 1) / WG_CHUNK;
-    G.chunks = (chunks + G.S - 1) / G.S;
-    float* part = L.wg_part;
-    G.job[0] = WgJob{L.daT[0], L.x16T, 16, part};
-    G.job[1] = WgJob{L.daT[1], L.hT[0], H, part + (size_t)G.S * H * 16};
-    G.job[2] = WgJob{L.daT[2], L.hT[1], H, part + (size_t)G.S * H * (16 + H)};
-    if ((e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_TOTAL))) return e;
-    mlp_tc_wgrad_kernel<<<3 * 2 * G.S, THREADS, WG_TOTAL, s>>>(G, L.status);
-    if ((e = cudaGetLastError())) return e;
-    FinishArgs F;
-    F.dW[0] = L.dW1;
-    F.dW[1] = L.dW2;
-    F.dW[2] = L.dW3;
-    for (int l = 0; l < 3; ++l) {
-      F.db[l] = L.db[l];
-      F.daT[l] = L.daT[l];
+    G.job[0] = WgJob{L.daT[0], L.x16T, 16, L.dW1, L.db[0]};
+    G.job[1] = WgJob{L.daT[1], L.hT[0], H, L.dW2, L.db[1]};
+    G.job[2] = WgJob{L.daT[2], L.hT[1], H, L.dW3, L.db[2]};
+    G.tsum = L.wg_part;
+    G.tiles = ntiles;
+    G.dW4 = L.dW4;
+    G.db4 = L.db4;
+    if ((e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_TOTAL)))
+      return e;
+    if ((e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = WG_TOTAL;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // the most splits (up to 16) whose six clusters can all be resident
+    int S = chunks < WG_MAX_S ? chunks : WG_MAX_S;
+    for (; S > 1; S = S > 8 ? 8 : S / 2) {
+      at[0].val.clusterDim.x = (unsigned)S;
+      cfg.gridDim = dim3((unsigned)(3 * 2 * S));
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, mlp_tc_wgrad_kernel, &cfg) == cudaSuccess && clusters >= 6) break;
+      (void)cudaGetLastError();
     }
-    F.dW4 = L.dW4;
-    F.db4 = L.db4;
-    F.h3T = L.hT[2];
-    F.dz = L.dz;
-    F.red_blocks = 2 * num_sms;
-    const int bias_blocks = (4 * H + 1 + 7) / 8;  // one warp per output, 8 warps per block
-    mlp_grad_finish_kernel<<<F.red_blocks + bias_blocks, 256, 0, s>>>(G, F);
-    if ((e = cudaGetLastError())) return e;
+    G.S = S;
+    G.chunks = (chunks + S - 1) / S;
+    at[0].val.clusterDim.x = (unsigned)S;
+    cfg.gridDim = dim3((unsigned)(3 * 2 * S));
+    if ((e = cudaLaunchKernelEx(&cfg, mlp_tc_wgrad_kernel, G, L.status))) return e;
   }
   return cudaSuccess;
 }
