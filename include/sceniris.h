@@ -406,6 +406,15 @@ typedef struct {
  * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
  * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
 sc_status sc_mlp_adam_step(sc_ctx* ctx, sc_mlp* mlp, const float* grads, const sc_train_params* params);
+/* One training step on n labelled targets (device, rows in the given order):
+ * the gradients of sc_surrogate_grads and the Adam update of
+ * sc_mlp_adam_step in one pass (the weight-gradient kernel applies the
+ * update to each gradient as it writes it), leaving the same parameters,
+ * moments, step count and gradients as those two calls. The batch limits of
+ * sc_surrogate_grads apply (params->batch is not used). loss (host, may be
+ * NULL) receives the mean BCE. */
+sc_status sc_mlp_train_step(sc_ctx* ctx, sc_mlp* mlp, const float* targets, const uint8_t* labels, int32_t n,
+                            const sc_train_params* params, float* loss);
 /* Train on n labelled targets (device): a fresh network (Adam step 0) first
  * takes its standardisation from the training set; every epoch visits the
  * targets in a shuffled order (an affine permutation mod n) in whole

@@ -134,6 +134,7 @@ SIGNATURES = {
     "sc_surrogate_infer": (ctypes.c_int, [P, P, P, I32, P]),
     "sc_surrogate_grads": (ctypes.c_int, [P, P, P, P, I32, P, P]),
     "sc_mlp_adam_step": (ctypes.c_int, [P, P, P, ctypes.POINTER(ScTrainParams)]),
+    "sc_mlp_train_step": (ctypes.c_int, [P, P, P, P, I32, ctypes.POINTER(ScTrainParams), P]),
     "sc_surrogate_train": (ctypes.c_int, [P, P, P, P, I32, ctypes.POINTER(ScTrainParams), P]),
     "sc_surrogate_tune_threshold": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, P]),
     "sc_mlp_save": (ctypes.c_int, [P, P, ctypes.c_char_p]),
@@ -493,6 +494,13 @@ class Surrogate:
 
     def adam_step(self, grads: torch.Tensor | None, params: ScTrainParams):
         _check(lib().sc_mlp_adam_step(self.ctx.handle, self.handle, _ptr(grads), ctypes.byref(params)))
+
+    def train_step(self, targets: torch.Tensor, labels: torch.Tensor, params: ScTrainParams) -> float:
+        """One gradient + Adam step on the rows in order; returns the mean BCE."""
+        loss = ctypes.c_float()
+        _check(lib().sc_mlp_train_step(self.ctx.handle, self.handle, _ptr(targets), _ptr(labels), targets.shape[0],
+                                       ctypes.byref(params), ctypes.byref(loss)))
+        return loss.value
 
     def train(self, targets: torch.Tensor, labels: torch.Tensor, params: ScTrainParams):
         loss = np.zeros(max(1, params.epochs), np.float32)

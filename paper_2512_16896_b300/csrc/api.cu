@@ -678,6 +678,27 @@ static sc_status check_train(const sc_train_params* p) {
   return SC_OK;
 }
 
+sc_status sc_mlp_train_step(sc_ctx* ctx, sc_mlp* m, const float* targets, const uint8_t* labels, int32_t n,
+                            const sc_train_params* p, float* loss) {
+  g_err.clear();
+  if (sc_status s = check_ctx(ctx)) return s;
+  if (!m) return fail(SC_ERR_INVALID, "mlp is NULL");
+  if (sc_status s = check_train(p)) return s;
+  if (n < 1 || n > (1 << 20)) return fail(SC_ERR_INVALID, "n = %d outside 1..2^20", n);
+  if (!targets || !labels) return fail(SC_ERR_INVALID, "targets or labels is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = sc::mlp_reserve(m->st, n);
+  if (e) return fail(SC_ERR_OOM, "surrogate training buffers: %s", cudaGetErrorString(e));
+  e = sc::mlp_train_step(m->st, targets, labels, nullptr, n, m->loss_dev, ctx->d_status, ctx->num_sms, p->lr,
+                         p->beta1, p->beta2, p->eps, ctx->stream);
+  if (!e && loss) {
+    e = cudaMemcpyAsync(loss, m->loss_dev, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e) return cuda_fail(e, "training step");
+  return SC_OK;
+}
+
 sc_status sc_mlp_adam_step(sc_ctx* ctx, sc_mlp* m, const float* grads, const sc_train_params* p) {
   g_err.clear();
   if (sc_status s = check_ctx(ctx)) return s;
@@ -721,9 +742,8 @@ sc_status sc_surrogate_train(sc_ctx* ctx, sc_mlp* m, const float* targets, const
     if (e) return cuda_fail(e, "epoch shuffle");
     float loss_acc = 0.f;
     for (int bi = 0; bi < nb; ++bi) {
-      e = sc::mlp_gradients(m->st, targets, labels, m->index + (size_t)bi * p->batch, p->batch, m->loss_dev,
-                            ctx->d_status, ctx->num_sms, ctx->stream);
-      if (!e) e = sc::mlp_adam(m->st, p->lr, p->beta1, p->beta2, p->eps, ctx->stream);
+      e = sc::mlp_train_step(m->st, targets, labels, m->index + (size_t)bi * p->batch, p->batch, m->loss_dev,
+                             ctx->d_status, ctx->num_sms, p->lr, p->beta1, p->beta2, p->eps, ctx->stream);
       if (e) return cuda_fail(e, "training step");
       if (loss_per_epoch && bi == nb - 1) {  // the epoch's last batch reports its mean BCE
         float l = 0.f;

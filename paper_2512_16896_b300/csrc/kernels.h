@@ -158,6 +158,9 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
 // forward pass with its caches, the backward pass through the activations
 // and the weight gradients dW1..dW3 (bias and last-layer gradients are
 // summed by the caller). Feature-major arrays have row stride ld.
+namespace mlpp {
+struct AdamArgs;
+}
 struct TrainTcLaunch {
   MlpTcWeights w;
   const void* W2tc;  // bf16 canonical [in][out] copies (B operands of dH = dA W)
@@ -171,7 +174,7 @@ struct TrainTcLaunch {
   uint16_t* hT[2];       // [256][ld] h1, h2
   uint16_t* daT[3];      // [256][ld]
   float* dz;             // [n]
-  float* loss_sum;       // zeroed by the caller
+  float* loss_sum;       // the mean BCE (written by the step)
   float* wg_part;        // mlp_train_tc_part_bytes(ld): per-tile sums of dz h3 and dz
   float* dW1;            // [256][9]
   float* dW2;            // [256][256]
@@ -180,10 +183,17 @@ struct TrainTcLaunch {
   float* dW4;            // [256]
   float* db4;            // [1]
   int* status;
+  const mlpp::AdamArgs* adam;  // non-NULL: Adam on every parameter as its gradient is written
 };
 size_t mlp_train_tc_part_bytes(int Bcap);
 cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s);
 cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s);
+// One training step: the gradients of rows index[0..B) (as mlp_gradients)
+// with the Adam update (as mlp_adam) applied by the weight-gradient kernel
+// to each gradient it writes.
+cudaError_t mlp_train_step(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
+                           float* loss_dev, int* status, int num_sms, float lr, float b1, float b2, float eps,
+                           cudaStream_t s);
 cudaError_t mlp_epoch_index(int n, uint64_t seed, int epoch, int32_t* index, cudaStream_t s);
 float* mlp_params_ptr(MlpState* S);
 float* mlp_grads_ptr(MlpState* S);

@@ -19,18 +19,23 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mlp_adam.cuh"
 
 namespace sc {
 
 namespace {
 
-constexpr int H = 256;     // hidden width
-constexpr int KIN = 16;    // 9 input features padded to one k16 step
-
-// packed parameter offsets
-constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * 9, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
-              OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * H, OFF_W4 = OFF_B3 + H, OFF_B4 = OFF_W4 + H,
-              N_PARAMS = OFF_B4 + 1;
+using mlpp::H;
+using mlpp::KIN;
+using mlpp::OFF_W1;
+using mlpp::OFF_B1;
+using mlpp::OFF_W2;
+using mlpp::OFF_B2;
+using mlpp::OFF_W3;
+using mlpp::OFF_B3;
+using mlpp::OFF_W4;
+using mlpp::OFF_B4;
+using mlpp::N_PARAMS;
 
 // Features of one target (12 floats).
 __device__ __forceinline__ void features(const float* t, float x[9]) {
@@ -41,32 +46,9 @@ __device__ __forceinline__ void features(const float* t, float x[9]) {
 
 // Adam on the FP32 masters (step t, 1-based); each updated weight also
 // rewrites its bf16 copies in the canonical layouts (as mlp_copies_kernel).
-__global__ void mlp_adam_kernel(float* params, const float* grads, float* m, float* v, int n, float lr, float b1,
-                                float b2, float eps, float bc1, float bc2, __nv_bfloat16* W4, __nv_bfloat16* W1c,
-                                __nv_bfloat16* W2c, __nv_bfloat16* W3c, __nv_bfloat16* W2tc, __nv_bfloat16* W3tc) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = grads[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float p = params[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    params[i] = p;
-    const __nv_bfloat16 h = __float2bfloat16_rn(p);
-    if (i < OFF_B1) {  // W1 [256][9] -> canonical [256][16] (columns 9..15 stay zero)
-      W1c[canon_offset(i / 9, i % 9, KIN) / 2] = h;
-    } else if (i >= OFF_W2 && i < OFF_B2) {
-      const int o = (i - OFF_W2) / H, k = (i - OFF_W2) % H;
-      W2c[canon_offset(o, k, H) / 2] = h;
-      W2tc[canon_offset(k, o, H) / 2] = h;
-    } else if (i >= OFF_W3 && i < OFF_B3) {
-      const int o = (i - OFF_W3) / H, k = (i - OFF_W3) % H;
-      W3c[canon_offset(o, k, H) / 2] = h;
-      W3tc[canon_offset(k, o, H) / 2] = h;
-    } else if (i >= OFF_W4 && i < OFF_B4) {
-      W4[i - OFF_W4] = h;
-    }
-  }
+__global__ void mlp_adam_kernel(mlpp::AdamArgs a, const float* grads, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    mlpp::adam_update(a, i, grads[i]);
 }
 
 // bf16 copies of the weights in the tensor cores' canonical K-major layout:
@@ -298,13 +280,11 @@ cudaError_t mlp_reserve(MlpState* S, int Bcap) {
 // the tcgen05 forward, backward and weight-gradient contractions and the
 // bias and last-layer sums (mlp_train_tc.cu). Rows past B are never read
 // (the weight-gradient staging masks them).
-cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
-                          float* loss_dev, int* status, int num_sms, cudaStream_t s) {
+static cudaError_t gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
+                             float* loss_dev, int* status, int num_sms, const mlpp::AdamArgs* adam, cudaStream_t s) {
   if (B > S->Bcap) return cudaErrorInvalidValue;
   TrainViews v = carve(S, S->Bcap);
   float* loss = loss_dev ? loss_dev : v.loss_sum;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(loss, 0, 4, s))) return e;
   TrainTcLaunch L;
   L.w = tc_view(*S);
   L.W2tc = S->W2tc;
@@ -330,16 +310,49 @@ cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labe
   L.dW4 = S->grads + OFF_W4;
   L.db4 = S->grads + OFF_B4;
   L.status = status;
+  L.adam = adam;
   return mlp_train_tc_step(L, num_sms, s);
 }
 
-cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s) {
+// The Adam arguments of the next step (advances the step count).
+static mlpp::AdamArgs next_adam(MlpState* S, float lr, float b1, float b2, float eps) {
   S->step += 1;
   const double t = (double)S->step;
-  mlp_adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, s>>>(S->params, S->grads, S->m, S->v, N_PARAMS, lr, b1, b2, eps,
-                                                         (float)(1.0 - pow((double)b1, t)),
-                                                         (float)(1.0 - pow((double)b2, t)), S->W4, S->W1c, S->W2c,
-                                                         S->W3c, S->W2tc, S->W3tc);
+  mlpp::AdamArgs a;
+  a.params = S->params;
+  a.m = S->m;
+  a.v = S->v;
+  a.lr = lr;
+  a.b1 = b1;
+  a.b2 = b2;
+  a.eps = eps;
+  a.bc1 = (float)(1.0 - pow((double)b1, t));
+  a.bc2 = (float)(1.0 - pow((double)b2, t));
+  a.W4 = S->W4;
+  a.W1c = S->W1c;
+  a.W2c = S->W2c;
+  a.W3c = S->W3c;
+  a.W2tc = S->W2tc;
+  a.W3tc = S->W3tc;
+  return a;
+}
+
+cudaError_t mlp_gradients(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
+                          float* loss_dev, int* status, int num_sms, cudaStream_t s) {
+  return gradients(S, targets, labels, index, B, loss_dev, status, num_sms, nullptr, s);
+}
+
+cudaError_t mlp_train_step(MlpState* S, const float* targets, const uint8_t* labels, const int32_t* index, int B,
+                           float* loss_dev, int* status, int num_sms, float lr, float b1, float b2, float eps,
+                           cudaStream_t s) {
+  if (B > S->Bcap) return cudaErrorInvalidValue;
+  const mlpp::AdamArgs a = next_adam(S, lr, b1, b2, eps);
+  return gradients(S, targets, labels, index, B, loss_dev, status, num_sms, &a, s);
+}
+
+cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  const mlpp::AdamArgs a = next_adam(S, lr, b1, b2, eps);
+  mlp_adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, s>>>(a, S->grads, N_PARAMS);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,9 @@
 // pre-activations, accumulations and gradients in FP32. Every mbarrier wait is
 // bounded; on timeout the CTA latches kDevTimeout, drains its own copies and
 // MMAs, frees TMEM and returns.
+#include <cstring>
+
+#include "mlp_adam.cuh"
 #include "mlp_tc_core.cuh"
 
 namespace sc {
@@ -49,6 +52,7 @@ __device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x 
 // CTA has initialised its mbarriers before it is sent anything; none leaves
 // while its copies may still be read), and every CTA passes both, whatever
 // its bounded waits did.
+constexpr int TS_LD = H + 2;  // per-tile sums: dW4 (256), db4, the BCE sum
 constexpr int FB_CTAS = 4;
 constexpr int FB_NS = H / FB_CTAS;                     // features per CTA
 constexpr int FB_BLK = TILE * FB_NS * 2;               // one CTA's block of an operand, 16 KB
@@ -88,8 +92,7 @@ struct FbArgs {
   uint16_t* hT[2];        // [256][ld] h1, h2, bf16, feature-major
   uint16_t* daT[3];       // [256][ld] dL/da1, da2, da3, bf16, feature-major
   float* dz;              // [n] dL/dz
-  float* loss_sum;        // mean BCE (sum / n)
-  float* tsum;            // [tiles][257] over each tile's rows: dW4 = sum dz h3 (256), db4 = sum dz
+  float* tsum;            // [tiles][TS_LD] over each tile's rows: dW4 = sum dz h3 (256), db4 = sum dz, the BCE sum
 };
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -417,13 +420,13 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     }
     sdz[tid] = bf16_round(dz);
     sdzf[tid] = dz;
-    if (rank == 0) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
-      if (lane == 0) atomicAdd(A.loss_sum, loss * A.inv_n);
-    }
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+    if (lane == 0) shalf[warp] = loss;
   }
   __syncthreads();
+  if (ok && rank == 0 && tid == 0)  // the tile's BCE sum, its four warps in order
+    A.tsum[(size_t)tile * TS_LD + H + 1] = ((shalf[0] + shalf[1]) + shalf[2]) + shalf[3];
   // ---- backward. dA3 = bf16(bf16(dz) W4 * SiLU'(z3)) into A1
   if (ok) {
     uint32_t g[32], hw[16];
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
 #pragma unroll
       for (int j = 0; j < 8; ++j) sred[(warp >> 1) * FB_NS + kg * 8 + j] = acc[j];
     __syncthreads();
-    float* ts = A.tsum + (size_t)tile * (H + 1);
+    float* ts = A.tsum + (size_t)tile * TS_LD;
     if (tid < FB_NS) ts[fs + tid] = ((sred[tid] + sred[FB_NS + tid]) + sred[2 * FB_NS + tid]) + sred[3 * FB_NS + tid];
     if (rank == 0 && tid == FB_NS) {
       float t = 0.f;
@@ -527,8 +530,10 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
 // cluster; each CTA accumulates its split in TMEM, copies it to its shared
 // memory, and after a cluster barrier sums one slice of rows over all S
 // partials in split order (distributed shared-memory loads), writing dW and
-// db directly. Thread block (0) also adds the fused kernel's per-tile sums
-// of dW4 and db4 in tile order.
+// db directly. The fused kernel's per-tile sums of dW4, db4 and the loss are
+// added by a warp per output while the first chunk is staged. With Adam arguments, the CTA that writes a
+// gradient also applies the Adam update to its parameter (a training step
+// then needs no separate update launch).
 
 struct WgJob {
   const uint16_t* A;  // dL/da feature-major [256][ld]: A operand rows = output features
@@ -536,6 +541,7 @@ struct WgJob {
   int N;              // 256, or 16 for the first layer (9 inputs padded to 16)
   float* dW;          // [256][256], or [256][9]
   float* db;          // [256]
+  int off_w, off_b;   // offsets of dW and db in the packed parameters
 };
 
 struct WgArgs {
@@ -544,20 +550,24 @@ struct WgArgs {
   int ld;
   int S;         // K splits = CTAs per cluster
   int chunks;    // 64-row chunks per split
-  const float* tsum;  // [tiles][257] per-tile sums of dz h3 | dz
+  const float* tsum;  // [tiles][TS_LD] per-tile sums of dz h3 | dz | BCE
   int tiles;
   float* dW4;    // [256]
   float* db4;    // [1]
+  float* loss;   // mean BCE
+  float inv_n;
+  mlpp::AdamArgs adam;  // params NULL: gradients only
 };
 
 constexpr int WG_CHUNK = 64;                            // batch rows per staged chunk (K)
 constexpr int WG_NB = H + 16;                           // B rows staged: inputs, then the ones block
 constexpr int WG_STAGE_A = 128 * WG_CHUNK * 2;          // 16 KB
 constexpr int WG_STAGE = WG_STAGE_A + WG_NB * WG_CHUNK * 2;  // + 34 KB
+constexpr int WG_NST = 4;                               // chunk stages in flight
 constexpr int WG_LD = WG_NB + 4;                        // floats per row of a CTA's partial (padded)
 constexpr int WG_RED = TILE * WG_LD * 4;                // the partial, over the stages once they are read
-constexpr int WG_BAR = (2 * WG_STAGE > WG_RED ? 2 * WG_STAGE : WG_RED);  // 2 mbarriers
-constexpr int WG_TMEM = WG_BAR + 16;
+constexpr int WG_BAR = (WG_NST * WG_STAGE > WG_RED ? WG_NST * WG_STAGE : WG_RED);  // WG_NST mbarriers
+constexpr int WG_TMEM = WG_BAR + 8 * WG_NST;
 constexpr int WG_TOTAL = WG_TMEM + 16;
 constexpr int WG_MAX_S = 16;
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory of one CTA");
@@ -585,7 +595,8 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
 // bf16 matrix into the canonical K-major layout (K = 64) by asynchronous
 // 16-byte copies (cp.async; whole vectors past n are zero-filled by the copy,
 // a vector that straddles n is assembled by the thread); batch columns at or
-// past n read as zero. Row `skip` (if in range) is left to the caller.
+// past n read as zero. Row `skip` (if in range) is left to the caller; the
+// caller commits the copies as a group.
 __device__ __forceinline__ void stage_chunk_async(uint8_t* dst, const uint16_t* src, int row0, int rows, int k0,
                                                   int n, int ld, int tid, int skip) {
   for (int v = tid; v < rows * (WG_CHUNK / 8); v += THREADS) {
@@ -607,7 +618,6 @@ __device__ __forceinline__ void stage_chunk_async(uint8_t* dst, const uint16_t* 
                                                 e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
     }
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Rows [r0, r0 + rows) of a staged B chunk: row `ones` holds bf16 1.0 for
@@ -642,10 +652,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   const uint32_t bar0 = s0 + WG_BAR;
   float* red = reinterpret_cast<float*>(smem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + WG_TMEM);
-  if (tid == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
-  }
+  if (tid == 0)
+    for (int i = 0; i < WG_NST; ++i) mbar_init(bar0 + 8 * i, 1);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(ncols)
@@ -660,14 +668,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   constexpr uint32_t idesc_w = make_idesc(TILE, H), idesc_n = make_idesc(TILE, 16);
   const int c_first = split * G.chunks;
   const int c_end = min(c_first + G.chunks, (G.n + WG_CHUNK - 1) / WG_CHUNK);
-  uint32_t commits[2] = {0u, 0u};  // MMA commits issued to each stage's barrier
-  uint32_t waited[2] = {0u, 0u};   // phases of each barrier already waited for
+  uint32_t commits[WG_NST] = {};  // MMA commits issued to each stage's barrier
+  uint32_t waited[WG_NST] = {};   // phases of each barrier already waited for
   bool ok = true;
   int issued = 0;
-  // chunk c is staged in buffer (c - c_first) & 1; chunk c + 1 is copied in
-  // while the tensor cores work on chunk c
+  // chunk c is staged in buffer (c - c_first) % WG_NST, up to WG_NST chunks
+  // in flight; a buffer is restaged once the MMAs that read it are done
   auto stage = [&](int cix) {
-    uint8_t* sa = smem + ((cix - c_first) & 1) * WG_STAGE;
+    uint8_t* sa = smem + ((cix - c_first) % WG_NST) * WG_STAGE;
     uint8_t* sb = sa + WG_STAGE_A;
     const int k0 = cix * WG_CHUNK;
     stage_chunk_async(sa, J.A, mt * TILE, TILE, k0, G.n, G.ld, tid, -1);
@@ -678,27 +686,36 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
       stage_chunk_async(sb, J.B, 0, 16, k0, G.n, G.ld, tid, ones);
       stage_ones(sb, ones, 1, ones, k0, G.n, tid);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  if (c_first < c_end) stage(c_first);
-  for (int cix = c_first; cix < c_end && ok; ++cix) {
-    const int s = (cix - c_first) & 1;
-    const bool more = cix + 1 < c_end;
-    if (more) {
-      const int s1 = s ^ 1;
-      if (commits[s1] > waited[s1]) {  // the MMAs that last read the next buffer are done
-        ok = mbar_wait(bar0 + 8 * s1, waited[s1] & 1);
-        if (ok) ++waited[s1];
+  const int nc = c_end > c_first ? c_end - c_first : 0;
+  for (int i = 0; i < nc && i < WG_NST; ++i) stage(c_first + i);
+  // meanwhile the last layer's dW4 and db4 and the mean BCE from the fused
+  // kernel's per-tile sums: a warp per output, lanes over the tiles, a
+  // butterfly across the lanes
+  for (int o = blockIdx.x * (THREADS / 32) + warp; o < TS_LD; o += gridDim.x * (THREADS / 32)) {
+    float t = 0.f;
+    for (int i = lane; i < G.tiles; i += 32) t += G.tsum[(size_t)i * TS_LD + o];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+    if (lane == 0) {
+      if (o == H + 1) {
+        *G.loss = t * G.inv_n;
+      } else {
+        if (o < H) G.dW4[o] = t;
+        else *G.db4 = t;
+        if (G.adam.params) mlpp::adam_update(G.adam, o < H ? mlpp::OFF_W4 + o : mlpp::OFF_B4, t);
       }
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      stage(cix + 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of chunk cix landed
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
+  }
+  for (int i = 0; i < nc && ok; ++i) {
+    const int s = i % WG_NST;
+    // chunk i landed (this thread's copies; later chunks may stay in flight)
+    const int later = min(nc - 1 - i, WG_NST - 1);
+    if (later >= 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
+    else if (later == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (later == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -720,10 +737,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
     }
     ++commits[s];
     ++issued;
+    if (i + WG_NST < nc) {  // restage this buffer with chunk i + WG_NST once its MMAs are done
+      ok = mbar_wait(bar0 + 8 * s, waited[s] & 1);
+      if (ok) ++waited[s];
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      stage(c_first + i + WG_NST);
+    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing of this thread's left in flight
   // every commit made must be waited for before TMEM is read or freed
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < WG_NST; ++s)
     while (commits[s] > waited[s]) {
       if (!mbar_wait(bar0 + 8 * s, waited[s] & 1)) ok = false;
       ++waited[s];
@@ -765,36 +792,61 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   tc_fence_before();
   cluster_arrive();
   cluster_wait();
-  // rows [split R, split R + R) of the tile: the S partials added in split order
+  // rows [split R, split R + R) of the tile: the S partials added in split
+  // order; the gradients written, then (with Adam arguments) the updates of
+  // up to 12 parameters at a time with their loads in flight together
   if (ok) {
     const int R = (TILE + S - 1) / S;
     const int q4 = NB / 4;
-    for (int e = tid; e < R * q4; e += THREADS) {
-      const int row = split * R + e / q4, c = (e % q4) * 4;
-      if (row >= TILE) break;
-      const uint32_t a = s0 + (uint32_t)(row * LDr + c) * 4u;
-      float4 v[WG_MAX_S];
+    const int nw = wide ? H : 9;  // weights per output feature
+    for (int e0 = tid; e0 < R * q4; e0 += 3 * THREADS) {
+      float val[12];
+      int pidx[12];
 #pragma unroll
-      for (int q = 0; q < WG_MAX_S; ++q)
-        if (q < S) v[q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
-      float4 t = v[0];
+      for (int k = 0; k < 3; ++k) {
 #pragma unroll
-      for (int q = 1; q < WG_MAX_S; ++q)
-        if (q < S) {
-          t.x += v[q].x; t.y += v[q].y; t.z += v[q].z; t.w += v[q].w;
+        for (int j = 0; j < 4; ++j) pidx[4 * k + j] = -1;
+        const int e = e0 + k * THREADS;
+        const int row = split * R + e / q4, c = (e % q4) * 4;
+        if (e >= R * q4 || row >= TILE) continue;
+        const uint32_t a = s0 + (uint32_t)(row * LDr + c) * 4u;
+        float4 v[WG_MAX_S];
+#pragma unroll
+        for (int q = 0; q < WG_MAX_S; ++q)
+          if (q < S) v[q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
+        float4 t = v[0];
+#pragma unroll
+        for (int q = 1; q < WG_MAX_S; ++q)
+          if (q < S) {
+            t.x += v[q].x; t.y += v[q].y; t.z += v[q].z; t.w += v[q].w;
+          }
+        const int o = mt * TILE + row;
+        const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int cj = c + j;
+          val[4 * k + j] = tv[j];
+          if (cj < nw) {
+            J.dW[o * nw + cj] = tv[j];
+            pidx[4 * k + j] = J.off_w + o * nw + cj;
+          } else if (cj == nw) {
+            J.db[o] = tv[j];
+            pidx[4 * k + j] = J.off_b + o;
+          }
         }
-      const int o = mt * TILE + row;
-      const float tv[4] = {t.x, t.y, t.z, t.w};
+      }
+      if (G.adam.params) {
+        float m0[12], v0[12], p0[12];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cj = c + j;
-        if (wide) {
-          if (cj < H) J.dW[(size_t)o * H + cj] = tv[j];
-          else if (cj == H) J.db[o] = tv[j];
-        } else {
-          if (cj < 9) J.dW[o * 9 + cj] = tv[j];
-          else if (cj == 9) J.db[o] = tv[j];
-        }
+        for (int k = 0; k < 12; ++k)
+          if (pidx[k] >= 0) {
+            m0[k] = G.adam.m[pidx[k]];
+            v0[k] = G.adam.v[pidx[k]];
+            p0[k] = G.adam.params[pidx[k]];
+          }
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          if (pidx[k] >= 0) mlpp::adam_apply(G.adam, pidx[k], val[k], m0[k], v0[k], p0[k]);
       }
     }
   }
@@ -802,14 +854,6 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   cluster_arrive();
   cluster_wait();
   if (!ok && tid == 0) latch_error(status, kDevTimeout);
-  // the last layer: dW4 and db4 from the per-tile sums, in tile order
-  if (blockIdx.x == 0)
-    for (int o = tid; o <= H; o += THREADS) {
-      float t = 0.f;
-      for (int i = 0; i < G.tiles; ++i) t += G.tsum[(size_t)i * (H + 1) + o];
-      if (o < H) G.dW4[o] = t;
-      else *G.db4 = t;
-    }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -820,12 +864,45 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
 
 }  // namespace
 
-size_t mlp_train_tc_part_bytes(int Bcap) { return (size_t)((Bcap + TILE - 1) / TILE) * (H + 1) * 4; }
+size_t mlp_train_tc_part_bytes(int Bcap) { return (size_t)((Bcap + TILE - 1) / TILE) * TS_LD * 4; }
+
+namespace {
+
+// Per device: the kernels' attributes set, and the split count chosen for
+// each chunk count up to WG_MAX_S (0: not yet), so that a training step
+// makes no host calls beyond its two launches once a device has been seen.
+constexpr int kMaxDevices = 64;
+struct TrainLaunchCache {
+  bool attrs = false;
+  int splits[WG_MAX_S + 1] = {};
+};
+TrainLaunchCache g_train_cache[kMaxDevices];
+
+cudaError_t train_launch_setup(TrainLaunchCache** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  TrainLaunchCache& c = g_train_cache[dev];
+  if (!c.attrs) {
+    if ((e = cudaFuncSetAttribute(mlp_train_fb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_TOTAL)) ||
+        (e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_TOTAL)) ||
+        (e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)))
+      return e;
+    c.attrs = true;
+  }
+  *out = &c;
+  return cudaSuccess;
+}
+
+}  // namespace
 
 cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s) {
   if (L.n <= 0) return cudaSuccess;
   const int ntiles = (L.n + TILE - 1) / TILE;
-  cudaError_t e;
+  TrainLaunchCache* cache = nullptr;
+  cudaError_t e = train_launch_setup(&cache);
+  if (e) return e;
   // ---- forward and backward through the activations, a cluster per tile
   {
     FbArgs A;
@@ -843,10 +920,7 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     for (int l = 0; l < 3; ++l) A.daT[l] = L.daT[l];
     for (int l = 0; l < 2; ++l) A.hT[l] = L.hT[l];
     A.dz = L.dz;
-    A.loss_sum = L.loss_sum;
     A.tsum = L.wg_part;
-    if ((e = cudaFuncSetAttribute(mlp_train_fb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_TOTAL)))
-      return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(FB_CTAS * ntiles));
     cfg.blockDim = dim3(FB_THREADS);
@@ -867,16 +941,20 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     G.n = L.n;
     G.ld = L.ld;
     const int chunks = (L.n + WG_CHUNK - 1) / WG_CHUNK;
-    G.job[0] = WgJob{L.daT[0], L.x16T, 16, L.dW1, L.db[0]};
-    G.job[1] = WgJob{L.daT[1], L.hT[0], H, L.dW2, L.db[1]};
-    G.job[2] = WgJob{L.daT[2], L.hT[1], H, L.dW3, L.db[2]};
+    G.job[0] = WgJob{L.daT[0], L.x16T, 16, L.dW1, L.db[0], mlpp::OFF_W1, mlpp::OFF_B1};
+    G.job[1] = WgJob{L.daT[1], L.hT[0], H, L.dW2, L.db[1], mlpp::OFF_W2, mlpp::OFF_B2};
+    G.job[2] = WgJob{L.daT[2], L.hT[1], H, L.dW3, L.db[2], mlpp::OFF_W3, mlpp::OFF_B3};
+    if (L.adam) {
+      G.adam = *L.adam;
+    } else {
+      std::memset(&G.adam, 0, sizeof(G.adam));
+    }
     G.tsum = L.wg_part;
     G.tiles = ntiles;
     G.dW4 = L.dW4;
     G.db4 = L.db4;
-    if ((e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_TOTAL)))
-      return e;
-    if ((e = cudaFuncSetAttribute(mlp_tc_wgrad_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
+    G.loss = L.loss_sum;
+    G.inv_n = 1.f / (float)L.n;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = WG_TOTAL;
@@ -888,13 +966,18 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     // the most splits (up to 16) whose six clusters can all be resident
-    int S = chunks < WG_MAX_S ? chunks : WG_MAX_S;
-    for (; S > 1; S = S > 8 ? 8 : S / 2) {
-      at[0].val.clusterDim.x = (unsigned)S;
-      cfg.gridDim = dim3((unsigned)(3 * 2 * S));
-      int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, mlp_tc_wgrad_kernel, &cfg) == cudaSuccess && clusters >= 6) break;
-      (void)cudaGetLastError();
+    const int cmax = chunks < WG_MAX_S ? chunks : WG_MAX_S;
+    int S = cache->splits[cmax];
+    if (S == 0) {
+      for (S = cmax; S > 1; S = S > 8 ? 8 : S / 2) {
+        at[0].val.clusterDim.x = (unsigned)S;
+        cfg.gridDim = dim3((unsigned)(3 * 2 * S));
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, mlp_tc_wgrad_kernel, &cfg) == cudaSuccess && clusters >= 6)
+          break;
+        (void)cudaGetLastError();
+      }
+      cache->splits[cmax] = S;
     }
     G.S = S;
     G.chunks = (chunks + S - 1) / S;

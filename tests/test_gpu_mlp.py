@@ -99,6 +99,32 @@ def test_gradients_match_oracle(sc, ctx, n):
     net.close()
 
 
+# The fused training step (the weight-gradient kernel applies Adam to each
+# gradient it writes) leaves the same bits as the gradient call followed by
+# the Adam call, over two steps (bias corrections of t = 1 and 2); one full
+# batch and a ragged one.
+@pytest.mark.parametrize("n", [4096, 1000])
+def test_fused_train_step_equals_gradients_then_adam(sc, ctx, n):
+    P = random_net(5)
+    a, b = sc.Surrogate(ctx, seed=0), sc.Surrogate(ctx, seed=0)
+    for net in (a, b):
+        net.set(pack(P), P.mu, P.sigma, 0.0)
+    tg = torch.from_numpy(synth.topdown_targets(seed=13, n=n)).cuda()
+    y = torch.from_numpy((np.random.default_rng(6).uniform(size=n) < 0.5).astype(np.uint8)).cuda()
+    tp = sc.train_params(lr=1e-3)
+    for _ in range(2):
+        _, la = a.grads(tg, y)
+        a.adam_step(None, tp)  # the gradients the last call left on the device
+        lb = b.train_step(tg, y, tp)
+        assert la == lb
+    pa, pb = a.get()[0], b.get()[0]
+    assert np.array_equal(pa, pb), np.abs(pa - pb).max()
+    assert not np.array_equal(pa, pack(P))
+    assert torch.equal(a.infer(tg), b.infer(tg))  # the bf16 weight copies agree too
+    a.close()
+    b.close()
+
+
 def test_adam_step_matches_formula(sc, ctx):
     P = random_net(3)
     net = sc.Surrogate(ctx, seed=0)
