@@ -168,11 +168,11 @@ struct TrainTcLaunch {
   const float* targets;
   const uint8_t* labels;
   const int32_t* index;  // batch row -> target / label (NULL: identity)
-  int n, ld;
+  int n;
   float* logits;         // [n]
-  uint16_t* x16T;        // [16][ld]
-  uint16_t* hT[2];       // [256][ld] h1, h2
-  uint16_t* daT[3];      // [256][ld]
+  uint8_t* x16T;         // chunk-tiled (64-row chunks, canonical K-major over the rows): 16 features
+  uint8_t* hT[2];        // chunk-tiled, 256 features: h1, h2
+  uint8_t* daT[3];       // chunk-tiled, 256 features: dL/da1..3
   float* dz;             // [n]
   float* loss_sum;       // the mean BCE (written by the step)
   float* wg_part;        // mlp_train_tc_part_bytes(ld): per-tile sums of dz h3 and dz

@@ -233,9 +233,9 @@ cudaError_t mlp_infer_counted(const MlpState* S, const float* targets, const int
 // the loss word and the per-tile sums of dz h3 and dz. (SiLU'(z) stays in
 // the tensor memory of the fused forward-backward kernel.)
 struct TrainViews {
-  uint16_t* x16T;   // [KIN][Bcap]
-  uint16_t* hT[2];  // [H][Bcap] h1, h2
-  uint16_t* daT[3]; // [H][Bcap]
+  uint8_t* x16T;    // chunk-tiled [Bt / 64][16 x 64] bf16
+  uint8_t* hT[2];   // chunk-tiled [Bt / 64][256 x 64] bf16: h1, h2
+  uint8_t* daT[3];  // chunk-tiled [Bt / 64][256 x 64] bf16
   float* dz;        // [Bcap]
   float* logits;    // [Bcap]
   float* loss_sum;
@@ -244,19 +244,23 @@ struct TrainViews {
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// rows of the chunk-tiled caches: whole 128-row tiles
+static size_t tiled_rows(int Bcap) { return ((size_t)Bcap + 127) / 128 * 128; }
+
 static size_t train_bytes(int Bcap) {
-  const size_t Bp = (size_t)Bcap;
-  return align256(Bp * KIN * 2) + 2 * align256(Bp * H * 2) + 3 * align256(Bp * H * 2) +
-         2 * align256(Bp * 4) + 256 + align256(mlp_train_tc_part_bytes(Bcap));
+  const size_t Bp = (size_t)Bcap, Bt = tiled_rows(Bcap);
+  return align256(Bt * KIN * 2) + 2 * align256(Bt * H * 2) + 3 * align256(Bt * H * 2) + 2 * align256(Bp * 4) + 256 +
+         align256(mlp_train_tc_part_bytes(Bcap));
 }
 
 static TrainViews carve(MlpState* S, int Bcap) {
   char* p = static_cast<char*>(S->train_buf);
   auto take = [&](size_t bytes) { char* r = p; p += align256(bytes); return r; };
+  const size_t Bt = tiled_rows(Bcap);
   TrainViews v;
-  v.x16T = reinterpret_cast<uint16_t*>(take((size_t)Bcap * KIN * 2));
-  for (int l = 0; l < 2; ++l) v.hT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
-  for (int l = 0; l < 3; ++l) v.daT[l] = reinterpret_cast<uint16_t*>(take((size_t)Bcap * H * 2));
+  v.x16T = reinterpret_cast<uint8_t*>(take(Bt * KIN * 2));
+  for (int l = 0; l < 2; ++l) v.hT[l] = reinterpret_cast<uint8_t*>(take(Bt * H * 2));
+  for (int l = 0; l < 3; ++l) v.daT[l] = reinterpret_cast<uint8_t*>(take(Bt * H * 2));
   v.dz = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.logits = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.loss_sum = reinterpret_cast<float*>(take(256));
@@ -293,7 +297,6 @@ static cudaError_t gradients(MlpState* S, const float* targets, const uint8_t* l
   L.labels = labels;
   L.index = index;
   L.n = B;
-  L.ld = S->Bcap;
   L.logits = v.logits;
   L.x16T = v.x16T;
   for (int l = 0; l < 2; ++l) L.hT[l] = v.hT[l];

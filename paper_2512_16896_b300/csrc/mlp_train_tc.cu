@@ -70,7 +70,8 @@ constexpr int FB_HALF = FB_PART + FB_CTAS * TILE * 4;  // [128] partial logit of
 constexpr int FB_DZ = FB_HALF + TILE * 4;              // [128] bf16-rounded dz of the tile
 constexpr int FB_DZF = FB_DZ + TILE * 4;               // [128] dz of the tile
 constexpr int FB_RED = FB_DZF + TILE * 4;              // [4][64] partial sums of dW4
-constexpr int FB_BAR = FB_RED + 4 * FB_NS * 4;         // 6 mbarriers
+constexpr int FB_STG = FB_RED + 4 * FB_NS * 4;         // [2][8 KB] a block transposed for its bulk store
+constexpr int FB_BAR = FB_STG + 2 * 8192;              // 6 mbarriers
 constexpr int FB_TMEM = FB_BAR + 48;
 constexpr int FB_TOTAL = FB_TMEM + 16;
 constexpr uint32_t FB_TCOLS = 4 * FB_NS;               // TMEM: accumulator, SiLU'(z1), SiLU'(z2), SiLU'(z3)
@@ -85,12 +86,12 @@ struct FbArgs {
   const float* targets;
   const uint8_t* labels;  // [targets], through index
   const int32_t* index;   // batch row -> target / label (NULL: identity)
-  int n, ld;
+  int n;
   float inv_n;
   float* logits;          // [n]
-  uint16_t* x16T;         // [16][ld] standardised input, bf16, feature-major
-  uint16_t* hT[2];        // [256][ld] h1, h2, bf16, feature-major
-  uint16_t* daT[3];       // [256][ld] dL/da1, da2, da3, bf16, feature-major
+  uint8_t* x16T;          // chunk-tiled (see below), 16 features: the standardised input and a row of ones
+  uint8_t* hT[2];         // chunk-tiled, 256 features: h1, h2
+  uint8_t* daT[3];        // chunk-tiled, 256 features: dL/da1, da2, da3
   float* dz;              // [n] dL/dz
   float* tsum;            // [tiles][TS_LD] over each tile's rows: dW4 = sum dz h3 (256), db4 = sum dz, the BCE sum
 };
@@ -145,35 +146,53 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32]) 
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// One 64-feature block ([128][64] bf16, canonical K-major, K = 64) out
-// feature-major: dstT[f0 + k][row0 + r] (row stride ld), one 8 x 8 core
-// matrix per step (eight 16-byte shared loads, a register transpose, eight
-// 16-byte global stores). Row groups at or past `rows` are skipped (ld, a
-// multiple of 16, covers every row group below it).
-__device__ __forceinline__ void copy_out_block(const uint8_t* blk, uint16_t* dstT, int ld, int row0, int rows, int f0,
+// The weight gradients read the batch in 64-row chunks, so the caches they
+// read are kept "chunk-tiled": chunk c holds rows [64 c, 64 c + 64) of every
+// feature f in the canonical K-major layout with K = the 64 rows, at byte
+// canon_offset(f, r % 64, 64) of a F x 128-byte tile (F = 256 or 16); the
+// weight-gradient kernel stages a chunk with one bulk copy per operand.
+
+// This CTA's 64-feature block of a 128-row tile (canonical, K = features)
+// into the chunk-tiled layout: each 8 x 8 core matrix transposed in
+// registers into the staging buffer (8 KB per chunk, the CTA's features
+// contiguous there), then one bulk store per chunk. The previous bulk store
+// has read the staging buffer before it is written again.
+__device__ __forceinline__ void copy_out_tiled(const uint8_t* blk, uint8_t* stg, uint8_t* dst, int tile, int fs,
                                                int tid) {
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncthreads();
   for (int cm = tid; cm < (TILE / 8) * (FB_NS / 8); cm += FB_THREADS) {
-    const int rg = cm / (FB_NS / 8), kg = cm % (FB_NS / 8);
-    if (rg * 8 >= rows) continue;
-    const uint8_t* src = blk + rg * (FB_NS / 8) * 128 + kg * 128;  // core matrix (rg, kg): 8 rows x 16 bytes
+    const int rg = cm / (FB_NS / 8), kg = cm % (FB_NS / 8);  // rows 8 rg.., features 8 kg..
+    const uint8_t* src = blk + rg * (FB_NS / 8) * 128 + kg * 128;
     uint32_t w[8][4];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * r);
       w[r][0] = v.x; w[r][1] = v.y; w[r][2] = v.z; w[r][3] = v.w;
     }
+    uint8_t* d = stg + (rg >> 3) * 8192 + kg * 1024 + (rg & 7) * 128;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {  // columns 2p, 2p + 1 of the core matrix
+    for (int p = 0; p < 4; ++p) {  // features 2p, 2p + 1 of the core matrix, over its 8 rows
       uint32_t lo[4], hi[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {  // rows 2q, 2q + 1
         lo[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x5410);
         hi[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x7632);
       }
-      const size_t base = (size_t)(f0 + kg * 8 + 2 * p) * ld + row0 + rg * 8;
-      *reinterpret_cast<uint4*>(dstT + base) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      *reinterpret_cast<uint4*>(dstT + base + ld) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(d + (2 * p) * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(d + (2 * p + 1) * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     }
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 8192;" ::"l"(
+                       dst + (size_t)(2 * tile + h) * (H * 128) + (size_t)(fs / 8) * 1024),
+                   "r"(smem_u32(stg + h * 8192))
+                   : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   }
 }
 
@@ -216,6 +235,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   float* sdz = reinterpret_cast<float*>(smem + FB_DZ);
   float* sdzf = reinterpret_cast<float*>(smem + FB_DZF);
   float* sred = reinterpret_cast<float*>(smem + FB_RED);
+  uint8_t* stg = smem + FB_STG;
   const int tile = row0 / TILE;
   const uint32_t s0 = smem_u32(smem);
   const uint32_t bar_a = s0 + FB_BAR, bar_b = bar_a + 8, bar_m = bar_a + 16;  // weights, weights, MMAs
@@ -283,9 +303,24 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     for (int q = 0; q < 2; ++q)
       *reinterpret_cast<uint4*>(smem + FB_X + canon_offset(tid, q * 8, 16)) =
           make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
-    if (rank == 0 && row < n) {
+    if (rank == 0) {  // the tile's two chunks of X, with input slot 9 = 1 on rows < n (bias gradients)
+      uint16_t* st = reinterpret_cast<uint16_t*>(stg);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) A.x16T[(size_t)i * A.ld + row] = (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
+      for (int i = 0; i < 16; ++i) {
+        const uint16_t v = i == 9 ? (row < n ? (uint16_t)0x3F80u : (uint16_t)0) : (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
+        st[((tid >> 6) * 2048 + canon_offset(i, tid & 63, 64)) / 2] = v;
+      }
+    }
+  }
+  if (rank == 0) {
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 4096;" ::"l"(
+                       A.x16T + (size_t)tile * 4096),
+                   "r"(smem_u32(stg))
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
   fence_proxy_async();
@@ -373,7 +408,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   cluster_wait();  // every CTA's mbarriers are ready
   if (ok) publish(own0, FB_BLK, bar_x0);
   // z2 = h1 W2^T once every block of h1 is here; this CTA's h1 out meanwhile
-  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.hT[0], A.ld, row0, n - row0, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, stg, A.hT[0], tile, fs, tid);
   if (ok) wait_bar(bar_x0, got_x0);
   if (ok && tid == 0) mbar_expect(bar_x0, FB_RECV);  // dA2 arrives in A0
   if (ok) ++iss_x0;
@@ -384,7 +419,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   if (ok) fwd_epilogue(1, own1);
   if (ok) publish(own1, FB_BLK, bar_x1);
   // z3 = h2 W3^T
-  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.hT[1], A.ld, row0, n - row0, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.hT[1], tile, fs, tid);
   if (ok) wait_bar(bar_x1, got_x1);
   if (ok && tid == 0) mbar_expect(bar_x1, FB_RECV);  // dA3 arrives in A1
   if (ok) ++iss_x1;
@@ -439,7 +474,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     fb_put_row(own1, trow, cb, hw);
     publish(own1, FB_BLK, bar_x1);
   }
-  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.daT[2], A.ld, row0, n - row0, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.daT[2], tile, fs, tid);
   // dW4 = sum dz h3 and db4 = sum dz over the tile's rows, this CTA's
   // features of h3 (its block of A0): thread (row group set, 8 features,
   // row in group) with 16-byte loads, the 8 rows of a group added across
@@ -488,14 +523,15 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     publish(own0, FB_BLK, bar_x0);
   }
   // dH1 = dA2 W2 -> dA1 into this CTA's block of A1 (dA3 there is read)
-  if (ok) copy_out_block(smem + FB_A0 + rank * FB_BLK, A.daT[1], A.ld, row0, n - row0, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, stg, A.daT[1], tile, fs, tid);
   if (ok) wait_bar(bar_x0, got_x0);
   if (ok) wait_bar(bar_b, got_b);
   if (ok) issue(FB_A0, FB_WB);
   if (ok) wait_bar(bar_m, got_m);
   if (ok) bwd_epilogue(tg1, own1);
   __syncthreads();
-  if (ok) copy_out_block(smem + FB_A1 + rank * FB_BLK, A.daT[0], A.ld, row0, n - row0, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.daT[0], tile, fs, tid);
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the bulk stores are done
 
   if (!ok) {
     if (tid == 0) latch_error(status, kDevTimeout);
@@ -536,9 +572,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
 // then needs no separate update launch).
 
 struct WgJob {
-  const uint16_t* A;  // dL/da feature-major [256][ld]: A operand rows = output features
-  const uint16_t* B;  // activations feature-major [N][ld]: B operand rows = input features
-  int N;              // 256, or 16 for the first layer (9 inputs padded to 16)
+  const uint8_t* A;   // dL/da, chunk-tiled (256 features): A operand rows = output features
+  const uint8_t* B;   // activations, chunk-tiled (N features): B operand rows = input features
+  int N;              // 256, or 16 for the first layer (9 inputs, the ones in slot 9, zeros)
   float* dW;          // [256][256], or [256][9]
   float* db;          // [256]
   int off_w, off_b;   // offsets of dW and db in the packed parameters
@@ -547,7 +583,6 @@ struct WgJob {
 struct WgArgs {
   WgJob job[3];
   int n;         // batch rows
-  int ld;
   int S;         // K splits = CTAs per cluster
   int chunks;    // 64-row chunks per split
   const float* tsum;  // [tiles][TS_LD] per-tile sums of dz h3 | dz | BCE
@@ -566,8 +601,8 @@ constexpr int WG_STAGE = WG_STAGE_A + WG_NB * WG_CHUNK * 2;  // + 34 KB
 constexpr int WG_NST = 4;                               // chunk stages in flight
 constexpr int WG_LD = WG_NB + 4;                        // floats per row of a CTA's partial (padded)
 constexpr int WG_RED = TILE * WG_LD * 4;                // the partial, over the stages once they are read
-constexpr int WG_BAR = (WG_NST * WG_STAGE > WG_RED ? WG_NST * WG_STAGE : WG_RED);  // WG_NST mbarriers
-constexpr int WG_TMEM = WG_BAR + 8 * WG_NST;
+constexpr int WG_BAR = (WG_NST * WG_STAGE > WG_RED ? WG_NST * WG_STAGE : WG_RED);  // 2 x WG_NST mbarriers
+constexpr int WG_TMEM = WG_BAR + 16 * WG_NST;
 constexpr int WG_TOTAL = WG_TMEM + 16;
 constexpr int WG_MAX_S = 16;
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory of one CTA");
@@ -591,33 +626,13 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
   return v;
 }
 
-// Rows [row0, row0 + rows) x batch columns [k0, k0 + 64) of a feature-major
-// bf16 matrix into the canonical K-major layout (K = 64) by asynchronous
-// 16-byte copies (cp.async; whole vectors past n are zero-filled by the copy,
-// a vector that straddles n is assembled by the thread); batch columns at or
-// past n read as zero. Row `skip` (if in range) is left to the caller; the
-// caller commits the copies as a group.
-__device__ __forceinline__ void stage_chunk_async(uint8_t* dst, const uint16_t* src, int row0, int rows, int k0,
-                                                  int n, int ld, int tid, int skip) {
-  for (int v = tid; v < rows * (WG_CHUNK / 8); v += THREADS) {
-    const int r = v >> 3, kv = (v & 7) * 8;
-    if (r == skip) continue;
-    const int k = k0 + kv;
-    const uint16_t* p = src + (size_t)(row0 + r) * ld + k;
-    uint8_t* d = dst + canon_offset(r, kv, WG_CHUNK);
-    if (k + 8 <= n || k >= n) {
-      const uint32_t bytes = k < n ? 16u : 0u;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(d)), "l"(k < n ? p : src),
-                   "r"(bytes)
-                   : "memory");
-    } else {
-      uint16_t e[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = k + j < n ? p[j] : (uint16_t)0;
-      *reinterpret_cast<uint4*>(d) = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
-                                                e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
-    }
-  }
+// Global -> shared bulk copy of `bytes` (a multiple of 16, at most 32 KB;
+// 16-byte aligned ends) completing on `bar`, whose expected byte count the
+// caller has already raised.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 // Rows [r0, r0 + rows) of a staged B chunk: row `ones` holds bf16 1.0 for
@@ -649,11 +664,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   const uint32_t ncols = wide ? 512u : 32u;        // TMEM columns (a power of two >= NB)
   const int LDr = NB + 4;                          // row stride of the partial in shared memory
   const uint32_t s0 = smem_u32(smem);
-  const uint32_t bar0 = s0 + WG_BAR;
+  const uint32_t bar0 = s0 + WG_BAR;               // MMAs done with stage s: bar0 + 8 s
+  const uint32_t barf = bar0 + 8 * WG_NST;          // stage s landed: barf + 8 s
   float* red = reinterpret_cast<float*>(smem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + WG_TMEM);
   if (tid == 0)
-    for (int i = 0; i < WG_NST; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < 2 * WG_NST; ++i) mbar_init(bar0 + 8 * i, 1);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(ncols)
@@ -670,23 +686,28 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   const int c_end = min(c_first + G.chunks, (G.n + WG_CHUNK - 1) / WG_CHUNK);
   uint32_t commits[WG_NST] = {};  // MMA commits issued to each stage's barrier
   uint32_t waited[WG_NST] = {};   // phases of each barrier already waited for
+  uint32_t fills[WG_NST] = {};    // copies issued into each stage
+  uint32_t landed[WG_NST] = {};   // ... and waited for
   bool ok = true;
   int issued = 0;
-  // chunk c is staged in buffer (c - c_first) % WG_NST, up to WG_NST chunks
-  // in flight; a buffer is restaged once the MMAs that read it are done
+  const uint32_t bytes_b = (uint32_t)J.N * WG_CHUNK * 2;
+  // chunk c is staged in buffer (c - c_first) % WG_NST by two bulk copies
+  // (its 128 features of dA, the N input features) and, for N = 256, the
+  // block of ones written by the threads; up to WG_NST chunks in flight, a
+  // buffer restaged once the MMAs that read it are done
   auto stage = [&](int cix) {
-    uint8_t* sa = smem + ((cix - c_first) % WG_NST) * WG_STAGE;
-    uint8_t* sb = sa + WG_STAGE_A;
-    const int k0 = cix * WG_CHUNK;
-    stage_chunk_async(sa, J.A, mt * TILE, TILE, k0, G.n, G.ld, tid, -1);
-    if (wide) {
-      stage_chunk_async(sb, J.B, 0, H, k0, G.n, G.ld, tid, -1);
-      stage_ones(sb, H, 16, ones, k0, G.n, tid);
-    } else {
-      stage_chunk_async(sb, J.B, 0, 16, k0, G.n, G.ld, tid, ones);
-      stage_ones(sb, ones, 1, ones, k0, G.n, tid);
+    const int s = (cix - c_first) % WG_NST;
+    const uint32_t sa = s0 + s * WG_STAGE, sb = sa + WG_STAGE_A;
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(barf + 8 * s),
+                   "r"((uint32_t)WG_STAGE_A + bytes_b)
+                   : "memory");
+      bulk_copy(sa, J.A + (size_t)cix * (H * 128) + (size_t)mt * WG_STAGE_A, WG_STAGE_A, barf + 8 * s);
+      bulk_copy(sb, J.B + (size_t)cix * bytes_b, bytes_b, barf + 8 * s);
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    ++fills[s];
+    if (wide) stage_ones(smem + s * WG_STAGE + WG_STAGE_A, H, 16, ones, cix * WG_CHUNK, G.n, tid);
+    fence_proxy_async();
   };
   const int nc = c_end > c_first ? c_end - c_first : 0;
   for (int i = 0; i < nc && i < WG_NST; ++i) stage(c_first + i);
@@ -710,15 +731,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   }
   for (int i = 0; i < nc && ok; ++i) {
     const int s = i % WG_NST;
-    // chunk i landed (this thread's copies; later chunks may stay in flight)
-    const int later = min(nc - 1 - i, WG_NST - 1);
-    if (later >= 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
-    else if (later == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-    else if (later == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    {  // chunk i landed
+      const bool w = mbar_wait(barf + 8 * s, landed[s] & 1);
+      if (w) ++landed[s];
+      tc_fence_before();
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+    }
     const uint32_t sa = s0 + s * WG_STAGE, sb = sa + WG_STAGE_A;
     if (tid == 0) {
       tc_fence_after();
@@ -748,8 +769,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
       stage(c_first + i + WG_NST);
     }
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing of this thread's left in flight
-  // every commit made must be waited for before TMEM is read or freed
+  // every copy and every commit made must be waited for before the shared
+  // memory is reused or TMEM is read or freed
+  for (int s = 0; s < WG_NST; ++s)
+    while (fills[s] > landed[s]) {
+      if (!mbar_wait(barf + 8 * s, landed[s] & 1)) ok = false;
+      ++landed[s];
+    }
   for (int s = 0; s < WG_NST; ++s)
     while (commits[s] > waited[s]) {
       if (!mbar_wait(bar0 + 8 * s, waited[s] & 1)) ok = false;
@@ -913,7 +939,6 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     A.labels = L.labels;
     A.index = L.index;
     A.n = L.n;
-    A.ld = L.ld;
     A.inv_n = 1.f / (float)L.n;
     A.logits = L.logits;
     A.x16T = L.x16T;
@@ -939,7 +964,6 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
   {
     WgArgs G;
     G.n = L.n;
-    G.ld = L.ld;
     const int chunks = (L.n + WG_CHUNK - 1) / WG_CHUNK;
     G.job[0] = WgJob{L.daT[0], L.x16T, 16, L.dW1, L.db[0], mlpp::OFF_W1, mlpp::OFF_B1};
     G.job[1] = WgJob{L.daT[1], L.hT[0], H, L.dW2, L.db[1], mlpp::OFF_W2, mlpp::OFF_B2};
