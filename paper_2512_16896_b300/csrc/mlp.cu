@@ -329,8 +329,8 @@ static mlpp::AdamArgs next_adam(MlpState* S, float lr, float b1, float b2, float
   a.b1 = b1;
   a.b2 = b2;
   a.eps = eps;
-  a.bc1 = (float)(1.0 - pow((double)b1, t));
-  a.bc2 = (float)(1.0 - pow((double)b2, t));
+  a.ibc1 = (float)(1.0 / (1.0 - pow((double)b1, t)));
+  a.ibc2 = (float)(1.0 / (1.0 - pow((double)b2, t)));
   a.W4 = S->W4;
   a.W1c = S->W1c;
   a.W2c = S->W2c;

@@ -25,7 +25,7 @@ struct AdamArgs {
   float* m;
   float* v;
   float lr, b1, b2, eps;
-  float bc1, bc2;  // 1 - b1^t, 1 - b2^t of this step
+  float ibc1, ibc2;  // 1 / (1 - b1^t), 1 / (1 - b2^t) of this step
   __nv_bfloat16* W4;
   __nv_bfloat16* W1c;
   __nv_bfloat16* W2c;
@@ -34,21 +34,20 @@ struct AdamArgs {
   __nv_bfloat16* W3tc;
 };
 
-// Adam on parameter i with gradient gi, given its current moments and value
-// (loaded by the caller, so that several updates can have their loads in
-// flight together); stores them and the updated weight's bf16 copies. Every
-// operation is an explicitly rounded intrinsic (no contraction left to the
-// compiler), so the update has the same bits in every kernel it is inlined
-// into.
-__device__ __forceinline__ void adam_apply(const AdamArgs& a, int i, float gi, float m0, float v0, float p0) {
-  const float mi = __fmaf_rn(a.b1, m0, __fmul_rn(__fsub_rn(1.f, a.b1), gi));
-  const float vi = __fmaf_rn(a.b2, v0, __fmul_rn(__fmul_rn(__fsub_rn(1.f, a.b2), gi), gi));
-  a.m[i] = mi;
-  a.v[i] = vi;
-  const float step =
-      __fdiv_rn(__fmul_rn(a.lr, __fdiv_rn(mi, a.bc1)), __fadd_rn(__fsqrt_rn(__fdiv_rn(vi, a.bc2)), a.eps));
-  const float p = __fsub_rn(p0, step);
-  a.params[i] = p;
+// The Adam arithmetic of one parameter: new moments and value from the
+// gradient and the current ones. Every operation is an explicitly rounded
+// intrinsic (no contraction left to the compiler), so the update has the
+// same bits in every kernel it is inlined into.
+__device__ __forceinline__ void adam_core(const AdamArgs& a, float gi, float m0, float v0, float p0, float& mi,
+                                          float& vi, float& p) {
+  mi = __fmaf_rn(a.b1, m0, __fmul_rn(__fsub_rn(1.f, a.b1), gi));
+  vi = __fmaf_rn(a.b2, v0, __fmul_rn(__fmul_rn(__fsub_rn(1.f, a.b2), gi), gi));
+  const float mhat = __fmul_rn(mi, a.ibc1), vhat = __fmul_rn(vi, a.ibc2);
+  p = __fsub_rn(p0, __fdiv_rn(__fmul_rn(a.lr, mhat), __fadd_rn(__fsqrt_rn(vhat), a.eps)));
+}
+
+// The bf16 copies of updated parameter i with value p.
+__device__ __forceinline__ void adam_copies(const AdamArgs& a, int i, float p) {
   const __nv_bfloat16 h = __float2bfloat16_rn(p);
   if (i < OFF_B1) {  // W1 [256][9] -> canonical [256][16] (columns 9..15 stay zero)
     a.W1c[canon_offset(i / 9, i % 9, KIN) / 2] = h;
@@ -63,6 +62,18 @@ __device__ __forceinline__ void adam_apply(const AdamArgs& a, int i, float gi, f
   } else if (i >= OFF_W4 && i < OFF_B4) {
     a.W4[i - OFF_W4] = h;
   }
+}
+
+// Adam on parameter i with gradient gi, given its current moments and value
+// (loaded by the caller, so that several updates can have their loads in
+// flight together); stores them and the updated weight's bf16 copies.
+__device__ __forceinline__ void adam_apply(const AdamArgs& a, int i, float gi, float m0, float v0, float p0) {
+  float mi, vi, p;
+  adam_core(a, gi, m0, v0, p0, mi, vi, p);
+  a.m[i] = mi;
+  a.v[i] = vi;
+  a.params[i] = p;
+  adam_copies(a, i, p);
 }
 
 // Adam on parameter i with gradient gi.

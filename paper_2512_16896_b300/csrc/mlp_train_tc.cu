@@ -605,7 +605,9 @@ constexpr int WG_BAR = (WG_NST * WG_STAGE > WG_RED ? WG_NST * WG_STAGE : WG_RED)
 constexpr int WG_TMEM = WG_BAR + 16 * WG_NST;
 constexpr int WG_TOTAL = WG_TMEM + 16;
 constexpr int WG_MAX_S = 16;
+constexpr int WG_RB = 32;  // reduced rows held at a time, past the partial
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory of one CTA");
+static_assert(WG_RED + WG_RB * WG_LD * 4 <= WG_BAR, "reduced rows fit past the partial");
 
 // 16 consecutive f32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
@@ -818,63 +820,115 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
   tc_fence_before();
   cluster_arrive();
   cluster_wait();
-  // rows [split R, split R + R) of the tile: the S partials added in split
-  // order; the gradients written, then (with Adam arguments) the updates of
-  // up to 12 parameters at a time with their loads in flight together
-  if (ok) {
-    const int R = (TILE + S - 1) / S;
-    const int q4 = NB / 4;
-    const int nw = wide ? H : 9;  // weights per output feature
-    for (int e0 = tid; e0 < R * q4; e0 += 3 * THREADS) {
-      float val[12];
-      int pidx[12];
+  // rows [split R, split R + R) of the tile (R = 128 / S rounded up), up to
+  // WG_RB at a time: the S partials added in split order into shared memory
+  // past the partial, every thread with the loads of two float4 groups in
+  // flight together
+  float* rs = reinterpret_cast<float*>(smem + WG_RED);  // [WG_RB][LDr] reduced rows
+  const int R = (TILE + S - 1) / S;
+  const int rall = min(TILE, split * R + R) - split * R;  // this CTA's rows (none for a trailing split)
+  for (int rb = 0; rb < rall; rb += WG_RB) {
+    const int r1 = min(WG_RB, rall - rb);
+    const int row0 = split * R + rb;
+    if (ok) {
+      const int q4 = NB / 4;
+      const int ng = r1 * q4;
+      for (int g0 = tid; g0 < ng; g0 += 2 * THREADS) {
+        float4 v[2][WG_MAX_S];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+        for (int u = 0; u < 2; ++u) {
+          const int g = g0 + u * THREADS;
+          if (g >= ng) continue;
+          const uint32_t a = s0 + (uint32_t)((row0 + g / q4) * LDr + (g % q4) * 4) * 4u;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) pidx[4 * k + j] = -1;
-        const int e = e0 + k * THREADS;
-        const int row = split * R + e / q4, c = (e % q4) * 4;
-        if (e >= R * q4 || row >= TILE) continue;
-        const uint32_t a = s0 + (uint32_t)(row * LDr + c) * 4u;
-        float4 v[WG_MAX_S];
+          for (int q = 0; q < WG_MAX_S; ++q)
+            if (q < S) v[u][q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
+        }
 #pragma unroll
-        for (int q = 0; q < WG_MAX_S; ++q)
-          if (q < S) v[q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
-        float4 t = v[0];
+        for (int u = 0; u < 2; ++u) {
+          const int g = g0 + u * THREADS;
+          if (g >= ng) continue;
+          float4 t = v[u][0];
 #pragma unroll
-        for (int q = 1; q < WG_MAX_S; ++q)
-          if (q < S) {
-            t.x += v[q].x; t.y += v[q].y; t.z += v[q].z; t.w += v[q].w;
-          }
-        const int o = mt * TILE + row;
-        const float tv[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cj = c + j;
-          val[4 * k + j] = tv[j];
-          if (cj < nw) {
-            J.dW[o * nw + cj] = tv[j];
-            pidx[4 * k + j] = J.off_w + o * nw + cj;
-          } else if (cj == nw) {
-            J.db[o] = tv[j];
-            pidx[4 * k + j] = J.off_b + o;
-          }
+          for (int q = 1; q < WG_MAX_S; ++q)
+            if (q < S) {
+              t.x += v[u][q].x; t.y += v[u][q].y; t.z += v[u][q].z; t.w += v[u][q].w;
+            }
+          *reinterpret_cast<float4*>(rs + (g / q4) * LDr + (g % q4) * 4) = t;
         }
       }
-      if (G.adam.params) {
-        float m0[12], v0[12], p0[12];
+    }
+    __syncthreads();
+    // the gradients out and, with Adam arguments, their parameters updated
+    if (ok) {
+      const int o0 = mt * TILE + row0;  // first output feature of this block
+      if (wide) {
+        __nv_bfloat16* Wc = jb == 1 ? G.adam.W2c : G.adam.W3c;
+        __nv_bfloat16* Wtc = jb == 1 ? G.adam.W2tc : G.adam.W3tc;
+        const int ng = r1 * (H / 4);
+        for (int g0 = tid; g0 < ng; g0 += 2 * THREADS) {
+          float4 t[2], m0[2], v0[2], p0[2];
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-          if (pidx[k] >= 0) {
-            m0[k] = G.adam.m[pidx[k]];
-            v0[k] = G.adam.v[pidx[k]];
-            p0[k] = G.adam.params[pidx[k]];
+          for (int u = 0; u < 2; ++u) {
+            const int g = g0 + u * THREADS;
+            if (g >= ng) continue;
+            const int rl = g / (H / 4), c = (g % (H / 4)) * 4, o = o0 + rl;
+            t[u] = *reinterpret_cast<const float4*>(rs + rl * LDr + c);
+            *reinterpret_cast<float4*>(J.dW + (size_t)o * H + c) = t[u];
+            if (G.adam.params) {
+              const size_t i = (size_t)J.off_w + (size_t)o * H + c;
+              m0[u] = *reinterpret_cast<const float4*>(G.adam.m + i);
+              v0[u] = *reinterpret_cast<const float4*>(G.adam.v + i);
+              p0[u] = *reinterpret_cast<const float4*>(G.adam.params + i);
+            }
           }
+          if (!G.adam.params) continue;
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-          if (pidx[k] >= 0) mlpp::adam_apply(G.adam, pidx[k], val[k], m0[k], v0[k], p0[k]);
+          for (int u = 0; u < 2; ++u) {
+            const int g = g0 + u * THREADS;
+            if (g >= ng) continue;
+            const int rl = g / (H / 4), c = (g % (H / 4)) * 4, o = o0 + rl;
+            const size_t i = (size_t)J.off_w + (size_t)o * H + c;
+            const float gs[4] = {t[u].x, t[u].y, t[u].z, t[u].w}, ms[4] = {m0[u].x, m0[u].y, m0[u].z, m0[u].w},
+                        vs[4] = {v0[u].x, v0[u].y, v0[u].z, v0[u].w}, ps[4] = {p0[u].x, p0[u].y, p0[u].z, p0[u].w};
+            float mn[4], vn[4], pn[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mlpp::adam_core(G.adam, gs[j], ms[j], vs[j], ps[j], mn[j], vn[j], pn[j]);
+            *reinterpret_cast<float4*>(G.adam.m + i) = make_float4(mn[0], mn[1], mn[2], mn[3]);
+            *reinterpret_cast<float4*>(G.adam.v + i) = make_float4(vn[0], vn[1], vn[2], vn[3]);
+            *reinterpret_cast<float4*>(G.adam.params + i) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            // bf16 copies: 4 consecutive inputs of output o ([out][in], 8 bytes) and
+            // the transposed copy's 4 rows
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(pn[0], pn[1]), h23 = __floats2bfloat162_rn(pn[2], pn[3]);
+            *reinterpret_cast<uint2*>(Wc + canon_offset(o, c, H) / 2) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Wtc[canon_offset(c + j, o, H) / 2] = __float2bfloat16_rn(pn[j]);
+          }
+        }
+        for (int rl = tid; rl < r1; rl += THREADS) {  // the bias gradients
+          const int o = o0 + rl;
+          const float t = rs[rl * LDr + H];
+          J.db[o] = t;
+          if (G.adam.params) mlpp::adam_update(G.adam, J.off_b + o, t);
+        }
+      } else {  // the first layer: 9 weights and the bias per output
+        for (int e = tid; e < r1 * 10; e += THREADS) {
+          const int rl = e / 10, c = e % 10, o = o0 + rl;
+          const float t = rs[rl * LDr + c];
+          int pi;
+          if (c < 9) {
+            J.dW[o * 9 + c] = t;
+            pi = J.off_w + o * 9 + c;
+          } else {
+            J.db[o] = t;
+            pi = J.off_b + o;
+          }
+          if (G.adam.params) mlpp::adam_update(G.adam, pi, t);
+        }
       }
     }
+    __syncthreads();  // the reduced rows are read before the next block replaces them
   }
   // no CTA leaves while another may still read its shared memory
   cluster_arrive();
