@@ -109,6 +109,13 @@ __device__ __forceinline__ uint32_t map_shared_rank(uint32_t addr, uint32_t rank
   return r;
 }
 
+// Programmatic dependent launch: the next kernel of the stream may be
+// scheduled once every CTA of this one has signalled; griddep_wait blocks
+// until the previous kernel has completed and its memory is visible (every
+// global read or write of the training kernels comes after it).
+__device__ __forceinline__ void griddep_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void cluster_arrive() {
   asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
@@ -251,6 +258,8 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     for (int i = 0; i < 6; ++i) mbar_init(bar_a + 8 * i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  griddep_signal();
+  griddep_wait();  // the previous step's weight update and its reads of the caches are done
   __syncthreads();
   // phases issued and completed on each mbarrier (the same in every thread)
   int iss_a = 1, iss_b = 1, iss_m = 0, iss_x0 = 1, iss_x1 = 1, iss_p = 1;
@@ -679,6 +688,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  griddep_signal();
+  griddep_wait();  // the fused kernel's caches and sums are written; its reads of the weights are done
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1005,13 +1016,15 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     cfg.blockDim = dim3(FB_THREADS);
     cfg.dynamicSmemBytes = FB_TOTAL;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = FB_CTAS;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if ((e = cudaLaunchKernelEx(&cfg, mlp_train_fb_kernel, A, L.status))) return e;
   }
   // ---- weight and bias gradients, split-K over the CTAs of a cluster
@@ -1037,12 +1050,14 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = WG_TOTAL;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     // the most splits (up to 16) whose six clusters can all be resident
     const int cmax = chunks < WG_MAX_S ? chunks : WG_MAX_S;
     int S = cache->splits[cmax];
