@@ -898,7 +898,6 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
 // round), and each logit is decided at once (logit >= tau).
 struct GateIO {
   static constexpr int kColGroups = 2;  // 8 warps: leaves room on the SM for the IK blocks of the other side stream
-  static constexpr bool kStores = false;
   ReachArgs A;
   __device__ int rows() const { return *(volatile const int*)A.n_reach; }
   __device__ void features(int row, float f[9]) const {
@@ -908,10 +907,6 @@ struct GateIO {
     f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
   }
   __device__ void emit(int row, bool valid, float logit) const { gate_route(A, row, valid, logit >= A.tau); }
-  __device__ void store_input(int, const uint32_t*) const {}
-  __device__ void store_grad(int, int, int, const float*) const {}
-  __device__ uint16_t* act_out(int) const { return nullptr; }
-  __device__ int act_ld() const { return 0; }
 };
 
 // The 4D reachability map's decision on the round's reach queue (the grasp

@@ -6,10 +6,11 @@
 //
 // This file keeps the network's state (FP32 masters, Adam moments, the bf16
 // weight copies in the tensor cores' canonical layout, the input
-// standardisation) and the small kernels around a training step: bias and
-// last-layer gradients, Adam, the weight copies, initialisation, the epoch
-// shuffle. The contractions of inference and training run on tcgen05
-// (mlp_tc_core.cuh, mlp_tc.cu, mlp_train_tc.cu).
+// standardisation, the training buffers) and the small kernels around
+// training: the standalone Adam step, the weight copies, initialisation,
+// the epoch shuffle. The contractions of inference and training run on
+// tcgen05 (mlp_tc_core.cuh, mlp_tc.cu, mlp_train_tc.cu); a training step
+// applies Adam inside its weight-gradient kernel (mlp_adam.cuh).
 // Rounding points (matching the FP64 reference): standardised input, every
 // SiLU output, W copies, and every dL/da are rounded to bf16; biases,
 // pre-activations, accumulations, gradients and Adam state are FP32.

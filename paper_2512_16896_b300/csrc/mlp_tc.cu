@@ -9,7 +9,6 @@ namespace {
 // Rows from a target array [n][12] (R row-major, p), logits to an array.
 struct PlainIO {
   static constexpr int kColGroups = 4;
-  static constexpr bool kStores = false;
   const float* targets;
   int n;
   const int* n_dev;  // optional device row count (n is then its cap)
@@ -24,10 +23,6 @@ struct PlainIO {
   __device__ void emit(int row, bool valid, float logit) const {
     if (valid) logits[row] = logit;
   }
-  __device__ void store_input(int, const uint32_t*) const {}
-  __device__ void store_grad(int, int, int, const float*) const {}
-  __device__ uint16_t* act_out(int) const { return nullptr; }
-  __device__ int act_ld() const { return 0; }
 };
 
 }  // namespace

@@ -154,41 +154,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
 // and a few FMA-pipe operations per activation. For a < -87 the denominator
 // overflows and the result is -0 (the exact value is below 1e-36 in magnitude).
 __device__ __forceinline__ float silu_f(float a) { return __fdividef(a, 1.f + __expf(-a)); }
-// The same logistic (for training, which also keeps SiLU'(a) = s (1 + a (1 - s))).
+// The same logistic, for training, which also keeps SiLU'(a) = s (1 + a (1 - s)).
 __device__ __forceinline__ float sigmoid_f(float a) { return __fdividef(1.f, 1.f + __expf(-a)); }
 __device__ __forceinline__ float silu_grad_from(float a, float s) { return s * fmaf(a, 1.f - s, 1.f); }
-
-// Copies a 128 x 256 bf16 operand in the canonical K-major layout (K = 256)
-// out feature-major: dstT[k][row0 + r] (row stride ld), one 8 x 8 core matrix
-// per step: eight 16-byte shared loads, a register transpose, eight 16-byte
-// global stores. Row groups at or past `rows` are skipped (ld, a multiple of
-// 16, covers every row group below it).
-__device__ __forceinline__ void copy_out_transposed(const uint8_t* sa, uint16_t* dstT, int ld, int row0, int rows,
-                                                    int tid, int nthreads) {
-  for (int cm = tid; cm < (TILE / 8) * (H / 8); cm += nthreads) {
-    const int rg = cm / (H / 8), kg = cm % (H / 8);
-    if (rg * 8 >= rows) continue;
-    const uint8_t* src = sa + rg * (H / 8) * 128 + kg * 128;  // core matrix (rg, kg): 8 rows x 16 bytes
-    uint32_t w[8][4];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * r);
-      w[r][0] = v.x; w[r][1] = v.y; w[r][2] = v.z; w[r][3] = v.w;
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {  // columns 2p, 2p + 1 of the core matrix
-      uint32_t lo[4], hi[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {  // rows 2q, 2q + 1
-        lo[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x5410);
-        hi[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x7632);
-      }
-      const size_t base = (size_t)(kg * 8 + 2 * p) * ld + row0 + rg * 8;
-      *reinterpret_cast<uint4*>(dstT + base) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      *reinterpret_cast<uint4*>(dstT + base + ld) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    }
-  }
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -199,11 +167,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // Epilogue of layers 1 and 2 for one thread's row and its CW columns:
 // TMEM -> + bias -> SiLU -> bf16 -> next A operand (canonical, K = 256); the
 // next 32 columns are loaded from TMEM while the current ones are computed.
-// A training IO (IO::kStores) also keeps every pre-activation and bf16
-// activation of batch row `grow` (io.store, only when `valid`).
-template <class IO, int CW>
-__device__ __forceinline__ void epilogue_to_a(const IO& io, int layer, uint32_t taddr, const float* bias, uint8_t* sa,
-                                              int row, int col0, int grow, bool valid) {
+template <int CW>
+__device__ __forceinline__ void epilogue_to_a(uint32_t taddr, const float* bias, uint8_t* sa, int row, int col0) {
   uint32_t r[2][32];
   tmem_ld32_async(taddr, r[0]);
   tmem_wait_ld();
@@ -214,23 +179,12 @@ __device__ __forceinline__ void epilogue_to_a(const IO& io, int layer, uint32_t 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t w[4];
-      float g[8];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = col0 + c0 + q * 8 + 2 * j;
         const float p0 = __uint_as_float(r[cur][q * 8 + 2 * j]) + bias[c];
         const float p1 = __uint_as_float(r[cur][q * 8 + 2 * j + 1]) + bias[c + 1];
-        if constexpr (IO::kStores) {
-          const float s0 = sigmoid_f(p0), s1 = sigmoid_f(p1);
-          w[j] = pack_bf16(p0 * s0, p1 * s1);
-          g[2 * j] = silu_grad_from(p0, s0);
-          g[2 * j + 1] = silu_grad_from(p1, s1);
-        } else {
-          w[j] = pack_bf16(silu_f(p0), silu_f(p1));
-        }
-      }
-      if constexpr (IO::kStores) {
-        if (valid) io.store_grad(layer, grow, col0 + c0 + q * 8, g);
+        w[j] = pack_bf16(silu_f(p0), silu_f(p1));
       }
       *reinterpret_cast<uint4*>(sa + canon_offset(row, col0 + c0 + q * 8, H)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -244,13 +198,8 @@ __device__ __forceinline__ void epilogue_to_a(const IO& io, int layer, uint32_t 
 // each, valid = row < rows(), so warp collectives may be used), and
 // IO::kColGroups (2 or 4): the CTA has 4 x kColGroups warps, warp w handling
 // TMEM lanes 32 (w % 4) .. + 31 and columns (w / 4) H / kColGroups .. (more
-// warps hide more of the epilogue's latency; the training IO keeps 2 for its
-// register budget). With
-// IO::kStores it also receives store_input(row, x16 as 8 packed bf16 pairs),
-// store_grad(layer, row, col8, SiLU'(z) of 8 columns) for layers 0..2 and
-// act_out(layer), the feature-major destination ([256][act_ld]) each
-// layer's bf16 activations are copied to from the shared operand while the
-// next contraction runs (training keeps them for the backward pass).
+// warps hide more of the epilogue's latency; fewer leave room on the SM for
+// other kernels).
 template <class IO>
 __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -323,9 +272,6 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
       for (int q = 0; q < 2; ++q)
         *reinterpret_cast<uint4*>(sa + canon_offset(tid, q * 8, 16)) =
             make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
-      if constexpr (IO::kStores) {
-        if (row < n) io.store_input(row, xb);
-      }
     }
     fence_proxy_async();
     tc_fence_before();
@@ -346,8 +292,7 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
       ok = false;
       break;
     }
-    const int grow = tile * TILE + trow;
-    epilogue_to_a<IO, CW>(io, 0, taddr, sbias, sa, trow, col0, grow, grow < n);
+    epilogue_to_a<CW>(taddr, sbias, sa, trow, col0);
 
     // ---- layers 2 and 3
     for (int layer = 0; layer < 2; ++layer) {
@@ -370,8 +315,6 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
                  idesc, s > 0);
         tc_commit(bar_m);
       }
-      if constexpr (IO::kStores)  // h1 / h2 out while the tensor cores read the same operand
-        copy_out_transposed(sa, io.act_out(layer), io.act_ld(), tile * TILE, n - tile * TILE, tid, NT);
       m_pending = true;
       ok = mbar_wait(bar_m, ph_m);
       if (ok) {
@@ -390,7 +333,7 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
         w_pending = true;
       }
       if (layer == 0) {
-        epilogue_to_a<IO, CW>(io, 1, taddr, sbias + H, sa, trow, col0, grow, grow < n);
+        epilogue_to_a<CW>(taddr, sbias + H, sa, trow, col0);
       } else {
         // h3 = bf16(SiLU(acc + b3)); logit = W4 . h3 + b4
         const float* b3 = sbias + 2 * H + col0;
@@ -404,41 +347,18 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
           const int cur = (c0 / 32) & 1;
           if (c0 + 32 < CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
 #pragma unroll
-          for (int j8 = 0; j8 < 32; j8 += 8) {
-            uint32_t hw[4];
-            float g[8];
-#pragma unroll
-            for (int j = j8; j < j8 + 8; j += 2) {
-              const float p0 = __uint_as_float(r[cur][j]) + b3[c0 + j];
-              const float p1 = __uint_as_float(r[cur][j + 1]) + b3[c0 + j + 1];
-              uint32_t hb;
-              if constexpr (IO::kStores) {
-                const float s0 = sigmoid_f(p0), s1 = sigmoid_f(p1);
-                hb = pack_bf16(p0 * s0, p1 * s1);
-                g[j - j8] = silu_grad_from(p0, s0);
-                g[j - j8 + 1] = silu_grad_from(p1, s1);
-              } else {
-                hb = pack_bf16(silu_f(p0), silu_f(p1));
-              }
-              hw[(j - j8) / 2] = hb;
-              z = fmaf(__uint_as_float(hb << 16), w4[c0 + j], z);
-              z = fmaf(__uint_as_float(hb & 0xFFFF0000u), w4[c0 + j + 1], z);
-            }
-            if constexpr (IO::kStores) {  // h3 into the (free) operand buffer, SiLU'(z3) out
-              if (grow < n) io.store_grad(2, grow, col0 + c0 + j8, g);
-              *reinterpret_cast<uint4*>(sa + canon_offset(trow, col0 + c0 + j8, H)) =
-                  make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            }
+          for (int j = 0; j < 32; j += 2) {
+            const float p0 = __uint_as_float(r[cur][j]) + b3[c0 + j];
+            const float p1 = __uint_as_float(r[cur][j + 1]) + b3[c0 + j + 1];
+            const uint32_t hb = pack_bf16(silu_f(p0), silu_f(p1));
+            z = fmaf(__uint_as_float(hb << 16), w4[c0 + j], z);
+            z = fmaf(__uint_as_float(hb & 0xFFFF0000u), w4[c0 + j + 1], z);
           }
           if (c0 + 32 < CW) tmem_wait_ld();
         }
         if (cg > 0) spart[(cg - 1) * TILE + trow] = z;
         tc_fence_before();
         __syncthreads();  // TMEM reads done before the next tile's MMA; partials visible
-        if constexpr (IO::kStores) {
-          copy_out_transposed(sa, io.act_out(2), io.act_ld(), tile * TILE, n - tile * TILE, tid, NT);
-          __syncthreads();  // the operand is read before the next tile's features overwrite it
-        }
         const int row = tile * TILE + trow;
         if (cg == 0) {  // column groups summed in order
 #pragma unroll

@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
       uint16_t* st = reinterpret_cast<uint16_t*>(stg);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const uint16_t v = i == 9 ? (row < n ? (uint16_t)0x3F80u : (uint16_t)0) : (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
+        const uint16_t v =
+            i == 9 ? (row < n ? (uint16_t)0x3F80u : (uint16_t)0) : (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
         st[((tid >> 6) * 2048 + canon_offset(i, tid & 63, 64)) / 2] = v;
       }
     }
