@@ -131,6 +131,8 @@ struct MlpTcWeights {
   const void* W1c;         // bf16 [256][16] canonical layout (see canon_offset)
   const void* W2c;         // bf16 [256][256] canonical layout
   const void* W3c;
+  const void* W2k;         // the same K-sliced: 16 x [256][16] canonical (8 KB each)
+  const void* W3k;
   const void* W4;          // bf16 [256]
   const float* mu;         // [9]
   const float* inv_sigma;  // [9]

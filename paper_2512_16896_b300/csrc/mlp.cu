@@ -53,16 +53,20 @@ __global__ void mlp_adam_kernel(mlpp::AdamArgs a, const float* grads, int n) {
 }
 
 // bf16 copies of the weights in the tensor cores' canonical K-major layout:
-// W1c, W2c, W3c ([out][in], B operands of the forward pass) and W2tc, W3tc
+// W1c, W2c, W3c ([out][in], B operands of the forward pass; W2k, W3k the
+// same K-sliced for the inference kernel's stream) and W2tc, W3tc
 // ([in][out], B operands of the backward pass dH = dA W); W4 plain.
 __global__ void mlp_copies_kernel(const float* params, __nv_bfloat16* W4, __nv_bfloat16* W1c, __nv_bfloat16* W2c,
-                                  __nv_bfloat16* W3c, __nv_bfloat16* W2tc, __nv_bfloat16* W3tc) {
+                                  __nv_bfloat16* W3c, __nv_bfloat16* W2k, __nv_bfloat16* W3k, __nv_bfloat16* W2tc,
+                                  __nv_bfloat16* W3tc) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * H; i += gridDim.x * blockDim.x) {
     const int n = i / H, k = i % H;
     const __nv_bfloat16 w2 = __float2bfloat16_rn(params[OFF_W2 + i]);
     const __nv_bfloat16 w3 = __float2bfloat16_rn(params[OFF_W3 + i]);
     W2c[canon_offset(n, k, H) / 2] = w2;
     W3c[canon_offset(n, k, H) / 2] = w3;
+    W2k[mlpp::kslice_offset(n, k) / 2] = w2;
+    W3k[mlpp::kslice_offset(n, k) / 2] = w3;
     W2tc[canon_offset(k, n, H) / 2] = w2;
     W3tc[canon_offset(k, n, H) / 2] = w3;
     if (i < H * KIN) {
@@ -139,6 +143,7 @@ struct MlpState {
   float* grads = nullptr;
   __nv_bfloat16* W4 = nullptr;
   __nv_bfloat16 *W1c = nullptr, *W2c = nullptr, *W3c = nullptr;  // canonical [out][in] (forward)
+  __nv_bfloat16 *W2k = nullptr, *W3k = nullptr;                   // the same, K-sliced (inference stream)
   __nv_bfloat16 *W2tc = nullptr, *W3tc = nullptr;                 // canonical [in][out] (backward)
   float* mu = nullptr;
   float* inv_sigma = nullptr;
@@ -157,7 +162,8 @@ cudaError_t mlp_alloc(MlpState** out) {
   if ((e = cudaMalloc(&S->params, nf * 4)) || (e = cudaMalloc(&S->m, nf * 4)) || (e = cudaMalloc(&S->v, nf * 4)) ||
       (e = cudaMalloc(&S->grads, nf * 4)) || (e = cudaMalloc(&S->W4, H * 2)) ||
       (e = cudaMalloc(&S->W1c, H * KIN * 2)) || (e = cudaMalloc(&S->W2c, H * H * 2)) ||
-      (e = cudaMalloc(&S->W3c, H * H * 2)) || (e = cudaMalloc(&S->W2tc, H * H * 2)) ||
+      (e = cudaMalloc(&S->W3c, H * H * 2)) || (e = cudaMalloc(&S->W2k, H * H * 2)) ||
+      (e = cudaMalloc(&S->W3k, H * H * 2)) || (e = cudaMalloc(&S->W2tc, H * H * 2)) ||
       (e = cudaMalloc(&S->W3tc, H * H * 2)) || (e = cudaMalloc(&S->mu, 64)) ||
       (e = cudaMalloc(&S->inv_sigma, 64)) || (e = cudaMalloc(&S->moments, 18 * 8))) {
     mlp_free(S);
@@ -169,15 +175,15 @@ cudaError_t mlp_alloc(MlpState** out) {
 
 void mlp_free(MlpState* S) {
   if (!S) return;
-  void* ptrs[] = {S->params, S->m,    S->v,    S->grads, S->W4,        S->W1c,      S->W2c,
-                  S->W3c,    S->W2tc, S->W3tc, S->mu,    S->inv_sigma, S->moments,  S->train_buf};
+  void* ptrs[] = {S->params, S->m,   S->v,    S->grads, S->W4, S->W1c,        S->W2c,      S->W3c,
+                  S->W2k,    S->W3k, S->W2tc, S->W3tc,  S->mu, S->inv_sigma, S->moments, S->train_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete S;
 }
 
 cudaError_t mlp_refresh_copies(MlpState* S, cudaStream_t s) {
-  mlp_copies_kernel<<<128, 256, 0, s>>>(S->params, S->W4, S->W1c, S->W2c, S->W3c, S->W2tc, S->W3tc);
+  mlp_copies_kernel<<<128, 256, 0, s>>>(S->params, S->W4, S->W1c, S->W2c, S->W3c, S->W2k, S->W3k, S->W2tc, S->W3tc);
   return cudaGetLastError();
 }
 
@@ -207,6 +213,8 @@ static MlpTcWeights tc_view(const MlpState& S) {
   w.W1c = S.W1c;
   w.W2c = S.W2c;
   w.W3c = S.W3c;
+  w.W2k = S.W2k;
+  w.W3k = S.W3k;
   w.W4 = S.W4;
   w.mu = S.mu;
   w.inv_sigma = S.inv_sigma;
@@ -336,6 +344,8 @@ static mlpp::AdamArgs next_adam(MlpState* S, float lr, float b1, float b2, float
   a.W1c = S->W1c;
   a.W2c = S->W2c;
   a.W3c = S->W3c;
+  a.W2k = S->W2k;
+  a.W3k = S->W3k;
   a.W2tc = S->W2tc;
   a.W3tc = S->W3tc;
   return a;

@@ -18,8 +18,16 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * 9, OFF_W2 = OFF_B1 + H, OFF_B2 =
               OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * H, OFF_W4 = OFF_B3 + H, OFF_B4 = OFF_W4 + H,
               N_PARAMS = OFF_B4 + 1;
 
+// Byte offset of W[o][k] (256 x 256) in the K-sliced copy the inference
+// kernel streams: 4 slices of 64 inputs, each 32 KB in the canonical K-major
+// layout with K = 64.
+__host__ __device__ __forceinline__ uint32_t kslice_offset(int o, int k) {
+  return (uint32_t)(k >> 6) * 32768u + canon_offset(o, k & 63, 64);
+}
+
 // Adam state and the bf16 weight copies one update writes: W1c, W2c, W3c
-// ([out][in], canonical K-major), W2tc, W3tc ([in][out]), W4 plain.
+// ([out][in], canonical K-major), W2k, W3k (the same, K-sliced), W2tc, W3tc
+// ([in][out]), W4 plain.
 struct AdamArgs {
   float* params;  // FP32 masters; NULL: no update
   float* m;
@@ -30,6 +38,8 @@ struct AdamArgs {
   __nv_bfloat16* W1c;
   __nv_bfloat16* W2c;
   __nv_bfloat16* W3c;
+  __nv_bfloat16* W2k;
+  __nv_bfloat16* W3k;
   __nv_bfloat16* W2tc;
   __nv_bfloat16* W3tc;
 };
@@ -54,10 +64,12 @@ __device__ __forceinline__ void adam_copies(const AdamArgs& a, int i, float p) {
   } else if (i >= OFF_W2 && i < OFF_B2) {
     const int o = (i - OFF_W2) / H, k = (i - OFF_W2) % H;
     a.W2c[canon_offset(o, k, H) / 2] = h;
+    a.W2k[kslice_offset(o, k) / 2] = h;
     a.W2tc[canon_offset(k, o, H) / 2] = h;
   } else if (i >= OFF_W3 && i < OFF_B3) {
     const int o = (i - OFF_W3) / H, k = (i - OFF_W3) % H;
     a.W3c[canon_offset(o, k, H) / 2] = h;
+    a.W3k[kslice_offset(o, k) / 2] = h;
     a.W3tc[canon_offset(k, o, H) / 2] = h;
   } else if (i >= OFF_W4 && i < OFF_B4) {
     a.W4[i - OFF_W4] = h;

@@ -39,14 +39,21 @@ namespace {
 constexpr int H = 256;
 constexpr int TILE = 128;
 constexpr int THREADS = 256;  // the training kernels' CTA; the forward pass takes 128 x IO::kColGroups
-constexpr int SM_W1 = 0;                      // [256][16] bf16 canonical, 8 KB
-constexpr int SM_W = SM_W1 + 8192;            // [256][256] bf16 canonical, 128 KB
-constexpr int SM_A = SM_W + 131072;           // [128][256] bf16 canonical, 64 KB
-constexpr int SM_BIAS = SM_A + 65536;         // b1 b2 b3 W4 as f32, 4 KB
-constexpr int SM_PART = SM_BIAS + 4 * H * 4;  // [3][128] partial logits of column groups 1..3
-constexpr int SM_BAR = SM_PART + 3 * TILE * 4;  // 2 mbarriers
-constexpr int SM_TMEM = SM_BAR + 16;          // TMEM base address written by tcgen05.alloc
+// Shared memory of the inference kernel (two tiles in flight):
+constexpr int PP_KS = 64;                             // inputs per streamed weight slice
+constexpr int PP_SLICE = H * PP_KS * 2;               // 32 KB: PP_KS inputs of all 256 outputs
+constexpr int PP_RING = 2;                            // weight slices in flight
+constexpr int SM_A = 0;                               // [2 slots][128][256] bf16 canonical operands
+constexpr int SM_WR = SM_A + 2 * TILE * H * 2;        // the weight slice ring
+constexpr int SM_W1 = SM_WR + PP_RING * PP_SLICE;     // [256][16] bf16 canonical, 8 KB
+constexpr int SM_BIAS = SM_W1 + 8192;                 // b1 b2 b3 W4 as f32, 4 KB
+constexpr int SM_PART = SM_BIAS + 4 * H * 4;          // [2 slots][3][128] partial logits of column groups 1..3
+constexpr int SM_BAR = SM_PART + 2 * 3 * TILE * 4;    // mbarriers: ring full, ring empty, accumulator full, operand ready
+constexpr int SM_NBAR = 2 * PP_RING + 4 + 1;          // ... and the MMA drain
+constexpr int SM_FLAG = SM_BAR + 8 * SM_NBAR;         // abort flag
+constexpr int SM_TMEM = SM_FLAG + 16;                 // TMEM base address written by tcgen05.alloc
 constexpr int SM_TOTAL = SM_TMEM + 16;
+static_assert(SM_TOTAL <= 227 * 1024, "shared memory of one CTA");
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -89,6 +96,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (done) return true;
     if (clock64() - t0 > kWaitCycles) return false;
   }
+}
+
+// As mbar_wait, but also gives up at once when another role of the CTA has
+// set *abort, and sets it when its own cycle budget runs out.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -207,34 +238,58 @@ __device__ __forceinline__ void epilogue_to_a(uint32_t taddr, const float* bias,
 // (the 9 raw features of a row < rows(), called by one thread per row) and
 // emit(row, valid, logit) (called by every thread of warps 0..3, one row
 // each, valid = row < rows(), so warp collectives may be used), and
-// IO::kColGroups (2 or 4): the CTA has 4 x kColGroups warps, warp w handling
+// IO::kColGroups (2 or 4): 4 x kColGroups epilogue warps, warp w handling
 // TMEM lanes 32 (w % 4) .. + 31 and columns (w / 4) H / kColGroups .. (more
 // warps hide more of the epilogue's latency; fewer leave room on the SM for
 // other kernels).
+//
+// One persistent CTA per SM keeps two of its tiles in flight, each in its
+// own slot (a 64 KB operand buffer and 256 TMEM columns), so the tensor
+// cores work on one slot while the epilogue warps work on the other: the
+// epilogues go slot 0 layer 1, slot 1 layer 1, slot 0 layer 2, ... and the
+// MMAs of a slot's next layer run under the other slot's epilogue. W2 and W3
+// do not fit beside two operands, so one producer thread streams them
+// through a ring of K-slices (64 inputs of all 256 outputs, 32 KB each, from
+// the K-sliced weight copies) in the order one MMA thread consumes them, four
+// M = 128, N = 256, K = 16 MMAs per slice; W1 stays resident. Roles meet on mbarriers: slice full (bulk
+// copy) and empty (MMA commit), accumulator full (MMA commit), operand
+// ready (every epilogue warp has written its part and finished its TMEM
+// reads). Every wait is bounded; a role whose wait gives up sets a shared
+// abort flag that ends the others' waits, and the CTA then latches
+// kDevTimeout, waits (bounded) for its own copies and MMAs and frees TMEM.
 template <class IO>
-__global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
+__global__ void __launch_bounds__(128 * IO::kColGroups + 64, 1) mlp_tc_kernel(MlpTcWeights w, IO io, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int CG = IO::kColGroups, NT = 128 * CG, CW = H / CG;
+  constexpr int CG = IO::kColGroups, NE = 128 * CG, NT = NE + 64, CW = H / CG;
   static_assert(CG == 2 || CG == 4, "two or four column groups");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = io.rows();
   const int ntiles = (n + TILE - 1) / TILE;
   if ((int)blockIdx.x >= ntiles) return;  // uniform for the CTA, before any allocation
+  const int T = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;  // tiles blockIdx.x + i gridDim.x, i < T
 
-  uint8_t* sw1 = smem + SM_W1;
-  uint8_t* sw = smem + SM_W;
-  uint8_t* sa = smem + SM_A;
+  const uint32_t s0 = smem_u32(smem);
   float* sbias = reinterpret_cast<float*>(smem + SM_BIAS);  // b1 | b2 | b3 | W4
   float* spart = reinterpret_cast<float*>(smem + SM_PART);
-  const uint32_t bar_w = smem_u32(smem + SM_BAR), bar_m = bar_w + 8;
+  const uint32_t bar_full = s0 + SM_BAR, bar_empty = bar_full + 8 * PP_RING;
+  const uint32_t bar_acc = bar_empty + 8 * PP_RING, bar_ready = bar_acc + 16, bar_drain = bar_ready + 16;
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + SM_FLAG);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TMEM);
 
   if (tid == 0) {
-    mbar_init(bar_w, 1);
-    mbar_init(bar_m, 1);
+    for (int i = 0; i < PP_RING; ++i) {
+      mbar_init(bar_full + 8 * i, 1);
+      mbar_init(bar_empty + 8 * i, 1);
+    }
+    for (int p = 0; p < 2; ++p) {
+      mbar_init(bar_acc + 8 * p, 1);
+      mbar_init(bar_ready + 8 * p, NE / 32);
+    }
+    mbar_init(bar_drain, 1);
+    *abort = 0;
   }
   for (int i = tid; i < 8192 / 16; i += NT)
-    reinterpret_cast<uint4*>(sw1)[i] = __ldg(reinterpret_cast<const uint4*>(w.W1c) + i);
+    reinterpret_cast<uint4*>(smem + SM_W1)[i] = __ldg(reinterpret_cast<const uint4*>(w.W1c) + i);
   for (int i = tid; i < H; i += NT) {
     sbias[i] = __ldg(w.params + w.off_b1 + i);
     sbias[H + i] = __ldg(w.params + w.off_b2 + i);
@@ -243,7 +298,8 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
   }
   const float b4 = __ldg(w.params + w.off_b4);
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(H)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(2 * H)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -252,144 +308,170 @@ __global__ void __launch_bounds__(128 * IO::kColGroups, 1) mlp_tc_kernel(MlpTcWe
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const int quarter = warp & 3, cg = warp >> 2;
-  const int trow = quarter * 32 + lane;  // this thread's row in the tile (= TMEM lane)
-  const int col0 = cg * CW;              // this thread's columns
-  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
-  constexpr uint32_t idesc = make_idesc(TILE, H);
+  const uint32_t tmem = *tslot;  // slot p: columns 256 p .. + 255
+  int issued = 0;                 // weight slices the producer issued (its thread only)
 
-  uint32_t ph_w = 0, ph_m = 0;
-  bool w_pending = true, m_pending = false, ok = true;
-  if (tid == 0) bulk_load(smem_u32(sw), w.W2c, 131072, bar_w);
-
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // ---- layer-1 operand: standardised features, bf16, K padded to 16
-    if (tid < TILE) {
-      const int row = tile * TILE + tid;
+  if (warp < NE / 32) {
+    // ---- epilogue warps
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int trow = quarter * 32 + lane;  // this thread's row in the tile (= TMEM lane)
+    const int col0 = cg * CW;              // this thread's columns
+    // tile i's layer-1 operand (standardised features, bf16, K padded to 16)
+    // into slot p, one row per thread of warps 0..3
+    auto features = [&](int p, int i) {
+      if (cg != 0) return;
+      const int row = ((int)blockIdx.x + i * (int)gridDim.x) * TILE + trow;
       float x[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] = 0.f;
+      for (int k = 0; k < 16; ++k) x[k] = 0.f;
       if (row < n) {
         float f[9];
         io.features(row, f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) x[i] = (f[i] - __ldg(w.mu + i)) * __ldg(w.inv_sigma + i);
+        for (int k = 0; k < 9; ++k) x[k] = (f[k] - __ldg(w.mu + k)) * __ldg(w.inv_sigma + k);
       }
       uint32_t xb[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) xb[i] = pack_bf16(x[2 * i], x[2 * i + 1]);
+      for (int k = 0; k < 8; ++k) xb[k] = pack_bf16(x[2 * k], x[2 * k + 1]);
+      uint8_t* sa = smem + SM_A + p * (TILE * H * 2);
 #pragma unroll
       for (int q = 0; q < 2; ++q)
-        *reinterpret_cast<uint4*>(sa + canon_offset(tid, q * 8, 16)) =
+        *reinterpret_cast<uint4*>(sa + canon_offset(trow, q * 8, 16)) =
             make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      tc_mma(tmem, make_desc(smem_u32(sa), 128, 256), make_desc(smem_u32(sw1), 128, 256), idesc, 0);
-      tc_commit(bar_m);
-    }
-    m_pending = true;
-    ok = mbar_wait(bar_m, ph_m);
-    if (ok) {
-      ph_m ^= 1;
-      m_pending = false;
-    }
-    tc_fence_after();
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    epilogue_to_a<CW>(taddr, sbias, sa, trow, col0);
-
-    // ---- layers 2 and 3
-    for (int layer = 0; layer < 2; ++layer) {
+    };
+    // this warp's part of slot p's operand is written and its TMEM reads are done
+    auto ready = [&](int p) {
       fence_proxy_async();
       tc_fence_before();
-      ok = mbar_wait(bar_w, ph_w);  // this layer's weights have landed
-      if (ok) {
-        ph_w ^= 1;
-        w_pending = false;
-      }
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll 1
-        for (int s = 0; s < H / 16; ++s)
-          tc_mma(tmem, make_desc(smem_u32(sa) + 256 * s, 128, 4096), make_desc(smem_u32(sw) + 256 * s, 128, 4096),
-                 idesc, s > 0);
-        tc_commit(bar_m);
-      }
-      m_pending = true;
-      ok = mbar_wait(bar_m, ph_m);
-      if (ok) {
-        ph_m ^= 1;
-        m_pending = false;
-      }
-      tc_fence_after();
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      // The MMAs have read the weight buffer: bring in the next weights (W3,
-      // or the next tile's W2) while the epilogue runs.
-      if (layer == 0 || tile + (int)gridDim.x < ntiles) {
-        if (tid == 0) bulk_load(smem_u32(sw), layer == 0 ? w.W3c : w.W2c, 131072, bar_w);
-        w_pending = true;
-      }
-      if (layer == 0) {
-        epilogue_to_a<CW>(taddr, sbias + H, sa, trow, col0);
-      } else {
-        // h3 = bf16(SiLU(acc + b3)); logit = W4 . h3 + b4
-        const float* b3 = sbias + 2 * H + col0;
-        const float* w4 = sbias + 3 * H + col0;
-        float z = 0.f;
-        uint32_t r[2][32];
-        tmem_ld32_async(taddr, r[0]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int c0 = 0; c0 < CW; c0 += 32) {
-          const int cur = (c0 / 32) & 1;
-          if (c0 + 32 < CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const float p0 = __uint_as_float(r[cur][j]) + b3[c0 + j];
-            const float p1 = __uint_as_float(r[cur][j + 1]) + b3[c0 + j + 1];
-            const uint32_t hb = pack_bf16(silu_f(p0), silu_f(p1));
-            z = fmaf(__uint_as_float(hb << 16), w4[c0 + j], z);
-            z = fmaf(__uint_as_float(hb & 0xFFFF0000u), w4[c0 + j + 1], z);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_ready + 8 * p);
+    };
+    bool ok = true;
+    uint32_t ph_acc[2] = {0u, 0u};
+    for (int p = 0; p < 2 && p < T; ++p) {
+      features(p, p);
+      ready(p);
+    }
+    for (int i0 = 0; i0 < T && ok; i0 += 2)
+      for (int layer = 0; layer < 3 && ok; ++layer)
+        for (int p = 0; p < 2; ++p) {
+          const int i = i0 + p;
+          if (i >= T) break;
+          ok = mbar_wait_or_abort(bar_acc + 8 * p, ph_acc[p], abort);
+          if (!ok) break;
+          ph_acc[p] ^= 1;
+          tc_fence_after();
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(H * p + col0);
+          uint8_t* sa = smem + SM_A + p * (TILE * H * 2);
+          if (layer < 2) {
+            epilogue_to_a<CW>(taddr, sbias + layer * H, sa, trow, col0);
+            ready(p);
+            continue;
           }
-          if (c0 + 32 < CW) tmem_wait_ld();
-        }
-        if (cg > 0) spart[(cg - 1) * TILE + trow] = z;
-        tc_fence_before();
-        __syncthreads();  // TMEM reads done before the next tile's MMA; partials visible
-        const int row = tile * TILE + trow;
-        if (cg == 0) {  // column groups summed in order
+          // h3 = bf16(SiLU(acc + b3)); logit = W4 . h3 + b4
+          const float* b3 = sbias + 2 * H + col0;
+          const float* w4 = sbias + 3 * H + col0;
+          float z = 0.f;
+          uint32_t r[2][32];
+          tmem_ld32_async(taddr, r[0]);
+          tmem_wait_ld();
 #pragma unroll
-          for (int g = 1; g < CG; ++g) z += spart[(g - 1) * TILE + trow];
-          io.emit(row, row < n, z + b4);
+          for (int c0 = 0; c0 < CW; c0 += 32) {
+            const int cur = (c0 / 32) & 1;
+            if (c0 + 32 < CW) tmem_ld32_async(taddr + c0 + 32, r[cur ^ 1]);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const float p0 = __uint_as_float(r[cur][j]) + b3[c0 + j];
+              const float p1 = __uint_as_float(r[cur][j + 1]) + b3[c0 + j + 1];
+              const uint32_t hb = pack_bf16(silu_f(p0), silu_f(p1));
+              z = fmaf(__uint_as_float(hb << 16), w4[c0 + j], z);
+              z = fmaf(__uint_as_float(hb & 0xFFFF0000u), w4[c0 + j + 1], z);
+            }
+            if (c0 + 32 < CW) tmem_wait_ld();
+          }
+          float* sp = spart + p * 3 * TILE;
+          if (cg > 0) sp[(cg - 1) * TILE + trow] = z;
+          asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");  // the column groups' partials (epilogue warps)
+          // the next tile of this slot: its features, once this slot's TMEM is read
+          if (i + 2 < T) features(p, i + 2);
+          if (cg == 0) {  // column groups summed in order
+#pragma unroll
+            for (int g = 1; g < CG; ++g) z += sp[(g - 1) * TILE + trow];
+            const int row = ((int)blockIdx.x + i * (int)gridDim.x) * TILE + trow;
+            io.emit(row, row < n, z + b4);
+          }
+          if (i + 2 < T) ready(p);
         }
-      }
+  } else if (warp == NE / 32) {
+    // ---- producer: W2 and W3 slices, in the order the MMA thread takes them
+    if (lane == 0) {
+      bool ok = true;
+      for (int i0 = 0; i0 < T && ok; i0 += 2)
+        for (int layer = 1; layer < 3 && ok; ++layer)
+          for (int p = 0; p < 2 && ok; ++p) {
+            if (i0 + p >= T) break;
+            const char* wl = static_cast<const char*>(layer == 1 ? w.W2k : w.W3k);
+            for (int j = 0; j < H / PP_KS && ok; ++j) {
+              const int r = issued % PP_RING;
+              if (issued >= PP_RING)  // the MMAs that read this ring slot are done
+                ok = mbar_wait_or_abort(bar_empty + 8 * r, (uint32_t)((issued / PP_RING - 1) & 1), abort);
+              if (!ok) break;
+              bulk_load(s0 + SM_WR + r * PP_SLICE, wl + (size_t)j * PP_SLICE, PP_SLICE, bar_full + 8 * r);
+              ++issued;
+            }
+          }
+    }
+  } else {
+    // ---- MMA thread
+    if (lane == 0) {
+      bool ok = true;
+      int used = 0;
+      uint32_t ph_ready[2] = {0u, 0u};
+      for (int i0 = 0; i0 < T && ok; i0 += 2)
+        for (int layer = 0; layer < 3 && ok; ++layer)
+          for (int p = 0; p < 2 && ok; ++p) {
+            if (i0 + p >= T) break;
+            ok = mbar_wait_or_abort(bar_ready + 8 * p, ph_ready[p], abort);
+            if (!ok) break;
+            ph_ready[p] ^= 1;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(H * p);
+            const uint32_t a = s0 + SM_A + p * (TILE * H * 2);
+            if (layer == 0) {
+              tc_mma(d, make_desc(a, 128, 256), make_desc(s0 + SM_W1, 128, 256), make_idesc(TILE, H), 0);
+            } else {
+              for (int j = 0; j < H / PP_KS && ok; ++j, ++used) {
+                const int r = used % PP_RING;
+                ok = mbar_wait_or_abort(bar_full + 8 * r, (uint32_t)((used / PP_RING) & 1), abort);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t b = s0 + SM_WR + r * PP_SLICE;
+#pragma unroll
+                for (int k = 0; k < PP_KS / 16; ++k)
+                  tc_mma(d, make_desc(a + (PP_KS / 16 * j + k) * 256, 128, 4096),
+                         make_desc(b + 256 * k, 128, PP_KS / 8 * 128), make_idesc(TILE, H), (j > 0 || k > 0) ? 1u : 0u);
+                tc_commit(bar_empty + 8 * r);
+              }
+            }
+            if (ok) tc_commit(bar_acc + 8 * p);
+          }
+      // every MMA this thread issued has completed before TMEM is freed
+      tc_commit(bar_drain);
+      mbar_wait(bar_drain, 0);
     }
   }
-  if (!ok) {
+  __syncthreads();
+  if (*abort) {
     if (tid == 0) latch_error(status, kDevTimeout);
-    // Drain what this CTA still has in flight before its TMEM and shared memory go away.
-    if (w_pending) mbar_wait(bar_w, ph_w);
-    if (m_pending) mbar_wait(bar_m, ph_m);
+    if (warp == NE / 32 && lane == 0)  // this producer's copies have landed before the CTA leaves
+      for (int u = issued > PP_RING ? issued - PP_RING : 0; u < issued; ++u)
+        mbar_wait(bar_full + 8 * (u % PP_RING), (uint32_t)((u / PP_RING) & 1));
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * H) : "memory");
   }
 }
 
@@ -404,7 +486,7 @@ cudaError_t launch_mlp_tc(const MlpTcWeights& w, const IO& io, int n_cap, int* s
   if (e) return e;
   const int tiles = (n_cap + TILE - 1) / TILE;
   const int grid = tiles < num_sms ? tiles : num_sms;
-  mlp_tc_kernel<IO><<<grid, 128 * IO::kColGroups, SM_TOTAL, s>>>(w, io, status);
+  mlp_tc_kernel<IO><<<grid, 128 * IO::kColGroups + 64, SM_TOTAL, s>>>(w, io, status);
   return cudaGetLastError();
 }
 

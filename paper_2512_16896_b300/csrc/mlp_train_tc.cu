@@ -876,6 +876,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
       const int o0 = mt * TILE + row0;  // first output feature of this block
       if (wide) {
         __nv_bfloat16* Wc = jb == 1 ? G.adam.W2c : G.adam.W3c;
+        __nv_bfloat16* Wk = jb == 1 ? G.adam.W2k : G.adam.W3k;
         __nv_bfloat16* Wtc = jb == 1 ? G.adam.W2tc : G.adam.W3tc;
         const int ng = r1 * (H / 4);
         for (int g0 = tid; g0 < ng; g0 += 2 * THREADS) {
@@ -909,11 +910,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
             *reinterpret_cast<float4*>(G.adam.m + i) = make_float4(mn[0], mn[1], mn[2], mn[3]);
             *reinterpret_cast<float4*>(G.adam.v + i) = make_float4(vn[0], vn[1], vn[2], vn[3]);
             *reinterpret_cast<float4*>(G.adam.params + i) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-            // bf16 copies: 4 consecutive inputs of output o ([out][in], 8 bytes) and
-            // the transposed copy's 4 rows
+            // bf16 copies: 4 consecutive inputs of output o ([out][in] and
+            // K-sliced, 8 bytes each) and the transposed copy's 4 rows
             const __nv_bfloat162 h01 = __floats2bfloat162_rn(pn[0], pn[1]), h23 = __floats2bfloat162_rn(pn[2], pn[3]);
-            *reinterpret_cast<uint2*>(Wc + canon_offset(o, c, H) / 2) =
-                make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            const uint2 h4 = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            *reinterpret_cast<uint2*>(Wc + canon_offset(o, c, H) / 2) = h4;
+            *reinterpret_cast<uint2*>(Wk + mlpp::kslice_offset(o, c) / 2) = h4;
 #pragma unroll
             for (int j = 0; j < 4; ++j) Wtc[canon_offset(c + j, o, H) / 2] = __float2bfloat16_rn(pn[j]);
           }
