@@ -811,6 +811,10 @@ __global__ void __launch_bounds__(256, 3) gen_chain_kernel(GenStepArgs g, ChainA
 // reach-flagged objects, in the reach list, get a top-down grasp target in
 // the robot base frame; an optional learned gate sends the ones it predicts
 // unreachable back to retry; exact IK decides the rest.
+// Logit margin above the gate's threshold within which a passed target is
+// "doubtful" (likelier unreachable, so likelier to run every IK iteration).
+constexpr float kDoubtful = 5.f;
+
 struct ReachArgs {
   sc_scene_batch b;
   const int32_t* cand_t;
@@ -821,8 +825,12 @@ struct ReachArgs {
   const int32_t* list_reach;  // this round's reach queue
   const int* n_reach;
   float* targets;        // [cap][12]
-  int32_t* list_ik;      // positions in the reach list the gate passed
-  int* n_ik;
+  int32_t* list_ik;      // positions in the reach list the gate passed: those within
+                         // kDoubtful of the threshold from the front, the others
+                         // from the back (capacity ik_cap), so IK starts with the
+                         // targets likeliest to run every iteration
+  int* n_ik;             // [2]: front and back counts
+  int ik_cap;
   int32_t* list_gen;     // the round after next: retries and next objects
   int* n_gen;
   unsigned int* claim;   // IK work counter of the round (zeroed at init)
@@ -858,19 +866,25 @@ __device__ __forceinline__ void reach_advance(const ReachArgs& A, int c, int k, 
 
 
 // A gate's decision on reach-queue entry `row` (warp-uniform call; `valid`
-// false on lanes past the queue): a pass goes to the IK list, a rejection
-// retries (or ends invalid); appends aggregated per warp.
-__device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool valid, bool pass) {
+// false on lanes past the queue): a pass goes to the IK list (a doubtful one
+// to its front, the others to its back), a rejection retries (or ends
+// invalid); appends aggregated per warp.
+__device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool valid, bool pass, bool doubtful) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   pass = valid && pass;
-  const unsigned mp = __ballot_sync(0xFFFFFFFFu, pass);
-  if (mp) {
-    const int leader = __ffs(mp) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(A.n_ik, __popc(mp));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pass) A.list_ik[base + __popc(mp & lt)] = row;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const bool mine = pass && (doubtful == (side == 0));
+    const unsigned mp = __ballot_sync(0xFFFFFFFFu, mine);
+    if (mp) {
+      const int leader = __ffs(mp) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(A.n_ik + side, __popc(mp));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      const int pos = base + __popc(mp & lt);
+      if (mine) A.list_ik[side == 0 ? pos : A.ik_cap - 1 - pos] = row;
+    }
   }
   const bool rej = valid && !pass;
   int c = 0;
@@ -906,7 +920,9 @@ struct GateIO {
     f[3] = __ldg(t + 0); f[4] = __ldg(t + 3); f[5] = __ldg(t + 6);
     f[6] = __ldg(t + 1); f[7] = __ldg(t + 4); f[8] = __ldg(t + 7);
   }
-  __device__ void emit(int row, bool valid, float logit) const { gate_route(A, row, valid, logit >= A.tau); }
+  __device__ void emit(int row, bool valid, float logit) const {
+    gate_route(A, row, valid, logit >= A.tau, logit < A.tau + kDoubtful);
+  }
 };
 
 // The 4D reachability map's decision on the round's reach queue (the grasp
@@ -926,7 +942,7 @@ __global__ void reach_map_gate_kernel(ReachArgs A) {
       for (int j = 0; j < 12; ++j) o[j] = t[j];
       pass = (int)rmap_score(A.map_counts, rmap_cell(A.map_grid, o)) >= A.map_tau;
     }
-    gate_route(A, i, valid, pass);
+    gate_route(A, i, valid, pass, true);
   }
 }
 
@@ -936,14 +952,15 @@ __global__ void reach_map_gate_kernel(ReachArgs A) {
 // current one) from a grid sized to the resident blocks.
 __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  const int n = A.gated ? *(volatile const int*)A.n_ik : *(volatile const int*)A.n_reach;
+  const int nf = A.gated ? *(volatile const int*)A.n_ik : 0;  // front part of the IK list
+  const int n = A.gated ? nf + *(volatile const int*)(A.n_ik + 1) : *(volatile const int*)A.n_reach;
   const int warps_total = gridDim.x * warps;
   unsigned long long solves = 0, seed_iters = 0;
   int j = blockIdx.x * warps + (threadIdx.x >> 5);
   while (j < n) {
     int next = 0;
     if (lane == 0) next = warps_total + (int)atomicAdd(A.claim, 1u);
-    const int i = A.gated ? A.list_ik[j] : j;
+    const int i = A.gated ? A.list_ik[j < nf ? j : A.ik_cap - 1 - (j - nf)] : j;
     const int c = A.list_reach[i];
     const int k = A.st.kc[c], r = A.st.rc[c];
     const ikc::Target T = ikc::load_target(A.targets + 12 * (size_t)i);
@@ -1159,8 +1176,8 @@ int generate_rounds(int reach_objects, int max_retries) {
 
 // Scratch: round lists G[3], reach queues Q[2] and gate-passed lists IK[2]
 // (int32 [n] each), two slots of grasp targets (12 floats); counts
-// (list lengths per round [NR + 2], reach queue and IK lengths per round
-// [NR] each); work counters (generation claims per round, the chained
+// (list lengths per round [NR + 2], reach queue lengths per round [NR], the
+// IK list's two part lengths per round [2 NR]); work counters (generation claims per round, the chained
 // launch's, IK claims per round); the per-candidate state (object, try,
 // alive); the per-call tables (candidate templates, TmplInfo records,
 // inverse edge lengths, world-box frames, triangle chunk balls); then the
@@ -1177,7 +1194,7 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   GenScratch L;
   L.lists = 0;
   L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 12 * n * sizeof(float));
-  L.counters = up(L.counts + ((NR + 2) + 2 * NR) * sizeof(int));
+  L.counters = up(L.counts + ((NR + 2) + 3 * NR) * sizeof(int));
   L.kc = up(L.counters + (2 * NR + 1) * sizeof(unsigned int));
   L.rc = up(L.kc + (size_t)b.n_cand);
   L.alive = up(L.rc + (size_t)b.n_cand * sizeof(uint16_t));
@@ -1229,10 +1246,10 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   float* targets[2] = {fb, fb + 12 * (size_t)n};
   const int NRmax = generate_rounds(K, R);
   int* counts = reinterpret_cast<int*>(sb + SL.counts);
-  const int n_counts = (NRmax + 2) + 2 * NRmax;
+  const int n_counts = (NRmax + 2) + 3 * NRmax;
   int* cnt_gen = counts;                  // [NR + 2]
   int* cnt_reach = counts + (NRmax + 2);  // [NR]
-  int* cnt_ik = cnt_reach + NRmax;        // [NR]
+  int* cnt_ik = cnt_reach + NRmax;        // [NR][2]
   unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
   const int n_counters = 2 * NRmax + 1;  // generation claims per round, the chained launch's, IK claims per round
   CandState st;
@@ -1365,7 +1382,8 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ra.n_reach = cnt_reach + i;
     ra.targets = targets[i % 2];
     ra.list_ik = IK[i % 2];
-    ra.n_ik = cnt_ik + i;
+    ra.n_ik = cnt_ik + 2 * i;
+    ra.ik_cap = n;
     ra.list_gen = G[(i + 2) % 3];
     ra.n_gen = cnt_gen + i + 2;
     ra.claim = counters + NRmax + 1 + i;
