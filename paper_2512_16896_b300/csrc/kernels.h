@@ -177,7 +177,7 @@ struct TrainTcLaunch {
   uint8_t* daT[3];       // chunk-tiled, 256 features: dL/da1..3
   float* dz;             // [n]
   float* loss_sum;       // the mean BCE (written by the step)
-  float* wg_part;        // mlp_train_tc_part_bytes(ld): per-tile sums of dz h3 and dz
+  float* tile_sums;      // mlp_train_tc_tile_sum_bytes(n): per-tile sums of dz h3, dz and the BCE
   float* dW1;            // [256][9]
   float* dW2;            // [256][256]
   float* dW3;
@@ -187,7 +187,7 @@ struct TrainTcLaunch {
   int* status;
   const mlpp::AdamArgs* adam;  // non-NULL: Adam on every parameter as its gradient is written
 };
-size_t mlp_train_tc_part_bytes(int Bcap);
+size_t mlp_train_tc_tile_sum_bytes(int Bcap);
 cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t s);
 cudaError_t mlp_adam(MlpState* S, float lr, float b1, float b2, float eps, cudaStream_t s);
 // One training step: the gradients of rows index[0..B) (as mlp_gradients)

@@ -248,7 +248,7 @@ struct TrainViews {
   float* dz;        // [Bcap]
   float* logits;    // [Bcap]
   float* loss_sum;
-  float* part;      // mlp_train_tc_part_bytes(Bcap): per-tile sums
+  float* part;      // mlp_train_tc_tile_sum_bytes(Bcap): per-tile sums
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -259,7 +259,7 @@ static size_t tiled_rows(int Bcap) { return ((size_t)Bcap + 127) / 128 * 128; }
 static size_t train_bytes(int Bcap) {
   const size_t Bp = (size_t)Bcap, Bt = tiled_rows(Bcap);
   return align256(Bt * KIN * 2) + 2 * align256(Bt * H * 2) + 3 * align256(Bt * H * 2) + 2 * align256(Bp * 4) + 256 +
-         align256(mlp_train_tc_part_bytes(Bcap));
+         align256(mlp_train_tc_tile_sum_bytes(Bcap));
 }
 
 static TrainViews carve(MlpState* S, int Bcap) {
@@ -273,7 +273,7 @@ static TrainViews carve(MlpState* S, int Bcap) {
   v.dz = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.logits = reinterpret_cast<float*>(take((size_t)Bcap * 4));
   v.loss_sum = reinterpret_cast<float*>(take(256));
-  v.part = reinterpret_cast<float*>(take(mlp_train_tc_part_bytes(Bcap)));
+  v.part = reinterpret_cast<float*>(take(mlp_train_tc_tile_sum_bytes(Bcap)));
   return v;
 }
 
@@ -312,7 +312,7 @@ static cudaError_t gradients(MlpState* S, const float* targets, const uint8_t* l
   for (int l = 0; l < 3; ++l) L.daT[l] = v.daT[l];
   L.dz = v.dz;
   L.loss_sum = loss;
-  L.wg_part = v.part;
+  L.tile_sums = v.part;
   L.dW1 = S->grads + OFF_W1;
   L.dW2 = S->grads + OFF_W2;
   L.dW3 = S->grads + OFF_W3;

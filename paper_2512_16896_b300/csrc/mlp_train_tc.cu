@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
 
 }  // namespace
 
-size_t mlp_train_tc_part_bytes(int Bcap) { return (size_t)((Bcap + TILE - 1) / TILE) * TS_LD * 4; }
+size_t mlp_train_tc_tile_sum_bytes(int Bcap) { return (size_t)((Bcap + TILE - 1) / TILE) * TS_LD * 4; }
 
 namespace {
 
@@ -1013,7 +1013,7 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     for (int l = 0; l < 3; ++l) A.daT[l] = L.daT[l];
     for (int l = 0; l < 2; ++l) A.hT[l] = L.hT[l];
     A.dz = L.dz;
-    A.tsum = L.wg_part;
+    A.tsum = L.tile_sums;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(FB_CTAS * ntiles));
     cfg.blockDim = dim3(FB_THREADS);
@@ -1043,7 +1043,7 @@ cudaError_t mlp_train_tc_step(const TrainTcLaunch& L, int num_sms, cudaStream_t 
     } else {
       std::memset(&G.adam, 0, sizeof(G.adam));
     }
-    G.tsum = L.wg_part;
+    G.tsum = L.tile_sums;
     G.tiles = ntiles;
     G.dW4 = L.dW4;
     G.db4 = L.db4;
