@@ -911,7 +911,7 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
 // rows are the round's reach queue (grasp targets written by the generation
 // round), and each logit is decided at once (logit >= tau).
 struct GateIO {
-  static constexpr int kColGroups = 2;  // 8 warps: leaves room on the SM for the IK blocks of the other side stream
+  static constexpr int kColGroups = 4;  // 16 epilogue warps (8 left room for more IK blocks but ran slower)
   ReachArgs A;
   __device__ int rows() const { return *(volatile const int*)A.n_reach; }
   __device__ void features(int row, float f[9]) const {
