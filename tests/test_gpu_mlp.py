@@ -76,9 +76,11 @@ def test_forward_matches_oracle(sc, ctx, n):
 
 
 # one 4096-row batch (32 tiles); a ragged batch (a partial tile and a
-# partial 64-row chunk of the weight-gradient reduction); more tiles than
-# CTAs (each CTA reloads the W^T copies between its tiles)
-@pytest.mark.parametrize("n", [4096, 1000, 2 * 148 * 128 + 77])
+# partial 64-row chunk of the weight-gradient reduction); more tiles than the
+# GPU holds at once; and small batches whose weight-gradient clusters have
+# 1, 2 and 5 CTAs (a split count that is no power of two; 128 / S rows of the
+# cross-split reduction per CTA, in several blocks for S <= 2)
+@pytest.mark.parametrize("n", [4096, 1000, 2 * 148 * 128 + 77, 1, 100, 300])
 def test_gradients_match_oracle(sc, ctx, n):
     P = random_net(2)
     net = sc.Surrogate(ctx, seed=0)
