@@ -70,8 +70,7 @@ constexpr int FB_HALF = FB_PART + FB_CTAS * TILE * 4;  // [128] partial logit of
 constexpr int FB_DZ = FB_HALF + TILE * 4;              // [128] bf16-rounded dz of the tile
 constexpr int FB_DZF = FB_DZ + TILE * 4;               // [128] dz of the tile
 constexpr int FB_RED = FB_DZF + TILE * 4;              // [4][64] partial sums of dW4
-constexpr int FB_STG = FB_RED + 4 * FB_NS * 4;         // [2][8 KB] a block transposed for its bulk store
-constexpr int FB_BAR = FB_STG + 2 * 8192;              // 6 mbarriers
+constexpr int FB_BAR = FB_RED + 4 * FB_NS * 4;         // 6 mbarriers
 constexpr int FB_TMEM = FB_BAR + 48;
 constexpr int FB_TOTAL = FB_TMEM + 16;
 constexpr uint32_t FB_TCOLS = 4 * FB_NS;               // TMEM: accumulator, SiLU'(z1), SiLU'(z2), SiLU'(z3)
@@ -160,46 +159,21 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32]) 
 // weight-gradient kernel stages a chunk with one bulk copy per operand.
 
 // This CTA's 64-feature block of a 128-row tile (canonical, K = features)
-// into the chunk-tiled layout: each 8 x 8 core matrix transposed in
-// registers into the staging buffer (8 KB per chunk, the CTA's features
-// contiguous there), then one bulk store per chunk. The previous bulk store
-// has read the staging buffer before it is written again.
-__device__ __forceinline__ void copy_out_tiled(const uint8_t* blk, uint8_t* stg, uint8_t* dst, int tile, int fs,
-                                               int tid) {
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-  __syncthreads();
-  for (int cm = tid; cm < (TILE / 8) * (FB_NS / 8); cm += FB_THREADS) {
+// into the chunk-tiled layout, a core matrix per warp at a time: its 128
+// contiguous bytes loaded as one 32-bit word per lane (row lane / 4,
+// features 2 (lane % 4) and + 1), transposed across the warp
+// (movmatrix.m8n8.trans), and stored as 128 contiguous bytes of the
+// transposed core matrix (feature rows of 8 batch rows).
+__device__ __forceinline__ void copy_out_tiled(const uint8_t* blk, uint8_t* dst, int tile, int fs, int warp,
+                                               int lane) {
+#pragma unroll 4
+  for (int cm = warp; cm < (TILE / 8) * (FB_NS / 8); cm += FB_THREADS / 32) {
     const int rg = cm / (FB_NS / 8), kg = cm % (FB_NS / 8);  // rows 8 rg.., features 8 kg..
-    const uint8_t* src = blk + rg * (FB_NS / 8) * 128 + kg * 128;
-    uint32_t w[8][4];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * r);
-      w[r][0] = v.x; w[r][1] = v.y; w[r][2] = v.z; w[r][3] = v.w;
-    }
-    uint8_t* d = stg + (rg >> 3) * 8192 + kg * 1024 + (rg & 7) * 128;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {  // features 2p, 2p + 1 of the core matrix, over its 8 rows
-      uint32_t lo[4], hi[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {  // rows 2q, 2q + 1
-        lo[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x5410);
-        hi[q] = __byte_perm(w[2 * q][p], w[2 * q + 1][p], 0x7632);
-      }
-      *reinterpret_cast<uint4*>(d + (2 * p) * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      *reinterpret_cast<uint4*>(d + (2 * p + 1) * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    }
-  }
-  fence_proxy_async();
-  __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 8192;" ::"l"(
-                       dst + (size_t)(2 * tile + h) * (H * 128) + (size_t)(fs / 8) * 1024),
-                   "r"(smem_u32(stg + h * 8192))
-                   : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(blk + rg * (FB_NS / 8) * 128 + kg * 128 + 4 * lane);
+    uint32_t t;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(t) : "r"(v));
+    *reinterpret_cast<uint32_t*>(dst + (size_t)(2 * tile + (rg >> 3)) * (H * 128) + (size_t)(fs / 8 + kg) * 1024 +
+                                 (rg & 7) * 128 + 4 * lane) = t;
   }
 }
 
@@ -242,7 +216,6 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   float* sdz = reinterpret_cast<float*>(smem + FB_DZ);
   float* sdzf = reinterpret_cast<float*>(smem + FB_DZF);
   float* sred = reinterpret_cast<float*>(smem + FB_RED);
-  uint8_t* stg = smem + FB_STG;
   const int tile = row0 / TILE;
   const uint32_t s0 = smem_u32(smem);
   const uint32_t bar_a = s0 + FB_BAR, bar_b = bar_a + 8, bar_m = bar_a + 16;  // weights, weights, MMAs
@@ -313,24 +286,11 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
       *reinterpret_cast<uint4*>(smem + FB_X + canon_offset(tid, q * 8, 16)) =
           make_uint4(xb[4 * q], xb[4 * q + 1], xb[4 * q + 2], xb[4 * q + 3]);
     if (rank == 0) {  // the tile's two chunks of X, with input slot 9 = 1 on rows < n (bias gradients)
-      uint16_t* st = reinterpret_cast<uint16_t*>(stg);
+      uint16_t* xt = reinterpret_cast<uint16_t*>(A.x16T + (size_t)tile * 4096 + (tid >> 6) * 2048);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const uint16_t v =
+      for (int i = 0; i < 16; ++i)
+        xt[canon_offset(i, tid & 63, 64) / 2] =
             i == 9 ? (row < n ? (uint16_t)0x3F80u : (uint16_t)0) : (uint16_t)(xb[i >> 1] >> (16 * (i & 1)));
-        st[((tid >> 6) * 2048 + canon_offset(i, tid & 63, 64)) / 2] = v;
-      }
-    }
-  }
-  if (rank == 0) {
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 4096;" ::"l"(
-                       A.x16T + (size_t)tile * 4096),
-                   "r"(smem_u32(stg))
-                   : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
   fence_proxy_async();
@@ -418,7 +378,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   cluster_wait();  // every CTA's mbarriers are ready
   if (ok) publish(own0, FB_BLK, bar_x0);
   // z2 = h1 W2^T once every block of h1 is here; this CTA's h1 out meanwhile
-  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, stg, A.hT[0], tile, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, A.hT[0], tile, fs, warp, lane);
   if (ok) wait_bar(bar_x0, got_x0);
   if (ok && tid == 0) mbar_expect(bar_x0, FB_RECV);  // dA2 arrives in A0
   if (ok) ++iss_x0;
@@ -429,7 +389,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
   if (ok) fwd_epilogue(1, own1);
   if (ok) publish(own1, FB_BLK, bar_x1);
   // z3 = h2 W3^T
-  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.hT[1], tile, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, A.hT[1], tile, fs, warp, lane);
   if (ok) wait_bar(bar_x1, got_x1);
   if (ok && tid == 0) mbar_expect(bar_x1, FB_RECV);  // dA3 arrives in A1
   if (ok) ++iss_x1;
@@ -484,7 +444,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     fb_put_row(own1, trow, cb, hw);
     publish(own1, FB_BLK, bar_x1);
   }
-  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.daT[2], tile, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, A.daT[2], tile, fs, warp, lane);
   // dW4 = sum dz h3 and db4 = sum dz over the tile's rows, this CTA's
   // features of h3 (its block of A0): thread (row group set, 8 features,
   // row in group) with 16-byte loads, the 8 rows of a group added across
@@ -533,15 +493,14 @@ __global__ void __launch_bounds__(FB_THREADS, 1) mlp_train_fb_kernel(FbArgs A, i
     publish(own0, FB_BLK, bar_x0);
   }
   // dH1 = dA2 W2 -> dA1 into this CTA's block of A1 (dA3 there is read)
-  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, stg, A.daT[1], tile, fs, tid);
+  if (ok) copy_out_tiled(smem + FB_A0 + rank * FB_BLK, A.daT[1], tile, fs, warp, lane);
   if (ok) wait_bar(bar_x0, got_x0);
   if (ok) wait_bar(bar_b, got_b);
   if (ok) issue(FB_A0, FB_WB);
   if (ok) wait_bar(bar_m, got_m);
   if (ok) bwd_epilogue(tg1, own1);
   __syncthreads();
-  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, stg, A.daT[0], tile, fs, tid);
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the bulk stores are done
+  if (ok) copy_out_tiled(smem + FB_A1 + rank * FB_BLK, A.daT[0], tile, fs, warp, lane);
 
   if (!ok) {
     if (tid == 0) latch_error(status, kDevTimeout);
