@@ -802,10 +802,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
     const int r1 = min(WG_RB, rall - rb);
     const int row0 = split * R + rb;
     if (ok) {
-      const int q4 = NB / 4;
+      // float4 groups: the 256 weight columns of a wide layer (its ones block
+      // contributes only column H, summed below as a scalar), or all 16
+      // columns of the first layer
+      const int q4 = wide ? H / 4 : NB / 4;
       const int ng = r1 * q4;
       for (int g0 = tid; g0 < ng; g0 += 2 * THREADS) {
         float4 v[2][WG_MAX_S];
+        float vb[WG_MAX_S];
+        const bool bias = wide && g0 == tid && tid < r1;  // row tid's bias column, in the same round
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int g = g0 + u * THREADS;
@@ -814,6 +819,18 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_wgrad_kernel(WgArgs G, int*
 #pragma unroll
           for (int q = 0; q < WG_MAX_S; ++q)
             if (q < S) v[u][q] = ld_cluster_f4(map_shared_rank(a, (uint32_t)q));
+        }
+        if (bias) {
+          const uint32_t a = s0 + (uint32_t)((row0 + tid) * LDr + H) * 4u;
+#pragma unroll
+          for (int q = 0; q < WG_MAX_S; ++q)
+            if (q < S)
+              asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(vb[q]) : "r"(map_shared_rank(a, (uint32_t)q)) : "memory");
+          float t = vb[0];
+#pragma unroll
+          for (int q = 1; q < WG_MAX_S; ++q)
+            if (q < S) t += vb[q];
+          rs[tid * LDr + H] = t;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
