@@ -69,26 +69,64 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 // sin r (through r^9) and cos r (through r^10), whose truncation errors on
 // that interval are below 2e-9 and 1.2e-10, and the quadrant rotation by j.
 // Absolute error about one float ulp of the result.
-__device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
-  const float j = rintf(x * 0.63661977236758134f);   // nearest multiple of pi/2
-  float r = fmaf(j, -1.57079637050628662f, x);       // float(pi/2) = pi/2 + 4.371139e-8
-  r = fmaf(j, 4.37113900630947700e-8f, r);
-  const float r2 = r * r;
-  float ps = 2.75573192239858907e-6f;                // 1/9!, -1/7!, 1/5!, -1/3!
-  ps = fmaf(ps, r2, -1.98412698412698413e-4f);
-  ps = fmaf(ps, r2, 8.33333333333333333e-3f);
-  ps = fmaf(ps, r2, -1.66666666666666667e-1f);
-  const float sn = fmaf(ps * r2, r, r);
-  float pc = -2.75573192239858907e-7f;               // -1/10!, 1/8!, -1/6!, 1/4!, -1/2!
-  pc = fmaf(pc, r2, 2.48015873015873016e-5f);
-  pc = fmaf(pc, r2, -1.38888888888888889e-3f);
-  pc = fmaf(pc, r2, 4.16666666666666667e-2f);
-  pc = fmaf(pc, r2, -0.5f);
-  const float cs = fmaf(pc, r2, 1.f);
+namespace cw {
+constexpr float kTwoOverPi = 0.63661977236758134f;
+constexpr float kPio2Hi = 1.57079637050628662f;  // float(pi/2) = pi/2 + 4.371139e-8
+constexpr float kPio2Lo = 4.37113900630947700e-8f;
+constexpr float kS4 = 2.75573192239858907e-6f, kS3 = -1.98412698412698413e-4f,  // 1/9!, -1/7!, 1/5!, -1/3!
+    kS2 = 8.33333333333333333e-3f, kS1 = -1.66666666666666667e-1f;
+constexpr float kC5 = -2.75573192239858907e-7f, kC4 = 2.48015873015873016e-5f,  // -1/10!, 1/8!, -1/6!, 1/4!, -1/2!
+    kC3 = -1.38888888888888889e-3f, kC2 = 4.16666666666666667e-2f, kC1 = -0.5f;
+
+// sin and cos of j (pi/2) + r from sin r, cos r.
+__device__ __forceinline__ void quadrant(float j, float sn, float cs, float* s, float* c) {
   const int q = (int)j;
   const float s1 = (q & 1) ? cs : sn, c1 = (q & 1) ? sn : cs;
   *s = (q & 2) ? -s1 : s1;
   *c = ((q + 1) & 2) ? -c1 : c1;
+}
+}  // namespace cw
+
+__device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
+  const float j = rintf(x * cw::kTwoOverPi);  // nearest multiple of pi/2
+  float r = fmaf(j, -cw::kPio2Hi, x);
+  r = fmaf(j, cw::kPio2Lo, r);
+  const float r2 = r * r;
+  float ps = cw::kS4;
+  ps = fmaf(ps, r2, cw::kS3);
+  ps = fmaf(ps, r2, cw::kS2);
+  ps = fmaf(ps, r2, cw::kS1);
+  const float sn = fmaf(ps * r2, r, r);
+  float pc = cw::kC5;
+  pc = fmaf(pc, r2, cw::kC4);
+  pc = fmaf(pc, r2, cw::kC3);
+  pc = fmaf(pc, r2, cw::kC2);
+  pc = fmaf(pc, r2, cw::kC1);
+  const float cs = fmaf(pc, r2, 1.f);
+  cw::quadrant(j, sn, cs, s, c);
+}
+
+// sincos_cw of two angles at once: the reduction and both series on the
+// packed two-lane FP32 instructions, each lane rounding as the scalar form
+// (the same bits as two sincos_cw calls).
+__device__ __forceinline__ void sincos_cw2(float2 x, float2* s, float2* c) {
+  float2 j = __fmul2_rn(x, make_float2(cw::kTwoOverPi, cw::kTwoOverPi));
+  j.x = rintf(j.x);
+  j.y = rintf(j.y);
+  float2 r = __ffma2_rn(j, make_float2(-cw::kPio2Hi, -cw::kPio2Hi), x);
+  r = __ffma2_rn(j, make_float2(cw::kPio2Lo, cw::kPio2Lo), r);
+  const float2 r2 = __fmul2_rn(r, r);
+  float2 ps = __ffma2_rn(make_float2(cw::kS4, cw::kS4), r2, make_float2(cw::kS3, cw::kS3));
+  ps = __ffma2_rn(ps, r2, make_float2(cw::kS2, cw::kS2));
+  ps = __ffma2_rn(ps, r2, make_float2(cw::kS1, cw::kS1));
+  const float2 sn = __ffma2_rn(__fmul2_rn(ps, r2), r, r);
+  float2 pc = __ffma2_rn(make_float2(cw::kC5, cw::kC5), r2, make_float2(cw::kC4, cw::kC4));
+  pc = __ffma2_rn(pc, r2, make_float2(cw::kC3, cw::kC3));
+  pc = __ffma2_rn(pc, r2, make_float2(cw::kC2, cw::kC2));
+  pc = __ffma2_rn(pc, r2, make_float2(cw::kC1, cw::kC1));
+  const float2 cs = __ffma2_rn(pc, r2, make_float2(1.f, 1.f));
+  cw::quadrant(j.x, sn.x, cs.x, &s->x, &c->x);
+  cw::quadrant(j.y, sn.y, cs.y, &s->y, &c->y);
 }
 
 // Uniform float in [0, 1) from the top 24 bits of a word (exact in FP32).

@@ -949,7 +949,9 @@ __global__ void reach_map_gate_kernel(ReachArgs A) {
 // Exact IK, one warp per entry; seeds keyed by (candidate, object, try).
 // Entries cost from one check to 100 steps, so warps claim them one at a
 // time (first entry static, the claim for the next issued before solving the
-// current one) from a grid sized to the resident blocks.
+// current one) from a grid sized to the resident blocks. kRight: the signed
+// forward kinematics of arms whose middle twists are +-pi/2 (ArmK::right).
+template <bool kRight>
 __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   const int nf = A.gated ? *(volatile const int*)A.n_ik : 0;  // front part of the IK list
@@ -965,7 +967,8 @@ __global__ void __launch_bounds__(128) reach_ik_kernel(ReachArgs A) {
     const int k = A.st.kc[c], r = A.st.rc[c];
     const ikc::Target T = ikc::load_target(A.targets + 12 * (size_t)i);
     float q[7], pe2, sr, cr;
-    const ikc::Solve s = ikc::warp_solve(A.ik, T, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, lane, q, pe2, sr, cr);
+    const ikc::Solve s =
+        ikc::warp_solve<kRight>(A.ik, T, (uint32_t)c, ((uint32_t)k << 16) | (uint32_t)r, lane, q, pe2, sr, cr);
     ++solves;
     seed_iters += (unsigned long long)s.checks * (unsigned long long)A.ik.seeds;
     __syncwarp();  // every lane has read the state before the winner updates it
@@ -1342,7 +1345,10 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   if (small_blocks < 1) small_blocks = 1;
   const MlpTcWeights gate_w = a.gate ? mlp_tc_weights(a.gate) : MlpTcWeights{};
   int ik_per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ik_per_sm, reach_ik_kernel, 128, 0)) != cudaSuccess) return e;
+  const bool ik_right = a.arm && ra.ik.arm.right;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+           &ik_per_sm, ik_right ? reach_ik_kernel<true> : reach_ik_kernel<false>, 128, 0)) != cudaSuccess)
+    return e;
   const int ik_blocks = num_sms * (ik_per_sm > 0 ? ik_per_sm : 1);
   // ---- rounds. Round i: generation on s reads G[i % 3] (filled by round
   // i-1's generation and round i-2's reach stage) and writes G[(i+1) % 3]
@@ -1397,7 +1403,10 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
       a.timer->end(sr);
       a.timer->begin(2, sr);
     }
-    reach_ik_kernel<<<ik_blocks, 128, 0, sr>>>(ra);
+    if (ik_right)
+      reach_ik_kernel<true><<<ik_blocks, 128, 0, sr>>>(ra);
+    else
+      reach_ik_kernel<false><<<ik_blocks, 128, 0, sr>>>(ra);
     if (a.timer) a.timer->end(sr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ev_reach[i], sr)) != cudaSuccess) return e;

@@ -23,6 +23,9 @@ using namespace ikc;
 // Targets cost from one check to iters steps, so warps claim them one at a
 // time (first target static, the claim for the next issued before solving
 // the current one) from a grid sized to the resident blocks.
+// kRight: the signed forward kinematics of arms whose middle twists are
+// +-pi/2 (ArmK::right).
+template <bool kRight>
 __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -35,7 +38,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
     const Target T = load_target(K.targets + 12 * (size_t)i);
     const uint32_t tid = K.target_ids ? __ldg(&K.target_ids[i]) : (uint32_t)i;
     float q[7], pe2, s, c;
-    const Solve r = warp_solve(K, T, tid, 0u, lane, q, pe2, s, c);
+    const Solve r = warp_solve<kRight>(K, T, tid, 0u, lane, q, pe2, s, c);
     seed_iters += (unsigned long long)r.checks * (unsigned long long)K.seeds;
     if (lane == r.winner) {
       K.reach[i] = r.found;
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(128) ik_kernel(IkArgs K) {
 
 // One DLS step for each (target, configuration) pair: the building block the
 // tests compare against the FP64 step.
+template <bool kRight>
 __global__ void ik_step_kernel(ArmK arm, float lambda2, const float* targets, const float* q_in, int n, float* q_out,
                                float* tool) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -60,17 +64,20 @@ __global__ void ik_step_kernel(ArmK arm, float lambda2, const float* targets, co
     float q[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) q[j] = q_in[7 * (size_t)i + j];
-    float z[7][3], p[7][3], R[9], t[3];
-    fk(arm, q, z, p, R, t);
+    float z[7][3], p[7][3], Rh[9], t[3];
+    fk<kRight>(arm, q, z, p, Rh, t);
     if (tool) {
+      float R[9];
+      tool_rotation(arm, Rh, R);
 #pragma unroll
       for (int j = 0; j < 9; ++j) tool[12 * (size_t)i + j] = R[j];
 #pragma unroll
       for (int j = 0; j < 3; ++j) tool[12 * (size_t)i + 9 + j] = t[j];
     }
+    const Target H = target_frame(arm, T);
     float v[3], c;
-    rot_error(T, R, v, &c);
-    dls_step(arm, lambda2, T, q, z, p, R, t, v);
+    rot_error(H, Rh, v, &c);
+    dls_step(arm, lambda2, H, q, z, p, Rh, t, v);
 #pragma unroll
     for (int j = 0; j < 7; ++j) q_out[7 * (size_t)i + j] = q[j];
   }
@@ -80,8 +87,13 @@ __global__ void ik_step_kernel(ArmK arm, float lambda2, const float* targets, co
 
 int ik_resident_blocks(int num_sms) {
   static int per_sm = 0;
-  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ik_kernel, 128, 0) != cudaSuccess)
-    per_sm = 4;
+  if (per_sm == 0) {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, ik_kernel<false>, 128, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_kernel<true>, 128, 0) != cudaSuccess)
+      a = b = 4;
+    per_sm = a < b ? a : b;
+  }
   return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -108,7 +120,10 @@ cudaError_t launch_ik(const sc_arm& arm, const sc_ik_params& P, const float* tar
   int blocks = (n + warps - 1) / warps;
   const int cap = ik_resident_blocks(num_sms);
   if (blocks > cap) blocks = cap;
-  ik_kernel<<<blocks, threads, 0, s>>>(K);
+  if (K.arm.right)
+    ik_kernel<true><<<blocks, threads, 0, s>>>(K);
+  else
+    ik_kernel<false><<<blocks, threads, 0, s>>>(K);
   return cudaGetLastError();
 }
 
@@ -117,7 +132,11 @@ cudaError_t launch_ik_step(const sc_arm& arm, float lambda, const float* targets
   if (n <= 0) return cudaSuccess;
   int blocks = (n + 127) / 128;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
-  ik_step_kernel<<<blocks, 128, 0, s>>>(make_arm(arm), lambda * lambda, targets, q_in, n, q_out, tool);
+  const ArmK k = make_arm(arm);
+  if (k.right)
+    ik_step_kernel<true><<<blocks, 128, 0, s>>>(k, lambda * lambda, targets, q_in, n, q_out, tool);
+  else
+    ik_step_kernel<false><<<blocks, 128, 0, s>>>(k, lambda * lambda, targets, q_in, n, q_out, tool);
   return cudaGetLastError();
 }
 
