@@ -65,18 +65,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 // sin and cos of a bounded angle (the callers pass yaws the sampler drew in
 // [0, 2 pi) and joint angles clamped to their limits; valid for |x| < 2^20): Cody
 // and Waite's additive range reduction x = j (pi/2) + r with pi/2 split into
-// its float value and the remainder, |r| <= pi/4, then the Taylor series of
-// sin r (through r^9) and cos r (through r^10), whose truncation errors on
-// that interval are below 2e-9 and 1.2e-10, and the quadrant rotation by j.
-// Absolute error about one float ulp of the result.
+// its float value and the remainder, |r| <= pi/4, then minimax polynomials
+// on that interval, sin r = r + r^3 (s1 + s2 r^2 + s3 r^4) (relative error
+// 3.8e-9) and cos r = 1 + r^2 (c1 + ... + c4 r^6) (absolute error 5.4e-11),
+// from a Remez exchange (sincos_minimax.py), and the quadrant rotation by j.
+// Error within 1.5 float ulps of the result.
 namespace cw {
 constexpr float kTwoOverPi = 0.63661977236758134f;
 constexpr float kPio2Hi = 1.57079637050628662f;  // float(pi/2) = pi/2 + 4.371139e-8
 constexpr float kPio2Lo = 4.37113900630947700e-8f;
-constexpr float kS4 = 2.75573192239858907e-6f, kS3 = -1.98412698412698413e-4f,  // 1/9!, -1/7!, 1/5!, -1/3!
-    kS2 = 8.33333333333333333e-3f, kS1 = -1.66666666666666667e-1f;
-constexpr float kC5 = -2.75573192239858907e-7f, kC4 = 2.48015873015873016e-5f,  // -1/10!, 1/8!, -1/6!, 1/4!, -1/2!
-    kC3 = -1.38888888888888889e-3f, kC2 = 4.16666666666666667e-2f, kC1 = -0.5f;
+constexpr float kS1 = -0.16666654609547418f, kS2 = 0.0083321607618011673f, kS3 = -0.00019515283185388041f;
+constexpr float kC1 = -0.49999999725108215f, kC2 = 0.041666623324343622f, kC3 = -0.0013886763794352274f,
+                kC4 = 2.4390450701653411e-5f;
 
 // sin and cos of j (pi/2) + r from sin r, cos r.
 __device__ __forceinline__ void quadrant(float j, float sn, float cs, float* s, float* c) {
@@ -92,14 +92,10 @@ __device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
   float r = fmaf(j, -cw::kPio2Hi, x);
   r = fmaf(j, cw::kPio2Lo, r);
   const float r2 = r * r;
-  float ps = cw::kS4;
-  ps = fmaf(ps, r2, cw::kS3);
-  ps = fmaf(ps, r2, cw::kS2);
+  float ps = fmaf(cw::kS3, r2, cw::kS2);
   ps = fmaf(ps, r2, cw::kS1);
   const float sn = fmaf(ps * r2, r, r);
-  float pc = cw::kC5;
-  pc = fmaf(pc, r2, cw::kC4);
-  pc = fmaf(pc, r2, cw::kC3);
+  float pc = fmaf(cw::kC4, r2, cw::kC3);
   pc = fmaf(pc, r2, cw::kC2);
   pc = fmaf(pc, r2, cw::kC1);
   const float cs = fmaf(pc, r2, 1.f);
@@ -116,12 +112,10 @@ __device__ __forceinline__ void sincos_cw2(float2 x, float2* s, float2* c) {
   float2 r = __ffma2_rn(j, make_float2(-cw::kPio2Hi, -cw::kPio2Hi), x);
   r = __ffma2_rn(j, make_float2(cw::kPio2Lo, cw::kPio2Lo), r);
   const float2 r2 = __fmul2_rn(r, r);
-  float2 ps = __ffma2_rn(make_float2(cw::kS4, cw::kS4), r2, make_float2(cw::kS3, cw::kS3));
-  ps = __ffma2_rn(ps, r2, make_float2(cw::kS2, cw::kS2));
+  float2 ps = __ffma2_rn(make_float2(cw::kS3, cw::kS3), r2, make_float2(cw::kS2, cw::kS2));
   ps = __ffma2_rn(ps, r2, make_float2(cw::kS1, cw::kS1));
   const float2 sn = __ffma2_rn(__fmul2_rn(ps, r2), r, r);
-  float2 pc = __ffma2_rn(make_float2(cw::kC5, cw::kC5), r2, make_float2(cw::kC4, cw::kC4));
-  pc = __ffma2_rn(pc, r2, make_float2(cw::kC3, cw::kC3));
+  float2 pc = __ffma2_rn(make_float2(cw::kC4, cw::kC4), r2, make_float2(cw::kC3, cw::kC3));
   pc = __ffma2_rn(pc, r2, make_float2(cw::kC2, cw::kC2));
   pc = __ffma2_rn(pc, r2, make_float2(cw::kC1, cw::kC1));
   const float2 cs = __ffma2_rn(pc, r2, make_float2(1.f, 1.f));
