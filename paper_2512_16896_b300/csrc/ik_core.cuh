@@ -132,19 +132,20 @@ struct Target {
 };
 
 // The target as rot_error compares it with fk's Rh: R* X^T (X = Rx of the
-// last joint's twist) with its columns times A.gs. With R = R0 X the tool's
-// rotation (R0 = the columns of Rh times A.gs), sum_k r_k x r*_k = R0's
-// columns crossed with R* X^T's (X X^T = I) and likewise the trace, so the
-// errors are those of R against R*. Once per solve.
+// last joint's twist) with its columns times A.gs / 2. With R = R0 X the
+// tool's rotation (R0 = the columns of Rh times A.gs), sum_k r_k x r*_k =
+// R0's columns crossed with R* X^T's (X X^T = I) and likewise the trace, so
+// the errors are those of R against R*; the factor 1/2 of the error and of
+// the cosine is applied here once per solve (exact: a power of two).
 __device__ __forceinline__ Target target_frame(const ArmK& A, const Target& T) {
   const float ca = A.ca[6], sa = A.sa[6];
   Target H;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const float r0 = T.R[3 * r], r1 = T.R[3 * r + 1], r2 = T.R[3 * r + 2];
-    H.R[3 * r] = A.gs[0] * r0;
-    H.R[3 * r + 1] = A.gs[1] * fmaf(ca, r1, -sa * r2);
-    H.R[3 * r + 2] = A.gs[2] * fmaf(sa, r1, ca * r2);
+    H.R[3 * r] = (0.5f * A.gs[0]) * r0;
+    H.R[3 * r + 1] = (0.5f * A.gs[1]) * fmaf(ca, r1, -sa * r2);
+    H.R[3 * r + 2] = (0.5f * A.gs[2]) * fmaf(sa, r1, ca * r2);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) H.p[i] = T.p[i];
@@ -154,9 +155,10 @@ __device__ __forceinline__ Target target_frame(const ArmK& A, const Target& T) {
 // Orientation error of R against the target's R*, in the world frame: w =
 // 1/2 sum_k r_k x r*_k over the columns (|w| = sine of the angle of R^T R*,
 // since w = R vee(M - M^T) / 2 with M = R^T R*), and c = (tr(R^T R*) - 1) / 2
-// = (sum_ij R_ij R*_ij - 1) / 2 (its cosine).
+// = (sum_ij R_ij R*_ij - 1) / 2 (its cosine). T is the target as
+// target_frame gives it, its columns already halved.
 __device__ __forceinline__ void rot_error(const Target& T, const float R[9], float w[3], float* c) {
-  float wx = 0.f, wy = 0.f, wz = 0.f, tr = -1.f;
+  float wx = 0.f, wy = 0.f, wz = 0.f, tr = -0.5f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float ax = R[k], ay = R[3 + k], az = R[6 + k];        // column k of R
@@ -166,10 +168,10 @@ __device__ __forceinline__ void rot_error(const Target& T, const float R[9], flo
     wz = fmaf(ax, by, fmaf(-ay, bx, wz));
     tr = fmaf(ax, bx, fmaf(ay, by, fmaf(az, bz, tr)));
   }
-  w[0] = 0.5f * wx;
-  w[1] = 0.5f * wy;
-  w[2] = 0.5f * wz;
-  *c = 0.5f * tr;
+  w[0] = wx;
+  w[1] = wy;
+  w[2] = wz;
+  *c = tr;
 }
 
 // Success test of one configuration; v (world-frame error), s2 = |v|^2 and c
