@@ -66,12 +66,13 @@ __device__ __forceinline__ void fk(const ArmK& A, const float q[7], float z[7][3
                                    float t[3]) {
   float sq[7], cq[7];
 #pragma unroll
-  for (int i = 0; i < 7; i += 2) {
+  for (int i = 0; i < 6; i += 2) {  // joints in pairs, the seventh alone
     float2 s2, c2;
-    sincos_cw2(make_float2(q[i], q[i + 1 < 7 ? i + 1 : i]), &s2, &c2);
+    sincos_cw2(make_float2(q[i], q[i + 1]), &s2, &c2);
     sq[i] = s2.x; cq[i] = c2.x;
-    if (i + 1 < 7) { sq[i + 1] = s2.y; cq[i + 1] = c2.y; }
+    sq[i + 1] = s2.y; cq[i + 1] = c2.y;
   }
+  sincos_cw(q[6], &sq[6], &cq[6]);
   z[0][0] = 0.f; z[0][1] = 0.f; z[0][2] = 1.f;
   p[0][0] = 0.f; p[0][1] = 0.f; p[0][2] = 0.f;
   const float ca0 = A.ca[0], sa0 = A.sa[0];
