@@ -418,7 +418,7 @@ sc_status sc_generate(sc_ctx* ctx, const sc_scene_batch* batch, const sc_gen_par
     a.ext_rel = (batch->n_parts > 0 || batch->n_tri > 0) ? 2 : ctx->ext_rel ? 1 : 0;
   }
   if (a.reach_objects > 0) {  // side streams and events of the rounds
-    const size_t need_ev = 3 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;
+    const size_t need_ev = 2 * (size_t)sc::generate_rounds(a.reach_objects, params->max_retries) + 1;
     for (int j = 0; j < 2; ++j) {
       if (!ctx->side[j]) {
         cudaError_t e = cudaStreamCreateWithFlags(&ctx->side[j], cudaStreamNonBlocking);

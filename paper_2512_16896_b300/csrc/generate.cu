@@ -831,9 +831,7 @@ struct ReachArgs {
                          // targets likeliest to run every iteration
   int* n_ik;             // [2]: front and back counts
   int ik_cap;
-  int32_t* list_rej;     // the round after next, list A: retries of the gate's rejections
-  int* n_rej;
-  int32_t* list_gen;     // the round after next, list B: IK outcomes (retries and next objects)
+  int32_t* list_gen;     // the round after next: retries and next objects
   int* n_gen;
   unsigned int* claim;   // IK work counter of the round (zeroed at init)
   const uint2* map_counts;  // 4D reachability map gate (NULL: the surrogate or none)
@@ -901,9 +899,9 @@ __device__ __forceinline__ void gate_route(const ReachArgs& A, int row, bool val
   if (mr) {
     const int leader = __ffs(mr) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(A.n_rej, __popc(mr));
+    if (lane == leader) base = atomicAdd(A.n_gen, __popc(mr));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (retry) A.list_rej[base + __popc(mr & lt)] = c;
+    if (retry) A.list_gen[base + __popc(mr & lt)] = c;
   }
   const unsigned mj = __ballot_sync(0xFFFFFFFFu, rej);
   if (lane == 0 && mj) atomicAdd(&A.stats[3], (unsigned long long)__popc(mj));
@@ -1179,11 +1177,10 @@ int generate_rounds(int reach_objects, int max_retries) {
   return 2 * reach_objects * (max_retries + 1);
 }
 
-// Scratch: round lists A[3] and B[3], reach queues Q[3] and gate-passed
-// lists IK[2] (int32 [n] each), three slots of grasp targets (12 floats);
-// counts (list A and list B lengths per round [NR + 2] each, reach queue
-// lengths per round [NR], the IK list's two part lengths per round [2 NR]);
-// work counters (generation claims per round and list [2 NR], the chained
+// Scratch: round lists G[3], reach queues Q[2] and gate-passed lists IK[2]
+// (int32 [n] each), two slots of grasp targets (12 floats); counts
+// (list lengths per round [NR + 2], reach queue lengths per round [NR], the
+// IK list's two part lengths per round [2 NR]); work counters (generation claims per round, the chained
 // launch's, IK claims per round); the per-candidate state (object, try,
 // alive); the per-call tables (candidate templates, TmplInfo records,
 // inverse edge lengths, world-box frames, triangle chunk balls); then the
@@ -1199,9 +1196,9 @@ static GenScratch gen_scratch_layout(const sc_scene_batch& b, int n_items, int m
   const size_t NR = (size_t)generate_rounds(b.max_obj, max_retries);
   GenScratch L;
   L.lists = 0;
-  L.counts = up(L.lists + 11 * n * sizeof(int32_t) + 3 * 12 * n * sizeof(float));
-  L.counters = up(L.counts + (2 * (NR + 2) + 3 * NR) * sizeof(int));
-  L.kc = up(L.counters + (3 * NR + 1) * sizeof(unsigned int));
+  L.counts = up(L.lists + 7 * n * sizeof(int32_t) + 2 * 12 * n * sizeof(float));
+  L.counters = up(L.counts + ((NR + 2) + 3 * NR) * sizeof(int));
+  L.kc = up(L.counters + (2 * NR + 1) * sizeof(unsigned int));
   L.rc = up(L.kc + (size_t)b.n_cand);
   L.alive = up(L.rc + (size_t)b.n_cand * sizeof(uint16_t));
   L.cand_t = up(L.alive + (size_t)b.n_cand);
@@ -1238,28 +1235,26 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   // the rest run in one chained launch
   const int k_begin = reach ? (a.reach_objects < K ? a.reach_objects : K) : 0;
   const int NR = generate_rounds(k_begin, R);
-  if (k_begin > 0 && (a.n_events < 3 * NR + 1 || !a.side[0] || !a.side[1])) {
+  if (k_begin > 0 && (a.n_events < 2 * NR + 1 || !a.side[0] || !a.side[1])) {
     *why = "internal: too few events or side streams for the rounds";
     return cudaErrorInvalidValue;
   }
   const GenScratch SL = gen_scratch_layout(b, n, R);
   char* sb = static_cast<char*>(a.scratch);
   int32_t* ib = reinterpret_cast<int32_t*>(sb + SL.lists);
-  int32_t* GA[3] = {ib, ib + n, ib + 2 * (size_t)n};
-  int32_t* GB[3] = {ib + 3 * (size_t)n, ib + 4 * (size_t)n, ib + 5 * (size_t)n};
-  int32_t* Q[3] = {ib + 6 * (size_t)n, ib + 7 * (size_t)n, ib + 8 * (size_t)n};
-  int32_t* IK[2] = {ib + 9 * (size_t)n, ib + 10 * (size_t)n};
-  float* fb = reinterpret_cast<float*>(ib + 11 * (size_t)n);
-  float* targets[3] = {fb, fb + 12 * (size_t)n, fb + 24 * (size_t)n};
+  int32_t* G[3] = {ib, ib + n, ib + 2 * (size_t)n};
+  int32_t* Q[2] = {ib + 3 * (size_t)n, ib + 4 * (size_t)n};
+  int32_t* IK[2] = {ib + 5 * (size_t)n, ib + 6 * (size_t)n};
+  float* fb = reinterpret_cast<float*>(ib + 7 * (size_t)n);
+  float* targets[2] = {fb, fb + 12 * (size_t)n};
   const int NRmax = generate_rounds(K, R);
   int* counts = reinterpret_cast<int*>(sb + SL.counts);
-  const int n_counts = 2 * (NRmax + 2) + 3 * NRmax;
-  int* cnt_a = counts;                        // [NR + 2] (cnt_a[0] = n, set by gen_init_kernel)
-  int* cnt_b = counts + (NRmax + 2);          // [NR + 2]
-  int* cnt_reach = counts + 2 * (NRmax + 2);  // [NR]
-  int* cnt_ik = cnt_reach + NRmax;            // [NR][2]
+  const int n_counts = (NRmax + 2) + 3 * NRmax;
+  int* cnt_gen = counts;                  // [NR + 2]
+  int* cnt_reach = counts + (NRmax + 2);  // [NR]
+  int* cnt_ik = cnt_reach + NRmax;        // [NR][2]
   unsigned int* counters = reinterpret_cast<unsigned int*>(sb + SL.counters);
-  const int n_counters = 3 * NRmax + 1;  // generation claims per round and list, the chained launch's, IK claims per round
+  const int n_counters = 2 * NRmax + 1;  // generation claims per round, the chained launch's, IK claims per round
   CandState st;
   st.kc = reinterpret_cast<uint8_t*>(sb + SL.kc);
   st.rc = reinterpret_cast<uint16_t*>(sb + SL.rc);
@@ -1295,7 +1290,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     int blocks = (n + 255) / 256;
     blocks = blocks < num_sms * 4 ? blocks : num_sms * 4;
     if (blocks < 1) blocks = 1;
-    gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, GA[0], counts, n_counts, counters, n_counters,
+    gen_init_kernel<<<blocks, 256, 0, s>>>(b, a.order, n, G[0], counts, n_counts, counters, n_counters,
                                            reinterpret_cast<float4*>(a.poses), a.valid, a.band, a.tries, a.stats,
                                            a.status, st);
     int tmax = b.n_cand > b.n_templates ? b.n_cand : b.n_templates;
@@ -1355,74 +1350,55 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
            &ik_per_sm, ik_right ? reach_ik_kernel<true> : reach_ik_kernel<false>, 128, 0)) != cudaSuccess)
     return e;
   const int ik_blocks = num_sms * (ik_per_sm > 0 ? ik_per_sm : 1);
-  // ---- rounds. Round i's candidates come in two lists: A[i % 3] (filled by
-  // round i-1's generation and the gate of round i-2: collision retries,
-  // next non-reach objects, retries of gate rejections) and B[i % 3] (filled
-  // by the IK of round i-2: its retries and next objects). Generation on s
-  // takes list A once the gate of round i-2 is done, so it runs while that
-  // round's IK is still solving, then list B after the IK; both append to
-  // the next round's list A and to the reach queue Q[i % 3]. The reach stage
-  // of round i runs on side stream i % 2 after both: the gate (rejections to
-  // A[(i+2) % 3]), then IK (outcomes to B[(i+2) % 3]). Every candidate is in
-  // one list at a time and a try depends only on its candidate's state, so
-  // the order of the launches changes no result.
+  // ---- rounds. Round i: generation on s reads G[i % 3] (filled by round
+  // i-1's generation and round i-2's reach stage) and writes G[(i+1) % 3]
+  // and the reach queue Q[i % 2]; the reach stage of round i runs on side
+  // stream i % 2 after it and writes G[(i+2) % 3]. Generation of round i
+  // waits for the reach stage of round i-2, so reach stages overlap the next
+  // rounds' generation and each other.
   cudaEvent_t* ev_gen = a.events + 1;
-  cudaEvent_t* ev_gate = a.events + 1 + NR;
-  cudaEvent_t* ev_reach = a.events + 1 + 2 * NR;
+  cudaEvent_t* ev_reach = a.events + 1 + NR;
   if (NR > 0) {
     if ((e = cudaEventRecord(a.events[0], s)) != cudaSuccess) return e;
     for (int j = 0; j < 2; ++j)
       if ((e = cudaStreamWaitEvent(a.side[j], a.events[0], 0)) != cudaSuccess) return e;
   }
-  auto round_launch = [&](const GenStepArgs& gr) {
+  for (int i = 0; i < NR; ++i) {
+    if (i >= 2 && (e = cudaStreamWaitEvent(s, ev_reach[i - 2], 0)) != cudaSuccess) return e;
+    g.list_in = G[i % 3];
+    g.n_in = cnt_gen + i;
+    g.list_gen = G[(i + 1) % 3];
+    g.n_gen = cnt_gen + i + 1;
+    g.list_reach = Q[i % 2];
+    g.n_reach = cnt_reach + i;
+    g.targets = targets[i % 2];  // free: this round waited for the reach stage of round i - 2
+    g.counter = counters + i;
     if (a.timer) a.timer->begin(0, s);
     switch (cfg.a_per_lane) {
-      case 1: launch_round<1>(gr, a.ext_rel, grid, cfg.threads, smem, s); break;
-      case 2: launch_round<2>(gr, a.ext_rel, grid, cfg.threads, smem, s); break;
-      default: launch_round<4>(gr, a.ext_rel, grid, cfg.threads, smem, s); break;
+      case 1: launch_round<1>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
+      case 2: launch_round<2>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
+      default: launch_round<4>(g, a.ext_rel, grid, cfg.threads, smem, s); break;
     }
     if (a.timer) a.timer->end(s);
-    return cudaGetLastError();
-  };
-  for (int i = 0; i < NR; ++i) {
-    g.list_gen = GA[(i + 1) % 3];
-    g.n_gen = cnt_a + i + 1;
-    g.list_reach = Q[i % 3];
-    g.n_reach = cnt_reach + i;
-    g.targets = targets[i % 3];  // free: the reach stage of round i - 3 ended before list B of round i - 1
-    if (i >= 2 && (e = cudaStreamWaitEvent(s, ev_gate[i - 2], 0)) != cudaSuccess) return e;
-    g.list_in = GA[i % 3];
-    g.n_in = cnt_a + i;
-    g.counter = counters + 2 * i;
-    if ((e = round_launch(g)) != cudaSuccess) return e;
-    if (i >= 2) {
-      if ((e = cudaStreamWaitEvent(s, ev_reach[i - 2], 0)) != cudaSuccess) return e;
-      g.list_in = GB[i % 3];
-      g.n_in = cnt_b + i;
-      g.counter = counters + 2 * i + 1;
-      if ((e = round_launch(g)) != cudaSuccess) return e;
-    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ev_gen[i], s)) != cudaSuccess) return e;
     cudaStream_t sr = a.side[i % 2];
     if ((e = cudaStreamWaitEvent(sr, ev_gen[i], 0)) != cudaSuccess) return e;
-    ra.list_reach = Q[i % 3];
+    ra.list_reach = Q[i % 2];
     ra.n_reach = cnt_reach + i;
-    ra.targets = targets[i % 3];
+    ra.targets = targets[i % 2];
     ra.list_ik = IK[i % 2];
     ra.n_ik = cnt_ik + 2 * i;
     ra.ik_cap = n;
-    ra.list_rej = GA[(i + 2) % 3];
-    ra.n_rej = cnt_a + i + 2;
-    ra.list_gen = GB[(i + 2) % 3];
-    ra.n_gen = cnt_b + i + 2;
-    ra.claim = counters + 2 * NRmax + 1 + i;
+    ra.list_gen = G[(i + 2) % 3];
+    ra.n_gen = cnt_gen + i + 2;
+    ra.claim = counters + NRmax + 1 + i;
     if (a.timer) a.timer->begin(1, sr);
     if (a.map_counts) reach_map_gate_kernel<<<small_blocks, 256, 0, sr>>>(ra);
     if (a.gate) {  // gate forward pass and decision in one launch
       e = launch_mlp_tc(gate_w, GateIO{ra}, n, a.status, num_sms, sr);
       if (e != cudaSuccess) return e;
     }
-    if ((e = cudaEventRecord(ev_gate[i], sr)) != cudaSuccess) return e;
     if (a.timer) {
       a.timer->end(sr);
       a.timer->begin(2, sr);
@@ -1445,7 +1421,7 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
     ca.n = n;
     ca.k_begin = k_begin;
     ca.alive = st.alive;
-    ca.counter = counters + 2 * NRmax;
+    ca.counter = counters + NRmax;
     switch (cfg.a_per_lane) {
       case 1: launch_chain<1>(g, ca, a.ext_rel, grid, cfg.threads, smem, s); break;
       case 2: launch_chain<2>(g, ca, a.ext_rel, grid, cfg.threads, smem, s); break;

@@ -91,7 +91,7 @@ struct GenerateLaunch {
   float* q_reach;        // [P][7] IK solution of every reach-checked placed object (may be NULL)
   StageTimer* timer;     // NULL: no timing
   // rounds of the objects with reachability: two side streams for the reach
-  // stages and 3 * generate_rounds(reach_objects, max_retries) + 1 events
+  // stages and 2 * generate_rounds(reach_objects, max_retries) + 1 events
   cudaStream_t side[2];
   cudaEvent_t* events;
   int n_events;
