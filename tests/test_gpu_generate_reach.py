@@ -42,18 +42,25 @@ def ctx(sc):
     c.close()
 
 
-def run(sc, ctx, db, b, seed, gate=None, retries=10, rmap=None, ik=None):
+# an arm with no twist a multiple of pi/2: the reach stage then runs the
+# general forward kinematics instead of the signed right-angle form
+GENERAL_ARM = (*synth.arm_arrays()[:2], np.array([0.3, -1.2, 0.9, 1.4, -0.7, 1.1, 0.5], np.float32),
+               *synth.arm_arrays()[3:])
+
+
+def run(sc, ctx, db, b, seed, gate=None, retries=10, rmap=None, ik=None, arm_arrays=None):
     q = torch.full((db.n_poses, 7), float("nan"), device="cuda")
     order = torch.from_numpy(sc.order_by_work(b)).cuda()
-    arm = sc.make_arm(*synth.arm_arrays())
+    arm = sc.make_arm(*(arm_arrays or synth.arm_arrays()))
     P, V, B, T = sc.generate(ctx, db, seed=seed, max_retries=retries, order=order, arm=arm,
                              ik=sc.ik_params(seed=seed) if ik is None else ik, gate=gate, q_reach=q, rmap=rmap)
     ctx.synchronize()
     return [x.clone() for x in (P, V, B, T, q)]
 
 
-def verify_emitted(b, P, V, q, tol_pos=5e-3, tol_rot=0.05):
+def verify_emitted(b, P, V, q, tol_pos=5e-3, tol_rot=0.05, arm_o=None):
     """Every valid scene: whole-scene collision-free and reach-verified in FP64."""
+    arm_o = arm_o or ARM_O
     P, V, q = P.cpu().numpy().astype(np.float64), V.cpu().numpy(), q.cpu().numpy().astype(np.float64)
     sel = np.nonzero(V)[0].astype(np.int32)
     assert len(sel) > 0
@@ -69,7 +76,7 @@ def verify_emitted(b, P, V, q, tol_pos=5e-3, tol_rot=0.05):
             if b.obj_rel[o0 + k] & synth.REL_REACH:
                 row = offs[c] + k
                 tgt = oracle.grasp_target(P[row], float(b.obj_half[o0 + k, 2]), b.tmpl_base[t])
-                pe, re = oracle.pose_error(ARM_O, q[row], tgt)
+                pe, re = oracle.pose_error(arm_o, q[row], tgt)
                 assert pe <= tol_pos + 1e-5 and re <= tol_rot + 1e-5, (c, k, pe, re)
                 assert np.all(np.abs(q[row]) <= 2.8 + 1e-6)
                 checked += 1
@@ -103,18 +110,20 @@ def band_report(V, B, T, ov, ob, ot, what):
 ZERO_ITER = dict(tol_pos=0.3, tol_rot=1.2, iters=0, seeds=32)
 
 
-@pytest.mark.parametrize("make,seed", [
-    (lambda: synth.ragged(seed=41, n_templates=24, cand_per_template=16, obj_range=(2, 12)), 11),
-    (lambda: synth.hard(seed=42, n_templates=16, cand_per_template=16, obj_range=(3, 8), n_reach=2), 12),
-])
-def test_reach_decisions_exact_at_zero_iterations(sc, ctx, make, seed):
+@pytest.mark.parametrize("make,seed,arm", [
+    (lambda: synth.ragged(seed=41, n_templates=24, cand_per_template=16, obj_range=(2, 12)), 11, None),
+    (lambda: synth.hard(seed=42, n_templates=16, cand_per_template=16, obj_range=(3, 8), n_reach=2), 12, None),
+    (lambda: synth.ragged(seed=41, n_templates=24, cand_per_template=16, obj_range=(2, 12)), 11, GENERAL_ARM),
+], ids=["ragged", "hard", "ragged-general-arm"])
+def test_reach_decisions_exact_at_zero_iterations(sc, ctx, make, seed, arm):
     """iters = 0 (the seeds decide), tolerances 0.3 m / 1.2 rad so that about
     one try in eight reaches: valid flags and try counts equal the oracle's on
     every candidate neither side bands, and emitted scenes are verified."""
     b = make()
     db = sc.DeviceBatch(b)
-    P, V, B, T, q = run(sc, ctx, db, b, seed=seed, ik=sc.ik_params(seed=seed, **ZERO_ITER))
-    op, ov, ob, ot = oracle.generate(b, seed=seed, arm=ARM_O, ikp=oracle.ik_params(seed=seed, **ZERO_ITER))
+    arm_o = oracle.make_arm(*arm) if arm is not None else ARM_O
+    P, V, B, T, q = run(sc, ctx, db, b, seed=seed, ik=sc.ik_params(seed=seed, **ZERO_ITER), arm_arrays=arm)
+    op, ov, ob, ot = oracle.generate(b, seed=seed, arm=arm_o, ikp=oracle.ik_params(seed=seed, **ZERO_ITER))
     gv, gt = V.cpu().numpy(), T.cpu().numpy()
     band = B.cpu().numpy().astype(bool) | ob.astype(bool)
     keep = ~band
@@ -123,7 +132,7 @@ def test_reach_decisions_exact_at_zero_iterations(sc, ctx, make, seed):
     assert np.array_equal(gt[keep], ot[keep]), np.nonzero(gt[keep] != ot[keep])
     assert ov[keep].sum() >= 5 and ov[keep].mean() < 0.98, ov[keep].mean()  # both outcomes occur
     if gv.sum():
-        verify_emitted(b, P, V, q, tol_pos=0.3, tol_rot=1.2)
+        verify_emitted(b, P, V, q, tol_pos=0.3, tol_rot=1.2, arm_o=arm_o)
 
 
 def test_gate_extremes(sc, ctx):

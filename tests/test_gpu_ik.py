@@ -40,25 +40,45 @@ def gpu_arm(sc):
     return sc.make_arm(*synth.arm_arrays())
 
 
-def test_single_dls_step_matches_fp64(sc, ctx):
+# Arms beyond the workload's: the kernels run a signed forward kinematics
+# when the twists of joints 2..6 are all +-pi/2 and the general one
+# otherwise, and fold the last twist into the target in both.
+def _arm_arrays(name):
+    d, a, alpha, qmin, qmax = synth.arm_arrays()
+    if name == "iiwa-like":  # right-angle twists with another sign pattern, the first +-pi/2 and the last 0
+        d = np.array([0.34, 0.0, 0.4, 0.0, 0.4, 0.0, 0.126], np.float32)
+        a = np.zeros(7, np.float32)
+        alpha = np.array([-np.pi / 2, np.pi / 2, np.pi / 2, -np.pi / 2, -np.pi / 2, np.pi / 2, 0.0], np.float32)
+    elif name == "general":  # no twist a multiple of pi/2
+        alpha = np.array([0.3, -1.2, 0.9, 1.4, -0.7, 1.1, 0.5], np.float32)
+    return d, a, alpha, qmin, qmax
+
+
+ARMS = ["workload", "iiwa-like", "general"]
+
+
+@pytest.mark.parametrize("arm", ARMS)
+def test_single_dls_step_matches_fp64(sc, ctx, arm):
+    ref_arm = oracle.make_arm(*_arm_arrays(arm))
     rng = np.random.default_rng(0)
     n = 512
     q = rng.uniform(-2.6, 2.6, (n, 7)).astype(np.float32)
     tg = np.zeros((n, 12), np.float32)
     for i in range(n):  # targets near the configuration's own tool pose
-        F = oracle.fk_frames(ARM_ORACLE, q[i].astype(np.float64))[7]
+        F = oracle.fk_frames(ref_arm, q[i].astype(np.float64))[7]
         from scipy.spatial.transform import Rotation
         Rt = Rotation.from_rotvec(rng.normal(size=3) * 0.2).as_matrix() @ F[:3, :3]
         tg[i, :9] = Rt.ravel()
         tg[i, 9:] = F[:3, 3] + rng.normal(size=3) * 0.05
-    qo, tool = sc.ik_dls_step(ctx, gpu_arm(sc), 0.05, torch.from_numpy(tg).cuda(), torch.from_numpy(q).cuda())
+    qo, tool = sc.ik_dls_step(ctx, sc.make_arm(*_arm_arrays(arm)), 0.05, torch.from_numpy(tg).cuda(),
+                              torch.from_numpy(q).cuda())
     ctx.synchronize()
     qo, tool = qo.cpu().numpy().astype(np.float64), tool.cpu().numpy().astype(np.float64)
     worst_fk, worst_step = 0.0, 0.0
     for i in range(n):
-        F = oracle.fk_frames(ARM_ORACLE, q[i].astype(np.float64))[7]
+        F = oracle.fk_frames(ref_arm, q[i].astype(np.float64))[7]
         worst_fk = max(worst_fk, np.abs(tool[i, 9:] - F[:3, 3]).max(), np.abs(tool[i, :9] - F[:3, :3].ravel()).max())
-        ref = oracle.dls_step(ARM_ORACLE, 0.05, q[i].astype(np.float64), tg[i].astype(np.float64))
+        ref = oracle.dls_step(ref_arm, 0.05, q[i].astype(np.float64), tg[i].astype(np.float64))
         d_ref = ref - q[i]
         d_gpu = qo[i] - q[i]
         worst_step = max(worst_step, np.abs(d_gpu - d_ref).max() / max(1.0, np.abs(d_ref).max()))
@@ -66,13 +86,16 @@ def test_single_dls_step_matches_fp64(sc, ctx):
     assert worst_step <= 1e-4, worst_step
 
 
-def test_reach_labels_agree_and_reachable_is_verified(sc, ctx):
+@pytest.mark.parametrize("arm", ARMS)
+def test_reach_labels_agree_and_reachable_is_verified(sc, ctx, arm):
+    ref_arm = oracle.make_arm(*_arm_arrays(arm))
     tg = synth.topdown_targets(seed=3, n=1024)
     P = sc.ik_params(seed=3)
-    reach, q, err, band = sc.ik_reach(ctx, gpu_arm(sc), P, torch.from_numpy(tg).cuda(), with_band=True)
+    reach, q, err, band = sc.ik_reach(ctx, sc.make_arm(*_arm_arrays(arm)), P, torch.from_numpy(tg).cuda(),
+                                      with_band=True)
     ctx.synchronize()
     reach, q, err = reach.cpu().numpy(), q.cpu().numpy().astype(np.float64), err.cpu().numpy()
-    oreach, oq, oerr, _, oband = oracle.ik_reach(ARM_ORACLE, oracle.ik_params(seed=3), tg, with_band=True)
+    oreach, oq, oerr, _, oband = oracle.ik_reach(ref_arm, oracle.ik_params(seed=3), tg, with_band=True)
     agree = np.mean(reach == oreach)
     assert agree >= 0.99, agree
     banded = band.cpu().numpy().astype(bool) | oband.astype(bool)
@@ -83,12 +106,12 @@ def test_reach_labels_agree_and_reachable_is_verified(sc, ctx):
     assert 0.2 <= reach.mean() <= 0.95, reach.mean()
     # every GPU "reachable" verified in FP64 forward kinematics
     for i in np.nonzero(reach)[0]:
-        pe, re = oracle.pose_error(ARM_ORACLE, q[i], tg[i].astype(np.float64))
+        pe, re = oracle.pose_error(ref_arm, q[i], tg[i].astype(np.float64))
         assert pe <= 5e-3 + 1e-5 and re <= 0.05 + 1e-5, (i, pe, re)
         assert np.all(np.abs(q[i]) <= 2.8 + 1e-6)
     # reported errors are the FK errors of the returned configuration
     for i in range(0, 1024, 37):
-        pe, re = oracle.pose_error(ARM_ORACLE, q[i], tg[i].astype(np.float64))
+        pe, re = oracle.pose_error(ref_arm, q[i], tg[i].astype(np.float64))
         assert abs(err[i, 0] - pe) <= 1e-5 and abs(err[i, 1] - re) <= 1e-3
 
 
@@ -105,15 +128,18 @@ def test_beyond_reach_never_reachable_and_few_seeds(sc, ctx):
     assert np.array_equal(r1.cpu().numpy(), o1)  # no iteration: the seeds themselves decide
 
 
-def test_zero_iterations_exact_outside_the_band(sc, ctx):
+@pytest.mark.parametrize("arm", ARMS)
+def test_zero_iterations_exact_outside_the_band(sc, ctx, arm):
     """Loose tolerances and no step: the seeds decide; labels, band flags and
     the returned seed (lowest succeeding, else least position error) match
     the oracle wherever neither side bands."""
+    ref_arm = oracle.make_arm(*_arm_arrays(arm))
     tg = synth.topdown_targets(seed=9, n=2048)
     kw = dict(tol_pos=0.3, tol_rot=1.2, iters=0, seeds=32, seed=4)
-    r, q, err, band = sc.ik_reach(ctx, gpu_arm(sc), sc.ik_params(**kw), torch.from_numpy(tg).cuda(), with_band=True)
+    r, q, err, band = sc.ik_reach(ctx, sc.make_arm(*_arm_arrays(arm)), sc.ik_params(**kw),
+                                  torch.from_numpy(tg).cuda(), with_band=True)
     ctx.synchronize()
-    o, oq, oerr, _, ob = oracle.ik_reach(ARM_ORACLE, oracle.ik_params(**kw), tg, with_band=True)
+    o, oq, oerr, _, ob = oracle.ik_reach(ref_arm, oracle.ik_params(**kw), tg, with_band=True)
     r, q, band = r.cpu().numpy(), q.cpu().numpy().astype(np.float64), band.cpu().numpy()
     keep = ~(band.astype(bool) | ob.astype(bool))
     assert keep.mean() >= 0.97
