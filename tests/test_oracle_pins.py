@@ -397,15 +397,42 @@ def test_generate_without_retries_equals_whole_scene_check():
 ARM = oracle.make_arm(*synth.arm_arrays())
 
 
-def _dh_scipy(q):
+def _dh_scipy(q, d=synth.ARM_D, a=synth.ARM_A, alpha=synth.ARM_ALPHA):
     T = np.eye(4)
     for i in range(7):
         Rz = np.eye(4); Rz[:3, :3] = Rotation.from_euler("z", q[i]).as_matrix()
-        Tz = np.eye(4); Tz[2, 3] = synth.ARM_D[i]
-        Tx = np.eye(4); Tx[0, 3] = synth.ARM_A[i]
-        Rx = np.eye(4); Rx[:3, :3] = Rotation.from_euler("x", float(np.float32(synth.ARM_ALPHA[i]))).as_matrix()
+        Tz = np.eye(4); Tz[2, 3] = float(np.float32(d[i]))
+        Tx = np.eye(4); Tx[0, 3] = float(np.float32(a[i]))
+        Rx = np.eye(4); Rx[:3, :3] = Rotation.from_euler("x", float(np.float32(alpha[i]))).as_matrix()
         T = T @ Rz @ Tz @ Tx @ Rx
     return T
+
+
+# The workloads' arm has twists 0 and +-pi/2 only, whose cosines or sines
+# vanish; these two make every term of the DH product count.
+OTHER_ARMS = {
+    "iiwa-like": ([0.34, 0.0, 0.4, 0.0, 0.4, 0.0, 0.126], [0.0] * 7,
+                  [-math.pi / 2, math.pi / 2, math.pi / 2, -math.pi / 2, -math.pi / 2, math.pi / 2, 0.0]),
+    "general": (list(synth.ARM_D), list(synth.ARM_A), [0.3, -1.2, 0.9, 1.4, -0.7, 1.1, 0.5]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(OTHER_ARMS))
+def test_fk_and_jacobian_on_other_arms(name):
+    d, a, alpha = OTHER_ARMS[name]
+    f = lambda v: np.array(v, np.float32)
+    arm = oracle.make_arm(f(d), f(a), f(alpha), f([-2.8] * 7), f([2.8] * 7))
+    rng = np.random.default_rng(12)
+    h = 1e-6
+    for q in [np.zeros(7)] + [rng.uniform(-2.8, 2.8, 7) for _ in range(10)]:
+        assert np.allclose(oracle.fk_frames(arm, q)[7], _dh_scipy(q, d, a, alpha), atol=1e-7)
+        J = oracle.jacobian(arm, q)
+        for i in range(7):
+            dq = np.zeros(7); dq[i] = h
+            Fp, Fm = oracle.fk_frames(arm, q + dq)[7], oracle.fk_frames(arm, q - dq)[7]
+            assert np.allclose(J[:3, i], (Fp[:3, 3] - Fm[:3, 3]) / (2 * h), atol=1e-7)
+            assert np.allclose(J[3:, i], Rotation.from_matrix(Fp[:3, :3] @ Fm[:3, :3].T).as_rotvec() / (2 * h),
+                               atol=1e-7)
 
 
 def test_fk_matches_scipy_dh_chain():
