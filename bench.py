@@ -568,6 +568,7 @@ def run_ours(args, wl):
         "stages": {"gen_ms_per_step": gen_rf["ms_per_step"], "ik_ms_per_step": ik_rf["ms_per_step"],
                    "gate_ms_per_step": sum(s["ms_stage"][1] for s in main["stats"]) / len(main["stats"]),
                    "ik_solves_per_step": st0["ik_solves"], "gate_rejections_per_step": st0["gate_rejections"],
+                   "reach_bound_rejections_per_step": st0["reach_bound_rejections"],
                    "sphere_pairs_per_step": st0["sphere_pairs"], "cull_tests_per_step": st0["cull_tests"],
                    "point_triangle_per_step": st0["sphere_tri_pairs"],
                    "exhaustive_pairs_per_step": st0["exhaustive_pairs"],

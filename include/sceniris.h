@@ -581,6 +581,11 @@ typedef struct {
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
                                   spheres x all spheres of the objects placed before it) */
   int64_t sphere_tri_pairs;    /* point-triangle distances: ball culls and exact sphere distances */
+  int64_t reach_bound_rejections; /* collision-free tries of reach-flagged objects whose grasp target
+                                     lies beyond the arm's reach (|a_0| + sum of sqrt(a_i^2 + d_i^2)
+                                     over the other links + tol_pos + 1e-4 from the shoulder): they
+                                     fail without the gate or IK, as IK would fail them (no check
+                                     within the band) */
 } sc_gen_stats;
 sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured

@@ -46,14 +46,16 @@ class ScSampleParams(ctypes.Structure):
 class ScGenStats(ctypes.Structure):
     _fields_ = [("sphere_pairs", I64), ("sphere_box_pairs", I64), ("ik_solves", I64), ("gate_rejections", I64),
                 ("ik_seed_iterations", I64), ("ms_stage", ctypes.c_float * 3), ("launches_stage", I32 * 3),
-                ("cull_tests", I64), ("exhaustive_pairs", I64), ("sphere_tri_pairs", I64)]
+                ("cull_tests", I64), ("exhaustive_pairs", I64), ("sphere_tri_pairs", I64),
+                ("reach_bound_rejections", I64)]
 
     def as_dict(self):
         return {"sphere_pairs": self.sphere_pairs, "sphere_box_pairs": self.sphere_box_pairs,
                 "ik_solves": self.ik_solves, "gate_rejections": self.gate_rejections,
                 "ik_seed_iterations": self.ik_seed_iterations, "ms_stage": list(self.ms_stage),
                 "launches_stage": list(self.launches_stage), "cull_tests": self.cull_tests,
-                "exhaustive_pairs": self.exhaustive_pairs, "sphere_tri_pairs": self.sphere_tri_pairs}
+                "exhaustive_pairs": self.exhaustive_pairs, "sphere_tri_pairs": self.sphere_tri_pairs,
+                "reach_bound_rejections": self.reach_bound_rejections}
 
 
 class ScRmapParams(ctypes.Structure):

@@ -21,7 +21,7 @@ struct sc_ctx {
   void* scratch = nullptr;
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;
-  unsigned long long* d_stats = nullptr;  // [8] (generation); [0..1] and [7] (collision)
+  unsigned long long* d_stats = nullptr;  // [9] (generation); [0..1] and [7] (collision)
   // grow-on-demand scratch of sc_generate (candidate lists and counters)
   void* gen_scratch = nullptr;
   size_t gen_scratch_bytes = 0;
@@ -1017,7 +1017,7 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   if (sc_status s = check_ctx(ctx)) return s;
   if (!out) return fail(SC_ERR_INVALID, "out is NULL");
   DeviceGuard g(ctx->device);
-  unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
   if (!e) e = cudaStreamSynchronize(ctx->stream);
   if (e) return cuda_fail(e, "stats read");
@@ -1030,6 +1030,7 @@ sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out) {
   out->cull_tests = (int64_t)h[5];
   out->exhaustive_pairs = (int64_t)h[6];
   out->sphere_tri_pairs = (int64_t)h[7];
+  out->reach_bound_rejections = (int64_t)h[8];
   if (ctx->timing) {
     for (int i = 0; i < ctx->timer.used; ++i) {
       float ms = 0.f;

@@ -58,6 +58,11 @@ struct GenStepArgs {
   const float4* tri_chunk;  // [tri_chunk_slots] bounding ball (centre, radius) of 32 triangles (world frame)
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, max_retries, seg_len;
+  // reach bound: a grasp target farther than sqrt(reach_r2) from the
+  // shoulder (0, 0, reach_z0) of the arm's base frame fails the exact IK with
+  // no check in its band, so such a try is rejected without the reach stage
+  // (reach_r2 < 0: none)
+  float reach_r2, reach_z0;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
   CandState st;
   const int32_t* list_in;  // this round's candidates
@@ -176,7 +181,7 @@ __device__ __forceinline__ void sweep_block(const float4* astage, int fill, cons
 
 // Work counted by lane 0 of a warp.
 struct TryCounters {
-  unsigned long long pairs = 0, box = 0, cull = 0, exh = 0, tri = 0;
+  unsigned long long pairs = 0, box = 0, cull = 0, exh = 0, tri = 0, far = 0;
 };
 
 struct TryOut {
@@ -609,6 +614,7 @@ __device__ __forceinline__ void add_counters(const GenStepArgs& g, const TryCoun
     atomicAdd(&g.stats[5], cnt.cull);
     atomicAdd(&g.stats[6], cnt.exh);
     if (cnt.tri) atomicAdd(&g.stats[7], cnt.tri);
+    if (cnt.far) atomicAdd(&g.stats[8], cnt.far);
   }
 }
 
@@ -674,10 +680,21 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
       cp_async_commit();
       const TryOut res =
           gen_try<APL, true, MODE>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
-      bool done = false;
-      if (res.pass && g.list_reach && (rel & SC_REL_REACH)) {
+      bool done = false, placed = res.pass;
+      const bool reach_try = placed && g.list_reach && (rel & SC_REL_REACH);
+      if (reach_try && g.reach_r2 >= 0.f) {  // the reach bound: a grasp target no configuration reaches
+        const float4 pk = W.opose[k];
+        const float4 base = __ldg(reinterpret_cast<const float4*>(b.tmpl_base) + t);
+        const float wx = pk.x - base.x, wy = pk.y - base.y;
+        const float wz = pk.z + __ldg(&b.obj_half[4 * (o0 + k) + 2]) - base.z - g.reach_z0;
+        if (wx * wx + wy * wy + wz * wz > g.reach_r2) {
+          placed = false;  // the try fails as an IK rejection would
+          cnt.far += lane == 0;
+        }
+      }
+      if (reach_try && placed) {
         route = kRouteReach;
-      } else if (res.pass) {  // object k placed
+      } else if (placed) {  // object k placed
         done = k + 1 == nt;
         if (!done) route = k + 1 < g.st.k_begin ? kRouteGen : kRouteNone;
       } else if (r < g.max_retries) {
@@ -688,11 +705,11 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
         atomicAdd(&g.tries[c], 1);
         if (done) {
           g.valid[c] = 1;
-        } else if (res.pass && route != kRouteReach) {
+        } else if (placed && route != kRouteReach) {
           g.st.kc[c] = (uint8_t)(k + 1);
           g.st.rc[c] = 0;
           if (route == kRouteNone) g.st.alive[c] = 1;
-        } else if (!res.pass && route == kRouteGen) {
+        } else if (!placed && route == kRouteGen) {
           g.st.rc[c] = (uint16_t)(r + 1);
         }
       }
@@ -1127,7 +1144,7 @@ __global__ void gen_init_kernel(sc_scene_batch b, const int32_t* order, int n, i
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += stride) counts[i] = (i == 0) ? n : 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counters; i += stride) counters[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x < 8 && stats) stats[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 9 && stats) stats[threadIdx.x] = 0;
 }
 
 template <int APL, int MODE>
@@ -1311,6 +1328,21 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.seed = a.seed_dev;
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
+  g.reach_r2 = -1.f;
+  g.reach_z0 = 0.f;
+  if (reach) {
+    // every frame origin of the chain, and the tool, lies within |a_0| + the
+    // sum over the other links of sqrt(a_i^2 + d_i^2) of (0, 0, d_0) (link i
+    // adds a_i x_i + d_i z_i, x_i perpendicular to z_i); beyond that plus
+    // tol_pos the position error exceeds tol_pos by more than the band's 1e-5
+    // (the 1e-4 margin also covers FP32 rounding)
+    double rmax = fabs((double)a.arm->dh_a[0]);
+    for (int i = 1; i < 7; ++i)
+      rmax += sqrt((double)a.arm->dh_a[i] * a.arm->dh_a[i] + (double)a.arm->dh_d[i] * a.arm->dh_d[i]);
+    const double bound = rmax + (double)a.ik->tol_pos + 1e-4;
+    g.reach_r2 = (float)(bound * bound);
+    g.reach_z0 = a.arm->dh_d[0];
+  }
   g.max_sk = max_sk;
   g.seg_len = cfg.seg_len;
   g.st = st;
