@@ -519,6 +519,36 @@ def test_ik_reaches_fk_targets_and_never_beyond_reach():
     assert reach.sum() == 0
 
 
+@pytest.mark.parametrize("name", ["workload"] + sorted(OTHER_ARMS))
+def test_reach_bound_of_the_generation_rounds(name):
+    """The rounds reject a try whose grasp target lies farther than
+    |a_0| + sum_{i>0} sqrt(a_i^2 + d_i^2) + tol_pos + 1e-4 from (0, 0, d_0):
+    the tool never leaves that ball (every link adds a_i x_i + d_i z_i with
+    x_i perpendicular to z_i), and targets just beyond it are unreachable and
+    unbanded for the exact IK."""
+    if name == "workload":
+        d, a, alpha = synth.ARM_D, synth.ARM_A, synth.ARM_ALPHA
+    else:
+        d, a, alpha = OTHER_ARMS[name]
+    f = lambda v: np.array(v, np.float32)
+    arm = oracle.make_arm(f(d), f(a), f(alpha), f([-2.8] * 7), f([2.8] * 7))
+    d32, a32 = f(d).astype(np.float64), f(a).astype(np.float64)
+    rmax = abs(a32[0]) + np.sum(np.sqrt(a32[1:] ** 2 + d32[1:] ** 2))
+    shoulder = np.array([0.0, 0.0, d32[0]])
+    rng = np.random.default_rng(13)
+    far_q = max(np.linalg.norm(oracle.fk_frames(arm, q)[7][:3, 3] - shoulder)
+                for q in rng.uniform(-2.8, 2.8, (2000, 7)))
+    assert far_q <= rmax + 1e-9 and far_q >= 0.9 * rmax  # the ball bounds the tool, not loosely
+    tol_pos = 5e-3
+    n = 64
+    u = rng.normal(size=(n, 3)); u /= np.linalg.norm(u, axis=1, keepdims=True)
+    pos = shoulder + u * (rmax + tol_pos + 1e-4 + rng.uniform(0.0, 2e-3, (n, 1)))
+    rot = Rotation.random(n, random_state=7).as_matrix().reshape(n, 9)
+    tg = np.concatenate([rot, pos], axis=1).astype(np.float32)
+    reach, _, _, _, band = oracle.ik_reach(arm, oracle.ik_params(seeds=8, iters=100), tg, with_band=True)
+    assert reach.sum() == 0 and band.sum() == 0
+
+
 def _seed_q(seed, target, s, hi=0):
     """Seed s of a target as the documented draw: q_j = qmin + (qmax - qmin) u_j,
     u = (w >> 8) 2^-24 of Philox4x32-10 word j % 4 at counter (target, s, j / 4,
