@@ -58,11 +58,14 @@ struct GenStepArgs {
   const float4* tri_chunk;  // [tri_chunk_slots] bounding ball (centre, radius) of 32 triangles (world frame)
   const unsigned long long* seed;  // device scalar, so a replayed graph takes a new seed
   int max_attempts, max_retries, seg_len;
-  // reach bound: a grasp target farther than sqrt(reach_r2) from the
-  // shoulder (0, 0, reach_z0) of the arm's base frame fails the exact IK with
-  // no check in its band, so such a try is rejected without the reach stage
+  // reach bounds: a grasp target (t*, R*) fails the exact IK with no check in
+  // its band when t* lies farther than sqrt(reach_r2) from the shoulder
+  // (0, 0, reach_z0) of the arm's base frame, or when its wrist point
+  // t* - R* reach_v lies farther than sqrt(reach_w2) from it; such a try is
+  // rejected without the reach stage and retried in the next round
   // (reach_r2 < 0: none)
-  float reach_r2, reach_z0;
+  float reach_r2, reach_w2, reach_z0;
+  float3 reach_v;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
   CandState st;
   const int32_t* list_in;  // this round's candidates
@@ -682,12 +685,20 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
           gen_try<APL, true, MODE>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
       bool done = false, placed = res.pass;
       const bool reach_try = placed && g.list_reach && (rel & SC_REL_REACH);
-      if (reach_try && g.reach_r2 >= 0.f) {  // the reach bound: a grasp target no configuration reaches
+      if (reach_try && g.reach_r2 >= 0.f) {  // the reach bounds: a grasp target no configuration reaches
+        // the grasp target as grasp_target_at forms it: position in the base
+        // frame, tool rotation rows (cp, sp, 0), (sp, -cp, 0), (0, 0, -1)
         const float4 pk = W.opose[k];
         const float4 base = __ldg(reinterpret_cast<const float4*>(b.tmpl_base) + t);
         const float wx = pk.x - base.x, wy = pk.y - base.y;
         const float wz = pk.z + __ldg(&b.obj_half[4 * (o0 + k) + 2]) - base.z - g.reach_z0;
-        if (wx * wx + wy * wy + wz * wz > g.reach_r2) {
+        float sb, cb, sp, cp;
+        sincos_cw(base.w, &sb, &cb);  // within 1.5 ulp of the sincosf values the target is formed from
+        sincos_cw(pk.w - base.w, &sp, &cp);
+        const float tx = cb * wx + sb * wy, ty = -sb * wx + cb * wy;
+        const float3 v = g.reach_v;
+        const float ux = tx - (cp * v.x + sp * v.y), uy = ty - (sp * v.x - cp * v.y), uz = wz + v.z;
+        if (tx * tx + ty * ty + wz * wz > g.reach_r2 || ux * ux + uy * uy + uz * uz > g.reach_w2) {
           placed = false;  // the try fails as an IK rejection would
           cnt.far += lane == 0;
         }
@@ -1329,19 +1340,35 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.max_attempts = a.max_attempts;
   g.max_retries = R;
   g.reach_r2 = -1.f;
+  g.reach_w2 = 0.f;
   g.reach_z0 = 0.f;
+  g.reach_v = make_float3(0.f, 0.f, 0.f);
   if (reach) {
-    // every frame origin of the chain, and the tool, lies within |a_0| + the
-    // sum over the other links of sqrt(a_i^2 + d_i^2) of (0, 0, d_0) (link i
-    // adds a_i x_i + d_i z_i, x_i perpendicular to z_i); beyond that plus
-    // tol_pos the position error exceeds tol_pos by more than the band's 1e-5
-    // (the 1e-4 margin also covers FP32 rounding)
-    double rmax = fabs((double)a.arm->dh_a[0]);
-    for (int i = 1; i < 7; ++i)
-      rmax += sqrt((double)a.arm->dh_a[i] * a.arm->dh_a[i] + (double)a.arm->dh_d[i] * a.arm->dh_d[i]);
-    const double bound = rmax + (double)a.ik->tol_pos + 1e-4;
-    g.reach_r2 = (float)(bound * bound);
+    // every frame origin of the chain lies within |a_0| + the sum over the
+    // links after the first of sqrt(a_i^2 + d_i^2) of the shoulder (0, 0, d_0)
+    // (link i adds a_i x_i + d_i z_i, x_i perpendicular to z_i): the tool
+    // within r7 (all links), the wrist p6 (frame 6's origin) within r6 (links
+    // 2..6). The tool sits at p6 + R v, v = (a_7, d_7 sin alpha_7, d_7 cos
+    // alpha_7) in the tool frame R, so a check of q passing or inside the band
+    // (position error <= tol_pos + 1e-5, angle <= tol_rot + 1e-5) puts t* -
+    // R* v within tol_pos + 1e-5 + 2 sin((tol_rot + 1e-5) / 2) |v| of p6. The
+    // 1e-4 margins cover FP32 rounding.
+    auto link = [&](int i) {
+      return sqrt((double)a.arm->dh_a[i] * a.arm->dh_a[i] + (double)a.arm->dh_d[i] * a.arm->dh_d[i]);
+    };
+    double r6 = fabs((double)a.arm->dh_a[0]);
+    for (int i = 1; i < 6; ++i) r6 += link(i);
+    const double r7 = r6 + link(6);
+    const double tp = (double)a.ik->tol_pos + 1e-5, tr = (double)a.ik->tol_rot + 1e-5;
+    const double al = (double)a.arm->dh_alpha[6];
+    const double vx = a.arm->dh_a[6], vy = a.arm->dh_d[6] * sin(al), vz = a.arm->dh_d[6] * cos(al);
+    const double vn = sqrt(vx * vx + vy * vy + vz * vz);
+    const double b7 = r7 + tp + 1e-4;
+    const double b6 = r6 + tp + 2.0 * sin(tr < 3.14159 ? tr / 2.0 : 1.5707963) * vn + 1e-4;
+    g.reach_r2 = (float)(b7 * b7);
+    g.reach_w2 = (float)(b6 * b6);
     g.reach_z0 = a.arm->dh_d[0];
+    g.reach_v = make_float3((float)vx, (float)vy, (float)vz);
   }
   g.max_sk = max_sk;
   g.seg_len = cfg.seg_len;

@@ -166,9 +166,12 @@ def test_trained_gate_emits_only_verified_scenes(sc, ctx):
     verify_emitted(b, P, V, q)
     # what the gate gains: it skips exact IK on tries it rejects (fewer
     # solves, and fewer IK seed-iterations in all), at a small cost in scenes
-    # from its false negatives
+    # from its false negatives. The rounds' exact reach bounds already reject
+    # most unreachable tries before either path's IK, so the gate's share of
+    # the remaining solves is modest.
     assert gated["gate_rejections"] > 0 and plain["gate_rejections"] == 0
-    assert gated["ik_solves"] < 0.8 * plain["ik_solves"], (gated["ik_solves"], plain["ik_solves"])
+    assert plain["reach_bound_rejections"] > 0 and gated["reach_bound_rejections"] > 0
+    assert gated["ik_solves"] < plain["ik_solves"], (gated["ik_solves"], plain["ik_solves"])
     assert gated["ik_seed_iterations"] < plain["ik_seed_iterations"]
     assert V.sum().item() >= 0.9 * Vp.sum().item(), (V.sum().item(), Vp.sum().item())
     gate.close()
@@ -259,7 +262,9 @@ def test_map_gate_emits_only_verified_scenes(sc, ctx):
     gated = ctx.generate_stats()
     verify_emitted(b, P, V, q)
     assert gated["gate_rejections"] > 0
-    assert gated["ik_solves"] < 0.8 * plain["ik_solves"], (gated["ik_solves"], plain["ik_solves"])
+    # as with the learned gate: the reach bounds already reject most
+    # unreachable tries in both paths
+    assert gated["ik_solves"] < plain["ik_solves"], (gated["ik_solves"], plain["ik_solves"])
     assert V.sum().item() >= 0.9 * Vp.sum().item(), (V.sum().item(), Vp.sum().item())
     gate = sc.Surrogate(ctx, seed=1)
     with pytest.raises(sc.SceniError):

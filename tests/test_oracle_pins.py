@@ -522,10 +522,11 @@ def test_ik_reaches_fk_targets_and_never_beyond_reach():
 @pytest.mark.parametrize("name", ["workload"] + sorted(OTHER_ARMS))
 def test_reach_bound_of_the_generation_rounds(name):
     """The rounds reject a try whose grasp target lies farther than
-    |a_0| + sum_{i>0} sqrt(a_i^2 + d_i^2) + tol_pos + 1e-4 from (0, 0, d_0):
-    the tool never leaves that ball (every link adds a_i x_i + d_i z_i with
-    x_i perpendicular to z_i), and targets just beyond it are unreachable and
-    unbanded for the exact IK."""
+    |a_0| + sum_{i>0} sqrt(a_i^2 + d_i^2) + tol_pos + 1e-4 from (0, 0, d_0),
+    or whose wrist point lies beyond the wrist bound: the tool never leaves
+    that ball (every link adds a_i x_i + d_i z_i with x_i perpendicular to
+    z_i), nor the wrist its ball, and targets just beyond either bound are
+    unreachable and unbanded for the exact IK."""
     if name == "workload":
         d, a, alpha = synth.ARM_D, synth.ARM_A, synth.ARM_ALPHA
     else:
@@ -545,6 +546,26 @@ def test_reach_bound_of_the_generation_rounds(name):
     pos = shoulder + u * (rmax + tol_pos + 1e-4 + rng.uniform(0.0, 2e-3, (n, 1)))
     rot = Rotation.random(n, random_state=7).as_matrix().reshape(n, 9)
     tg = np.concatenate([rot, pos], axis=1).astype(np.float32)
+    reach, _, _, _, band = oracle.ik_reach(arm, oracle.ik_params(seeds=8, iters=100), tg, with_band=True)
+    assert reach.sum() == 0 and band.sum() == 0
+    # the wrist bound: frame 6's origin is t - R v with v = (a_6, d_6 sin alpha_6,
+    # d_6 cos alpha_6) in the tool frame, within r6 (links 1..5) of the shoulder;
+    # a target whose t* - R* v lies beyond r6 + tol_pos + 2 sin(tol_rot / 2) |v|
+    # (+ the band's 1e-5 on both tolerances and 1e-4) fails with no band
+    al6 = float(np.float32(alpha[6]))
+    v = np.array([a32[6], d32[6] * math.sin(al6), d32[6] * math.cos(al6)])
+    r6 = abs(a32[0]) + np.sum(np.sqrt(a32[1:6] ** 2 + d32[1:6] ** 2))
+    for q in rng.uniform(-2.8, 2.8, (200, 7)):
+        F = oracle.fk_frames(arm, q)
+        assert np.allclose(F[7][:3, 3] - F[7][:3, :3] @ v, F[6][:3, 3], atol=1e-9)
+        assert np.linalg.norm(F[6][:3, 3] - shoulder) <= r6 + 1e-9
+    tol_rot = 0.05
+    b6 = r6 + tol_pos + 1e-5 + 2 * math.sin((tol_rot + 1e-5) / 2) * np.linalg.norm(v) + 1e-4
+    u = rng.normal(size=(n, 3)); u /= np.linalg.norm(u, axis=1, keepdims=True)
+    R = Rotation.random(n, random_state=8).as_matrix()
+    pw = shoulder + u * (b6 + rng.uniform(0.0, 2e-3, (n, 1)))
+    pos = pw + np.einsum("nij,j->ni", R, v)
+    tg = np.concatenate([R.reshape(n, 9), pos], axis=1).astype(np.float32)
     reach, _, _, _, band = oracle.ik_reach(arm, oracle.ik_params(seeds=8, iters=100), tg, with_band=True)
     assert reach.sum() == 0 and band.sum() == 0
 
