@@ -286,6 +286,32 @@ def run_reference(args, wl):
 # --------------------------------------------------------------------------- GPU arm
 
 
+def in_bound_targets(seed, n, box, ikp):
+    """n top-down targets drawn uniformly over box (base frame) among those the
+    generation rounds' reach bounds keep: the tool within r7 + tol_pos of the
+    shoulder and the wrist point t - R v within r6 + tol_pos + 2 sin(tol_rot / 2)
+    |v| (r6, r7: the summed link lengths up to the wrist and the tool; v: the
+    last link's offset in the tool frame), each with the rounds' 1e-5 + 1e-4."""
+    d, a, alpha = (np.asarray(x, np.float64) for x in synth.arm_arrays()[:3])
+    link = np.sqrt(a ** 2 + d ** 2)
+    r6 = abs(a[0]) + link[1:6].sum()
+    r7 = r6 + link[6]
+    v = np.array([a[6], d[6] * np.sin(alpha[6]), d[6] * np.cos(alpha[6])])
+    tp, tr = ikp.tol_pos + 1e-5, ikp.tol_rot + 1e-5
+    b7, b6 = r7 + tp + 1e-4, r6 + tp + 2.0 * np.sin(tr / 2.0) * np.linalg.norm(v) + 1e-4
+    shoulder = np.array([0.0, 0.0, d[0]])
+    out, got, k = [], 0, 0
+    while got < n:
+        t = synth.topdown_targets(seed=seed * 1000 + k, n=max(n, 65536), box=box)
+        p = t[:, 9:].astype(np.float64)
+        w = p - np.einsum("nij,j->ni", t[:, :9].astype(np.float64).reshape(-1, 3, 3), v)
+        keep = (np.linalg.norm(p - shoulder, axis=1) <= b7) & (np.linalg.norm(w - shoulder, axis=1) <= b6)
+        out.append(t[keep])
+        got += int(keep.sum())
+        k += 1
+    return np.ascontiguousarray(np.concatenate(out)[:n])
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -320,8 +346,9 @@ def run_ours(args, wl):
     if reach and not args.no_gate:
         t0 = time.perf_counter()
         box = ((-0.2, 2.2), (-1.3, 1.3), (0.0, 0.8))  # base-frame region of the workload's grasp targets
-        tr = torch.from_numpy(synth.topdown_targets(seed=seed + 4, n=args.train_labels, box=box)).to(dev)
-        ho = torch.from_numpy(synth.topdown_targets(seed=seed + 5, n=262144, box=box)).to(dev)
+        # the gate only sees tries the rounds' reach bounds keep, so it learns from those
+        tr = torch.from_numpy(in_bound_targets(seed + 4, args.train_labels, box, ikp)).to(dev)
+        ho = torch.from_numpy(in_bound_targets(seed + 5, 262144, box, ikp)).to(dev)
         ytr, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=seed + 4), tr)
         yho, _, _ = sc.ik_reach(ctx, arm, sc.ik_params(seed=seed + 5), ho)
         ctx.synchronize()
@@ -334,6 +361,7 @@ def run_ours(args, wl):
         gate_info = {"train_labels": int(tr.shape[0]), "epochs": args.train_epochs, "final_loss": float(loss[-1]),
                      "tau": tau, "heldout_recall": recall, "heldout_pass_rate": pass_rate,
                      "heldout_reachable": float(yho.float().mean().item()),
+                     "targets": "top-down grasps uniform over the base-frame box, among those the rounds' reach bounds keep",
                      "label_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
                      "train_samples_per_s": int(args.train_epochs * tr.shape[0] / max(t2 - t1, 1e-9))}
         gate_info["vs_reach_map"], rmap = compare_gates(sc, ctx, gate, tr, ytr, ho, yho, recall, pass_rate)
