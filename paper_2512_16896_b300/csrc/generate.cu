@@ -61,9 +61,9 @@ struct GenStepArgs {
   // reach bounds: a grasp target (t*, R*) fails the exact IK with no check in
   // its band when t* lies farther than sqrt(reach_r2) from the shoulder
   // (0, 0, reach_z0) of the arm's base frame, or when its wrist point
-  // t* - R* reach_v lies farther than sqrt(reach_w2) from it; such a try is
-  // rejected without the reach stage and retried in the next round
-  // (reach_r2 < 0: none)
+  // t* - R* reach_v lies farther than sqrt(reach_w2) from it; such a try fails
+  // right after sampling (its collisions are not decided, its outcome does not
+  // depend on them) and is retried in the next round (reach_r2 < 0: none)
   float reach_r2, reach_w2, reach_z0;
   float3 reach_v;
   int max_sk;  // most spheres of one object in the batch (sizes the per-warp B area)
@@ -312,6 +312,25 @@ __device__ __forceinline__ TryOut gen_try(const GenStepArgs& g, const TmplInfo& 
   out.band = r.band;
   if (!r.placed) return out;
   const float4 pk = r.pose;
+  if (PREFETCHED && g.list_reach && (rel & SC_REL_REACH) && g.reach_r2 >= 0.f) {
+    // the reach bounds: the grasp target of this pose no configuration
+    // reaches, so the try fails whatever its collisions (which are then not
+    // decided); the grasp target as grasp_target_at forms it: position in the
+    // base frame, tool rotation rows (cp, sp, 0), (sp, -cp, 0), (0, 0, -1)
+    const float4 base = __ldg(reinterpret_cast<const float4*>(b.tmpl_base) + t);
+    const float wx = pk.x - base.x, wy = pk.y - base.y;
+    const float wz = pk.z + __ldg(&b.obj_half[4 * (o0 + k) + 2]) - base.z - g.reach_z0;
+    float sb, cb, sp, cp;
+    sincos_cw(base.w, &sb, &cb);  // within 1.5 ulp of the sincosf values the target is formed from
+    sincos_cw(pk.w - base.w, &sp, &cp);
+    const float tx = cb * wx + sb * wy, ty = -sb * wx + cb * wy;
+    const float3 v = g.reach_v;
+    const float ux = tx - (cp * v.x + sp * v.y), uy = ty - (sp * v.x - cp * v.y), uz = wz + v.z;
+    if (tx * tx + ty * ty + wz * wz > g.reach_r2 || ux * ux + uy * uy + uz * uz > g.reach_w2) {
+      cnt.far += lane == 0;
+      return out;
+    }
+  }
   const float rk = sqrtf(spec.H.x * spec.H.x + spec.H.y * spec.H.y + spec.H.z * spec.H.z);
   float skn, kcs;
   sincos_cw(pk.w, &skn, &kcs);
@@ -683,27 +702,10 @@ __global__ void __launch_bounds__(256, 3) gen_round_kernel(GenStepArgs g) {
       cp_async_commit();
       const TryOut res =
           gen_try<APL, true, MODE>(g, T, W, t, c, k, r, rel, Sprev, Sk, pbase, seed, g.poses + pbase, lane, cnt);
-      bool done = false, placed = res.pass;
+      bool done = false;
+      const bool placed = res.pass;
       const bool reach_try = placed && g.list_reach && (rel & SC_REL_REACH);
-      if (reach_try && g.reach_r2 >= 0.f) {  // the reach bounds: a grasp target no configuration reaches
-        // the grasp target as grasp_target_at forms it: position in the base
-        // frame, tool rotation rows (cp, sp, 0), (sp, -cp, 0), (0, 0, -1)
-        const float4 pk = W.opose[k];
-        const float4 base = __ldg(reinterpret_cast<const float4*>(b.tmpl_base) + t);
-        const float wx = pk.x - base.x, wy = pk.y - base.y;
-        const float wz = pk.z + __ldg(&b.obj_half[4 * (o0 + k) + 2]) - base.z - g.reach_z0;
-        float sb, cb, sp, cp;
-        sincos_cw(base.w, &sb, &cb);  // within 1.5 ulp of the sincosf values the target is formed from
-        sincos_cw(pk.w - base.w, &sp, &cp);
-        const float tx = cb * wx + sb * wy, ty = -sb * wx + cb * wy;
-        const float3 v = g.reach_v;
-        const float ux = tx - (cp * v.x + sp * v.y), uy = ty - (sp * v.x - cp * v.y), uz = wz + v.z;
-        if (tx * tx + ty * ty + wz * wz > g.reach_r2 || ux * ux + uy * uy + uz * uz > g.reach_w2) {
-          placed = false;  // the try fails as an IK rejection would
-          cnt.far += lane == 0;
-        }
-      }
-      if (reach_try && placed) {
+      if (reach_try) {
         route = kRouteReach;
       } else if (placed) {  // object k placed
         done = k + 1 == nt;
