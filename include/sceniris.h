@@ -508,6 +508,14 @@ typedef struct {
  * seed, block, object << 16 | try)) then decides; an unreachable grasp
  * retries too. Every emitted scene is thus verified by exact collision and
  * exact IK decisions; the gate only skips IK on tries it predicts to fail.
+ * Before any of this, right after the pose is sampled, a try whose grasp
+ * target lies beyond the arm's reach fails without collision checks, gate
+ * or IK: its position farther than |a_0| + sum_{i>0} sqrt(a_i^2 + d_i^2)
+ * + tol_pos from (0, 0, d_0) of the base frame, or its wrist point t - R v
+ * (v = (a_6, d_6 sin alpha_6, d_6 cos alpha_6)) farther than the same sum
+ * over links 1..5 + tol_pos + 2 sin(tol_rot / 2) |v| (each with the band's
+ * 1e-5 and a 1e-4 margin). The exact IK would fail such a target with no
+ * check in its band, so valid flags and tries are those of running it.
  * A 4D reachability map (sc_rmap) can gate instead of the surrogate: the
  * grasp target's map score must reach the map's threshold
  * (sc_rmap_tune_threshold), decided where the target is formed. */
@@ -581,11 +589,9 @@ typedef struct {
   int64_t exhaustive_pairs;    /* sphere pairs of every decision without any cull (object k's
                                   spheres x all spheres of the objects placed before it) */
   int64_t sphere_tri_pairs;    /* point-triangle distances: ball culls and exact sphere distances */
-  int64_t reach_bound_rejections; /* collision-free tries of reach-flagged objects whose grasp target
-                                     lies beyond the arm's reach (|a_0| + sum of sqrt(a_i^2 + d_i^2)
-                                     over the other links + tol_pos + 1e-4 from the shoulder): they
-                                     fail without the gate or IK, as IK would fail them (no check
-                                     within the band) */
+  int64_t reach_bound_rejections; /* tries of reach-flagged objects whose grasp target lies beyond
+                                     the arm's reach (see sc_gen_reach): they fail right after
+                                     sampling, without collision checks, gate or IK */
 } sc_gen_stats;
 sc_status sc_generate_stats(sc_ctx* ctx, sc_gen_stats* out);
 /* Turn per-stage CUDA-event timing of sc_generate on or off (a graph captured
