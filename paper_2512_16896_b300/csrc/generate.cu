@@ -1346,15 +1346,15 @@ cudaError_t enqueue_generate(const sc_scene_batch& b, const GenerateLaunch& a, c
   g.reach_z0 = 0.f;
   g.reach_v = make_float3(0.f, 0.f, 0.f);
   if (reach) {
-    // every frame origin of the chain lies within |a_0| + the sum over the
-    // links after the first of sqrt(a_i^2 + d_i^2) of the shoulder (0, 0, d_0)
-    // (link i adds a_i x_i + d_i z_i, x_i perpendicular to z_i): the tool
-    // within r7 (all links), the wrist p6 (frame 6's origin) within r6 (links
-    // 2..6). The tool sits at p6 + R v, v = (a_7, d_7 sin alpha_7, d_7 cos
-    // alpha_7) in the tool frame R, so a check of q passing or inside the band
-    // (position error <= tol_pos + 1e-5, angle <= tol_rot + 1e-5) puts t* -
-    // R* v within tol_pos + 1e-5 + 2 sin((tol_rot + 1e-5) / 2) |v| of p6. The
-    // 1e-4 margins cover FP32 rounding.
+    // DH rows 0..6. Every frame origin of the chain lies within |a_0| + the
+    // sum over the rows after the first of sqrt(a_i^2 + d_i^2) of the
+    // shoulder (0, 0, d_0) (row i adds a_i x_i + d_i z_i, x_i perpendicular
+    // to z_i): the tool within r7 (rows 1..6), the wrist p6 (origin of frame
+    // 6) within r6 (rows 1..5). The tool sits at p6 + R v, v = (a_6, d_6 sin
+    // alpha_6, d_6 cos alpha_6) in the tool frame R, so a check of q passing
+    // or inside the band (position error <= tol_pos + 1e-5, angle <= tol_rot
+    // + 1e-5) puts t* - R* v within tol_pos + 1e-5 + 2 sin((tol_rot + 1e-5) /
+    // 2) |v| of p6. The 1e-4 margins cover FP32 rounding.
     auto link = [&](int i) {
       return sqrt((double)a.arm->dh_a[i] * a.arm->dh_a[i] + (double)a.arm->dh_d[i] * a.arm->dh_d[i]);
     };
